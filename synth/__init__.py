@@ -1,0 +1,211 @@
+"""Seeded synthetic inputs for the truncated-SVD workloads.
+
+This module only draws random numbers and lays them out; it contains none of
+the method's arithmetic (no Gram products, no power iterations, no deflation).
+Both the FP64 oracle and the GPU library consume the arrays it returns, so the
+two sides always see byte-identical inputs.
+
+Workload shapes follow the paper's synthetic experiments (Sec. V-D, the dense
+and sparse scaling matrices and the out-of-memory sparse run): dense FP32
+matrices with a prescribed spectrum plus Gaussian noise, and CSR matrices with
+uniformly random column positions and U(0,1) values.  The paper uses no public
+dataset; these generators stand in for its randomly generated matrices.
+
+Two back ends exist for the dense generator:
+  * NumPy (CPU), used by the tests and by every size the oracle can handle;
+  * PyTorch on a CUDA device (``dense_lowrank_blocks_torch``), used only to
+    fill very large pinned host buffers quickly.  It is seeded as well, but it
+    draws from torch's device generator, so its values differ from the NumPy
+    back end for the same seed.  The oracle checks such runs on the host
+    buffer that was actually produced, never on a regeneration.
+"""
+from __future__ import annotations
+
+import math
+import numpy as np
+
+__all__ = [
+    "orthonormal_columns",
+    "dense_prescribed",
+    "spectrum_geometric",
+    "spectrum_harmonic",
+    "spectrum_harmonic_clustered",
+    "dense_lowrank_rows",
+    "csr_uniform",
+    "csr_from_dense",
+    "start_normals",
+    "dense_lowrank_blocks_torch",
+]
+
+
+def _rng(seed: int, *stream: int) -> np.random.Generator:
+    """Independent Philox stream per (seed, *stream) tuple."""
+    ss = np.random.SeedSequence([int(seed) & 0xFFFFFFFF, *[int(s) & 0xFFFFFFFF for s in stream]])
+    return np.random.Generator(np.random.Philox(ss))
+
+
+def orthonormal_columns(rows: int, cols: int, seed: int, stream: int = 0) -> np.ndarray:
+    """Q factor of a seeded Gaussian rows x cols matrix (FP64), rows >= cols."""
+    g = _rng(seed, 101, stream).standard_normal((rows, cols))
+    q, r = np.linalg.qr(g)
+    # fix the sign so that the factor is a deterministic function of the seed
+    q *= np.sign(np.diag(r))[None, :]
+    return q
+
+
+def spectrum_geometric(count: int, rho: float) -> np.ndarray:
+    """sigma_i = rho**i, i = 0..count-1 (0-based: sigma_0 = 1)."""
+    return rho ** np.arange(count, dtype=np.float64)
+
+
+def spectrum_harmonic(count: int) -> np.ndarray:
+    """sigma_i = 1/(1+i), i = 0..count-1."""
+    return 1.0 / (1.0 + np.arange(count, dtype=np.float64))
+
+
+def spectrum_harmonic_clustered(count: int, i0: int = 10, gap: float = 1e-3) -> np.ndarray:
+    """Harmonic spectrum whose pair (i0, i0+1) is pulled to an absolute gap."""
+    s = spectrum_harmonic(count)
+    s[i0 + 1] = s[i0] - gap
+    return s
+
+
+def dense_prescribed(m: int, n: int, sigma: np.ndarray, noise: float, seed: int) -> dict:
+    """A = U diag(sigma) V^T + noise * N(0,1), built in FP64, stored as FP32.
+
+    U (m x r) and V (n x r) have orthonormal columns (QR of seeded Gaussians),
+    r = len(sigma) <= min(m, n).  Returns the FP32 matrix (row-major) together
+    with the FP64 construction factors.
+    """
+    sigma = np.asarray(sigma, dtype=np.float64)
+    r = sigma.shape[0]
+    assert r <= min(m, n)
+    U = orthonormal_columns(m, r, seed, 0)
+    V = orthonormal_columns(n, r, seed, 1)
+    A = (U * sigma[None, :]) @ V.T
+    if noise:
+        A += noise * _rng(seed, 202).standard_normal((m, n))
+    return {"A": np.ascontiguousarray(A, dtype=np.float32), "U": U, "V": V, "sigma": sigma}
+
+
+def dense_lowrank_rows(r0: int, r1: int, V: np.ndarray, sigma: np.ndarray, m_total: int,
+                       noise: float, seed: int) -> np.ndarray:
+    """Rows [r0, r1) of a rank-r matrix with a roughly prescribed spectrum.
+
+    Row i is (g_i / sqrt(m_total)) diag(sigma) V^T + noise * e_i, where g_i is a
+    seeded standard-normal r-vector drawn from a stream keyed on the row block,
+    so that any block can be regenerated on its own.  The left factor is only
+    approximately orthonormal (deviation ~ sqrt(r / m_total)); the singular
+    values of the result are therefore taken from the data, never from sigma.
+    """
+    rows = r1 - r0
+    r = sigma.shape[0]
+    g = _rng(seed, 303, r0).standard_normal((rows, r)) / math.sqrt(m_total)
+    A = (g * sigma[None, :]) @ V.T
+    if noise:
+        A += noise * _rng(seed, 404, r0).standard_normal((rows, V.shape[0]))
+    return np.ascontiguousarray(A, dtype=np.float32)
+
+
+def csr_uniform(m: int, n: int, nnz_per_row: float, seed: int, values: str = "uniform") -> dict:
+    """Random CSR matrix: per-row nnz ~ Poisson(nnz_per_row) (capped at n),
+    columns uniform without replacement and sorted, values U(0,1) in FP32.
+
+    row_ptr is int64, col_idx int32, values float32 (the layout the library
+    consumes).  Poisson(n*delta) approximates Binomial(n, delta) for the
+    paper's densities.
+    """
+    rng = _rng(seed, 505)
+    counts = np.minimum(rng.poisson(nnz_per_row, size=m), n).astype(np.int64)
+    row_ptr = np.zeros(m + 1, dtype=np.int64)
+    np.cumsum(counts, out=row_ptr[1:])
+    nnz = int(row_ptr[-1])
+    cols = np.empty(nnz, dtype=np.int64)
+    # draw with replacement, then redraw rows that happen to repeat a column
+    cols[:] = rng.integers(0, n, size=nnz)
+    rows_of = np.repeat(np.arange(m, dtype=np.int64), counts)
+    key = rows_of * n + cols
+    key.sort()
+    dup = np.nonzero(key[1:] == key[:-1])[0]
+    if dup.size:
+        bad_rows = np.unique(key[dup + 1] // n)
+        for rr in bad_rows:
+            a, b = row_ptr[rr], row_ptr[rr + 1]
+            key[a:b] = rr * n + np.sort(rng.choice(n, size=b - a, replace=False))
+    col_idx = (key - rows_of * n).astype(np.int32)
+    if values == "uniform":
+        vals = rng.random(nnz, dtype=np.float32)
+    elif values == "normal":
+        vals = rng.standard_normal(nnz).astype(np.float32)
+    else:
+        raise ValueError(values)
+    return {"row_ptr": row_ptr, "col_idx": col_idx, "values": vals, "m": m, "n": n}
+
+
+def csr_from_dense(A: np.ndarray) -> dict:
+    """Exact CSR image of a dense FP32 matrix (zeros dropped, columns sorted)."""
+    A = np.asarray(A, dtype=np.float32)
+    m, n = A.shape
+    mask = A != 0
+    counts = mask.sum(axis=1).astype(np.int64)
+    row_ptr = np.zeros(m + 1, dtype=np.int64)
+    np.cumsum(counts, out=row_ptr[1:])
+    r, c = np.nonzero(mask)
+    return {"row_ptr": row_ptr, "col_idx": c.astype(np.int32), "values": A[r, c].astype(np.float32),
+            "m": m, "n": n}
+
+
+def start_normals(n: int, k: int, seed: int) -> np.ndarray:
+    """k seeded standard-normal start draws of length n, FP64, column-major (n x k).
+
+    These are the N(0, 1) samples the power method starts from; passing them
+    to both sides makes the GPU path and the oracle follow one trajectory.
+    """
+    x = _rng(seed, 606).standard_normal((k, n))
+    return np.asfortranarray(x.T)
+
+
+def dense_lowrank_blocks_torch(out_host, m: int, n: int, rank: int, sigma: np.ndarray, noise: float,
+                               seed: int, block_rows: int, device="cuda"):
+    """Fill a pinned host FP32 buffer (m x n row-major) with the rank-r plus
+    noise workload, generating each row block on the GPU with torch.
+
+    Left factor: seeded Gaussian (m x r) made orthonormal by two rounds of
+    Cholesky QR over the whole height (the Gaussian stays on the device, 4 B
+    per entry).  Right factor: QR of a seeded Gaussian (n x r).  Each row
+    block is then U_b diag(sigma) V^T + noise * N(0,1), copied to the host.
+    Returns the FP64 factors on the host for reference.
+    """
+    import torch
+    dev = torch.device(device)
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(int(seed) * 1000003 + 17)
+    Ug = torch.randn((m, rank), generator=gen, device=dev, dtype=torch.float32)
+    for _ in range(2):  # CholeskyQR2: U <- U R^{-1}, twice, FP64 Gram
+        W = torch.zeros((rank, rank), dtype=torch.float64, device=dev)
+        for r0 in range(0, m, block_rows):
+            Ub = Ug[r0:r0 + block_rows].double()
+            W += Ub.T @ Ub
+        R = torch.linalg.cholesky(W).T  # upper
+        Rinv = torch.linalg.inv(R)
+        for r0 in range(0, m, block_rows):
+            Ug[r0:r0 + block_rows] = (Ug[r0:r0 + block_rows].double() @ Rinv).float()
+    gv = torch.Generator(device=dev)
+    gv.manual_seed(int(seed) * 1000003 + 29)
+    Vg = torch.randn((n, rank), generator=gv, device=dev, dtype=torch.float64)
+    Vq, Vr = torch.linalg.qr(Vg)
+    Vq = Vq * torch.sign(torch.diagonal(Vr))[None, :]
+    sig = torch.as_tensor(np.asarray(sigma, dtype=np.float64), device=dev)
+    SVt = (sig[:, None] * Vq.T).float()  # r x n
+    gn = torch.Generator(device=dev)
+    gn.manual_seed(int(seed) * 1000003 + 41)
+    buf = torch.empty((block_rows, n), dtype=torch.float32, device=dev)
+    for r0 in range(0, m, block_rows):
+        r1 = min(m, r0 + block_rows)
+        b = buf[: r1 - r0]
+        torch.randn(b.shape, generator=gn, device=dev, dtype=torch.float32, out=b)
+        b.mul_(noise)
+        b.addmm_(Ug[r0:r1], SVt)
+        out_host[r0:r1].copy_(b, non_blocking=False)
+    torch.cuda.synchronize(dev)
+    return {"V": Vq.cpu().numpy(), "sigma": np.asarray(sigma, dtype=np.float64)}
