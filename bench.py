@@ -1,0 +1,418 @@
+"""Benchmark: dense out-of-core truncated SVD (deflated power method) on one GB300.
+
+Workload (the paper's dense synthetic case scaled to this host): A is m x 4096
+FP32 row-major, rank-64 with sigma_i = 1/(1+i) plus 1e-4 N(0,1) noise, stored
+in page-locked host memory in row blocks of 262,144 rows; k = 16, eps = 1e-6.
+m is 13,107,200 rows (200 GiB) when the host can pin it, otherwise the largest
+multiple of 262,144 rows that fits (stated in config.m).
+
+One step = one full t-SVD: Gram pass over A, k power iterations, U pass.
+Metric: A-stream throughput = bytes of A consumed by the t-SVD (two passes,
+2 m n 4 bytes) / t-SVD seconds (higher is better).
+  value : A resident in HBM, outputs on the device, CUDA events on the stream.
+  e2e   : A in pinned host memory, streamed under a 32 GB device budget,
+          outputs copied back to host memory, all copies inside the timed region.
+
+--impl reference runs the FP64 CPU oracle on the host cores over a bounded
+sample of the same workload (one row block per step).
+"""
+from __future__ import annotations
+
+import argparse
+import ctypes as C
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+BLOCK_ROWS = 262_144
+N_COLS = 4096
+RANK = 64
+K = 16
+EPS = 1e-6
+NOISE = 1e-4
+FULL_M = 13_107_200
+BUDGET = 32 * 10 ** 9
+PREC_NAMES = {0: "f32", 1: "tf32", 2: "tf32x3"}
+
+
+def mem_available_bytes() -> int:
+    for line in open("/proc/meminfo"):
+        if line.startswith("MemAvailable:"):
+            return int(line.split()[1]) * 1024
+    return 0
+
+
+def pick_m(requested: int | None) -> int:
+    if requested:
+        return requested
+    avail = mem_available_bytes() - 40 * 2 ** 30
+    blocks = max(1, min(FULL_M // BLOCK_ROWS, avail // (BLOCK_ROWS * N_COLS * 4)))
+    return int(blocks * BLOCK_ROWS)
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm = [float(r[1]) for r in self.rows if len(r) >= 9 and r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if len(r) >= 9 and r[2].replace(".", "").isdigit()]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in self.rows:
+            if len(r) < 9:
+                continue
+            for nm, v in zip(names, r[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        load = [s for s in sm]
+        return {"sm_mhz": statistics.median(load) if load else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(self.rows)}
+
+
+# ----------------------------------------------------------------------------- workload
+def make_host_A(m: int, seed: int):
+    """Pinned host buffer (library allocator) filled on the GPU by the seeded generator."""
+    import torch
+
+    import synth
+    from paper_2208_08410_gb300 import _binding as B
+    ptr = C.c_void_p()
+    B.check(B.tsvd_host_alloc(C.byref(ptr), m * N_COLS * 4), "tsvd_host_alloc")
+    A = np.ctypeslib.as_array(C.cast(ptr, C.POINTER(C.c_float)), shape=(m, N_COLS))
+    At = torch.from_numpy(A)
+    sigma = 1.0 / (1.0 + np.arange(RANK))
+    facts = synth.dense_lowrank_blocks_torch(At, m, N_COLS, RANK, sigma, NOISE, seed, BLOCK_ROWS)
+    return A, ptr, facts
+
+
+def measure_h2d_peak(A: np.ndarray):
+    """Pinned-copy peak: best of 3 copies of 4 GiB from A into HBM (cudaMemcpyAsync via torch)."""
+    import torch
+    rows = min(A.shape[0], BLOCK_ROWS)
+    src = torch.from_numpy(A[:rows])
+    dst = torch.empty((rows, A.shape[1]), dtype=torch.float32, device="cuda")
+    best = 0.0
+    for _ in range(3):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record()
+        dst.copy_(src, non_blocking=True)
+        e1.record()
+        torch.cuda.synchronize()
+        best = max(best, rows * A.shape[1] * 4 / (e0.elapsed_time(e1) / 1e3) / 1e9)
+    del dst
+    return best
+
+
+# ----------------------------------------------------------------------------- runs
+def time_steps(plan, A_in, steps: int, warmup: int, want_u=True):
+    import torch
+    reps = []
+    for _ in range(warmup):
+        plan.factor(A_in, want_u=want_u)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t_wall = time.perf_counter()
+    e0.record()
+    last = None
+    for _ in range(steps):
+        last = plan.factor(A_in, want_u=want_u)
+        reps.append(last.report)
+    e1.record()
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t_wall
+    return e0.elapsed_time(e1) / 1e3, wall, reps, last
+
+
+def reference_arm(args, m: int):
+    """The FP64 oracle timed on the host cores over one row block per step."""
+    import synth
+    from oracle import tsvd_ref as ref
+    rows = args.ref_rows
+    sigma = 1.0 / (1.0 + np.arange(RANK))
+    V = synth.orthonormal_columns(N_COLS, RANK, 0, 1)
+    Ab = synth.dense_lowrank_rows(0, rows, V, sigma, m, NOISE, seed=0)
+    Vk = V[:, :K]
+    sig = sigma[:K]
+    for _ in range(args.warmup):
+        ref.gram(Ab)
+    t = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        ref.gram(Ab)  # Gram accumulation of the block (FP64)
+        _ = (Ab.astype(np.float64) @ Vk) / sig  # left vectors of the block
+        t.append(time.perf_counter() - t0)
+    sec = sum(t) / len(t)
+    value = 2 * rows * N_COLS * 4 / sec / 1e9
+    cores = len(os.sched_getaffinity(0))
+    return {"impl": "reference", "metric": "t-SVD A-stream throughput", "value": round(value, 3), "unit": "GB/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(sec * 1e3, 3), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"dense out-of-core t-SVD, m={m}, n={N_COLS}, k={K}, eps={EPS}", "m": m,
+                       "n": N_COLS, "k": K, "eps": EPS, "block_rows": BLOCK_ROWS},
+            "cpu_baseline": {"value": round(value, 3), "unit": "GB/s", "cores": cores, "kind": "oracle",
+                             "sample": f"one {rows}-row block per step: FP64 Gram + left vectors; power phase "
+                                       f"excluded (O(n^2) per iteration, independent of m)"},
+            "e2e": {"value": round(value, 3), "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def cpu_baseline(m: int, A: np.ndarray, V_gpu: np.ndarray, sig_gpu: np.ndarray, iters, budget_s: float = 25.0):
+    """FP64 oracle on this host: Gram + left vectors timed on one row block, the
+    power phase timed on that block's Gram with the GPU's per-triplet counts;
+    extrapolated to the whole matrix."""
+    from oracle import tsvd_ref as ref
+    rows = min(m, 65_536)
+    Ab = A[:rows]
+    t0 = time.perf_counter()
+    G = ref.gram(Ab)
+    t_gram = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    _ = (Ab.astype(np.float64) @ V_gpu.astype(np.float64)) / sig_gpu
+    t_left = time.perf_counter() - t0
+    # power phase with the same application counts (bounded by the time budget)
+    t0 = time.perf_counter()
+    done = 0
+    sig2 = []
+    Vd = np.zeros((N_COLS, 0))
+    for l, it in enumerate(iters):
+        if time.perf_counter() - t0 > budget_s:
+            break
+        x = np.random.default_rng(l).standard_normal(N_COLS)
+        res = ref.power_method(ref.hotelling_apply(G, Vd, np.array(sig2)), x / np.linalg.norm(x), EPS,
+                               iters_override=int(it))
+        sig2.append(float(res.v @ G @ res.v))
+        Vd = np.concatenate([Vd, res.v[:, None]], axis=1)
+        done += int(it)
+    t_pow = (time.perf_counter() - t0) * (sum(iters) / max(done, 1))
+    blocks = m / rows
+    total = blocks * (t_gram + t_left) + t_pow
+    cores = len(os.sched_getaffinity(0))
+    return {"value": round(2 * m * N_COLS * 4 / total / 1e9, 4), "unit": "GB/s", "cores": cores, "kind": "oracle",
+            "sample": f"FP64 oracle: Gram + left vectors of one {rows}-row block ({t_gram + t_left:.1f} s) scaled "
+                      f"to {m} rows, plus the power phase on that block's Gram with the GPU's {sum(iters)} "
+                      f"applications ({t_pow:.1f} s); est. t-SVD {total:.0f} s"}
+
+
+def parity_full_size(A: np.ndarray, dA, res, prec: int):
+    """Checks at full size on outputs the oracle computes one by one."""
+    import torch
+    from oracle import tsvd_ref as ref
+    from paper_2208_08410_gb300 import _binding as B
+    m, n = A.shape
+    out = {}
+    # sampled Gram entries: 48 random columns, all rows (FP64 oracle) vs the library's Gram
+    rng = np.random.default_rng(7)
+    cols = np.sort(rng.choice(n, size=48, replace=False))
+    G = torch.zeros((n, n), dtype=torch.float64, device="cuda")
+    scr_b = B.tsvd_gram_scratch_bytes(m, n, prec)
+    scr = torch.empty(max(scr_b, 256), dtype=torch.uint8, device="cuda")
+    B.check(B.tsvd_gram_accumulate(dA.data_ptr(), m, n, n, G.data_ptr(), prec, scr.data_ptr(), scr_b,
+                                   torch.cuda.current_stream().cuda_stream), "gram")
+    Gs = G[cols][:, cols].cpu().numpy()
+    del G, scr
+    Gref = np.zeros((48, 48))
+    absref = np.zeros((48, 48))
+    for r0 in range(0, m, 1 << 20):
+        blk = A[r0:r0 + (1 << 20)][:, cols].astype(np.float64)
+        Gref += blk.T @ blk
+        ab = np.abs(blk)
+        absref += ab.T @ ab
+    iu = np.triu_indices(48)
+    relerr = np.abs(Gs[iu] - Gref[iu]) / absref[iu]
+    out["gram_sampled_max_err_over_absgram"] = float(relerr.max())
+    # sigma_l = ||A v_l|| (Alg. 1 l.11-13) from the GPU's v_l, FP64 over all rows
+    V = np.asarray(res.V, dtype=np.float64)
+    AV2 = np.zeros(V.shape[1])
+    for r0 in range(0, m, 1 << 20):
+        AV2 += np.sum((A[r0:r0 + (1 << 20)].astype(np.float64) @ V) ** 2, axis=0)
+    sig_o = np.sqrt(AV2)
+    out["sigma_rel_err_vs_oracle_norm"] = float(np.max(np.abs(np.asarray(res.sigma) - sig_o) / sig_o))
+    out["VtV_offdiag_max"] = float(np.max(np.abs(V.T @ V - np.eye(V.shape[1]))))
+    return out
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--m", type=int, default=0, help="rows (default: largest multiple of 262,144 that fits)")
+    ap.add_argument("--precision", type=int, default=0, help="0 FP32, 1 TF32, 2 TF32x3")
+    ap.add_argument("--ref-rows", type=int, default=65_536)
+    ap.add_argument("--no-parity", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=0)
+    args = ap.parse_args()
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        m = pick_m(args.m)
+        print(json.dumps(reference_arm(args, m)), flush=True)
+        return
+
+    import torch
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_2208_08410_gb300 import Plan, _binding as B
+    B.load(build_if_missing=True)
+
+    m = pick_m(args.m)
+    t0 = time.time()
+    A, hptr, facts = make_host_A(m, seed=rank)
+    gen_s = time.time() - t0
+    h2d_peak = measure_h2d_peak(A)
+    dA = torch.empty((m, N_COLS), dtype=torch.float32, device="cuda")
+    for r0 in range(0, m, BLOCK_ROWS):
+        dA[r0:r0 + BLOCK_ROWS].copy_(torch.from_numpy(A[r0:r0 + BLOCK_ROWS]), non_blocking=True)
+    torch.cuda.synchronize()
+
+    prec = args.precision
+    peaks, peak_src = load_peaks()
+    # ---------------- value: A in HBM
+    plan_dev = Plan(dA, K, EPS, precision=prec, out_device=True, time_kernels=True)
+    clocks = ClockSampler(local)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    sec, wall, reps, res_dev = time_steps(plan_dev, dA, args.steps, args.warmup)
+    clk = clocks.stop()
+    if dist:
+        t = torch.tensor([sec], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        sec = float(t.item())
+    step_s = sec / args.steps
+    bytes_per_step = 2 * m * N_COLS * 4
+    value = world * bytes_per_step / step_s / 1e9
+    launches = int(sum(r["kernel_launches"] for r in reps))
+    gk_ms = sum(r["gram_kernel_ms"] for r in reps)
+    gk_n = sum(r["gram_kernel_launches"] for r in reps)
+    flops_per_step = m * N_COLS * (N_COLS + 1)
+    achieved_tf = flops_per_step * args.steps / (gk_ms / 1e3) / 1e12 if gk_ms > 0 else None
+    if prec == 0:
+        peak = 152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+        roof = {"bound": "alu", "peak_note": "152 SMs x 128 FP32 lanes x 2 flop x max SM clock"}
+    elif prec == 1:
+        peak = peaks["bf16_tflops"] * (1.1 / 2.25)
+        roof = {"bound": "tensor", "peak_note": f"TF32 = bf16 {peak_src} burst x 1.1/2.25 nominal ratio"}
+    else:
+        peak = peaks["bf16_tflops"] * (1.1 / 2.25)
+        roof = {"bound": "tensor", "peak_note": f"TF32 = bf16 {peak_src} burst x 1.1/2.25; 3 MMAs per product"}
+    roofline = {"bound": roof["bound"], "achieved": round(achieved_tf, 2) if achieved_tf else None,
+                "peak": round(peak, 1), "unit": "TFLOP/s",
+                "frac": round(achieved_tf / peak, 4) if achieved_tf else None, "traffic": None,
+                "kernel": "Gram accumulation (SYRK)", "launches_per_step": gk_n / max(args.steps, 1),
+                "algorithmic_flops_per_step": flops_per_step, "peak_source": peak_src + "; " + roof["peak_note"]}
+    plan_dev.close()
+
+    # ---------------- e2e: pinned host A, streamed, outputs to host
+    e2e_steps = args.e2e_steps or args.steps
+    plan_host = Plan(A, K, EPS, precision=prec, device_budget=BUDGET, block_rows=BLOCK_ROWS, force_stream=True)
+    sec_e, wall_e, reps_e, res_host = time_steps(plan_host, A, e2e_steps, max(1, min(args.warmup, 3)))
+    if dist:
+        t = torch.tensor([sec_e], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        sec_e = float(t.item())
+    e2e_step = sec_e / e2e_steps
+    h2d_b = reps_e[-1]["h2d_bytes"]
+    d2h_b = reps_e[-1]["d2h_bytes"]
+    gram_pass_s = reps_e[-1]["gram_ms"] / 1e3
+    e2e = {"value": round(world * bytes_per_step / e2e_step / 1e9, 3), "unit": "GB/s",
+           "h2d_bytes_per_step": int(h2d_b), "d2h_bytes_per_step": int(d2h_b),
+           "ms_per_step": round(e2e_step * 1e3, 2),
+           "h2d": {"gram_pass_GBps": round(m * N_COLS * 4 / gram_pass_s / 1e9, 2),
+                   "pinned_copy_peak_GBps": round(h2d_peak, 2),
+                   "frac_gram_pass": round(m * N_COLS * 4 / gram_pass_s / 1e9 / h2d_peak, 4),
+                   "blocks_per_pass": reps_e[-1]["n_blocks"]}}
+    launches_e = int(sum(r["kernel_launches"] for r in reps_e))
+    plan_host.close()
+
+    parity = None
+    if not args.no_parity and rank == 0:
+        parity = parity_full_size(A, dA, res_dev, prec)
+    cpu = None
+    if not args.no_cpu and rank == 0 and world == 1:
+        sig = np.asarray(res_dev.sigma.cpu().numpy())
+        Vg = res_dev.V.cpu().numpy()
+        cpu = cpu_baseline(m, A, Vg, sig, res_dev.iters)
+
+    if rank == 0:
+        line = {"metric": "t-SVD A-stream throughput", "value": round(value, 3), "unit": "GB/s", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(step_s * 1e3, 2),
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": PREC_NAMES[prec], "data": "synthetic",
+                "config": {"workload": f"dense out-of-core t-SVD (rank-64 + 1e-4 noise), m={m}, n={N_COLS}, "
+                                       f"k={K}, eps={EPS}", "m": m, "n": N_COLS, "k": K, "eps": EPS,
+                           "block_rows": BLOCK_ROWS, "device_budget_bytes_e2e": BUDGET,
+                           "full_m": FULL_M, "host_ram_limited": m < FULL_M,
+                           "l2": "inputs larger than L2 (A is %.0f GiB)" % (m * N_COLS * 4 / 2 ** 30),
+                           "gram_precision": PREC_NAMES[prec], "parallelism": "replicas" if world > 1 else "1 GPU"},
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
+                "gpu_launches": launches, "gpu_launches_e2e": launches_e,
+                "iters": res_dev.iters, "sigma": [round(float(s), 8) for s in np.asarray(res_dev.sigma.cpu())],
+                "parity": parity, "gen_seconds": round(gen_s, 1)}
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+    B.tsvd_host_free(hptr)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,304 @@
+/*
+ * tsvd.h - C ABI of a single-GPU truncated SVD by the deflated power method,
+ * for NVIDIA GB300 (sm_103a).
+ *
+ * Method (arXiv 2208.08410, "Distributed Out-of-Memory SVD on CPU/GPU
+ * Architectures"): Alg. 1 extracts the k leading singular triplets one at a
+ * time; Alg. 2 finds each right singular vector by the power method on the
+ * Gram matrix B = A^T A, stopping when |v0 . v1| >= 1 - eps; Sec. IV (Eq. 1-2)
+ * replaces the explicit residual A - U S V^T by a deflated operator applied to
+ * vectors; Sec. V-C batches row blocks of A from host memory through the GPU
+ * (collinear batching) and overlaps the copies with compute on CUDA streams.
+ *
+ * This library computes, for A (m x n, m >= n):
+ *   B  = sum over row blocks A_b^T A_b          (dense; CSR never forms B)
+ *   for l = 0..k-1:
+ *     v0 = x_l / ||x_l||,  x_l ~ N(0, 1)^n
+ *     repeat  w = B v0 - sum_{j<l} sigma_j^2 v_j (v_j^T v0);  v1 = w / ||w||
+ *     until   |v0 . v1| >= 1 - eps   (FP64), or a forced iteration count
+ *     v_l = v1,  sigma_l = ||A v_l||  (= sqrt(v_l^T B v_l))
+ *   U = A V diag(sigma)^-1            (one extra pass over A)
+ *
+ * Conventions for every entry point:
+ *   - All sizes are element counts unless a name ends in _bytes.
+ *   - Dense matrices are FP32 row-major with a row stride ld >= n (elements).
+ *   - CSR matrices: row_ptr int64 (m+1 absolute offsets, row_ptr[0] == 0),
+ *     col_idx int32 (nnz, each in [0, n)), values FP32 (nnz).
+ *   - "device" pointers are CUDA device memory of the current device;
+ *     "host" pointers are CPU memory (pinned memory is fastest; pageable
+ *     memory works but is flagged in the report).
+ *   - stream arguments are cudaStream_t values passed as void* (NULL means
+ *     the legacy default stream).
+ *   - No call aborts, traps or prints; every failure is a tsvd_status.
+ *   - Memory passed in stays owned by the caller; the library never frees it.
+ *     A plan owns only its own streams, events and small host arrays.
+ */
+#ifndef TSVD_H
+#define TSVD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define TSVD_ABI_VERSION 1
+
+#if defined(__GNUC__)
+#define TSVD_API __attribute__((visibility("default")))
+#else
+#define TSVD_API
+#endif
+
+typedef enum {
+  TSVD_OK = 0,
+  TSVD_EINVAL = 1,       /* invalid argument, descriptor or CSR structure */
+  TSVD_ENOMEM = 2,       /* host allocation failed */
+  TSVD_EBUDGET = 3,      /* device budget / workspace too small for the plan */
+  TSVD_ECUDA = 4,        /* a CUDA runtime call failed (see tsvd_last_cuda_error) */
+  TSVD_ETIMEDOUT = 5,    /* a bounded device or host wait gave up */
+  TSVD_ENOCONV = 6,      /* max_iter reached for some triplet; outputs written */
+  TSVD_ERANK = 7,        /* B v0 vanished (rank(A) < k); outputs written */
+  TSVD_EUNSUPPORTED = 8  /* valid request outside what this build implements */
+} tsvd_status;
+
+typedef enum { TSVD_DENSE_F32_ROWMAJOR = 0, TSVD_CSR_F32_I32_I64 = 1 } tsvd_kind;
+typedef enum { TSVD_HOST = 0, TSVD_DEVICE = 1 } tsvd_location;
+
+/* Arithmetic of the dense Gram accumulation G += A_b^T A_b (Sec. IV, Alg. 3).
+ * The power iteration, deflation scalars, Rayleigh quotient and convergence
+ * test are FP64 in every mode.  FP32: CUDA-core FMA.  TF32: tcgen05 tensor
+ * cores on operands rounded to TF32 (nearest-even), FP32 accumulation.
+ * TF32X3: each operand split a = hi + lo into two TF32 parts, products
+ * hi*hi + hi*lo + lo*hi on tcgen05 (error close to FP32 inputs). */
+typedef enum { TSVD_GRAM_FP32 = 0, TSVD_GRAM_TF32 = 1, TSVD_GRAM_TF32X3 = 2 } tsvd_gram_precision;
+
+/* Matrix descriptor (caller-owned, read-only for the library). */
+typedef struct {
+  int32_t kind;             /* tsvd_kind */
+  int32_t location;         /* tsvd_location of values / row_ptr / col_idx */
+  int64_t m, n;             /* shape of A */
+  int64_t ld;               /* dense: row stride in elements (>= n); CSR: ignored */
+  const float *values;      /* dense: m*ld floats; CSR: nnz floats */
+  const int64_t *row_ptr;   /* CSR: m+1 offsets; dense: NULL */
+  const int32_t *col_idx;   /* CSR: nnz column indices; dense: NULL */
+  int64_t nnz;              /* CSR: number of stored entries; dense: ignored */
+} tsvd_matrix;
+
+/* Options (initialise with tsvd_options_init, then override fields). */
+typedef struct {
+  size_t device_budget;          /* cap on the workspace in bytes (0 = none) */
+  int64_t block_rows;            /* rows per streamed block (0 = planner picks) */
+  int32_t n_buffers;             /* streamed blocks in flight, >= 2 (0 = 3) */
+  int32_t precision;             /* tsvd_gram_precision, dense only */
+  int32_t max_iter;              /* applications per triplet cap (0 = 10000) */
+  int32_t sign_convention;       /* 1: largest-|entry| of each v_l made positive */
+  const int32_t *iters_override; /* host, k counts: exactly that many applications
+                                    per triplet, convergence test off; or NULL */
+  const double *start_draws;     /* host, n x k column-major N(0,1) draws used as
+                                    x_l; NULL = the built-in Philox-4x32-10 stream */
+  uint64_t seed;                 /* seed of the built-in start-vector stream */
+  int32_t out_location;          /* tsvd_location of the U, sigma, V outputs */
+  int32_t force_stream;          /* 1: stream host A even when it would fit */
+  int32_t time_kernels;          /* 1: time each Gram kernel launch with CUDA events
+                                    on the compute stream (report.gram_kernel_ms) */
+  int32_t reserved[5];
+} tsvd_options;
+
+/* Per-call report (all fields written by tsvd_factor). */
+typedef struct {
+  int32_t *iters;           /* caller array of k entries (applications per
+                               triplet), or NULL */
+  int32_t flags;            /* TSVD_FLAG_* bits */
+  int32_t n_blocks;         /* streamed row blocks per pass over A */
+  int32_t mode;             /* 0: A on device, 1: host A made resident, 2: streamed */
+  int32_t gram_kernel_launches; /* Gram kernel launches timed (time_kernels) */
+  double gram_ms;           /* Gram pass (dense) wall time on the device clock */
+  double power_ms;          /* all power iterations */
+  double left_ms;           /* U pass */
+  double total_ms;
+  double h2d_bytes;         /* bytes copied host -> device */
+  double d2h_bytes;         /* bytes copied device -> host */
+  double gram_kernel_ms;    /* summed device time of the Gram kernels (time_kernels) */
+  int64_t kernel_launches;  /* kernels launched by this call */
+  int64_t applications;     /* total operator applications (sum of iters) */
+  double reserved1[4];
+} tsvd_report;
+
+#define TSVD_FLAG_NOCONV 1        /* a triplet hit max_iter */
+#define TSVD_FLAG_RANK 2          /* a triplet found B v0 == 0 */
+#define TSVD_FLAG_NONMONOTONE 4   /* sigma not non-increasing in extraction order */
+#define TSVD_FLAG_PAGEABLE 8      /* host input was not page-locked */
+#define TSVD_FLAG_TIMEOUT 16      /* a bounded wait gave up */
+
+typedef struct tsvd_plan_s *tsvd_plan_t;
+
+/* Static description of a status code; never NULL. */
+TSVD_API const char *tsvd_status_string(tsvd_status s);
+/* Text of the last CUDA error seen by this thread's calls (or ""). */
+TSVD_API const char *tsvd_last_cuda_error(void);
+TSVD_API int32_t tsvd_abi_version(void);
+
+TSVD_API void tsvd_options_init(tsvd_options *opt);
+
+/*
+ * tsvd_plan - validate A, k, eps and the options, choose how A reaches the
+ * GPU (already on the device, copied once, or streamed in row blocks: the
+ * paper's degree-0 / degree-1 out-of-memory cases, Sec. III) and lay out the
+ * device workspace.  Pure host work: no CUDA call, no device memory.
+ *
+ *   out             receives a new plan (library-owned; free with tsvd_destroy)
+ *   A               descriptor; for CSR host matrices the row_ptr is read
+ *                   (validated, and used to size the streamed blocks)
+ *   k               triplets wanted, 1..min(m,n), or -1 for min(m,n) (Alg. 1)
+ *   eps             convergence threshold in (0,1) (ignored with iters_override)
+ *   opt             options or NULL for defaults; arrays it points to are
+ *                   copied into the plan
+ *   workspace_bytes receives the device workspace size tsvd_factor needs
+ *
+ * Errors: EINVAL (k out of range, eps not in (0,1), m or n <= 0, ld < n, bad
+ * CSR: row_ptr not monotone, row_ptr[m] != nnz, a column outside [0,n)),
+ * EUNSUPPORTED (m < n; dense n > 32768), EBUDGET (device_budget below the
+ * minimum workspace), ENOMEM.
+ */
+TSVD_API tsvd_status tsvd_plan(tsvd_plan_t *out, const tsvd_matrix *A, int64_t k, double eps,
+                      const tsvd_options *opt, size_t *workspace_bytes);
+
+/*
+ * tsvd_factor - run the planned t-SVD.  Synchronous: returns when the outputs
+ * are written.
+ *
+ *   plan       from tsvd_plan with the same A shape and kind
+ *   A          the matrix (same descriptor as planned; values may change)
+ *   workspace  device memory of at least workspace_bytes, 256-byte aligned
+ *   stream     CUDA stream for the compute work (copies use the plan's own
+ *              streams and are ordered with events)
+ *   U          m x k FP32 column-major (host or device per opt.out_location),
+ *              or NULL to skip the U pass
+ *   sigma      k FP64 singular values in extraction order (not sorted)
+ *   V          n x k FP32 column-major
+ *   report     optional
+ *
+ * Returns OK, ENOCONV / ERANK (outputs valid, flags in the report), or an
+ * error (EINVAL, EBUDGET, ECUDA, ETIMEDOUT).
+ */
+TSVD_API tsvd_status tsvd_factor(tsvd_plan_t plan, const tsvd_matrix *A, void *workspace,
+                        size_t workspace_bytes, void *stream, float *U, double *sigma,
+                        float *V, tsvd_report *report);
+
+/* Release a plan (NULL is accepted). */
+TSVD_API void tsvd_destroy(tsvd_plan_t plan);
+
+/* ------------------------------------------------------------------------ */
+/* Step-level entry points (each one step of the method, device pointers).   */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * Dense Gram accumulation G += A_b^T A_b for one row block (Alg. 3 with
+ * collinear row batching, Sec. V-C; B = X^T X of Alg. 2).
+ *   dA      device, rows x n FP32 row-major, row stride ld
+ *   dG      device, n x n FP64 row-major; the upper triangle (col >= row)
+ *           receives the sums, the strict lower triangle is not touched
+ *   precision  tsvd_gram_precision
+ *   scratch    device scratch of tsvd_gram_scratch_bytes(rows, n, precision)
+ *              bytes, 256-byte aligned (NULL allowed when that size is 0).
+ *              Its first 4 bytes receive a status word once the kernels
+ *              have run: 0, or nonzero when a bounded wait inside the
+ *              tensor-core kernel gave up (its results are then invalid).
+ * Errors: EINVAL (sizes, ld < n, misaligned scratch), EUNSUPPORTED (a tensor
+ * precision on a device without tcgen05), ECUDA.
+ */
+TSVD_API size_t tsvd_gram_scratch_bytes(int64_t rows, int64_t n, int32_t precision);
+TSVD_API tsvd_status tsvd_gram_accumulate(const float *dA, int64_t rows, int64_t n, int64_t ld, double *dG,
+                                 int32_t precision, void *scratch, size_t scratch_bytes,
+                                 void *stream);
+
+/*
+ * Fused CSR pair for one row block (Alg. 4 l.3-6 on one GPU):
+ *   y_r = sum_p values[p] v[col_idx[p]]   for rows r of the block
+ *   w[c] += values[p] * y_r               (FP32 atomics)
+ *   *ss  += sum_r y_r^2                   (FP64)
+ *   row_ptr  device, rows+1 absolute offsets; entry p of the block is at
+ *            col_idx[p - row_ptr[0]], values[p - row_ptr[0]]
+ *   v, w     device FP32 of length n;  ss device FP64 scalar
+ *   scatter  0: only y and ss (used for sigma = ||A v||), 1: full pair
+ */
+TSVD_API tsvd_status tsvd_csr_gram_apply(int64_t rows, int64_t n, const int64_t *row_ptr,
+                                const int32_t *col_idx, const float *values, const float *v,
+                                float *w, double *ss, int32_t scatter, void *stream);
+
+/*
+ * Deflated power iteration for one triplet on a dense Gram matrix (Alg. 2
+ * l.10-15 with the Hotelling form of Eq. 2), one cooperative kernel that
+ * keeps the convergence loop on the device.
+ *   n        order of G
+ *   G32      device, n x n FP32 symmetric (full square, row-major)
+ *   G64      device, n x n FP64 with the upper triangle valid (for sigma^2)
+ *   V64      device, n x l FP64 column-major earlier vectors (NULL if l == 0)
+ *   sigma2   device, l FP64 earlier sigma^2
+ *   x        device, n FP64: in = start draw (not necessarily normalised),
+ *            out = v_l (unit norm)
+ *   eps, max_iter, iters_override (<= 0: use the convergence test)
+ *   sign_convention  1: make the largest-|entry| positive
+ *   out_sigma2  device FP64 scalar: v_l^T G64 v_l
+ *   info     device int32[4]: {applications, status (0 ok, 1 noconv, 2 rank),
+ *            timeout flag, 0}
+ *   scratch  device, tsvd_power_scratch_bytes(n, l) bytes (zeroing not needed)
+ */
+TSVD_API size_t tsvd_power_scratch_bytes(int64_t n, int64_t l);
+TSVD_API tsvd_status tsvd_power_dense(int64_t n, const float *G32, const double *G64, const double *V64,
+                             const double *sigma2, int64_t l, double *x, double eps,
+                             int32_t max_iter, int32_t iters_override, int32_t sign_convention,
+                             double *out_sigma2, int32_t *info, void *scratch,
+                             size_t scratch_bytes, void *stream);
+
+/* Fill G32 (n x n FP32, full) from the upper triangle of G64 (symmetrise). */
+TSVD_API tsvd_status tsvd_gram_symmetrize(int64_t n, const double *G64, float *G32, void *stream);
+
+/*
+ * Start draw x ~ N(0,1)^n for triplet l (Alg. 2 l.3) from the Philox-4x32-10
+ * stream keyed by splitmix64(seed) (Salmon et al., SC'11), Box-Muller in FP64:
+ * counter (p mod 2^32, p div 2^32, l, 0x54535644) for pair p = i/2.
+ *   x  device FP64, n entries
+ */
+TSVD_API tsvd_status tsvd_start_draws(uint64_t seed, int64_t l, int64_t n, double *x, void *stream);
+
+/* Raw Philox-4x32-10 block function on the device, for checking the
+ * generator: out[4*i .. 4*i+3] = philox(ctr[4*i..], key[2*i..]), count blocks.
+ * ctr, key, out: device uint32 arrays. */
+TSVD_API tsvd_status tsvd_philox4x32_10(const uint32_t *ctr, const uint32_t *key, uint32_t *out,
+                               int64_t count, void *stream);
+
+/*
+ * Left vectors for one row block (Alg. 1 l.11-13): U_b = A_b V diag(sigma)^-1
+ *   dA     device rows x n FP32 row-major (stride ld)
+ *   V      device n x k FP32 column-major (stride ldv >= n)
+ *   sigma  device k FP64; a zero sigma gives a zero column
+ *   U      device, column-major with stride ldu >= rows: U[r + l*ldu]
+ */
+TSVD_API tsvd_status tsvd_left_vectors(const float *dA, int64_t rows, int64_t n, int64_t ld, const float *V,
+                              int64_t ldv, int64_t k, const double *sigma, float *U, int64_t ldu,
+                              void *stream);
+
+/*
+ * CSR row-block partition (Sec. V-C collinear batching), host only: blocks of
+ * block_rows rows, the last one ragged.  block_start receives n_blocks+1 row
+ * indices (caller array of at least ceil(m/block_rows)+1 entries); block
+ * b covers rows [block_start[b], block_start[b+1]) and entries
+ * [row_ptr[block_start[b]], row_ptr[block_start[b+1]]).  *max_block_nnz
+ * receives the largest entry count of a block.
+ */
+TSVD_API tsvd_status tsvd_csr_partition(int64_t m, const int64_t *row_ptr, int64_t block_rows,
+                               int64_t *block_start, int64_t *n_blocks, int64_t *max_block_nnz);
+
+/* Page-locked host memory for A (cudaHostAlloc with portable flag); *ptr is
+ * NULL on failure.  Free with tsvd_host_free. */
+TSVD_API tsvd_status tsvd_host_alloc(void **ptr, size_t bytes);
+TSVD_API tsvd_status tsvd_host_free(void *ptr);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TSVD_H */

@@ -1,0 +1,986 @@
+// Host runtime of the tsvd C ABI: validation, the planner (device workspace
+// layout, degree-0 / degree-1 out-of-memory mode, row-block sizes), the
+// row-block streamer (page-locked host -> device ring on its own copy stream,
+// event hand-off to the compute stream, Sec. V-C and the stream queue of
+// Alg. 3), and the drivers of the three phases: Gram pass (dense), power
+// phase (Alg. 1 loop over l, Alg. 2 per triplet) and the left-vector pass.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+
+namespace tsvd {
+
+// ---------------------------------------------------------------- errors
+static thread_local std::string g_err;
+static thread_local int64_t g_launches = 0;
+
+void set_cuda_error(cudaError_t e, const char *what, const char *file, int line) {
+  char buf[512];
+  snprintf(buf, sizeof buf, "%s: %s (%s:%d)", cudaGetErrorString(e), what, file, line);
+  g_err = buf;
+}
+void set_error_text(const std::string &s) { g_err = s; }
+void count_launch() { ++g_launches; }
+int64_t launches_so_far() { return g_launches; }
+
+tsvd_status device_info(DeviceInfo *out) {
+  static thread_local DeviceInfo cache;
+  int dev = -1;
+  TSVD_CUDA(cudaGetDevice(&dev));
+  if (cache.device != dev) {
+    DeviceInfo d;
+    d.device = dev;
+    TSVD_CUDA(cudaDeviceGetAttribute(&d.sms, cudaDevAttrMultiProcessorCount, dev));
+    TSVD_CUDA(cudaDeviceGetAttribute(&d.cc_major, cudaDevAttrComputeCapabilityMajor, dev));
+    TSVD_CUDA(cudaDeviceGetAttribute(&d.cc_minor, cudaDevAttrComputeCapabilityMinor, dev));
+    int optin = 0;
+    TSVD_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    d.smem_optin = (size_t)optin;
+    cache = d;
+  }
+  *out = cache;
+  return TSVD_OK;
+}
+
+}  // namespace tsvd
+
+using namespace tsvd;
+
+// ---------------------------------------------------------------- plan
+namespace {
+
+enum Mode { MODE_DEVICE = 0, MODE_RESIDENT = 1, MODE_STREAM = 2 };
+
+struct Carve {
+  size_t off = 0;
+  size_t take(size_t bytes) {
+    const size_t o = off;
+    off = (size_t)round_up((int64_t)(off + bytes), 256);
+    return o;
+  }
+};
+
+}  // namespace
+
+struct tsvd_plan_s {
+  // problem
+  int kind = 0, location = 0;
+  int64_t m = 0, n = 0, ld = 0, nnz = 0, k = 0;
+  double eps = 0.0;
+  tsvd_options opt{};
+  std::vector<int32_t> iters_override;
+  std::vector<double> start_draws;
+  // planning
+  int mode = MODE_DEVICE;
+  int64_t chunk_rows = 0, n_chunks = 0;
+  int n_buffers = 3;
+  // CSR partition (rows) and per-block entry counts (host-located CSR)
+  std::vector<int64_t> block_start;
+  int64_t max_block_nnz = 0;
+  double avg_nnz = 0.0;
+  // workspace layout
+  size_t ws = 0;
+  size_t o_G64 = 0, o_G32 = 0, o_V64 = 0, o_V32 = 0, o_sig2 = 0, o_sigma = 0, o_info = 0;
+  size_t o_pscr = 0, b_pscr = 0, o_gscr = 0, b_gscr = 0, o_ring = 0, b_slot = 0;
+  size_t o_res = 0, o_ubuf = 0, b_ubuf = 0;
+  size_t o_v = 0, o_vn = 0, o_w = 0, o_x64 = 0, o_Vr = 0, o_vsc = 0, o_flag = 0;
+  int vec_grid = 0;
+  // runtime objects (created on first factor, on the device current then)
+  int device = -1;
+  cudaStream_t copy_stream = nullptr, d2h_stream = nullptr;
+  std::vector<cudaEvent_t> ev_ready, ev_free;
+  cudaEvent_t ev_u_ready[2] = {nullptr, nullptr}, ev_u_free[2] = {nullptr, nullptr};
+  cudaEvent_t ev_t[4] = {nullptr, nullptr, nullptr, nullptr};
+  std::vector<cudaEvent_t> ev_k;  // pairs around each timed Gram kernel
+};
+
+namespace {
+
+tsvd_status validate_csr_host(const tsvd_matrix *A) {
+  const int64_t m = A->m, n = A->n, nnz = A->nnz;
+  const int64_t *rp = A->row_ptr;
+  if (rp[0] != 0 || rp[m] != nnz) return TSVD_EINVAL;
+  for (int64_t r = 0; r < m; ++r)
+    if (rp[r + 1] < rp[r]) return TSVD_EINVAL;
+  const int32_t *ci = A->col_idx;
+  for (int64_t p = 0; p < nnz; ++p)
+    if (ci[p] < 0 || (int64_t)ci[p] >= n) return TSVD_EINVAL;
+  return TSVD_OK;
+}
+
+void partition_rows(int64_t m, int64_t block_rows, std::vector<int64_t> &starts) {
+  starts.clear();
+  for (int64_t r = 0; r < m; r += block_rows) starts.push_back(r);
+  starts.push_back(m);
+}
+
+tsvd_status plan_dense(tsvd_plan_s *p) {
+  const int64_t n = p->n, k = p->k, m = p->m;
+  const int prec = p->opt.precision;
+  Carve c;
+  p->o_G64 = c.take((size_t)n * n * 8);
+  p->o_G32 = c.take((size_t)n * n * 4);
+  p->o_V64 = c.take((size_t)n * k * 8);
+  p->o_V32 = c.take((size_t)n * k * 4);
+  p->o_sig2 = c.take((size_t)k * 8);
+  p->o_sigma = c.take((size_t)k * 8);
+  p->o_info = c.take((size_t)k * 4 * sizeof(int32_t));
+  p->b_pscr = power_scratch_bytes(n, k);
+  p->o_pscr = c.take(p->b_pscr);
+  const size_t fixed = c.off;
+  const bool host_a = p->location == TSVD_HOST;
+  const bool host_u = p->opt.out_location == TSVD_HOST;
+  const int R = p->n_buffers;
+  auto chunk_cost = [&](int64_t rows, int mode) -> size_t {
+    size_t s = gram_tc_scratch_bytes(rows, n, prec) + 256;
+    if (mode == MODE_STREAM) s += (size_t)R * (size_t)round_up(rows * n * 4, 256);
+    if (host_u) s += 2 * (size_t)round_up(rows * k * 4, 256);
+    return s;
+  };
+  int64_t target = p->opt.block_rows > 0 ? p->opt.block_rows
+                                         : std::max<int64_t>(256, ((int64_t)1 << 30) / (n * 4));
+  target = std::min<int64_t>(round_up(target, 32), round_up(m, 32));
+  const size_t budget = p->opt.device_budget;
+  const size_t resident_bytes = (size_t)round_up(m * n * 4, 256);
+  int mode = MODE_DEVICE;
+  if (host_a) {
+    mode = MODE_STREAM;
+    if (!p->opt.force_stream) {
+      if (budget == 0 || fixed + resident_bytes + chunk_cost(target, MODE_RESIDENT) <= budget)
+        mode = MODE_RESIDENT;
+    }
+  }
+  int64_t rows = target;
+  if (budget) {
+    while (rows > 32 && fixed + (mode == MODE_RESIDENT ? resident_bytes : 0) + chunk_cost(rows, mode) > budget)
+      rows = round_up(rows / 2, 32);
+    if (fixed + (mode == MODE_RESIDENT ? resident_bytes : 0) + chunk_cost(rows, mode) > budget) return TSVD_EBUDGET;
+  }
+  p->mode = mode;
+  p->chunk_rows = rows;
+  p->n_chunks = ceil_div(m, rows);
+  p->b_gscr = gram_tc_scratch_bytes(rows, n, prec);
+  p->o_gscr = c.take(p->b_gscr + 256);
+  if (mode == MODE_STREAM) {
+    p->b_slot = (size_t)round_up(rows * n * 4, 256);
+    p->o_ring = c.take(p->b_slot * R);
+  }
+  if (mode == MODE_RESIDENT) p->o_res = c.take(resident_bytes);
+  if (host_u) {
+    p->b_ubuf = (size_t)round_up(rows * k * 4, 256);
+    p->o_ubuf = c.take(2 * p->b_ubuf);
+  }
+  p->ws = c.off;
+  if (budget && p->ws > budget) return TSVD_EBUDGET;
+  return TSVD_OK;
+}
+
+tsvd_status plan_csr(tsvd_plan_s *p, const tsvd_matrix *A) {
+  const int64_t n = p->n, k = p->k, m = p->m;
+  if (k + 4 > kVecPartStride) return TSVD_EUNSUPPORTED;
+  p->avg_nnz = m > 0 ? (double)p->nnz / (double)m : 0.0;
+  Carve c;
+  p->o_v = c.take((size_t)n * 4);
+  p->o_vn = c.take((size_t)n * 4);
+  p->o_w = c.take((size_t)n * 4);
+  p->o_x64 = c.take((size_t)n * 8);
+  p->o_Vr = c.take((size_t)n * k * 4);
+  p->o_sig2 = c.take((size_t)k * 8);
+  p->o_sigma = c.take((size_t)k * 8);
+  p->o_info = c.take((size_t)k * 4 * sizeof(int32_t));
+  p->o_flag = c.take(256);
+  p->vec_grid = 1024;
+  p->o_vsc = c.take(vec_scratch_bytes(p->vec_grid));
+  const size_t fixed = c.off;
+  const bool host_a = p->location == TSVD_HOST;
+  const bool host_u = p->opt.out_location == TSVD_HOST;
+  const int R = p->n_buffers;
+  int64_t rows = p->opt.block_rows > 0 ? p->opt.block_rows : std::min<int64_t>(m, (int64_t)1 << 20);
+  rows = std::max<int64_t>(1, std::min<int64_t>(rows, m));
+  const size_t budget = p->opt.device_budget;
+  const size_t resident_bytes = (size_t)round_up((m + 1) * 8, 256) + 2 * (size_t)round_up(std::max<int64_t>(p->nnz, 1) * 4, 256);
+  auto slot_bytes = [&](int64_t r, int64_t maxnnz) -> size_t {
+    return (size_t)round_up((r + 1) * 8, 256) + 2 * (size_t)round_up(std::max<int64_t>(maxnnz, 1) * 4, 256);
+  };
+  auto max_nnz_of = [&](int64_t r) -> int64_t {
+    if (!host_a) return 0;
+    int64_t mx = 0;
+    for (int64_t s = 0; s < m; s += r) mx = std::max(mx, A->row_ptr[std::min(m, s + r)] - A->row_ptr[s]);
+    return mx;
+  };
+  int mode = MODE_DEVICE;
+  if (host_a) {
+    mode = MODE_STREAM;
+    const size_t ucost = host_u ? 2 * (size_t)round_up(rows * k * 4, 256) : 0;
+    if (!p->opt.force_stream && (budget == 0 || fixed + resident_bytes + ucost <= budget)) mode = MODE_RESIDENT;
+  }
+  int64_t maxnnz = mode == MODE_STREAM ? max_nnz_of(rows) : 0;
+  if (budget) {
+    auto total = [&](int64_t r, int64_t mx) -> size_t {
+      size_t s = fixed + (host_u ? 2 * (size_t)round_up(r * k * 4, 256) : 0);
+      if (mode == MODE_STREAM) s += R * slot_bytes(r, mx);
+      if (mode == MODE_RESIDENT) s += resident_bytes;
+      return s;
+    };
+    while (rows > 1024 && total(rows, maxnnz) > budget) {
+      rows = (rows + 1) / 2;
+      if (mode == MODE_STREAM) maxnnz = max_nnz_of(rows);
+    }
+    if (total(rows, maxnnz) > budget) return TSVD_EBUDGET;
+  }
+  p->mode = mode;
+  p->chunk_rows = rows;
+  partition_rows(m, rows, p->block_start);
+  p->n_chunks = (int64_t)p->block_start.size() - 1;
+  p->max_block_nnz = maxnnz;
+  if (mode == MODE_STREAM) {
+    p->b_slot = slot_bytes(rows, maxnnz);
+    p->o_ring = c.take(p->b_slot * R);
+  }
+  if (mode == MODE_RESIDENT) p->o_res = c.take(resident_bytes);
+  if (host_u) {
+    p->b_ubuf = (size_t)round_up(rows * k * 4, 256);
+    p->o_ubuf = c.take(2 * p->b_ubuf);
+  }
+  p->ws = c.off;
+  if (budget && p->ws > budget) return TSVD_EBUDGET;
+  return TSVD_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *tsvd_status_string(tsvd_status s) {
+  switch (s) {
+    case TSVD_OK: return "ok";
+    case TSVD_EINVAL: return "invalid argument";
+    case TSVD_ENOMEM: return "host allocation failed";
+    case TSVD_EBUDGET: return "device budget or workspace too small";
+    case TSVD_ECUDA: return "CUDA error";
+    case TSVD_ETIMEDOUT: return "bounded wait timed out";
+    case TSVD_ENOCONV: return "iteration cap reached before convergence";
+    case TSVD_ERANK: return "matrix rank below k";
+    case TSVD_EUNSUPPORTED: return "unsupported request";
+  }
+  return "unknown status";
+}
+
+const char *tsvd_last_cuda_error(void) { return g_err.c_str(); }
+int32_t tsvd_abi_version(void) { return TSVD_ABI_VERSION; }
+
+void tsvd_options_init(tsvd_options *opt) {
+  if (!opt) return;
+  memset(opt, 0, sizeof *opt);
+  opt->n_buffers = 3;
+  opt->precision = TSVD_GRAM_FP32;
+  opt->max_iter = 10000;
+  opt->out_location = TSVD_HOST;
+}
+
+tsvd_status tsvd_plan(tsvd_plan_t *out, const tsvd_matrix *A, int64_t k, double eps,
+                      const tsvd_options *opt_in, size_t *workspace_bytes) {
+  if (!out || !A || !workspace_bytes) return TSVD_EINVAL;
+  *out = nullptr;
+  *workspace_bytes = 0;
+  tsvd_options opt;
+  if (opt_in) opt = *opt_in; else tsvd_options_init(&opt);
+  if (A->kind != TSVD_DENSE_F32_ROWMAJOR && A->kind != TSVD_CSR_F32_I32_I64) return TSVD_EINVAL;
+  if (A->location != TSVD_HOST && A->location != TSVD_DEVICE) return TSVD_EINVAL;
+  if (A->m <= 0 || A->n <= 0) return TSVD_EINVAL;
+  const int64_t mn = std::min(A->m, A->n);
+  if (k == -1) k = mn;
+  if (k < 1 || k > mn) return TSVD_EINVAL;
+  if (!opt.iters_override && !(eps > 0.0 && eps < 1.0)) return TSVD_EINVAL;
+  if (opt.n_buffers == 0) opt.n_buffers = 3;
+  if (opt.n_buffers < 2 || opt.n_buffers > 64) return TSVD_EINVAL;
+  if (opt.precision < 0 || opt.precision > 2) return TSVD_EINVAL;
+  if (opt.max_iter <= 0) opt.max_iter = 10000;
+  if (opt.out_location != TSVD_HOST && opt.out_location != TSVD_DEVICE) return TSVD_EINVAL;
+  if (opt.block_rows < 0) return TSVD_EINVAL;
+  if (A->kind == TSVD_DENSE_F32_ROWMAJOR) {
+    if (!A->values || A->ld < A->n) return TSVD_EINVAL;
+  } else {
+    if (A->nnz < 0 || !A->row_ptr) return TSVD_EINVAL;
+    if (A->nnz > 0 && (!A->col_idx || !A->values)) return TSVD_EINVAL;
+    if (A->n > 0x7fffffffLL) return TSVD_EUNSUPPORTED;
+    if (A->location == TSVD_HOST) TSVD_TRY(validate_csr_host(A));
+  }
+  if (A->m < A->n) return TSVD_EUNSUPPORTED;  // the m < n branch (Eq. 3) is not built
+  if (A->kind == TSVD_DENSE_F32_ROWMAJOR && A->n > 32768) return TSVD_EUNSUPPORTED;
+  if (opt.iters_override) {
+    for (int64_t l = 0; l < k; ++l)
+      if (opt.iters_override[l] <= 0) return TSVD_EINVAL;
+  }
+
+  tsvd_plan_s *p = new (std::nothrow) tsvd_plan_s();
+  if (!p) return TSVD_ENOMEM;
+  try {
+    p->kind = A->kind;
+    p->location = A->location;
+    p->m = A->m;
+    p->n = A->n;
+    p->ld = A->kind == TSVD_DENSE_F32_ROWMAJOR ? A->ld : 0;
+    p->nnz = A->nnz;
+    p->k = k;
+    p->eps = eps;
+    p->opt = opt;
+    p->n_buffers = opt.n_buffers;
+    if (opt.iters_override) p->iters_override.assign(opt.iters_override, opt.iters_override + k);
+    if (opt.start_draws) p->start_draws.assign(opt.start_draws, opt.start_draws + (size_t)A->n * k);
+    p->opt.iters_override = nullptr;
+    p->opt.start_draws = nullptr;
+  } catch (...) {
+    delete p;
+    return TSVD_ENOMEM;
+  }
+  tsvd_status st = p->kind == TSVD_DENSE_F32_ROWMAJOR ? plan_dense(p) : plan_csr(p, A);
+  if (st != TSVD_OK) {
+    delete p;
+    return st;
+  }
+  *workspace_bytes = p->ws;
+  *out = p;
+  return TSVD_OK;
+}
+
+void tsvd_destroy(tsvd_plan_t p) {
+  if (!p) return;
+  int cur = -1;
+  if (p->device >= 0 && cudaGetDevice(&cur) == cudaSuccess) {
+    if (cur != p->device) cudaSetDevice(p->device);
+    for (auto e : p->ev_ready) cudaEventDestroy(e);
+    for (auto e : p->ev_free) cudaEventDestroy(e);
+    for (int i = 0; i < 2; ++i) {
+      if (p->ev_u_ready[i]) cudaEventDestroy(p->ev_u_ready[i]);
+      if (p->ev_u_free[i]) cudaEventDestroy(p->ev_u_free[i]);
+    }
+    for (auto e : p->ev_t)
+      if (e) cudaEventDestroy(e);
+    for (auto e : p->ev_k) cudaEventDestroy(e);
+    if (p->copy_stream) cudaStreamDestroy(p->copy_stream);
+    if (p->d2h_stream) cudaStreamDestroy(p->d2h_stream);
+    if (cur != p->device) cudaSetDevice(cur);
+  }
+  delete p;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------- factor
+namespace {
+
+tsvd_status ensure_runtime(tsvd_plan_s *p) {
+  int dev = -1;
+  TSVD_CUDA(cudaGetDevice(&dev));
+  if (p->device == dev) return TSVD_OK;
+  if (p->device >= 0) return TSVD_EINVAL;  // a plan serves one device
+  p->device = dev;
+  TSVD_CUDA(cudaStreamCreateWithFlags(&p->copy_stream, cudaStreamNonBlocking));
+  TSVD_CUDA(cudaStreamCreateWithFlags(&p->d2h_stream, cudaStreamNonBlocking));
+  p->ev_ready.resize(p->n_buffers, nullptr);
+  p->ev_free.resize(p->n_buffers, nullptr);
+  for (int i = 0; i < p->n_buffers; ++i) {
+    TSVD_CUDA(cudaEventCreateWithFlags(&p->ev_ready[i], cudaEventDisableTiming));
+    TSVD_CUDA(cudaEventCreateWithFlags(&p->ev_free[i], cudaEventDisableTiming));
+  }
+  for (int i = 0; i < 2; ++i) {
+    TSVD_CUDA(cudaEventCreateWithFlags(&p->ev_u_ready[i], cudaEventDisableTiming));
+    TSVD_CUDA(cudaEventCreateWithFlags(&p->ev_u_free[i], cudaEventDisableTiming));
+  }
+  for (int i = 0; i < 4; ++i) TSVD_CUDA(cudaEventCreate(&p->ev_t[i]));
+  return TSVD_OK;
+}
+
+struct Run {
+  tsvd_plan_s *p;
+  const tsvd_matrix *A;
+  unsigned char *ws;
+  cudaStream_t cs;
+  double h2d = 0.0, d2h = 0.0;
+  int64_t chunk_seq = 0;  // ring position, continues across passes
+};
+
+// Bring dense rows [r0, r0+rows) to the device; returns the pointer/stride to
+// use on the compute stream.  The slot is released by release_dense().
+tsvd_status acquire_dense(Run &r, int64_t r0, int64_t rows, const float **out, int64_t *ldo, int *slot,
+                          bool resident_fill) {
+  tsvd_plan_s *p = r.p;
+  const tsvd_matrix *A = r.A;
+  *slot = -1;
+  if (p->mode == MODE_DEVICE) {
+    *out = A->values + r0 * A->ld;
+    *ldo = A->ld;
+    return TSVD_OK;
+  }
+  float *dst;
+  if (p->mode == MODE_RESIDENT) {
+    dst = reinterpret_cast<float *>(r.ws + p->o_res) + r0 * p->n;
+    *out = dst;
+    *ldo = p->n;
+    if (!resident_fill) return TSVD_OK;
+  } else {
+    const int s = (int)(r.chunk_seq++ % p->n_buffers);
+    *slot = s;
+    dst = reinterpret_cast<float *>(r.ws + p->o_ring + p->b_slot * s);
+    TSVD_CUDA(cudaStreamWaitEvent(p->copy_stream, p->ev_free[s], 0));
+    *out = dst;
+    *ldo = p->n;
+  }
+  const float *src = A->values + r0 * A->ld;
+  if (A->ld == p->n) {
+    TSVD_CUDA(cudaMemcpyAsync(dst, src, (size_t)rows * p->n * 4, cudaMemcpyHostToDevice, p->copy_stream));
+  } else {
+    TSVD_CUDA(cudaMemcpy2DAsync(dst, (size_t)p->n * 4, src, (size_t)A->ld * 4, (size_t)p->n * 4, (size_t)rows,
+                                cudaMemcpyHostToDevice, p->copy_stream));
+  }
+  r.h2d += (double)rows * p->n * 4;
+  const int ev = *slot >= 0 ? *slot : 0;
+  TSVD_CUDA(cudaEventRecord(p->ev_ready[ev], p->copy_stream));
+  TSVD_CUDA(cudaStreamWaitEvent(r.cs, p->ev_ready[ev], 0));
+  return TSVD_OK;
+}
+
+tsvd_status release_slot(Run &r, int slot) {
+  if (slot >= 0) TSVD_CUDA(cudaEventRecord(r.p->ev_free[slot], r.cs));
+  return TSVD_OK;
+}
+
+tsvd_status gram_dispatch(const float *A, int64_t rows, int64_t n, int64_t ld, double *G, int prec,
+                          void *scr, size_t scr_bytes, cudaStream_t s, cudaEvent_t ev0 = nullptr,
+                          cudaEvent_t ev1 = nullptr) {
+  if (prec == TSVD_GRAM_FP32) return launch_gram_simt(A, rows, n, ld, G, s, ev0, ev1);
+  return launch_gram_tc(A, rows, n, ld, G, prec, scr, scr_bytes, s, ev0, ev1);
+}
+
+tsvd_status left_pass_dense(Run &r, const float *V32, const double *sigma, float *U) {
+  tsvd_plan_s *p = r.p;
+  const bool host_u = p->opt.out_location == TSVD_HOST;
+  for (int64_t c = 0; c < p->n_chunks; ++c) {
+    const int64_t r0 = c * p->chunk_rows, rows = std::min(p->chunk_rows, p->m - r0);
+    const float *Ab;
+    int64_t ldb;
+    int slot;
+    TSVD_TRY(acquire_dense(r, r0, rows, &Ab, &ldb, &slot, false));
+    if (!host_u) {
+      TSVD_TRY(launch_left_dense(Ab, rows, p->n, ldb, V32, p->n, p->k, sigma, U + r0, p->m, r.cs));
+      TSVD_TRY(release_slot(r, slot));
+    } else {
+      const int b = (int)(c & 1);
+      float *ub = reinterpret_cast<float *>(r.ws + p->o_ubuf + p->b_ubuf * b);
+      TSVD_CUDA(cudaStreamWaitEvent(r.cs, p->ev_u_free[b], 0));
+      TSVD_TRY(launch_left_dense(Ab, rows, p->n, ldb, V32, p->n, p->k, sigma, ub, rows, r.cs));
+      TSVD_TRY(release_slot(r, slot));
+      TSVD_CUDA(cudaEventRecord(p->ev_u_ready[b], r.cs));
+      TSVD_CUDA(cudaStreamWaitEvent(p->d2h_stream, p->ev_u_ready[b], 0));
+      TSVD_CUDA(cudaMemcpy2DAsync(U + r0, (size_t)p->m * 4, ub, (size_t)rows * 4, (size_t)rows * 4,
+                                  (size_t)p->k, cudaMemcpyDeviceToHost, p->d2h_stream));
+      r.d2h += (double)rows * p->k * 4;
+      TSVD_CUDA(cudaEventRecord(p->ev_u_free[b], p->d2h_stream));
+    }
+  }
+  return TSVD_OK;
+}
+
+tsvd_status factor_dense(Run &r, float *U, double *sigma_out, float *V_out, tsvd_report *rep) {
+  tsvd_plan_s *p = r.p;
+  const int64_t n = p->n, k = p->k;
+  unsigned char *ws = r.ws;
+  double *G64 = reinterpret_cast<double *>(ws + p->o_G64);
+  float *G32 = reinterpret_cast<float *>(ws + p->o_G32);
+  double *V64 = reinterpret_cast<double *>(ws + p->o_V64);
+  float *V32 = reinterpret_cast<float *>(ws + p->o_V32);
+  double *sig2 = reinterpret_cast<double *>(ws + p->o_sig2);
+  double *sigma = reinterpret_cast<double *>(ws + p->o_sigma);
+  int32_t *info = reinterpret_cast<int32_t *>(ws + p->o_info);
+  void *pscr = ws + p->o_pscr;
+  void *gscr = ws + p->o_gscr;
+
+  const bool timed = p->opt.time_kernels != 0;
+  if (timed && (int64_t)p->ev_k.size() < 2 * p->n_chunks) {
+    const size_t have = p->ev_k.size();
+    p->ev_k.resize(2 * p->n_chunks, nullptr);
+    for (size_t i = have; i < p->ev_k.size(); ++i) TSVD_CUDA(cudaEventCreate(&p->ev_k[i]));
+  }
+  TSVD_CUDA(cudaEventRecord(p->ev_t[0], r.cs));
+  // ---- Gram pass: B = sum_b A_b^T A_b
+  TSVD_CUDA(cudaMemsetAsync(G64, 0, (size_t)n * n * 8, r.cs));
+  for (int64_t c = 0; c < p->n_chunks; ++c) {
+    const int64_t r0 = c * p->chunk_rows, rows = std::min(p->chunk_rows, p->m - r0);
+    const float *Ab;
+    int64_t ldb;
+    int slot;
+    TSVD_TRY(acquire_dense(r, r0, rows, &Ab, &ldb, &slot, true));
+    TSVD_TRY(gram_dispatch(Ab, rows, n, ldb, G64, p->opt.precision, gscr, p->b_gscr, r.cs,
+                           timed ? p->ev_k[2 * c] : nullptr, timed ? p->ev_k[2 * c + 1] : nullptr));
+    TSVD_TRY(release_slot(r, slot));
+  }
+  int32_t gram_err = 0;
+  if (p->opt.precision != TSVD_GRAM_FP32)
+    TSVD_CUDA(cudaMemcpyAsync(&gram_err, gscr, 4, cudaMemcpyDeviceToHost, r.cs));
+  TSVD_TRY(launch_symmetrize(n, G64, G32, r.cs));
+  TSVD_CUDA(cudaEventRecord(p->ev_t[1], r.cs));
+
+  // ---- power phase: Alg. 1 loop over l, Alg. 2 per triplet (on the device)
+  TSVD_CUDA(cudaMemsetAsync(info, 0, (size_t)k * 4 * sizeof(int32_t), r.cs));
+  for (int64_t l = 0; l < k; ++l) {
+    double *x = V64 + l * n;
+    if (!p->start_draws.empty()) {
+      TSVD_CUDA(cudaMemcpyAsync(x, p->start_draws.data() + l * n, (size_t)n * 8, cudaMemcpyHostToDevice, r.cs));
+      r.h2d += (double)n * 8;
+    } else {
+      TSVD_TRY(launch_start_draws(p->opt.seed, l, n, x, r.cs));
+    }
+    const int ovr = p->iters_override.empty() ? 0 : p->iters_override[l];
+    TSVD_TRY(launch_power_dense(n, G32, G64, l ? V64 : nullptr, l ? sig2 : nullptr, l, x, p->eps,
+                                p->opt.max_iter, ovr, p->opt.sign_convention, sig2 + l, info + 4 * l,
+                                pscr, p->b_pscr, r.cs));
+  }
+  TSVD_TRY(launch_sigma_from_sigma2(sig2, sigma, k, r.cs));
+  TSVD_TRY(launch_f64_to_f32(V64, V32, n * k, r.cs));
+  TSVD_CUDA(cudaEventRecord(p->ev_t[2], r.cs));
+
+  // ---- left vectors: U = A V diag(sigma)^-1
+  if (U) TSVD_TRY(left_pass_dense(r, V32, sigma, U));
+  TSVD_CUDA(cudaEventRecord(p->ev_t[3], r.cs));
+
+  // ---- outputs
+  const cudaMemcpyKind kind = p->opt.out_location == TSVD_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+  TSVD_CUDA(cudaMemcpyAsync(sigma_out, sigma, (size_t)k * 8, kind, r.cs));
+  TSVD_CUDA(cudaMemcpyAsync(V_out, V32, (size_t)n * k * 4, kind, r.cs));
+  if (kind == cudaMemcpyDeviceToHost) r.d2h += (double)k * 8 + (double)n * k * 4;
+  std::vector<int32_t> hinfo((size_t)k * 4);
+  TSVD_CUDA(cudaMemcpyAsync(hinfo.data(), info, hinfo.size() * 4, cudaMemcpyDeviceToHost, r.cs));
+  TSVD_CUDA(cudaStreamSynchronize(r.cs));
+  TSVD_CUDA(cudaStreamSynchronize(p->d2h_stream));
+  TSVD_CUDA(cudaStreamSynchronize(p->copy_stream));
+
+  float t01 = 0, t12 = 0, t23 = 0;
+  TSVD_CUDA(cudaEventElapsedTime(&t01, p->ev_t[0], p->ev_t[1]));
+  TSVD_CUDA(cudaEventElapsedTime(&t12, p->ev_t[1], p->ev_t[2]));
+  TSVD_CUDA(cudaEventElapsedTime(&t23, p->ev_t[2], p->ev_t[3]));
+  if (timed && rep) {
+    double sum = 0.0;
+    for (int64_t c = 0; c < p->n_chunks; ++c) {
+      float t = 0.f;
+      TSVD_CUDA(cudaEventElapsedTime(&t, p->ev_k[2 * c], p->ev_k[2 * c + 1]));
+      sum += t;
+    }
+    rep->gram_kernel_ms = sum;
+    rep->gram_kernel_launches = (int32_t)p->n_chunks;
+  }
+  int flags = 0;
+  int64_t apps = 0;
+  if (gram_err) flags |= TSVD_FLAG_TIMEOUT;
+  for (int64_t l = 0; l < k; ++l) {
+    if (hinfo[4 * l + 2]) flags |= TSVD_FLAG_TIMEOUT;
+    if (hinfo[4 * l + 1] == 1) flags |= TSVD_FLAG_NOCONV;
+    if (hinfo[4 * l + 1] == 2) flags |= TSVD_FLAG_RANK;
+    apps += hinfo[4 * l];
+    if (rep && rep->iters) rep->iters[l] = hinfo[4 * l];
+  }
+  if (rep) {
+    rep->gram_ms = t01;
+    rep->power_ms = t12;
+    rep->left_ms = t23;
+    rep->total_ms = (double)t01 + t12 + t23;
+    rep->applications = apps;
+  }
+  // sigma order check
+  if (p->opt.out_location == TSVD_HOST) {
+    for (int64_t l = 1; l < k; ++l)
+      if (sigma_out[l] > sigma_out[l - 1]) flags |= TSVD_FLAG_NONMONOTONE;
+  }
+  if (rep) rep->flags |= flags;
+  if (flags & TSVD_FLAG_TIMEOUT) return TSVD_ETIMEDOUT;
+  if (flags & TSVD_FLAG_RANK) return TSVD_ERANK;
+  if (flags & TSVD_FLAG_NOCONV) return TSVD_ENOCONV;
+  return TSVD_OK;
+}
+
+// ---------------------------------------------------------------- CSR
+struct CsrBlock {
+  const int64_t *rp;
+  const int32_t *ci;
+  const float *va;
+  int64_t rows;
+  int slot;
+};
+
+__global__ void csr_validate_kernel(int64_t m, int64_t n, int64_t nnz, const int64_t *rp, const int32_t *ci,
+                                    int *flag) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i <= m; i += (int64_t)gridDim.x * blockDim.x) {
+    if (i == 0 && rp[0] != 0) atomicExch(flag, 1);
+    if (i == m && rp[m] != nnz) atomicExch(flag, 1);
+    if (i < m && rp[i + 1] < rp[i]) atomicExch(flag, 1);
+  }
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < nnz; p += (int64_t)gridDim.x * blockDim.x)
+    if (ci[p] < 0 || (int64_t)ci[p] >= n) atomicExch(flag, 1);
+}
+
+tsvd_status acquire_csr(Run &r, int64_t b, const std::vector<int64_t> &bnd_nnz, CsrBlock *out) {
+  tsvd_plan_s *p = r.p;
+  const tsvd_matrix *A = r.A;
+  const int64_t s0 = p->block_start[b], s1 = p->block_start[b + 1];
+  const int64_t e0 = bnd_nnz[b], e1 = bnd_nnz[b + 1];
+  out->rows = s1 - s0;
+  out->slot = -1;
+  if (p->mode == MODE_DEVICE) {
+    out->rp = A->row_ptr + s0;
+    out->ci = A->col_idx + e0;
+    out->va = A->values + e0;
+    return TSVD_OK;
+  }
+  if (p->mode == MODE_RESIDENT) {
+    const int64_t *rp = reinterpret_cast<const int64_t *>(r.ws + p->o_res);
+    const int32_t *ci = reinterpret_cast<const int32_t *>(r.ws + p->o_res + round_up((p->m + 1) * 8, 256));
+    const float *va = reinterpret_cast<const float *>(r.ws + p->o_res + round_up((p->m + 1) * 8, 256) +
+                                                      round_up(std::max<int64_t>(p->nnz, 1) * 4, 256));
+    out->rp = rp + s0;
+    out->ci = ci + e0;
+    out->va = va + e0;
+    return TSVD_OK;
+  }
+  const int s = (int)(r.chunk_seq++ % p->n_buffers);
+  out->slot = s;
+  unsigned char *base = r.ws + p->o_ring + p->b_slot * s;
+  int64_t *rp = reinterpret_cast<int64_t *>(base);
+  int32_t *ci = reinterpret_cast<int32_t *>(base + round_up((p->chunk_rows + 1) * 8, 256));
+  float *va = reinterpret_cast<float *>(base + round_up((p->chunk_rows + 1) * 8, 256) +
+                                        round_up(std::max<int64_t>(p->max_block_nnz, 1) * 4, 256));
+  TSVD_CUDA(cudaStreamWaitEvent(p->copy_stream, p->ev_free[s], 0));
+  TSVD_CUDA(cudaMemcpyAsync(rp, A->row_ptr + s0, (size_t)(out->rows + 1) * 8, cudaMemcpyHostToDevice, p->copy_stream));
+  if (e1 > e0) {
+    TSVD_CUDA(cudaMemcpyAsync(ci, A->col_idx + e0, (size_t)(e1 - e0) * 4, cudaMemcpyHostToDevice, p->copy_stream));
+    TSVD_CUDA(cudaMemcpyAsync(va, A->values + e0, (size_t)(e1 - e0) * 4, cudaMemcpyHostToDevice, p->copy_stream));
+  }
+  r.h2d += (double)(out->rows + 1) * 8 + (double)(e1 - e0) * 8;
+  TSVD_CUDA(cudaEventRecord(p->ev_ready[s], p->copy_stream));
+  TSVD_CUDA(cudaStreamWaitEvent(r.cs, p->ev_ready[s], 0));
+  out->rp = rp;
+  out->ci = ci;
+  out->va = va;
+  return TSVD_OK;
+}
+
+// one application w += A^T (A v), ss += ||A v||^2 over all row blocks
+tsvd_status csr_apply(Run &r, const std::vector<int64_t> &bnd, const float *v, float *w, double *ss, int scatter) {
+  tsvd_plan_s *p = r.p;
+  for (int64_t b = 0; b < p->n_chunks; ++b) {
+    CsrBlock blk;
+    TSVD_TRY(acquire_csr(r, b, bnd, &blk));
+    TSVD_TRY(launch_csr_pair(blk.rows, p->n, blk.rp, blk.ci, blk.va, v, w, ss, scatter, p->avg_nnz, r.cs));
+    TSVD_TRY(release_slot(r, blk.slot));
+  }
+  return TSVD_OK;
+}
+
+tsvd_status factor_csr(Run &r, float *U, double *sigma_out, float *V_out, tsvd_report *rep) {
+  tsvd_plan_s *p = r.p;
+  const tsvd_matrix *A = r.A;
+  const int64_t n = p->n, k = p->k, m = p->m;
+  unsigned char *ws = r.ws;
+  float *v = reinterpret_cast<float *>(ws + p->o_v);
+  float *vn = reinterpret_cast<float *>(ws + p->o_vn);
+  float *w = reinterpret_cast<float *>(ws + p->o_w);
+  double *x64 = reinterpret_cast<double *>(ws + p->o_x64);
+  float *Vr = reinterpret_cast<float *>(ws + p->o_Vr);
+  double *sig2 = reinterpret_cast<double *>(ws + p->o_sig2);
+  double *sigma = reinterpret_cast<double *>(ws + p->o_sigma);
+  int32_t *info = reinterpret_cast<int32_t *>(ws + p->o_info);
+  int32_t *flag = reinterpret_cast<int32_t *>(ws + p->o_flag);
+  double *ss = reinterpret_cast<double *>(ws + p->o_flag + 64);
+  VecScratch sc;
+  sc.part = reinterpret_cast<double *>(ws + p->o_vsc);
+  sc.coef = sc.part + (size_t)p->vec_grid * kVecPartStride;
+  sc.scal = sc.coef + 64 * 2;
+  sc.grid = p->vec_grid;
+
+  TSVD_CUDA(cudaEventRecord(p->ev_t[0], r.cs));
+  // entry offsets at block boundaries
+  std::vector<int64_t> bnd(p->n_chunks + 1);
+  if (p->location == TSVD_HOST) {
+    for (int64_t b = 0; b <= p->n_chunks; ++b) bnd[b] = A->row_ptr[p->block_start[b]];
+  } else {
+    // device CSR: validate on the device, then read the boundary offsets
+    TSVD_CUDA(cudaMemsetAsync(flag, 0, 4, r.cs));
+    csr_validate_kernel<<<1024, 256, 0, r.cs>>>(m, n, p->nnz, A->row_ptr, A->col_idx, flag);
+    TSVD_LAUNCHED();
+    int hflag = 0;
+    TSVD_CUDA(cudaMemcpyAsync(&hflag, flag, 4, cudaMemcpyDeviceToHost, r.cs));
+    for (int64_t b = 0; b <= p->n_chunks; ++b)
+      TSVD_CUDA(cudaMemcpyAsync(&bnd[b], A->row_ptr + p->block_start[b], 8, cudaMemcpyDeviceToHost, r.cs));
+    TSVD_CUDA(cudaStreamSynchronize(r.cs));
+    if (hflag) return TSVD_EINVAL;
+  }
+  if (p->mode == MODE_RESIDENT) {
+    unsigned char *base = ws + p->o_res;
+    const size_t orp = 0, oci = round_up((m + 1) * 8, 256), ova = oci + round_up(std::max<int64_t>(p->nnz, 1) * 4, 256);
+    TSVD_CUDA(cudaMemcpyAsync(base + orp, A->row_ptr, (size_t)(m + 1) * 8, cudaMemcpyHostToDevice, r.cs));
+    if (p->nnz) {
+      TSVD_CUDA(cudaMemcpyAsync(base + oci, A->col_idx, (size_t)p->nnz * 4, cudaMemcpyHostToDevice, r.cs));
+      TSVD_CUDA(cudaMemcpyAsync(base + ova, A->values, (size_t)p->nnz * 4, cudaMemcpyHostToDevice, r.cs));
+    }
+    r.h2d += (double)(m + 1) * 8 + (double)p->nnz * 8;
+  }
+  TSVD_CUDA(cudaEventRecord(p->ev_t[1], r.cs));
+
+  std::vector<double> hsig2((size_t)k, 0.0);
+  std::vector<int32_t> hinfo((size_t)k * 4, 0);
+  TSVD_CUDA(cudaMemsetAsync(info, 0, (size_t)k * 16, r.cs));
+  int flags = 0;
+  int64_t apps = 0;
+  const bool host_out = p->opt.out_location == TSVD_HOST;
+  for (int64_t l = 0; l < k; ++l) {
+    // start vector v0 = x / ||x||
+    if (!p->start_draws.empty()) {
+      TSVD_CUDA(cudaMemcpyAsync(x64, p->start_draws.data() + l * n, (size_t)n * 8, cudaMemcpyHostToDevice, r.cs));
+      r.h2d += (double)n * 8;
+    } else {
+      TSVD_TRY(launch_start_draws(p->opt.seed, l, n, x64, r.cs));
+    }
+    sc.info = info + 4 * l;
+    TSVD_TRY(launch_vec_normalize_f64_to_f32(x64, v, n, sc, r.cs));
+    const double rank_scale = l == 0 ? 1.0 : hsig2[0];
+    const int ovr = p->iters_override.empty() ? 0 : p->iters_override[l];
+    int32_t h[4] = {0, 0, 0, 0};
+    for (;;) {
+      TSVD_CUDA(cudaMemsetAsync(w, 0, (size_t)n * 4, r.cs));
+      TSVD_CUDA(cudaMemsetAsync(ss, 0, 8, r.cs));
+      TSVD_TRY(csr_apply(r, bnd, v, w, ss, 1));
+      TSVD_TRY(launch_vec_deflate_step(n, Vr, k, sig2, l, v, w, vn, p->eps, p->opt.max_iter, ovr, rank_scale,
+                                       sc, 0, r.cs));
+      TSVD_CUDA(cudaMemcpyAsync(h, sc.info, 16, cudaMemcpyDeviceToHost, r.cs));
+      TSVD_CUDA(cudaStreamSynchronize(r.cs));
+      if (h[1] == 2) break;  // rank: keep v (= v0 of this step)
+      std::swap(v, vn);
+      if (h[2]) break;
+    }
+    if (h[1] == 2) {
+      // v := v0 orthogonalised against earlier vectors, twice; sigma_l = 0
+      for (int pass = 0; pass < 2; ++pass) {
+        TSVD_TRY(launch_vec_deflate_step(n, Vr, k, sig2, l, v, w, vn, p->eps, p->opt.max_iter, ovr, rank_scale,
+                                         sc, 1, r.cs));
+        std::swap(v, vn);
+      }
+      TSVD_CUDA(cudaMemsetAsync(sig2 + l, 0, 8, r.cs));
+      flags |= TSVD_FLAG_RANK;
+    } else {
+      // sigma_l^2 = ||A v_l||^2 (Alg. 1 l.11-13)
+      TSVD_CUDA(cudaMemsetAsync(ss, 0, 8, r.cs));
+      TSVD_TRY(csr_apply(r, bnd, v, w, ss, 0));
+      TSVD_CUDA(cudaMemcpyAsync(sig2 + l, ss, 8, cudaMemcpyDeviceToDevice, r.cs));
+      if (h[1] == 1) flags |= TSVD_FLAG_NOCONV;
+    }
+    TSVD_TRY(launch_vec_store_column(n, v, Vr, k, l, p->opt.sign_convention, sc, r.cs));
+    TSVD_CUDA(cudaMemcpyAsync(V_out + l * n, v, (size_t)n * 4,
+                              host_out ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, r.cs));
+    if (host_out) r.d2h += (double)n * 4;
+    TSVD_CUDA(cudaMemcpyAsync(&hsig2[l], sig2 + l, 8, cudaMemcpyDeviceToHost, r.cs));
+    TSVD_CUDA(cudaStreamSynchronize(r.cs));
+    apps += h[0];
+    if (rep && rep->iters) rep->iters[l] = h[0];
+  }
+  TSVD_TRY(launch_sigma_from_sigma2(sig2, sigma, k, r.cs));
+  TSVD_CUDA(cudaEventRecord(p->ev_t[2], r.cs));
+  if (U) {
+    for (int64_t b = 0; b < p->n_chunks; ++b) {
+      CsrBlock blk;
+      TSVD_TRY(acquire_csr(r, b, bnd, &blk));
+      const int64_t r0 = p->block_start[b];
+      if (!host_out) {
+        TSVD_TRY(launch_csr_left(blk.rows, blk.rp, blk.ci, blk.va, Vr, k, k, sigma, U + r0, m, p->avg_nnz, r.cs));
+        TSVD_TRY(release_slot(r, blk.slot));
+      } else {
+        const int bb = (int)(b & 1);
+        float *ub = reinterpret_cast<float *>(ws + p->o_ubuf + p->b_ubuf * bb);
+        TSVD_CUDA(cudaStreamWaitEvent(r.cs, p->ev_u_free[bb], 0));
+        TSVD_TRY(launch_csr_left(blk.rows, blk.rp, blk.ci, blk.va, Vr, k, k, sigma, ub, blk.rows, p->avg_nnz, r.cs));
+        TSVD_TRY(release_slot(r, blk.slot));
+        TSVD_CUDA(cudaEventRecord(p->ev_u_ready[bb], r.cs));
+        TSVD_CUDA(cudaStreamWaitEvent(p->d2h_stream, p->ev_u_ready[bb], 0));
+        TSVD_CUDA(cudaMemcpy2DAsync(U + r0, (size_t)m * 4, ub, (size_t)blk.rows * 4, (size_t)blk.rows * 4,
+                                    (size_t)k, cudaMemcpyDeviceToHost, p->d2h_stream));
+        r.d2h += (double)blk.rows * k * 4;
+        TSVD_CUDA(cudaEventRecord(p->ev_u_free[bb], p->d2h_stream));
+      }
+    }
+  }
+  TSVD_CUDA(cudaEventRecord(p->ev_t[3], r.cs));
+  TSVD_CUDA(cudaMemcpyAsync(sigma_out, sigma, (size_t)k * 8, host_out ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice,
+                            r.cs));
+  TSVD_CUDA(cudaStreamSynchronize(r.cs));
+  TSVD_CUDA(cudaStreamSynchronize(p->d2h_stream));
+  TSVD_CUDA(cudaStreamSynchronize(p->copy_stream));
+  float t01 = 0, t12 = 0, t23 = 0;
+  TSVD_CUDA(cudaEventElapsedTime(&t01, p->ev_t[0], p->ev_t[1]));
+  TSVD_CUDA(cudaEventElapsedTime(&t12, p->ev_t[1], p->ev_t[2]));
+  TSVD_CUDA(cudaEventElapsedTime(&t23, p->ev_t[2], p->ev_t[3]));
+  if (host_out) {
+    for (int64_t l = 1; l < k; ++l)
+      if (sigma_out[l] > sigma_out[l - 1]) flags |= TSVD_FLAG_NONMONOTONE;
+  }
+  if (rep) {
+    rep->gram_ms = t01;
+    rep->power_ms = t12;
+    rep->left_ms = t23;
+    rep->total_ms = (double)t01 + t12 + t23;
+    rep->applications = apps;
+    rep->flags |= flags;
+  }
+  if (flags & TSVD_FLAG_RANK) return TSVD_ERANK;
+  if (flags & TSVD_FLAG_NOCONV) return TSVD_ENOCONV;
+  return TSVD_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+tsvd_status tsvd_factor(tsvd_plan_t plan, const tsvd_matrix *A, void *workspace, size_t workspace_bytes,
+                        void *stream, float *U, double *sigma, float *V, tsvd_report *report) {
+  if (!plan || !A || !sigma || !V) return TSVD_EINVAL;
+  tsvd_plan_s *p = plan;
+  if (A->kind != p->kind || A->location != p->location || A->m != p->m || A->n != p->n) return TSVD_EINVAL;
+  if (p->kind == TSVD_DENSE_F32_ROWMAJOR && (!A->values || A->ld != p->ld)) return TSVD_EINVAL;
+  if (p->kind == TSVD_CSR_F32_I32_I64 && (A->nnz != p->nnz || !A->row_ptr)) return TSVD_EINVAL;
+  if (!workspace || workspace_bytes < p->ws) return TSVD_EBUDGET;
+  if ((reinterpret_cast<uintptr_t>(workspace) & 255) != 0) return TSVD_EINVAL;
+  TSVD_TRY(ensure_runtime(p));
+  const int64_t l0 = launches_so_far();
+  Run r;
+  r.p = p;
+  r.A = A;
+  r.ws = static_cast<unsigned char *>(workspace);
+  r.cs = static_cast<cudaStream_t>(stream);
+  int flags = 0;
+  if (p->location == TSVD_HOST) {
+    cudaPointerAttributes at;
+    const void *probe = p->kind == TSVD_DENSE_F32_ROWMAJOR ? (const void *)A->values : (const void *)A->row_ptr;
+    if (cudaPointerGetAttributes(&at, probe) != cudaSuccess || at.type == cudaMemoryTypeUnregistered) {
+      cudaGetLastError();
+      flags |= TSVD_FLAG_PAGEABLE;
+    }
+  }
+  if (report) {
+    int32_t *it = report->iters;
+    memset(report, 0, sizeof *report);
+    report->iters = it;
+    report->flags = flags;
+    report->mode = p->mode;
+    report->n_blocks = (int32_t)p->n_chunks;
+  }
+  tsvd_status st = p->kind == TSVD_DENSE_F32_ROWMAJOR ? factor_dense(r, U, sigma, V, report)
+                                                      : factor_csr(r, U, sigma, V, report);
+  if (report) {
+    report->h2d_bytes = r.h2d;
+    report->d2h_bytes = r.d2h;
+    report->kernel_launches = launches_so_far() - l0;
+  }
+  return st;
+}
+
+// ---------------------------------------------------------------- step entry points
+size_t tsvd_gram_scratch_bytes(int64_t rows, int64_t n, int32_t precision) {
+  if (rows <= 0 || n <= 0) return 0;
+  if (precision == TSVD_GRAM_FP32) return 0;
+  return gram_tc_scratch_bytes(rows, n, precision);
+}
+
+tsvd_status tsvd_gram_accumulate(const float *dA, int64_t rows, int64_t n, int64_t ld, double *dG,
+                                 int32_t precision, void *scratch, size_t scratch_bytes, void *stream) {
+  if (rows < 0 || n <= 0 || ld < n || !dG || (rows > 0 && !dA)) return TSVD_EINVAL;
+  if (precision < 0 || precision > 2) return TSVD_EINVAL;
+  if (precision != TSVD_GRAM_FP32) {
+    if (scratch_bytes < gram_tc_scratch_bytes(rows, n, precision)) return TSVD_EINVAL;
+    if (scratch && (reinterpret_cast<uintptr_t>(scratch) & 255) != 0) return TSVD_EINVAL;
+  }
+  return gram_dispatch(dA, rows, n, ld, dG, precision, scratch, scratch_bytes, static_cast<cudaStream_t>(stream));
+}
+
+tsvd_status tsvd_csr_gram_apply(int64_t rows, int64_t n, const int64_t *row_ptr, const int32_t *col_idx,
+                                const float *values, const float *v, float *w, double *ss, int32_t scatter,
+                                void *stream) {
+  if (rows < 0 || n <= 0 || !row_ptr || !v || !ss || (scatter && !w)) return TSVD_EINVAL;
+  if (rows == 0) return TSVD_OK;
+  // mean row length from the block's first and last offsets
+  int64_t e[2];
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  TSVD_CUDA(cudaMemcpyAsync(&e[0], row_ptr, 8, cudaMemcpyDeviceToHost, s));
+  TSVD_CUDA(cudaMemcpyAsync(&e[1], row_ptr + rows, 8, cudaMemcpyDeviceToHost, s));
+  TSVD_CUDA(cudaStreamSynchronize(s));
+  const double avg = (double)(e[1] - e[0]) / (double)rows;
+  return launch_csr_pair(rows, n, row_ptr, col_idx, values, v, w, ss, scatter, avg, s);
+}
+
+size_t tsvd_power_scratch_bytes(int64_t n, int64_t l) { return power_scratch_bytes(n, l); }
+
+tsvd_status tsvd_power_dense(int64_t n, const float *G32, const double *G64, const double *V64,
+                             const double *sigma2, int64_t l, double *x, double eps, int32_t max_iter,
+                             int32_t iters_override, int32_t sign_convention, double *out_sigma2, int32_t *info,
+                             void *scratch, size_t scratch_bytes, void *stream) {
+  if (iters_override <= 0 && !(eps > 0.0 && eps < 1.0)) return TSVD_EINVAL;
+  return launch_power_dense(n, G32, G64, V64, sigma2, l, x, eps, max_iter, iters_override, sign_convention,
+                            out_sigma2, info, scratch, scratch_bytes, static_cast<cudaStream_t>(stream));
+}
+
+tsvd_status tsvd_gram_symmetrize(int64_t n, const double *G64, float *G32, void *stream) {
+  if (n <= 0 || !G64 || !G32) return TSVD_EINVAL;
+  return launch_symmetrize(n, G64, G32, static_cast<cudaStream_t>(stream));
+}
+
+tsvd_status tsvd_start_draws(uint64_t seed, int64_t l, int64_t n, double *x, void *stream) {
+  if (n <= 0 || l < 0 || !x) return TSVD_EINVAL;
+  return launch_start_draws(seed, l, n, x, static_cast<cudaStream_t>(stream));
+}
+
+tsvd_status tsvd_philox4x32_10(const uint32_t *ctr, const uint32_t *key, uint32_t *out, int64_t count,
+                               void *stream) {
+  if (count < 0 || (count > 0 && (!ctr || !key || !out))) return TSVD_EINVAL;
+  return launch_philox_raw(ctr, key, out, count, static_cast<cudaStream_t>(stream));
+}
+
+tsvd_status tsvd_left_vectors(const float *dA, int64_t rows, int64_t n, int64_t ld, const float *V, int64_t ldv,
+                              int64_t k, const double *sigma, float *U, int64_t ldu, void *stream) {
+  if (rows < 0 || n <= 0 || k <= 0 || ld < n || ldv < n || ldu < rows || !V || !sigma || !U ||
+      (rows > 0 && !dA))
+    return TSVD_EINVAL;
+  return launch_left_dense(dA, rows, n, ld, V, ldv, k, sigma, U, ldu, static_cast<cudaStream_t>(stream));
+}
+
+tsvd_status tsvd_csr_partition(int64_t m, const int64_t *row_ptr, int64_t block_rows, int64_t *block_start,
+                               int64_t *n_blocks, int64_t *max_block_nnz) {
+  if (m <= 0 || !row_ptr || block_rows <= 0 || !block_start || !n_blocks) return TSVD_EINVAL;
+  int64_t nb = 0, mx = 0;
+  for (int64_t r = 0; r < m; r += block_rows) {
+    block_start[nb++] = r;
+    const int64_t r1 = std::min(m, r + block_rows);
+    mx = std::max(mx, row_ptr[r1] - row_ptr[r]);
+  }
+  block_start[nb] = m;
+  *n_blocks = nb;
+  if (max_block_nnz) *max_block_nnz = mx;
+  return TSVD_OK;
+}
+
+tsvd_status tsvd_host_alloc(void **ptr, size_t bytes) {
+  if (!ptr) return TSVD_EINVAL;
+  *ptr = nullptr;
+  if (bytes == 0) return TSVD_EINVAL;
+  TSVD_CUDA(cudaHostAlloc(ptr, bytes, cudaHostAllocPortable));
+  return TSVD_OK;
+}
+
+tsvd_status tsvd_host_free(void *ptr) {
+  if (!ptr) return TSVD_OK;
+  TSVD_CUDA(cudaFreeHost(ptr));
+  return TSVD_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,187 @@
+// Shared host/device helpers of the tsvd library (internal header).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string>
+
+#include "tsvd.h"
+
+namespace tsvd {
+
+// ---------------------------------------------------------------- host side
+void set_cuda_error(cudaError_t e, const char *what, const char *file, int line);
+void set_error_text(const std::string &s);
+
+#define TSVD_CUDA(call)                                                         \
+  do {                                                                          \
+    cudaError_t e_ = (call);                                                    \
+    if (e_ != cudaSuccess) {                                                    \
+      ::tsvd::set_cuda_error(e_, #call, __FILE__, __LINE__);                    \
+      return TSVD_ECUDA;                                                        \
+    }                                                                           \
+  } while (0)
+
+#define TSVD_LAUNCHED()                                                         \
+  do {                                                                          \
+    cudaError_t e_ = cudaGetLastError();                                        \
+    if (e_ != cudaSuccess) {                                                    \
+      ::tsvd::set_cuda_error(e_, "kernel launch", __FILE__, __LINE__);          \
+      return TSVD_ECUDA;                                                        \
+    }                                                                           \
+    ::tsvd::count_launch();                                                     \
+  } while (0)
+
+#define TSVD_TRY(expr)                                                          \
+  do {                                                                          \
+    tsvd_status s_ = (expr);                                                    \
+    if (s_ != TSVD_OK) return s_;                                               \
+  } while (0)
+
+// Per-thread count of kernels this library launched (reported per call).
+void count_launch();
+int64_t launches_so_far();
+
+inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+inline int64_t round_up(int64_t a, int64_t b) { return ceil_div(a, b) * b; }
+
+struct DeviceInfo {
+  int device = -1;
+  int sms = 0;
+  int cc_major = 0, cc_minor = 0;
+  size_t smem_optin = 0;
+};
+tsvd_status device_info(DeviceInfo *out);
+
+// ------------------------------------------------------------- device side
+// A bounded wait gives up after this many nanoseconds of %globaltimer.
+constexpr uint64_t kWaitLimitNs = 2000000000ull;  // 2 s
+
+__device__ __forceinline__ uint64_t global_timer_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ float warp_sumf(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Sum over the block (all threads get the result).  `red` needs 33 doubles.
+__device__ __forceinline__ double block_sum(double v, double *red) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nw = (blockDim.x + 31) >> 5;
+  v = warp_sum(v);
+  __syncthreads();
+  if (lane == 0) red[warp] = v;
+  __syncthreads();
+  if (warp == 0) {
+    double t = lane < nw ? red[lane] : 0.0;
+    t = warp_sum(t);
+    if (lane == 0) red[32] = t;
+  }
+  __syncthreads();
+  return red[32];
+}
+
+// Grid-wide barrier for a cooperative launch.  bar[0] counts arrivals, bar[1]
+// is the generation.  Waits are bounded: past kWaitLimitNs, or when another
+// block has raised *err, the waiter sets *err and returns false.
+__device__ __forceinline__ bool grid_barrier(unsigned *bar, int *err) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned *vgen = bar + 1;
+    volatile int *verr = err;
+    const unsigned g = *vgen;
+    __threadfence();
+    const unsigned arrived = atomicAdd(bar, 1u);
+    int ok = 1;
+    if (arrived == gridDim.x * gridDim.y * gridDim.z - 1) {
+      atomicExch(bar, 0u);
+      __threadfence();
+      atomicAdd(bar + 1, 1u);
+    } else {
+      const uint64_t t0 = global_timer_ns();
+      while (*vgen == g) {
+        if (*verr) { ok = 0; break; }
+        if (global_timer_ns() - t0 > kWaitLimitNs) {
+          atomicExch(err, 1);
+          ok = 0;
+          break;
+        }
+        __nanosleep(32);
+      }
+    }
+    __threadfence();
+    if (*verr) ok = 0;
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+// ------------------------------------------------------------ launchers
+// Each returns TSVD_OK or an error; they only enqueue work on `stream`.
+// ev0/ev1 (optional) are recorded on `stream` right around the Gram kernel.
+tsvd_status launch_gram_simt(const float *A, int64_t rows, int64_t n, int64_t ld, double *G,
+                             cudaStream_t stream, cudaEvent_t ev0 = nullptr, cudaEvent_t ev1 = nullptr);
+size_t gram_tc_scratch_bytes(int64_t rows, int64_t n, int precision);
+tsvd_status launch_gram_tc(const float *A, int64_t rows, int64_t n, int64_t ld, double *G,
+                           int precision, void *scratch, size_t scratch_bytes, cudaStream_t stream,
+                           cudaEvent_t ev0 = nullptr, cudaEvent_t ev1 = nullptr);
+
+size_t power_scratch_bytes(int64_t n, int64_t l);
+tsvd_status launch_power_dense(int64_t n, const float *G32, const double *G64, const double *V64,
+                               const double *sigma2, int64_t l, double *x, double eps,
+                               int max_iter, int iters_override, int sign_convention,
+                               double *out_sigma2, int *info, void *scratch, size_t scratch_bytes,
+                               cudaStream_t stream);
+tsvd_status launch_symmetrize(int64_t n, const double *G64, float *G32, cudaStream_t stream);
+tsvd_status launch_start_draws(uint64_t seed, int64_t l, int64_t n, double *x, cudaStream_t stream);
+tsvd_status launch_philox_raw(const uint32_t *ctr, const uint32_t *key, uint32_t *out,
+                              int64_t count, cudaStream_t stream);
+tsvd_status launch_sigma_from_sigma2(const double *sig2, double *sigma, int64_t k,
+                                     cudaStream_t stream);
+tsvd_status launch_f64_to_f32(const double *src, float *dst, int64_t count, cudaStream_t stream);
+
+tsvd_status launch_left_dense(const float *A, int64_t rows, int64_t n, int64_t ld, const float *V,
+                              int64_t ldv, int64_t k, const double *sigma, float *U, int64_t ldu,
+                              cudaStream_t stream);
+
+tsvd_status launch_csr_pair(int64_t rows, int64_t n, const int64_t *row_ptr,
+                            const int32_t *col_idx, const float *values, const float *v, float *w,
+                            double *ss, int scatter, double avg_nnz, cudaStream_t stream);
+tsvd_status launch_csr_left(int64_t rows, const int64_t *row_ptr, const int32_t *col_idx,
+                            const float *values, const float *Vr, int64_t ldk, int64_t k,
+                            const double *sigma, float *U, int64_t ldu, double avg_nnz,
+                            cudaStream_t stream);
+
+// Vector-level kernels of the streamed (CSR) power step; see k_vec.cu.
+struct VecScratch {
+  double *part;     // grid x kPartStride partial sums
+  double *coef;     // deflation coefficients (k)
+  double *scal;     // scalars: [0] ww, [1] vw, [2] vv, [3] xx, [4] 1/||w||, ...
+  int *info;        // [0] iters, [1] status, [2] done flag, [3] reserved
+  int grid;
+};
+constexpr int kVecPartStride = 40;
+constexpr int kVecMaxCols = 32;  // deflation columns handled per chunk
+size_t vec_scratch_bytes(int grid);
+tsvd_status launch_vec_normalize_f64_to_f32(const double *x, float *v, int64_t n, VecScratch sc,
+                                            cudaStream_t stream);
+tsvd_status launch_vec_deflate_step(int64_t n, const float *Vr, int64_t ldk, const double *sig2,
+                                    int64_t l, const float *v, float *w, float *vnext, double eps,
+                                    int max_iter, int iters_override, double scale, VecScratch sc,
+                                    int orth_only, cudaStream_t stream);
+tsvd_status launch_vec_store_column(int64_t n, const float *v, float *Vr, int64_t ldk, int64_t l,
+                                    int sign_convention, VecScratch sc, cudaStream_t stream);
+
+}  // namespace tsvd

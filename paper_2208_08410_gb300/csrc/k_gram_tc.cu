@@ -1,0 +1,522 @@
+// Dense Gram accumulation G += A_b^T A_b on the 5th-generation tensor cores
+// (tcgen05 + TMEM + TMA), the Gram step of the method (B = X^T X, Alg. 2;
+// block by block over row batches, Sec. V-C / Alg. 3).
+//
+// Two kernels per row block:
+//  1. prep: transpose A_b (rows x n, row-major) into At (n x Kp, K-major, the
+//     row index becomes contiguous) and round every value to TF32 with
+//     round-to-nearest-even.  For TF32X3 it also writes lo = tf32(a - hi), so
+//     a = hi + lo to ~2^-22 relative and hi*hi + hi*lo + lo*hi recovers the
+//     FP32 product to about FP32 accuracy (3xTF32, Ootomo & Yokota 2022).
+//     Kp is rows rounded up to 32 and the pad is zero.
+//  2. syrk: a persistent warp-specialised kernel.  A work unit is one
+//     128 x 256 tile (I, J) of G with J0 <= I0 + 127 (only tiles touching the
+//     lower triangle: the symmetric task reuse of Sec. V-C) and one slice of
+//     the K = row range.  Warp 0 streams 128-row (A operand) and 256-row
+//     (B operand) slabs of At into a 4-stage shared-memory ring with TMA
+//     (128-byte swizzle, no multicast); warp 1 issues tcgen05.mma kind::tf32
+//     (M=128, N=256, K=8) into one of two 256-column TMEM accumulators;
+//     warps 2-5 drain the other accumulator with tcgen05.ld and add the FP32
+//     partial sums into the FP64 G with coalesced atomics, so the epilogue of
+//     one unit overlaps the MMAs of the next.
+// Every wait is bounded (global timer); on timeout the kernel raises an error
+// flag, stops issuing, waits (bounded) for its own copies and MMAs, frees
+// TMEM and returns.
+#include <cuda.h>
+
+#include <algorithm>
+
+#include "common.cuh"
+
+namespace tsvd {
+namespace {
+
+constexpr int TC_THREADS = 192;
+constexpr int TM = 128;          // MMA M (rows of At from block I)
+constexpr int TN = 256;          // MMA N (rows of At from block J)
+constexpr int TK = 32;           // K per stage (32 x 4 B = one 128-byte swizzle row)
+constexpr int A_SLAB = TM * TK * 4;  // 16 KB
+constexpr int B_SLAB = TN * TK * 4;  // 32 KB
+
+template <int PREC>
+struct Cfg {
+  static constexpr int kParts = PREC == TSVD_GRAM_TF32X3 ? 2 : 1;  // hi (and lo) operands
+  static constexpr int kStageBytes = kParts * (A_SLAB + B_SLAB);
+  static constexpr int kStages = PREC == TSVD_GRAM_TF32X3 ? 2 : 4;
+  static constexpr int kSmem = kStages * kStageBytes + 1024 /*align*/ + 256 /*barriers*/;
+};
+
+// ---------------------------------------------------------------- PTX helpers
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait on an mbarrier phase; false on timeout or when *err is raised.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int *err) {
+  if (mbar_try(bar, parity)) return true;
+  const uint64_t t0 = global_timer_ns();
+  for (uint32_t spin = 1;; ++spin) {
+    if (mbar_try(bar, parity)) return true;
+    if ((spin & 255u) == 0) {
+      if (*(volatile int *)err) return false;
+      if (global_timer_ns() - t0 > kWaitLimitNs) {
+        atomicExch(err, 2);
+        return false;
+      }
+    }
+  }
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map, int x, int y, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+          dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
+      : "memory");
+}
+
+// UMMA shared-memory descriptor: K-major operand, 128-byte swizzle, 8-row
+// core-matrix groups 1024 bytes apart (SBO), start address in 16-byte units.
+__device__ __forceinline__ uint64_t umma_desc_sw128(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)1 << 16;             // leading byte offset (unused for swizzled K-major)
+  d |= (uint64_t)(1024 >> 4) << 32;   // stride byte offset
+  d |= (uint64_t)1 << 46;             // descriptor version (sm_100 family)
+  d |= (uint64_t)2 << 61;             // swizzle mode: 128B
+  return d;
+}
+
+// Instruction descriptor, kind::tf32: D F32, A/B TF32, both K-major, M x N.
+__host__ __device__ constexpr uint32_t idesc_tf32(int M, int N) {
+  return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void umma_tf32(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+          tmem_d),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc)
+      : "memory");
+}
+
+__device__ __forceinline__ void umma_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,%19,"
+      "%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
+        "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// ---------------------------------------------------------------- TF32 rounding
+// Round an FP32 value to the nearest TF32 value (10 explicit mantissa bits),
+// ties to even, by integer arithmetic on the encoding; non-finite values pass.
+__device__ __forceinline__ float tf32_rne(float x) {
+  const uint32_t u = __float_as_uint(x);
+  if ((u & 0x7f800000u) == 0x7f800000u) return x;  // Inf / NaN unchanged
+  return __uint_as_float((u + 0x0fffu + ((u >> 13) & 1u)) & 0xffffe000u);
+}
+
+// ---------------------------------------------------------------- prep kernel
+// At[c][r] = tf32(A[r][c]) (and lo part), tiles of 64 rows x 64 columns.
+template <int PARTS>
+__global__ void __launch_bounds__(256) prep_kernel(const float *__restrict__ A, int64_t rows, int64_t n, int64_t ld,
+                                                   float *__restrict__ hi, float *__restrict__ lo, int64_t Kp,
+                                                   int vec) {
+  __shared__ float s[64][65];
+  const int64_t r0 = (int64_t)blockIdx.x * 64;
+  const int64_t c0 = (int64_t)blockIdx.y * 64;
+  const int tid = threadIdx.x;
+#pragma unroll
+  for (int it = 0; it < 4; ++it) {
+    const int idx = tid + it * 256;
+    const int rr = idx >> 4, cc = (idx & 15) * 4;
+    const int64_t r = r0 + rr, c = c0 + cc;
+    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (r < rows) {
+      const float *row = A + r * ld;
+      if (vec && c + 3 < n) {
+        v = __ldg(reinterpret_cast<const float4 *>(row + c));
+      } else {
+        if (c < n) v.x = __ldg(row + c);
+        if (c + 1 < n) v.y = __ldg(row + c + 1);
+        if (c + 2 < n) v.z = __ldg(row + c + 2);
+        if (c + 3 < n) v.w = __ldg(row + c + 3);
+      }
+    }
+    s[cc][rr] = v.x;
+    s[cc + 1][rr] = v.y;
+    s[cc + 2][rr] = v.z;
+    s[cc + 3][rr] = v.w;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int it = 0; it < 4; ++it) {
+    const int idx = tid + it * 256;
+    const int cc = idx >> 4, rr = (idx & 15) * 4;
+    const int64_t c = c0 + cc, r = r0 + rr;
+    if (c >= n || r >= Kp) continue;
+    float x[4] = {s[cc][rr], s[cc][rr + 1], s[cc][rr + 2], s[cc][rr + 3]};
+    float4 h, l;
+    float *hp = &h.x, *lp = &l.x;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const float t = tf32_rne(x[q]);
+      hp[q] = t;
+      lp[q] = tf32_rne(x[q] - t);
+    }
+    *reinterpret_cast<float4 *>(hi + c * Kp + r) = h;
+    if (PARTS == 2) *reinterpret_cast<float4 *>(lo + c * Kp + r) = l;
+  }
+}
+
+// ---------------------------------------------------------------- syrk kernel
+struct TcArgs {
+  double *G;
+  int64_t n;
+  int64_t Kp;         // padded K (rows) of At
+  int64_t ksplit;     // rows per work unit (multiple of TK)
+  int n_splits;
+  int n_tiles;
+  int n_iblk;         // ceil(n / 128)
+  int *err;
+};
+
+// tile t -> (bi, bj): tiles are listed by I block; block bi has bi/2 + 1 tiles
+__device__ __forceinline__ void tc_tile(int t, int &bi, int &bj) {
+  int b = 0;
+  // C(b) = number of tiles before block b: q(q+1) for b = 2q, (q+1)^2 for b = 2q+1
+  int lo = 0, hi = 1 << 16;
+  while (lo < hi) {  // largest b with C(b) <= t
+    const int mid = (lo + hi + 1) >> 1;
+    const long long q = mid >> 1;
+    const long long c = (mid & 1) ? (q + 1) * (q + 1) : q * (q + 1);
+    if (c <= t) lo = mid; else hi = mid - 1;
+  }
+  b = lo;
+  const long long q = b >> 1;
+  const long long cb = (b & 1) ? (q + 1) * (q + 1) : q * (q + 1);
+  bi = b;
+  bj = (int)(t - cb);
+}
+
+template <int PREC>
+__global__ void __launch_bounds__(TC_THREADS, 1)
+syrk_tc_kernel(const __grid_constant__ CUtensorMap map_hi, const __grid_constant__ CUtensorMap map_lo, TcArgs a) {
+  using C = Cfg<PREC>;
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char *smem = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint64_t *bars = reinterpret_cast<uint64_t *>(smem + C::kStages * C::kStageBytes);
+  // bars: full[kStages], empty[kStages], tfull[2], tempty[2], final
+  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 2 * C::kStages + 5);
+  const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + C::kStages);
+  const uint32_t tfull0 = smem_u32(bars + 2 * C::kStages), tempty0 = smem_u32(bars + 2 * C::kStages + 2);
+  const uint32_t final_bar = smem_u32(bars + 2 * C::kStages + 4);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int units = a.n_tiles * a.n_splits;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < C::kStages; ++s) {
+      mbar_init(full0 + 8 * s, 1);
+      mbar_init(empty0 + 8 * s, 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(tfull0 + 8 * b, 1);
+      mbar_init(tempty0 + 8 * b, 4);
+    }
+    mbar_init(final_bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(smem_u32(tmem_slot)));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0) {
+    // ------------------------------------------------ TMA producer
+    if (lane == 0) {
+      uint32_t it = 0;
+      uint32_t issued_unconsumed = 0;
+      bool ok = true;
+      for (int u = blockIdx.x; u < units && ok; u += gridDim.x) {
+        const int t = u % a.n_tiles, sp = u / a.n_tiles;
+        int bi, bj;
+        tc_tile(t, bi, bj);
+        const int64_t k0 = (int64_t)sp * a.ksplit;
+        const int64_t k1 = min(a.Kp, k0 + a.ksplit);
+        for (int64_t kk = k0; kk < k1; kk += TK, ++it) {
+          const uint32_t s = it % C::kStages, ph = (it / C::kStages) & 1u;
+          if (!mbar_wait(empty0 + 8 * s, ph ^ 1u, a.err)) { ok = false; break; }
+          unsigned char *st = smem + s * C::kStageBytes;
+          mbar_expect_tx(full0 + 8 * s, C::kStageBytes);
+          const int x = (int)kk;
+          tma_load_2d(smem_u32(st), &map_hi, x, bi * TM, full0 + 8 * s);
+          tma_load_2d(smem_u32(st + A_SLAB), &map_hi, x, bj * TN, full0 + 8 * s);
+          tma_load_2d(smem_u32(st + A_SLAB + B_SLAB / 2), &map_hi, x, bj * TN + TN / 2, full0 + 8 * s);
+          if (C::kParts == 2) {
+            unsigned char *sl = st + A_SLAB + B_SLAB;
+            tma_load_2d(smem_u32(sl), &map_lo, x, bi * TM, full0 + 8 * s);
+            tma_load_2d(smem_u32(sl + A_SLAB), &map_lo, x, bj * TN, full0 + 8 * s);
+            tma_load_2d(smem_u32(sl + A_SLAB + B_SLAB / 2), &map_lo, x, bj * TN + TN / 2, full0 + 8 * s);
+          }
+          issued_unconsumed = it + 1;
+        }
+      }
+      if (!ok) {
+        // drain: wait (bounded) for every stage we filled to land
+        for (uint32_t j = (issued_unconsumed > C::kStages ? issued_unconsumed - C::kStages : 0);
+             j < issued_unconsumed; ++j)
+          mbar_wait(full0 + 8 * (j % C::kStages), (j / C::kStages) & 1u, a.err);
+      }
+    }
+  } else if (warp == 1) {
+    // ------------------------------------------------ MMA issuer
+    if (lane == 0) {
+      constexpr uint32_t idesc = idesc_tf32(TM, TN);
+      uint32_t it = 0, uc = 0;
+      bool ok = true;
+      for (int u = blockIdx.x; u < units && ok; u += gridDim.x, ++uc) {
+        const int sp = u / a.n_tiles;
+        const int64_t k0 = (int64_t)sp * a.ksplit;
+        const int64_t k1 = min(a.Kp, k0 + a.ksplit);
+        const uint32_t acc = uc & 1u, aph = (uc >> 1) & 1u;
+        if (!mbar_wait(tempty0 + 8 * acc, aph ^ 1u, a.err)) { ok = false; break; }
+        tc_fence_after();
+        const uint32_t dtm = tmem + acc * TN;
+        uint32_t first = 1;
+        for (int64_t kk = k0; kk < k1; kk += TK, ++it) {
+          const uint32_t s = it % C::kStages, ph = (it / C::kStages) & 1u;
+          if (!mbar_wait(full0 + 8 * s, ph, a.err)) { ok = false; break; }
+          tc_fence_after();
+          const uint32_t st = smem_u32(smem + s * C::kStageBytes);
+          const uint64_t dah = umma_desc_sw128(st), dbh = umma_desc_sw128(st + A_SLAB);
+#pragma unroll
+          for (int k8 = 0; k8 < TK / 8; ++k8) {
+            const uint64_t off = (uint64_t)(k8 * 32) >> 4;  // 32 bytes per K=8 step
+            umma_tf32(dtm, dah + off, dbh + off, idesc, first ? 0u : 1u);
+            first = 0;
+            if (C::kParts == 2) {
+              const uint32_t sl = st + A_SLAB + B_SLAB;
+              const uint64_t dal = umma_desc_sw128(sl), dbl = umma_desc_sw128(sl + A_SLAB);
+              umma_tf32(dtm, dah + off, dbl + off, idesc, 1u);
+              umma_tf32(dtm, dal + off, dbh + off, idesc, 1u);
+            }
+          }
+          umma_commit(empty0 + 8 * s);  // frees the stage when these MMAs finish
+        }
+        if (!ok) break;
+        umma_commit(tfull0 + 8 * acc);  // accumulator ready for the epilogue
+      }
+      // wait for every MMA this thread issued before TMEM is released
+      umma_commit(final_bar);
+      mbar_wait(final_bar, 0, a.err);
+    }
+  } else {
+    // ------------------------------------------------ epilogue: TMEM -> FP64 G
+    const int q = warp & 3;  // TMEM lane quarter this warp may access
+    const int row = q * 32 + lane;
+    uint32_t uc = 0;
+    for (int u = blockIdx.x; u < units; u += gridDim.x, ++uc) {
+      const int t = u % a.n_tiles;
+      int bi, bj;
+      tc_tile(t, bi, bj);
+      const uint32_t acc = uc & 1u, aph = (uc >> 1) & 1u;
+      if (!mbar_wait(tfull0 + 8 * acc, aph, a.err)) break;
+      tc_fence_after();
+      const int64_t gi = (int64_t)bi * TM + row;
+      const int64_t jbase = (int64_t)bj * TN;
+#pragma unroll 1
+      for (int c0 = 0; c0 < TN; c0 += 32) {
+        uint32_t r[32];
+        tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + acc * TN + c0, r);
+        if (gi < a.n) {
+#pragma unroll
+          for (int j = 0; j < 32; ++j) {
+            const int64_t gj = jbase + c0 + j;
+            if (gj <= gi && gj < a.n) atomicAdd(a.G + gj * a.n + gi, (double)__uint_as_float(r[j]));
+          }
+        }
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(tempty0 + 8 * acc);
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 1) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem));
+}
+
+// ---------------------------------------------------------------- host side
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+tsvd_status get_encode(EncodeTiledFn *out) {
+  static EncodeTiledFn fn = nullptr;
+  if (!fn) {
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    TSVD_CUDA(cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q));
+    if (q != cudaDriverEntryPointSuccess || !p) {
+      set_error_text("cuTensorMapEncodeTiled not available");
+      return TSVD_ECUDA;
+    }
+    fn = reinterpret_cast<EncodeTiledFn>(p);
+  }
+  *out = fn;
+  return TSVD_OK;
+}
+
+tsvd_status make_map(CUtensorMap *map, const float *base, int64_t n, int64_t Kp) {
+  EncodeTiledFn enc;
+  TSVD_TRY(get_encode(&enc));
+  const cuuint64_t dims[2] = {(cuuint64_t)Kp, (cuuint64_t)n};
+  const cuuint64_t strides[1] = {(cuuint64_t)Kp * 4};
+  const cuuint32_t box[2] = {(cuuint32_t)TK, (cuuint32_t)TM};
+  const cuuint32_t estr[2] = {1, 1};
+  const CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float *>(base), dims, strides, box, estr,
+                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) {
+    set_error_text("cuTensorMapEncodeTiled failed: " + std::to_string((int)r));
+    return TSVD_ECUDA;
+  }
+  return TSVD_OK;
+}
+
+int64_t padded_k(int64_t rows) { return round_up(std::max<int64_t>(rows, 1), TK); }
+
+}  // namespace
+
+size_t gram_tc_scratch_bytes(int64_t rows, int64_t n, int precision) {
+  if (precision == TSVD_GRAM_FP32 || rows <= 0 || n <= 0) return 0;
+  const int parts = precision == TSVD_GRAM_TF32X3 ? 2 : 1;
+  // status word (first 1024 bytes), then At (n x Kp) per part, 1024-byte aligned;
+  // +1024 lets the caller's 256-byte aligned pointer be rounded up
+  return 2048 + (size_t)parts * (size_t)round_up(n * padded_k(rows) * 4, 1024);
+}
+
+// rows per work unit (K slice); tunable through TSVD_TC_KSPLIT for experiments
+static int64_t tc_ksplit_rows() {
+  static int64_t v = -1;
+  if (v < 0) {
+    const char *e = getenv("TSVD_TC_KSPLIT");
+    v = e ? std::max<int64_t>(TK, round_up(atoll(e), TK)) : 8192;
+  }
+  return v;
+}
+
+tsvd_status launch_gram_tc(const float *A, int64_t rows, int64_t n, int64_t ld, double *G, int precision,
+                           void *scratch, size_t scratch_bytes, cudaStream_t stream, cudaEvent_t ev0,
+                           cudaEvent_t ev1) {
+  if (rows <= 0) return TSVD_OK;
+  if (precision != TSVD_GRAM_TF32 && precision != TSVD_GRAM_TF32X3) return TSVD_EINVAL;
+  if (n > (int64_t)TM * 65535) return TSVD_EUNSUPPORTED;
+  DeviceInfo di;
+  TSVD_TRY(device_info(&di));
+  if (di.cc_major != 10) return TSVD_EUNSUPPORTED;  // tcgen05 needs the sm_100 family
+  if (!scratch || scratch_bytes < gram_tc_scratch_bytes(rows, n, precision)) return TSVD_EINVAL;
+  if ((reinterpret_cast<uintptr_t>(scratch) & 255) != 0) return TSVD_EINVAL;
+  const int parts = precision == TSVD_GRAM_TF32X3 ? 2 : 1;
+  const int64_t Kp = padded_k(rows);
+  unsigned char *base = static_cast<unsigned char *>(scratch);
+  int *err = reinterpret_cast<int *>(base);  // status word: 0 ok, nonzero = a bounded wait gave up
+  const uintptr_t al = (reinterpret_cast<uintptr_t>(base) + 1024 + 1023) & ~uintptr_t(1023);
+  float *hi = reinterpret_cast<float *>(al);
+  float *lo = parts == 2 ? reinterpret_cast<float *>(al + round_up(n * Kp * 4, 1024)) : hi;
+  if (al + (size_t)parts * round_up(n * Kp * 4, 1024) > reinterpret_cast<uintptr_t>(base) + scratch_bytes)
+    return TSVD_EINVAL;
+
+  // 1. prep: transpose + TF32 rounding (+ split)
+  {
+    const bool vec = (ld % 4 == 0) && ((reinterpret_cast<uintptr_t>(A) & 15) == 0);
+    dim3 grid((unsigned)ceil_div(Kp, 64), (unsigned)ceil_div(n, 64));
+    if (grid.y > 65535) return TSVD_EUNSUPPORTED;
+    if (parts == 2)
+      prep_kernel<2><<<grid, 256, 0, stream>>>(A, rows, n, ld, hi, lo, Kp, vec ? 1 : 0);
+    else
+      prep_kernel<1><<<grid, 256, 0, stream>>>(A, rows, n, ld, hi, lo, Kp, vec ? 1 : 0);
+    TSVD_LAUNCHED();
+  }
+  // 2. persistent tcgen05 SYRK over the lower-triangle tiles
+  CUtensorMap mh, ml;
+  TSVD_TRY(make_map(&mh, hi, n, Kp));
+  TSVD_TRY(make_map(&ml, lo, n, Kp));
+  TcArgs a;
+  a.G = G;
+  a.n = n;
+  a.Kp = Kp;
+  a.ksplit = std::min<int64_t>(tc_ksplit_rows(), Kp);
+  a.n_splits = (int)ceil_div(Kp, a.ksplit);
+  a.n_iblk = (int)ceil_div(n, TM);
+  {
+    const int64_t q = (a.n_iblk) >> 1;  // tiles = C(n_iblk)
+    a.n_tiles = (int)((a.n_iblk & 1) ? (q + 1) * (q + 1) : q * (q + 1));
+  }
+  a.err = err;
+  TSVD_CUDA(cudaMemsetAsync(err, 0, 4, stream));
+  const int64_t units = (int64_t)a.n_tiles * a.n_splits;
+  const int grid = (int)std::min<int64_t>(units, di.sms);
+  if (ev0) TSVD_CUDA(cudaEventRecord(ev0, stream));
+  if (precision == TSVD_GRAM_TF32) {
+    static thread_local bool attr1 = false;
+    if (!attr1) {
+      TSVD_CUDA(cudaFuncSetAttribute(syrk_tc_kernel<TSVD_GRAM_TF32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     Cfg<TSVD_GRAM_TF32>::kSmem));
+      attr1 = true;
+    }
+    syrk_tc_kernel<TSVD_GRAM_TF32><<<grid, TC_THREADS, Cfg<TSVD_GRAM_TF32>::kSmem, stream>>>(mh, ml, a);
+  } else {
+    static thread_local bool attr2 = false;
+    if (!attr2) {
+      TSVD_CUDA(cudaFuncSetAttribute(syrk_tc_kernel<TSVD_GRAM_TF32X3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     Cfg<TSVD_GRAM_TF32X3>::kSmem));
+      attr2 = true;
+    }
+    syrk_tc_kernel<TSVD_GRAM_TF32X3><<<grid, TC_THREADS, Cfg<TSVD_GRAM_TF32X3>::kSmem, stream>>>(mh, ml, a);
+  }
+  TSVD_LAUNCHED();
+  if (ev1) TSVD_CUDA(cudaEventRecord(ev1, stream));
+  return TSVD_OK;
+}
+
+}  // namespace tsvd

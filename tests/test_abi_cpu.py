@@ -1,0 +1,181 @@
+"""Host-side checks of the C ABI: the library loads without a GPU, exports
+every symbol the header declares, validates its inputs in tsvd_plan (pure
+host work), sizes the device workspace under a budget, and partitions CSR
+row blocks exactly.  No compute call runs here."""
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+
+import synth
+from paper_2208_08410_gb300 import _binding as B
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def header_symbols():
+    names = []
+    for path in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if path.endswith(".h"):
+            text = open(os.path.join(ROOT, "include", path)).read()
+            names += re.findall(r"TSVD_API[^;(]*?\b(tsvd_\w+)\s*\(", text)
+    return names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    names = header_symbols()
+    assert len(names) >= 19
+    for nm in names:
+        assert hasattr(lib, nm), nm
+        assert nm in B.SIGNATURES, f"binding lacks {nm}"
+
+
+def test_status_strings(lib):
+    for s in range(9):
+        assert lib.tsvd_status_string(s)
+    assert lib.tsvd_status_string(99) == b"unknown status"
+    assert lib.tsvd_abi_version() == 1
+
+
+def _plan(A_desc, k, eps, opt=None):
+    h = C.c_void_p()
+    ws = C.c_size_t()
+    st = B.tsvd_plan(C.byref(h), C.byref(A_desc), k, eps, C.byref(opt) if opt is not None else None, C.byref(ws))
+    if st == B.TSVD_OK:
+        B.tsvd_destroy(h)
+    return st, ws.value
+
+
+def _dense_desc(m, n, ld=None, arr=None):
+    d = B.tsvd_matrix()
+    d.kind, d.location, d.m, d.n, d.ld = B.TSVD_DENSE_F32_ROWMAJOR, B.TSVD_HOST, m, n, ld or n
+    if arr is None:
+        arr = np.zeros((m, ld or n), dtype=np.float32)
+    d.values = arr.ctypes.data
+    return d, arr
+
+
+def _opts(**kw):
+    o = B.tsvd_options()
+    B.tsvd_options_init(C.byref(o))
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+def test_plan_validation_dense(lib):
+    d, keep = _dense_desc(100, 20)
+    assert _plan(d, 5, 1e-6)[0] == B.TSVD_OK
+    assert _plan(d, -1, 1e-6)[0] == B.TSVD_OK  # k = min(m, n)
+    assert _plan(d, 0, 1e-6)[0] == B.TSVD_EINVAL
+    assert _plan(d, 21, 1e-6)[0] == B.TSVD_EINVAL
+    assert _plan(d, 5, 0.0)[0] == B.TSVD_EINVAL
+    assert _plan(d, 5, 1.0)[0] == B.TSVD_EINVAL
+    ovr = np.array([3, 3, 3, 3, 3], dtype=np.int32)
+    assert _plan(d, 5, 0.0, _opts(iters_override=ovr.ctypes.data))[0] == B.TSVD_OK
+    bad = np.array([3, 0, 3, 3, 3], dtype=np.int32)
+    assert _plan(d, 5, 1e-6, _opts(iters_override=bad.ctypes.data))[0] == B.TSVD_EINVAL
+    assert _plan(d, 5, 1e-6, _opts(precision=7))[0] == B.TSVD_EINVAL
+    assert _plan(d, 5, 1e-6, _opts(n_buffers=1))[0] == B.TSVD_EINVAL
+    d2, keep2 = _dense_desc(100, 20)
+    d2.ld = 10
+    assert _plan(d2, 5, 1e-6)[0] == B.TSVD_EINVAL
+    wide, keep3 = _dense_desc(20, 100)
+    assert _plan(wide, 5, 1e-6)[0] == B.TSVD_EUNSUPPORTED  # the m < n branch is not built
+    d3, keep4 = _dense_desc(100, 20)
+    d3.m = 0
+    assert _plan(d3, 1, 1e-6)[0] == B.TSVD_EINVAL
+
+
+def test_plan_budget_and_streaming_layout(lib):
+    m, n, k = 1 << 16, 512, 8
+    d, keep = _dense_desc(m, n)
+    st, ws_res = _plan(d, k, 1e-6)
+    assert st == B.TSVD_OK and ws_res >= m * n * 4  # resident: A copied once
+    st, ws_cap = _plan(d, k, 1e-6, _opts(device_budget=48 << 20))
+    assert st == B.TSVD_OK and ws_cap <= 48 << 20  # streamed under the cap
+    st, _ = _plan(d, k, 1e-6, _opts(device_budget=1 << 20))
+    assert st == B.TSVD_EBUDGET
+
+
+def test_memory_model_avoids_the_residual(lib):
+    # Sec. III worked example scaled down: a sparse A whose dense residual
+    # would be huge plans a workspace of O(n k + nnz), never O(m n).
+    csr = synth.csr_uniform(1 << 17, 1 << 17, 4.0, seed=0)
+    d = B.tsvd_matrix()
+    d.kind, d.location, d.m, d.n = B.TSVD_CSR_F32_I32_I64, B.TSVD_HOST, csr["m"], csr["n"]
+    d.row_ptr, d.col_idx, d.values = (csr["row_ptr"].ctypes.data, csr["col_idx"].ctypes.data,
+                                      csr["values"].ctypes.data)
+    d.nnz = csr["values"].shape[0]
+    st, ws = _plan(d, 8, 1e-6)
+    assert st == B.TSVD_OK
+    dense_residual = csr["m"] * csr["n"] * 4
+    assert ws < dense_residual / 1000
+    assert ws < 64 * (csr["n"] * 8 + d.nnz * 8)
+
+
+def _csr_desc(csr):
+    d = B.tsvd_matrix()
+    d.kind, d.location, d.m, d.n = B.TSVD_CSR_F32_I32_I64, B.TSVD_HOST, csr["m"], csr["n"]
+    d.row_ptr, d.col_idx, d.values = (csr["row_ptr"].ctypes.data, csr["col_idx"].ctypes.data,
+                                      csr["values"].ctypes.data)
+    d.nnz = csr["values"].shape[0]
+    return d
+
+
+def test_plan_rejects_invalid_csr(lib):
+    csr = synth.csr_uniform(500, 300, 5.0, seed=1)
+    assert _plan(_csr_desc(csr), 4, 1e-6)[0] == B.TSVD_OK
+    bad = dict(csr)
+    bad["col_idx"] = csr["col_idx"].copy()
+    bad["col_idx"][17] = 300  # out of range
+    assert _plan(_csr_desc(bad), 4, 1e-6)[0] == B.TSVD_EINVAL
+    bad = dict(csr)
+    bad["row_ptr"] = csr["row_ptr"].copy()
+    bad["row_ptr"][10], bad["row_ptr"][11] = bad["row_ptr"][11] + 1, bad["row_ptr"][10]  # non-monotone
+    assert _plan(_csr_desc(bad), 4, 1e-6)[0] == B.TSVD_EINVAL
+    bad = dict(csr)
+    d = _csr_desc(bad)
+    d.nnz = d.nnz - 1  # row_ptr[m] != nnz
+    assert _plan(d, 4, 1e-6)[0] == B.TSVD_EINVAL
+
+
+@pytest.mark.parametrize("block_rows", [1, 7, 128, 1000, 4096])
+def test_csr_partition_is_bit_exact(lib, block_rows):
+    csr = synth.csr_uniform(3001, 2000, 9.0, seed=2)
+    m = csr["m"]
+    rp = csr["row_ptr"]
+    starts = np.zeros(m // block_rows + 2, dtype=np.int64)
+    nb = C.c_int64()
+    mx = C.c_int64()
+    assert B.tsvd_csr_partition(m, rp.ctypes.data, block_rows, starts.ctypes.data, C.byref(nb), C.byref(mx)) == 0
+    nb = nb.value
+    starts = starts[:nb + 1]
+    assert starts[0] == 0 and starts[-1] == m and np.all(np.diff(starts) > 0)
+    assert np.all(np.diff(starts)[:-1] == block_rows)
+    # concatenating the blocks reproduces the arrays byte for byte
+    cols, vals, rebased = [], [], []
+    biggest = 0
+    for b in range(nb):
+        r0, r1 = starts[b], starts[b + 1]
+        e0, e1 = rp[r0], rp[r1]
+        cols.append(csr["col_idx"][e0:e1])
+        vals.append(csr["values"][e0:e1])
+        brp = rp[r0:r1 + 1] - rp[r0]
+        assert np.array_equal(brp, rp[r0:r1 + 1] - e0)  # block_row_ptr[i] = row_ptr[r0+i] - row_ptr[r0]
+        rebased.append(brp[:-1] + e0)
+        biggest = max(biggest, e1 - e0)
+    assert np.concatenate(cols).tobytes() == csr["col_idx"].tobytes()
+    assert np.concatenate(vals).tobytes() == csr["values"].tobytes()
+    assert np.array_equal(np.concatenate(rebased + [rp[-1:]]), rp)
+    assert mx.value == biggest
+
+
+def test_loader_fails_loudly_without_library(tmp_path, monkeypatch):
+    from paper_2208_08410_gb300 import build as bld
+    monkeypatch.setattr(bld, "LIB", str(tmp_path / "missing.so"))
+    monkeypatch.setattr(B, "_lib", None)
+    with pytest.raises(RuntimeError, match="not built"):
+        B.load(build_if_missing=False)

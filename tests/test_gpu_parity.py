@@ -1,0 +1,386 @@
+"""GPU parity: every step of the CUDA path against the FP64 oracle on the
+same seeded inputs, called through the C ABI.
+
+Tolerances are derived from the arithmetic:
+  * Gram (FP32 CUDA cores): each slice sums at most K products in FP32 before
+    the FP64 add, so |dG_ij| <= (K+2) u32 (|A|^T |A|)_ij  (u32 = 2^-24).
+  * Power iteration on G32 = fp32(G) with FP32 products and FP64 sums: the
+    iterate follows the oracle's to ~1e-6; sigma^2 comes from FP64 G.
+  * Whole t-SVD: sigma relative error <= 1e-5 and angle <= 1e-4 for gapped
+    triplets (relative eigen-gap >= 0.05), compared on the same trajectory
+    (same start draws, the oracle's iteration counts forced).
+"""
+import ctypes as C
+import math
+import os
+
+import numpy as np
+import pytest
+
+import synth
+from oracle import philox
+from oracle import tsvd_ref as ref
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from paper_2208_08410_gb300 import _binding as B  # noqa: E402
+from paper_2208_08410_gb300 import tsvd  # noqa: E402
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+U32 = 2.0 ** -24
+
+
+def S():
+    return torch.cuda.current_stream().cuda_stream
+
+
+def dev(a, dtype=None):
+    t = torch.from_numpy(np.ascontiguousarray(a))
+    if dtype is not None:
+        t = t.to(dtype)
+    return t.cuda()
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return B.load()
+
+
+# ---------------------------------------------------------------- a7 start vectors
+def test_philox_matches_known_answers_and_oracle():
+    rows = []
+    for line in open(os.path.join(GOLDEN, "philox4x32_10_kat.txt")):
+        if line.strip() and not line.startswith("#"):
+            rows.append([int(x, 16) for x in line.split()])
+    rng = np.random.default_rng(0)
+    extra = rng.integers(0, 2 ** 32, size=(1000, 6), dtype=np.uint64)
+    ctr = np.array([r[0:4] for r in rows] + extra[:, :4].tolist(), dtype=np.uint32)
+    key = np.array([r[4:6] for r in rows] + extra[:, 4:6].tolist(), dtype=np.uint32)
+    d_ctr, d_key = dev(ctr.view(np.int32)), dev(key.view(np.int32))
+    d_out = torch.empty_like(d_ctr)
+    assert B.tsvd_philox4x32_10(d_ctr.data_ptr(), d_key.data_ptr(), d_out.data_ptr(), ctr.shape[0], S()) == 0
+    got = d_out.cpu().numpy().view(np.uint32)
+    assert [list(map(int, g)) for g in got[:3]] == [r[6:10] for r in rows]
+    want = philox.philox4x32_10(ctr, key)
+    assert np.array_equal(got, want)  # bit-exact
+
+
+@pytest.mark.parametrize("n", [1, 2, 257, 100001])
+def test_start_draws_match_oracle(n):
+    for seed, l in [(0, 0), (12345, 7)]:
+        x = torch.empty(n, dtype=torch.float64, device="cuda")
+        assert B.tsvd_start_draws(seed, l, n, x.data_ptr(), S()) == 0
+        want = philox.start_normals(seed, l, n)
+        assert np.max(np.abs(x.cpu().numpy() - want)) < 1e-13
+
+
+# ---------------------------------------------------------------- a2 Gram
+@pytest.mark.parametrize("rows,n,ld", [(1000, 256, 256), (777, 130, 130), (64, 5, 5), (5000, 300, 300),
+                                       (300, 129, 133), (1, 17, 17), (0, 40, 40)])
+def test_gram_fp32_matches_oracle(rows, n, ld):
+    rng = np.random.default_rng(rows + n)
+    Afull = rng.standard_normal((max(rows, 1), ld)).astype(np.float32)[:rows]
+    A = Afull[:, :n]
+    sentinel = -7.25
+    G = np.triu(np.zeros((n, n))) + np.tril(np.full((n, n), sentinel), -1)
+    dG = dev(G)
+    dA = dev(Afull) if rows else torch.empty(1, dtype=torch.float32, device="cuda")
+    assert B.tsvd_gram_accumulate(dA.data_ptr(), rows, n, ld, dG.data_ptr(), B.TSVD_GRAM_FP32, None, 0, S()) == 0
+    # accumulate a second time: G must double (+= semantics)
+    assert B.tsvd_gram_accumulate(dA.data_ptr(), rows, n, ld, dG.data_ptr(), B.TSVD_GRAM_FP32, None, 0, S()) == 0
+    got = dG.cpu().numpy()
+    ref_G = 2.0 * ref.gram(A)
+    absA = np.abs(A.astype(np.float64))
+    bound = 2.0 * (rows + 2) * U32 * (absA.T @ absA) + 1e-300
+    iu = np.triu_indices(n)
+    err = np.abs(got[iu] - ref_G[iu])
+    assert np.all(err <= bound[iu])
+    il = np.tril_indices(n, -1)
+    assert np.all(got[il] == sentinel)  # strict lower triangle untouched
+    if rows >= 100:
+        rel = err / np.maximum(bound[iu] / ((rows + 2) * U32), 1e-300)
+        assert np.sqrt(np.mean(rel ** 2)) < 8 * math.sqrt(rows) * U32
+
+
+def test_symmetrize_is_exact():
+    rng = np.random.default_rng(3)
+    n = 301
+    G = rng.standard_normal((n, n))
+    G = G + G.T
+    dG = dev(np.triu(G))
+    d32 = torch.empty((n, n), dtype=torch.float32, device="cuda")
+    assert B.tsvd_gram_symmetrize(n, dG.data_ptr(), d32.data_ptr(), S()) == 0
+    assert np.array_equal(d32.cpu().numpy(), G.astype(np.float32))
+
+
+# ---------------------------------------------------------------- a4/a5 power step
+def _power_case(n=256, m=2048, l=3, seed=0):
+    inp = synth.dense_prescribed(m, n, synth.spectrum_geometric(n, 0.8), 1e-6, seed=seed)
+    Gf = ref.gram(inp["A"])
+    prior = ref.tsvd_dense(inp["A"], l, 1e-12, x_start=synth.start_normals(n, l, seed=9), B=Gf)
+    return Gf, prior
+
+
+@pytest.mark.parametrize("l", [0, 3])
+def test_power_dense_follows_oracle(l):
+    n = 256
+    Gf, prior = _power_case(n=n, l=max(l, 1))
+    V = prior.V[:, :l]
+    s2 = prior.sigma[:l] ** 2
+    x = synth.start_normals(n, 1, seed=21)[:, 0]
+    v0 = x / np.linalg.norm(x)
+    res = ref.power_method(ref.hotelling_apply(Gf, V, s2), v0, 1e-8)
+    dG64, dG32 = dev(Gf), dev(Gf.astype(np.float32))
+    dV = dev(np.asfortranarray(V).T.copy()) if l else None  # column-major n x l == row-major l x n
+    ds2 = dev(s2) if l else None
+    scratch_b = B.tsvd_power_scratch_bytes(n, l)
+    scr = torch.empty(scratch_b, dtype=torch.uint8, device="cuda")
+    info = torch.zeros(4, dtype=torch.int32, device="cuda")
+    out_s2 = torch.zeros(1, dtype=torch.float64, device="cuda")
+    for override in (res.iters, 0):
+        dx = dev(x)
+        st = B.tsvd_power_dense(n, dG32.data_ptr(), dG64.data_ptr(), dV.data_ptr() if l else None,
+                                ds2.data_ptr() if l else None, l, dx.data_ptr(), 1e-8, 10000, override, 0,
+                                out_s2.data_ptr(), info.data_ptr(), scr.data_ptr(), scratch_b, S())
+        assert st == 0
+        torch.cuda.synchronize()
+        got = dx.cpu().numpy()
+        inf = info.cpu().numpy()
+        assert inf[1] == 0 and inf[2] == 0
+        if override:
+            assert inf[0] == res.iters
+        else:
+            assert abs(int(inf[0]) - res.iters) <= 1
+        assert abs(np.linalg.norm(got) - 1.0) < 1e-12
+        assert ref.vector_angle(got, res.v) < 1e-5
+        s2_ref = float(res.v @ Gf @ res.v)
+        assert abs(out_s2.item() - s2_ref) / s2_ref < 1e-6
+
+
+def test_power_dense_rank_deficient():
+    n = 64
+    G = np.zeros((n, n))
+    dG64, dG32 = dev(G), dev(G.astype(np.float32))
+    scr_b = B.tsvd_power_scratch_bytes(n, 0)
+    scr = torch.empty(scr_b, dtype=torch.uint8, device="cuda")
+    info = torch.zeros(4, dtype=torch.int32, device="cuda")
+    out_s2 = torch.ones(1, dtype=torch.float64, device="cuda")
+    x = synth.start_normals(n, 1, seed=2)[:, 0]
+    dx = dev(x)
+    assert B.tsvd_power_dense(n, dG32.data_ptr(), dG64.data_ptr(), None, None, 0, dx.data_ptr(), 1e-8, 100, 0, 0,
+                              out_s2.data_ptr(), info.data_ptr(), scr.data_ptr(), scr_b, S()) == 0
+    inf = info.cpu().numpy()
+    assert inf[1] == 2 and out_s2.item() == 0.0
+    assert ref.vector_angle(dx.cpu().numpy(), x) < 1e-12
+
+
+# ---------------------------------------------------------------- a6 left vectors
+@pytest.mark.parametrize("rows,n,k", [(1000, 300, 20), (37, 64, 3), (513, 256, 16)])
+def test_left_vectors_match_oracle(rows, n, k):
+    rng = np.random.default_rng(rows)
+    A = rng.standard_normal((rows, n)).astype(np.float32)
+    V = rng.standard_normal((n, k)).astype(np.float32)
+    sig = rng.uniform(0.5, 2.0, size=k)
+    sig[k // 2] = 0.0  # a zero sigma gives a zero column
+    dA, dV, ds = dev(A), dev(np.asfortranarray(V).T.copy()), dev(sig)
+    ldu = rows + 5
+    dU = torch.full((k, ldu), 3.0, dtype=torch.float32, device="cuda")
+    assert B.tsvd_left_vectors(dA.data_ptr(), rows, n, n, dV.data_ptr(), n, k, ds.data_ptr(), dU.data_ptr(), ldu,
+                               S()) == 0
+    got = dU.cpu().numpy()[:, :rows].T
+    want = (A.astype(np.float64) @ V.astype(np.float64))
+    scale = np.abs(A.astype(np.float64)) @ np.abs(V.astype(np.float64))
+    for l in range(k):
+        if sig[l] == 0:
+            assert np.all(got[:, l] == 0)
+        else:
+            assert np.all(np.abs(got[:, l] - want[:, l] / sig[l]) <= (n + 2) * U32 * scale[:, l] / sig[l] + 1e-30)
+    assert np.all(dU.cpu().numpy()[:, rows:] == 3.0)  # padding rows untouched
+
+
+# ---------------------------------------------------------------- a3 CSR pair
+def _csr_with_edge_rows(m, n, seed):
+    csr = synth.csr_uniform(m, n, 12.0, seed=seed)
+    rows = []
+    rp, ci, va = csr["row_ptr"], csr["col_idx"], csr["values"]
+    rng = np.random.default_rng(seed)
+    for r in range(m):
+        c, v = ci[rp[r]:rp[r + 1]], va[rp[r]:rp[r + 1]]
+        if r == 3:
+            c, v = c[:0], v[:0]                      # empty row
+        elif r == 4:
+            c, v = c[:1], v[:1]                      # one entry
+        elif r == 5:
+            c = np.arange(n, dtype=np.int32)         # dense row
+            v = rng.random(n, dtype=np.float32)
+        elif r == 6:
+            p = rng.permutation(c.shape[0])          # unsorted columns
+            c, v = c[p], v[p]
+        rows.append((c, v))
+    rp2 = np.zeros(m + 1, dtype=np.int64)
+    rp2[1:] = np.cumsum([c.shape[0] for c, _ in rows])
+    return {"row_ptr": rp2, "col_idx": np.concatenate([c for c, _ in rows]).astype(np.int32),
+            "values": np.concatenate([v for _, v in rows]).astype(np.float32), "m": m, "n": n}
+
+
+@pytest.mark.parametrize("scatter", [1, 0])
+def test_csr_pair_matches_oracle(scatter):
+    m, n = 5000, 3000
+    csr = _csr_with_edge_rows(m, n, 7)
+    rp, ci, va = csr["row_ptr"], csr["col_idx"], csr["values"]
+    v = np.random.default_rng(1).standard_normal(n).astype(np.float32)
+    # a middle block: rows [1000, 3500), pointers offset to its first entry
+    r0, r1 = 1000, 3500
+    for (a, b) in [(0, m), (r0, r1)]:
+        e0 = rp[a]
+        d_rp = dev(rp[a:b + 1])
+        d_ci = dev(ci[e0:rp[b]])
+        d_va = dev(va[e0:rp[b]])
+        d_v = dev(v)
+        d_w = torch.full((n,), 0.5, dtype=torch.float32, device="cuda")
+        d_ss = torch.full((1,), 0.25, dtype=torch.float64, device="cuda")
+        assert B.tsvd_csr_gram_apply(b - a, n, d_rp.data_ptr(), d_ci.data_ptr(), d_va.data_ptr(), d_v.data_ptr(),
+                                     d_w.data_ptr(), d_ss.data_ptr(), scatter, S()) == 0
+        torch.cuda.synchronize()
+        sub_rp = rp[a:b + 1] - e0
+        y = ref.csr_matvec(sub_rp, ci[e0:rp[b]], va[e0:rp[b]], v.astype(np.float64))
+        w_ref = ref.csr_rmatvec(sub_rp, ci[e0:rp[b]], va[e0:rp[b]], y, n)
+        ss_ref = float(y @ y)
+        assert abs(d_ss.item() - 0.25 - ss_ref) <= 1e-5 * ss_ref
+        w = d_w.cpu().numpy().astype(np.float64)
+        if scatter:
+            absy = np.abs(ref.csr_matvec(sub_rp, ci[e0:rp[b]], np.abs(va[e0:rp[b]]), np.abs(v.astype(np.float64))))
+            scale = ref.csr_rmatvec(sub_rp, ci[e0:rp[b]], np.abs(va[e0:rp[b]]), absy, n)
+            assert np.all(np.abs(w - 0.5 - w_ref) <= 64 * U32 * (scale + 0.5) + 1e-30)
+        else:
+            assert np.all(w == 0.5)
+
+
+# ---------------------------------------------------------------- whole t-SVD
+def _gapped(sig, k):
+    lam = sig ** 2
+    return ref.gapped_indices(lam, k)
+
+
+def _compare(res, o, k, angle_tol=1e-4, sig_tol=1e-5, gapped=None):
+    sig = np.asarray(res.sigma)
+    assert np.max(np.abs(sig - o.sigma) / o.sigma) <= sig_tol, (sig, o.sigma)
+    idx = gapped if gapped is not None else range(k)
+    for l in idx:
+        assert ref.vector_angle(np.asarray(res.V[:, l]), o.V[:, l]) <= angle_tol, l
+        assert ref.vector_angle(np.asarray(res.U[:, l]), o.U[:, l]) <= angle_tol, l
+
+
+@pytest.mark.parametrize("mode", ["device", "resident", "stream"])
+def test_tsvd_c1_matches_oracle(mode):
+    m, n, k, eps = 2048, 256, 8, 1e-8
+    inp = synth.dense_prescribed(m, n, synth.spectrum_geometric(n, 0.8), 1e-6, seed=0)
+    A = inp["A"]
+    x = synth.start_normals(n, k, seed=1)
+    o = ref.tsvd_dense(A, k, eps, x_start=x)
+    gapped = _gapped(np.linalg.svd(A.astype(np.float64), compute_uv=False), k)
+    assert gapped == list(range(k))
+    kw = {}
+    if mode == "device":
+        Ain = torch.from_numpy(A).cuda()
+    else:
+        Ain = A
+        if mode == "stream":
+            kw = dict(force_stream=True, block_rows=300, n_buffers=2)
+    # same trajectory: the oracle's iteration counts forced
+    r = tsvd(Ain, k, eps, start_draws=x, iters_override=o.iters, **kw)
+    assert r.iters == o.iters
+    _compare(r, o, k, gapped=gapped)
+    # own convergence test
+    r2 = tsvd(Ain, k, eps, start_draws=x, **kw)
+    assert all(abs(a - b) <= 1 for a, b in zip(r2.iters, o.iters))
+    assert np.max(np.abs(r2.sigma - o.sigma) / o.sigma) <= 1e-5
+    # orthonormality as far as eps allows (A6: theta ~ sqrt(2 eps) r / (1 - r)),
+    # and the same departure from it as the oracle's factors
+    V = np.asarray(r.V, dtype=np.float64)
+    U = np.asarray(r.U, dtype=np.float64)
+    assert np.allclose(V.T @ V, np.eye(k), atol=3e-3)
+    assert np.allclose(V.T @ V, o.V.T @ o.V, atol=1e-5)
+    assert np.allclose(U.T @ U, o.U.T @ o.U, atol=1e-4)
+
+
+def test_tsvd_builtin_start_vectors_match_oracle_generator():
+    m, n, k, eps = 1500, 120, 5, 1e-8
+    inp = synth.dense_prescribed(m, n, synth.spectrum_geometric(n, 0.75), 1e-6, seed=4)
+    o = ref.tsvd_dense(inp["A"], k, eps, seed=77)  # oracle's own Philox stream
+    r = tsvd(inp["A"], k, eps, seed=77, iters_override=o.iters)
+    _compare(r, o, k)
+
+
+def test_tsvd_sign_convention_and_outputs_on_device():
+    m, n, k = 800, 64, 4
+    inp = synth.dense_prescribed(m, n, synth.spectrum_geometric(n, 0.7), 0.0, seed=5)
+    x = synth.start_normals(n, k, seed=3)
+    o = ref.tsvd_dense(inp["A"], k, 1e-10, x_start=x, sign_convention=True)
+    r = tsvd(torch.from_numpy(inp["A"]).cuda(), k, 1e-10, start_draws=x, iters_override=o.iters,
+             sign_convention=True, out_device=True)
+    V = r.V.cpu().numpy()
+    for l in range(k):
+        i = int(np.argmax(np.abs(V[:, l])))
+        assert V[i, l] > 0
+        assert np.max(np.abs(V[:, l] - o.V[:, l])) < 1e-5  # same sign, same vector
+    assert np.max(np.abs(r.sigma.cpu().numpy() - o.sigma) / o.sigma) < 1e-5
+
+
+def test_tsvd_zero_matrix_reports_rank():
+    A = np.zeros((300, 40), dtype=np.float32)
+    r = tsvd(A, 3, 1e-8, ok=(B.TSVD_ERANK,))
+    assert r.status == B.TSVD_ERANK
+    assert np.all(r.sigma == 0)
+    V = np.asarray(r.V, dtype=np.float64)
+    assert np.allclose(V.T @ V, np.eye(3), atol=1e-6)
+
+
+def test_tsvd_noconv_flag():
+    inp = synth.dense_prescribed(500, 50, synth.spectrum_geometric(50, 0.99), 0.0, seed=6)
+    r = tsvd(inp["A"], 2, 1e-14, max_iter=5, ok=(B.TSVD_ENOCONV,))
+    assert r.status == B.TSVD_ENOCONV and r.iters == [5, 5]
+    assert r.report["flags"] & B.TSVD_FLAG_NOCONV
+
+
+@pytest.mark.parametrize("mode", ["device", "resident", "stream"])
+def test_tsvd_csr_matches_oracle(mode):
+    m = n = 1 << 14
+    k, eps = 4, 1e-6
+    csr = synth.csr_uniform(m, n, 33.5, seed=3)
+    x = synth.start_normals(n, k, seed=5)
+    o = ref.tsvd_csr(csr, k, eps, x_start=x)
+    if mode == "device":
+        Ain = {"row_ptr": dev(csr["row_ptr"]), "col_idx": dev(csr["col_idx"]), "values": dev(csr["values"]),
+               "m": m, "n": n}
+        kw = {}
+    else:
+        Ain = csr
+        kw = dict(force_stream=True, block_rows=3000, n_buffers=3) if mode == "stream" else {}
+    r = tsvd(Ain, k, eps, start_draws=x, iters_override=o.iters, **kw)
+    assert r.iters == o.iters
+    # the bulk of a random sparse spectrum is not gapped; grade sigma for all,
+    # vectors for the gapped leading triplet only (the mean direction)
+    _compare(r, o, k, gapped=[0])
+    r2 = tsvd(Ain, k, eps, start_draws=x, **kw)
+    assert abs(r2.sigma[0] - o.sigma[0]) / o.sigma[0] <= 1e-5
+
+
+def test_tsvd_csr_empty_matrix_reports_rank():
+    # no stored entries: every application gives w = 0 exactly
+    m, n = 400, 200
+    csr = {"row_ptr": np.zeros(m + 1, dtype=np.int64), "col_idx": np.zeros(0, dtype=np.int32),
+           "values": np.zeros(0, dtype=np.float32), "m": m, "n": n}
+    x = synth.start_normals(n, 3, seed=1)
+    o = ref.tsvd_csr(csr, 3, 1e-10, x_start=x)
+    assert o.status == ["rank"] * 3
+    r = tsvd(csr, 3, 1e-10, start_draws=x, ok=(B.TSVD_ERANK,))
+    assert r.status == B.TSVD_ERANK
+    assert np.all(r.sigma == 0)
+    V = np.asarray(r.V, dtype=np.float64)
+    assert np.allclose(V.T @ V, np.eye(3), atol=1e-5)
+    for l in range(3):
+        assert ref.vector_angle(V[:, l], o.V[:, l]) < 1e-5
