@@ -269,14 +269,112 @@ def parity_full_size(A: np.ndarray, dA, res, prec: int):
     relerr = np.abs(Gs[iu] - Gref[iu]) / absref[iu]
     out["gram_sampled_max_err_over_absgram"] = float(relerr.max())
     # sigma_l = ||A v_l|| (Alg. 1 l.11-13) from the GPU's v_l, FP64 over all rows
-    V = np.asarray(res.V, dtype=np.float64)
+    V = res.V.cpu().numpy().astype(np.float64) if hasattr(res.V, "cpu") else np.asarray(res.V, dtype=np.float64)
+    sig_g = res.sigma.cpu().numpy() if hasattr(res.sigma, "cpu") else np.asarray(res.sigma)
     AV2 = np.zeros(V.shape[1])
     for r0 in range(0, m, 1 << 20):
         AV2 += np.sum((A[r0:r0 + (1 << 20)].astype(np.float64) @ V) ** 2, axis=0)
     sig_o = np.sqrt(AV2)
-    out["sigma_rel_err_vs_oracle_norm"] = float(np.max(np.abs(np.asarray(res.sigma) - sig_o) / sig_o))
+    out["sigma_rel_err_vs_oracle_norm"] = float(np.max(np.abs(sig_g - sig_o) / sig_o))
     out["VtV_offdiag_max"] = float(np.max(np.abs(V.T @ V - np.eye(V.shape[1]))))
     return out
+
+
+def kernel_case(args):
+    """Single-kernel microbenchmarks on device-resident inputs larger than L2
+    (used for the per-kernel roofline table and as the small ncu case)."""
+    import torch
+    from paper_2208_08410_gb300 import _binding as B
+    B.load(build_if_missing=True)
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream().cuda_stream
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(1)
+    out = {"case": args.case}
+    reps = args.steps
+
+    def timed(fn):
+        for _ in range(args.warmup):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / 1e3 / reps
+
+    peaks, src = load_peaks()
+    if args.case == "gram":
+        m = args.m or BLOCK_ROWS
+        n = args.n
+        A = torch.randn((m, n), generator=gen, device="cuda", dtype=torch.float32)
+        G = torch.zeros((n, n), dtype=torch.float64, device="cuda")
+        sb = B.tsvd_gram_scratch_bytes(m, n, args.precision)
+        scr = torch.empty(max(sb, 256), dtype=torch.uint8, device="cuda")
+
+        def fn():
+            B.check(B.tsvd_gram_accumulate(A.data_ptr(), m, n, n, G.data_ptr(), args.precision, scr.data_ptr(), sb,
+                                           stream), "gram")
+        t = timed(fn)
+        fl = m * n * (n + 1)
+        out.update({"m": m, "n": n, "precision": PREC_NAMES[args.precision], "ms": round(t * 1e3, 3),
+                    "tflops_algorithmic": round(fl / t / 1e12, 2),
+                    "note": "time covers prep (transpose/round) + SYRK for tensor precisions"})
+    elif args.case == "power":
+        n = args.n
+        X = torch.randn((n, n), generator=gen, device="cuda", dtype=torch.float64)
+        G64 = (X @ X.T).contiguous()
+        G32 = G64.float()
+        x = torch.randn(n, generator=gen, device="cuda", dtype=torch.float64)
+        sb = B.tsvd_power_scratch_bytes(n, 0)
+        scr = torch.empty(sb, dtype=torch.uint8, device="cuda")
+        info = torch.zeros(4, dtype=torch.int32, device="cuda")
+        s2 = torch.zeros(1, dtype=torch.float64, device="cuda")
+        iters = 200
+
+        def fn():
+            B.check(B.tsvd_power_dense(n, G32.data_ptr(), G64.data_ptr(), None, None, 0, x.data_ptr(), 1e-8, 10000,
+                                       iters, 0, s2.data_ptr(), info.data_ptr(), scr.data_ptr(), sb, stream), "power")
+        t = timed(fn)
+        per_it = t / iters
+        out.update({"n": n, "iters_per_launch": iters, "us_per_iteration": round(per_it * 1e6, 2),
+                    "GBps_G32": round(4 * n * n / per_it / 1e9, 1)})
+    elif args.case == "csr":
+        import synth
+        m = args.m or (1 << 22)
+        csr = synth.csr_uniform(m, m, 33.5, seed=1)
+        rp = torch.from_numpy(csr["row_ptr"]).cuda()
+        ci = torch.from_numpy(csr["col_idx"]).cuda()
+        va = torch.from_numpy(csr["values"]).cuda()
+        v = torch.rand(m, generator=gen, device="cuda", dtype=torch.float32)
+        w = torch.zeros(m, dtype=torch.float32, device="cuda")
+        ss = torch.zeros(1, dtype=torch.float64, device="cuda")
+        nnz = int(va.shape[0])
+
+        def fn():
+            B.check(B.tsvd_csr_gram_apply(m, m, rp.data_ptr(), ci.data_ptr(), va.data_ptr(), v.data_ptr(),
+                                          w.data_ptr(), ss.data_ptr(), 1, stream), "csr")
+        t = timed(fn)
+        alg = 8 * nnz + 8 * (m + 1) + 4 * m + 8 * m
+        out.update({"m": m, "nnz": nnz, "ms": round(t * 1e3, 3), "GBps_algorithmic": round(alg / t / 1e9, 1),
+                    "frac_hbm": round(alg / t / 1e9 / peaks["hbm_gbs"], 3)})
+    elif args.case == "left":
+        m = args.m or BLOCK_ROWS
+        n, k = args.n, K
+        A = torch.randn((m, n), generator=gen, device="cuda", dtype=torch.float32)
+        V = torch.randn((k, n), generator=gen, device="cuda", dtype=torch.float32)
+        sig = torch.ones(k, dtype=torch.float64, device="cuda")
+        U = torch.empty((k, m), dtype=torch.float32, device="cuda")
+
+        def fn():
+            B.check(B.tsvd_left_vectors(A.data_ptr(), m, n, n, V.data_ptr(), n, k, sig.data_ptr(), U.data_ptr(), m,
+                                        stream), "left")
+        t = timed(fn)
+        out.update({"m": m, "n": n, "k": k, "ms": round(t * 1e3, 3), "GBps_A": round(m * n * 4 / t / 1e9, 1),
+                    "frac_hbm": round(m * n * 4 / t / 1e9 / peaks["hbm_gbs"], 3)})
+    print(json.dumps(out), flush=True)
 
 
 def main():
@@ -291,7 +389,13 @@ def main():
     ap.add_argument("--no-parity", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=0)
+    ap.add_argument("--case", default="", choices=["", "gram", "power", "csr", "left"],
+                    help="single-kernel microbenchmark instead of the t-SVD step")
+    ap.add_argument("--n", type=int, default=N_COLS)
     args = ap.parse_args()
+    if args.case:
+        kernel_case(args)
+        return
 
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))

@@ -15,10 +15,11 @@
 //     the K = row range.  Warp 0 streams 128-row (A operand) and 256-row
 //     (B operand) slabs of At into a 4-stage shared-memory ring with TMA
 //     (128-byte swizzle, no multicast); warp 1 issues tcgen05.mma kind::tf32
-//     (M=128, N=256, K=8) into one of two 256-column TMEM accumulators;
-//     warps 2-5 drain the other accumulator with tcgen05.ld and add the FP32
-//     partial sums into the FP64 G with coalesced atomics, so the epilogue of
-//     one unit overlaps the MMAs of the next.
+//     (M=128, N=256, K=8) into one of two 256-column TMEM accumulators, one
+//     short K segment at a time; warps 2-17 drain the other accumulator with
+//     tcgen05.ld into FP32 registers (round-to-nearest adds), so draining one
+//     segment overlaps the MMAs of the next, and add each unit's sum into the
+//     FP64 G with coalesced atomics.
 // Every wait is bounded (global timer); on timeout the kernel raises an error
 // flag, stops issuing, waits (bounded) for its own copies and MMAs, frees
 // TMEM and returns.
@@ -31,7 +32,9 @@
 namespace tsvd {
 namespace {
 
-constexpr int TC_THREADS = 192;
+constexpr int TC_EPI_WARPS = 16;  // 4 TMEM lane quarters x 4 column groups of 64
+constexpr int TC_EPI_COLS = 64;   // accumulator columns per epilogue thread
+constexpr int TC_THREADS = 64 + 32 * TC_EPI_WARPS;  // TMA warp, MMA warp, epilogue warps
 constexpr int TM = 128;          // MMA M (rows of At from block I)
 constexpr int TN = 256;          // MMA N (rows of At from block J)
 constexpr int TK = 32;           // K per stage (32 x 4 B = one 128-byte swizzle row)
@@ -129,16 +132,29 @@ __device__ __forceinline__ void umma_commit(uint32_t bar) {
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+// acc[0..15] += TMEM columns [taddr, taddr+16) of this thread's lane (one
+// statement so the load, its wait and the round-to-nearest adds stay together)
+__device__ __forceinline__ void tmem_add16(uint32_t taddr, float *acc) {
   asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,%19,"
-      "%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
-        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
-        "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
-        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-      : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      "{\n .reg .f32 t<16>;\n"
+      " tcgen05.ld.sync.aligned.32x32b.x16.b32 {t0,t1,t2,t3,t4,t5,t6,t7,t8,t9,t10,t11,t12,t13,t14,t15}, [%16];\n"
+      " tcgen05.wait::ld.sync.aligned;\n"
+      " add.rn.f32 %0, %0, t0;\n add.rn.f32 %1, %1, t1;\n add.rn.f32 %2, %2, t2;\n add.rn.f32 %3, %3, t3;\n"
+      " add.rn.f32 %4, %4, t4;\n add.rn.f32 %5, %5, t5;\n add.rn.f32 %6, %6, t6;\n add.rn.f32 %7, %7, t7;\n"
+      " add.rn.f32 %8, %8, t8;\n add.rn.f32 %9, %9, t9;\n add.rn.f32 %10, %10, t10;\n add.rn.f32 %11, %11, t11;\n"
+      " add.rn.f32 %12, %12, t12;\n add.rn.f32 %13, %13, t13;\n add.rn.f32 %14, %14, t14;\n add.rn.f32 %15, %15, t15;\n"
+      "}\n"
+      : "+f"(acc[0]), "+f"(acc[1]), "+f"(acc[2]), "+f"(acc[3]), "+f"(acc[4]), "+f"(acc[5]), "+f"(acc[6]),
+        "+f"(acc[7]), "+f"(acc[8]), "+f"(acc[9]), "+f"(acc[10]), "+f"(acc[11]), "+f"(acc[12]), "+f"(acc[13]),
+        "+f"(acc[14]), "+f"(acc[15])
+      : "r"(taddr)
+      : "memory");
+}
+
+// *p += (double)x with a fire-and-forget global reduction
+__device__ __forceinline__ void red_add_f64_from_f32(double *p, float x) {
+  asm volatile("{\n .reg .f64 d;\n cvt.f64.f32 d, %1;\n red.global.add.f64 [%0], d;\n}\n" ::"l"(p), "f"(x)
+               : "memory");
 }
 
 // ---------------------------------------------------------------- TF32 rounding
@@ -208,7 +224,8 @@ struct TcArgs {
   double *G;
   int64_t n;
   int64_t Kp;         // padded K (rows) of At
-  int64_t ksplit;     // rows per work unit (multiple of TK)
+  int64_t ksplit;     // rows per work unit (multiple of TK * seg_stages)
+  int seg_stages;     // stages per TMEM accumulation segment
   int n_splits;
   int n_tiles;
   int n_iblk;         // ceil(n / 128)
@@ -217,7 +234,6 @@ struct TcArgs {
 
 // tile t -> (bi, bj): tiles are listed by I block; block bi has bi/2 + 1 tiles
 __device__ __forceinline__ void tc_tile(int t, int &bi, int &bj) {
-  int b = 0;
   // C(b) = number of tiles before block b: q(q+1) for b = 2q, (q+1)^2 for b = 2q+1
   int lo = 0, hi = 1 << 16;
   while (lo < hi) {  // largest b with C(b) <= t
@@ -226,13 +242,18 @@ __device__ __forceinline__ void tc_tile(int t, int &bi, int &bj) {
     const long long c = (mid & 1) ? (q + 1) * (q + 1) : q * (q + 1);
     if (c <= t) lo = mid; else hi = mid - 1;
   }
-  b = lo;
-  const long long q = b >> 1;
-  const long long cb = (b & 1) ? (q + 1) * (q + 1) : q * (q + 1);
-  bi = b;
+  const long long q = lo >> 1;
+  const long long cb = (lo & 1) ? (q + 1) * (q + 1) : q * (q + 1);
+  bi = lo;
   bj = (int)(t - cb);
 }
 
+// The tensor core adds each MMA into the FP32 TMEM accumulator with a
+// directed (toward-zero) rounding, so a long accumulation chain drifts low by
+// about 0.4 ulp per MMA.  The accumulator is therefore restarted every
+// `seg_stages` stages (a segment of 16-48 MMAs) and the segment sums are
+// added into FP32 registers of the epilogue warps with round-to-nearest;
+// only the sum over a whole work unit goes to the FP64 G.
 template <int PREC>
 __global__ void __launch_bounds__(TC_THREADS, 1)
 syrk_tc_kernel(const __grid_constant__ CUtensorMap map_hi, const __grid_constant__ CUtensorMap map_lo, TcArgs a) {
@@ -247,6 +268,7 @@ syrk_tc_kernel(const __grid_constant__ CUtensorMap map_hi, const __grid_constant
   const uint32_t final_bar = smem_u32(bars + 2 * C::kStages + 4);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int units = a.n_tiles * a.n_splits;
+  const int64_t seg_rows = (int64_t)a.seg_stages * TK;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < C::kStages; ++s) {
@@ -255,7 +277,7 @@ syrk_tc_kernel(const __grid_constant__ CUtensorMap map_hi, const __grid_constant
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(tfull0 + 8 * b, 1);
-      mbar_init(tempty0 + 8 * b, 4);
+      mbar_init(tempty0 + 8 * b, TC_EPI_WARPS);
     }
     mbar_init(final_bar, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -273,7 +295,6 @@ syrk_tc_kernel(const __grid_constant__ CUtensorMap map_hi, const __grid_constant
     // ------------------------------------------------ TMA producer
     if (lane == 0) {
       uint32_t it = 0;
-      uint32_t issued_unconsumed = 0;
       bool ok = true;
       for (int u = blockIdx.x; u < units && ok; u += gridDim.x) {
         const int t = u % a.n_tiles, sp = u / a.n_tiles;
@@ -296,87 +317,100 @@ syrk_tc_kernel(const __grid_constant__ CUtensorMap map_hi, const __grid_constant
             tma_load_2d(smem_u32(sl + A_SLAB), &map_lo, x, bj * TN, full0 + 8 * s);
             tma_load_2d(smem_u32(sl + A_SLAB + B_SLAB / 2), &map_lo, x, bj * TN + TN / 2, full0 + 8 * s);
           }
-          issued_unconsumed = it + 1;
         }
       }
       if (!ok) {
-        // drain: wait (bounded) for every stage we filled to land
-        for (uint32_t j = (issued_unconsumed > C::kStages ? issued_unconsumed - C::kStages : 0);
-             j < issued_unconsumed; ++j)
-          mbar_wait(full0 + 8 * (j % C::kStages), (j / C::kStages) & 1u, a.err);
+        // drain: wait (bounded) for the stages still in flight to land
+        const uint32_t from = it > (uint32_t)C::kStages ? it - C::kStages : 0;
+        for (uint32_t j = from; j < it; ++j) mbar_wait(full0 + 8 * (j % C::kStages), (j / C::kStages) & 1u, a.err);
       }
     }
   } else if (warp == 1) {
     // ------------------------------------------------ MMA issuer
     if (lane == 0) {
       constexpr uint32_t idesc = idesc_tf32(TM, TN);
-      uint32_t it = 0, uc = 0;
+      uint32_t it = 0, sc = 0;  // stage counter, segment counter
       bool ok = true;
-      for (int u = blockIdx.x; u < units && ok; u += gridDim.x, ++uc) {
+      for (int u = blockIdx.x; u < units && ok; u += gridDim.x) {
         const int sp = u / a.n_tiles;
         const int64_t k0 = (int64_t)sp * a.ksplit;
         const int64_t k1 = min(a.Kp, k0 + a.ksplit);
-        const uint32_t acc = uc & 1u, aph = (uc >> 1) & 1u;
-        if (!mbar_wait(tempty0 + 8 * acc, aph ^ 1u, a.err)) { ok = false; break; }
-        tc_fence_after();
-        const uint32_t dtm = tmem + acc * TN;
-        uint32_t first = 1;
-        for (int64_t kk = k0; kk < k1; kk += TK, ++it) {
-          const uint32_t s = it % C::kStages, ph = (it / C::kStages) & 1u;
-          if (!mbar_wait(full0 + 8 * s, ph, a.err)) { ok = false; break; }
+        for (int64_t g0 = k0; g0 < k1 && ok; g0 += seg_rows, ++sc) {
+          const int64_t g1 = min(k1, g0 + seg_rows);
+          const uint32_t acc = sc & 1u, aph = (sc >> 1) & 1u;
+          if (!mbar_wait(tempty0 + 8 * acc, aph ^ 1u, a.err)) { ok = false; break; }
           tc_fence_after();
-          const uint32_t st = smem_u32(smem + s * C::kStageBytes);
-          const uint64_t dah = umma_desc_sw128(st), dbh = umma_desc_sw128(st + A_SLAB);
+          const uint32_t dtm = tmem + acc * TN;
+          uint32_t first = 1;
+          for (int64_t kk = g0; kk < g1; kk += TK, ++it) {
+            const uint32_t s = it % C::kStages, ph = (it / C::kStages) & 1u;
+            if (!mbar_wait(full0 + 8 * s, ph, a.err)) { ok = false; break; }
+            tc_fence_after();
+            const uint32_t st = smem_u32(smem + s * C::kStageBytes);
+            const uint64_t dah = umma_desc_sw128(st), dbh = umma_desc_sw128(st + A_SLAB);
 #pragma unroll
-          for (int k8 = 0; k8 < TK / 8; ++k8) {
-            const uint64_t off = (uint64_t)(k8 * 32) >> 4;  // 32 bytes per K=8 step
-            umma_tf32(dtm, dah + off, dbh + off, idesc, first ? 0u : 1u);
-            first = 0;
-            if (C::kParts == 2) {
-              const uint32_t sl = st + A_SLAB + B_SLAB;
-              const uint64_t dal = umma_desc_sw128(sl), dbl = umma_desc_sw128(sl + A_SLAB);
-              umma_tf32(dtm, dah + off, dbl + off, idesc, 1u);
-              umma_tf32(dtm, dal + off, dbh + off, idesc, 1u);
+            for (int k8 = 0; k8 < TK / 8; ++k8) {
+              const uint64_t off = (uint64_t)(k8 * 32) >> 4;  // 32 bytes per K=8 step
+              if (C::kParts == 2) {
+                const uint32_t sl = st + A_SLAB + B_SLAB;
+                const uint64_t dal = umma_desc_sw128(sl), dbl = umma_desc_sw128(sl + A_SLAB);
+                umma_tf32(dtm, dal + off, dbh + off, idesc, first ? 0u : 1u);  // small terms first
+                first = 0;
+                umma_tf32(dtm, dah + off, dbl + off, idesc, 1u);
+              }
+              umma_tf32(dtm, dah + off, dbh + off, idesc, first ? 0u : 1u);
+              first = 0;
             }
+            umma_commit(empty0 + 8 * s);  // frees the stage when these MMAs finish
           }
-          umma_commit(empty0 + 8 * s);  // frees the stage when these MMAs finish
+          if (!ok) break;
+          umma_commit(tfull0 + 8 * acc);  // segment sum ready for the epilogue
         }
-        if (!ok) break;
-        umma_commit(tfull0 + 8 * acc);  // accumulator ready for the epilogue
       }
       // wait for every MMA this thread issued before TMEM is released
       umma_commit(final_bar);
       mbar_wait(final_bar, 0, a.err);
     }
   } else {
-    // ------------------------------------------------ epilogue: TMEM -> FP64 G
-    const int q = warp & 3;  // TMEM lane quarter this warp may access
+    // ------------------------------------------------ epilogue: TMEM -> registers -> FP64 G
+    const int q = warp & 3;                     // TMEM lane quarter this warp may access
+    const int h = (warp - 2) >> 2;              // which 64 of the 256 columns
     const int row = q * 32 + lane;
-    uint32_t uc = 0;
-    for (int u = blockIdx.x; u < units; u += gridDim.x, ++uc) {
-      const int t = u % a.n_tiles;
+    float accr[TC_EPI_COLS];
+#pragma unroll
+    for (int j = 0; j < TC_EPI_COLS; ++j) accr[j] = 0.f;
+    uint32_t sc = 0;
+    bool ok = true;
+    for (int u = blockIdx.x; u < units && ok; u += gridDim.x) {
+      const int t = u % a.n_tiles, sp = u / a.n_tiles;
       int bi, bj;
       tc_tile(t, bi, bj);
-      const uint32_t acc = uc & 1u, aph = (uc >> 1) & 1u;
-      if (!mbar_wait(tfull0 + 8 * acc, aph, a.err)) break;
-      tc_fence_after();
-      const int64_t gi = (int64_t)bi * TM + row;
-      const int64_t jbase = (int64_t)bj * TN;
-#pragma unroll 1
-      for (int c0 = 0; c0 < TN; c0 += 32) {
-        uint32_t r[32];
-        tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + acc * TN + c0, r);
-        if (gi < a.n) {
+      const int64_t k0 = (int64_t)sp * a.ksplit;
+      const int64_t k1 = min(a.Kp, k0 + a.ksplit);
+      for (int64_t g0 = k0; g0 < k1; g0 += seg_rows, ++sc) {
+        const uint32_t acc = sc & 1u, aph = (sc >> 1) & 1u;
+        if (!mbar_wait(tfull0 + 8 * acc, aph, a.err)) { ok = false; break; }
+        tc_fence_after();
+        const uint32_t tbase = tmem + ((uint32_t)(q * 32) << 16) + acc * TN + h * TC_EPI_COLS;
 #pragma unroll
-          for (int j = 0; j < 32; ++j) {
-            const int64_t gj = jbase + c0 + j;
-            if (gj <= gi && gj < a.n) atomicAdd(a.G + gj * a.n + gi, (double)__uint_as_float(r[j]));
-          }
-        }
+        for (int c = 0; c < TC_EPI_COLS / 16; ++c) tmem_add16(tbase + c * 16, accr + c * 16);
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(tempty0 + 8 * acc);
       }
-      tc_fence_before();
-      __syncwarp();
-      if (lane == 0) mbar_arrive(tempty0 + 8 * acc);
+      if (!ok) break;
+      const int64_t gi = (int64_t)bi * TM + row;
+      const int64_t jbase = (int64_t)bj * TN + h * TC_EPI_COLS;
+      // columns gj <= gi of this row (the lower triangle of G), stored at G[gj][gi]
+      const int jlim = gi < a.n ? (int)min((int64_t)TC_EPI_COLS, gi - jbase + 1) : 0;
+      double *gp = a.G + jbase * a.n + gi;
+      const int64_t stride = a.n;
+#pragma unroll
+      for (int j = 0; j < TC_EPI_COLS; ++j) {
+        if (j < jlim) red_add_f64_from_f32(gp, accr[j]);
+        gp += stride;
+        accr[j] = 0.f;
+      }
     }
   }
   tc_fence_before();
@@ -435,14 +469,12 @@ size_t gram_tc_scratch_bytes(int64_t rows, int64_t n, int precision) {
   return 2048 + (size_t)parts * (size_t)round_up(n * padded_k(rows) * 4, 1024);
 }
 
-// rows per work unit (K slice); tunable through TSVD_TC_KSPLIT for experiments
-static int64_t tc_ksplit_rows() {
-  static int64_t v = -1;
-  if (v < 0) {
-    const char *e = getenv("TSVD_TC_KSPLIT");
-    v = e ? std::max<int64_t>(TK, round_up(atoll(e), TK)) : 8192;
-  }
-  return v;
+// Stages per TMEM accumulation segment (bounds the truncation drift of one
+// FP32 accumulation chain to ~16-24 MMAs); TSVD_TC_SEG overrides it.
+static int tc_seg_stages(int precision) {
+  const char *e = getenv("TSVD_TC_SEG");
+  if (e) return std::max(1, atoi(e));
+  return precision == TSVD_GRAM_TF32X3 ? 2 : 4;
 }
 
 tsvd_status launch_gram_tc(const float *A, int64_t rows, int64_t n, int64_t ld, double *G, int precision,
@@ -485,12 +517,24 @@ tsvd_status launch_gram_tc(const float *A, int64_t rows, int64_t n, int64_t ld, 
   a.G = G;
   a.n = n;
   a.Kp = Kp;
-  a.ksplit = std::min<int64_t>(tc_ksplit_rows(), Kp);
-  a.n_splits = (int)ceil_div(Kp, a.ksplit);
+  a.seg_stages = tc_seg_stages(precision);
   a.n_iblk = (int)ceil_div(n, TM);
   {
     const int64_t q = (a.n_iblk) >> 1;  // tiles = C(n_iblk)
     a.n_tiles = (int)((a.n_iblk & 1) ? (q + 1) * (q + 1) : q * (q + 1));
+  }
+  {
+    // K slices: aim for >= 8 units per SM (load balance across the persistent
+    // grid) without slices shorter than 4096 rows (FP64 atomics per unit)
+    const int64_t quantum = (int64_t)TK * a.seg_stages;
+    const int64_t want_units = 8LL * di.sms;
+    int64_t splits = std::max<int64_t>(1, ceil_div(want_units, a.n_tiles));
+    int64_t ks = round_up(ceil_div(Kp, splits), quantum);
+    ks = std::max<int64_t>(ks, std::min<int64_t>(round_up(4096, quantum), round_up(Kp, quantum)));
+    const char *e = getenv("TSVD_TC_KSPLIT");
+    if (e) ks = std::max<int64_t>(quantum, round_up(atoll(e), quantum));
+    a.ksplit = ks;
+    a.n_splits = (int)ceil_div(Kp, ks);
   }
   a.err = err;
   TSVD_CUDA(cudaMemsetAsync(err, 0, 4, stream));

@@ -384,3 +384,78 @@ def test_tsvd_csr_empty_matrix_reports_rank():
     assert np.allclose(V.T @ V, np.eye(3), atol=1e-5)
     for l in range(3):
         assert ref.vector_angle(V[:, l], o.V[:, l]) < 1e-5
+
+
+# ---------------------------------------------------------------- a2 Gram on tcgen05
+def _tc_case(rows, n, ld, seed):
+    rng = np.random.default_rng(seed)
+    Afull = rng.standard_normal((max(rows, 1), ld)).astype(np.float32)[:rows]
+    return Afull
+
+
+@pytest.mark.parametrize("prec", [B.TSVD_GRAM_TF32, B.TSVD_GRAM_TF32X3])
+@pytest.mark.parametrize("rows,n,ld", [(1000, 256, 256), (777, 130, 130), (64, 5, 5), (5000, 300, 300),
+                                       (300, 129, 133), (20000, 512, 512), (1, 17, 17), (70, 640, 640)])
+def test_gram_tensor_cores_match_oracle(prec, rows, n, ld):
+    """TF32: operands rounded to nearest (|da| <= 2^-11 |a|), exact products,
+    FP32 accumulation over a K slice then FP64; TF32X3: a = hi + lo to
+    2^-22 |a|, three products.  Bound: (e_in + (K+2) 2^-23) (|A|^T |A|)."""
+    Afull = _tc_case(rows, n, ld, rows * 7 + n)
+    A = Afull[:, :n]
+    sentinel = -7.25
+    G = np.tril(np.full((n, n), sentinel), -1)
+    dG = dev(G)
+    dA = dev(Afull) if rows else torch.empty(1, dtype=torch.float32, device="cuda")
+    sb = B.tsvd_gram_scratch_bytes(rows, n, prec)
+    scr = torch.empty(max(sb, 256), dtype=torch.uint8, device="cuda")
+    assert B.tsvd_gram_accumulate(dA.data_ptr(), rows, n, ld, dG.data_ptr(), prec, scr.data_ptr(), sb, S()) == 0
+    torch.cuda.synchronize()
+    assert int(scr[:4].view(torch.int32).item()) == 0  # no bounded wait gave up
+    got = dG.cpu().numpy()
+    ref_G = ref.gram(A)
+    absA = np.abs(A.astype(np.float64))
+    absG = absA.T @ absA
+    e_in = 2.0 ** -10 + 2.0 ** -22 if prec == B.TSVD_GRAM_TF32 else 3 * 2.0 ** -22
+    K = min(rows, 8192)
+    bound = (e_in + (K + 2) * 2.0 ** -23) * absG + 1e-300
+    iu = np.triu_indices(n)
+    err = got[iu] - ref_G[iu]
+    assert np.all(np.abs(err) <= bound[iu]), float(np.max(np.abs(err) / bound[iu]))
+    il = np.tril_indices(n, -1)
+    assert np.all(got[il] == sentinel)
+    if rows >= 1000:
+        # no systematic bias on the diagonal (a biased Gram shifts every sigma)
+        d = np.arange(n)
+        bias = float(np.mean((got[d, d] - ref_G[d, d]) / ref_G[d, d]))
+        # short TMEM accumulation segments keep the toward-zero drift of the
+        # tensor-core accumulator to ~0.4 ulp x (16..24 MMAs) ~ 5e-7
+        assert abs(bias) < 2e-6, bias
+
+
+def test_tsvd_tf32x3_c1_matches_oracle():
+    m, n, k, eps = 2048, 256, 8, 1e-8
+    inp = synth.dense_prescribed(m, n, synth.spectrum_geometric(n, 0.8), 1e-6, seed=0)
+    x = synth.start_normals(n, k, seed=1)
+    o = ref.tsvd_dense(inp["A"], k, eps, x_start=x)
+    r = tsvd(torch.from_numpy(inp["A"]).cuda(), k, eps, start_draws=x, iters_override=o.iters,
+             precision=B.TSVD_GRAM_TF32X3)
+    _compare(r, o, k)
+
+
+@pytest.mark.parametrize("prec", [B.TSVD_GRAM_TF32, B.TSVD_GRAM_TF32X3])
+def test_tsvd_tensor_cores_c2_shape(prec):
+    # the out-of-core workload's structure at a size the oracle handles:
+    # rank-64, sigma_i = 1/(1+i), 1e-4 noise; streamed in row blocks
+    m, n, k, eps = 1 << 17, 512, 8, 1e-6
+    sig = 1.0 / (1.0 + np.arange(64))
+    V = synth.orthonormal_columns(n, 64, 3, 1)
+    A = synth.dense_lowrank_rows(0, m, V, sig, m, 1e-4, seed=3)
+    x = synth.start_normals(n, k, seed=2)
+    Gf = ref.gram(A)
+    o = ref.tsvd_dense(A, k, eps, x_start=x, B=Gf)
+    lam = np.linalg.eigvalsh(Gf)[::-1]
+    gapped = ref.gapped_indices(lam, k)
+    r = tsvd(A, k, eps, start_draws=x, iters_override=o.iters, precision=prec, force_stream=True,
+             block_rows=1 << 15)
+    assert r.report["n_blocks"] == 4
+    _compare(r, o, k, gapped=gapped)
