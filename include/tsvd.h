@@ -136,7 +136,8 @@ typedef struct tsvd_plan_s *tsvd_plan_t;
 
 /* Static description of a status code; never NULL. */
 TSVD_API const char *tsvd_status_string(tsvd_status s);
-/* Text of the last CUDA error seen by this thread's calls (or ""). */
+/* Text of the last CUDA error or argument error recorded by this thread's
+ * calls (or ""). */
 TSVD_API const char *tsvd_last_cuda_error(void);
 TSVD_API int32_t tsvd_abi_version(void);
 
@@ -252,6 +253,35 @@ TSVD_API tsvd_status tsvd_power_dense(int64_t n, const float *G32, const double 
                              int32_t max_iter, int32_t iters_override, int32_t sign_convention,
                              double *out_sigma2, int32_t *info, void *scratch,
                              size_t scratch_bytes, void *stream);
+
+/*
+ * tsvd_power_dense_noalloc - the deflated power iteration of tsvd_power_dense
+ * for callers that cannot allocate device memory.  The paper has no
+ * counterpart; it exists for integration.  Some callers cannot call
+ * cudaMalloc: their device memory belongs to another allocator (a
+ * framework's caching pool, a process whose device memory is capped or fully
+ * reserved up front), or they run where an allocation and the device
+ * synchronisation it may imply are not allowed.  This entry point allocates
+ * nothing: its scratch is one fixed-size array in the library's device
+ * memory, held by every GPU that loads the library until the process exits.
+ *
+ * Arguments and outputs are those of tsvd_power_dense minus the scratch
+ * pointer and size; the caller still passes all inputs and outputs.
+ * Limits: n <= TSVD_NOALLOC_MAX_N and l <= TSVD_NOALLOC_MAX_L, otherwise
+ * TSVD_EINVAL with a message in tsvd_last_cuda_error().
+ * The first call on a device looks up the array's device address for that
+ * device (cudaGetSymbolAddress, with that device current); make that first
+ * call before any stream capture.  All calls share the one array, which keeps
+ * the last call's contents (the call clears what must start at zero): calls
+ * that overlap on the GPU, on any streams, race and give wrong results.
+ */
+#define TSVD_NOALLOC_MAX_N 16384
+#define TSVD_NOALLOC_MAX_L 64
+TSVD_API tsvd_status tsvd_power_dense_noalloc(int64_t n, const float *G32, const double *G64,
+                                              const double *V64, const double *sigma2, int64_t l,
+                                              double *x, double eps, int32_t max_iter,
+                                              int32_t iters_override, int32_t sign_convention,
+                                              double *out_sigma2, int32_t *info, void *stream);
 
 /* Fill G32 (n x n FP32, full) from the upper triangle of G64 (symmetrise). */
 TSVD_API tsvd_status tsvd_gram_symmetrize(int64_t n, const double *G64, float *G32, void *stream);

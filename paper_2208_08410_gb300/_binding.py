@@ -15,6 +15,7 @@ TSVD_ETIMEDOUT, TSVD_ENOCONV, TSVD_ERANK, TSVD_EUNSUPPORTED = 5, 6, 7, 8
 TSVD_DENSE_F32_ROWMAJOR, TSVD_CSR_F32_I32_I64 = 0, 1
 TSVD_HOST, TSVD_DEVICE = 0, 1
 TSVD_GRAM_FP32, TSVD_GRAM_TF32, TSVD_GRAM_TF32X3 = 0, 1, 2
+TSVD_NOALLOC_MAX_N, TSVD_NOALLOC_MAX_L = 16384, 64
 TSVD_FLAG_NOCONV, TSVD_FLAG_RANK, TSVD_FLAG_NONMONOTONE, TSVD_FLAG_PAGEABLE, TSVD_FLAG_TIMEOUT = 1, 2, 4, 8, 16
 
 STATUS_NAMES = {0: "TSVD_OK", 1: "TSVD_EINVAL", 2: "TSVD_ENOMEM", 3: "TSVD_EBUDGET", 4: "TSVD_ECUDA",
@@ -64,6 +65,7 @@ SIGNATURES = {
     "tsvd_csr_gram_apply": (C.c_int, [_I64, _I64, _P, _P, _P, _P, _P, _P, _I32, _P]),
     "tsvd_power_scratch_bytes": (_SZ, [_I64, _I64]),
     "tsvd_power_dense": (C.c_int, [_I64, _P, _P, _P, _P, _I64, _P, _D, _I32, _I32, _I32, _P, _P, _P, _SZ, _P]),
+    "tsvd_power_dense_noalloc": (C.c_int, [_I64, _P, _P, _P, _P, _I64, _P, _D, _I32, _I32, _I32, _P, _P, _P]),
     "tsvd_gram_symmetrize": (C.c_int, [_I64, _P, _P, _P]),
     "tsvd_start_draws": (C.c_int, [C.c_uint64, _I64, _I64, _P, _P]),
     "tsvd_philox4x32_10": (C.c_int, [_P, _P, _P, _I64, _P]),

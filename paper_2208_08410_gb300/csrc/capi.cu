@@ -930,6 +930,15 @@ tsvd_status tsvd_power_dense(int64_t n, const float *G32, const double *G64, con
                             out_sigma2, info, scratch, scratch_bytes, static_cast<cudaStream_t>(stream));
 }
 
+tsvd_status tsvd_power_dense_noalloc(int64_t n, const float *G32, const double *G64, const double *V64,
+                                     const double *sigma2, int64_t l, double *x, double eps, int32_t max_iter,
+                                     int32_t iters_override, int32_t sign_convention, double *out_sigma2,
+                                     int32_t *info, void *stream) {
+  if (iters_override <= 0 && !(eps > 0.0 && eps < 1.0)) return TSVD_EINVAL;
+  return launch_power_dense_noalloc(n, G32, G64, V64, sigma2, l, x, eps, max_iter, iters_override,
+                                    sign_convention, out_sigma2, info, static_cast<cudaStream_t>(stream));
+}
+
 tsvd_status tsvd_gram_symmetrize(int64_t n, const double *G64, float *G32, void *stream) {
   if (n <= 0 || !G64 || !G32) return TSVD_EINVAL;
   return launch_symmetrize(n, G64, G32, static_cast<cudaStream_t>(stream));

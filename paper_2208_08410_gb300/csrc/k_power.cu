@@ -15,6 +15,7 @@
 // Also here: the symmetrising copy G64 -> G32, the Philox-4x32-10 start
 // draws, and small conversions.
 #include <algorithm>
+#include <mutex>
 
 #include "common.cuh"
 
@@ -466,6 +467,50 @@ tsvd_status launch_philox_raw(const uint32_t *ctr, const uint32_t *key, uint32_t
   philox_raw_kernel<<<(unsigned)blocks, 256, 0, stream>>>(ctr, key, out, count);
   TSVD_LAUNCHED();
   return TSVD_OK;
+}
+
+// ---------------------------------------------------------------- no-allocation variant
+// Scratch of tsvd_power_dense_noalloc: one file-scope device array sized for
+// the largest problem it accepts.  Every GPU that loads the library holds it
+// until the process exits.  Host code may not use the array's name as a
+// device address (on the host it is only a stand-in for the symbol), so its
+// device address is looked up once per device with cudaGetSymbolAddress.
+constexpr int64_t kNoallocScratchBytes =
+    256 + 2 * TSVD_NOALLOC_MAX_N * 8 + (int64_t)kMaxPowerBlocks * ((TSVD_NOALLOC_MAX_L + 8 + 3) / 4 * 4) * 8;
+static __device__ __align__(256) unsigned char g_power_noalloc_scratch[kNoallocScratchBytes];
+
+static tsvd_status noalloc_scratch(void **out) {
+  static std::mutex mu;
+  static void *addr[128] = {};
+  int dev = -1;
+  TSVD_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 128) return TSVD_EUNSUPPORTED;
+  std::lock_guard<std::mutex> lock(mu);
+  if (!addr[dev]) {
+    void *p = nullptr;
+    TSVD_CUDA(cudaGetSymbolAddress(&p, g_power_noalloc_scratch));
+    if (!p) return TSVD_ECUDA;
+    addr[dev] = p;
+  }
+  *out = addr[dev];
+  return TSVD_OK;
+}
+
+tsvd_status launch_power_dense_noalloc(int64_t n, const float *G32, const double *G64, const double *V64,
+                                       const double *sigma2, int64_t l, double *x, double eps, int max_iter,
+                                       int iters_override, int sign_convention, double *out_sigma2, int *info,
+                                       cudaStream_t stream) {
+  if (n > TSVD_NOALLOC_MAX_N || l > TSVD_NOALLOC_MAX_L) {
+    set_error_text("tsvd_power_dense_noalloc: n must be <= " + std::to_string(TSVD_NOALLOC_MAX_N) +
+                   " and l <= " + std::to_string(TSVD_NOALLOC_MAX_L) + " (fixed static scratch)");
+    return TSVD_EINVAL;
+  }
+  void *scratch = nullptr;
+  TSVD_TRY(noalloc_scratch(&scratch));
+  const size_t need = power_scratch_bytes(n, l);
+  if (need > (size_t)kNoallocScratchBytes) return TSVD_EINVAL;
+  return launch_power_dense(n, G32, G64, V64, sigma2, l, x, eps, max_iter, iters_override, sign_convention,
+                            out_sigma2, info, scratch, (size_t)kNoallocScratchBytes, stream);
 }
 
 tsvd_status launch_sigma_from_sigma2(const double *sig2, double *sigma, int64_t k, cudaStream_t stream) {
