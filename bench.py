@@ -60,6 +60,31 @@ def pick_m(requested: int | None) -> int:
     return int(blocks * BLOCK_ROWS)
 
 
+def source_digest(*paths) -> str:
+    """sha256 over source files (identifies the kernel a stored ncu capture measured)."""
+    import hashlib
+    h = hashlib.sha256()
+    for pth in paths:
+        with open(os.path.join(ROOT, pth), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
+
+
+def measured_traffic(kernel: str, rows: int, n: int):
+    """DRAM bytes (read + write) per launch from the committed ncu capture of
+    `kernel`, or None when no capture matches this launch configuration or the
+    kernel's source changed since the capture."""
+    pth = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    if not os.path.exists(pth):
+        return None
+    rec = json.load(open(pth)).get(kernel)
+    if not rec or rec.get("rows") != rows or rec.get("n") != n:
+        return None
+    if rec.get("source_sha256") != source_digest(*rec["sources"]):
+        return None
+    return int(rec["dram_bytes_read"]) + int(rec["dram_bytes_write"])
+
+
 def load_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -133,37 +158,77 @@ def make_host_A(m: int, seed: int):
 
 
 def measure_h2d_peak(A: np.ndarray):
-    """Pinned-copy peak: best of 3 copies of 4 GiB from A into HBM (cudaMemcpyAsync via torch)."""
+    """Pinned host -> HBM copy rates (cudaMemcpyAsync via torch, one copy stream):
+    burst = best of 3 copies of the first 4 GiB block; sustained = every row
+    block of A copied back to back into a 2-buffer ring (what a streamed pass
+    over the whole matrix can reach)."""
     import torch
     rows = min(A.shape[0], BLOCK_ROWS)
-    src = torch.from_numpy(A[:rows])
-    dst = torch.empty((rows, A.shape[1]), dtype=torch.float32, device="cuda")
+    dst = [torch.empty((rows, A.shape[1]), dtype=torch.float32, device="cuda") for _ in range(2)]
     best = 0.0
+    src = torch.from_numpy(A[:rows])
     for _ in range(3):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         torch.cuda.synchronize()
         e0.record()
-        dst.copy_(src, non_blocking=True)
+        dst[0].copy_(src, non_blocking=True)
         e1.record()
         torch.cuda.synchronize()
         best = max(best, rows * A.shape[1] * 4 / (e0.elapsed_time(e1) / 1e3) / 1e9)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    total = 0
+    for i, r0 in enumerate(range(0, A.shape[0], rows)):
+        blk = torch.from_numpy(A[r0:r0 + rows])
+        dst[i & 1][:blk.shape[0]].copy_(blk, non_blocking=True)
+        total += blk.numel() * 4
+    e1.record()
+    torch.cuda.synchronize()
+    sustained = total / (e0.elapsed_time(e1) / 1e3) / 1e9
     del dst
-    return best
+    return best, sustained
+
+
+# ----------------------------------------------------------------------------- multi-rank
+def whole_job_rate(sec_local: float, units_local: float, dist=None, device="cpu"):
+    """Whole-job throughput over ranks: (units summed over ranks) / (time of the
+    slowest rank).  Ranks run independent replicas of the workload, so no data
+    moves between them; only these two scalars are reduced."""
+    import torch
+    if dist is None or not dist.is_initialized() or dist.get_world_size() == 1:
+        return units_local / sec_local, sec_local
+    t = torch.tensor([sec_local], dtype=torch.float64, device=device)
+    u = torch.tensor([units_local], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(u.item()) / float(t.item()), float(t.item())
 
 
 # ----------------------------------------------------------------------------- runs
-def time_steps(plan, A_in, steps: int, warmup: int, want_u=True):
+def pinned_array(shape, dtype):
+    """Page-locked host array from the library's allocator (freed at exit)."""
+    from paper_2208_08410_gb300 import _binding as B
+    nbytes = int(np.prod(shape)) * np.dtype(dtype).itemsize
+    ptr = C.c_void_p()
+    B.check(B.tsvd_host_alloc(C.byref(ptr), max(nbytes, 16)), "tsvd_host_alloc")
+    ctype = {np.float32: C.c_float, np.float64: C.c_double}[dtype]
+    return np.ctypeslib.as_array(C.cast(ptr, C.POINTER(ctype)), shape=shape)
+
+
+def time_steps(plan, A_in, steps: int, warmup: int, want_u=True, outs=None):
     import torch
     reps = []
+    outs = outs or {}
     for _ in range(warmup):
-        plan.factor(A_in, want_u=want_u)
+        plan.factor(A_in, want_u=want_u, **outs)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     t_wall = time.perf_counter()
     e0.record()
     last = None
     for _ in range(steps):
-        last = plan.factor(A_in, want_u=want_u)
+        last = plan.factor(A_in, want_u=want_u, **outs)
         reps.append(last.report)
     e1.record()
     torch.cuda.synchronize()
@@ -244,36 +309,44 @@ def cpu_baseline(m: int, A: np.ndarray, V_gpu: np.ndarray, sig_gpu: np.ndarray, 
 def parity_full_size(A: np.ndarray, dA, res, prec: int):
     """Checks at full size on outputs the oracle computes one by one."""
     import torch
-    from oracle import tsvd_ref as ref
     from paper_2208_08410_gb300 import _binding as B
     m, n = A.shape
     out = {}
-    # sampled Gram entries: 48 random columns, all rows (FP64 oracle) vs the library's Gram
+    stream = torch.cuda.current_stream().cuda_stream
+    # sampled Gram entries: 48 random columns over all rows (FP64 oracle) vs the
+    # library's Gram accumulated block by block with the same entry point
     rng = np.random.default_rng(7)
     cols = np.sort(rng.choice(n, size=48, replace=False))
     G = torch.zeros((n, n), dtype=torch.float64, device="cuda")
-    scr_b = B.tsvd_gram_scratch_bytes(m, n, prec)
+    scr_b = B.tsvd_gram_scratch_bytes(BLOCK_ROWS, n, prec)
     scr = torch.empty(max(scr_b, 256), dtype=torch.uint8, device="cuda")
-    B.check(B.tsvd_gram_accumulate(dA.data_ptr(), m, n, n, G.data_ptr(), prec, scr.data_ptr(), scr_b,
-                                   torch.cuda.current_stream().cuda_stream), "gram")
+    for r0 in range(0, m, BLOCK_ROWS):
+        rows = min(BLOCK_ROWS, m - r0)
+        B.check(B.tsvd_gram_accumulate(dA[r0:].data_ptr(), rows, n, n, G.data_ptr(), prec, scr.data_ptr(), scr_b,
+                                       stream), "gram")
+    torch.cuda.synchronize()
     Gs = G[cols][:, cols].cpu().numpy()
     del G, scr
     Gref = np.zeros((48, 48))
     absref = np.zeros((48, 48))
-    for r0 in range(0, m, 1 << 20):
-        blk = A[r0:r0 + (1 << 20)][:, cols].astype(np.float64)
+    step = 1 << 18
+    for r0 in range(0, m, step):
+        blk = A[r0:r0 + step][:, cols].astype(np.float64)
         Gref += blk.T @ blk
         ab = np.abs(blk)
         absref += ab.T @ ab
     iu = np.triu_indices(48)
-    relerr = np.abs(Gs[iu] - Gref[iu]) / absref[iu]
+    # the library stores the upper triangle (row j <= column i) of G
+    Gsu = np.where(np.arange(48)[:, None] <= np.arange(48)[None, :], Gs, Gs.T)
+    relerr = np.abs(Gsu[iu] - Gref[iu]) / absref[iu]
     out["gram_sampled_max_err_over_absgram"] = float(relerr.max())
-    # sigma_l = ||A v_l|| (Alg. 1 l.11-13) from the GPU's v_l, FP64 over all rows
+    # sigma_l = ||A v_l|| (Alg. 1 l.11-13) for the GPU's v_l, FP64 over all rows
     V = res.V.cpu().numpy().astype(np.float64) if hasattr(res.V, "cpu") else np.asarray(res.V, dtype=np.float64)
     sig_g = res.sigma.cpu().numpy() if hasattr(res.sigma, "cpu") else np.asarray(res.sigma)
     AV2 = np.zeros(V.shape[1])
-    for r0 in range(0, m, 1 << 20):
-        AV2 += np.sum((A[r0:r0 + (1 << 20)].astype(np.float64) @ V) ** 2, axis=0)
+    step = 1 << 16
+    for r0 in range(0, m, step):
+        AV2 += np.sum((A[r0:r0 + step].astype(np.float64) @ V) ** 2, axis=0)
     sig_o = np.sqrt(AV2)
     out["sigma_rel_err_vs_oracle_norm"] = float(np.max(np.abs(sig_g - sig_o) / sig_o))
     out["VtV_offdiag_max"] = float(np.max(np.abs(V.T @ V - np.eye(V.shape[1]))))
@@ -420,7 +493,7 @@ def main():
     t0 = time.time()
     A, hptr, facts = make_host_A(m, seed=rank)
     gen_s = time.time() - t0
-    h2d_peak = measure_h2d_peak(A)
+    h2d_burst, h2d_peak = measure_h2d_peak(A)
     dA = torch.empty((m, N_COLS), dtype=torch.float32, device="cuda")
     for r0 in range(0, m, BLOCK_ROWS):
         dA[r0:r0 + BLOCK_ROWS].copy_(torch.from_numpy(A[r0:r0 + BLOCK_ROWS]), non_blocking=True)
@@ -437,13 +510,10 @@ def main():
     clocks.start()
     sec, wall, reps, res_dev = time_steps(plan_dev, dA, args.steps, args.warmup)
     clk = clocks.stop()
-    if dist:
-        t = torch.tensor([sec], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        sec = float(t.item())
-    step_s = sec / args.steps
     bytes_per_step = 2 * m * N_COLS * 4
-    value = world * bytes_per_step / step_s / 1e9
+    rate, sec = whole_job_rate(sec, bytes_per_step * args.steps, dist, "cuda")
+    step_s = sec / args.steps
+    value = rate / 1e9
     launches = int(sum(r["kernel_launches"] for r in reps))
     gk_ms = sum(r["gram_kernel_ms"] for r in reps)
     gk_n = sum(r["gram_kernel_launches"] for r in reps)
@@ -458,30 +528,38 @@ def main():
     else:
         peak = peaks["bf16_tflops"] * (1.1 / 2.25)
         roof = {"bound": "tensor", "peak_note": f"TF32 = bf16 {peak_src} burst x 1.1/2.25; 3 MMAs per product"}
+    chunk_rows = int(round(m / max(gk_n / max(args.steps, 1), 1)))
+    kname = {0: "syrk_simt_kernel", 1: "syrk_tc_kernel<TF32>", 2: "syrk_tc_kernel<TF32X3>"}[prec]
     roofline = {"bound": roof["bound"], "achieved": round(achieved_tf, 2) if achieved_tf else None,
                 "peak": round(peak, 1), "unit": "TFLOP/s",
-                "frac": round(achieved_tf / peak, 4) if achieved_tf else None, "traffic": None,
+                "frac": round(achieved_tf / peak, 4) if achieved_tf else None,
+                "traffic": measured_traffic(kname, chunk_rows, N_COLS),
                 "kernel": "Gram accumulation (SYRK)", "launches_per_step": gk_n / max(args.steps, 1),
                 "algorithmic_flops_per_step": flops_per_step, "peak_source": peak_src + "; " + roof["peak_note"]}
     plan_dev.close()
+    del plan_dev
+    torch.cuda.empty_cache()
 
     # ---------------- e2e: pinned host A, streamed, outputs to host
     e2e_steps = args.e2e_steps or args.steps
     plan_host = Plan(A, K, EPS, precision=prec, device_budget=BUDGET, block_rows=BLOCK_ROWS, force_stream=True)
-    sec_e, wall_e, reps_e, res_host = time_steps(plan_host, A, e2e_steps, max(1, min(args.warmup, 3)))
-    if dist:
-        t = torch.tensor([sec_e], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        sec_e = float(t.item())
+    outs = {"U": pinned_array((K, m), np.float32), "sigma": pinned_array((K,), np.float64),
+            "V": pinned_array((K, N_COLS), np.float32)}
+    sec_e, wall_e, reps_e, res_host = time_steps(plan_host, A, e2e_steps, args.warmup, outs=outs)
+    rate_e, sec_e = whole_job_rate(sec_e, bytes_per_step * e2e_steps, dist, "cuda")
     e2e_step = sec_e / e2e_steps
     h2d_b = reps_e[-1]["h2d_bytes"]
     d2h_b = reps_e[-1]["d2h_bytes"]
     gram_pass_s = reps_e[-1]["gram_ms"] / 1e3
-    e2e = {"value": round(world * bytes_per_step / e2e_step / 1e9, 3), "unit": "GB/s",
+    e2e = {"value": round(rate_e / 1e9, 3), "unit": "GB/s",
            "h2d_bytes_per_step": int(h2d_b), "d2h_bytes_per_step": int(d2h_b),
            "ms_per_step": round(e2e_step * 1e3, 2),
+           "phases_ms": {"gram": round(reps_e[-1]["gram_ms"], 2), "power": round(reps_e[-1]["power_ms"], 2),
+                         "left": round(reps_e[-1]["left_ms"], 2)},
            "h2d": {"gram_pass_GBps": round(m * N_COLS * 4 / gram_pass_s / 1e9, 2),
                    "pinned_copy_peak_GBps": round(h2d_peak, 2),
+                   "pinned_copy_burst_GBps": round(h2d_burst, 2),
+                   "peak_note": "peak = sustained pinned copy of every row block of A back to back",
                    "frac_gram_pass": round(m * N_COLS * 4 / gram_pass_s / 1e9 / h2d_peak, 4),
                    "blocks_per_pass": reps_e[-1]["n_blocks"]}}
     launches_e = int(sum(r["kernel_launches"] for r in reps_e))
@@ -509,6 +587,8 @@ def main():
                            "gram_precision": PREC_NAMES[prec], "parallelism": "replicas" if world > 1 else "1 GPU"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
                 "gpu_launches": launches, "gpu_launches_e2e": launches_e,
+                "phases_ms": {"gram": round(reps[-1]["gram_ms"], 2), "power": round(reps[-1]["power_ms"], 2),
+                              "left": round(reps[-1]["left_ms"], 2), "applications": reps[-1]["applications"]},
                 "iters": res_dev.iters, "sigma": [round(float(s), 8) for s in np.asarray(res_dev.sigma.cpu())],
                 "parity": parity, "gen_seconds": round(gen_s, 1)}
         print(json.dumps(line), flush=True)

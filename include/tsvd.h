@@ -123,7 +123,9 @@ typedef struct {
   double gram_kernel_ms;    /* summed device time of the Gram kernels (time_kernels) */
   int64_t kernel_launches;  /* kernels launched by this call */
   int64_t applications;     /* total operator applications (sum of iters) */
-  double reserved1[4];
+  int32_t ring_slots;       /* row blocks the streaming ring holds (mode 2) */
+  int32_t reserved2;
+  double reserved1[3];
 } tsvd_report;
 
 #define TSVD_FLAG_NOCONV 1        /* a triplet hit max_iter */
@@ -231,13 +233,17 @@ TSVD_API tsvd_status tsvd_csr_gram_apply(int64_t rows, int64_t n, const int64_t 
 
 /*
  * Deflated power iteration for one triplet on a dense Gram matrix (Alg. 2
- * l.10-15 with the Hotelling form of Eq. 2), one cooperative kernel that
- * keeps the convergence loop on the device.
+ * l.10-15 with the deflated operator of Eq. 2 in its Hotelling form), one
+ * cooperative kernel that keeps the convergence loop on the device.
  *   n        order of G
- *   G32      device, n x n FP32 symmetric (full square, row-major)
- *   G64      device, n x n FP64 with the upper triangle valid (for sigma^2)
- *   V64      device, n x l FP64 column-major earlier vectors (NULL if l == 0)
- *   sigma2   device, l FP64 earlier sigma^2
+ *   G32      device, n x n FP32 row-major: the Gram matrix already deflated
+ *            by the earlier triplets, G - sum_{j<l} sigma_j^2 v_j v_j^T
+ *            (tsvd_gram_symmetrize, then tsvd_gram_deflate once per triplet)
+ *   G64      device, n x n FP64 with the upper triangle of the undeflated G
+ *            (for sigma_l^2 = v_l^T G v_l)
+ *   V64      device, n x l FP64 column-major earlier vectors and
+ *   sigma2   device, l FP64 earlier sigma^2: used only when B v0 vanishes
+ *            (then v_l = v0 made orthogonal to V64, sigma_l = 0); NULL if l == 0
  *   x        device, n FP64: in = start draw (not necessarily normalised),
  *            out = v_l (unit norm)
  *   eps, max_iter, iters_override (<= 0: use the convergence test)
@@ -282,6 +288,11 @@ TSVD_API tsvd_status tsvd_power_dense_noalloc(int64_t n, const float *G32, const
                                               double *x, double eps, int32_t max_iter,
                                               int32_t iters_override, int32_t sign_convention,
                                               double *out_sigma2, int32_t *info, void *stream);
+
+/* Hotelling deflation of the FP32 Gram copy by one triplet:
+ * G32 -= sigma2[0] * v v^T (v device FP64 n, sigma2 device FP64 scalar). */
+TSVD_API tsvd_status tsvd_gram_deflate(int64_t n, float *G32, const double *v, const double *sigma2,
+                                       void *stream);
 
 /* Fill G32 (n x n FP32, full) from the upper triangle of G64 (symmetrise). */
 TSVD_API tsvd_status tsvd_gram_symmetrize(int64_t n, const double *G64, float *G32, void *stream);

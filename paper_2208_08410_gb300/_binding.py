@@ -41,7 +41,8 @@ class tsvd_report(C.Structure):
                 ("gram_kernel_launches", C.c_int32), ("gram_ms", C.c_double), ("power_ms", C.c_double),
                 ("left_ms", C.c_double), ("total_ms", C.c_double), ("h2d_bytes", C.c_double),
                 ("d2h_bytes", C.c_double), ("gram_kernel_ms", C.c_double), ("kernel_launches", C.c_int64),
-                ("applications", C.c_int64), ("reserved1", C.c_double * 4)]
+                ("applications", C.c_int64), ("ring_slots", C.c_int32), ("reserved2", C.c_int32),
+                ("reserved1", C.c_double * 3)]
 
 
 _P = C.c_void_p
@@ -67,6 +68,7 @@ SIGNATURES = {
     "tsvd_power_dense": (C.c_int, [_I64, _P, _P, _P, _P, _I64, _P, _D, _I32, _I32, _I32, _P, _P, _P, _SZ, _P]),
     "tsvd_power_dense_noalloc": (C.c_int, [_I64, _P, _P, _P, _P, _I64, _P, _D, _I32, _I32, _I32, _P, _P, _P]),
     "tsvd_gram_symmetrize": (C.c_int, [_I64, _P, _P, _P]),
+    "tsvd_gram_deflate": (C.c_int, [_I64, _P, _P, _P, _P]),
     "tsvd_start_draws": (C.c_int, [C.c_uint64, _I64, _I64, _P, _P]),
     "tsvd_philox4x32_10": (C.c_int, [_P, _P, _P, _I64, _P]),
     "tsvd_left_vectors": (C.c_int, [_P, _I64, _I64, _I64, _P, _I64, _I64, _P, _P, _I64, _P]),

@@ -167,14 +167,23 @@ tsvd_status plan_dense(tsvd_plan_s *p) {
   p->n_chunks = ceil_div(m, rows);
   p->b_gscr = gram_tc_scratch_bytes(rows, n, prec);
   p->o_gscr = c.take(p->b_gscr + 256);
-  if (mode == MODE_STREAM) {
-    p->b_slot = (size_t)round_up(rows * n * 4, 256);
-    p->o_ring = c.take(p->b_slot * R);
-  }
   if (mode == MODE_RESIDENT) p->o_res = c.take(resident_bytes);
   if (host_u) {
     p->b_ubuf = (size_t)round_up(rows * k * 4, 256);
     p->o_ubuf = c.take(2 * p->b_ubuf);
+  }
+  if (mode == MODE_STREAM) {
+    // ring of row blocks, carved last: under a budget it takes every slot that
+    // fits, so the blocks still resident after the Gram pass serve the U pass
+    p->b_slot = (size_t)round_up(rows * n * 4, 256);
+    int64_t slots = R;
+    if (budget && budget > c.off + (size_t)R * p->b_slot) {
+      const int64_t extra = (int64_t)((budget - c.off - (size_t)R * p->b_slot) / p->b_slot);
+      slots = std::min<int64_t>(std::max<int64_t>(R, p->n_chunks), R + extra);
+      slots = std::min<int64_t>(slots, 64);
+    }
+    p->n_buffers = (int)slots;
+    p->o_ring = c.take(p->b_slot * slots);
   }
   p->ws = c.off;
   if (budget && p->ws > budget) return TSVD_EBUDGET;
@@ -462,17 +471,29 @@ tsvd_status gram_dispatch(const float *A, int64_t rows, int64_t n, int64_t ld, d
 tsvd_status left_pass_dense(Run &r, const float *V32, const double *sigma, float *U) {
   tsvd_plan_s *p = r.p;
   const bool host_u = p->opt.out_location == TSVD_HOST;
-  for (int64_t c = 0; c < p->n_chunks; ++c) {
+  // In the streamed mode the last n_buffers row blocks of the Gram pass are
+  // still in the ring (block c in slot c % n_buffers): use them first, then
+  // stream the others through the slots they free.
+  const int64_t nc = p->n_chunks;
+  const int64_t first_res = p->mode == MODE_STREAM ? std::max<int64_t>(0, nc - p->n_buffers) : nc;
+  for (int64_t idx = 0; idx < nc; ++idx) {
+    const int64_t c = p->mode == MODE_STREAM ? (idx < nc - first_res ? first_res + idx : idx - (nc - first_res)) : idx;
     const int64_t r0 = c * p->chunk_rows, rows = std::min(p->chunk_rows, p->m - r0);
     const float *Ab;
     int64_t ldb;
     int slot;
-    TSVD_TRY(acquire_dense(r, r0, rows, &Ab, &ldb, &slot, false));
+    if (p->mode == MODE_STREAM && c >= first_res) {
+      slot = (int)(c % p->n_buffers);
+      Ab = reinterpret_cast<const float *>(r.ws + p->o_ring + p->b_slot * slot);
+      ldb = p->n;
+    } else {
+      TSVD_TRY(acquire_dense(r, r0, rows, &Ab, &ldb, &slot, false));
+    }
     if (!host_u) {
       TSVD_TRY(launch_left_dense(Ab, rows, p->n, ldb, V32, p->n, p->k, sigma, U + r0, p->m, r.cs));
       TSVD_TRY(release_slot(r, slot));
     } else {
-      const int b = (int)(c & 1);
+      const int b = (int)(idx & 1);
       float *ub = reinterpret_cast<float *>(r.ws + p->o_ubuf + p->b_ubuf * b);
       TSVD_CUDA(cudaStreamWaitEvent(r.cs, p->ev_u_free[b], 0));
       TSVD_TRY(launch_left_dense(Ab, rows, p->n, ldb, V32, p->n, p->k, sigma, ub, rows, r.cs));
@@ -541,6 +562,8 @@ tsvd_status factor_dense(Run &r, float *U, double *sigma_out, float *V_out, tsvd
     TSVD_TRY(launch_power_dense(n, G32, G64, l ? V64 : nullptr, l ? sig2 : nullptr, l, x, p->eps,
                                 p->opt.max_iter, ovr, p->opt.sign_convention, sig2 + l, info + 4 * l,
                                 pscr, p->b_pscr, r.cs));
+    // Hotelling deflation of the FP32 Gram copy for the next triplet
+    if (l + 1 < k) TSVD_TRY(launch_gram_deflate(n, G32, x, sig2 + l, r.cs));
   }
   TSVD_TRY(launch_sigma_from_sigma2(sig2, sigma, k, r.cs));
   TSVD_TRY(launch_f64_to_f32(V64, V32, n * k, r.cs));
@@ -875,6 +898,7 @@ tsvd_status tsvd_factor(tsvd_plan_t plan, const tsvd_matrix *A, void *workspace,
     report->flags = flags;
     report->mode = p->mode;
     report->n_blocks = (int32_t)p->n_chunks;
+    report->ring_slots = p->mode == MODE_STREAM ? p->n_buffers : 0;
   }
   tsvd_status st = p->kind == TSVD_DENSE_F32_ROWMAJOR ? factor_dense(r, U, sigma, V, report)
                                                       : factor_csr(r, U, sigma, V, report);
@@ -937,6 +961,11 @@ tsvd_status tsvd_power_dense_noalloc(int64_t n, const float *G32, const double *
   if (iters_override <= 0 && !(eps > 0.0 && eps < 1.0)) return TSVD_EINVAL;
   return launch_power_dense_noalloc(n, G32, G64, V64, sigma2, l, x, eps, max_iter, iters_override,
                                     sign_convention, out_sigma2, info, static_cast<cudaStream_t>(stream));
+}
+
+tsvd_status tsvd_gram_deflate(int64_t n, float *G32, const double *v, const double *sigma2, void *stream) {
+  if (n <= 0 || !G32 || !v || !sigma2) return TSVD_EINVAL;
+  return launch_gram_deflate(n, G32, v, sigma2, static_cast<cudaStream_t>(stream));
 }
 
 tsvd_status tsvd_gram_symmetrize(int64_t n, const double *G64, float *G32, void *stream) {

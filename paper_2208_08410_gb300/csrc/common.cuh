@@ -43,6 +43,7 @@ void count_launch();
 int64_t launches_so_far();
 
 inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+__device__ __forceinline__ int64_t ceil_div_dev(int64_t a, int64_t b) { return (a + b - 1) / b; }
 inline int64_t round_up(int64_t a, int64_t b) { return ceil_div(a, b) * b; }
 
 struct DeviceInfo {
@@ -91,36 +92,55 @@ __device__ __forceinline__ double block_sum(double v, double *red) {
   return red[32];
 }
 
+// gpu-scope acquire / release primitives for the grid barrier
+__device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned *p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ unsigned atom_add_acq_rel_gpu(unsigned *p, unsigned v) {
+  unsigned old;
+  asm volatile("atom.add.acq_rel.gpu.global.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+  return old;
+}
+__device__ __forceinline__ void red_add_release_gpu(unsigned *p, unsigned v) {
+  asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ void st_relaxed_gpu(unsigned *p, unsigned v) {
+  asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
 // Grid-wide barrier for a cooperative launch.  bar[0] counts arrivals, bar[1]
-// is the generation.  Waits are bounded: past kWaitLimitNs, or when another
-// block has raised *err, the waiter sets *err and returns false.
+// is the generation.  Thread 0 of each block arrives with an acquire-release
+// add (publishing the block's writes, which __syncthreads ordered before it);
+// the last arrival resets the count and bumps the generation with a release;
+// the others poll the generation with acquire loads.  Waits are bounded: past
+// kWaitLimitNs, or when another block has raised *err, the waiter sets *err
+// and returns false.
 __device__ __forceinline__ bool grid_barrier(unsigned *bar, int *err) {
   __shared__ int s_ok;
   __syncthreads();
   if (threadIdx.x == 0) {
-    volatile unsigned *vgen = bar + 1;
     volatile int *verr = err;
-    const unsigned g = *vgen;
-    __threadfence();
-    const unsigned arrived = atomicAdd(bar, 1u);
+    const unsigned g = ld_acquire_gpu(bar + 1);
+    const unsigned arrived = atom_add_acq_rel_gpu(bar, 1u);
     int ok = 1;
     if (arrived == gridDim.x * gridDim.y * gridDim.z - 1) {
-      atomicExch(bar, 0u);
-      __threadfence();
-      atomicAdd(bar + 1, 1u);
+      st_relaxed_gpu(bar, 0u);
+      red_add_release_gpu(bar + 1, 1u);
     } else {
       const uint64_t t0 = global_timer_ns();
-      while (*vgen == g) {
-        if (*verr) { ok = 0; break; }
-        if (global_timer_ns() - t0 > kWaitLimitNs) {
-          atomicExch(err, 1);
-          ok = 0;
-          break;
+      for (uint32_t spin = 0; ld_acquire_gpu(bar + 1) == g; ++spin) {
+        if ((spin & 63u) == 63u) {
+          if (*verr) { ok = 0; break; }
+          if (global_timer_ns() - t0 > kWaitLimitNs) {
+            atomicExch(err, 1);
+            ok = 0;
+            break;
+          }
         }
-        __nanosleep(32);
       }
     }
-    __threadfence();
     if (*verr) ok = 0;
     s_ok = ok;
   }
@@ -149,6 +169,7 @@ tsvd_status launch_power_dense_noalloc(int64_t n, const float *G32, const double
                                        int iters_override, int sign_convention, double *out_sigma2, int *info,
                                        cudaStream_t stream);
 tsvd_status launch_symmetrize(int64_t n, const double *G64, float *G32, cudaStream_t stream);
+tsvd_status launch_gram_deflate(int64_t n, float *G32, const double *v, const double *sigma2, cudaStream_t stream);
 tsvd_status launch_start_draws(uint64_t seed, int64_t l, int64_t n, double *x, cudaStream_t stream);
 tsvd_status launch_philox_raw(const uint32_t *ctr, const uint32_t *key, uint32_t *out,
                               int64_t count, cudaStream_t stream);

@@ -167,55 +167,38 @@ __device__ __forceinline__ float tf32_rne(float x) {
 }
 
 // ---------------------------------------------------------------- prep kernel
-// At[c][r] = tf32(A[r][c]) (and lo part), tiles of 64 rows x 64 columns.
+// At[c][r] = tf32(A[r][c]) (and the lo part).  A block of 32 x 8 threads moves
+// a 32-row x 128-column strip as four 32 x 32 tiles through shared memory, so
+// both the reads (along a row of A) and the writes (along a row of At) are
+// 128-byte coalesced; 16 loads per thread are in flight before the first store.
 template <int PARTS>
 __global__ void __launch_bounds__(256) prep_kernel(const float *__restrict__ A, int64_t rows, int64_t n, int64_t ld,
-                                                   float *__restrict__ hi, float *__restrict__ lo, int64_t Kp,
-                                                   int vec) {
-  __shared__ float s[64][65];
-  const int64_t r0 = (int64_t)blockIdx.x * 64;
-  const int64_t c0 = (int64_t)blockIdx.y * 64;
-  const int tid = threadIdx.x;
+                                                   float *__restrict__ hi, float *__restrict__ lo, int64_t Kp) {
+  __shared__ float s[4][32][33];
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int64_t r0 = (int64_t)blockIdx.x * 32;
+  const int64_t c0 = (int64_t)blockIdx.y * 128;
 #pragma unroll
-  for (int it = 0; it < 4; ++it) {
-    const int idx = tid + it * 256;
-    const int rr = idx >> 4, cc = (idx & 15) * 4;
-    const int64_t r = r0 + rr, c = c0 + cc;
-    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (r < rows) {
-      const float *row = A + r * ld;
-      if (vec && c + 3 < n) {
-        v = __ldg(reinterpret_cast<const float4 *>(row + c));
-      } else {
-        if (c < n) v.x = __ldg(row + c);
-        if (c + 1 < n) v.y = __ldg(row + c + 1);
-        if (c + 2 < n) v.z = __ldg(row + c + 2);
-        if (c + 3 < n) v.w = __ldg(row + c + 3);
-      }
+  for (int t = 0; t < 4; ++t) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int64_t r = r0 + ty + 8 * i, c = c0 + 32 * t + tx;
+      s[t][ty + 8 * i][tx] = (r < rows && c < n) ? __ldg(A + r * ld + c) : 0.f;
     }
-    s[cc][rr] = v.x;
-    s[cc + 1][rr] = v.y;
-    s[cc + 2][rr] = v.z;
-    s[cc + 3][rr] = v.w;
   }
   __syncthreads();
 #pragma unroll
-  for (int it = 0; it < 4; ++it) {
-    const int idx = tid + it * 256;
-    const int cc = idx >> 4, rr = (idx & 15) * 4;
-    const int64_t c = c0 + cc, r = r0 + rr;
-    if (c >= n || r >= Kp) continue;
-    float x[4] = {s[cc][rr], s[cc][rr + 1], s[cc][rr + 2], s[cc][rr + 3]};
-    float4 h, l;
-    float *hp = &h.x, *lp = &l.x;
+  for (int t = 0; t < 4; ++t) {
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const float t = tf32_rne(x[q]);
-      hp[q] = t;
-      lp[q] = tf32_rne(x[q] - t);
+    for (int i = 0; i < 4; ++i) {
+      const int64_t c = c0 + 32 * t + ty + 8 * i, r = r0 + tx;
+      if (c < n && r < Kp) {
+        const float x = s[t][tx][ty + 8 * i];
+        const float h = tf32_rne(x);
+        hi[c * Kp + r] = h;
+        if (PARTS == 2) lo[c * Kp + r] = tf32_rne(x - h);
+      }
     }
-    *reinterpret_cast<float4 *>(hi + c * Kp + r) = h;
-    if (PARTS == 2) *reinterpret_cast<float4 *>(lo + c * Kp + r) = l;
   }
 }
 
@@ -500,13 +483,12 @@ tsvd_status launch_gram_tc(const float *A, int64_t rows, int64_t n, int64_t ld, 
 
   // 1. prep: transpose + TF32 rounding (+ split)
   {
-    const bool vec = (ld % 4 == 0) && ((reinterpret_cast<uintptr_t>(A) & 15) == 0);
-    dim3 grid((unsigned)ceil_div(Kp, 64), (unsigned)ceil_div(n, 64));
-    if (grid.y > 65535) return TSVD_EUNSUPPORTED;
+    dim3 grid((unsigned)ceil_div(Kp, 32), (unsigned)ceil_div(n, 128)), block(32, 8);
+    if (grid.y > 65535 || grid.x > 0x7fffffffu) return TSVD_EUNSUPPORTED;
     if (parts == 2)
-      prep_kernel<2><<<grid, 256, 0, stream>>>(A, rows, n, ld, hi, lo, Kp, vec ? 1 : 0);
+      prep_kernel<2><<<grid, block, 0, stream>>>(A, rows, n, ld, hi, lo, Kp);
     else
-      prep_kernel<1><<<grid, 256, 0, stream>>>(A, rows, n, ld, hi, lo, Kp, vec ? 1 : 0);
+      prep_kernel<1><<<grid, block, 0, stream>>>(A, rows, n, ld, hi, lo, Kp);
     TSVD_LAUNCHED();
   }
   // 2. persistent tcgen05 SYRK over the lower-triangle tiles
@@ -524,8 +506,9 @@ tsvd_status launch_gram_tc(const float *A, int64_t rows, int64_t n, int64_t ld, 
     a.n_tiles = (int)((a.n_iblk & 1) ? (q + 1) * (q + 1) : q * (q + 1));
   }
   {
-    // K slices: aim for >= 8 units per SM (load balance across the persistent
-    // grid) without slices shorter than 4096 rows (FP64 atomics per unit)
+    // K slices: about 8 units per SM balance the persistent grid; fewer,
+    // longer units keep the FP64 reductions into G (one 128 x 256 tile per
+    // unit) small, so slices are never shorter than 4096 rows
     const int64_t quantum = (int64_t)TK * a.seg_stages;
     const int64_t want_units = 8LL * di.sms;
     int64_t splits = std::max<int64_t>(1, ceil_div(want_units, a.n_tiles));

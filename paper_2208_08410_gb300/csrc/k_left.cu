@@ -4,27 +4,34 @@
 //
 // A is rows x n row-major; V is n x k column-major.  A block of 256 threads
 // owns 64 rows; each warp keeps 8 rows x 16 columns of partial sums in
-// registers while the lanes stride along the row (coalesced loads of A).  V
-// is staged through shared memory 256 rows at a time (transposed to
-// [j][l]), so each staged value feeds 8 rows.  Columns are processed 16 at a
-// time (A is re-read for k > 16).
+// registers.  A lane reads four consecutive entries of a row with one 16-byte
+// load (coalesced across the warp, 16 such loads in flight per lane); the
+// matching 4 x 16 entries of V come from shared memory, where V is staged 256
+// rows at a time, column by column (j contiguous, so the staging writes and
+// the 16-byte reads are free of bank conflicts).  Each staged value of V feeds
+// 8 rows.  Columns are processed 16 at a time (A is re-read for k > 16).
+#include <cuda.h>
+
 #include <algorithm>
 
 #include "common.cuh"
 
 namespace tsvd {
+
+__device__ int g_left_status;  // nonzero once a bounded wait of the TMA kernel gave up
+
 namespace {
 
 constexpr int LT = 256;   // threads
 constexpr int LR = 8;     // rows per warp
 constexpr int LK = 16;    // columns per pass
-constexpr int LJ = 256;   // V rows staged per step
+constexpr int LJ = 256;   // V rows staged per step (= 32 lanes x 4 x 2)
 
 __global__ void __launch_bounds__(LT, 1)
 left_dense_kernel(const float *__restrict__ A, int64_t rows, int64_t n, int64_t ld,
                   const float *__restrict__ V, int64_t ldv, int64_t k, const double *__restrict__ sigma,
-                  float *__restrict__ U, int64_t ldu, int l0) {
-  __shared__ __align__(16) float Vs[LJ][LK];
+                  float *__restrict__ U, int64_t ldu, int l0, int vec) {
+  __shared__ __align__(16) float Vs[LK][LJ];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t row0 = (int64_t)blockIdx.x * (LT / 32) * LR + (int64_t)warp * LR;
   float acc[LR][LK];
@@ -32,28 +39,48 @@ left_dense_kernel(const float *__restrict__ A, int64_t rows, int64_t n, int64_t 
   for (int r = 0; r < LR; ++r)
 #pragma unroll
     for (int t = 0; t < LK; ++t) acc[r][t] = 0.f;
-  const int kc = (int)std::min<int64_t>(LK, k - l0);
+  const int kc = (int)min((int64_t)LK, k - l0);
+  const float *arow[LR];
+#pragma unroll
+  for (int r = 0; r < LR; ++r) arow[r] = A + min(row0 + r, rows - 1) * ld;  // clamp: rows past the end are not stored
 
   for (int64_t j0 = 0; j0 < n; j0 += LJ) {
     __syncthreads();
     for (int e = threadIdx.x; e < LJ * LK; e += LT) {
-      const int jj = e % LJ, t = e / LJ;  // consecutive threads read consecutive j of one column
+      const int jj = e % LJ, t = e / LJ;
       const int64_t j = j0 + jj;
-      Vs[jj][t] = (t < kc && j < n) ? __ldg(V + (int64_t)(l0 + t) * ldv + j) : 0.f;
+      Vs[t][jj] = (t < kc && j < n) ? __ldg(V + (int64_t)(l0 + t) * ldv + j) : 0.f;
     }
     __syncthreads();
-    const int jmax = (int)std::min<int64_t>(LJ, n - j0);
-    for (int jj = lane; jj < jmax; jj += 32) {
-      const float4 *vq = reinterpret_cast<const float4 *>(&Vs[jj][0]);
-      const float4 q0 = vq[0], q1 = vq[1], q2 = vq[2], q3 = vq[3];
-      const float vv[LK] = {q0.x, q0.y, q0.z, q0.w, q1.x, q1.y, q1.z, q1.w,
-                            q2.x, q2.y, q2.z, q2.w, q3.x, q3.y, q3.z, q3.w};
 #pragma unroll
-      for (int r = 0; r < LR; ++r) {
-        const int64_t row = row0 + r;
-        const float a = row < rows ? __ldg(A + row * ld + j0 + jj) : 0.f;
+    for (int s = 0; s < 2; ++s) {
+      const int jj = 128 * s + 4 * lane;
+      const int64_t j = j0 + jj;
+      float4 a[LR];
+      if (vec && j + 3 < n) {
 #pragma unroll
-        for (int t = 0; t < LK; ++t) acc[r][t] = fmaf(a, vv[t], acc[r][t]);
+        for (int r = 0; r < LR; ++r) a[r] = __ldg(reinterpret_cast<const float4 *>(arow[r] + j));
+      } else {
+#pragma unroll
+        for (int r = 0; r < LR; ++r) {
+          a[r].x = j < n ? __ldg(arow[r] + j) : 0.f;
+          a[r].y = j + 1 < n ? __ldg(arow[r] + j + 1) : 0.f;
+          a[r].z = j + 2 < n ? __ldg(arow[r] + j + 2) : 0.f;
+          a[r].w = j + 3 < n ? __ldg(arow[r] + j + 3) : 0.f;
+        }
+      }
+#pragma unroll
+      for (int t = 0; t < LK; ++t) {
+        const float4 vq = *reinterpret_cast<const float4 *>(&Vs[t][jj]);
+#pragma unroll
+        for (int r = 0; r < LR; ++r) {
+          float x = acc[r][t];
+          x = fmaf(a[r].x, vq.x, x);
+          x = fmaf(a[r].y, vq.y, x);
+          x = fmaf(a[r].z, vq.z, x);
+          x = fmaf(a[r].w, vq.w, x);
+          acc[r][t] = x;
+        }
       }
     }
   }
@@ -66,14 +93,173 @@ left_dense_kernel(const float *__restrict__ A, int64_t rows, int64_t n, int64_t 
 #pragma unroll
   for (int t = 0; t < LK; ++t) {
     if (lane == t && t < kc) {
-      const double s = __ldg(sigma + l0 + t);
+      const double sg = __ldg(sigma + l0 + t);
 #pragma unroll
       for (int r = 0; r < LR; ++r) {
         const int64_t row = row0 + r;
-        if (row < rows) U[row + (int64_t)(l0 + t) * ldu] = s > 0.0 ? (float)((double)acc[r][t] / s) : 0.f;
+        if (row < rows) U[row + (int64_t)(l0 + t) * ldu] = sg > 0.0 ? (float)((double)acc[r][t] / sg) : 0.f;
       }
     }
   }
+}
+
+
+// ---------------------------------------------------------------- TMA variant
+// Same arithmetic, but a persistent block streams 64-row x 128-column tiles
+// of A and the matching 128 x 16 tile of V^T into a four-stage shared-memory
+// ring with TMA, three tiles ahead, so HBM latency is hidden by the copy
+// engine instead of by warp occupancy.  Each of the 16 warps owns 4 rows of
+// the tile (4 x 16 accumulators per thread).
+constexpr int TT = 512;                         // threads (16 warps)
+constexpr int TRW = 4;                          // rows per warp
+constexpr int TLH = 16;                         // columns of V per sweep
+constexpr int TR = 64;                          // rows per tile
+constexpr int TJ = 128;                         // columns per chunk (32 lanes x 4)
+constexpr int T_ABYTES = TR * TJ * 4;           // 32 KB
+constexpr int T_VBYTES = LK * TJ * 4;           // 8 KB
+constexpr int T_STAGE = T_ABYTES + T_VBYTES;    // 40 KB
+constexpr int T_NST = 4;                        // stages (three tiles in flight)
+constexpr int T_SMEM = T_NST * T_STAGE + 1024 + 64;
+
+__device__ __forceinline__ uint32_t su32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ bool mbar_wait_l(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  const uint64_t t0 = global_timer_ns();
+  for (uint32_t spin = 0;; ++spin) {
+    asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+                 : "=r"(ok) : "r"(bar), "r"(parity) : "memory");
+    if (ok) return true;
+    if ((spin & 255u) == 255u) {
+      if (*(volatile int *)&g_left_status) return false;
+      if (global_timer_ns() - t0 > kWaitLimitNs) {
+        atomicExch(&g_left_status, 1);
+        return false;
+      }
+    }
+  }
+}
+
+__global__ void __launch_bounds__(TT, 1)
+left_tma_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapV, int64_t rows,
+                int64_t n, int64_t k, const double *__restrict__ sigma, float *__restrict__ U, int64_t ldu, int l0) {
+  extern __shared__ __align__(1024) unsigned char smraw[];
+  unsigned char *sm = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smraw) + 1023) & ~uintptr_t(1023));
+  uint64_t *full = reinterpret_cast<uint64_t *>(sm + T_NST * T_STAGE);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t tiles = ceil_div_dev(rows, TR);
+  const int64_t chunks = ceil_div_dev(n, TJ);
+  const int kc = (int)min((int64_t)LK, k - l0);
+  if (threadIdx.x == 0) {
+    for (int b = 0; b < T_NST; ++b)
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(full + b)) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  // the block's work: tiles blockIdx.x, +gridDim.x, ...; each tile = `chunks` chunks
+  const int64_t my_tiles = tiles > blockIdx.x ? ceil_div_dev(tiles - blockIdx.x, gridDim.x) : 0;
+  const int64_t total = my_tiles * chunks;
+  auto issue = [&](int64_t c) {  // chunk sequence number c -> stage c % T_NST
+    const int64_t tile = blockIdx.x + (c / chunks) * gridDim.x;
+    const int j0 = (int)((c % chunks) * TJ);
+    const uint32_t st = su32(sm + (c % T_NST) * T_STAGE);
+    const uint32_t bar = su32(full + (c % T_NST));
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(T_STAGE) : "memory");
+    asm volatile("cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
+                 ::"r"(st), "l"(reinterpret_cast<uint64_t>(&mapA)), "r"(j0), "r"((int)(tile * TR)), "r"(bar) : "memory");
+    asm volatile("cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
+                 ::"r"(st + T_ABYTES), "l"(reinterpret_cast<uint64_t>(&mapV)), "r"(j0), "r"(l0), "r"(bar) : "memory");
+  };
+  if (threadIdx.x == 0) {
+    for (int64_t c = 0; c < T_NST - 1 && c < total; ++c) issue(c);
+  }
+  float acc[1][TRW][TLH];
+  bool ok = true;
+  for (int64_t c = 0; c < total; ++c) {
+    const int64_t cj = c % chunks;
+    if (cj == 0) {
+#pragma unroll
+      for (int r = 0; r < TRW; ++r)
+#pragma unroll
+        for (int t = 0; t < TLH; ++t) acc[0][r][t] = 0.f;
+    }
+    // stage (c + T_NST - 1) % T_NST was released by the sync at the end of iteration c - 1
+    if (threadIdx.x == 0 && c + T_NST - 1 < total) issue(c + T_NST - 1);
+    if (!mbar_wait_l(su32(full + (c % T_NST)), (uint32_t)((c / T_NST) & 1))) ok = false;
+    if (__syncthreads_or(!ok)) break;
+    const float *As = reinterpret_cast<const float *>(sm + (c % T_NST) * T_STAGE);
+    const float *Vs = reinterpret_cast<const float *>(sm + (c % T_NST) * T_STAGE + T_ABYTES);
+    const int jj = 4 * lane;
+#pragma unroll
+    for (int h = 0; h < 1; ++h) {
+      float4 a[TRW];
+#pragma unroll
+      for (int r = 0; r < TRW; ++r) a[r] = *reinterpret_cast<const float4 *>(As + (warp * TRW + r) * TJ + jj);
+#pragma unroll
+      for (int t = 0; t < TLH; ++t) {
+        const float4 vq = *reinterpret_cast<const float4 *>(Vs + (h * TLH + t) * TJ + jj);
+#pragma unroll
+        for (int r = 0; r < TRW; ++r) {
+          float x = acc[h][r][t];
+          x = fmaf(a[r].x, vq.x, x);
+          x = fmaf(a[r].y, vq.y, x);
+          x = fmaf(a[r].z, vq.z, x);
+          x = fmaf(a[r].w, vq.w, x);
+          acc[h][r][t] = x;
+        }
+      }
+    }
+    __syncthreads();  // every warp is done with this stage before it is refilled
+    if (cj == chunks - 1) {
+      const int64_t tile = blockIdx.x + (c / chunks) * gridDim.x;
+      const int64_t row0 = tile * TR + warp * TRW;
+#pragma unroll
+      for (int r = 0; r < TRW; ++r)
+#pragma unroll
+        for (int t = 0; t < TLH; ++t) acc[0][r][t] = warp_sumf(acc[0][r][t]);
+      // lane t writes column l0 + t of the warp's rows (select, no dynamic indexing)
+#pragma unroll
+      for (int r = 0; r < TRW; ++r) {
+        float v = 0.f;
+#pragma unroll
+        for (int t = 0; t < TLH; ++t) v = (lane == t) ? acc[0][r][t] : v;
+        const int64_t row = row0 + r;
+        if (lane < kc && row < rows) {
+          const double sg = __ldg(sigma + l0 + lane);
+          U[row + (int64_t)(l0 + lane) * ldu] = sg > 0.0 ? (float)((double)v / sg) : 0.f;
+        }
+      }
+    }
+  }
+  // a copy may still be in flight if the loop broke early: wait (bounded) for it
+  if (!ok && threadIdx.x == 0) {
+    for (int b = 0; b < T_NST; ++b) mbar_wait_l(su32(full + b), 0);
+  }
+  __syncthreads();
+}
+
+typedef CUresult (*EncodeTiledFnL)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                   const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+tsvd_status encode_2d(CUtensorMap *map, const float *base, int64_t inner, int64_t outer, int64_t stride_elems,
+                      uint32_t box_inner, uint32_t box_outer) {
+  static EncodeTiledFnL fn = nullptr;
+  if (!fn) {
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    TSVD_CUDA(cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q));
+    if (q != cudaDriverEntryPointSuccess || !p) return TSVD_ECUDA;
+    fn = reinterpret_cast<EncodeTiledFnL>(p);
+  }
+  const cuuint64_t dims[2] = {(cuuint64_t)inner, (cuuint64_t)outer};
+  const cuuint64_t strides[1] = {(cuuint64_t)stride_elems * 4};
+  const cuuint32_t box[2] = {box_inner, box_outer};
+  const cuuint32_t es[2] = {1, 1};
+  const CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float *>(base), dims, strides, box, es,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? TSVD_OK : TSVD_ECUDA;
 }
 
 }  // namespace
@@ -85,9 +271,31 @@ tsvd_status launch_left_dense(const float *A, int64_t rows, int64_t n, int64_t l
   const int64_t rows_per_block = (LT / 32) * LR;
   const int64_t blocks = ceil_div(rows, rows_per_block);
   if (blocks > 0x7fffffffLL) return TSVD_EINVAL;
+  const bool vec = (ld % 4 == 0) && ((reinterpret_cast<uintptr_t>(A) & 15) == 0);
+  DeviceInfo di;
+  TSVD_TRY(device_info(&di));
+  // TMA needs 16-byte aligned bases and strides
+  const bool tma = vec && di.cc_major == 10 && (ldv % 4 == 0) && ((reinterpret_cast<uintptr_t>(V) & 15) == 0) &&
+                   rows >= TR && n >= 64;
   for (int64_t l0 = 0; l0 < k; l0 += LK) {
-    left_dense_kernel<<<(unsigned)blocks, LT, 0, stream>>>(A, rows, n, ld, V, ldv, k, sigma, U, ldu, (int)l0);
-    TSVD_LAUNCHED();
+    if (tma) {
+      CUtensorMap ma, mv;
+      TSVD_TRY(encode_2d(&ma, A, n, rows, ld, TJ, TR));
+      TSVD_TRY(encode_2d(&mv, V, n, k, ldv, TJ, LK));
+      static thread_local bool attr = false;
+      if (!attr) {
+        TSVD_CUDA(cudaFuncSetAttribute(left_tma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, T_SMEM));
+        attr = true;
+      }
+      const int64_t tiles = ceil_div(rows, TR);
+      const int grid = (int)std::min<int64_t>(tiles, di.sms);
+      left_tma_kernel<<<grid, TT, T_SMEM, stream>>>(ma, mv, rows, n, k, sigma, U, ldu, (int)l0);
+      TSVD_LAUNCHED();
+    } else {
+      left_dense_kernel<<<(unsigned)blocks, LT, 0, stream>>>(A, rows, n, ld, V, ldv, k, sigma, U, ldu, (int)l0,
+                                                             vec ? 1 : 0);
+      TSVD_LAUNCHED();
+    }
   }
   return TSVD_OK;
 }

@@ -6,12 +6,15 @@
 //     w = G v0 - sum_{j<l} sigma_j^2 v_j (v_j^T v0)
 // and closes with sigma_l^2 = v_l^T G v_l (Alg. 1 l.11-13: sigma = ||A v||).
 //
-// One cooperative launch runs the whole loop: each block owns a contiguous
-// range of rows; two bounded grid barriers per iteration separate
-//   A: w_raw = G32 v (FP32 products, FP64 row sums) and partial v_j^T v
-//   B: deflation, partial ||w||^2, v.w, v.v (FP64)
-//   C: every block reduces the partials in the same fixed order, so all
-//      blocks take the same convergence decision without a host round trip.
+// The FP32 copy of G is deflated in place once per triplet (rank-1 update,
+// tsvd_gram_deflate), so an iteration is one GEMV with the deflated matrix:
+// the same Hotelling operator as above, applied as a matrix.  One cooperative
+// launch runs the whole loop; each block owns a contiguous range of rows and
+// an iteration has a single bounded grid barrier:
+//   w = G32_defl v for the block's rows (FP32 products, FP64 row sums) and
+//   the block's partial ||w||^2, v.w, v.v (FP64) -> barrier -> every block
+//   reduces the partials in the same fixed order, so all blocks take the same
+//   convergence decision without a host round trip.
 // Also here: the symmetrising copy G64 -> G32, the Philox-4x32-10 start
 // draws, and small conversions.
 #include <algorithm>
@@ -39,7 +42,7 @@ struct PowerArgs {
   int sign_convention;
   double *out_sigma2;
   int *info;
-  double *wb0, *wb1;   // n each
+  float *wb0, *wb1;    // n each: the FP32 iterate (unnormalised w) in two buffers
   double *part;        // gridDim.x * ps
   int ps;              // partial stride (doubles)
   unsigned *bar;       // 2 counters
@@ -47,11 +50,49 @@ struct PowerArgs {
   int64_t rows_per_block;
 };
 
+// s + e == a + b exactly (Knuth's TwoSum, FP32, no FMA contraction possible)
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+  s = a + b;
+  const float bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
+
+// Warp sum of FP32 values carried as an unevaluated hi + lo pair (every
+// partial addition is error-free); every lane ends with the same pair.
+// GB300's FP64 pipe is narrow, so the row sums stay in FP32 and only lane 0
+// forms the FP64 value.
+__device__ __forceinline__ void warp_sum_f32x2(float &hi, float &lo) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const float ho = __shfl_xor_sync(0xffffffffu, hi, o);
+    const float lo2 = __shfl_xor_sync(0xffffffffu, lo, o);
+    float s, e;
+    two_sum(hi, ho, s, e);
+    hi = s;
+    lo = lo + lo2 + e;
+  }
+}
+
+// sum of part[c*ps + off] over blocks c = lane, lane+32, ... (the loads are
+// issued together, then added in a fixed order)
+__device__ __forceinline__ double lane_partials(const double *part, int ps, int off, int lane) {
+  double v[8];
+#pragma unroll
+  for (int u = 0; u < 8; ++u) {
+    const int c = lane + 32 * u;
+    v[u] = c < (int)gridDim.x ? __ldcg(part + (int64_t)c * ps + off) : 0.0;
+  }
+  double t = 0.0;
+#pragma unroll
+  for (int u = 0; u < 8; ++u) t += v[u];
+  for (int c = lane + 256; c < (int)gridDim.x; c += 32) t += __ldcg(part + (int64_t)c * ps + off);
+  return t;
+}
+
 // reduce part[c*ps + off] over all blocks c, same order in every block
 __device__ double reduce_partials(const double *part, int ps, int off, double *red) {
-  double t = 0.0;
   if (threadIdx.x < 32) {
-    for (int c = threadIdx.x; c < (int)gridDim.x; c += 32) t += __ldcg(part + (int64_t)c * ps + off);
+    double t = lane_partials(part, ps, off, threadIdx.x);
     t = warp_sum(t);
     if (threadIdx.x == 0) red[32] = t;
   }
@@ -63,9 +104,10 @@ __device__ double reduce_partials(const double *part, int ps, int off, double *r
 
 __global__ void __launch_bounds__(PT, 1) power_dense_kernel(PowerArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  float *vs = reinterpret_cast<float *>(smem_raw);                          // n floats (padded)
-  double *coef = reinterpret_cast<double *>(smem_raw + ((a.n + 3) / 4) * 16);  // l doubles
+  float *vs = reinterpret_cast<float *>(smem_raw);                                // n floats (padded)
+  double *coef = reinterpret_cast<double *>(smem_raw + ((a.n + 3) / 4) * 16);    // l doubles
   __shared__ double red[33];
+  __shared__ double wred[3 * (PT / 32)];
   __shared__ double s_scal[4];
 
   const int64_t n = a.n;
@@ -87,147 +129,235 @@ __global__ void __launch_bounds__(PT, 1) power_dense_kernel(PowerArgs a) {
   if (threadIdx.x == 0) mypart[0] = s;
   if (!grid_barrier(a.bar, a.err)) return;
   const double xx = reduce_partials(a.part, ps, 0, red);
-  const double *vsrc = a.x;
-  double vscale = xx > 0.0 ? 1.0 / sqrt(xx) : 0.0;
+  if (threadIdx.x == 0) s_scal[0] = xx > 0.0 ? 1.0 / sqrt(xx) : 0.0;
+  __syncthreads();
+  double vscale = s_scal[0];
+  __syncthreads();
   const double rank_scale = (l == 0) ? 1.0 : __ldcg(a.sig2);
 
   int it = 0, status = 0;
-  double *wnext = a.wb0;
+  const float *vsrc = nullptr;  // FP32 iterate of the previous step (unnormalised)
+  float *wnext = a.wb0;
   for (;;) {
-    // ---- phase A: w_raw = G32 v, partial c_j = v_j^T v
-    for (int64_t j = threadIdx.x; j < n; j += PT) vs[j] = (float)(__ldcg(vsrc + j) * vscale);
+    // ---- v = w_prev / ||w_prev|| into shared memory (FP32)
+    if (it == 0) {
+      for (int64_t j = threadIdx.x; j < n; j += PT) vs[j] = (float)(__ldcg(a.x + j) * vscale);
+    } else {
+      const float sc = (float)vscale;
+      int64_t j = threadIdx.x;
+      for (; j + 7 * PT < n; j += 8 * PT) {
+        float t[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) t[u] = __ldcg(vsrc + j + u * PT);
+#pragma unroll
+        for (int u = 0; u < 8; ++u) vs[j + u * PT] = t[u] * sc;
+      }
+      for (; j < n; j += PT) vs[j] = __ldcg(vsrc + j) * sc;
+    }
     __syncthreads();
-    for (int64_t i = r0 + warp; i < r1; i += nwarps) {
-      const float *g = a.G32 + i * n;
-      float acc0 = 0.f, acc1 = 0.f, acc2 = 0.f, acc3 = 0.f;
+    // ---- w = G32_defl v for this block's rows, partial ||w||^2, v.w, v.v
+    double ww = 0.0, vw = 0.0, vv = 0.0;
+    for (int64_t i = r0 + 2 * warp; i < r1; i += 2 * nwarps) {
+      // rows i and i+1 (the second may be past the block's range)
+      const bool two = i + 1 < r1;
+      const float *g0 = a.G32 + i * n;
+      const float *g1 = a.G32 + (two ? i + 1 : i) * n;
+      float p0 = 0.f, p1 = 0.f, p2 = 0.f, p3 = 0.f, q0 = 0.f, q1 = 0.f, q2 = 0.f, q3 = 0.f;
       if (vec) {
-        const float4 *g4 = reinterpret_cast<const float4 *>(g);
+        const float4 *ga = reinterpret_cast<const float4 *>(g0);
+        const float4 *gb = reinterpret_cast<const float4 *>(g1);
         const float4 *v4 = reinterpret_cast<const float4 *>(vs);
         const int64_t n4 = n >> 2;
-        for (int64_t q = lane; q < n4; q += 32) {
-          const float4 gq = __ldg(g4 + q);
-          const float4 vq = v4[q];
-          acc0 = fmaf(gq.x, vq.x, acc0);
-          acc1 = fmaf(gq.y, vq.y, acc1);
-          acc2 = fmaf(gq.z, vq.z, acc2);
-          acc3 = fmaf(gq.w, vq.w, acc3);
+        int64_t q = lane;
+        // sixteen independent 16-byte loads in flight per lane
+        for (; q + 32 * 7 < n4; q += 32 * 8) {
+          float4 ra[8], rb[8];
+#pragma unroll
+          for (int u = 0; u < 8; ++u) {
+            ra[u] = __ldg(ga + q + 32 * u);
+            rb[u] = __ldg(gb + q + 32 * u);
+          }
+#pragma unroll
+          for (int u = 0; u < 8; ++u) {
+            const float4 vq = v4[q + 32 * u];
+            p0 = fmaf(ra[u].x, vq.x, p0); p1 = fmaf(ra[u].y, vq.y, p1);
+            p2 = fmaf(ra[u].z, vq.z, p2); p3 = fmaf(ra[u].w, vq.w, p3);
+            q0 = fmaf(rb[u].x, vq.x, q0); q1 = fmaf(rb[u].y, vq.y, q1);
+            q2 = fmaf(rb[u].z, vq.z, q2); q3 = fmaf(rb[u].w, vq.w, q3);
+          }
+        }
+        for (; q < n4; q += 32) {
+          const float4 xa = __ldg(ga + q), xb = __ldg(gb + q), vq = v4[q];
+          p0 = fmaf(xa.x, vq.x, p0); p1 = fmaf(xa.y, vq.y, p1);
+          p2 = fmaf(xa.z, vq.z, p2); p3 = fmaf(xa.w, vq.w, p3);
+          q0 = fmaf(xb.x, vq.x, q0); q1 = fmaf(xb.y, vq.y, q1);
+          q2 = fmaf(xb.z, vq.z, q2); q3 = fmaf(xb.w, vq.w, q3);
         }
       } else {
-        for (int64_t q = lane; q < n; q += 32) acc0 = fmaf(__ldg(g + q), vs[q], acc0);
+        for (int64_t q = lane; q < n; q += 32) {
+          p0 = fmaf(__ldg(g0 + q), vs[q], p0);
+          q0 = fmaf(__ldg(g1 + q), vs[q], q0);
+        }
       }
-      double t = ((double)acc0 + (double)acc1) + ((double)acc2 + (double)acc3);
-      t = warp_sum(t);
-      if (lane == 0) wnext[i] = t;
+      float h0, e0, h1, e1, sa, ea, sb2, eb;
+      two_sum(p0, p1, sa, ea);
+      two_sum(p2, p3, sb2, eb);
+      two_sum(sa, sb2, h0, e0);
+      e0 += ea + eb;
+      two_sum(q0, q1, sa, ea);
+      two_sum(q2, q3, sb2, eb);
+      two_sum(sa, sb2, h1, e1);
+      e1 += ea + eb;
+      warp_sum_f32x2(h0, e0);
+      warp_sum_f32x2(h1, e1);
+      if (lane == 0) {
+        // the iterate is stored in FP32; the sums use exactly the stored values,
+        // so 1/||w|| normalises the stored vector to FP64 accuracy
+        const double t0 = (double)(float)((double)h0 + (double)e0);
+        const double t1 = (double)(float)((double)h1 + (double)e1);
+        const double v0i = (double)vs[i];
+        wnext[i] = (float)t0;
+        ww += t0 * t0;
+        vw += v0i * t0;
+        vv += v0i * v0i;
+        if (two) {
+          const double v1i = (double)vs[i + 1];
+          wnext[i + 1] = (float)t1;
+          ww += t1 * t1;
+          vw += v1i * t1;
+          vv += v1i * v1i;
+        }
+      }
     }
-    for (int j = warp; j < l; j += nwarps) {
-      const double *vj = a.V64 + (int64_t)j * n;
-      double t = 0.0;
-      for (int64_t i = r0 + lane; i < r1; i += 32) t += __ldg(vj + i) * (__ldcg(vsrc + i) * vscale);
-      t = warp_sum(t);
-      if (lane == 0) mypart[1 + j] = t;
-    }
-    if (!grid_barrier(a.bar, a.err)) return;
-
-    // ---- phase B: deflate (Hotelling), partial norms
-    for (int j = warp; j < l; j += nwarps) {
-      double t = 0.0;
-      for (int c = lane; c < (int)gridDim.x; c += 32) t += __ldcg(a.part + (int64_t)c * ps + 1 + j);
-      t = warp_sum(t);
-      if (lane == 0) coef[j] = __ldg(a.sig2 + j) * t;
+    // block sums of the three values (only lane 0 of each warp holds any)
+    if (lane == 0) {
+      wred[3 * warp] = ww;
+      wred[3 * warp + 1] = vw;
+      wred[3 * warp + 2] = vv;
     }
     __syncthreads();
-    double ww = 0.0, vw = 0.0, vv = 0.0;
-    for (int64_t i = r0 + threadIdx.x; i < r1; i += PT) {
-      double wi = __ldcg(wnext + i);
-      for (int j = 0; j < l; ++j) wi -= __ldg(a.V64 + (int64_t)j * n + i) * coef[j];
-      wnext[i] = wi;
-      const double vi = __ldcg(vsrc + i) * vscale;
-      ww += wi * wi;
-      vw += vi * wi;
-      vv += vi * vi;
-    }
-    ww = block_sum(ww, red);
-    vw = block_sum(vw, red);
-    vv = block_sum(vv, red);
+    // partials alternate between two slots, so a block still reading the
+    // previous iteration's sums is never overwritten
+    const int slot = 1 + (it & 1) * 3;
     if (threadIdx.x == 0) {
-      mypart[1 + l] = ww;
-      mypart[2 + l] = vw;
-      mypart[3 + l] = vv;
+      double t0 = 0.0, t1 = 0.0, t2 = 0.0;
+      for (int w = 0; w < nwarps; ++w) {
+        t0 += wred[3 * w];
+        t1 += wred[3 * w + 1];
+        t2 += wred[3 * w + 2];
+      }
+      mypart[slot] = t0;
+      mypart[slot + 1] = t1;
+      mypart[slot + 2] = t2;
     }
     if (!grid_barrier(a.bar, a.err)) return;
 
-    // ---- phase C: identical decision in every block
-    const double tww = reduce_partials(a.part, ps, 1 + l, red);
-    const double tvw = reduce_partials(a.part, ps, 2 + l, red);
-    const double tvv = reduce_partials(a.part, ps, 3 + l, red);
+    // ---- identical decision in every block (warp 0 reduces, thread 0 decides:
+    // FP64 division and square roots are slow on this part, so no other thread
+    // repeats them)
+    if (warp == 0) {
+      double t0 = lane_partials(a.part, ps, slot, lane);
+      double t1 = lane_partials(a.part, ps, slot + 1, lane);
+      double t2 = lane_partials(a.part, ps, slot + 2, lane);
+      t0 = warp_sum(t0);
+      t1 = warp_sum(t1);
+      t2 = warp_sum(t2);
+      if (lane == 0) {
+        const int it1 = it + 1;
+        const double nw = sqrt(t0);
+        int st = 0, done = 0;
+        double sc = 0.0;
+        if (!(nw > 1e-30 * rank_scale)) {
+          st = 2;
+          done = 1;
+        } else {
+          sc = 1.0 / nw;
+          const double cosv = fabs(t1) / (nw * sqrt(t2));
+          if (a.iters_override > 0) {
+            done = it1 >= a.iters_override;
+          } else {
+            done = cosv >= 1.0 - a.eps;
+            if (!done && it1 >= a.max_iter) {
+              done = 1;
+              st = 1;
+            }
+          }
+        }
+        s_scal[0] = sc;
+        s_scal[1] = (double)st;
+        s_scal[2] = (double)done;
+      }
+    }
+    __syncthreads();
     ++it;
-    const double nw = sqrt(tww);
-    if (!(nw > 1e-30 * rank_scale)) {
+    const int st = (int)s_scal[1];
+    const bool done = s_scal[2] != 0.0;
+    if (st == 2) {
       status = 2;
       break;
     }
-    const double cosv = fabs(tvw) / (nw * sqrt(tvv));
     vsrc = wnext;
-    vscale = 1.0 / nw;
+    vscale = s_scal[0];
     wnext = (wnext == a.wb0) ? a.wb1 : a.wb0;
-    bool done;
-    if (a.iters_override > 0) {
-      done = it >= a.iters_override;
-    } else {
-      done = cosv >= 1.0 - a.eps;
-      if (!done && it >= a.max_iter) {
-        done = true;
-        status = 1;
-      }
+    __syncthreads();  // s_scal is rewritten in the next iteration
+    if (done) {
+      status = st;
+      break;
     }
-    if (done) break;
   }
 
+  // ---- the block's rows of v_l (FP64) into x
   if (status == 2) {
-    // rank(A) < l+1: v = v0 made orthogonal to v_0..v_{l-1} (two passes), sigma = 0
+    // rank(A) < l+1: v = v0 made orthogonal to v_0..v_{l-1} (two passes), sigma = 0.
+    // v0 is the vector of the step whose B v0 vanished (x itself on the first step).
+    for (int64_t i = r0 + threadIdx.x; i < r1; i += PT)
+      a.x[i] = it <= 1 ? __ldcg(a.x + i) * vscale : (double)__ldcg(vsrc + i) * vscale;
     for (int pass = 0; pass < 2; ++pass) {
+      __syncthreads();
       for (int j = warp; j < l; j += nwarps) {
         const double *vj = a.V64 + (int64_t)j * n;
         double t = 0.0;
-        for (int64_t i = r0 + lane; i < r1; i += 32) t += __ldg(vj + i) * (__ldcg(vsrc + i) * vscale);
+        for (int64_t i = r0 + lane; i < r1; i += 32) t += __ldg(vj + i) * a.x[i];
         t = warp_sum(t);
-        if (lane == 0) mypart[1 + j] = t;
+        if (lane == 0) mypart[7 + j] = t;
       }
       if (!grid_barrier(a.bar, a.err)) return;
       for (int j = warp; j < l; j += nwarps) {
-        double t = 0.0;
-        for (int c = lane; c < (int)gridDim.x; c += 32) t += __ldcg(a.part + (int64_t)c * ps + 1 + j);
+        double t = lane_partials(a.part, ps, 7 + j, lane);
         t = warp_sum(t);
         if (lane == 0) coef[j] = t;
       }
       __syncthreads();
       double nn = 0.0;
       for (int64_t i = r0 + threadIdx.x; i < r1; i += PT) {
-        double wi = __ldcg(vsrc + i) * vscale;
+        double wi = a.x[i];
         for (int j = 0; j < l; ++j) wi -= __ldg(a.V64 + (int64_t)j * n + i) * coef[j];
-        wnext[i] = wi;
+        a.x[i] = wi;
         nn += wi * wi;
       }
       nn = block_sum(nn, red);
-      if (threadIdx.x == 0) mypart[1 + l] = nn;
+      if (threadIdx.x == 0) mypart[7 + l] = nn;
       if (!grid_barrier(a.bar, a.err)) return;
-      const double tn = reduce_partials(a.part, ps, 1 + l, red);
-      vsrc = wnext;
-      vscale = tn > 0.0 ? 1.0 / sqrt(tn) : 0.0;
-      wnext = (wnext == a.wb0) ? a.wb1 : a.wb0;
+      const double tn = reduce_partials(a.part, ps, 7 + l, red);
+      if (threadIdx.x == 0) s_scal[0] = tn > 0.0 ? 1.0 / sqrt(tn) : 0.0;
+      __syncthreads();
+      const double sc = s_scal[0];
+      __syncthreads();
+      for (int64_t i = r0 + threadIdx.x; i < r1; i += PT) a.x[i] *= sc;
     }
+  } else {
+    for (int64_t i = r0 + threadIdx.x; i < r1; i += PT) a.x[i] = (double)__ldcg(vsrc + i) * vscale;
   }
+  __syncthreads();
 
   // ---- sign convention: largest |v_i| positive, lowest index on ties
-  double sign = 1.0;
   if (a.sign_convention) {
     double best = -1.0;
     int64_t bidx = 0;
     for (int64_t i = r0 + threadIdx.x; i < r1; i += PT) {
-      const double m = fabs(__ldcg(vsrc + i));
+      const double m = fabs(a.x[i]);
       if (m > best) { best = m; bidx = i; }
     }
-    // block arg-max (ties -> lower index)
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
       const double ob = __shfl_xor_sync(0xffffffffu, best, o);
@@ -241,46 +371,47 @@ __global__ void __launch_bounds__(PT, 1) power_dense_kernel(PowerArgs a) {
     if (threadIdx.x == 0) {
       for (int w = 1; w < nwarps; ++w)
         if (sb[w] > best || (sb[w] == best && si[w] < bidx)) { best = sb[w]; bidx = si[w]; }
-      mypart[1 + l] = best;
-      mypart[2 + l] = (double)bidx;
+      mypart[8 + l] = best;
+      mypart[9 + l] = (double)bidx;
     }
     if (!grid_barrier(a.bar, a.err)) return;
     if (threadIdx.x == 0) {
       double gb = -1.0;
       int64_t gi = 0;
       for (int c = 0; c < (int)gridDim.x; ++c) {
-        const double cb = __ldcg(a.part + (int64_t)c * ps + 1 + l);
-        const int64_t ci = (int64_t)__ldcg(a.part + (int64_t)c * ps + 2 + l);
+        const double cb = __ldcg(a.part + (int64_t)c * ps + 8 + l);
+        const int64_t ci = (int64_t)__ldcg(a.part + (int64_t)c * ps + 9 + l);
         if (cb > gb || (cb == gb && ci < gi)) { gb = cb; gi = ci; }
       }
-      s_scal[0] = __ldcg(vsrc + gi) < 0.0 ? -1.0 : 1.0;
+      s_scal[0] = __ldcg(a.x + gi) < 0.0 ? -1.0 : 1.0;
     }
     __syncthreads();
-    sign = s_scal[0];
+    const double sign = s_scal[0];
+    __syncthreads();  // every block reads x[gi] before any block flips its rows
+    if (!grid_barrier(a.bar, a.err)) return;
+    for (int64_t i = r0 + threadIdx.x; i < r1; i += PT) a.x[i] *= sign;
   }
 
-  // ---- write v_l and the Rayleigh quotient v^T G64 v (upper triangle)
-  const double fs = sign * vscale;
-  for (int64_t i = r0 + threadIdx.x; i < r1; i += PT) a.x[i] = __ldcg(vsrc + i) * fs;
+  // ---- Rayleigh quotient sigma^2 = v^T G64 v (upper triangle, FP64), once per triplet
+  if (!grid_barrier(a.bar, a.err)) return;
   double q = 0.0;
   if (status != 2) {
     for (int64_t i = r0 + warp; i < r1; i += nwarps) {
       const double *g = a.G64 + i * n;
       double t = 0.0;
       for (int64_t j = i + lane; j < n; j += 32) {
-        const double gv = __ldg(g + j) * __ldcg(vsrc + j);
+        const double gv = __ldg(g + j) * __ldcg(a.x + j);
         t += (j == i) ? gv : 2.0 * gv;
       }
       t = warp_sum(t);
-      if (lane == 0) q += t * __ldcg(vsrc + i);
+      if (lane == 0) q += t * __ldcg(a.x + i);
     }
-    q *= vscale * vscale;
   }
   q = block_sum(q, red);
-  if (threadIdx.x == 0) mypart[3 + l] = q;
+  if (threadIdx.x == 0) mypart[10 + l] = q;
   if (!grid_barrier(a.bar, a.err)) return;
   if (blockIdx.x == 0) {
-    const double tq = reduce_partials(a.part, ps, 3 + l, red);
+    const double tq = reduce_partials(a.part, ps, 10 + l, red);
     if (threadIdx.x == 0) {
       *a.out_sigma2 = status == 2 ? 0.0 : fmax(tq, 0.0);
       a.info[0] = it;
@@ -375,6 +506,18 @@ __global__ void philox_raw_kernel(const uint32_t *ctr, const uint32_t *key, uint
   }
 }
 
+// G32[i][j] -= sigma2 * v_i * v_j : the Hotelling deflation of the FP32 Gram
+// copy by one extracted triplet (row factor sigma2 * v_i formed in FP64, one
+// FP32 fused multiply-add per entry).  Grid: (n/4 / 64, n) with 64 threads.
+__global__ void deflate_rank1_kernel(int64_t n, float *__restrict__ G32, const double *__restrict__ v,
+                                     const double *__restrict__ sigma2) {
+  const int64_t i = blockIdx.y;
+  const float ci = (float)(__ldg(sigma2) * __ldg(v + i));
+  float *row = G32 + i * n;
+  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x)
+    row[j] = fmaf(-ci, (float)__ldg(v + j), row[j]);
+}
+
 __global__ void sigma_kernel(const double *sig2, double *sigma, int64_t k) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < k) sigma[i] = sqrt(fmax(sig2[i], 0.0));
@@ -388,9 +531,15 @@ __global__ void f64_to_f32_kernel(const double *src, float *dst, int64_t count) 
 
 }  // namespace
 
+// per-block partial layout (doubles): [0] ||x||^2, [1..3] and [4..6] the
+// loop's ||w||^2, v.w, v.v in alternating iterations, [7..7+l) and [7+l] the
+// rank-deficient projection, [8+l], [9+l] the sign search, [10+l] v^T G v;
+// regions written after the loop never overlap ones a slower block may still read
+static int64_t power_part_stride(int64_t l) { return round_up(l + 12, 4); }
+
 size_t power_scratch_bytes(int64_t n, int64_t l) {
-  const size_t ps = (size_t)round_up(l + 8, 4);
-  return 256 + 2 * (size_t)round_up(n, 32) * sizeof(double) + (size_t)kMaxPowerBlocks * ps * sizeof(double);
+  const size_t ps = (size_t)power_part_stride(l);
+  return 256 + 2 * (size_t)round_up(n, 64) * sizeof(float) + (size_t)kMaxPowerBlocks * ps * sizeof(double);
 }
 
 tsvd_status launch_power_dense(int64_t n, const float *G32, const double *G64, const double *V64,
@@ -415,7 +564,7 @@ tsvd_status launch_power_dense(int64_t n, const float *G32, const double *G64, c
   int per_sm = 0;
   TSVD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, power_dense_kernel, PT, smem));
   if (per_sm < 1) return TSVD_EUNSUPPORTED;
-  int64_t grid = std::min<int64_t>({(int64_t)di.sms * per_sm, ceil_div(n, 32), kMaxPowerBlocks});
+  int64_t grid = std::min<int64_t>({(int64_t)di.sms * per_sm, ceil_div(n, 16), kMaxPowerBlocks});
   grid = std::max<int64_t>(grid, 1);
   const int64_t rows_per_block = ceil_div(n, grid);
   grid = ceil_div(n, rows_per_block);
@@ -427,10 +576,10 @@ tsvd_status launch_power_dense(int64_t n, const float *G32, const double *G64, c
   a.sign_convention = sign_convention; a.out_sigma2 = out_sigma2; a.info = info;
   a.bar = reinterpret_cast<unsigned *>(s);
   a.err = reinterpret_cast<int *>(s + 64);
-  a.wb0 = reinterpret_cast<double *>(s + 256);
-  a.wb1 = a.wb0 + round_up(n, 32);
-  a.part = a.wb1 + round_up(n, 32);
-  a.ps = (int)round_up(l + 8, 4);
+  a.wb0 = reinterpret_cast<float *>(s + 256);
+  a.wb1 = a.wb0 + round_up(n, 64);
+  a.part = reinterpret_cast<double *>(a.wb1 + round_up(n, 64));
+  a.ps = (int)power_part_stride(l);
   a.rows_per_block = rows_per_block;
   TSVD_CUDA(cudaMemsetAsync(s, 0, 256, stream));
   void *args[] = {&a};
@@ -476,7 +625,7 @@ tsvd_status launch_philox_raw(const uint32_t *ctr, const uint32_t *key, uint32_t
 // device address (on the host it is only a stand-in for the symbol), so its
 // device address is looked up once per device with cudaGetSymbolAddress.
 constexpr int64_t kNoallocScratchBytes =
-    256 + 2 * TSVD_NOALLOC_MAX_N * 8 + (int64_t)kMaxPowerBlocks * ((TSVD_NOALLOC_MAX_L + 8 + 3) / 4 * 4) * 8;
+    256 + 2 * TSVD_NOALLOC_MAX_N * 4 + (int64_t)kMaxPowerBlocks * ((TSVD_NOALLOC_MAX_L + 12 + 3) / 4 * 4) * 8;
 static __device__ __align__(256) unsigned char g_power_noalloc_scratch[kNoallocScratchBytes];
 
 static tsvd_status noalloc_scratch(void **out) {
@@ -511,6 +660,16 @@ tsvd_status launch_power_dense_noalloc(int64_t n, const float *G32, const double
   if (need > (size_t)kNoallocScratchBytes) return TSVD_EINVAL;
   return launch_power_dense(n, G32, G64, V64, sigma2, l, x, eps, max_iter, iters_override, sign_convention,
                             out_sigma2, info, scratch, (size_t)kNoallocScratchBytes, stream);
+}
+
+tsvd_status launch_gram_deflate(int64_t n, float *G32, const double *v, const double *sigma2, cudaStream_t stream) {
+  if (n <= 0) return TSVD_OK;
+  if (n > 0x7fffffffLL) return TSVD_EINVAL;
+  const unsigned gx = (unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(n, 256), 8));
+  dim3 grid(gx, (unsigned)n);
+  deflate_rank1_kernel<<<grid, 256, 0, stream>>>(n, G32, v, sigma2);
+  TSVD_LAUNCHED();
+  return TSVD_OK;
 }
 
 tsvd_status launch_sigma_from_sigma2(const double *sig2, double *sigma, int64_t k, cudaStream_t stream) {

@@ -35,6 +35,7 @@ __all__ = [
     "csr_from_dense",
     "start_normals",
     "dense_lowrank_blocks_torch",
+    "csr_uniform_torch",
 ]
 
 
@@ -181,20 +182,21 @@ def dense_lowrank_blocks_torch(out_host, m: int, n: int, rank: int, sigma: np.nd
     gen = torch.Generator(device=dev)
     gen.manual_seed(int(seed) * 1000003 + 17)
     Ug = torch.randn((m, rank), generator=gen, device=dev, dtype=torch.float32)
-    for _ in range(2):  # CholeskyQR2: U <- U R^{-1}, twice, FP64 Gram
+    for _ in range(2):  # CholeskyQR2: U <- U R^{-1}, twice, FP64 Gram (small factorisations on the host)
         W = torch.zeros((rank, rank), dtype=torch.float64, device=dev)
         for r0 in range(0, m, block_rows):
             Ub = Ug[r0:r0 + block_rows].double()
             W += Ub.T @ Ub
-        R = torch.linalg.cholesky(W).T  # upper
-        Rinv = torch.linalg.inv(R)
+        R = np.linalg.cholesky(W.cpu().numpy()).T  # upper
+        Rinv = torch.as_tensor(np.linalg.inv(R), device=dev)
         for r0 in range(0, m, block_rows):
             Ug[r0:r0 + block_rows] = (Ug[r0:r0 + block_rows].double() @ Rinv).float()
     gv = torch.Generator(device=dev)
     gv.manual_seed(int(seed) * 1000003 + 29)
-    Vg = torch.randn((n, rank), generator=gv, device=dev, dtype=torch.float64)
-    Vq, Vr = torch.linalg.qr(Vg)
-    Vq = Vq * torch.sign(torch.diagonal(Vr))[None, :]
+    Vg = torch.randn((n, rank), generator=gv, device=dev, dtype=torch.float64).cpu().numpy()
+    Vq_np, Vr_np = np.linalg.qr(Vg)
+    Vq_np = Vq_np * np.sign(np.diag(Vr_np))[None, :]
+    Vq = torch.as_tensor(Vq_np, device=dev)
     sig = torch.as_tensor(np.asarray(sigma, dtype=np.float64), device=dev)
     SVt = (sig[:, None] * Vq.T).float()  # r x n
     gn = torch.Generator(device=dev)
@@ -207,5 +209,39 @@ def dense_lowrank_blocks_torch(out_host, m: int, n: int, rank: int, sigma: np.nd
         b.mul_(noise)
         b.addmm_(Ug[r0:r1], SVt)
         out_host[r0:r1].copy_(b, non_blocking=False)
-    torch.cuda.synchronize(dev)
-    return {"V": Vq.cpu().numpy(), "sigma": np.asarray(sigma, dtype=np.float64)}
+    if dev.type == "cuda":
+        torch.cuda.synchronize(dev)
+    return {"V": Vq_np, "sigma": np.asarray(sigma, dtype=np.float64)}
+
+
+def csr_uniform_torch(m: int, n: int, nnz_per_row: float, seed: int, device="cuda"):
+    """CSR matrix like csr_uniform, drawn on the GPU with torch (for sizes
+    where the NumPy generator is too slow): per-row nnz ~ Poisson(nnz_per_row),
+    columns uniform without replacement and sorted (rows that drew a repeated
+    column redraw it until none repeat), values U(0,1) FP32.  Returns torch
+    tensors on `device` (row_ptr int64, col_idx int32, values float32)."""
+    import torch
+    dev = torch.device(device)
+    g = torch.Generator(device=dev)
+    g.manual_seed(int(seed) * 7919 + 3)
+    rate = torch.full((m,), float(nnz_per_row), dtype=torch.float32, device=dev)
+    counts = torch.poisson(rate, generator=g).to(torch.int64).clamp_(max=n)
+    row_ptr = torch.zeros(m + 1, dtype=torch.int64, device=dev)
+    torch.cumsum(counts, 0, out=row_ptr[1:])
+    nnz = int(row_ptr[-1].item())
+    rows = torch.repeat_interleave(torch.arange(m, device=dev, dtype=torch.int64), counts)
+    cols = torch.randint(0, n, (nnz,), generator=g, device=dev, dtype=torch.int64)
+    for _ in range(64):
+        key = rows * n + cols
+        key, _ = torch.sort(key)
+        cols = key - rows * n  # rows is already non-decreasing, so it stays aligned
+        dup = torch.zeros(nnz, dtype=torch.bool, device=dev)
+        if nnz > 1:
+            dup[1:] = key[1:] == key[:-1]
+        nd = int(dup.sum().item())
+        if nd == 0:
+            break
+        cols[dup] = torch.randint(0, n, (nd,), generator=g, device=dev, dtype=torch.int64)
+        del key
+    vals = torch.rand(nnz, generator=g, device=dev, dtype=torch.float32)
+    return {"row_ptr": row_ptr, "col_idx": cols.to(torch.int32), "values": vals, "m": m, "n": n}

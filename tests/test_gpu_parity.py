@@ -136,6 +136,12 @@ def test_power_dense_follows_oracle(l):
     dG64, dG32 = dev(Gf), dev(Gf.astype(np.float32))
     dV = dev(np.asfortranarray(V).T.copy()) if l else None  # column-major n x l == row-major l x n
     ds2 = dev(s2) if l else None
+    for j in range(l):  # Hotelling deflation of the FP32 copy, one triplet at a time
+        assert B.tsvd_gram_deflate(n, dG32.data_ptr(), dV[j].data_ptr(), ds2[j:].data_ptr(), S()) == 0
+    if l:
+        want = (Gf - V @ np.diag(s2) @ V.T).astype(np.float32)
+        got32 = dG32.cpu().numpy()
+        assert np.max(np.abs(got32 - want)) <= 4 * 2.0 ** -24 * np.max(np.abs(Gf))
     scratch_b = B.tsvd_power_scratch_bytes(n, l)
     scr = torch.empty(scratch_b, dtype=torch.uint8, device="cuda")
     info = torch.zeros(4, dtype=torch.int32, device="cuda")
@@ -442,8 +448,9 @@ def test_tsvd_tf32x3_c1_matches_oracle():
     _compare(r, o, k)
 
 
-@pytest.mark.parametrize("prec", [B.TSVD_GRAM_TF32, B.TSVD_GRAM_TF32X3])
-def test_tsvd_tensor_cores_c2_shape(prec):
+@pytest.mark.parametrize("prec,budget", [(B.TSVD_GRAM_TF32, 0), (B.TSVD_GRAM_TF32X3, 0),
+                                         (B.TSVD_GRAM_TF32, 256 << 20)])
+def test_tsvd_tensor_cores_c2_shape(prec, budget):
     # the out-of-core workload's structure at a size the oracle handles:
     # rank-64, sigma_i = 1/(1+i), 1e-4 noise; streamed in row blocks
     m, n, k, eps = 1 << 17, 512, 8, 1e-6
@@ -455,7 +462,10 @@ def test_tsvd_tensor_cores_c2_shape(prec):
     o = ref.tsvd_dense(A, k, eps, x_start=x, B=Gf)
     lam = np.linalg.eigvalsh(Gf)[::-1]
     gapped = ref.gapped_indices(lam, k)
+    # under a budget the ring takes every slot that fits and the U pass
+    # starts from the row blocks still resident after the Gram pass
     r = tsvd(A, k, eps, start_draws=x, iters_override=o.iters, precision=prec, force_stream=True,
-             block_rows=1 << 15)
-    assert r.report["n_blocks"] == 4
+             block_rows=(1 << 14) if budget else (1 << 15), device_budget=budget)
+    assert r.report["n_blocks"] == (8 if budget else 4)
+    assert r.report["ring_slots"] == (6 if budget else 3)
     _compare(r, o, k, gapped=gapped)
