@@ -175,17 +175,22 @@ def measure_h2d_peak(A: np.ndarray):
         e1.record()
         torch.cuda.synchronize()
         best = max(best, rows * A.shape[1] * 4 / (e0.elapsed_time(e1) / 1e3) / 1e9)
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    evs = []
     torch.cuda.synchronize()
-    e0.record()
     total = 0
     for i, r0 in enumerate(range(0, A.shape[0], rows)):
         blk = torch.from_numpy(A[r0:r0 + rows])
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
         dst[i & 1][:blk.shape[0]].copy_(blk, non_blocking=True)
+        b.record()
+        evs.append((a, b, blk.numel() * 4))
         total += blk.numel() * 4
-    e1.record()
     torch.cuda.synchronize()
-    sustained = total / (e0.elapsed_time(e1) / 1e3) / 1e9
+    sustained = total / (evs[0][0].elapsed_time(evs[-1][1]) / 1e3) / 1e9
+    per = sorted(nb / (x.elapsed_time(y) / 1e3) / 1e9 for x, y, nb in evs)
+    measure_h2d_peak.per_block = {"min": round(per[0], 1), "median": round(per[len(per) // 2], 1),
+                                  "max": round(per[-1], 1)}
     del dst
     return best, sustained
 
@@ -450,6 +455,67 @@ def kernel_case(args):
     print(json.dumps(out), flush=True)
 
 
+def csr_workload(args):
+    """Sparse out-of-core t-SVD: m = n = 2^25 (default), ~33.5 entries per row
+    at uniform random positions, U(0,1) values, row blocks of 2^20 rows under a
+    4 GB device budget, k = 16.  A-stream throughput = CSR bytes consumed per
+    step (every operator application, the sigma passes and the U pass read the
+    whole matrix) / step seconds.  The number of applications per triplet is
+    fixed with --csr-iters (the paper's out-of-memory runs fix it at 100) to
+    bound the run time."""
+    import torch
+
+    import synth
+    from paper_2208_08410_gb300 import Plan, _binding as B
+    B.load(build_if_missing=True)
+    torch.cuda.set_device(0)
+    m = args.m or (1 << 25)
+    k = K
+    t0 = time.time()
+    dcsr = synth.csr_uniform_torch(m, m, 33.5, seed=1)
+    nnz = int(dcsr["values"].shape[0])
+    csr_bytes = 8 * (m + 1) + 8 * nnz
+    # pinned host copy for the streamed run
+    hrp = pinned_array((m + 1,), np.float64).view(np.int64)
+    hvals = pinned_array((nnz,), np.float32)
+    hci = pinned_array((nnz,), np.float32).view(np.int32)
+    hrp[:] = dcsr["row_ptr"].cpu().numpy()
+    hci[:] = dcsr["col_idx"].cpu().numpy()
+    hvals[:] = dcsr["values"].cpu().numpy()
+    host = {"row_ptr": hrp, "col_idx": hci, "values": hvals, "m": m, "n": m}
+    gen_s = time.time() - t0
+    iters = [args.csr_iters] * k
+    plan_d = Plan(dcsr, k, EPS, out_device=True, iters_override=iters)
+    sec, wall, reps, res = time_steps(plan_d, dcsr, args.steps, args.warmup)
+    apps = reps[-1]["applications"]
+    passes = apps + k + 1  # applications, one sigma pass per triplet, the U pass
+    value = csr_bytes * passes * args.steps / sec / 1e9
+    plan_d.close()
+    del plan_d
+    torch.cuda.empty_cache()
+    plan_h = Plan(host, k, EPS, iters_override=iters, device_budget=4 * 10 ** 9, block_rows=1 << 20,
+                  force_stream=True, time_kernels=True)
+    sec_e, wall_e, reps_e, res_e = time_steps(plan_h, host, max(1, args.e2e_steps or args.steps), args.warmup)
+    nst = max(1, args.e2e_steps or args.steps)
+    e2e = csr_bytes * passes * nst / sec_e / 1e9
+    line = {"metric": "t-SVD A-stream throughput (CSR)", "value": round(value, 2), "unit": "GB/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(sec / args.steps * 1e3, 1),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"sparse CSR t-SVD, m=n={m}, ~33.5 nnz/row ({nnz} nnz), k={k}, "
+                                   f"{args.csr_iters} applications per triplet", "m": m, "nnz": nnz,
+                       "csr_bytes": csr_bytes, "k": k, "block_rows_e2e": 1 << 20,
+                       "device_budget_bytes_e2e": 4 * 10 ** 9},
+            "e2e": {"value": round(e2e, 2), "unit": "GB/s", "ms_per_step": round(sec_e / nst * 1e3, 1),
+                    "h2d_bytes_per_step": int(reps_e[-1]["h2d_bytes"]),
+                    "d2h_bytes_per_step": int(reps_e[-1]["d2h_bytes"]),
+                    "blocks_per_pass": reps_e[-1]["n_blocks"],
+                    "copy_stream_GBps": round(reps_e[-1]["h2d_bytes"] / (reps_e[-1]["h2d_copy_ms"] / 1e3) / 1e9, 2)
+                    if reps_e[-1]["h2d_copy_ms"] else None},
+            "sigma": [round(float(x), 6) for x in res.sigma.cpu().numpy()], "gen_seconds": round(gen_s, 1),
+            "gpu_launches": int(sum(r["kernel_launches"] for r in reps))}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -465,9 +531,14 @@ def main():
     ap.add_argument("--case", default="", choices=["", "gram", "power", "csr", "left"],
                     help="single-kernel microbenchmark instead of the t-SVD step")
     ap.add_argument("--n", type=int, default=N_COLS)
+    ap.add_argument("--workload", default="dense", choices=["dense", "csr"])
+    ap.add_argument("--csr-iters", type=int, default=10)
     args = ap.parse_args()
     if args.case:
         kernel_case(args)
+        return
+    if args.workload == "csr" and args.impl != "reference":
+        csr_workload(args)
         return
 
     rank = int(os.environ.get("RANK", "0"))
@@ -542,7 +613,8 @@ def main():
 
     # ---------------- e2e: pinned host A, streamed, outputs to host
     e2e_steps = args.e2e_steps or args.steps
-    plan_host = Plan(A, K, EPS, precision=prec, device_budget=BUDGET, block_rows=BLOCK_ROWS, force_stream=True)
+    plan_host = Plan(A, K, EPS, precision=prec, device_budget=BUDGET, block_rows=BLOCK_ROWS, force_stream=True,
+                     time_kernels=True)
     outs = {"U": pinned_array((K, m), np.float32), "sigma": pinned_array((K,), np.float64),
             "V": pinned_array((K, N_COLS), np.float32)}
     sec_e, wall_e, reps_e, res_host = time_steps(plan_host, A, e2e_steps, args.warmup, outs=outs)
@@ -559,9 +631,13 @@ def main():
            "h2d": {"gram_pass_GBps": round(m * N_COLS * 4 / gram_pass_s / 1e9, 2),
                    "pinned_copy_peak_GBps": round(h2d_peak, 2),
                    "pinned_copy_burst_GBps": round(h2d_burst, 2),
+                   "pinned_copy_per_block_GBps": getattr(measure_h2d_peak, "per_block", None),
                    "peak_note": "peak = sustained pinned copy of every row block of A back to back",
                    "frac_gram_pass": round(m * N_COLS * 4 / gram_pass_s / 1e9 / h2d_peak, 4),
-                   "blocks_per_pass": reps_e[-1]["n_blocks"]}}
+                   "blocks_per_pass": reps_e[-1]["n_blocks"], "ring_slots": reps_e[-1]["ring_slots"],
+                   "block_copies_per_step": reps_e[-1]["h2d_copies"],
+                   "copy_stream_GBps": round(reps_e[-1]["h2d_bytes"] / (reps_e[-1]["h2d_copy_ms"] / 1e3) / 1e9, 2)
+                   if reps_e[-1]["h2d_copy_ms"] else None}}
     launches_e = int(sum(r["kernel_launches"] for r in reps_e))
     plan_host.close()
 

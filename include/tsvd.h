@@ -101,8 +101,9 @@ typedef struct {
   uint64_t seed;                 /* seed of the built-in start-vector stream */
   int32_t out_location;          /* tsvd_location of the U, sigma, V outputs */
   int32_t force_stream;          /* 1: stream host A even when it would fit */
-  int32_t time_kernels;          /* 1: time each Gram kernel launch with CUDA events
-                                    on the compute stream (report.gram_kernel_ms) */
+  int32_t time_kernels;          /* 1: time each Gram kernel launch (compute stream)
+                                    and each block copy (copy stream) with CUDA events
+                                    (report.gram_kernel_ms, report.h2d_copy_ms) */
   int32_t reserved[5];
 } tsvd_options;
 
@@ -124,8 +125,9 @@ typedef struct {
   int64_t kernel_launches;  /* kernels launched by this call */
   int64_t applications;     /* total operator applications (sum of iters) */
   int32_t ring_slots;       /* row blocks the streaming ring holds (mode 2) */
-  int32_t reserved2;
-  double reserved1[3];
+  int32_t h2d_copies;       /* host -> device block copies timed (time_kernels) */
+  double h2d_copy_ms;       /* summed duration of those copies on the copy stream */
+  double reserved1[2];
 } tsvd_report;
 
 #define TSVD_FLAG_NOCONV 1        /* a triplet hit max_iter */

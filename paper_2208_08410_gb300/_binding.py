@@ -41,8 +41,8 @@ class tsvd_report(C.Structure):
                 ("gram_kernel_launches", C.c_int32), ("gram_ms", C.c_double), ("power_ms", C.c_double),
                 ("left_ms", C.c_double), ("total_ms", C.c_double), ("h2d_bytes", C.c_double),
                 ("d2h_bytes", C.c_double), ("gram_kernel_ms", C.c_double), ("kernel_launches", C.c_int64),
-                ("applications", C.c_int64), ("ring_slots", C.c_int32), ("reserved2", C.c_int32),
-                ("reserved1", C.c_double * 3)]
+                ("applications", C.c_int64), ("ring_slots", C.c_int32), ("h2d_copies", C.c_int32),
+                ("h2d_copy_ms", C.c_double), ("reserved1", C.c_double * 2)]
 
 
 _P = C.c_void_p

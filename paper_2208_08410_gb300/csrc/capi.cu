@@ -98,6 +98,7 @@ struct tsvd_plan_s {
   cudaEvent_t ev_u_ready[2] = {nullptr, nullptr}, ev_u_free[2] = {nullptr, nullptr};
   cudaEvent_t ev_t[4] = {nullptr, nullptr, nullptr, nullptr};
   std::vector<cudaEvent_t> ev_k;  // pairs around each timed Gram kernel
+  std::vector<cudaEvent_t> ev_c;  // pairs around each timed block copy
 };
 
 namespace {
@@ -373,6 +374,7 @@ void tsvd_destroy(tsvd_plan_t p) {
     for (auto e : p->ev_t)
       if (e) cudaEventDestroy(e);
     for (auto e : p->ev_k) cudaEventDestroy(e);
+    for (auto e : p->ev_c) cudaEventDestroy(e);
     if (p->copy_stream) cudaStreamDestroy(p->copy_stream);
     if (p->d2h_stream) cudaStreamDestroy(p->d2h_stream);
     if (cur != p->device) cudaSetDevice(cur);
@@ -414,7 +416,33 @@ struct Run {
   cudaStream_t cs;
   double h2d = 0.0, d2h = 0.0;
   int64_t chunk_seq = 0;  // ring position, continues across passes
+  int64_t copies = 0;     // timed block copies recorded so far
 };
+
+// Events around a block copy on the copy stream (only with time_kernels).
+tsvd_status copy_event(Run &r, bool start) {
+  tsvd_plan_s *p = r.p;
+  if (!p->opt.time_kernels) return TSVD_OK;
+  const size_t idx = (size_t)(2 * r.copies + (start ? 0 : 1));
+  while (p->ev_c.size() <= idx) {
+    cudaEvent_t e;
+    TSVD_CUDA(cudaEventCreate(&e));
+    p->ev_c.push_back(e);
+  }
+  TSVD_CUDA(cudaEventRecord(p->ev_c[idx], p->copy_stream));
+  if (!start) ++r.copies;
+  return TSVD_OK;
+}
+
+tsvd_status copy_time_ms(Run &r, double *ms) {
+  *ms = 0.0;
+  for (int64_t c = 0; c < r.copies; ++c) {
+    float t = 0.f;
+    TSVD_CUDA(cudaEventElapsedTime(&t, r.p->ev_c[2 * c], r.p->ev_c[2 * c + 1]));
+    *ms += t;
+  }
+  return TSVD_OK;
+}
 
 // Bring dense rows [r0, r0+rows) to the device; returns the pointer/stride to
 // use on the compute stream.  The slot is released by release_dense().
@@ -443,12 +471,14 @@ tsvd_status acquire_dense(Run &r, int64_t r0, int64_t rows, const float **out, i
     *ldo = p->n;
   }
   const float *src = A->values + r0 * A->ld;
+  TSVD_TRY(copy_event(r, true));
   if (A->ld == p->n) {
     TSVD_CUDA(cudaMemcpyAsync(dst, src, (size_t)rows * p->n * 4, cudaMemcpyHostToDevice, p->copy_stream));
   } else {
     TSVD_CUDA(cudaMemcpy2DAsync(dst, (size_t)p->n * 4, src, (size_t)A->ld * 4, (size_t)p->n * 4, (size_t)rows,
                                 cudaMemcpyHostToDevice, p->copy_stream));
   }
+  TSVD_TRY(copy_event(r, false));
   r.h2d += (double)rows * p->n * 4;
   const int ev = *slot >= 0 ? *slot : 0;
   TSVD_CUDA(cudaEventRecord(p->ev_ready[ev], p->copy_stream));
@@ -906,6 +936,13 @@ tsvd_status tsvd_factor(tsvd_plan_t plan, const tsvd_matrix *A, void *workspace,
     report->h2d_bytes = r.h2d;
     report->d2h_bytes = r.d2h;
     report->kernel_launches = launches_so_far() - l0;
+    if (st == TSVD_OK || st == TSVD_ENOCONV || st == TSVD_ERANK) {
+      double ms = 0.0;
+      if (copy_time_ms(r, &ms) == TSVD_OK) {
+        report->h2d_copy_ms = ms;
+        report->h2d_copies = (int32_t)r.copies;
+      }
+    }
   }
   return st;
 }
