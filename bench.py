@@ -42,7 +42,7 @@ EPS = 1e-6
 NOISE = 1e-4
 FULL_M = 13_107_200
 BUDGET = 32 * 10 ** 9
-PREC_NAMES = {0: "f32", 1: "tf32", 2: "tf32x3"}
+PREC_NAMES = {0: "f32", 1: "tf32", 2: "tf32x3", 3: "bf16x3"}
 
 
 def mem_available_bytes() -> int:
@@ -399,6 +399,7 @@ def kernel_case(args):
         fl = m * n * (n + 1)
         out.update({"m": m, "n": n, "precision": PREC_NAMES[args.precision], "ms": round(t * 1e3, 3),
                     "tflops_algorithmic": round(fl / t / 1e12, 2),
+                    "frac_of_dtype_peak_burst": round(fl / t / 1e12 / dtype_peak(args.precision, peaks, False)[0], 4),
                     "note": "time covers prep (transpose/round) + SYRK for tensor precisions"})
     elif args.case == "power":
         n = args.n
@@ -455,6 +456,230 @@ def kernel_case(args):
     print(json.dumps(out), flush=True)
 
 
+def tf32_in_core(dA, args, m, res_ref, peaks):
+    """The same in-core step with the Gram in plain TF32 (one MMA per product;
+    reduced precision, reported beside the FP32-class headline, never as it):
+    throughput, SYRK fraction of the TF32 peak and the largest relative change
+    of sigma against the 3xTF32 run."""
+    import torch
+
+    from paper_2208_08410_gb300 import Plan
+    plan = Plan(dA, K, EPS, precision=1, out_device=True, time_kernels=True)
+    sec, wall, reps, res = time_steps(plan, dA, args.steps, args.warmup)
+    plan.close()
+    gk_ms = sum(r["gram_kernel_ms"] for r in reps)
+    tf = m * N_COLS * (N_COLS + 1) * args.steps / (gk_ms / 1e3) / 1e12
+    peak, _ = dtype_peak(1, peaks, sustained=True)
+    s1 = np.asarray(res.sigma.cpu(), dtype=np.float64)
+    s0 = np.asarray(res_ref.sigma.cpu(), dtype=np.float64)
+    return {"value": round(2 * m * N_COLS * 4 * args.steps / sec / 1e9, 3), "unit": "GB/s",
+            "ms_per_step": round(sec / args.steps * 1e3, 2), "syrk_tflops": round(tf, 1),
+            "syrk_frac_of_tf32_peak": round(tf / peak, 4),
+            "sigma_max_rel_diff_vs_tf32x3": float("%.3g" % np.max(np.abs(s1 - s0) / s0))}
+
+
+PEAK_NOTES = {
+    0: "152 SMs x 128 FP32 lanes x 2 flop x max SM clock",
+    1: "TF32 = bf16 {src} {kind} x 1.1/2.25 nominal ratio",
+    2: "3xTF32 = TF32 peak / 3 (three TF32 MMAs per product); TF32 = bf16 {src} {kind} x 1.1/2.25",
+    3: "BF16x3 = bf16 {src} {kind} / 3 (three BF16 MMAs per product)",
+}
+
+
+def c1_latency(reps: int = 50):
+    """In-core tiny case (m = 2048, n = 256, sigma_i = 0.8^i plus 1e-6 noise,
+    k = 8, eps = 1e-8, plain FP32 Gram): latency-bound (G is 256 KB), so the
+    figures are the device time of one whole t-SVD call (CUDA events on the
+    launching stream, median of `reps`), the time per power application and
+    the kernel launches per call."""
+    import torch
+
+    import synth
+    from paper_2208_08410_gb300 import Plan
+    inp = synth.dense_prescribed(2048, 256, synth.spectrum_geometric(256, 0.8), 1e-6, seed=0)
+    dA = torch.from_numpy(inp["A"]).cuda()
+    plan = Plan(dA, 8, 1e-8, precision=0, out_device=True, time_kernels=True)
+    for _ in range(5):
+        plan.factor(dA)
+    torch.cuda.synchronize()
+    times, reps_out = [], []
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        r = plan.factor(dA)
+        e1.record()
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+        reps_out.append(r.report)
+    plan.close()
+    t = float(np.median(times))
+    rep = reps_out[-1]
+    return {"workload": "m=2048, n=256, sigma_i=0.8^i + 1e-6 noise, k=8, eps=1e-8, FP32 Gram, A in HBM",
+            "ms_per_tsvd": round(t, 4), "ms_min": round(float(np.min(times)), 4),
+            "us_per_power_application": round(rep["power_ms"] * 1e3 / max(rep["applications"], 1), 3),
+            "applications": rep["applications"], "kernel_launches_per_tsvd": rep["kernel_launches"],
+            "phases_ms": {"gram": round(rep["gram_ms"], 4), "power": round(rep["power_ms"], 4),
+                          "left": round(rep["left_ms"], 4)}}
+
+
+def dtype_peak(prec: int, peaks: dict, sustained: bool = True):
+    """Roofline denominator of the Gram arithmetic in TFLOP/s (algorithmic
+    flops: a split mode's three MMAs per product count once).  Kernels timed
+    inside a long step take the sustained bf16 figure, kernels timed alone
+    the burst one."""
+    bf = peaks["bf16_tflops_sustained"] if sustained else peaks["bf16_tflops"]
+    if prec == 0:
+        return 152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12, "alu"
+    if prec == 1:
+        return bf * (1.1 / 2.25), "tensor"
+    if prec == 2:
+        return bf * (1.1 / 2.25) / 3, "tensor"
+    return bf / 3, "tensor"
+
+
+def c4_workload(args):
+    """Mixed-precision Gram on a clustered spectrum: m = 2^20, n = 8192,
+    sigma_i = 1/(1+i) with sigma_11 = sigma_10 - 1e-3, k = 32, eps = 1e-8, A
+    resident in HBM (32 GiB), stacked-orthogonal construction (its singular
+    values are the prescribed sigma to ~1e-8).  Every Gram precision runs the
+    same t-SVD; the line reports seconds per t-SVD, the Gram kernel against
+    its dtype's peak and the sigma error against the closed form."""
+    import torch
+
+    import synth
+    from paper_2208_08410_gb300 import Plan, _binding as B
+    B.load(build_if_missing=True)
+    torch.cuda.set_device(0)
+    n, copies, k, eps = 8192, 128, 32, 1e-8
+    m = n * copies
+    t0 = time.time()
+    sig_t = synth.spectrum_harmonic_clustered(n, 10, 1e-3)
+    fac = synth.stacked_factor(n, sig_t, copies, seed=0)
+    dA = torch.empty((m, n), dtype=torch.float32, device="cuda")
+    synth.stacked_rows_torch(dA, fac["M32"], seed=0)
+    torch.cuda.synchronize()
+    gen_s = time.time() - t0
+    peaks, peak_src = load_peaks()
+    flops = m * n * (n + 1)
+    rows = {}
+    for prec in (0, 1, 2, 3):
+        plan = Plan(dA, k, eps, precision=prec, out_device=True, time_kernels=True)
+        sec, wall, reps, res = time_steps(plan, dA, args.steps, args.warmup, want_u=True)
+        plan.close()
+        sig = np.asarray(res.sigma.cpu(), dtype=np.float64)
+        err = float(np.max(np.abs(sig - sig_t[:k]) / sig_t[:k]))
+        gk = sum(r["gram_kernel_ms"] for r in reps) / 1e3
+        tf = flops * args.steps / gk / 1e12 if gk > 0 else None
+        pk, bound = dtype_peak(prec, peaks, sustained=True)
+        rows[PREC_NAMES[prec]] = {
+            "seconds_per_tsvd": round(sec / args.steps, 4), "sigma_max_rel_err_vs_truth": float("%.3g" % err),
+            "gram_tflops": round(tf, 1) if tf else None, "gram_peak_tflops": round(pk, 1), "bound": bound,
+            "gram_frac_of_dtype_peak": round(tf / pk, 4) if tf else None,
+            "phases_ms": {"gram": round(reps[-1]["gram_ms"], 1), "power": round(reps[-1]["power_ms"], 1),
+                          "left": round(reps[-1]["left_ms"], 1)},
+            "applications": reps[-1]["applications"], "gpu_launches": int(sum(r["kernel_launches"] for r in reps))}
+        torch.cuda.empty_cache()
+    ok = {p: r for p, r in rows.items() if r["sigma_max_rel_err_vs_truth"] <= 1e-5}
+    best = min(ok, key=lambda p: ok[p]["seconds_per_tsvd"]) if ok else None
+    fp32 = rows["f32"]["seconds_per_tsvd"]
+    line = {"metric": "t-SVD seconds, mixed-precision Gram at sigma err <= 1e-5 (clustered spectrum)",
+            "value": ok[best]["seconds_per_tsvd"] if best else None, "unit": "s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": best, "data": "synthetic",
+            "config": {"workload": f"dense in-core t-SVD, stacked-orthogonal A, m={m}, n={n}, sigma_i=1/(1+i), "
+                                   f"sigma_11=sigma_10-1e-3, k={k}, eps={eps}", "m": m, "n": n, "k": k, "eps": eps,
+                       "l2": "inputs larger than L2 (A is 32 GiB)"},
+            "speedup_vs_f32": round(fp32 / ok[best]["seconds_per_tsvd"], 3) if best else None,
+            "precisions": rows, "gen_seconds": round(gen_s, 1), "peak_source": peak_src}
+    print(json.dumps(line), flush=True)
+
+
+def csr_pair_checks(dcsr, host, m, nnz, peaks, peak_src, args):
+    """Full-size measurements of the fused CSR pair (one operator application
+    w = A^T (A v), ||A v||^2) on the device-resident matrix:
+    - roofline: average duration of tsvd_csr_gram_apply over the whole matrix
+      (CUDA events on the launching stream) against HBM with the algorithmic
+      bytes 8 nnz + 8 (m+1) + 4n (v) + 8n (w read + written);
+    - cpu_baseline: the oracle's time for sampled row blocks, scaled to one
+      application of the whole matrix."""
+    import torch
+
+    from paper_2208_08410_gb300 import _binding as B
+    stream = torch.cuda.current_stream().cuda_stream
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(7)
+    v = torch.rand(m, generator=gen, device="cuda", dtype=torch.float32)
+    w = torch.zeros(m, dtype=torch.float32, device="cuda")
+    ss = torch.zeros(1, dtype=torch.float64, device="cuda")
+    rp, ci, va = dcsr["row_ptr"], dcsr["col_idx"], dcsr["values"]
+
+    def apply_all():
+        B.check(B.tsvd_csr_gram_apply(m, m, rp.data_ptr(), ci.data_ptr(), va.data_ptr(), v.data_ptr(),
+                                      w.data_ptr(), ss.data_ptr(), 1, stream), "tsvd_csr_gram_apply")
+    for _ in range(3):
+        apply_all()
+    reps = 10
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        apply_all()
+    e1.record()
+    torch.cuda.synchronize()
+    t = e0.elapsed_time(e1) / 1e3 / reps
+    alg = 8 * nnz + 8 * (m + 1) + 4 * m + 8 * m
+    roofline = {"bound": "hbm", "achieved": round(alg / t / 1e9, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": round(alg / t / 1e9 / peaks["hbm_gbs"], 4),
+                "traffic": measured_traffic("csr_pair_kernel", m, m), "kernel": "csr_pair_kernel (fused CSR pair)",
+                "ms_per_application": round(t * 1e3, 3), "algorithmic_bytes": alg,
+                "peak_source": f"{peak_src} copy bandwidth"}
+    cpu = None
+    if not args.no_cpu:
+        from oracle.csr_c import csr_gram_apply as oracle_apply
+        vh = v.cpu().numpy().astype(np.float64)
+        bl = 1 << 20
+        t0 = time.time()
+        rows_done = 0
+        sample = []
+        for b in range(0, m, bl * 8):
+            oracle_apply(host["row_ptr"], host["col_idx"], host["values"], vh, r0=b, r1=min(m, b + bl))
+            rows_done += min(m, b + bl) - b
+            sample.append(b)
+            if time.time() - t0 > 15.0:
+                break
+        sec = (time.time() - t0) * m / rows_done
+        cpu = {"value": round(alg / sec / 1e9, 4), "unit": "GB/s", "cores": 1, "kind": "oracle",
+               "sample": f"oracle FP64 C operator on {len(sample)} row blocks of {bl} rows "
+                         f"({rows_done} of {m} rows), scaled to one application",
+               "seconds_per_application": round(sec, 2)}
+    return roofline, cpu
+
+
+def csr_oom_sweep(host, m, nnz, args):
+    """Single-GPU analogue of the paper's out-of-memory sweep (Sec. VI-B,
+    Fig. 4): the streamed CSR t-SVD timed over the number of row blocks n_b
+    (block rows 2^19 .. 2^21) and the ring depth q_s (2 .. 4 buffers), with the
+    device footprint of each plan.  k = 4 and 3 applications per triplet keep
+    the sweep short; every point reads the whole matrix 4*3 + 4 + 1 times."""
+    import torch
+
+    from paper_2208_08410_gb300 import Plan
+    k, iters = 4, 3
+    out = []
+    for br in (1 << 19, 1 << 20, 1 << 21):
+        for nb in (2, 3, 4):
+            plan = Plan(host, k, EPS, iters_override=[iters] * k, block_rows=br, n_buffers=nb,
+                        device_budget=16 * 10 ** 9, force_stream=True, time_kernels=True)
+            sec, wall, reps, res = time_steps(plan, host, 2, 1)
+            r = reps[-1]
+            out.append({"block_rows": br, "n_blocks": r["n_blocks"], "n_buffers": nb,
+                        "workspace_bytes": plan.workspace_bytes, "seconds_per_tsvd": round(sec / 2, 3),
+                        "h2d_GBps": round(r["h2d_bytes"] / (sec / 2) / 1e9, 1)})
+            plan.close()
+            torch.cuda.empty_cache()
+    return {"k": k, "applications_per_triplet": iters, "points": out}
+
+
 def csr_workload(args):
     """Sparse out-of-core t-SVD: m = n = 2^25 (default), ~33.5 entries per row
     at uniform random positions, U(0,1) values, row blocks of 2^20 rows under a
@@ -485,6 +710,8 @@ def csr_workload(args):
     host = {"row_ptr": hrp, "col_idx": hci, "values": hvals, "m": m, "n": m}
     gen_s = time.time() - t0
     iters = [args.csr_iters] * k
+    peaks, peak_src = load_peaks()
+    roofline, cpu = csr_pair_checks(dcsr, host, m, nnz, peaks, peak_src, args)
     plan_d = Plan(dcsr, k, EPS, out_device=True, iters_override=iters)
     sec, wall, reps, res = time_steps(plan_d, dcsr, args.steps, args.warmup)
     apps = reps[-1]["applications"]
@@ -498,6 +725,8 @@ def csr_workload(args):
     sec_e, wall_e, reps_e, res_e = time_steps(plan_h, host, max(1, args.e2e_steps or args.steps), args.warmup)
     nst = max(1, args.e2e_steps or args.steps)
     e2e = csr_bytes * passes * nst / sec_e / 1e9
+    plan_h.close()
+    sweep = csr_oom_sweep(host, m, nnz, args) if args.sweep else None
     line = {"metric": "t-SVD A-stream throughput (CSR)", "value": round(value, 2), "unit": "GB/s", "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(sec / args.steps * 1e3, 1),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
@@ -511,6 +740,7 @@ def csr_workload(args):
                     "blocks_per_pass": reps_e[-1]["n_blocks"],
                     "copy_stream_GBps": round(reps_e[-1]["h2d_bytes"] / (reps_e[-1]["h2d_copy_ms"] / 1e3) / 1e9, 2)
                     if reps_e[-1]["h2d_copy_ms"] else None},
+            "roofline": roofline, "cpu_baseline": cpu, "oom_sweep": sweep,
             "sigma": [round(float(x), 6) for x in res.sigma.cpu().numpy()], "gen_seconds": round(gen_s, 1),
             "gpu_launches": int(sum(r["kernel_launches"] for r in reps))}
     print(json.dumps(line), flush=True)
@@ -523,7 +753,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--m", type=int, default=0, help="rows (default: largest multiple of 262,144 that fits)")
-    ap.add_argument("--precision", type=int, default=0, help="0 FP32, 1 TF32, 2 TF32x3")
+    ap.add_argument("--precision", type=int, default=2,
+                    help="Gram arithmetic: 0 FP32 CUDA cores, 1 TF32, 2 3xTF32 (FP32-class, default), 3 BF16x3")
     ap.add_argument("--ref-rows", type=int, default=65_536)
     ap.add_argument("--no-parity", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
@@ -531,14 +762,18 @@ def main():
     ap.add_argument("--case", default="", choices=["", "gram", "power", "csr", "left"],
                     help="single-kernel microbenchmark instead of the t-SVD step")
     ap.add_argument("--n", type=int, default=N_COLS)
-    ap.add_argument("--workload", default="dense", choices=["dense", "csr"])
+    ap.add_argument("--workload", default="dense", choices=["dense", "csr", "c4"])
     ap.add_argument("--csr-iters", type=int, default=10)
+    ap.add_argument("--sweep", action="store_true", help="CSR: out-of-memory sweep over n_b and q_s")
     args = ap.parse_args()
     if args.case:
         kernel_case(args)
         return
     if args.workload == "csr" and args.impl != "reference":
         csr_workload(args)
+        return
+    if args.workload == "c4" and args.impl != "reference":
+        c4_workload(args)
         return
 
     rank = int(os.environ.get("RANK", "0"))
@@ -590,17 +825,11 @@ def main():
     gk_n = sum(r["gram_kernel_launches"] for r in reps)
     flops_per_step = m * N_COLS * (N_COLS + 1)
     achieved_tf = flops_per_step * args.steps / (gk_ms / 1e3) / 1e12 if gk_ms > 0 else None
-    if prec == 0:
-        peak = 152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
-        roof = {"bound": "alu", "peak_note": "152 SMs x 128 FP32 lanes x 2 flop x max SM clock"}
-    elif prec == 1:
-        peak = peaks["bf16_tflops"] * (1.1 / 2.25)
-        roof = {"bound": "tensor", "peak_note": f"TF32 = bf16 {peak_src} burst x 1.1/2.25 nominal ratio"}
-    else:
-        peak = peaks["bf16_tflops"] * (1.1 / 2.25)
-        roof = {"bound": "tensor", "peak_note": f"TF32 = bf16 {peak_src} burst x 1.1/2.25; 3 MMAs per product"}
+    peak, bound = dtype_peak(prec, peaks, sustained=True)
+    roof = {"bound": bound, "peak_note": PEAK_NOTES[prec].format(src=peak_src, kind="sustained")}
     chunk_rows = int(round(m / max(gk_n / max(args.steps, 1), 1)))
-    kname = {0: "syrk_simt_kernel", 1: "syrk_tc_kernel<TF32>", 2: "syrk_tc_kernel<TF32X3>"}[prec]
+    kname = {0: "syrk_simt_kernel", 1: "syrk_tc_kernel<TF32>", 2: "syrk_tc_kernel<TF32X3>",
+             3: "syrk_tc_kernel<BF16X3>"}[prec]
     roofline = {"bound": roof["bound"], "achieved": round(achieved_tf, 2) if achieved_tf else None,
                 "peak": round(peak, 1), "unit": "TFLOP/s",
                 "frac": round(achieved_tf / peak, 4) if achieved_tf else None,
@@ -610,6 +839,11 @@ def main():
     plan_dev.close()
     del plan_dev
     torch.cuda.empty_cache()
+    alt = None
+    if prec == 2:
+        alt = tf32_in_core(dA, args, m, res_dev, peaks)
+        torch.cuda.empty_cache()
+    small = c1_latency() if rank == 0 else None
 
     # ---------------- e2e: pinned host A, streamed, outputs to host
     e2e_steps = args.e2e_steps or args.steps
@@ -637,7 +871,9 @@ def main():
                    "blocks_per_pass": reps_e[-1]["n_blocks"], "ring_slots": reps_e[-1]["ring_slots"],
                    "block_copies_per_step": reps_e[-1]["h2d_copies"],
                    "copy_stream_GBps": round(reps_e[-1]["h2d_bytes"] / (reps_e[-1]["h2d_copy_ms"] / 1e3) / 1e9, 2)
-                   if reps_e[-1]["h2d_copy_ms"] else None}}
+                   if reps_e[-1]["h2d_copy_ms"] else None,
+                   "copy_min_GBps": round(reps_e[-1]["h2d_copy_min_gbps"], 1),
+                   "copy_max_GBps": round(reps_e[-1]["h2d_copy_max_gbps"], 1)}}
     launches_e = int(sum(r["kernel_launches"] for r in reps_e))
     plan_host.close()
 
@@ -654,14 +890,17 @@ def main():
         line = {"metric": "t-SVD A-stream throughput", "value": round(value, 3), "unit": "GB/s", "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(step_s * 1e3, 2),
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-                "dtype": PREC_NAMES[prec], "data": "synthetic",
+                "dtype": "f32" if prec != 1 else "tf32", "data": "synthetic",
                 "config": {"workload": f"dense out-of-core t-SVD (rank-64 + 1e-4 noise), m={m}, n={N_COLS}, "
                                        f"k={K}, eps={EPS}", "m": m, "n": N_COLS, "k": K, "eps": EPS,
                            "block_rows": BLOCK_ROWS, "device_budget_bytes_e2e": BUDGET,
                            "full_m": FULL_M, "host_ram_limited": m < FULL_M,
                            "l2": "inputs larger than L2 (A is %.0f GiB)" % (m * N_COLS * 4 / 2 ** 30),
-                           "gram_precision": PREC_NAMES[prec], "parallelism": "replicas" if world > 1 else "1 GPU"},
-                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
+                           "gram_precision": PREC_NAMES[prec] + (" (FP32-class split: hi*hi + hi*lo + lo*hi on the "
+                                                                 "tensor cores, FP32 accumulate)" if prec == 2 else ""),
+                           "parallelism": "replicas" if world > 1 else "1 GPU"},
+                "roofline": roofline, "cpu_baseline": cpu, "oom_sweep": sweep, "e2e": e2e, "clocks": clk, "tf32_in_core": alt,
+                "c1_latency": small,
                 "gpu_launches": launches, "gpu_launches_e2e": launches_e,
                 "phases_ms": {"gram": round(reps[-1]["gram_ms"], 2), "power": round(reps[-1]["power_ms"], 2),
                               "left": round(reps[-1]["left_ms"], 2), "applications": reps[-1]["applications"]},

@@ -71,8 +71,19 @@ typedef enum { TSVD_HOST = 0, TSVD_DEVICE = 1 } tsvd_location;
  * test are FP64 in every mode.  FP32: CUDA-core FMA.  TF32: tcgen05 tensor
  * cores on operands rounded to TF32 (nearest-even), FP32 accumulation.
  * TF32X3: each operand split a = hi + lo into two TF32 parts, products
- * hi*hi + hi*lo + lo*hi on tcgen05 (error close to FP32 inputs). */
-typedef enum { TSVD_GRAM_FP32 = 0, TSVD_GRAM_TF32 = 1, TSVD_GRAM_TF32X3 = 2 } tsvd_gram_precision;
+ * hi*hi + hi*lo + lo*hi on tcgen05 (error close to FP32 inputs).
+ * BF16X3: the same three-product split with two BF16 parts (hi = bf16(a),
+ * mid = bf16(a - hi), both nearest-even; a - hi - mid is below 2^-16 |a|),
+ * on tcgen05 kind::f16 at the BF16 rate (the paper's abstract runs the
+ * products on tensor cores where the device has them).  The dropped mid*mid
+ * term gives this mode a small downward bias on the diagonal (at most 2^-16
+ * relative). */
+typedef enum {
+  TSVD_GRAM_FP32 = 0,
+  TSVD_GRAM_TF32 = 1,
+  TSVD_GRAM_TF32X3 = 2,
+  TSVD_GRAM_BF16X3 = 3
+} tsvd_gram_precision;
 
 /* Matrix descriptor (caller-owned, read-only for the library). */
 typedef struct {
@@ -127,7 +138,8 @@ typedef struct {
   int32_t ring_slots;       /* row blocks the streaming ring holds (mode 2) */
   int32_t h2d_copies;       /* host -> device block copies timed (time_kernels) */
   double h2d_copy_ms;       /* summed duration of those copies on the copy stream */
-  double reserved1[2];
+  double h2d_copy_min_gbps; /* slowest single timed copy, 1e9 bytes per second */
+  double h2d_copy_max_gbps; /* fastest single timed copy */
 } tsvd_report;
 
 #define TSVD_FLAG_NOCONV 1        /* a triplet hit max_iter */

@@ -195,6 +195,20 @@ def tsvd_dense(A: np.ndarray, k: int, eps: float, x_start=None, seed: int = 0,
     M = A64 if right else A64.T  # Eq. 3 is Eq. 2 applied to A^T
     if B is None:
         B = gram(M)
+    sig, W, iters, status = right_vectors(B, k, eps, x_start, seed, max_iter, iters_override, sign_convention)
+    # Alg. 1 l.11-13 (or l.15-17): the other factor from A and sigma
+    with np.errstate(divide="ignore", invalid="ignore"):
+        other = (M @ W) / np.where(sig > 0, sig, np.inf)[None, :]
+    if right:
+        return TSVDResult(other, sig, W, iters, status)
+    return TSVDResult(W, sig, other, iters, status)
+
+
+def right_vectors(B: np.ndarray, k: int, eps: float, x_start=None, seed: int = 0, max_iter: int = 10000,
+                  iters_override=None, sign_convention: bool = False):
+    """The loop of Alg. 1 over l on a formed Gram matrix B (FP64): Alg. 2 for
+    each triplet with B deflated in Hotelling form, sigma_l = sqrt(v_l^T B v_l).
+    Returns (sigma, V, iters, status)."""
     d = B.shape[0]
     W = np.zeros((d, 0))
     sig = np.zeros(k)
@@ -219,12 +233,7 @@ def tsvd_dense(A: np.ndarray, k: int, eps: float, x_start=None, seed: int = 0,
         W = np.concatenate([W, v[:, None]], axis=1)
         iters.append(res.iters)
         status.append(res.status)
-    # Alg. 1 l.11-13 (or l.15-17): the other factor from A and sigma
-    with np.errstate(divide="ignore", invalid="ignore"):
-        other = (M @ W) / np.where(sig > 0, sig, np.inf)[None, :]
-    if right:
-        return TSVDResult(other, sig, W, iters, status)
-    return TSVDResult(W, sig, other, iters, status)
+    return sig, W, iters, status
 
 
 # ----------------------------------------------------------------------------

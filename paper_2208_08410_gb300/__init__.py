@@ -145,7 +145,7 @@ class Plan:
         st = self.lib.tsvd_factor(self.handle, C.byref(self.mat), self.workspace.data_ptr(), self.workspace_bytes,
                                   stream, _ptr(U) if want_u else None, _ptr(sigma), _ptr(V), C.byref(rep))
         B.check(st, "tsvd_factor", ok=ok)
-        report = {f: getattr(rep, f) for f, _ in B.tsvd_report._fields_ if f not in ("iters", "reserved1")}
+        report = {f: getattr(rep, f) for f, _ in B.tsvd_report._fields_ if f != "iters"}
         # U and V are stored column-major (m x k / n x k): expose them as (rows, k) views
         Uo = U.T if U is not None else None
         return TSVDResult(Uo, sigma, V.T, iters.tolist(), st, report)

@@ -14,7 +14,7 @@ TSVD_OK, TSVD_EINVAL, TSVD_ENOMEM, TSVD_EBUDGET, TSVD_ECUDA = 0, 1, 2, 3, 4
 TSVD_ETIMEDOUT, TSVD_ENOCONV, TSVD_ERANK, TSVD_EUNSUPPORTED = 5, 6, 7, 8
 TSVD_DENSE_F32_ROWMAJOR, TSVD_CSR_F32_I32_I64 = 0, 1
 TSVD_HOST, TSVD_DEVICE = 0, 1
-TSVD_GRAM_FP32, TSVD_GRAM_TF32, TSVD_GRAM_TF32X3 = 0, 1, 2
+TSVD_GRAM_FP32, TSVD_GRAM_TF32, TSVD_GRAM_TF32X3, TSVD_GRAM_BF16X3 = 0, 1, 2, 3
 TSVD_NOALLOC_MAX_N, TSVD_NOALLOC_MAX_L = 16384, 64
 TSVD_FLAG_NOCONV, TSVD_FLAG_RANK, TSVD_FLAG_NONMONOTONE, TSVD_FLAG_PAGEABLE, TSVD_FLAG_TIMEOUT = 1, 2, 4, 8, 16
 
@@ -42,7 +42,8 @@ class tsvd_report(C.Structure):
                 ("left_ms", C.c_double), ("total_ms", C.c_double), ("h2d_bytes", C.c_double),
                 ("d2h_bytes", C.c_double), ("gram_kernel_ms", C.c_double), ("kernel_launches", C.c_int64),
                 ("applications", C.c_int64), ("ring_slots", C.c_int32), ("h2d_copies", C.c_int32),
-                ("h2d_copy_ms", C.c_double), ("reserved1", C.c_double * 2)]
+                ("h2d_copy_ms", C.c_double), ("h2d_copy_min_gbps", C.c_double),
+                ("h2d_copy_max_gbps", C.c_double)]
 
 
 _P = C.c_void_p

@@ -310,7 +310,7 @@ tsvd_status tsvd_plan(tsvd_plan_t *out, const tsvd_matrix *A, int64_t k, double 
   if (!opt.iters_override && !(eps > 0.0 && eps < 1.0)) return TSVD_EINVAL;
   if (opt.n_buffers == 0) opt.n_buffers = 3;
   if (opt.n_buffers < 2 || opt.n_buffers > 64) return TSVD_EINVAL;
-  if (opt.precision < 0 || opt.precision > 2) return TSVD_EINVAL;
+  if (opt.precision < TSVD_GRAM_FP32 || opt.precision > TSVD_GRAM_BF16X3) return TSVD_EINVAL;
   if (opt.max_iter <= 0) opt.max_iter = 10000;
   if (opt.out_location != TSVD_HOST && opt.out_location != TSVD_DEVICE) return TSVD_EINVAL;
   if (opt.block_rows < 0) return TSVD_EINVAL;
@@ -417,6 +417,7 @@ struct Run {
   double h2d = 0.0, d2h = 0.0;
   int64_t chunk_seq = 0;  // ring position, continues across passes
   int64_t copies = 0;     // timed block copies recorded so far
+  std::vector<double> copy_bytes;  // bytes of each timed copy
 };
 
 // Events around a block copy on the copy stream (only with time_kernels).
@@ -434,12 +435,19 @@ tsvd_status copy_event(Run &r, bool start) {
   return TSVD_OK;
 }
 
-tsvd_status copy_time_ms(Run &r, double *ms) {
+tsvd_status copy_time_ms(Run &r, double *ms, double *min_gbps, double *max_gbps) {
   *ms = 0.0;
+  *min_gbps = 0.0;
+  *max_gbps = 0.0;
   for (int64_t c = 0; c < r.copies; ++c) {
     float t = 0.f;
     TSVD_CUDA(cudaEventElapsedTime(&t, r.p->ev_c[2 * c], r.p->ev_c[2 * c + 1]));
     *ms += t;
+    if (t > 0.f) {
+      const double g = r.copy_bytes[(size_t)c] / ((double)t * 1e6);
+      if (c == 0 || g < *min_gbps) *min_gbps = g;
+      if (g > *max_gbps) *max_gbps = g;
+    }
   }
   return TSVD_OK;
 }
@@ -479,6 +487,7 @@ tsvd_status acquire_dense(Run &r, int64_t r0, int64_t rows, const float **out, i
                                 cudaMemcpyHostToDevice, p->copy_stream));
   }
   TSVD_TRY(copy_event(r, false));
+  if (p->opt.time_kernels) r.copy_bytes.push_back((double)rows * p->n * 4);
   r.h2d += (double)rows * p->n * 4;
   const int ev = *slot >= 0 ? *slot : 0;
   TSVD_CUDA(cudaEventRecord(p->ev_ready[ev], p->copy_stream));
@@ -937,10 +946,12 @@ tsvd_status tsvd_factor(tsvd_plan_t plan, const tsvd_matrix *A, void *workspace,
     report->d2h_bytes = r.d2h;
     report->kernel_launches = launches_so_far() - l0;
     if (st == TSVD_OK || st == TSVD_ENOCONV || st == TSVD_ERANK) {
-      double ms = 0.0;
-      if (copy_time_ms(r, &ms) == TSVD_OK) {
+      double ms = 0.0, gmin = 0.0, gmax = 0.0;
+      if (copy_time_ms(r, &ms, &gmin, &gmax) == TSVD_OK) {
         report->h2d_copy_ms = ms;
         report->h2d_copies = (int32_t)r.copies;
+        report->h2d_copy_min_gbps = gmin;
+        report->h2d_copy_max_gbps = gmax;
       }
     }
   }
@@ -957,7 +968,7 @@ size_t tsvd_gram_scratch_bytes(int64_t rows, int64_t n, int32_t precision) {
 tsvd_status tsvd_gram_accumulate(const float *dA, int64_t rows, int64_t n, int64_t ld, double *dG,
                                  int32_t precision, void *scratch, size_t scratch_bytes, void *stream) {
   if (rows < 0 || n <= 0 || ld < n || !dG || (rows > 0 && !dA)) return TSVD_EINVAL;
-  if (precision < 0 || precision > 2) return TSVD_EINVAL;
+  if (precision < TSVD_GRAM_FP32 || precision > TSVD_GRAM_BF16X3) return TSVD_EINVAL;
   if (precision != TSVD_GRAM_FP32) {
     if (scratch_bytes < gram_tc_scratch_bytes(rows, n, precision)) return TSVD_EINVAL;
     if (scratch && (reinterpret_cast<uintptr_t>(scratch) & 255) != 0) return TSVD_EINVAL;

@@ -8,14 +8,19 @@
 //     round-to-nearest-even.  For TF32X3 it also writes lo = tf32(a - hi), so
 //     a = hi + lo to ~2^-22 relative and hi*hi + hi*lo + lo*hi recovers the
 //     FP32 product to about FP32 accuracy (3xTF32, Ootomo & Yokota 2022).
-//     Kp is rows rounded up to 32 and the pad is zero.
+//     For BF16X3 it writes two BF16 parts hi = bf16(a), mid = bf16(a - hi)
+//     (both nearest-even) and the products hi*hi + hi*mid + mid*hi run as
+//     kind::f16 MMAs (BF16 x 3, Henry, Tang & Heinecke 2019).
+//     Kp is rows rounded up to one stage of K (32 TF32 or 64 BF16 rows) and
+//     the pad is zero.
 //  2. syrk: a persistent warp-specialised kernel.  A work unit is one
 //     128 x 256 tile (I, J) of G with J0 <= I0 + 127 (only tiles touching the
 //     lower triangle: the symmetric task reuse of Sec. V-C) and one slice of
 //     the K = row range.  Warp 0 streams 128-row (A operand) and 256-row
 //     (B operand) slabs of At into a 4-stage shared-memory ring with TMA
 //     (128-byte swizzle, no multicast); warp 1 issues tcgen05.mma kind::tf32
-//     (M=128, N=256, K=8) into one of two 256-column TMEM accumulators, one
+//     (M=128, N=256, K=8) or kind::f16 with BF16 operands (K=16) into one of
+//     two 256-column TMEM accumulators, one
 //     short K segment at a time; warps 2-17 drain the other accumulator with
 //     tcgen05.ld into FP32 registers (round-to-nearest adds), so draining one
 //     segment overlaps the MMAs of the next, and add each unit's sum into the
@@ -37,17 +42,23 @@ constexpr int TC_EPI_COLS = 64;   // accumulator columns per epilogue thread
 constexpr int TC_THREADS = 64 + 32 * TC_EPI_WARPS;  // TMA warp, MMA warp, epilogue warps
 constexpr int TM = 128;          // MMA M (rows of At from block I)
 constexpr int TN = 256;          // MMA N (rows of At from block J)
-constexpr int TK = 32;           // K per stage (32 x 4 B = one 128-byte swizzle row)
-constexpr int A_SLAB = TM * TK * 4;  // 16 KB
-constexpr int B_SLAB = TN * TK * 4;  // 32 KB
+constexpr int ROW_BYTES = 128;   // K bytes per stage: one 128-byte swizzle row
+constexpr int A_SLAB = TM * ROW_BYTES;  // 16 KB
+constexpr int B_SLAB = TN * ROW_BYTES;  // 32 KB
+constexpr int MMA_K_BYTES = 32;  // K bytes per MMA (8 TF32 or 16 BF16)
 
 template <int PREC>
 struct Cfg {
-  static constexpr int kParts = PREC == TSVD_GRAM_TF32X3 ? 2 : 1;  // hi (and lo) operands
+  static constexpr bool kBf16 = PREC == TSVD_GRAM_BF16X3;
+  static constexpr int kElem = kBf16 ? 2 : 4;                       // bytes per operand element
+  static constexpr int kTK = ROW_BYTES / kElem;                     // K rows per stage
+  static constexpr int kParts = PREC == TSVD_GRAM_TF32 ? 1 : 2;     // hi (and lo / mid) operands
   static constexpr int kStageBytes = kParts * (A_SLAB + B_SLAB);
-  static constexpr int kStages = PREC == TSVD_GRAM_TF32X3 ? 2 : 4;
+  static constexpr int kStages = kParts == 2 ? 2 : 4;
   static constexpr int kSmem = kStages * kStageBytes + 1024 /*align*/ + 256 /*barriers*/;
 };
+
+__host__ __device__ constexpr int stage_rows(int precision) { return precision == TSVD_GRAM_BF16X3 ? 64 : 32; }
 
 // ---------------------------------------------------------------- PTX helpers
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
@@ -125,6 +136,27 @@ __device__ __forceinline__ void umma_tf32(uint32_t tmem_d, uint64_t a, uint64_t 
       : "memory");
 }
 
+// Instruction descriptor, kind::f16 with BF16 A and B: D F32, both K-major.
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void umma_bf16(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+          tmem_d),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc)
+      : "memory");
+}
+
+template <int PREC>
+__device__ __forceinline__ void umma(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t acc) {
+  if (PREC == TSVD_GRAM_BF16X3)
+    umma_bf16(tmem_d, a, b, idesc_bf16(TM, TN), acc);
+  else
+    umma_tf32(tmem_d, a, b, idesc_tf32(TM, TN), acc);
+}
+
 __device__ __forceinline__ void umma_commit(uint32_t bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
 }
@@ -166,14 +198,24 @@ __device__ __forceinline__ float tf32_rne(float x) {
   return __uint_as_float((u + 0x0fffu + ((u >> 13) & 1u)) & 0xffffe000u);
 }
 
+// Round an FP32 value to the nearest BF16 value (8 significant bits), ties to
+// even, returned as its 16-bit encoding; NaN stays NaN, Inf stays Inf.
+__device__ __forceinline__ uint16_t bf16_rne_bits(float x) {
+  const uint32_t u = __float_as_uint(x);
+  if ((u & 0x7f800000u) == 0x7f800000u) return (uint16_t)((u >> 16) | ((u & 0xffffu) ? 0x40u : 0u));
+  return (uint16_t)((u + 0x7fffu + ((u >> 16) & 1u)) >> 16);
+}
+
+__device__ __forceinline__ float bf16_bits_value(uint16_t b) { return __uint_as_float((uint32_t)b << 16); }
+
 // ---------------------------------------------------------------- prep kernel
-// At[c][r] = tf32(A[r][c]) (and the lo part).  A block of 32 x 8 threads moves
-// a 32-row x 128-column strip as four 32 x 32 tiles through shared memory, so
-// both the reads (along a row of A) and the writes (along a row of At) are
-// 128-byte coalesced; 16 loads per thread are in flight before the first store.
-template <int PARTS>
+// At[c][r] = round(A[r][c]) (and the second part).  A block of 32 x 8 threads
+// moves a 32-row x 128-column strip as four 32 x 32 tiles through shared
+// memory, so both the reads (along a row of A) and the writes (along a row of
+// At) are coalesced; 16 loads per thread are in flight before the first store.
+template <int PREC>
 __global__ void __launch_bounds__(256) prep_kernel(const float *__restrict__ A, int64_t rows, int64_t n, int64_t ld,
-                                                   float *__restrict__ hi, float *__restrict__ lo, int64_t Kp) {
+                                                   void *__restrict__ hi_, void *__restrict__ lo_, int64_t Kp) {
   __shared__ float s[4][32][33];
   const int tx = threadIdx.x, ty = threadIdx.y;
   const int64_t r0 = (int64_t)blockIdx.x * 32;
@@ -194,9 +236,15 @@ __global__ void __launch_bounds__(256) prep_kernel(const float *__restrict__ A, 
       const int64_t c = c0 + 32 * t + ty + 8 * i, r = r0 + tx;
       if (c < n && r < Kp) {
         const float x = s[t][tx][ty + 8 * i];
-        const float h = tf32_rne(x);
-        hi[c * Kp + r] = h;
-        if (PARTS == 2) lo[c * Kp + r] = tf32_rne(x - h);
+        if (PREC == TSVD_GRAM_BF16X3) {
+          const uint16_t h = bf16_rne_bits(x);
+          static_cast<uint16_t *>(hi_)[c * Kp + r] = h;
+          static_cast<uint16_t *>(lo_)[c * Kp + r] = bf16_rne_bits(x - bf16_bits_value(h));  // x - h is exact
+        } else {
+          const float h = tf32_rne(x);
+          static_cast<float *>(hi_)[c * Kp + r] = h;
+          if (PREC == TSVD_GRAM_TF32X3) static_cast<float *>(lo_)[c * Kp + r] = tf32_rne(x - h);
+        }
       }
     }
   }
@@ -207,7 +255,7 @@ struct TcArgs {
   double *G;
   int64_t n;
   int64_t Kp;         // padded K (rows) of At
-  int64_t ksplit;     // rows per work unit (multiple of TK * seg_stages)
+  int64_t ksplit;     // rows per work unit (multiple of stage rows * seg_stages)
   int seg_stages;     // stages per TMEM accumulation segment
   int n_splits;
   int n_tiles;
@@ -250,6 +298,7 @@ syrk_tc_kernel(const __grid_constant__ CUtensorMap map_hi, const __grid_constant
   const uint32_t tfull0 = smem_u32(bars + 2 * C::kStages), tempty0 = smem_u32(bars + 2 * C::kStages + 2);
   const uint32_t final_bar = smem_u32(bars + 2 * C::kStages + 4);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  constexpr int TK = C::kTK;
   const int units = a.n_tiles * a.n_splits;
   const int64_t seg_rows = (int64_t)a.seg_stages * TK;
 
@@ -311,7 +360,6 @@ syrk_tc_kernel(const __grid_constant__ CUtensorMap map_hi, const __grid_constant
   } else if (warp == 1) {
     // ------------------------------------------------ MMA issuer
     if (lane == 0) {
-      constexpr uint32_t idesc = idesc_tf32(TM, TN);
       uint32_t it = 0, sc = 0;  // stage counter, segment counter
       bool ok = true;
       for (int u = blockIdx.x; u < units && ok; u += gridDim.x) {
@@ -332,16 +380,16 @@ syrk_tc_kernel(const __grid_constant__ CUtensorMap map_hi, const __grid_constant
             const uint32_t st = smem_u32(smem + s * C::kStageBytes);
             const uint64_t dah = umma_desc_sw128(st), dbh = umma_desc_sw128(st + A_SLAB);
 #pragma unroll
-            for (int k8 = 0; k8 < TK / 8; ++k8) {
-              const uint64_t off = (uint64_t)(k8 * 32) >> 4;  // 32 bytes per K=8 step
+            for (int kq = 0; kq < ROW_BYTES / MMA_K_BYTES; ++kq) {
+              const uint64_t off = (uint64_t)(kq * MMA_K_BYTES) >> 4;  // descriptor start, 16-byte units
               if (C::kParts == 2) {
                 const uint32_t sl = st + A_SLAB + B_SLAB;
                 const uint64_t dal = umma_desc_sw128(sl), dbl = umma_desc_sw128(sl + A_SLAB);
-                umma_tf32(dtm, dal + off, dbh + off, idesc, first ? 0u : 1u);  // small terms first
+                umma<PREC>(dtm, dal + off, dbh + off, first ? 0u : 1u);  // small terms first
                 first = 0;
-                umma_tf32(dtm, dah + off, dbl + off, idesc, 1u);
+                umma<PREC>(dtm, dah + off, dbl + off, 1u);
               }
-              umma_tf32(dtm, dah + off, dbh + off, idesc, first ? 0u : 1u);
+              umma<PREC>(dtm, dah + off, dbh + off, first ? 0u : 1u);
               first = 0;
             }
             umma_commit(empty0 + 8 * s);  // frees the stage when these MMAs finish
@@ -423,14 +471,19 @@ tsvd_status get_encode(EncodeTiledFn *out) {
   return TSVD_OK;
 }
 
-tsvd_status make_map(CUtensorMap *map, const float *base, int64_t n, int64_t Kp) {
+// At viewed as n rows of Kp elements; the box is one 128-byte swizzle row of K
+// by 128 rows (so every x coordinate the kernel passes is a multiple of 128 bytes)
+tsvd_status make_map(CUtensorMap *map, const void *base, int64_t n, int64_t Kp, int precision) {
   EncodeTiledFn enc;
   TSVD_TRY(get_encode(&enc));
+  const bool bf = precision == TSVD_GRAM_BF16X3;
+  const int64_t elem = bf ? 2 : 4;
   const cuuint64_t dims[2] = {(cuuint64_t)Kp, (cuuint64_t)n};
-  const cuuint64_t strides[1] = {(cuuint64_t)Kp * 4};
-  const cuuint32_t box[2] = {(cuuint32_t)TK, (cuuint32_t)TM};
+  const cuuint64_t strides[1] = {(cuuint64_t)(Kp * elem)};
+  const cuuint32_t box[2] = {(cuuint32_t)(ROW_BYTES / elem), (cuuint32_t)TM};
   const cuuint32_t estr[2] = {1, 1};
-  const CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float *>(base), dims, strides, box, estr,
+  const CUresult r = enc(map, bf ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2,
+                         const_cast<void *>(base), dims, strides, box, estr,
                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) {
@@ -440,61 +493,83 @@ tsvd_status make_map(CUtensorMap *map, const float *base, int64_t n, int64_t Kp)
   return TSVD_OK;
 }
 
-int64_t padded_k(int64_t rows) { return round_up(std::max<int64_t>(rows, 1), TK); }
+int64_t padded_k(int64_t rows, int precision) {
+  return round_up(std::max<int64_t>(rows, 1), stage_rows(precision));
+}
+
+int tc_parts(int precision) { return precision == TSVD_GRAM_TF32 ? 1 : 2; }
+int64_t tc_elem(int precision) { return precision == TSVD_GRAM_BF16X3 ? 2 : 4; }
+
+template <int PREC>
+tsvd_status launch_syrk(const CUtensorMap &mh, const CUtensorMap &ml, const TcArgs &a, int grid,
+                        cudaStream_t stream) {
+  static thread_local bool attr = false;
+  if (!attr) {
+    TSVD_CUDA(cudaFuncSetAttribute(syrk_tc_kernel<PREC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   Cfg<PREC>::kSmem));
+    attr = true;
+  }
+  syrk_tc_kernel<PREC><<<grid, TC_THREADS, Cfg<PREC>::kSmem, stream>>>(mh, ml, a);
+  TSVD_LAUNCHED();
+  return TSVD_OK;
+}
 
 }  // namespace
 
 size_t gram_tc_scratch_bytes(int64_t rows, int64_t n, int precision) {
   if (precision == TSVD_GRAM_FP32 || rows <= 0 || n <= 0) return 0;
-  const int parts = precision == TSVD_GRAM_TF32X3 ? 2 : 1;
   // status word (first 1024 bytes), then At (n x Kp) per part, 1024-byte aligned;
   // +1024 lets the caller's 256-byte aligned pointer be rounded up
-  return 2048 + (size_t)parts * (size_t)round_up(n * padded_k(rows) * 4, 1024);
+  return 2048 + (size_t)tc_parts(precision) *
+                    (size_t)round_up(n * padded_k(rows, precision) * tc_elem(precision), 1024);
 }
 
 // Stages per TMEM accumulation segment (bounds the truncation drift of one
-// FP32 accumulation chain to ~16-24 MMAs); TSVD_TC_SEG overrides it.
+// FP32 accumulation chain to 16-24 MMAs); TSVD_TC_SEG overrides it.
 static int tc_seg_stages(int precision) {
   const char *e = getenv("TSVD_TC_SEG");
   if (e) return std::max(1, atoi(e));
-  return precision == TSVD_GRAM_TF32X3 ? 2 : 4;
+  return precision == TSVD_GRAM_TF32 ? 4 : 2;
 }
 
 tsvd_status launch_gram_tc(const float *A, int64_t rows, int64_t n, int64_t ld, double *G, int precision,
                            void *scratch, size_t scratch_bytes, cudaStream_t stream, cudaEvent_t ev0,
                            cudaEvent_t ev1) {
   if (rows <= 0) return TSVD_OK;
-  if (precision != TSVD_GRAM_TF32 && precision != TSVD_GRAM_TF32X3) return TSVD_EINVAL;
+  if (precision != TSVD_GRAM_TF32 && precision != TSVD_GRAM_TF32X3 && precision != TSVD_GRAM_BF16X3)
+    return TSVD_EINVAL;
   if (n > (int64_t)TM * 65535) return TSVD_EUNSUPPORTED;
   DeviceInfo di;
   TSVD_TRY(device_info(&di));
   if (di.cc_major != 10) return TSVD_EUNSUPPORTED;  // tcgen05 needs the sm_100 family
   if (!scratch || scratch_bytes < gram_tc_scratch_bytes(rows, n, precision)) return TSVD_EINVAL;
   if ((reinterpret_cast<uintptr_t>(scratch) & 255) != 0) return TSVD_EINVAL;
-  const int parts = precision == TSVD_GRAM_TF32X3 ? 2 : 1;
-  const int64_t Kp = padded_k(rows);
+  const int parts = tc_parts(precision);
+  const int64_t Kp = padded_k(rows, precision);
+  const int64_t part_bytes = round_up(n * Kp * tc_elem(precision), 1024);
   unsigned char *base = static_cast<unsigned char *>(scratch);
   int *err = reinterpret_cast<int *>(base);  // status word: 0 ok, nonzero = a bounded wait gave up
   const uintptr_t al = (reinterpret_cast<uintptr_t>(base) + 1024 + 1023) & ~uintptr_t(1023);
-  float *hi = reinterpret_cast<float *>(al);
-  float *lo = parts == 2 ? reinterpret_cast<float *>(al + round_up(n * Kp * 4, 1024)) : hi;
-  if (al + (size_t)parts * round_up(n * Kp * 4, 1024) > reinterpret_cast<uintptr_t>(base) + scratch_bytes)
-    return TSVD_EINVAL;
+  void *hi = reinterpret_cast<void *>(al);
+  void *lo = parts == 2 ? reinterpret_cast<void *>(al + part_bytes) : hi;
+  if (al + (size_t)parts * part_bytes > reinterpret_cast<uintptr_t>(base) + scratch_bytes) return TSVD_EINVAL;
 
-  // 1. prep: transpose + TF32 rounding (+ split)
+  // 1. prep: transpose + rounding (+ split); Kp is a multiple of 32, the prep row tile
   {
     dim3 grid((unsigned)ceil_div(Kp, 32), (unsigned)ceil_div(n, 128)), block(32, 8);
     if (grid.y > 65535 || grid.x > 0x7fffffffu) return TSVD_EUNSUPPORTED;
-    if (parts == 2)
-      prep_kernel<2><<<grid, block, 0, stream>>>(A, rows, n, ld, hi, lo, Kp);
+    if (precision == TSVD_GRAM_BF16X3)
+      prep_kernel<TSVD_GRAM_BF16X3><<<grid, block, 0, stream>>>(A, rows, n, ld, hi, lo, Kp);
+    else if (precision == TSVD_GRAM_TF32X3)
+      prep_kernel<TSVD_GRAM_TF32X3><<<grid, block, 0, stream>>>(A, rows, n, ld, hi, lo, Kp);
     else
-      prep_kernel<1><<<grid, block, 0, stream>>>(A, rows, n, ld, hi, lo, Kp);
+      prep_kernel<TSVD_GRAM_TF32><<<grid, block, 0, stream>>>(A, rows, n, ld, hi, lo, Kp);
     TSVD_LAUNCHED();
   }
   // 2. persistent tcgen05 SYRK over the lower-triangle tiles
   CUtensorMap mh, ml;
-  TSVD_TRY(make_map(&mh, hi, n, Kp));
-  TSVD_TRY(make_map(&ml, lo, n, Kp));
+  TSVD_TRY(make_map(&mh, hi, n, Kp, precision));
+  TSVD_TRY(make_map(&ml, lo, n, Kp, precision));
   TcArgs a;
   a.G = G;
   a.n = n;
@@ -509,7 +584,7 @@ tsvd_status launch_gram_tc(const float *A, int64_t rows, int64_t n, int64_t ld, 
     // K slices: about 8 units per SM balance the persistent grid; fewer,
     // longer units keep the FP64 reductions into G (one 128 x 256 tile per
     // unit) small, so slices are never shorter than 4096 rows
-    const int64_t quantum = (int64_t)TK * a.seg_stages;
+    const int64_t quantum = (int64_t)stage_rows(precision) * a.seg_stages;
     const int64_t want_units = 8LL * di.sms;
     int64_t splits = std::max<int64_t>(1, ceil_div(want_units, a.n_tiles));
     int64_t ks = round_up(ceil_div(Kp, splits), quantum);
@@ -524,24 +599,12 @@ tsvd_status launch_gram_tc(const float *A, int64_t rows, int64_t n, int64_t ld, 
   const int64_t units = (int64_t)a.n_tiles * a.n_splits;
   const int grid = (int)std::min<int64_t>(units, di.sms);
   if (ev0) TSVD_CUDA(cudaEventRecord(ev0, stream));
-  if (precision == TSVD_GRAM_TF32) {
-    static thread_local bool attr1 = false;
-    if (!attr1) {
-      TSVD_CUDA(cudaFuncSetAttribute(syrk_tc_kernel<TSVD_GRAM_TF32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     Cfg<TSVD_GRAM_TF32>::kSmem));
-      attr1 = true;
-    }
-    syrk_tc_kernel<TSVD_GRAM_TF32><<<grid, TC_THREADS, Cfg<TSVD_GRAM_TF32>::kSmem, stream>>>(mh, ml, a);
-  } else {
-    static thread_local bool attr2 = false;
-    if (!attr2) {
-      TSVD_CUDA(cudaFuncSetAttribute(syrk_tc_kernel<TSVD_GRAM_TF32X3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     Cfg<TSVD_GRAM_TF32X3>::kSmem));
-      attr2 = true;
-    }
-    syrk_tc_kernel<TSVD_GRAM_TF32X3><<<grid, TC_THREADS, Cfg<TSVD_GRAM_TF32X3>::kSmem, stream>>>(mh, ml, a);
-  }
-  TSVD_LAUNCHED();
+  if (precision == TSVD_GRAM_TF32)
+    TSVD_TRY(launch_syrk<TSVD_GRAM_TF32>(mh, ml, a, grid, stream));
+  else if (precision == TSVD_GRAM_TF32X3)
+    TSVD_TRY(launch_syrk<TSVD_GRAM_TF32X3>(mh, ml, a, grid, stream));
+  else
+    TSVD_TRY(launch_syrk<TSVD_GRAM_BF16X3>(mh, ml, a, grid, stream));
   if (ev1) TSVD_CUDA(cudaEventRecord(ev1, stream));
   return TSVD_OK;
 }

@@ -36,6 +36,8 @@ __all__ = [
     "start_normals",
     "dense_lowrank_blocks_torch",
     "csr_uniform_torch",
+    "stacked_factor",
+    "stacked_rows_torch",
 ]
 
 
@@ -168,8 +170,9 @@ def start_normals(n: int, k: int, seed: int) -> np.ndarray:
 
 def dense_lowrank_blocks_torch(out_host, m: int, n: int, rank: int, sigma: np.ndarray, noise: float,
                                seed: int, block_rows: int, device="cuda"):
-    """Fill a pinned host FP32 buffer (m x n row-major) with the rank-r plus
-    noise workload, generating each row block on the GPU with torch.
+    """Fill an FP32 buffer (m x n row-major; pinned host memory or a device
+    tensor) with the rank-r plus noise workload, generating each row block on
+    the GPU with torch.
 
     Left factor: seeded Gaussian (m x r) made orthonormal by two rounds of
     Cholesky QR over the whole height (the Gaussian stays on the device, 4 B
@@ -245,3 +248,44 @@ def csr_uniform_torch(m: int, n: int, nnz_per_row: float, seed: int, device="cud
         del key
     vals = torch.rand(nnz, generator=g, device=dev, dtype=torch.float32)
     return {"row_ptr": row_ptr, "col_idx": cols.to(torch.int32), "values": vals, "m": m, "n": n}
+
+
+def stacked_factor(n: int, sigma: np.ndarray, copies: int, seed: int) -> dict:
+    """Generator matrix of the stacked-orthogonal dense workload (copies * n rows).
+
+    A = stack_b (S_b P_b) M with M = fl32(W diag(sigma) V^T / sqrt(copies)),
+    W and V the Q factors of two seeded n x n Gaussians, P_b a random row
+    permutation and S_b random signs per block (drawn by stacked_rows_torch).
+    U = stack_b S_b P_b W / sqrt(copies) has orthonormal columns exactly
+    (sum_b W^T P_b^T S_b S_b P_b W / copies = I), so the singular values of A
+    are sigma up to the FP32 rounding of M, its right singular vectors are the
+    columns of V, and A^T A = copies * M^T M exactly (a row permutation and
+    signs leave each block's Gram M^T M unchanged).  Returns M (FP32), V, sigma.
+    """
+    sigma = np.asarray(sigma, dtype=np.float64)
+    W = orthonormal_columns(n, n, seed, stream=7)
+    V = orthonormal_columns(n, n, seed, stream=8)
+    M = (W * sigma[None, :]) @ V.T
+    M *= 1.0 / math.sqrt(copies)
+    return {"M32": M.astype(np.float32), "V": V, "sigma": sigma, "copies": int(copies)}
+
+
+def stacked_rows_torch(out, M32: np.ndarray, seed: int):
+    """Fill `out` (a torch FP32 tensor of copies * n rows and n columns, on any
+    device) with the stacked workload of stacked_factor: rows [b n, (b+1) n)
+    are M32 with its rows permuted and signs flipped at random (torch
+    generator of out's device, seeded)."""
+    import torch
+    n = M32.shape[0]
+    m = out.shape[0]
+    if m % n or out.shape[1] != n:
+        raise ValueError("out must have a multiple of n rows and n columns")
+    dev = out.device
+    Md = torch.as_tensor(np.ascontiguousarray(M32), device=dev)
+    g = torch.Generator(device=dev)
+    g.manual_seed(int(seed) * 1000003 + 53)
+    for b in range(m // n):
+        perm = torch.randperm(n, generator=g, device=dev)
+        sgn = torch.randint(0, 2, (n,), generator=g, device=dev).to(torch.float32).mul_(2.0).sub_(1.0)
+        torch.mul(Md[perm], sgn[:, None], out=out[b * n:(b + 1) * n])
+    return out

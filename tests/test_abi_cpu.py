@@ -78,6 +78,9 @@ def test_plan_validation_dense(lib):
     bad = np.array([3, 0, 3, 3, 3], dtype=np.int32)
     assert _plan(d, 5, 1e-6, _opts(iters_override=bad.ctypes.data))[0] == B.TSVD_EINVAL
     assert _plan(d, 5, 1e-6, _opts(precision=7))[0] == B.TSVD_EINVAL
+    assert _plan(d, 5, 1e-6, _opts(precision=4))[0] == B.TSVD_EINVAL
+    for prec in (B.TSVD_GRAM_FP32, B.TSVD_GRAM_TF32, B.TSVD_GRAM_TF32X3, B.TSVD_GRAM_BF16X3):
+        assert _plan(d, 5, 1e-6, _opts(precision=prec))[0] == B.TSVD_OK
     assert _plan(d, 5, 1e-6, _opts(n_buffers=1))[0] == B.TSVD_EINVAL
     d2, keep2 = _dense_desc(100, 20)
     d2.ld = 10
@@ -179,3 +182,18 @@ def test_loader_fails_loudly_without_library(tmp_path, monkeypatch):
     monkeypatch.setattr(B, "_lib", None)
     with pytest.raises(RuntimeError, match="not built"):
         B.load(build_if_missing=False)
+
+
+def test_gram_scratch_sizes(lib):
+    """Tensor-core scratch: a status word, then one (TF32) or two parts of the
+    K-major copy At (n x Kp); Kp is rows rounded up to a stage of 128 bytes of
+    K (32 FP32 or 64 BF16 rows); each part is 1024-byte aligned."""
+    rows, n = 1000, 300
+
+    def up(x, q):
+        return -(-x // q) * q
+    assert B.tsvd_gram_scratch_bytes(rows, n, B.TSVD_GRAM_FP32) == 0
+    assert B.tsvd_gram_scratch_bytes(rows, n, B.TSVD_GRAM_TF32) == 2048 + up(n * up(rows, 32) * 4, 1024)
+    assert B.tsvd_gram_scratch_bytes(rows, n, B.TSVD_GRAM_TF32X3) == 2048 + 2 * up(n * up(rows, 32) * 4, 1024)
+    assert B.tsvd_gram_scratch_bytes(rows, n, B.TSVD_GRAM_BF16X3) == 2048 + 2 * up(n * up(rows, 64) * 2, 1024)
+    assert B.tsvd_gram_scratch_bytes(0, n, B.TSVD_GRAM_BF16X3) == 0

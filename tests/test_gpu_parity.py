@@ -26,6 +26,7 @@ pytestmark = pytest.mark.gpu
 
 from paper_2208_08410_gb300 import _binding as B  # noqa: E402
 from paper_2208_08410_gb300 import tsvd  # noqa: E402
+from clustered_checks import check_clustered  # noqa: E402
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
 U32 = 2.0 ** -24
@@ -399,13 +400,28 @@ def _tc_case(rows, n, ld, seed):
     return Afull
 
 
-@pytest.mark.parametrize("prec", [B.TSVD_GRAM_TF32, B.TSVD_GRAM_TF32X3])
+def _split_error(prec) -> float:
+    """Relative error of one product a*b as the tensor-core mode forms it.
+    TF32: both operands rounded to 11 significant bits (2^-11 each).
+    TF32X3: a = hi + lo + r with |r| <= 2^-22 |a|; the dropped lo*lo and the
+    r terms stay below 3 * 2^-22.  BF16X3: hi = bf16(a) (|a - hi| <= 2^-8 |a|),
+    mid = bf16(a - hi) (|a - hi - mid| <= 2^-16 |a|); the dropped mid*mid and
+    the four remainder terms sum to at most
+    2^-16 ((1+2^-8)^2 + 2 (1+2^-8) + 2^-7 (1+2^-8) + 2^-16)."""
+    if prec == B.TSVD_GRAM_TF32:
+        return 2.0 ** -10 + 2.0 ** -22
+    if prec == B.TSVD_GRAM_TF32X3:
+        return 3 * 2.0 ** -22
+    u = 1 + 2.0 ** -8
+    return 2.0 ** -16 * (u * u + 2 * u + 2.0 ** -7 * u + 2.0 ** -16)
+
+
+@pytest.mark.parametrize("prec", [B.TSVD_GRAM_TF32, B.TSVD_GRAM_TF32X3, B.TSVD_GRAM_BF16X3])
 @pytest.mark.parametrize("rows,n,ld", [(1000, 256, 256), (777, 130, 130), (64, 5, 5), (5000, 300, 300),
                                        (300, 129, 133), (20000, 512, 512), (1, 17, 17), (70, 640, 640)])
 def test_gram_tensor_cores_match_oracle(prec, rows, n, ld):
-    """TF32: operands rounded to nearest (|da| <= 2^-11 |a|), exact products,
-    FP32 accumulation over a K slice then FP64; TF32X3: a = hi + lo to
-    2^-22 |a|, three products.  Bound: (e_in + (K+2) 2^-23) (|A|^T |A|)."""
+    """Products with the split error of the mode (_split_error), FP32
+    accumulation over a K slice, then FP64.  Bound: (e_in + (K+2) 2^-23) (|A|^T |A|)."""
     Afull = _tc_case(rows, n, ld, rows * 7 + n)
     A = Afull[:, :n]
     sentinel = -7.25
@@ -421,7 +437,7 @@ def test_gram_tensor_cores_match_oracle(prec, rows, n, ld):
     ref_G = ref.gram(A)
     absA = np.abs(A.astype(np.float64))
     absG = absA.T @ absA
-    e_in = 2.0 ** -10 + 2.0 ** -22 if prec == B.TSVD_GRAM_TF32 else 3 * 2.0 ** -22
+    e_in = _split_error(prec)
     K = min(rows, 8192)
     bound = (e_in + (K + 2) * 2.0 ** -23) * absG + 1e-300
     iu = np.triu_indices(n)
@@ -434,17 +450,42 @@ def test_gram_tensor_cores_match_oracle(prec, rows, n, ld):
         d = np.arange(n)
         bias = float(np.mean((got[d, d] - ref_G[d, d]) / ref_G[d, d]))
         # short TMEM accumulation segments keep the toward-zero drift of the
-        # tensor-core accumulator to ~0.4 ulp x (16..24 MMAs) ~ 5e-7
-        assert abs(bias) < 2e-6, bias
+        # tensor-core accumulator to ~0.4 ulp x (16..24 MMAs) ~ 5e-7.  BF16X3
+        # also drops mid*mid >= 0 on the diagonal: E[(a - hi)^2 / a^2] is about
+        # 2^-15 / 12 = 2.5e-6 for Gaussian entries.
+        lim = 1e-5 if prec == B.TSVD_GRAM_BF16X3 else 2e-6
+        assert abs(bias) < lim, bias
 
 
-def test_tsvd_tf32x3_c1_matches_oracle():
+# ---------------------------------------------------------------- mixed precision (clustered spectrum)
+@pytest.mark.parametrize("prec", [B.TSVD_GRAM_FP32, B.TSVD_GRAM_TF32, B.TSVD_GRAM_TF32X3, B.TSVD_GRAM_BF16X3])
+def test_tsvd_clustered_spectrum_precisions_match_oracle(prec):
+    """Mixed-precision workload at reduced size: stacked-orthogonal A with a
+    harmonic spectrum and the pair sigma_10 - sigma_11 = 1e-3, k = 32,
+    eps = 1e-8; every Gram precision follows the oracle's trajectory."""
+    n, copies, k, eps = 1024, 16, 32, 1e-8
+    sig_t = synth.spectrum_harmonic_clustered(n, 10, 1e-3)
+    fac = synth.stacked_factor(n, sig_t, copies, seed=2)
+    A = torch.empty((copies * n, n), dtype=torch.float32, device="cuda")
+    synth.stacked_rows_torch(A, fac["M32"], seed=2)
+    Ah = A.cpu().numpy()
+    x = synth.start_normals(n, k, seed=4)
+    sig_o, V_o, it_o, st_o = ref.right_vectors(ref.gram(Ah), k, eps, x_start=x)
+    assert all(s == "ok" for s in st_o)
+    r = tsvd(A, k, eps, start_draws=x, iters_override=it_o, precision=prec, out_device=True)
+    assert r.iters == it_o
+    r.sigma = r.sigma.cpu().numpy()
+    r.V = r.V.cpu().numpy()
+    check_clustered(r, sig_o, V_o, k, prec, sig_t)
+
+
+@pytest.mark.parametrize("prec", [B.TSVD_GRAM_TF32X3, B.TSVD_GRAM_BF16X3])
+def test_tsvd_split_precisions_c1_match_oracle(prec):
     m, n, k, eps = 2048, 256, 8, 1e-8
     inp = synth.dense_prescribed(m, n, synth.spectrum_geometric(n, 0.8), 1e-6, seed=0)
     x = synth.start_normals(n, k, seed=1)
     o = ref.tsvd_dense(inp["A"], k, eps, x_start=x)
-    r = tsvd(torch.from_numpy(inp["A"]).cuda(), k, eps, start_draws=x, iters_override=o.iters,
-             precision=B.TSVD_GRAM_TF32X3)
+    r = tsvd(torch.from_numpy(inp["A"]).cuda(), k, eps, start_draws=x, iters_override=o.iters, precision=prec)
     _compare(r, o, k)
 
 

@@ -370,3 +370,29 @@ def test_pins_catch_planted_mistakes(monkeypatch):
         return M @ M.T if M.shape[0] == M.shape[1] else M.T @ M
     monkeypatch.setattr(ref, "gram", gram_t)
     assert not _pins_hold()
+
+
+def test_stacked_workload_identities():
+    """The stacked dense workload: A^T A = copies * M^T M exactly (row
+    permutations and signs), singular values = the prescribed sigma up to the
+    FP32 rounding of M, right singular vectors = the generator's V."""
+    torch = pytest.importorskip("torch")
+    n, copies = 48, 6
+    sig = synth.spectrum_harmonic_clustered(n, 10, 1e-3)
+    fac = synth.stacked_factor(n, sig, copies, seed=5)
+    A = torch.empty((copies * n, n), dtype=torch.float32)
+    synth.stacked_rows_torch(A, fac["M32"], seed=5)
+    A = A.numpy()
+    G = ref.gram(A)
+    Gs = copies * ref.gram(fac["M32"])
+    assert np.allclose(G, Gs, rtol=0, atol=1e-14 * np.abs(Gs).max())
+    s = np.linalg.svd(A.astype(np.float64), compute_uv=False)
+    # FP32 rounding of M: |dM| <= 2^-24 |M| per entry
+    assert np.max(np.abs(s - sig)) <= 2.0 ** -24 * np.sqrt(copies) * np.linalg.norm(np.abs(fac["M32"]), 2) * 4
+    lam, Q = np.linalg.eigh(G)
+    for i in (0, 5, 20):
+        assert ref.vector_angle(Q[:, n - 1 - i], fac["V"][:, i]) < 1e-5
+    # every block is a signed row permutation of M
+    for b in range(copies):
+        blk = np.abs(A[b * n:(b + 1) * n])
+        assert np.array_equal(np.sort(blk, axis=0), np.sort(np.abs(fac["M32"]), axis=0))
