@@ -594,6 +594,135 @@ def c4_workload(args):
     print(json.dumps(line), flush=True)
 
 
+def serve_workload(args):
+    """Serving: 10,000 dense t-SVD requests with Poisson arrivals at 2,000 req/s
+    drawn from a pool of 512 matrices (m log-uniform in [512, 65536], n
+    log-uniform in [64, 2048], sigma_i = rho^i with rho ~ U(0.5, 0.95), exact
+    rank where rho^i >= 1e-12), k ~ U{4..32} (capped by min(m, n)), eps = 1e-8,
+    each request with its own start seed.  Latency = completion - submission
+    on the server's clock.  A second pass submits every request at once
+    (capacity, solves/s); the plain per-request path (one tsvd_factor call at a
+    time, FP32 Gram) runs on a sample of the same requests as the baseline.
+    sigma is checked against the closed form rho^i for every request."""
+    import queue
+    import threading
+
+    import torch
+
+    import synth
+    from paper_2208_08410_gb300 import Plan, Server, _binding as B
+    B.load(build_if_missing=True)
+    torch.cuda.set_device(0)
+    n_pool, n_req, rate, eps = args.pool, args.requests, args.rate, 1e-8
+    t0 = time.time()
+    shapes = synth.serving_shapes(n_pool, seed=11)
+    pool = []
+    for i, sh in enumerate(shapes):
+        a = pinned_array((sh["m"], sh["n"]), np.float32)
+        synth.serving_matrix_torch(sh, seed=i, out=a)
+        pool.append(a)
+    torch.cuda.empty_cache()
+    gen_s = time.time() - t0
+    g = np.random.default_rng(12)
+    arrivals = np.cumsum(g.exponential(1.0 / rate, n_req))
+    picks = g.integers(0, n_pool, n_req)
+    ks = np.array([min(int(k), min(shapes[p]["m"], shapes[p]["n"]), shapes[p]["rank"])
+                   for p, k in zip(picks, g.integers(4, 33, n_req))])
+    m_max = max(sh["m"] for sh in shapes)
+    n_max = max(sh["n"] for sh in shapes)
+    slots = 768
+    outU = pinned_array((slots, 32 * m_max), np.float32)
+    outV = pinned_array((slots, 32 * n_max), np.float32)
+    outS = pinned_array((slots, 32), np.float64)
+
+    def run(server, timed_arrivals):
+        free = queue.Queue()
+        for sl in range(slots):
+            free.put(sl)
+        recs = queue.Queue()
+        errs = np.zeros(n_req)
+        lat = np.zeros(n_req)
+        done_t = np.zeros(n_req)
+        sub_t = np.zeros(n_req)
+        status = np.zeros(n_req, dtype=np.int64)
+
+        def collector():
+            for _ in range(n_req):
+                i, t, sl = recs.get()
+                st, info = server.wait(t, 600.0)
+                p, k = picks[i], ks[i]
+                sig = outS[sl, :k].copy()
+                truth = shapes[p]["rho"] ** np.arange(k)
+                errs[i] = float(np.max(np.abs(sig - truth) / truth))
+                lat[i] = info["done_s"] - info["submit_s"]
+                done_t[i], sub_t[i], status[i] = info["done_s"], info["submit_s"], st
+                free.put(sl)
+        th = threading.Thread(target=collector)
+        th.start()
+        start = time.perf_counter()
+        for i in range(n_req):
+            if timed_arrivals:
+                delay = start + arrivals[i] - time.perf_counter()
+                if delay > 0:
+                    time.sleep(delay)
+            sl = free.get()
+            p, k = picks[i], int(ks[i])
+            m, n = shapes[p]["m"], shapes[p]["n"]
+            t = server.submit(pool[p], k, eps, outU[sl, :m * k], outS[sl, :k], outV[sl, :n * k], seed=i)
+            recs.put((i, t, sl))
+        th.join()
+        span = float(done_t.max() - sub_t.min())
+        return {"p50_ms": round(float(np.percentile(lat, 50)) * 1e3, 3),
+                "p99_ms": round(float(np.percentile(lat, 99)) * 1e3, 3),
+                "mean_ms": round(float(lat.mean()) * 1e3, 3), "solves_per_s": round(n_req / span, 1),
+                "span_s": round(span, 3), "sigma_max_rel_err": float("%.3g" % errs.max()),
+                "frac_sigma_err_le_1e-5": float(np.mean(errs <= 1e-5)),
+                "status_counts": {B.STATUS_NAMES[int(c)]: int((status == c).sum()) for c in np.unique(status)}}
+
+    server = Server(device_budget=args.serve_budget << 30, n_streams=4, max_wave=256)
+    server.autotune(iters=30)
+    table = {d: server.cluster_for(d) for d in (64, 128, 256, 512, 1024, 2048)}
+    s0 = server.stats()
+    timed = run(server, True)
+    s1 = server.stats()
+    capacity = run(server, False)
+    s2 = server.stats()
+    server.close()
+    # baseline: the per-request path, one request at a time, FP32 Gram, same requests
+    # (the per-request path takes m >= n only, so the sample skips wide requests)
+    tb, n_tall = 0.0, 0
+    for i in range(min(args.baseline_requests, n_req)):
+        p, k = picks[i], int(ks[i])
+        m, n = shapes[p]["m"], shapes[p]["n"]
+        if m < n:
+            continue
+        torch.cuda.synchronize()
+        ts = time.perf_counter()
+        plan = Plan(pool[p], k, eps, seed=i)
+        plan.factor(pool[p], U=outU[0, :m * k], sigma=outS[0, :k], V=outV[0, :n * k])
+        plan.close()
+        torch.cuda.synchronize()
+        tb += time.perf_counter() - ts
+        n_tall += 1
+    base_rate = n_tall / tb if tb > 0 else None
+    launches = s2["kernel_launches"] - s0["kernel_launches"]
+    line = {"metric": "serve p50/p99 latency at sigma err <= 1e-5 (2,000 req/s Poisson)",
+            "value": timed["p99_ms"], "unit": "ms", "n_gpus": 1, "steps": 1, "warmup": 0,
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"{n_req} dense t-SVD requests, Poisson {rate} req/s, pool of {n_pool}: "
+                                   "m logU[512,65536], n logU[64,2048], sigma_i=rho^i, rho~U(0.5,0.95), "
+                                   "k~U{4..32}, eps=1e-8", "requests": n_req, "rate": rate, "pool": n_pool,
+                       "pool_bytes": int(sum(a.nbytes for a in pool)), "device_budget_gib": args.serve_budget},
+            "latency": timed, "capacity": capacity, "cluster_table": table,
+            "baseline_per_request": {"solves_per_s": round(base_rate, 1) if base_rate else None,
+                                     "requests": n_tall, "path": "tsvd_plan/tsvd_factor per request, FP32 Gram, "
+                                                                 "pinned host A, one at a time"},
+            "speedup_capacity_vs_per_request": round(capacity["solves_per_s"] / base_rate, 2) if base_rate else None,
+            "waves": s2["waves"] - s0["waves"], "gpu_launches": launches,
+            "peak_device_bytes": s2["peak_device_bytes"], "gen_seconds": round(gen_s, 1)}
+    print(json.dumps(line), flush=True)
+
+
 def csr_pair_checks(dcsr, host, m, nnz, peaks, peak_src, args):
     """Full-size measurements of the fused CSR pair (one operator application
     w = A^T (A v), ||A v||^2) on the device-resident matrix:
@@ -739,7 +868,11 @@ def csr_workload(args):
                     "d2h_bytes_per_step": int(reps_e[-1]["d2h_bytes"]),
                     "blocks_per_pass": reps_e[-1]["n_blocks"],
                     "copy_stream_GBps": round(reps_e[-1]["h2d_bytes"] / (reps_e[-1]["h2d_copy_ms"] / 1e3) / 1e9, 2)
-                    if reps_e[-1]["h2d_copy_ms"] else None},
+                    if reps_e[-1]["h2d_copy_ms"] else None,
+                    "copy_min_GBps": round(reps_e[-1]["h2d_copy_min_gbps"], 1),
+                    "copy_max_GBps": round(reps_e[-1]["h2d_copy_max_gbps"], 1),
+                    "pair_kernel_ms_per_step": round(reps_e[-1]["gram_kernel_ms"], 1),
+                    "pair_kernel_launches_per_step": reps_e[-1]["gram_kernel_launches"]},
             "roofline": roofline, "cpu_baseline": cpu, "oom_sweep": sweep,
             "sigma": [round(float(x), 6) for x in res.sigma.cpu().numpy()], "gen_seconds": round(gen_s, 1),
             "gpu_launches": int(sum(r["kernel_launches"] for r in reps))}
@@ -762,7 +895,12 @@ def main():
     ap.add_argument("--case", default="", choices=["", "gram", "power", "csr", "left"],
                     help="single-kernel microbenchmark instead of the t-SVD step")
     ap.add_argument("--n", type=int, default=N_COLS)
-    ap.add_argument("--workload", default="dense", choices=["dense", "csr", "c4"])
+    ap.add_argument("--workload", default="dense", choices=["dense", "csr", "c4", "serve"])
+    ap.add_argument("--pool", type=int, default=512)
+    ap.add_argument("--requests", type=int, default=10_000)
+    ap.add_argument("--rate", type=float, default=2000.0)
+    ap.add_argument("--serve-budget", type=int, default=48, help="server device budget, GiB")
+    ap.add_argument("--baseline-requests", type=int, default=200)
     ap.add_argument("--csr-iters", type=int, default=10)
     ap.add_argument("--sweep", action="store_true", help="CSR: out-of-memory sweep over n_b and q_s")
     args = ap.parse_args()
@@ -774,6 +912,9 @@ def main():
         return
     if args.workload == "c4" and args.impl != "reference":
         c4_workload(args)
+        return
+    if args.workload == "serve" and args.impl != "reference":
+        serve_workload(args)
         return
 
     rank = int(os.environ.get("RANK", "0"))

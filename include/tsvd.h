@@ -125,14 +125,15 @@ typedef struct {
   int32_t flags;            /* TSVD_FLAG_* bits */
   int32_t n_blocks;         /* streamed row blocks per pass over A */
   int32_t mode;             /* 0: A on device, 1: host A made resident, 2: streamed */
-  int32_t gram_kernel_launches; /* Gram kernel launches timed (time_kernels) */
+  int32_t gram_kernel_launches; /* Gram kernel launches (dense) or CSR pair launches
+                                   (sparse) timed (time_kernels) */
   double gram_ms;           /* Gram pass (dense) wall time on the device clock */
   double power_ms;          /* all power iterations */
   double left_ms;           /* U pass */
   double total_ms;
   double h2d_bytes;         /* bytes copied host -> device */
   double d2h_bytes;         /* bytes copied device -> host */
-  double gram_kernel_ms;    /* summed device time of the Gram kernels (time_kernels) */
+  double gram_kernel_ms;    /* summed device time of those launches (time_kernels) */
   int64_t kernel_launches;  /* kernels launched by this call */
   int64_t applications;     /* total operator applications (sum of iters) */
   int32_t ring_slots;       /* row blocks the streaming ring holds (mode 2) */
@@ -351,6 +352,99 @@ TSVD_API tsvd_status tsvd_csr_partition(int64_t m, const int64_t *row_ptr, int64
  * NULL on failure.  Free with tsvd_host_free. */
 TSVD_API tsvd_status tsvd_host_alloc(void **ptr, size_t bytes);
 TSVD_API tsvd_status tsvd_host_free(void *ptr);
+
+/* ------------------------------------------------------------------------ */
+/* Serving: many t-SVD requests of different m, n, k with continuous         */
+/* batching.  No counterpart in the paper (which factors one matrix); each   */
+/* request runs the same method (Alg. 1/2, Hotelling deflation, FP64         */
+/* Rayleigh quotient and convergence test; Eq. 3 when m < n).                */
+/* ------------------------------------------------------------------------ */
+typedef struct tsvd_server_s *tsvd_server_t;
+
+typedef struct {
+  size_t device_budget;   /* HBM the server allocates once and admits requests
+                             into (0: 8 GiB) */
+  int32_t max_inflight;   /* requests admitted at once (0: 4096) */
+  int32_t n_streams;      /* waves in flight at once, one stream each (0: 4) */
+  int32_t max_wave;       /* most requests one wave launches together (0: 512) */
+  int32_t cluster_cap;    /* largest thread-block cluster of the power kernel
+                             (1, 2, 4 or 8; 0: 8) */
+  int32_t reserved[8];
+} tsvd_server_options;
+
+/* Per-request record (tsvd_server_wait / tsvd_server_poll). */
+typedef struct {
+  int32_t status;         /* TSVD_OK, TSVD_ENOCONV, TSVD_ERANK, or an error */
+  int32_t flags;          /* TSVD_FLAG_* */
+  int64_t applications;   /* operator applications over all triplets */
+  double submit_s;        /* server clock (seconds since tsvd_server_create) */
+  double admit_s;         /* admitted into the device budget */
+  double launch_s;        /* its wave was launched */
+  double done_s;          /* its wave's completion was observed */
+  int32_t wave;           /* index of the wave it ran in */
+  int32_t cluster;        /* CTAs of its power-kernel cluster */
+} tsvd_request_info;
+
+typedef struct {
+  int64_t submitted, completed, failed;
+  int64_t waves;               /* waves launched */
+  int64_t kernel_launches;     /* kernels the scheduler launched */
+  int64_t peak_device_bytes;   /* high-water mark of the arena */
+  double busy_s;               /* time with at least one wave in flight */
+} tsvd_server_stats;
+
+TSVD_API tsvd_status tsvd_server_options_init(tsvd_server_options *opt);
+
+/* Allocates the device arena (device_budget bytes, on the current device) and
+ * starts the scheduler thread.  Errors: EINVAL (options), ENOMEM, ECUDA. */
+TSVD_API tsvd_status tsvd_server_create(tsvd_server_t *server, const tsvd_server_options *opt);
+
+/*
+ * Queue one dense request A = U Sigma V^T (truncated to k).
+ *   A        host, m x n FP32 row-major (row stride n); read by an
+ *            asynchronous copy once the request is admitted, so it must stay
+ *            valid and unchanged until the request completes.  Page-locked
+ *            memory (tsvd_host_alloc) lets the copy overlap other work.
+ *   U, sigma, V  host outputs: U m x k and V n x k column-major FP32, sigma k
+ *            FP64; written asynchronously, valid once the request completes.
+ *   k        1 <= k <= min(m, n), k <= 32;  min(m, n) <= 2048
+ *   eps, max_iter, seed, sign_convention  as for tsvd_plan / tsvd_options
+ *            (start draws: the built-in Philox-4x32-10 stream of `seed`)
+ *   ticket   receives the request's id
+ * Requests are admitted first in, first out as the device budget and
+ * max_inflight allow.  Errors: EINVAL (arguments), EBUDGET (the request alone
+ * exceeds the device budget), EUNSUPPORTED (min(m, n) > 2048 or k > 32).
+ */
+TSVD_API tsvd_status tsvd_server_submit(tsvd_server_t server, const float *A, int64_t m, int64_t n, int32_t k,
+                                        double eps, int32_t max_iter, uint64_t seed, int32_t sign_convention,
+                                        float *U, double *sigma, float *V, uint64_t *ticket);
+
+/* Block until the request completes or timeout_s passes (< 0: no limit).
+ * Returns the request's status (TSVD_ETIMEDOUT on timeout) and fills *info.
+ * A completed request's record is released by this call. */
+TSVD_API tsvd_status tsvd_server_wait(tsvd_server_t server, uint64_t ticket, double timeout_s, tsvd_request_info *info);
+
+TSVD_API tsvd_status tsvd_server_get_stats(tsvd_server_t server, tsvd_server_stats *stats);
+
+/* Message of the last failure inside the scheduler ("" if none). */
+TSVD_API const char *tsvd_server_last_error(tsvd_server_t server);
+
+/* Power-kernel cluster size the server uses for Gram dimension d. */
+TSVD_API int32_t tsvd_server_cluster_for(tsvd_server_t server, int64_t d);
+
+/*
+ * Pick the power-kernel cluster size per Gram dimension by measurement: for
+ * d in {64, 128, 256, 512, 1024, 2048} and each cluster size up to
+ * cluster_cap, time `iters` iterations of synthetic requests (as many as fill
+ * the GPU) and keep the size with the highest iterations per second over the
+ * whole GPU.  Call with no requests in flight.  The table is used by later
+ * submissions; tsvd_server_cluster_for reads it.
+ */
+TSVD_API tsvd_status tsvd_server_autotune(tsvd_server_t server, int32_t iters);
+
+/* Stop the scheduler (requests still queued fail with TSVD_ECUDA) and free
+ * the device arena.  NULL is accepted. */
+TSVD_API void tsvd_server_destroy(tsvd_server_t server);
 
 #ifdef __cplusplus
 }

@@ -171,3 +171,69 @@ def tsvd(A, k: int, eps: float, **kw) -> TSVDResult:
         return p.factor(want_u=want_u, ok=ok)
     finally:
         p.close()
+
+
+class Server:
+    """A t-SVD server (continuous batching of many requests on one GPU); see
+    tsvd_server_* in include/tsvd.h.  Inputs and outputs are host arrays the
+    caller keeps alive until the request completes (page-locked ones, e.g. from
+    tsvd_host_alloc, let the copies overlap other work)."""
+
+    def __init__(self, device_budget: int = 8 << 30, max_inflight: int = 0, n_streams: int = 0,
+                 max_wave: int = 0, cluster_cap: int = 0):
+        import torch
+        torch.cuda.init()
+        self.lib = B.load()
+        opt = B.tsvd_server_options()
+        self.lib.tsvd_server_options_init(C.byref(opt))
+        opt.device_budget = int(device_budget)
+        opt.max_inflight = int(max_inflight)
+        opt.n_streams = int(n_streams)
+        opt.max_wave = int(max_wave)
+        opt.cluster_cap = int(cluster_cap)
+        h = C.c_void_p()
+        B.check(self.lib.tsvd_server_create(C.byref(h), C.byref(opt)), "tsvd_server_create")
+        self.handle = h
+        self._keep = {}
+
+    def submit(self, A, k: int, eps: float, U, sigma, V, max_iter: int = 10000, seed: int = 0,
+               sign_convention: bool = False) -> int:
+        m, n = A.shape
+        t = C.c_uint64()
+        B.check(self.lib.tsvd_server_submit(self.handle, _ptr(A), m, n, int(k), float(eps), int(max_iter), int(seed),
+                                            int(bool(sign_convention)), _ptr(U), _ptr(sigma), _ptr(V), C.byref(t)),
+                "tsvd_server_submit")
+        self._keep[t.value] = (A, U, sigma, V)
+        return t.value
+
+    def wait(self, ticket: int, timeout_s: float = -1.0):
+        info = B.tsvd_request_info()
+        st = self.lib.tsvd_server_wait(self.handle, int(ticket), float(timeout_s), C.byref(info))
+        if st != B.TSVD_ETIMEDOUT:
+            self._keep.pop(ticket, None)
+        return st, {f: getattr(info, f) for f, _ in B.tsvd_request_info._fields_}
+
+    def stats(self) -> dict:
+        s = B.tsvd_server_stats()
+        B.check(self.lib.tsvd_server_get_stats(self.handle, C.byref(s)), "tsvd_server_get_stats")
+        return {f: getattr(s, f) for f, _ in B.tsvd_server_stats._fields_}
+
+    def cluster_for(self, d: int) -> int:
+        return int(self.lib.tsvd_server_cluster_for(self.handle, int(d)))
+
+    def autotune(self, iters: int = 50):
+        B.check(self.lib.tsvd_server_autotune(self.handle, int(iters)), "tsvd_server_autotune")
+
+    def last_error(self) -> str:
+        return self.lib.tsvd_server_last_error(self.handle).decode()
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self.lib.tsvd_server_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -46,6 +46,23 @@ class tsvd_report(C.Structure):
                 ("h2d_copy_max_gbps", C.c_double)]
 
 
+class tsvd_server_options(C.Structure):
+    _fields_ = [("device_budget", C.c_size_t), ("max_inflight", C.c_int32), ("n_streams", C.c_int32),
+                ("max_wave", C.c_int32), ("cluster_cap", C.c_int32), ("reserved", C.c_int32 * 8)]
+
+
+class tsvd_request_info(C.Structure):
+    _fields_ = [("status", C.c_int32), ("flags", C.c_int32), ("applications", C.c_int64),
+                ("submit_s", C.c_double), ("admit_s", C.c_double), ("launch_s", C.c_double),
+                ("done_s", C.c_double), ("wave", C.c_int32), ("cluster", C.c_int32)]
+
+
+class tsvd_server_stats(C.Structure):
+    _fields_ = [("submitted", C.c_int64), ("completed", C.c_int64), ("failed", C.c_int64),
+                ("waves", C.c_int64), ("kernel_launches", C.c_int64), ("peak_device_bytes", C.c_int64),
+                ("busy_s", C.c_double)]
+
+
 _P = C.c_void_p
 _I64 = C.c_int64
 _I32 = C.c_int32
@@ -76,6 +93,16 @@ SIGNATURES = {
     "tsvd_csr_partition": (C.c_int, [_I64, _P, _I64, _P, C.POINTER(_I64), C.POINTER(_I64)]),
     "tsvd_host_alloc": (C.c_int, [C.POINTER(_P), _SZ]),
     "tsvd_host_free": (C.c_int, [_P]),
+    "tsvd_server_options_init": (C.c_int, [C.POINTER(tsvd_server_options)]),
+    "tsvd_server_create": (C.c_int, [C.POINTER(_P), C.POINTER(tsvd_server_options)]),
+    "tsvd_server_submit": (C.c_int, [_P, _P, _I64, _I64, _I32, _D, _I32, C.c_uint64, _I32, _P, _P, _P,
+                                     C.POINTER(C.c_uint64)]),
+    "tsvd_server_wait": (C.c_int, [_P, C.c_uint64, _D, C.POINTER(tsvd_request_info)]),
+    "tsvd_server_get_stats": (C.c_int, [_P, C.POINTER(tsvd_server_stats)]),
+    "tsvd_server_last_error": (C.c_char_p, [_P]),
+    "tsvd_server_cluster_for": (_I32, [_P, _I64]),
+    "tsvd_server_autotune": (C.c_int, [_P, _I32]),
+    "tsvd_server_destroy": (None, [_P]),
 }
 
 _lib = None

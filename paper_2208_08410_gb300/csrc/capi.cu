@@ -418,6 +418,8 @@ struct Run {
   int64_t chunk_seq = 0;  // ring position, continues across passes
   int64_t copies = 0;     // timed block copies recorded so far
   std::vector<double> copy_bytes;  // bytes of each timed copy
+  double kernel_ms = 0.0;          // timed operator kernels (CSR pair)
+  int64_t kernel_launches = 0;
 };
 
 // Events around a block copy on the copy stream (only with time_kernels).
@@ -717,12 +719,16 @@ tsvd_status acquire_csr(Run &r, int64_t b, const std::vector<int64_t> &bnd_nnz, 
   float *va = reinterpret_cast<float *>(base + round_up((p->chunk_rows + 1) * 8, 256) +
                                         round_up(std::max<int64_t>(p->max_block_nnz, 1) * 4, 256));
   TSVD_CUDA(cudaStreamWaitEvent(p->copy_stream, p->ev_free[s], 0));
+  TSVD_TRY(copy_event(r, true));
   TSVD_CUDA(cudaMemcpyAsync(rp, A->row_ptr + s0, (size_t)(out->rows + 1) * 8, cudaMemcpyHostToDevice, p->copy_stream));
   if (e1 > e0) {
     TSVD_CUDA(cudaMemcpyAsync(ci, A->col_idx + e0, (size_t)(e1 - e0) * 4, cudaMemcpyHostToDevice, p->copy_stream));
     TSVD_CUDA(cudaMemcpyAsync(va, A->values + e0, (size_t)(e1 - e0) * 4, cudaMemcpyHostToDevice, p->copy_stream));
   }
-  r.h2d += (double)(out->rows + 1) * 8 + (double)(e1 - e0) * 8;
+  TSVD_TRY(copy_event(r, false));
+  const double bytes = (double)(out->rows + 1) * 8 + (double)(e1 - e0) * 8;
+  if (p->opt.time_kernels) r.copy_bytes.push_back(bytes);
+  r.h2d += bytes;
   TSVD_CUDA(cudaEventRecord(p->ev_ready[s], p->copy_stream));
   TSVD_CUDA(cudaStreamWaitEvent(r.cs, p->ev_ready[s], 0));
   out->rp = rp;
@@ -731,14 +737,32 @@ tsvd_status acquire_csr(Run &r, int64_t b, const std::vector<int64_t> &bnd_nnz, 
   return TSVD_OK;
 }
 
-// one application w += A^T (A v), ss += ||A v||^2 over all row blocks
+// one application w += A^T (A v), ss += ||A v||^2 over all row blocks; with
+// time_kernels each block's kernel is bracketed by events (read back by
+// csr_kernel_time once the stream has been synchronised)
 tsvd_status csr_apply(Run &r, const std::vector<int64_t> &bnd, const float *v, float *w, double *ss, int scatter) {
   tsvd_plan_s *p = r.p;
+  const bool timed = p->opt.time_kernels != 0;
   for (int64_t b = 0; b < p->n_chunks; ++b) {
     CsrBlock blk;
     TSVD_TRY(acquire_csr(r, b, bnd, &blk));
+    if (timed) TSVD_CUDA(cudaEventRecord(p->ev_k[2 * b], r.cs));
     TSVD_TRY(launch_csr_pair(blk.rows, p->n, blk.rp, blk.ci, blk.va, v, w, ss, scatter, p->avg_nnz, r.cs));
+    if (timed) TSVD_CUDA(cudaEventRecord(p->ev_k[2 * b + 1], r.cs));
     TSVD_TRY(release_slot(r, blk.slot));
+  }
+  return TSVD_OK;
+}
+
+// adds the durations of the last csr_apply's kernels (the stream must have been synchronised)
+tsvd_status csr_kernel_time(Run &r) {
+  tsvd_plan_s *p = r.p;
+  if (!p->opt.time_kernels) return TSVD_OK;
+  for (int64_t b = 0; b < p->n_chunks; ++b) {
+    float t = 0.f;
+    TSVD_CUDA(cudaEventElapsedTime(&t, p->ev_k[2 * b], p->ev_k[2 * b + 1]));
+    r.kernel_ms += t;
+    ++r.kernel_launches;
   }
   return TSVD_OK;
 }
@@ -764,6 +788,11 @@ tsvd_status factor_csr(Run &r, float *U, double *sigma_out, float *V_out, tsvd_r
   sc.scal = sc.coef + 64 * 2;
   sc.grid = p->vec_grid;
 
+  if (p->opt.time_kernels && (int64_t)p->ev_k.size() < 2 * p->n_chunks) {
+    const size_t have = p->ev_k.size();
+    p->ev_k.resize(2 * p->n_chunks, nullptr);
+    for (size_t i = have; i < p->ev_k.size(); ++i) TSVD_CUDA(cudaEventCreate(&p->ev_k[i]));
+  }
   TSVD_CUDA(cudaEventRecord(p->ev_t[0], r.cs));
   // entry offsets at block boundaries
   std::vector<int64_t> bnd(p->n_chunks + 1);
@@ -820,6 +849,7 @@ tsvd_status factor_csr(Run &r, float *U, double *sigma_out, float *V_out, tsvd_r
                                        sc, 0, r.cs));
       TSVD_CUDA(cudaMemcpyAsync(h, sc.info, 16, cudaMemcpyDeviceToHost, r.cs));
       TSVD_CUDA(cudaStreamSynchronize(r.cs));
+      TSVD_TRY(csr_kernel_time(r));
       if (h[1] == 2) break;  // rank: keep v (= v0 of this step)
       std::swap(v, vn);
       if (h[2]) break;
@@ -846,6 +876,7 @@ tsvd_status factor_csr(Run &r, float *U, double *sigma_out, float *V_out, tsvd_r
     if (host_out) r.d2h += (double)n * 4;
     TSVD_CUDA(cudaMemcpyAsync(&hsig2[l], sig2 + l, 8, cudaMemcpyDeviceToHost, r.cs));
     TSVD_CUDA(cudaStreamSynchronize(r.cs));
+    if (h[1] != 2) TSVD_TRY(csr_kernel_time(r));
     apps += h[0];
     if (rep && rep->iters) rep->iters[l] = h[0];
   }
@@ -895,6 +926,8 @@ tsvd_status factor_csr(Run &r, float *U, double *sigma_out, float *V_out, tsvd_r
     rep->total_ms = (double)t01 + t12 + t23;
     rep->applications = apps;
     rep->flags |= flags;
+    rep->gram_kernel_ms = r.kernel_ms;
+    rep->gram_kernel_launches = (int32_t)r.kernel_launches;
   }
   if (flags & TSVD_FLAG_RANK) return TSVD_ERANK;
   if (flags & TSVD_FLAG_NOCONV) return TSVD_ENOCONV;

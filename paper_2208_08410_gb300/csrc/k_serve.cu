@@ -1,0 +1,573 @@
+// Grouped kernels of the t-SVD server: many small requests per launch.
+//
+// Grouped SYRK (the Gram step of Alg. 2, B = X^T X, for every request of a
+// wave at once; G = A A^T for wide requests, Eq. 3).  One CTA per 64 x 64
+// tile of one request's lower triangle, over that request's whole K range:
+// 32-row slabs of both operand blocks go through shared memory, each thread
+// keeps a 4 x 4 block of FP32 sums, and every 512 rows the FP32 sums are
+// added into FP64 registers.  No atomics, so a request's Gram does not depend
+// on what else is in the wave.  The epilogue writes the tile and its mirror
+// into the FP64 matrix and its FP32 copy.
+//
+// Grouped power (Alg. 1 l.5-13 with Alg. 2 for each triplet, Hotelling
+// deflation).  One thread-block cluster per request; CTA c of C owns rows
+// [c R, (c+1) R) of G (R = ceil(d / C)), kept in shared memory when they fit.
+// An iteration: w = G32 v for the CTA's rows (FP32 products, error-free FP32
+// row sums), the rows of w stored into every CTA's next-iterate buffer and
+// the CTA's partial ||w||^2, v.w, v.v into every CTA's partial slots through
+// distributed shared memory, one cluster barrier, then every CTA adds the C
+// partials in rank order and takes the same decision.  After the loop every
+// CTA holds the whole v_l: sigma_l^2 = v_l^T G64 v_l (FP64, distributed by
+// rows, one more exchange) and the CTA's rows of G32 are deflated by
+// sigma_l^2 v_l v_l^T.
+//
+// Grouped other factor (Alg. 1 l.11-13 / l.15-17): U = A V Sigma^-1 for tall
+// requests, V = A^T U Sigma^-1 for wide ones.
+#include "philox.cuh"
+#include "serve.cuh"
+
+namespace tsvd {
+namespace {
+
+// ---------------------------------------------------------------- grouped SYRK
+__global__ void __launch_bounds__(256) srv_syrk_kernel(const SrvReq *__restrict__ reqs,
+                                                       const SrvTile *__restrict__ tiles) {
+  __shared__ __align__(16) float sI[32][kSrvTile + 4];
+  __shared__ __align__(16) float sJ[32][kSrvTile + 4];
+  const SrvTile t = tiles[blockIdx.x];
+  const SrvReq &q = reqs[t.req];
+  const float *__restrict__ A = q.A;
+  const int64_t ld = q.n;
+  const bool tr = q.trans != 0;
+  const int64_t d = tr ? q.m : q.n, K = tr ? q.n : q.m;
+  const int64_t i0 = (int64_t)t.ti * kSrvTile, j0 = (int64_t)t.tj * kSrvTile;
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  float acc[4][4];
+  double accd[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      acc[a][b] = 0.f;
+      accd[a][b] = 0.0;
+    }
+  int slabs = 0;
+  for (int64_t k0 = 0; k0 < K; k0 += 32) {
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int e = threadIdx.x + 256 * u;  // 0 .. 2047
+      // tall: element (kk, ii) is A[k0 + kk][i0 + ii] (coalesced along ii);
+      // wide: it is A[i0 + ii][k0 + kk] (coalesced along kk)
+      const int kk = tr ? (e & 31) : (e >> 6);
+      const int ii = tr ? (e >> 5) : (e & 63);
+      const int64_t gk = k0 + kk, gi = i0 + ii, gj = j0 + ii;
+      float vi = 0.f, vj = 0.f;
+      if (gk < K) {
+        if (gi < d) vi = tr ? __ldg(A + gi * ld + gk) : __ldg(A + gk * ld + gi);
+        if (gj < d) vj = tr ? __ldg(A + gj * ld + gk) : __ldg(A + gk * ld + gj);
+      }
+      sI[kk][ii] = vi;
+      sJ[kk][ii] = vj;
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int kk = 0; kk < 32; ++kk) {
+      const float4 a = *reinterpret_cast<const float4 *>(&sI[kk][ty * 4]);
+      const float4 b = *reinterpret_cast<const float4 *>(&sJ[kk][tx * 4]);
+      const float av[4] = {a.x, a.y, a.z, a.w}, bv[4] = {b.x, b.y, b.z, b.w};
+#pragma unroll
+      for (int x = 0; x < 4; ++x)
+#pragma unroll
+        for (int y = 0; y < 4; ++y) acc[x][y] = fmaf(av[x], bv[y], acc[x][y]);
+    }
+    __syncthreads();
+    if (++slabs == 16) {  // 512 rows of FP32 sums into FP64
+      slabs = 0;
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+          accd[a][b] += (double)acc[a][b];
+          acc[a][b] = 0.f;
+        }
+    }
+  }
+  double *__restrict__ G64 = q.G64;
+  float *__restrict__ G32 = q.G32;
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      const int64_t i = i0 + ty * 4 + a, j = j0 + tx * 4 + b;
+      if (i < d && j < d) {
+        const double v = accd[a][b] + (double)acc[a][b];
+        G64[i * d + j] = v;
+        G32[i * d + j] = (float)v;
+        if (t.ti != t.tj) {
+          G64[j * d + i] = v;
+          G32[j * d + i] = (float)v;
+        }
+      }
+    }
+}
+
+// ---------------------------------------------------------------- cluster helpers
+__device__ __forceinline__ uint32_t cta_rank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ uint32_t cta_count() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(r));
+  return r;
+}
+// every thread of every CTA of the cluster arrives; release/acquire at cluster scope
+__device__ __forceinline__ void cluster_sync_all() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+__device__ __forceinline__ uint32_t smem_addr(const void *p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ uint32_t peer_addr(uint32_t local, uint32_t rank) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(local), "r"(rank));
+  return r;
+}
+__device__ __forceinline__ void st_peer_f64(uint32_t addr, double v) {
+  asm volatile("st.shared::cluster.f64 [%0], %1;" ::"r"(addr), "d"(v) : "memory");
+}
+
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+  s = a + b;
+  const float bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
+__device__ __forceinline__ void warp_sum_pair(float &hi, float &lo) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const float ho = __shfl_xor_sync(0xffffffffu, hi, o);
+    const float lo2 = __shfl_xor_sync(0xffffffffu, lo, o);
+    float s, e;
+    two_sum(hi, ho, s, e);
+    hi = s;
+    lo = lo + lo2 + e;
+  }
+}
+
+constexpr int kMaxCluster = 8;
+constexpr int kPartSlot = 4;  // doubles per (parity, rank) slot
+
+struct PowerSmem {
+  float *vb[2];    // d (padded) each: the iterate, scaled in place at the start of an iteration
+  double *part;    // [2][kMaxCluster][kPartSlot]
+  double *xs;      // d: FP64 start draws, then v_l
+  float *Gs;       // R x d rows of G32 (resident mode)
+};
+
+__device__ __forceinline__ int64_t pad4(int64_t x) { return (x + 3) & ~int64_t(3); }
+
+// ---------------------------------------------------------------- grouped power
+__global__ void __launch_bounds__(kSrvPowerThreads, 1) srv_power_kernel(const SrvReq *__restrict__ reqs) {
+  extern __shared__ __align__(16) unsigned char srv_smem[];
+  __shared__ double wred[3 * (kSrvPowerThreads / 32)];
+  __shared__ double red[33];
+  __shared__ double s_scal[4];
+  const uint32_t C = cta_count(), rank = cta_rank();
+  const SrvReq &q = reqs[blockIdx.x / C];
+  const int64_t d = q.trans ? q.m : q.n;
+  const int k = q.k;
+  const int64_t R = srv_rows_per_cta(d, C);  // a multiple of 4, so every CTA's row range starts 16-byte aligned
+  const int64_t r0 = min(d, (int64_t)rank * R), r1 = min(d, r0 + R);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = kSrvPowerThreads / 32;
+  const int64_t dp = pad4(d);
+  PowerSmem sm;
+  sm.vb[0] = reinterpret_cast<float *>(srv_smem);
+  sm.vb[1] = sm.vb[0] + dp;
+  sm.part = reinterpret_cast<double *>(sm.vb[1] + dp);
+  sm.xs = sm.part + 2 * kMaxCluster * kPartSlot;
+  sm.Gs = reinterpret_cast<float *>(sm.xs + dp);
+  const bool res = q.resident != 0;
+  float *Grow0 = res ? sm.Gs : q.G32 + r0 * d;  // row r of this CTA at Grow0 + (r - r0) * d
+  if (res) {
+    for (int64_t e = threadIdx.x; e < (r1 - r0) * d; e += kSrvPowerThreads) sm.Gs[e] = q.G32[r0 * d + e];
+  }
+  __syncthreads();
+  uint32_t phase = 0;  // running count of cluster exchanges (selects the partial slots)
+  const bool vec = (d % 4) == 0;
+  double sig0sq = 1.0;  // sigma_0^2 (every CTA forms the same value)
+
+  for (int l = 0; l < k; ++l) {
+    // ---- start vector x ~ N(0,1)^d (every CTA draws all of it), v0 = x / ||x||
+    for (int64_t p = threadIdx.x; p < (d + 1) / 2; p += kSrvPowerThreads) {
+      double z0, z1;
+      start_normal_pair(q.key0, q.key1, (uint32_t)l, p, &z0, &z1);
+      sm.xs[2 * p] = z0;
+      if (2 * p + 1 < d) sm.xs[2 * p + 1] = z1;
+    }
+    __syncthreads();
+    double xx = 0.0;
+    for (int64_t i = threadIdx.x; i < d; i += kSrvPowerThreads) xx += sm.xs[i] * sm.xs[i];
+    xx = block_sum(xx, red);
+    const double inv = xx > 0.0 ? 1.0 / sqrt(xx) : 0.0;
+    for (int64_t i = threadIdx.x; i < d; i += kSrvPowerThreads) sm.vb[0][i] = (float)(sm.xs[i] * inv);
+    const double rank_scale = l == 0 ? 1.0 : sig0sq;
+    int cur = 0, it = 0, status = 0;
+    double vscale = 1.0;  // the iterate in vb[cur] times vscale is v0
+    for (;;) {
+      __syncthreads();
+      if (it > 0) {
+        const float sc = (float)vscale;
+        for (int64_t i = threadIdx.x; i < d; i += kSrvPowerThreads) sm.vb[cur][i] *= sc;
+        __syncthreads();
+      }
+      const float *v = sm.vb[cur];
+      float *nxt = sm.vb[cur ^ 1];
+      double ww = 0.0, vw = 0.0, vv = 0.0;
+      for (int64_t r = r0 + warp; r < r1; r += nwarps) {
+        const float *g = Grow0 + (r - r0) * d;
+        float p0 = 0.f, p1 = 0.f, p2 = 0.f, p3 = 0.f;
+        if (vec) {
+          const float4 *g4 = reinterpret_cast<const float4 *>(g);
+          const float4 *v4 = reinterpret_cast<const float4 *>(v);
+          for (int64_t c = lane; c < d / 4; c += 32) {
+            const float4 a = g4[c], b = v4[c];
+            p0 = fmaf(a.x, b.x, p0);
+            p1 = fmaf(a.y, b.y, p1);
+            p2 = fmaf(a.z, b.z, p2);
+            p3 = fmaf(a.w, b.w, p3);
+          }
+        } else {
+          for (int64_t c = lane; c < d; c += 32) p0 = fmaf(g[c], v[c], p0);
+        }
+        float h, e, sa, ea, sb, eb;
+        two_sum(p0, p1, sa, ea);
+        two_sum(p2, p3, sb, eb);
+        two_sum(sa, sb, h, e);
+        e += ea + eb;
+        warp_sum_pair(h, e);
+        if (lane == 0) {
+          const double t = (double)(float)((double)h + (double)e);
+          const double vr = (double)v[r];
+          ww += t * t;
+          vw += vr * t;
+          vv += vr * vr;
+          nxt[r] = (float)t;
+        }
+      }
+      if (lane == 0) {
+        wred[3 * warp] = ww;
+        wred[3 * warp + 1] = vw;
+        wred[3 * warp + 2] = vv;
+      }
+      __syncthreads();
+      // this CTA's rows of w into the same place of every other CTA's next iterate
+      if (C > 1) {
+        const uint32_t base = smem_addr(nxt + r0);
+        const int64_t n4 = (r1 - r0 + 3) / 4;  // r0 is a multiple of 4; the tail stays inside the padding
+        for (int64_t e = threadIdx.x; e < n4 * (C - 1); e += kSrvPowerThreads) {
+          const uint32_t c = (uint32_t)(e / n4);
+          const uint32_t peer = c >= rank ? c + 1 : c;
+          const int64_t q4 = e % n4;
+          const float4 x = reinterpret_cast<const float4 *>(nxt + r0)[q4];
+          const uint32_t pa = peer_addr(base + 16 * (uint32_t)q4, peer);
+          asm volatile("st.shared::cluster.v4.f32 [%0], {%1, %2, %3, %4};" ::"r"(pa), "f"(x.x), "f"(x.y), "f"(x.z),
+                       "f"(x.w)
+                       : "memory");
+        }
+      }
+      const int par = (int)(phase & 1u);
+      if (threadIdx.x == 0) {
+        double t0 = 0.0, t1 = 0.0, t2 = 0.0;
+        for (int w = 0; w < nwarps; ++w) {
+          t0 += wred[3 * w];
+          t1 += wred[3 * w + 1];
+          t2 += wred[3 * w + 2];
+        }
+        const uint32_t slot = smem_addr(sm.part + (par * kMaxCluster + rank) * kPartSlot);
+        for (uint32_t c = 0; c < C; ++c) {
+          const uint32_t pa = peer_addr(slot, c);
+          st_peer_f64(pa, t0);
+          st_peer_f64(pa + 8, t1);
+          st_peer_f64(pa + 16, t2);
+        }
+      }
+      cluster_sync_all();
+      ++phase;
+      if (threadIdx.x == 0) {
+        double t0 = 0.0, t1 = 0.0, t2 = 0.0;
+        for (uint32_t c = 0; c < C; ++c) {
+          const double *s = sm.part + (par * kMaxCluster + c) * kPartSlot;
+          t0 += s[0];
+          t1 += s[1];
+          t2 += s[2];
+        }
+        const int it1 = it + 1;
+        const double nw = sqrt(t0);
+        int st = 0, done = 0;
+        double sc = 0.0;
+        if (!(nw > 1e-30 * rank_scale)) {
+          st = 2;
+          done = 1;
+        } else {
+          sc = 1.0 / nw;
+          const double cosv = fabs(t1) / (nw * sqrt(t2));
+          done = cosv >= 1.0 - q.eps;
+          if (!done && it1 >= q.max_iter) {
+            done = 1;
+            st = 1;
+          }
+        }
+        s_scal[0] = sc;
+        s_scal[1] = (double)st;
+        s_scal[2] = (double)done;
+      }
+      __syncthreads();
+      ++it;
+      const int st = (int)s_scal[1];
+      const bool done = s_scal[2] != 0.0;
+      if (st == 2) {
+        status = 2;  // vb[cur] still holds v0 of this step
+        break;
+      }
+      vscale = s_scal[0];
+      cur ^= 1;
+      if (done) {
+        status = st;
+        break;
+      }
+    }
+    // ---- v_l (FP64, whole vector, every CTA)
+    __syncthreads();
+    if (status == 2) {
+      for (int64_t i = threadIdx.x; i < d; i += kSrvPowerThreads) sm.xs[i] = (double)sm.vb[cur][i];
+      for (int pass = 0; pass < 2; ++pass) {
+        for (int j = 0; j < l; ++j) {
+          const double *vj = q.V64 + (int64_t)j * d;
+          double c = 0.0;
+          for (int64_t i = threadIdx.x; i < d; i += kSrvPowerThreads) c += vj[i] * sm.xs[i];
+          c = block_sum(c, red);
+          for (int64_t i = threadIdx.x; i < d; i += kSrvPowerThreads) sm.xs[i] -= c * vj[i];
+          __syncthreads();
+        }
+        double nn = 0.0;
+        for (int64_t i = threadIdx.x; i < d; i += kSrvPowerThreads) nn += sm.xs[i] * sm.xs[i];
+        nn = block_sum(nn, red);
+        const double sc = nn > 0.0 ? 1.0 / sqrt(nn) : 0.0;
+        for (int64_t i = threadIdx.x; i < d; i += kSrvPowerThreads) sm.xs[i] *= sc;
+        __syncthreads();
+      }
+    } else {
+      for (int64_t i = threadIdx.x; i < d; i += kSrvPowerThreads) sm.xs[i] = (double)sm.vb[cur][i] * vscale;
+    }
+    __syncthreads();
+    if (q.sign_convention) {
+      // largest |v_i| positive, lowest index on ties (same scan in every CTA)
+      if (threadIdx.x == 0) {
+        double best = -1.0;
+        int64_t bi = 0;
+        for (int64_t i = 0; i < d; ++i) {
+          const double a = fabs(sm.xs[i]);
+          if (a > best) {
+            best = a;
+            bi = i;
+          }
+        }
+        s_scal[3] = sm.xs[bi] < 0.0 ? -1.0 : 1.0;
+      }
+      __syncthreads();
+      const double sg = s_scal[3];
+      for (int64_t i = threadIdx.x; i < d; i += kSrvPowerThreads) sm.xs[i] *= sg;
+      __syncthreads();
+    }
+    // ---- sigma_l^2 = v_l^T G64 v_l over this CTA's rows, exchanged like the partials
+    double qv = 0.0;
+    if (status != 2) {
+      for (int64_t r = r0 + warp; r < r1; r += nwarps) {
+        const double *g = q.G64 + r * d;
+        double t = 0.0;
+        for (int64_t c = lane; c < d; c += 32) t += g[c] * sm.xs[c];
+        t = warp_sum(t);
+        if (lane == 0) qv += t * sm.xs[r];
+      }
+    }
+    qv = block_sum(qv, red);
+    const int par = (int)(phase & 1u);
+    if (threadIdx.x == 0) {
+      const uint32_t slot = smem_addr(sm.part + (par * kMaxCluster + rank) * kPartSlot);
+      for (uint32_t c = 0; c < C; ++c) st_peer_f64(peer_addr(slot, c), qv);
+    }
+    cluster_sync_all();
+    ++phase;
+    double s2 = 0.0;
+    for (uint32_t c = 0; c < C; ++c) s2 += sm.part[(par * kMaxCluster + c) * kPartSlot];
+    s2 = status == 2 ? 0.0 : fmax(s2, 0.0);
+    if (l == 0) sig0sq = s2;
+    // ---- outputs of triplet l (each CTA its rows; rank 0 the scalars)
+    for (int64_t r = r0 + threadIdx.x; r < r1; r += kSrvPowerThreads) {
+      q.V64[(int64_t)l * d + r] = sm.xs[r];
+      q.vout[(int64_t)l * d + r] = (float)sm.xs[r];
+    }
+    if (rank == 0 && threadIdx.x == 0) {
+      q.sig2[l] = s2;
+      q.sigma[l] = sqrt(s2);
+      q.info[4 * l] = it;
+      q.info[4 * l + 1] = status;
+      q.info[4 * l + 2] = 0;
+      q.info[4 * l + 3] = 0;
+    }
+    // ---- Hotelling deflation of this CTA's rows of the FP32 copy
+    if (l + 1 < k && status != 2) {
+      for (int64_t r = r0 + warp; r < r1; r += nwarps) {
+        float *g = Grow0 + (r - r0) * d;
+        const float ci = (float)(s2 * sm.xs[r]);
+        for (int64_t c = lane; c < d; c += 32) g[c] = fmaf(-ci, (float)sm.xs[c], g[c]);
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------- grouped other factor
+// tall (trans 0): block = 16 rows of U, warp w handles rows 2w and 2w+1; a
+//                 128-column slab of V (l-major) is staged in shared memory
+// wide (trans 1): block = 128 columns of V; thread t handles column
+//                 128 b + (t & 127) and half of the k outputs (t >> 7)
+__global__ void __launch_bounds__(256) srv_other_kernel(const SrvReq *__restrict__ reqs,
+                                                        const SrvOtherItem *__restrict__ items) {
+  __shared__ float sv[kSrvMaxK * 128];
+  const SrvOtherItem it = items[blockIdx.x];
+  const SrvReq &q = reqs[it.req];
+  const int k = q.k;
+  const int64_t m = q.m, n = q.n;
+  const float *__restrict__ A = q.A;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (!q.trans) {
+    // U[r][l] = sum_j A[r][j] V[j][l] / sigma_l; V = vout (n x k)
+    const int64_t rbase = (int64_t)it.block * kSrvOtherRows;
+    float acc[2][kSrvMaxK];
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+      for (int l = 0; l < kSrvMaxK; ++l) acc[a][l] = 0.f;
+    for (int64_t j0 = 0; j0 < n; j0 += 128) {
+      __syncthreads();
+      for (int e = threadIdx.x; e < 128 * kSrvMaxK; e += 256) {
+        const int l = e >> 7, jj = e & 127;  // sv[l][jj]
+        sv[e] = (j0 + jj < n && l < k) ? q.vout[(int64_t)l * n + j0 + jj] : 0.f;
+      }
+      __syncthreads();
+#pragma unroll
+      for (int a = 0; a < 2; ++a) {
+        const int64_t r = rbase + warp * 2 + a;
+        if (r >= m) continue;
+#pragma unroll
+        for (int h = 0; h < 4; ++h) {
+          const int jj = lane + 32 * h;
+          const float x = (j0 + jj < n) ? __ldg(A + r * n + j0 + jj) : 0.f;
+#pragma unroll
+          for (int l = 0; l < kSrvMaxK; ++l) acc[a][l] = fmaf(x, sv[l * 128 + jj], acc[a][l]);
+        }
+      }
+    }
+#pragma unroll
+    for (int a = 0; a < 2; ++a) {
+      const int64_t r = rbase + warp * 2 + a;
+      float mine = 0.f;
+#pragma unroll
+      for (int l = 0; l < kSrvMaxK; ++l) {
+        const float s = warp_sumf(acc[a][l]);
+        mine = (lane == l) ? s : mine;
+      }
+      if (r < m && lane < k) {
+        const double sg = q.sigma[lane];
+        q.other[(int64_t)lane * m + r] = sg > 0.0 ? (float)((double)mine / sg) : 0.f;
+      }
+    }
+  } else {
+    // V[j][l] = sum_r A[r][j] U[r][l] / sigma_l; U = vout (m x k), staged row-major sv[rr][l]
+    const int64_t j = (int64_t)it.block * 128 + (threadIdx.x & 127);
+    const int half = threadIdx.x >> 7;
+    float acc[kSrvMaxK / 2];
+#pragma unroll
+    for (int l = 0; l < kSrvMaxK / 2; ++l) acc[l] = 0.f;
+    for (int64_t rb = 0; rb < m; rb += 128) {
+      __syncthreads();
+      for (int e = threadIdx.x; e < 128 * kSrvMaxK; e += 256) {
+        const int rr = e / kSrvMaxK, l = e % kSrvMaxK;
+        sv[e] = (rb + rr < m && l < k) ? q.vout[(int64_t)l * m + rb + rr] : 0.f;
+      }
+      __syncthreads();
+      const int64_t rn = min((int64_t)128, m - rb);
+      for (int64_t rr = 0; rr < rn; ++rr) {
+        const float x = j < n ? __ldg(A + (rb + rr) * n + j) : 0.f;
+        const float *ur = sv + rr * kSrvMaxK + half * (kSrvMaxK / 2);  // same address across the warp
+#pragma unroll
+        for (int l = 0; l < kSrvMaxK / 2; ++l) acc[l] = fmaf(x, ur[l], acc[l]);
+      }
+    }
+    if (j < n) {
+#pragma unroll
+      for (int l = 0; l < kSrvMaxK / 2; ++l) {
+        const int lg = half * (kSrvMaxK / 2) + l;
+        if (lg < k) {
+          const double sg = q.sigma[lg];
+          q.other[(int64_t)lg * n + j] = sg > 0.0 ? (float)((double)acc[l] / sg) : 0.f;
+        }
+      }
+    }
+  }
+}
+
+}  // namespace
+
+size_t srv_power_smem(int64_t d, int cluster, int resident) {
+  const int64_t dp = (d + 3) & ~int64_t(3);
+  size_t b = 2 * dp * 4 + 2 * kMaxCluster * kPartSlot * 8 + dp * 8;
+  if (resident) b += (size_t)srv_rows_per_cta(d, cluster) * d * 4;
+  return b;
+}
+
+tsvd_status launch_srv_syrk(const SrvReq *reqs, const SrvTile *tiles, int n_tiles, cudaStream_t stream) {
+  if (n_tiles <= 0) return TSVD_OK;
+  srv_syrk_kernel<<<n_tiles, 256, 0, stream>>>(reqs, tiles);
+  TSVD_LAUNCHED();
+  return TSVD_OK;
+}
+
+tsvd_status launch_srv_power(const SrvReq *reqs, int n_reqs, int cluster, size_t smem, cudaStream_t stream) {
+  if (n_reqs <= 0) return TSVD_OK;
+  if (cluster < 1 || cluster > kMaxCluster || (cluster & (cluster - 1))) return TSVD_EINVAL;
+  DeviceInfo di;
+  TSVD_TRY(device_info(&di));
+  if (smem > di.smem_optin) return TSVD_EINVAL;
+  static thread_local size_t attr = 0;
+  if (smem > 48 * 1024 && smem > attr) {
+    TSVD_CUDA(cudaFuncSetAttribute(srv_power_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    attr = smem;
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(n_reqs * cluster));
+  cfg.blockDim = dim3(kSrvPowerThreads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = stream;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = (unsigned)cluster;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  TSVD_CUDA(cudaLaunchKernelEx(&cfg, srv_power_kernel, reqs));
+  TSVD_LAUNCHED();
+  return TSVD_OK;
+}
+
+tsvd_status launch_srv_other(const SrvReq *reqs, const SrvOtherItem *items, int n_items, cudaStream_t stream) {
+  if (n_items <= 0) return TSVD_OK;
+  srv_other_kernel<<<n_items, 256, 0, stream>>>(reqs, items);
+  TSVD_LAUNCHED();
+  return TSVD_OK;
+}
+
+}  // namespace tsvd

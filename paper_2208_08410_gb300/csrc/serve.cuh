@@ -1,0 +1,72 @@
+// Grouped kernels of the t-SVD server (internal header).
+//
+// A wave of requests runs as three grouped launches, each over all requests of
+// the wave at once:
+//   1. grouped SYRK: every 64 x 64 tile of every request's Gram matrix
+//      (G = A^T A when m >= n, G = A A^T when m < n: Eq. 3), written as the
+//      symmetric FP64 matrix and its FP32 copy;
+//   2. grouped power: one thread-block cluster per request runs Alg. 1/2 for
+//      all k triplets (Hotelling deflation of the FP32 copy, FP64 Rayleigh
+//      quotient and convergence test);
+//   3. grouped other factor: U = A V Sigma^-1 (m >= n) or V = A^T U Sigma^-1
+//      (m < n), Alg. 1 l.11-13 / l.15-17.
+#pragma once
+
+#include <stdint.h>
+
+#include "common.cuh"
+
+namespace tsvd {
+
+// One request as the device sees it (all pointers are device memory).
+struct SrvReq {
+  const float *A;    // m x n, row-major, row stride n
+  int64_t m, n;
+  int32_t trans;     // 0: d = n, G = A^T A;  1: d = m, G = A A^T
+  int32_t k;
+  double *G64;       // d x d, full symmetric, row-major
+  float *G32;        // d x d FP32 copy (deflated in place triplet by triplet)
+  double *V64;       // d x k column-major: the power method's vectors
+  double *sig2;      // k
+  int32_t *info;     // 4 per triplet: applications, status (0 ok, 1 no convergence, 2 rank), 0, 0
+  float *vout;       // d x k column-major FP32 copy of V64
+  float *other;      // trans 0: U (m x k), trans 1: V (n x k); column-major
+  double *sigma;     // k
+  double eps;
+  int32_t max_iter;
+  int32_t sign_convention;
+  uint32_t key0, key1;  // Philox key of the start draws (splitmix64 of the seed)
+  int32_t cluster;      // CTAs that run this request's power method (1, 2, 4, 8)
+  int32_t resident;     // 1: the power kernel keeps the CTA's rows of G32 in shared memory
+};
+
+// Work item of the grouped SYRK: request, tile row, tile column (ti >= tj).
+struct SrvTile {
+  int32_t req, ti, tj, pad;
+};
+
+constexpr int kSrvTile = 64;         // SYRK tile edge
+constexpr int kSrvMaxDim = 2048;     // largest d the cluster power kernel takes
+constexpr int kSrvMaxK = 32;         // largest k
+constexpr int kSrvPowerThreads = 256;
+constexpr int kSrvOtherRows = 16;     // rows of U per block of the tall other-factor kernel
+constexpr int kSrvOtherCols = 128;    // columns of V per block of the wide one
+
+// rows of G each CTA of a cluster owns: ceil(d / cluster) rounded up to 4
+__host__ __device__ inline int64_t srv_rows_per_cta(int64_t d, int64_t cluster) {
+  return ((d + cluster - 1) / cluster + 3) & ~int64_t(3);
+}
+
+// Dynamic shared memory of the power kernel for (d, cluster, resident).
+size_t srv_power_smem(int64_t d, int cluster, int resident);
+
+tsvd_status launch_srv_syrk(const SrvReq *reqs, const SrvTile *tiles, int n_tiles, cudaStream_t stream);
+// All requests of one launch share the cluster size; `smem` covers the largest.
+tsvd_status launch_srv_power(const SrvReq *reqs, int n_reqs, int cluster, size_t smem, cudaStream_t stream);
+// Work items: (request, 16-row block of U) or (request, 128-column block of V).
+struct SrvOtherItem {
+  int32_t req, block;
+};
+tsvd_status launch_srv_other(const SrvReq *reqs, const SrvOtherItem *items, int n_items, cudaStream_t stream);
+
+}  // namespace tsvd

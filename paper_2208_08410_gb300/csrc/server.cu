@@ -1,0 +1,697 @@
+// t-SVD server: continuous batching of many small requests on one GPU.
+//
+// The server owns one device arena (the HBM budget), a scheduler thread and
+// `n_streams` CUDA streams.  Requests are admitted first in, first out while
+// the arena and the in-flight limit allow.  Admitted requests are launched in
+// waves: a wave takes up to `max_wave` of them, copies their matrices in,
+// runs the three grouped launches of serve.cuh over all of them (one power
+// launch per cluster size) and copies the results out, all on one stream, and
+// ends with an event.  Waves on different streams overlap on the device, so
+// requests that arrive while others run are admitted as memory frees up and
+// start without waiting for the running waves.  The scheduler polls the
+// events, completes the requests of finished waves and releases their memory.
+#include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "philox.cuh"
+#include "serve.cuh"
+
+namespace tsvd {
+namespace {
+
+constexpr size_t kAlign = 256;
+inline size_t al(size_t x) { return (x + kAlign - 1) & ~(kAlign - 1); }
+
+// First-fit allocator over one device allocation; free ranges are kept by
+// offset and merged with their neighbours on release.
+class Arena {
+ public:
+  unsigned char *base = nullptr;
+  size_t size = 0, used = 0, peak = 0;
+  std::map<size_t, size_t> free_;  // offset -> bytes
+
+  tsvd_status init(size_t bytes) {
+    bytes = bytes & ~(kAlign - 1);
+    if (cudaMalloc(&base, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      set_error_text("server: cudaMalloc of the device budget failed");
+      return TSVD_ENOMEM;
+    }
+    size = bytes;
+    free_[0] = bytes;
+    return TSVD_OK;
+  }
+  bool alloc(size_t bytes, size_t *off) {
+    bytes = al(std::max<size_t>(bytes, 1));
+    for (auto it = free_.begin(); it != free_.end(); ++it) {
+      if (it->second >= bytes) {
+        *off = it->first;
+        const size_t rest = it->second - bytes, o = it->first + bytes;
+        free_.erase(it);
+        if (rest) free_[o] = rest;
+        used += bytes;
+        peak = std::max(peak, used);
+        return true;
+      }
+    }
+    return false;
+  }
+  void release(size_t off, size_t bytes) {
+    bytes = al(std::max<size_t>(bytes, 1));
+    used -= bytes;
+    auto it = free_.emplace(off, bytes).first;
+    auto nx = std::next(it);
+    if (nx != free_.end() && it->first + it->second == nx->first) {
+      it->second += nx->second;
+      free_.erase(nx);
+    }
+    if (it != free_.begin()) {
+      auto pv = std::prev(it);
+      if (pv->first + pv->second == it->first) {
+        pv->second += it->second;
+        free_.erase(it);
+      }
+    }
+  }
+  void destroy() {
+    if (base) cudaFree(base);
+    base = nullptr;
+  }
+};
+
+struct Request {
+  uint64_t id = 0;
+  const float *A = nullptr;
+  int64_t m = 0, n = 0;
+  int32_t k = 0;
+  double eps = 0.0;
+  int32_t max_iter = 0;
+  uint64_t seed = 0;
+  int32_t sign = 0;
+  float *U = nullptr;
+  double *sigma = nullptr;
+  float *V = nullptr;
+  size_t off = 0, bytes = 0;  // arena region
+  SrvReq dq{};
+  bool done = false;
+  tsvd_request_info rec{};
+};
+using ReqPtr = std::shared_ptr<Request>;
+
+// device region of one request: A, G64, G32, V64, sig2, info, vout, other, sigma
+size_t request_bytes(int64_t m, int64_t n, int64_t k) {
+  const int64_t d = std::min(m, n), od = std::max(m, n);
+  return al(m * n * 4) + al(d * d * 8) + al(d * d * 4) + al(d * k * 8) + al(k * 8) + al(k * 16) + al(d * k * 4) +
+         al(od * k * 4) + al(k * 8);
+}
+
+void carve(Request &r, unsigned char *p) {
+  const int64_t m = r.m, n = r.n, k = r.k;
+  const int64_t d = std::min(m, n), od = std::max(m, n);
+  SrvReq &q = r.dq;
+  q.A = reinterpret_cast<const float *>(p);
+  p += al(m * n * 4);
+  q.G64 = reinterpret_cast<double *>(p);
+  p += al(d * d * 8);
+  q.G32 = reinterpret_cast<float *>(p);
+  p += al(d * d * 4);
+  q.V64 = reinterpret_cast<double *>(p);
+  p += al(d * k * 8);
+  q.sig2 = reinterpret_cast<double *>(p);
+  p += al(k * 8);
+  q.info = reinterpret_cast<int32_t *>(p);
+  p += al(k * 16);
+  q.vout = reinterpret_cast<float *>(p);
+  p += al(d * k * 4);
+  q.other = reinterpret_cast<float *>(p);
+  p += al(od * k * 4);
+  q.sigma = reinterpret_cast<double *>(p);
+  q.m = m;
+  q.n = n;
+  q.trans = m < n ? 1 : 0;  // Eq. 3: the left vectors from A A^T when m < n
+  q.k = (int32_t)k;
+  q.eps = r.eps;
+  q.max_iter = r.max_iter;
+  q.sign_convention = r.sign;
+  const uint64_t key = splitmix64(r.seed);
+  q.key0 = (uint32_t)key;
+  q.key1 = (uint32_t)(key >> 32);
+}
+
+struct Slot {  // one stream and the pinned staging of the wave it runs
+  cudaStream_t stream = nullptr;
+  cudaEvent_t done = nullptr;
+  unsigned char *stage = nullptr;  // pinned: descriptors, then info of every request
+  size_t stage_cap = 0;
+  bool busy = false;
+  std::vector<ReqPtr> reqs;
+  size_t dev_off = 0, dev_bytes = 0;  // descriptor arrays in the arena
+  size_t info_off = 0;                // offset of the info area in stage
+  double launched_s = 0.0;
+  int64_t wave = 0;
+};
+
+}  // namespace
+
+}  // namespace tsvd
+
+struct tsvd_server_s {
+  tsvd_server_options opt{};
+  int device = 0;
+  tsvd::Arena arena;
+  std::vector<tsvd::Slot> slots;
+  std::mutex mu;
+  std::condition_variable cv_done, cv_work;
+  std::deque<tsvd::ReqPtr> pending;                     // submitted, not admitted
+  std::deque<tsvd::ReqPtr> admitted;                    // in the arena, not launched
+  std::unordered_map<uint64_t, tsvd::ReqPtr> table;     // every request not yet waited for
+  uint64_t next_id = 1;
+  int64_t inflight = 0;                                 // admitted and not completed
+  bool stop = false;
+  std::thread thr;
+  std::chrono::steady_clock::time_point t0;
+  tsvd_server_stats stats{};
+  std::string err;
+  int32_t cluster_table[6] = {1, 1, 2, 4, 8, 8};        // d <= 64, 128, 256, 512, 1024, 2048
+  double busy_since = -1.0;
+
+  double now() const {
+    return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  }
+};
+
+namespace tsvd {
+namespace {
+
+int bucket_of(int64_t d) {
+  int b = 0;
+  for (int64_t lim = 64; b < 5 && d > lim; lim *= 2) ++b;
+  return b;
+}
+
+int cluster_for(const tsvd_server_s *s, int64_t d) {
+  int c = s->cluster_table[bucket_of(d)];
+  c = std::min(c, s->opt.cluster_cap);
+  while (c > 1 && srv_rows_per_cta(d, c) * (c - 1) >= d) c >>= 1;  // no CTA of the cluster without rows
+  return std::max(c, 1);
+}
+
+size_t power_smem_budget() {
+  DeviceInfo di;
+  if (device_info(&di) != TSVD_OK) return 48 * 1024;
+  return di.smem_optin > 2048 ? di.smem_optin - 2048 : di.smem_optin;  // room for the static arrays
+}
+
+// Build and enqueue one wave on slot `s` (scheduler thread, lock not held).
+tsvd_status launch_wave(tsvd_server_s *sv, Slot &s) {
+  std::vector<ReqPtr> &rs = s.reqs;
+  s.dev_bytes = 0;  // nothing of this wave in the arena yet
+  const size_t smem_cap = power_smem_budget();
+  for (auto &r : rs) {
+    const int64_t d = std::min(r->m, r->n);
+    r->dq.cluster = cluster_for(sv, d);
+    r->dq.resident = srv_power_smem(d, r->dq.cluster, 1) <= smem_cap ? 1 : 0;
+  }
+  // requests of one power launch share the cluster size and residency: sort by them
+  std::stable_sort(rs.begin(), rs.end(), [](const ReqPtr &a, const ReqPtr &b) {
+    return std::make_pair(a->dq.cluster, a->dq.resident) < std::make_pair(b->dq.cluster, b->dq.resident);
+  });
+  std::vector<SrvTile> tiles;
+  std::vector<SrvOtherItem> items;
+  std::vector<int64_t> tile_cost;
+  for (size_t i = 0; i < rs.size(); ++i) {
+    const Request &r = *rs[i];
+    const int64_t d = std::min(r.m, r.n), K = std::max(r.m, r.n);
+    const int T = (int)ceil_div(d, kSrvTile);
+    for (int ti = 0; ti < T; ++ti)
+      for (int tj = 0; tj <= ti; ++tj) {
+        tiles.push_back({(int32_t)i, ti, tj, 0});
+        tile_cost.push_back(K);
+      }
+    const int64_t nb = r.m >= r.n ? ceil_div(r.m, kSrvOtherRows) : ceil_div(r.n, kSrvOtherCols);
+    for (int64_t b = 0; b < nb; ++b) items.push_back({(int32_t)i, (int32_t)b});
+  }
+  // longest tiles first, so the tail of the launch is short
+  {
+    std::vector<size_t> idx(tiles.size());
+    for (size_t i = 0; i < idx.size(); ++i) idx[i] = i;
+    std::stable_sort(idx.begin(), idx.end(), [&](size_t a, size_t b) { return tile_cost[a] > tile_cost[b]; });
+    std::vector<SrvTile> t2(tiles.size());
+    for (size_t i = 0; i < idx.size(); ++i) t2[i] = tiles[idx[i]];
+    tiles.swap(t2);
+  }
+  const size_t b_req = al(rs.size() * sizeof(SrvReq)), b_tiles = al(tiles.size() * sizeof(SrvTile)),
+               b_items = al(items.size() * sizeof(SrvOtherItem));
+  size_t b_info = 0;
+  for (auto &r : rs) b_info += al(r->k * 16);
+  const size_t need_dev = b_req + b_tiles + b_items, need_stage = need_dev + b_info;
+  if (need_stage > s.stage_cap) {
+    if (s.stage) cudaFreeHost(s.stage);
+    s.stage = nullptr;
+    s.stage_cap = 0;
+    TSVD_CUDA(cudaHostAlloc(reinterpret_cast<void **>(&s.stage), need_stage, cudaHostAllocPortable));
+    s.stage_cap = need_stage;
+  }
+  {
+    std::lock_guard<std::mutex> lk(sv->mu);
+    if (!sv->arena.alloc(need_dev, &s.dev_off)) {
+      set_error_text("server: no arena room for the wave descriptors");
+      return TSVD_ENOMEM;
+    }
+  }
+  s.dev_bytes = need_dev;
+  unsigned char *dev = sv->arena.base + s.dev_off;
+  SrvReq *hreq = reinterpret_cast<SrvReq *>(s.stage);
+  for (size_t i = 0; i < rs.size(); ++i) hreq[i] = rs[i]->dq;
+  std::memcpy(s.stage + b_req, tiles.data(), tiles.size() * sizeof(SrvTile));
+  std::memcpy(s.stage + b_req + b_tiles, items.data(), items.size() * sizeof(SrvOtherItem));
+  s.info_off = need_dev;
+  cudaStream_t st = s.stream;
+  // inputs
+  for (auto &r : rs)
+    TSVD_CUDA(cudaMemcpyAsync(const_cast<float *>(r->dq.A), r->A, (size_t)r->m * r->n * 4, cudaMemcpyHostToDevice, st));
+  TSVD_CUDA(cudaMemcpyAsync(dev, s.stage, need_dev, cudaMemcpyHostToDevice, st));
+  const SrvReq *dreq = reinterpret_cast<const SrvReq *>(dev);
+  // 1. grouped SYRK
+  TSVD_TRY(launch_srv_syrk(dreq, reinterpret_cast<const SrvTile *>(dev + b_req), (int)tiles.size(), st));
+  // 2. grouped power, one launch per (cluster, residency) run of the sorted requests
+  for (size_t i = 0; i < rs.size();) {
+    size_t j = i;
+    size_t smem = 0;
+    while (j < rs.size() && rs[j]->dq.cluster == rs[i]->dq.cluster && rs[j]->dq.resident == rs[i]->dq.resident) {
+      smem = std::max(smem, srv_power_smem(std::min(rs[j]->m, rs[j]->n), rs[j]->dq.cluster, rs[j]->dq.resident));
+      ++j;
+    }
+    TSVD_TRY(launch_srv_power(dreq + i, (int)(j - i), rs[i]->dq.cluster, smem, st));
+    i = j;
+  }
+  // 3. grouped other factor
+  TSVD_TRY(launch_srv_other(dreq, reinterpret_cast<const SrvOtherItem *>(dev + b_req + b_tiles), (int)items.size(), st));
+  // outputs
+  size_t io = s.info_off;
+  for (auto &r : rs) {
+    const SrvReq &q = r->dq;
+    const int64_t k = r->k;
+    const float *usrc = q.trans ? q.vout : q.other;
+    const float *vsrc = q.trans ? q.other : q.vout;
+    TSVD_CUDA(cudaMemcpyAsync(r->U, usrc, (size_t)r->m * k * 4, cudaMemcpyDeviceToHost, st));
+    TSVD_CUDA(cudaMemcpyAsync(r->V, vsrc, (size_t)r->n * k * 4, cudaMemcpyDeviceToHost, st));
+    TSVD_CUDA(cudaMemcpyAsync(r->sigma, q.sigma, (size_t)k * 8, cudaMemcpyDeviceToHost, st));
+    TSVD_CUDA(cudaMemcpyAsync(s.stage + io, q.info, (size_t)k * 16, cudaMemcpyDeviceToHost, st));
+    io += al(k * 16);
+  }
+  TSVD_CUDA(cudaEventRecord(s.done, st));
+  return TSVD_OK;
+}
+
+// Complete the requests of a finished wave (lock held by the caller).
+void finish_wave(tsvd_server_s *sv, Slot &s, tsvd_status st) {
+  size_t io = s.info_off;
+  const double t = sv->now();
+  for (auto &r : s.reqs) {
+    int flags = 0, status = TSVD_OK;
+    int64_t apps = 0;
+    if (st == TSVD_OK) {
+      const int32_t *info = reinterpret_cast<const int32_t *>(s.stage + io);
+      for (int l = 0; l < r->k; ++l) {
+        apps += info[4 * l];
+        if (info[4 * l + 1] == 1) flags |= TSVD_FLAG_NOCONV;
+        if (info[4 * l + 1] == 2) flags |= TSVD_FLAG_RANK;
+      }
+      for (int l = 1; l < r->k; ++l)
+        if (r->sigma[l] > r->sigma[l - 1]) flags |= TSVD_FLAG_NONMONOTONE;
+      status = (flags & TSVD_FLAG_RANK) ? TSVD_ERANK : (flags & TSVD_FLAG_NOCONV) ? TSVD_ENOCONV : TSVD_OK;
+    } else {
+      status = st;
+    }
+    io += al(r->k * 16);
+    r->rec.status = status;
+    r->rec.flags = flags;
+    r->rec.applications = apps;
+    r->rec.done_s = t;
+    r->done = true;
+    sv->arena.release(r->off, r->bytes);
+    --sv->inflight;
+    if (status == TSVD_OK || status == TSVD_ENOCONV || status == TSVD_ERANK)
+      ++sv->stats.completed;
+    else
+      ++sv->stats.failed;
+  }
+  if (s.dev_bytes) sv->arena.release(s.dev_off, s.dev_bytes);
+  s.dev_bytes = 0;
+  s.reqs.clear();
+  s.busy = false;
+}
+
+void scheduler(tsvd_server_s *sv) {
+  cudaSetDevice(sv->device);
+  const int64_t l0 = launches_so_far();
+  std::unique_lock<std::mutex> lk(sv->mu);
+  while (true) {
+    bool progressed = false;
+    // completions
+    for (auto &s : sv->slots) {
+      if (!s.busy) continue;
+      const cudaError_t q = cudaEventQuery(s.done);
+      if (q == cudaErrorNotReady) continue;
+      tsvd_status st = TSVD_OK;
+      if (q != cudaSuccess) {
+        sv->err = std::string("server: wave failed: ") + cudaGetErrorString(q);
+        st = TSVD_ECUDA;
+      }
+      finish_wave(sv, s, st);
+      progressed = true;
+    }
+    if (progressed) sv->cv_done.notify_all();
+    // admission, first in first out
+    while (!sv->pending.empty() && sv->inflight < sv->opt.max_inflight) {
+      ReqPtr r = sv->pending.front();
+      size_t off = 0;
+      if (!sv->arena.alloc(r->bytes, &off)) break;
+      sv->pending.pop_front();
+      r->off = off;
+      carve(*r, sv->arena.base + off);
+      r->rec.admit_s = sv->now();
+      ++sv->inflight;
+      sv->admitted.push_back(r);
+      progressed = true;
+    }
+    // waves
+    for (auto &s : sv->slots) {
+      if (s.busy || sv->admitted.empty()) continue;
+      const size_t take = std::min(sv->admitted.size(), (size_t)sv->opt.max_wave);
+      s.reqs.assign(sv->admitted.begin(), sv->admitted.begin() + take);
+      sv->admitted.erase(sv->admitted.begin(), sv->admitted.begin() + take);
+      s.busy = true;
+      s.wave = sv->stats.waves++;
+      const double t = sv->now();
+      for (auto &r : s.reqs) {
+        r->rec.launch_s = t;
+        r->rec.wave = (int32_t)s.wave;
+      }
+      lk.unlock();
+      const tsvd_status st = launch_wave(sv, s);
+      lk.lock();
+      for (auto &r : s.reqs) r->rec.cluster = r->dq.cluster;
+      if (st != TSVD_OK) {
+        sv->err = std::string("server: launching a wave failed: ") + tsvd_last_cuda_error();
+        cudaStreamSynchronize(s.stream);
+        finish_wave(sv, s, st);
+        sv->cv_done.notify_all();
+      }
+      progressed = true;
+    }
+    sv->stats.kernel_launches = launches_so_far() - l0;
+    sv->stats.peak_device_bytes = (int64_t)sv->arena.peak;
+    bool any_busy = false;
+    for (auto &s : sv->slots) any_busy |= s.busy;
+    const double t = sv->now();
+    if (any_busy && sv->busy_since < 0) sv->busy_since = t;
+    if (!any_busy && sv->busy_since >= 0) {
+      sv->stats.busy_s += t - sv->busy_since;
+      sv->busy_since = -1.0;
+    }
+    if (sv->stop && !any_busy) break;
+    if (!progressed) {
+      if (any_busy)
+        sv->cv_work.wait_for(lk, std::chrono::microseconds(20));
+      else
+        sv->cv_work.wait_for(lk, std::chrono::milliseconds(5));
+    }
+  }
+}
+
+__global__ void fill_uniform_kernel(float *a, int64_t count, uint32_t seed) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x) {
+    uint32_t c[4] = {(uint32_t)i, (uint32_t)((uint64_t)i >> 32), seed, 0x41554e45u};
+    philox10(c, 0x12345678u, seed);
+    a[i] = (float)((double)c[0] * 0x1.0p-31 - 1.0);
+  }
+}
+
+}  // namespace
+}  // namespace tsvd
+
+using namespace tsvd;
+
+extern "C" {
+
+tsvd_status tsvd_server_options_init(tsvd_server_options *opt) {
+  if (!opt) return TSVD_EINVAL;
+  std::memset(opt, 0, sizeof *opt);
+  opt->device_budget = (size_t)8 << 30;
+  opt->max_inflight = 4096;
+  opt->n_streams = 4;
+  opt->max_wave = 512;
+  opt->cluster_cap = 8;
+  return TSVD_OK;
+}
+
+tsvd_status tsvd_server_create(tsvd_server_t *out, const tsvd_server_options *opt_in) {
+  if (!out) return TSVD_EINVAL;
+  *out = nullptr;
+  tsvd_server_options opt;
+  tsvd_server_options_init(&opt);
+  if (opt_in) {
+    opt = *opt_in;
+    if (!opt.device_budget) opt.device_budget = (size_t)8 << 30;
+    if (!opt.max_inflight) opt.max_inflight = 4096;
+    if (!opt.n_streams) opt.n_streams = 4;
+    if (!opt.max_wave) opt.max_wave = 512;
+    if (!opt.cluster_cap) opt.cluster_cap = 8;
+  }
+  if (opt.max_inflight < 1 || opt.n_streams < 1 || opt.n_streams > 64 || opt.max_wave < 1 ||
+      (opt.cluster_cap != 1 && opt.cluster_cap != 2 && opt.cluster_cap != 4 && opt.cluster_cap != 8))
+    return TSVD_EINVAL;
+  auto *sv = new tsvd_server_s();
+  sv->opt = opt;
+  sv->t0 = std::chrono::steady_clock::now();
+  cudaGetDevice(&sv->device);
+  tsvd_status st = sv->arena.init(opt.device_budget);
+  if (st != TSVD_OK) {
+    delete sv;
+    return st;
+  }
+  sv->slots.resize(opt.n_streams);
+  for (auto &s : sv->slots) {
+    if (cudaStreamCreateWithFlags(&s.stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&s.done, cudaEventDisableTiming) != cudaSuccess) {
+      set_cuda_error(cudaGetLastError(), "server streams", __FILE__, __LINE__);
+      tsvd_server_destroy(sv);
+      return TSVD_ECUDA;
+    }
+  }
+  sv->thr = std::thread(scheduler, sv);
+  *out = sv;
+  return TSVD_OK;
+}
+
+tsvd_status tsvd_server_submit(tsvd_server_t sv, const float *A, int64_t m, int64_t n, int32_t k, double eps,
+                               int32_t max_iter, uint64_t seed, int32_t sign_convention, float *U, double *sigma,
+                               float *V, uint64_t *ticket) {
+  if (!sv || !A || !U || !sigma || !V || !ticket || m <= 0 || n <= 0) return TSVD_EINVAL;
+  const int64_t d = std::min(m, n);
+  if (k < 1 || k > d) return TSVD_EINVAL;
+  if (!(eps > 0.0 && eps < 1.0)) return TSVD_EINVAL;
+  if (d > kSrvMaxDim || k > kSrvMaxK) return TSVD_EUNSUPPORTED;
+  auto r = std::make_shared<Request>();
+  r->A = A;
+  r->m = m;
+  r->n = n;
+  r->k = k;
+  r->eps = eps;
+  r->max_iter = max_iter > 0 ? max_iter : 10000;
+  r->seed = seed;
+  r->sign = sign_convention ? 1 : 0;
+  r->U = U;
+  r->sigma = sigma;
+  r->V = V;
+  r->bytes = request_bytes(m, n, k);
+  if (al(r->bytes) > sv->arena.size) return TSVD_EBUDGET;
+  {
+    std::lock_guard<std::mutex> lk(sv->mu);
+    if (sv->stop) return TSVD_EINVAL;
+    r->id = sv->next_id++;
+    r->rec.submit_s = sv->now();
+    sv->table[r->id] = r;
+    sv->pending.push_back(r);
+    ++sv->stats.submitted;
+    *ticket = r->id;
+  }
+  sv->cv_work.notify_one();
+  return TSVD_OK;
+}
+
+tsvd_status tsvd_server_wait(tsvd_server_t sv, uint64_t ticket, double timeout_s, tsvd_request_info *info) {
+  if (!sv) return TSVD_EINVAL;
+  std::unique_lock<std::mutex> lk(sv->mu);
+  auto it = sv->table.find(ticket);
+  if (it == sv->table.end()) return TSVD_EINVAL;
+  ReqPtr r = it->second;
+  auto pred = [&] { return r->done; };
+  if (timeout_s < 0) {
+    sv->cv_done.wait(lk, pred);
+  } else if (!sv->cv_done.wait_for(lk, std::chrono::duration<double>(timeout_s), pred)) {
+    return TSVD_ETIMEDOUT;
+  }
+  if (info) *info = r->rec;
+  sv->table.erase(ticket);
+  return (tsvd_status)r->rec.status;
+}
+
+tsvd_status tsvd_server_get_stats(tsvd_server_t sv, tsvd_server_stats *stats) {
+  if (!sv || !stats) return TSVD_EINVAL;
+  std::lock_guard<std::mutex> lk(sv->mu);
+  *stats = sv->stats;
+  if (sv->busy_since >= 0) stats->busy_s += sv->now() - sv->busy_since;
+  return TSVD_OK;
+}
+
+const char *tsvd_server_last_error(tsvd_server_t sv) { return sv ? sv->err.c_str() : ""; }
+
+int32_t tsvd_server_cluster_for(tsvd_server_t sv, int64_t d) {
+  if (!sv || d <= 0) return 0;
+  std::lock_guard<std::mutex> lk(sv->mu);
+  return cluster_for(sv, d);
+}
+
+tsvd_status tsvd_server_autotune(tsvd_server_t sv, int32_t iters) {
+  if (!sv || iters < 1) return TSVD_EINVAL;
+  {
+    std::lock_guard<std::mutex> lk(sv->mu);
+    if (sv->inflight || !sv->pending.empty()) return TSVD_EINVAL;
+  }
+  DeviceInfo di;
+  TSVD_TRY(device_info(&di));
+  const size_t smem_cap = power_smem_budget();
+  cudaStream_t st = nullptr;
+  TSVD_CUDA(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+  cudaEvent_t e0, e1;
+  TSVD_CUDA(cudaEventCreate(&e0));
+  TSVD_CUDA(cudaEventCreate(&e1));
+  const int64_t dims[6] = {64, 128, 256, 512, 1024, 2048};
+  const int k = 2;
+  tsvd_status result = TSVD_OK;
+  for (int b = 0; b < 6 && result == TSVD_OK; ++b) {
+    const int64_t d = dims[b];
+    double best = -1.0;
+    int best_c = 1;
+    for (int c = 1; c <= sv->opt.cluster_cap; c *= 2) {
+      if (c > 1 && srv_rows_per_cta(d, c) * (c - 1) >= d) break;
+      const int resident = srv_power_smem(d, c, 1) <= smem_cap ? 1 : 0;
+      const int nreq = std::max(1, di.sms / c);
+      const size_t per = request_bytes(d, d, k);
+      size_t off = 0;
+      {
+        std::lock_guard<std::mutex> lk(sv->mu);
+        if (!sv->arena.alloc(per * nreq + al(nreq * sizeof(SrvReq)) + al(nreq * (size_t)((d + 63) / 64) *
+                                                                          ((d + 63) / 64 + 1) / 2 * sizeof(SrvTile)),
+                             &off)) {
+          result = TSVD_EBUDGET;
+          break;
+        }
+      }
+      unsigned char *base = sv->arena.base + off;
+      std::vector<SrvReq> reqs(nreq);
+      std::vector<SrvTile> tiles;
+      for (int i = 0; i < nreq; ++i) {
+        Request r;
+        r.m = d;
+        r.n = d;
+        r.k = k;
+        r.eps = 1e-300;  // never met: every triplet runs exactly max_iter applications
+        r.max_iter = iters;
+        r.seed = (uint64_t)i;
+        carve(r, base + per * i);
+        r.dq.cluster = c;
+        r.dq.resident = resident;
+        reqs[i] = r.dq;
+        fill_uniform_kernel<<<64, 256, 0, st>>>(const_cast<float *>(r.dq.A), d * d, (uint32_t)i);
+        if (cudaGetLastError() != cudaSuccess) result = TSVD_ECUDA;
+        const int T = (int)ceil_div(d, kSrvTile);
+        for (int ti = 0; ti < T; ++ti)
+          for (int tj = 0; tj <= ti; ++tj) tiles.push_back({i, ti, tj, 0});
+      }
+      SrvReq *dreq = reinterpret_cast<SrvReq *>(base + per * nreq);
+      SrvTile *dtiles = reinterpret_cast<SrvTile *>(base + per * nreq + al(nreq * sizeof(SrvReq)));
+      cudaError_t ce = cudaMemcpyAsync(dreq, reqs.data(), nreq * sizeof(SrvReq), cudaMemcpyHostToDevice, st);
+      if (ce == cudaSuccess)
+        ce = cudaMemcpyAsync(dtiles, tiles.data(), tiles.size() * sizeof(SrvTile), cudaMemcpyHostToDevice, st);
+      tsvd_status ls = ce == cudaSuccess ? launch_srv_syrk(dreq, dtiles, (int)tiles.size(), st) : TSVD_ECUDA;
+      const size_t smem = srv_power_smem(d, c, resident);
+      if (ls == TSVD_OK) ls = launch_srv_power(dreq, nreq, c, smem, st);  // warm-up
+      if (ls == TSVD_OK && cudaEventRecord(e0, st) != cudaSuccess) ls = TSVD_ECUDA;
+      if (ls == TSVD_OK) ls = launch_srv_power(dreq, nreq, c, smem, st);
+      if (ls == TSVD_OK && cudaEventRecord(e1, st) != cudaSuccess) ls = TSVD_ECUDA;
+      float ms = 0.f;
+      if (ls == TSVD_OK && (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
+        ls = TSVD_ECUDA;
+      cudaStreamSynchronize(st);
+      {
+        std::lock_guard<std::mutex> lk(sv->mu);
+        sv->arena.release(off, per * nreq + al(nreq * sizeof(SrvReq)) +
+                                   al(nreq * (size_t)((d + 63) / 64) * ((d + 63) / 64 + 1) / 2 * sizeof(SrvTile)));
+      }
+      if (ls != TSVD_OK) {
+        result = ls;
+        break;
+      }
+      const double rate = (double)nreq * k * iters / (ms * 1e-3);  // applications per second, whole GPU
+      if (rate > best) {
+        best = rate;
+        best_c = c;
+      }
+    }
+    if (result == TSVD_OK) {
+      std::lock_guard<std::mutex> lk(sv->mu);
+      sv->cluster_table[b] = best_c;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaStreamDestroy(st);
+  return result;
+}
+
+void tsvd_server_destroy(tsvd_server_t sv) {
+  if (!sv) return;
+  {
+    std::lock_guard<std::mutex> lk(sv->mu);
+    sv->stop = true;
+    for (auto &r : sv->pending) {
+      r->rec.status = TSVD_ECUDA;
+      r->done = true;
+    }
+    sv->pending.clear();
+  }
+  sv->cv_work.notify_all();
+  if (sv->thr.joinable()) sv->thr.join();
+  {
+    std::lock_guard<std::mutex> lk(sv->mu);
+    for (auto &r : sv->admitted) {
+      r->rec.status = TSVD_ECUDA;
+      r->done = true;
+    }
+    sv->admitted.clear();
+  }
+  sv->cv_done.notify_all();
+  for (auto &s : sv->slots) {
+    if (s.stream) cudaStreamSynchronize(s.stream);
+    if (s.stream) cudaStreamDestroy(s.stream);
+    if (s.done) cudaEventDestroy(s.done);
+    if (s.stage) cudaFreeHost(s.stage);
+  }
+  sv->arena.destroy();
+  delete sv;
+}
+
+}  // extern "C"

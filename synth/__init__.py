@@ -38,6 +38,8 @@ __all__ = [
     "csr_uniform_torch",
     "stacked_factor",
     "stacked_rows_torch",
+    "serving_shapes",
+    "serving_matrix_torch",
 ]
 
 
@@ -289,3 +291,43 @@ def stacked_rows_torch(out, M32: np.ndarray, seed: int):
         sgn = torch.randint(0, 2, (n,), generator=g, device=dev).to(torch.float32).mul_(2.0).sub_(1.0)
         torch.mul(Md[perm], sgn[:, None], out=out[b * n:(b + 1) * n])
     return out
+
+
+def serving_shapes(count: int, seed: int, m_range=(512, 65536), n_range=(64, 2048), rho_range=(0.5, 0.95),
+                   tail: float = 1e-12) -> list:
+    """Shapes of the serving pool: m and n log-uniform in their ranges, a
+    geometric spectrum sigma_i = rho^i with rho uniform, truncated to the
+    rank where rho^i < tail (and to min(m, n))."""
+    g = _rng(seed, 707)
+    out = []
+    for _ in range(count):
+        m = int(round(math.exp(g.uniform(math.log(m_range[0]), math.log(m_range[1])))))
+        n = int(round(math.exp(g.uniform(math.log(n_range[0]), math.log(n_range[1])))))
+        rho = float(g.uniform(*rho_range))
+        r = min(min(m, n), int(math.ceil(math.log(tail) / math.log(rho))))
+        out.append({"m": m, "n": n, "rho": rho, "rank": r})
+    return out
+
+
+def serving_matrix_torch(shape: dict, seed: int, out=None, device="cuda"):
+    """A = Q1 diag(rho^i) Q2^T (exact rank r, no noise) for one pool entry:
+    Q1 (m x r) and Q2 (n x r) the Q factors of seeded Gaussians, formed on
+    the GPU in FP64 and rounded to FP32 once.  Written into `out` (an m x n
+    FP32 array or tensor) when given.  The singular values are rho^i, i < r,
+    up to that rounding."""
+    import torch
+    m, n, r, rho = shape["m"], shape["n"], shape["rank"], shape["rho"]
+    dev = torch.device(device)
+    g = torch.Generator(device=dev)
+    g.manual_seed(int(seed) * 1000003 + 97)
+    q1, _ = torch.linalg.qr(torch.randn((m, r), generator=g, device=dev, dtype=torch.float64))
+    q2, _ = torch.linalg.qr(torch.randn((n, r), generator=g, device=dev, dtype=torch.float64))
+    sig = torch.as_tensor(rho ** np.arange(r, dtype=np.float64), device=dev)
+    A = ((q1 * sig[None, :]) @ q2.T).to(torch.float32)
+    if out is not None:
+        if isinstance(out, np.ndarray):
+            out[:] = A.cpu().numpy()
+        else:
+            out.copy_(A)
+        return out
+    return A

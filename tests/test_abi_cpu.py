@@ -197,3 +197,18 @@ def test_gram_scratch_sizes(lib):
     assert B.tsvd_gram_scratch_bytes(rows, n, B.TSVD_GRAM_TF32X3) == 2048 + 2 * up(n * up(rows, 32) * 4, 1024)
     assert B.tsvd_gram_scratch_bytes(rows, n, B.TSVD_GRAM_BF16X3) == 2048 + 2 * up(n * up(rows, 64) * 2, 1024)
     assert B.tsvd_gram_scratch_bytes(0, n, B.TSVD_GRAM_BF16X3) == 0
+
+
+def test_server_options_validation(lib):
+    """Option checks happen before any device call, so they run without a GPU."""
+    opt = B.tsvd_server_options()
+    assert B.tsvd_server_options_init(C.byref(opt)) == B.TSVD_OK
+    assert opt.max_inflight > 0 and opt.n_streams > 0 and opt.max_wave > 0 and opt.cluster_cap == 8
+    h = C.c_void_p()
+    for field, bad in (("cluster_cap", 3), ("n_streams", 65), ("max_wave", -1), ("max_inflight", -5)):
+        o = B.tsvd_server_options()
+        B.tsvd_server_options_init(C.byref(o))
+        setattr(o, field, bad)
+        assert B.tsvd_server_create(C.byref(h), C.byref(o)) == B.TSVD_EINVAL, field
+    assert B.tsvd_server_submit(None, None, 10, 10, 1, 1e-6, 10, 0, 0, None, None, None, None) == B.TSVD_EINVAL
+    assert B.tsvd_server_cluster_for(None, 100) == 0

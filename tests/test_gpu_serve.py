@@ -1,0 +1,165 @@
+"""The t-SVD server (continuous batching) against the oracle, through the C ABI.
+
+Every request runs the same method as tsvd_factor (Alg. 1/2 with Hotelling
+deflation; Eq. 3 when m < n) with the built-in Philox start draws of its seed,
+which the oracle draws too, so both sides start from the same vectors and
+stop by their own convergence tests.  eps = 1e-10 keeps a one-iteration
+difference at the stopping threshold below ~1.4e-5 in angle.
+"""
+import ctypes as C
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import synth
+from oracle import tsvd_ref as ref
+from paper_2208_08410_gb300 import Server, _binding as B
+
+pytestmark = pytest.mark.gpu
+
+
+def _pinned(shape, dtype):
+    ptr = C.c_void_p()
+    nbytes = max(int(np.prod(shape)) * np.dtype(dtype).itemsize, 16)
+    B.check(B.tsvd_host_alloc(C.byref(ptr), nbytes), "tsvd_host_alloc")
+    ctype = {np.float32: C.c_float, np.float64: C.c_double}[dtype]
+    return ptr, np.ctypeslib.as_array(C.cast(ptr, C.POINTER(ctype)), shape=shape)
+
+
+class Pool:
+    """Page-locked inputs and outputs of a set of requests."""
+
+    def __init__(self):
+        self.ptrs = []
+
+    def arr(self, shape, dtype):
+        p, a = _pinned(shape, dtype)
+        self.ptrs.append(p)
+        return a
+
+    def close(self):
+        for p in self.ptrs:
+            B.tsvd_host_free(p)
+
+
+def _request(pool, m, n, rho, seed, noise=1e-7):
+    d = min(m, n)
+    sig = synth.spectrum_geometric(d, rho)
+    A = synth.dense_prescribed(max(m, n), d, sig, noise, seed=seed)["A"]
+    A = A if m >= n else np.ascontiguousarray(A.T)
+    hA = pool.arr((m, n), np.float32)
+    hA[:] = A
+    return hA
+
+
+def _outputs(pool, m, n, k):
+    return pool.arr((k, m), np.float32), pool.arr((k,), np.float64), pool.arr((k, n), np.float32)
+
+
+CASES = [  # m, n, k, rho
+    (3000, 64, 8, 0.7), (512, 200, 12, 0.8), (4096, 700, 16, 0.85), (300, 1000, 10, 0.75),
+    (2048, 2048, 6, 0.6), (9000, 130, 32, 0.8), (70, 70, 70 // 4, 0.5), (1500, 5, 5, 0.5),
+]
+
+
+def test_server_mixed_wave_matches_oracle():
+    B.load()
+    pool = Pool()
+    sv = Server(device_budget=4 << 30, n_streams=2)
+    try:
+        eps = 1e-10
+        jobs = []
+        for i, (m, n, k, rho) in enumerate(CASES):
+            A = _request(pool, m, n, rho, seed=100 + i)
+            U, s, V = _outputs(pool, m, n, k)
+            t = sv.submit(A, k, eps, U, s, V, seed=7 + i)
+            jobs.append((t, A, k, U, s, V, 7 + i))
+        for t, A, k, U, s, V, seed in jobs:
+            st, info = sv.wait(t, 120.0)
+            assert st == B.TSVD_OK, (st, sv.last_error())
+            o = ref.tsvd_dense(A, k, eps, seed=seed)
+            assert np.max(np.abs(s - o.sigma) / o.sigma) <= 1e-5
+            assert abs(info["applications"] - sum(o.iters)) <= k
+            m, n = A.shape
+            gapped = ref.gapped_indices(o.sigma ** 2, k)
+            # U is m x k and V is n x k, column-major (stored as k rows)
+            for l in gapped:
+                assert ref.vector_angle(V[l].astype(np.float64), o.V[:, l]) <= 1e-4, (m, n, l)
+                assert ref.vector_angle(U[l].astype(np.float64), o.U[:, l]) <= 1e-4, (m, n, l)
+        stats = sv.stats()
+        assert stats["completed"] == len(CASES) and stats["failed"] == 0
+        assert stats["kernel_launches"] >= 3
+    finally:
+        sv.close()
+        pool.close()
+
+
+def test_server_result_alone_equals_result_in_the_mix():
+    """Grouped kernels take no atomics and a request's cluster size depends on
+    its own shape only, so its outputs are bitwise the same in any wave."""
+    B.load()
+    pool = Pool()
+    m, n, k = 2500, 300, 10
+    A = _request(pool, m, n, 0.8, seed=5)
+    alone = _outputs(pool, m, n, k)
+    sv = Server(device_budget=2 << 30)
+    try:
+        st, _ = sv.wait(sv.submit(A, k, 1e-9, *alone, seed=3), 60.0)
+        assert st == B.TSVD_OK
+    finally:
+        sv.close()
+    sv = Server(device_budget=4 << 30, n_streams=3, max_wave=16)
+    mix = _outputs(pool, m, n, k)
+    tickets = []
+    try:
+        rng = np.random.default_rng(0)
+        for i in range(40):
+            mm, nn = int(rng.integers(64, 3000)), int(rng.integers(64, 900))
+            kk = int(rng.integers(1, min(mm, nn, 32) + 1))
+            Ai = _request(pool, mm, nn, float(rng.uniform(0.5, 0.9)), seed=1000 + i)
+            tickets.append(sv.submit(Ai, kk, 1e-9, *_outputs(pool, mm, nn, kk), seed=i))
+            if i == 17:
+                t_mix = sv.submit(A, k, 1e-9, *mix, seed=3)
+        for t in tickets:
+            st, _ = sv.wait(t, 120.0)
+            assert st in (B.TSVD_OK, B.TSVD_ENOCONV)
+        st, info = sv.wait(t_mix, 120.0)
+        assert st == B.TSVD_OK
+        for a, b in zip(alone, mix):
+            assert np.array_equal(a, b)
+        assert sv.stats()["waves"] >= 2
+    finally:
+        sv.close()
+        pool.close()
+
+
+def test_server_zero_matrix_reports_rank():
+    B.load()
+    pool = Pool()
+    sv = Server(device_budget=1 << 30)
+    try:
+        A = pool.arr((100, 40), np.float32)
+        A[:] = 0.0
+        U, s, V = _outputs(pool, 100, 40, 3)
+        st, info = sv.wait(sv.submit(A, 3, 1e-8, U, s, V), 30.0)
+        assert st == B.TSVD_ERANK and info["flags"] & B.TSVD_FLAG_RANK
+        assert np.all(s == 0.0)
+        Vd = V.astype(np.float64)
+        assert np.allclose(Vd @ Vd.T, np.eye(3), atol=1e-6)  # orthonormal fallback vectors
+    finally:
+        sv.close()
+        pool.close()
+
+
+def test_server_autotune_table():
+    B.load()
+    sv = Server(device_budget=6 << 30)
+    try:
+        sv.autotune(iters=20)
+        for d in (64, 128, 256, 512, 1024, 2048):
+            c = sv.cluster_for(d)
+            assert c in (1, 2, 4, 8)
+    finally:
+        sv.close()
