@@ -1040,7 +1040,7 @@ def main():
                            "gram_precision": PREC_NAMES[prec] + (" (FP32-class split: hi*hi + hi*lo + lo*hi on the "
                                                                  "tensor cores, FP32 accumulate)" if prec == 2 else ""),
                            "parallelism": "replicas" if world > 1 else "1 GPU"},
-                "roofline": roofline, "cpu_baseline": cpu, "oom_sweep": sweep, "e2e": e2e, "clocks": clk, "tf32_in_core": alt,
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk, "tf32_in_core": alt,
                 "c1_latency": small,
                 "gpu_launches": launches, "gpu_launches_e2e": launches_e,
                 "phases_ms": {"gram": round(reps[-1]["gram_ms"], 2), "power": round(reps[-1]["power_ms"], 2),

@@ -254,16 +254,17 @@ TSVD_API tsvd_status tsvd_csr_gram_apply(int64_t rows, int64_t n, const int64_t 
  *   G32      device, n x n FP32 row-major: the Gram matrix already deflated
  *            by the earlier triplets, G - sum_{j<l} sigma_j^2 v_j v_j^T
  *            (tsvd_gram_symmetrize, then tsvd_gram_deflate once per triplet)
- *   G64      device, n x n FP64 with the upper triangle of the undeflated G
- *            (for sigma_l^2 = v_l^T G v_l)
+ *   G64      device, n x n FP64: the upper triangle of the same deflated
+ *            matrix (FP64), for sigma_l^2 = v_l^T G v_l, formed as
+ *            v_l^T G64 v_l + sum_{j<l} sigma_j^2 (v_j . v_l)^2
  *   V64      device, n x l FP64 column-major earlier vectors and
- *   sigma2   device, l FP64 earlier sigma^2: used only when B v0 vanishes
- *            (then v_l = v0 made orthogonal to V64, sigma_l = 0); NULL if l == 0
+ *   sigma2   device, l FP64 earlier sigma^2 (the term above, and, when B v0
+ *            vanishes, v_l = v0 made orthogonal to V64, sigma_l = 0); NULL if l == 0
  *   x        device, n FP64: in = start draw (not necessarily normalised),
  *            out = v_l (unit norm)
  *   eps, max_iter, iters_override (<= 0: use the convergence test)
  *   sign_convention  1: make the largest-|entry| positive
- *   out_sigma2  device FP64 scalar: v_l^T G64 v_l
+ *   out_sigma2  device FP64 scalar: sigma_l^2
  *   info     device int32[4]: {applications, status (0 ok, 1 noconv, 2 rank),
  *            timeout flag, 0}
  *   scratch  device, tsvd_power_scratch_bytes(n, l) bytes (zeroing not needed)
@@ -304,9 +305,14 @@ TSVD_API tsvd_status tsvd_power_dense_noalloc(int64_t n, const float *G32, const
                                               int32_t iters_override, int32_t sign_convention,
                                               double *out_sigma2, int32_t *info, void *stream);
 
-/* Hotelling deflation of the FP32 Gram copy by one triplet:
- * G32 -= sigma2[0] * v v^T (v device FP64 n, sigma2 device FP64 scalar). */
-TSVD_API tsvd_status tsvd_gram_deflate(int64_t n, float *G32, const double *v, const double *sigma2,
+/* Hotelling deflation of the Gram matrix by one triplet (the deflated
+ * operator of Eq. 2 in Hotelling form), in FP64: on the upper triangle of
+ * G64 (n x n row-major, entry (i, j) with j >= i) G64 -= sigma2[0] v v^T, then
+ * G32 (n x n row-major FP32, both halves) = the FP32 rounding of the deflated
+ * G64.  v device FP64 n, sigma2 device FP64 scalar.  Rounding the FP32 copy
+ * from the deflated FP64 matrix keeps its error relative to the spectrum that
+ * remains. */
+TSVD_API tsvd_status tsvd_gram_deflate(int64_t n, double *G64, float *G32, const double *v, const double *sigma2,
                                        void *stream);
 
 /* Fill G32 (n x n FP32, full) from the upper triangle of G64 (symmetrise). */
@@ -365,11 +371,14 @@ typedef struct {
   size_t device_budget;   /* HBM the server allocates once and admits requests
                              into (0: 8 GiB) */
   int32_t max_inflight;   /* requests admitted at once (0: 4096) */
-  int32_t n_streams;      /* waves in flight at once, one stream each (0: 4) */
-  int32_t max_wave;       /* most requests one wave launches together (0: 512) */
+  int32_t n_streams;      /* waves in flight at once, one stream each (0: 8) */
+  int32_t max_wave;       /* most requests one wave launches together (0: 64) */
   int32_t cluster_cap;    /* largest thread-block cluster of the power kernel
                              (1, 2, 4 or 8; 0: 8) */
-  int32_t reserved[8];
+  size_t host_staging;    /* page-locked, device-mapped memory the kernels
+                             write each request's results into before they
+                             are copied to the caller (0: 2 GiB) */
+  int32_t reserved[6];
 } tsvd_server_options;
 
 /* Per-request record (tsvd_server_wait / tsvd_server_poll). */
@@ -406,10 +415,12 @@ TSVD_API tsvd_status tsvd_server_create(tsvd_server_t *server, const tsvd_server
  *            valid and unchanged until the request completes.  Page-locked
  *            memory (tsvd_host_alloc) lets the copy overlap other work.
  *   U, sigma, V  host outputs: U m x k and V n x k column-major FP32, sigma k
- *            FP64; written asynchronously, valid once the request completes.
+ *            FP64; the kernels write the results into the server's
+ *            page-locked staging and tsvd_server_wait copies them here.
  *   k        1 <= k <= min(m, n), k <= 32;  min(m, n) <= 2048
- *   eps, max_iter, seed, sign_convention  as for tsvd_plan / tsvd_options
- *            (start draws: the built-in Philox-4x32-10 stream of `seed`)
+ *   eps, max_iter, seed, sign_convention, iters_override  as for tsvd_plan /
+ *            tsvd_options (start draws: the built-in Philox-4x32-10 stream of
+ *            `seed`; iters_override: k forced application counts, or NULL)
  *   ticket   receives the request's id
  * Requests are admitted first in, first out as the device budget and
  * max_inflight allow.  Errors: EINVAL (arguments), EBUDGET (the request alone
@@ -417,11 +428,15 @@ TSVD_API tsvd_status tsvd_server_create(tsvd_server_t *server, const tsvd_server
  */
 TSVD_API tsvd_status tsvd_server_submit(tsvd_server_t server, const float *A, int64_t m, int64_t n, int32_t k,
                                         double eps, int32_t max_iter, uint64_t seed, int32_t sign_convention,
-                                        float *U, double *sigma, float *V, uint64_t *ticket);
+                                        const int32_t *iters_override, float *U, double *sigma, float *V,
+                                        uint64_t *ticket);
 
-/* Block until the request completes or timeout_s passes (< 0: no limit).
- * Returns the request's status (TSVD_ETIMEDOUT on timeout) and fills *info.
- * A completed request's record is released by this call. */
+/* Block until the request completes or timeout_s passes (< 0: no limit),
+ * then copy its results into the caller's U, sigma, V.  Returns the
+ * request's status (TSVD_ETIMEDOUT on timeout) and fills *info.  A completed
+ * request's record and staging are released by this call.  A request
+ * completes as soon as its own cluster has finished (a flag the kernel sets),
+ * not when the rest of its wave does. */
 TSVD_API tsvd_status tsvd_server_wait(tsvd_server_t server, uint64_t ticket, double timeout_s, tsvd_request_info *info);
 
 TSVD_API tsvd_status tsvd_server_get_stats(tsvd_server_t server, tsvd_server_stats *stats);

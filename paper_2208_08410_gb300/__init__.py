@@ -197,11 +197,15 @@ class Server:
         self._keep = {}
 
     def submit(self, A, k: int, eps: float, U, sigma, V, max_iter: int = 10000, seed: int = 0,
-               sign_convention: bool = False) -> int:
+               sign_convention: bool = False, iters_override=None) -> int:
         m, n = A.shape
         t = C.c_uint64()
+        ovr = None
+        if iters_override is not None:
+            ovr = np.ascontiguousarray(iters_override, dtype=np.int32)
         B.check(self.lib.tsvd_server_submit(self.handle, _ptr(A), m, n, int(k), float(eps), int(max_iter), int(seed),
-                                            int(bool(sign_convention)), _ptr(U), _ptr(sigma), _ptr(V), C.byref(t)),
+                                            int(bool(sign_convention)), _ptr(ovr), _ptr(U), _ptr(sigma), _ptr(V),
+                                            C.byref(t)),
                 "tsvd_server_submit")
         self._keep[t.value] = (A, U, sigma, V)
         return t.value

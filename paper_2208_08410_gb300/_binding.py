@@ -48,7 +48,8 @@ class tsvd_report(C.Structure):
 
 class tsvd_server_options(C.Structure):
     _fields_ = [("device_budget", C.c_size_t), ("max_inflight", C.c_int32), ("n_streams", C.c_int32),
-                ("max_wave", C.c_int32), ("cluster_cap", C.c_int32), ("reserved", C.c_int32 * 8)]
+                ("max_wave", C.c_int32), ("cluster_cap", C.c_int32), ("host_staging", C.c_size_t),
+                ("reserved", C.c_int32 * 6)]
 
 
 class tsvd_request_info(C.Structure):
@@ -86,7 +87,7 @@ SIGNATURES = {
     "tsvd_power_dense": (C.c_int, [_I64, _P, _P, _P, _P, _I64, _P, _D, _I32, _I32, _I32, _P, _P, _P, _SZ, _P]),
     "tsvd_power_dense_noalloc": (C.c_int, [_I64, _P, _P, _P, _P, _I64, _P, _D, _I32, _I32, _I32, _P, _P, _P]),
     "tsvd_gram_symmetrize": (C.c_int, [_I64, _P, _P, _P]),
-    "tsvd_gram_deflate": (C.c_int, [_I64, _P, _P, _P, _P]),
+    "tsvd_gram_deflate": (C.c_int, [_I64, _P, _P, _P, _P, _P]),
     "tsvd_start_draws": (C.c_int, [C.c_uint64, _I64, _I64, _P, _P]),
     "tsvd_philox4x32_10": (C.c_int, [_P, _P, _P, _I64, _P]),
     "tsvd_left_vectors": (C.c_int, [_P, _I64, _I64, _I64, _P, _I64, _I64, _P, _P, _I64, _P]),
@@ -95,7 +96,7 @@ SIGNATURES = {
     "tsvd_host_free": (C.c_int, [_P]),
     "tsvd_server_options_init": (C.c_int, [C.POINTER(tsvd_server_options)]),
     "tsvd_server_create": (C.c_int, [C.POINTER(_P), C.POINTER(tsvd_server_options)]),
-    "tsvd_server_submit": (C.c_int, [_P, _P, _I64, _I64, _I32, _D, _I32, C.c_uint64, _I32, _P, _P, _P,
+    "tsvd_server_submit": (C.c_int, [_P, _P, _I64, _I64, _I32, _D, _I32, C.c_uint64, _I32, _P, _P, _P, _P,
                                      C.POINTER(C.c_uint64)]),
     "tsvd_server_wait": (C.c_int, [_P, C.c_uint64, _D, C.POINTER(tsvd_request_info)]),
     "tsvd_server_get_stats": (C.c_int, [_P, C.POINTER(tsvd_server_stats)]),

@@ -604,7 +604,7 @@ tsvd_status factor_dense(Run &r, float *U, double *sigma_out, float *V_out, tsvd
                                 p->opt.max_iter, ovr, p->opt.sign_convention, sig2 + l, info + 4 * l,
                                 pscr, p->b_pscr, r.cs));
     // Hotelling deflation of the FP32 Gram copy for the next triplet
-    if (l + 1 < k) TSVD_TRY(launch_gram_deflate(n, G32, x, sig2 + l, r.cs));
+    if (l + 1 < k) TSVD_TRY(launch_gram_deflate(n, G64, G32, x, sig2 + l, r.cs));
   }
   TSVD_TRY(launch_sigma_from_sigma2(sig2, sigma, k, r.cs));
   TSVD_TRY(launch_f64_to_f32(V64, V32, n * k, r.cs));
@@ -1044,9 +1044,10 @@ tsvd_status tsvd_power_dense_noalloc(int64_t n, const float *G32, const double *
                                     sign_convention, out_sigma2, info, static_cast<cudaStream_t>(stream));
 }
 
-tsvd_status tsvd_gram_deflate(int64_t n, float *G32, const double *v, const double *sigma2, void *stream) {
-  if (n <= 0 || !G32 || !v || !sigma2) return TSVD_EINVAL;
-  return launch_gram_deflate(n, G32, v, sigma2, static_cast<cudaStream_t>(stream));
+tsvd_status tsvd_gram_deflate(int64_t n, double *G64, float *G32, const double *v, const double *sigma2,
+                              void *stream) {
+  if (n <= 0 || !G64 || !G32 || !v || !sigma2) return TSVD_EINVAL;
+  return launch_gram_deflate(n, G64, G32, v, sigma2, static_cast<cudaStream_t>(stream));
 }
 
 tsvd_status tsvd_gram_symmetrize(int64_t n, const double *G64, float *G32, void *stream) {

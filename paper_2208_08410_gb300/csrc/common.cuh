@@ -169,7 +169,8 @@ tsvd_status launch_power_dense_noalloc(int64_t n, const float *G32, const double
                                        int iters_override, int sign_convention, double *out_sigma2, int *info,
                                        cudaStream_t stream);
 tsvd_status launch_symmetrize(int64_t n, const double *G64, float *G32, cudaStream_t stream);
-tsvd_status launch_gram_deflate(int64_t n, float *G32, const double *v, const double *sigma2, cudaStream_t stream);
+tsvd_status launch_gram_deflate(int64_t n, double *G64, float *G32, const double *v, const double *sigma2,
+                                cudaStream_t stream);
 tsvd_status launch_start_draws(uint64_t seed, int64_t l, int64_t n, double *x, cudaStream_t stream);
 tsvd_status launch_philox_raw(const uint32_t *ctr, const uint32_t *key, uint32_t *out,
                               int64_t count, cudaStream_t stream);

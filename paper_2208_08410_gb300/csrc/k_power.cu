@@ -6,9 +6,14 @@
 //     w = G v0 - sum_{j<l} sigma_j^2 v_j (v_j^T v0)
 // and closes with sigma_l^2 = v_l^T G v_l (Alg. 1 l.11-13: sigma = ||A v||).
 //
-// The FP32 copy of G is deflated in place once per triplet (rank-1 update,
-// tsvd_gram_deflate), so an iteration is one GEMV with the deflated matrix:
-// the same Hotelling operator as above, applied as a matrix.  One cooperative
+// The Gram matrix is deflated once per triplet (rank-1 update in FP64 of
+// the FP64 upper triangle, tsvd_gram_deflate) and the FP32 copy the loop
+// reads is rounded from the deflated FP64 matrix, so an iteration is one
+// GEMV with the deflated matrix and the copy's rounding error is relative to
+// the spectrum that remains (deflating the FP32 copy itself would leave
+// errors of ~2^-24 sigma_0^2, larger than the small eigenvalues still to
+// find).  sigma_l^2 = v_l^T G v_l is formed as v_l^T G_defl v_l +
+// sum_{j<l} sigma_j^2 (v_j . v_l)^2.  One cooperative
 // launch runs the whole loop; each block owns a contiguous range of rows and
 // an iteration has a single bounded grid barrier:
 //   w = G32_defl v for the block's rows (FP32 products, FP64 row sums) and
@@ -393,7 +398,8 @@ __global__ void __launch_bounds__(PT, 1) power_dense_kernel(PowerArgs a) {
     for (int64_t i = r0 + threadIdx.x; i < r1; i += PT) a.x[i] *= sign;
   }
 
-  // ---- Rayleigh quotient sigma^2 = v^T G64 v (upper triangle, FP64), once per triplet
+  // ---- sigma^2 = v^T G v = v^T G_defl v (upper triangle of the deflated FP64
+  // matrix) + sum_{j<l} sigma_j^2 (v_j . v)^2, once per triplet
   if (!grid_barrier(a.bar, a.err)) return;
   double q = 0.0;
   if (status != 2) {
@@ -407,12 +413,25 @@ __global__ void __launch_bounds__(PT, 1) power_dense_kernel(PowerArgs a) {
       t = warp_sum(t);
       if (lane == 0) q += t * __ldcg(a.x + i);
     }
+    for (int j = warp; j < l; j += nwarps) {
+      const double *vj = a.V64 + (int64_t)j * n;
+      double t = 0.0;
+      for (int64_t i = r0 + lane; i < r1; i += 32) t += __ldg(vj + i) * __ldcg(a.x + i);
+      t = warp_sum(t);
+      if (lane == 0) mypart[11 + l + j] = t;
+    }
   }
   q = block_sum(q, red);
   if (threadIdx.x == 0) mypart[10 + l] = q;
   if (!grid_barrier(a.bar, a.err)) return;
   if (blockIdx.x == 0) {
-    const double tq = reduce_partials(a.part, ps, 10 + l, red);
+    double tq = reduce_partials(a.part, ps, 10 + l, red);
+    if (status != 2) {
+      for (int j = 0; j < l; ++j) {
+        const double c = reduce_partials(a.part, ps, 11 + l + j, red);
+        tq += __ldg(a.sig2 + j) * c * c;
+      }
+    }
     if (threadIdx.x == 0) {
       *a.out_sigma2 = status == 2 ? 0.0 : fmax(tq, 0.0);
       a.info[0] = it;
@@ -469,16 +488,34 @@ __global__ void philox_raw_kernel(const uint32_t *ctr, const uint32_t *key, uint
   }
 }
 
-// G32[i][j] -= sigma2 * v_i * v_j : the Hotelling deflation of the FP32 Gram
-// copy by one extracted triplet (row factor sigma2 * v_i formed in FP64, one
-// FP32 fused multiply-add per entry).  Grid: (n/4 / 64, n) with 64 threads.
-__global__ void deflate_rank1_kernel(int64_t n, float *__restrict__ G32, const double *__restrict__ v,
-                                     const double *__restrict__ sigma2) {
-  const int64_t i = blockIdx.y;
-  const float ci = (float)(__ldg(sigma2) * __ldg(v + i));
-  float *row = G32 + i * n;
-  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x)
-    row[j] = fmaf(-ci, (float)__ldg(v + j), row[j]);
+// Hotelling deflation by one extracted triplet, in FP64: for the upper
+// triangle of G64 (entry (i, j), j >= i, at i n + j) G64 -= sigma2 v_i v_j,
+// and the FP32 copy of the deflated matrix, both halves.  32 x 32 tiles of
+// the upper triangle; each mirrored FP32 tile goes through shared memory.
+__global__ void deflate_gram_kernel(int64_t n, double *__restrict__ G64, float *__restrict__ G32,
+                                    const double *__restrict__ v, const double *__restrict__ sigma2) {
+  __shared__ float t[32][33];
+  const int64_t bi = (int64_t)blockIdx.y * 32, bj = (int64_t)blockIdx.x * 32;
+  if (bj < bi) return;
+  const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8
+  const double s2 = __ldg(sigma2);
+  for (int r = ty; r < 32; r += 8) {
+    const int64_t i = bi + r, j = bj + tx;
+    float f = 0.f;
+    if (i < n && j < n && j >= i) {
+      const double g = fma(-s2 * __ldg(v + i), __ldg(v + j), G64[i * n + j]);
+      G64[i * n + j] = g;
+      f = (float)g;
+      G32[i * n + j] = f;
+    }
+    t[r][tx] = f;
+  }
+  __syncthreads();
+  // mirrored entries come from the tile (a diagonal tile mirrors only its strict upper part)
+  for (int r = ty; r < 32; r += 8) {
+    const int64_t i = bj + r, j = bi + tx;
+    if (i < n && j < n && (bj != bi || r > tx)) G32[i * n + j] = t[tx][r];
+  }
 }
 
 __global__ void sigma_kernel(const double *sig2, double *sigma, int64_t k) {
@@ -496,9 +533,10 @@ __global__ void f64_to_f32_kernel(const double *src, float *dst, int64_t count) 
 
 // per-block partial layout (doubles): [0] ||x||^2, [1..3] and [4..6] the
 // loop's ||w||^2, v.w, v.v in alternating iterations, [7..7+l) and [7+l] the
-// rank-deficient projection, [8+l], [9+l] the sign search, [10+l] v^T G v;
-// regions written after the loop never overlap ones a slower block may still read
-static int64_t power_part_stride(int64_t l) { return round_up(l + 12, 4); }
+// rank-deficient projection, [8+l], [9+l] the sign search, [10+l] v^T G v,
+// [11+l .. 11+2l) v_j . v; regions written after the loop never overlap ones
+// a slower block may still read
+static int64_t power_part_stride(int64_t l) { return round_up(2 * l + 12, 4); }
 
 size_t power_scratch_bytes(int64_t n, int64_t l) {
   const size_t ps = (size_t)power_part_stride(l);
@@ -588,7 +626,7 @@ tsvd_status launch_philox_raw(const uint32_t *ctr, const uint32_t *key, uint32_t
 // device address (on the host it is only a stand-in for the symbol), so its
 // device address is looked up once per device with cudaGetSymbolAddress.
 constexpr int64_t kNoallocScratchBytes =
-    256 + 2 * TSVD_NOALLOC_MAX_N * 4 + (int64_t)kMaxPowerBlocks * ((TSVD_NOALLOC_MAX_L + 12 + 3) / 4 * 4) * 8;
+    256 + 2 * TSVD_NOALLOC_MAX_N * 4 + (int64_t)kMaxPowerBlocks * ((2 * TSVD_NOALLOC_MAX_L + 12 + 3) / 4 * 4) * 8;
 static __device__ __align__(256) unsigned char g_power_noalloc_scratch[kNoallocScratchBytes];
 
 static tsvd_status noalloc_scratch(void **out) {
@@ -625,12 +663,13 @@ tsvd_status launch_power_dense_noalloc(int64_t n, const float *G32, const double
                             out_sigma2, info, scratch, (size_t)kNoallocScratchBytes, stream);
 }
 
-tsvd_status launch_gram_deflate(int64_t n, float *G32, const double *v, const double *sigma2, cudaStream_t stream) {
+tsvd_status launch_gram_deflate(int64_t n, double *G64, float *G32, const double *v, const double *sigma2,
+                                cudaStream_t stream) {
   if (n <= 0) return TSVD_OK;
-  if (n > 0x7fffffffLL) return TSVD_EINVAL;
-  const unsigned gx = (unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(n, 256), 8));
-  dim3 grid(gx, (unsigned)n);
-  deflate_rank1_kernel<<<grid, 256, 0, stream>>>(n, G32, v, sigma2);
+  const int64_t nb = ceil_div(n, 32);
+  if (nb > 65535) return TSVD_EUNSUPPORTED;
+  dim3 grid((unsigned)nb, (unsigned)nb), block(32, 8);
+  deflate_gram_kernel<<<grid, block, 0, stream>>>(n, G64, G32, v, sigma2);
   TSVD_LAUNCHED();
   return TSVD_OK;
 }

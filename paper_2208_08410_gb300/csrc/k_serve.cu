@@ -17,12 +17,18 @@
 // the CTA's partial ||w||^2, v.w, v.v into every CTA's partial slots through
 // distributed shared memory, one cluster barrier, then every CTA adds the C
 // partials in rank order and takes the same decision.  After the loop every
-// CTA holds the whole v_l: sigma_l^2 = v_l^T G64 v_l (FP64, distributed by
-// rows, one more exchange) and the CTA's rows of G32 are deflated by
-// sigma_l^2 v_l v_l^T.
+// CTA holds the whole v_l.  The CTA's rows of the FP64 Gram are kept deflated
+// (Hotelling, in FP64) and its rows of the FP32 copy are rounded from them,
+// so the copy's rounding error is relative to the spectrum that remains;
+// sigma_l^2 = v_l^T G v_l is formed as v_l^T G_defl v_l + sum_{j<l}
+// sigma_j^2 (v_j . v_l)^2 from row partials (one more exchange).
 //
-// Grouped other factor (Alg. 1 l.11-13 / l.15-17): U = A V Sigma^-1 for tall
-// requests, V = A^T U Sigma^-1 for wide ones.
+// After the k triplets the same cluster forms the other factor (Alg. 1
+// l.11-13 / l.15-17: U = A V Sigma^-1 for tall requests, V = A^T U Sigma^-1
+// for wide ones), writes U, sigma, V and the per-triplet info into the
+// request's page-locked, device-mapped staging and raises its completion
+// flag there (system-scope release), so a request completes as soon as its
+// own cluster finishes.
 #include "philox.cuh"
 #include "serve.cuh"
 
@@ -156,7 +162,7 @@ __device__ __forceinline__ void warp_sum_pair(float &hi, float &lo) {
 }
 
 constexpr int kMaxCluster = 8;
-constexpr int kPartSlot = 4;  // doubles per (parity, rank) slot
+constexpr int kPartSlot = kSrvMaxK + 4;  // doubles per (parity, rank) slot
 
 struct PowerSmem {
   float *vb[2];    // d (padded) each: the iterate, scaled in place at the start of an iteration
@@ -173,6 +179,9 @@ __global__ void __launch_bounds__(kSrvPowerThreads, 1) srv_power_kernel(const Sr
   __shared__ double wred[3 * (kSrvPowerThreads / 32)];
   __shared__ double red[33];
   __shared__ double s_scal[4];
+  __shared__ double s2hist[kSrvMaxK];   // sigma_j^2 of the triplets found so far
+  __shared__ __align__(16) float ostage[kSrvOtherChunk * kSrvMaxK];  // other factor: a chunk of V or U
+  __shared__ double cpart[kSrvMaxK + 1];  // this CTA's v^T G_defl v and v_j . v partials
   const uint32_t C = cta_count(), rank = cta_rank();
   const SrvReq &q = reqs[blockIdx.x / C];
   const int64_t d = q.trans ? q.m : q.n;
@@ -311,11 +320,15 @@ __global__ void __launch_bounds__(kSrvPowerThreads, 1) srv_power_kernel(const Sr
           done = 1;
         } else {
           sc = 1.0 / nw;
-          const double cosv = fabs(t1) / (nw * sqrt(t2));
-          done = cosv >= 1.0 - q.eps;
-          if (!done && it1 >= q.max_iter) {
-            done = 1;
-            st = 1;
+          if (q.iters_override) {
+            done = it1 >= q.iters_override[l];
+          } else {
+            const double cosv = fabs(t1) / (nw * sqrt(t2));
+            done = cosv >= 1.0 - q.eps;
+            if (!done && it1 >= q.max_iter) {
+              done = 1;
+              st = 1;
+            }
           }
         }
         s_scal[0] = sc;
@@ -380,7 +393,8 @@ __global__ void __launch_bounds__(kSrvPowerThreads, 1) srv_power_kernel(const Sr
       for (int64_t i = threadIdx.x; i < d; i += kSrvPowerThreads) sm.xs[i] *= sg;
       __syncthreads();
     }
-    // ---- sigma_l^2 = v_l^T G64 v_l over this CTA's rows, exchanged like the partials
+    // ---- sigma_l^2 = v^T G_defl v + sum_{j<l} sigma_j^2 (v_j . v)^2 from this
+    // CTA's rows, exchanged like the partials
     double qv = 0.0;
     if (status != 2) {
       for (int64_t r = r0 + warp; r < r1; r += nwarps) {
@@ -390,19 +404,38 @@ __global__ void __launch_bounds__(kSrvPowerThreads, 1) srv_power_kernel(const Sr
         t = warp_sum(t);
         if (lane == 0) qv += t * sm.xs[r];
       }
+      for (int j = warp; j < l; j += nwarps) {
+        const double *vj = q.V64 + (int64_t)j * d;  // rows this CTA wrote itself
+        double t = 0.0;
+        for (int64_t r = r0 + lane; r < r1; r += 32) t += vj[r] * sm.xs[r];
+        t = warp_sum(t);
+        if (lane == 0) cpart[1 + j] = t;
+      }
     }
     qv = block_sum(qv, red);
+    if (threadIdx.x == 0) cpart[0] = qv;
+    __syncthreads();
     const int par = (int)(phase & 1u);
-    if (threadIdx.x == 0) {
-      const uint32_t slot = smem_addr(sm.part + (par * kMaxCluster + rank) * kPartSlot);
-      for (uint32_t c = 0; c < C; ++c) st_peer_f64(peer_addr(slot, c), qv);
+    const int ncp = status == 2 ? 1 : l + 1;
+    if (threadIdx.x < (unsigned)ncp) {
+      const uint32_t slot = smem_addr(sm.part + (par * kMaxCluster + rank) * kPartSlot + threadIdx.x);
+      for (uint32_t c = 0; c < C; ++c) st_peer_f64(peer_addr(slot, c), cpart[threadIdx.x]);
     }
     cluster_sync_all();
     ++phase;
     double s2 = 0.0;
     for (uint32_t c = 0; c < C; ++c) s2 += sm.part[(par * kMaxCluster + c) * kPartSlot];
+    if (status != 2) {
+      for (int j = 0; j < l; ++j) {
+        double cj = 0.0;
+        for (uint32_t c = 0; c < C; ++c) cj += sm.part[(par * kMaxCluster + c) * kPartSlot + 1 + j];
+        s2 += s2hist[j] * cj * cj;
+      }
+    }
     s2 = status == 2 ? 0.0 : fmax(s2, 0.0);
     if (l == 0) sig0sq = s2;
+    __syncthreads();
+    if (threadIdx.x == 0) s2hist[l] = s2;
     // ---- outputs of triplet l (each CTA its rows; rank 0 the scalars)
     for (int64_t r = r0 + threadIdx.x; r < r1; r += kSrvPowerThreads) {
       q.V64[(int64_t)l * d + r] = sm.xs[r];
@@ -416,106 +449,115 @@ __global__ void __launch_bounds__(kSrvPowerThreads, 1) srv_power_kernel(const Sr
       q.info[4 * l + 2] = 0;
       q.info[4 * l + 3] = 0;
     }
-    // ---- Hotelling deflation of this CTA's rows of the FP32 copy
+    // ---- Hotelling deflation of this CTA's rows: FP64 Gram in FP64, FP32 copy rounded from it
     if (l + 1 < k && status != 2) {
       for (int64_t r = r0 + warp; r < r1; r += nwarps) {
-        float *g = Grow0 + (r - r0) * d;
-        const float ci = (float)(s2 * sm.xs[r]);
-        for (int64_t c = lane; c < d; c += 32) g[c] = fmaf(-ci, (float)sm.xs[c], g[c]);
+        double *g64 = q.G64 + r * d;
+        float *g32 = Grow0 + (r - r0) * d;
+        const double cr = s2 * sm.xs[r];
+        for (int64_t c = lane; c < d; c += 32) {
+          const double g = fma(-cr, sm.xs[c], g64[c]);
+          g64[c] = g;
+          g32[c] = (float)g;
+        }
       }
     }
     __syncthreads();
   }
-}
 
-// ---------------------------------------------------------------- grouped other factor
-// tall (trans 0): block = 16 rows of U, warp w handles rows 2w and 2w+1; a
-//                 128-column slab of V (l-major) is staged in shared memory
-// wide (trans 1): block = 128 columns of V; thread t handles column
-//                 128 b + (t & 127) and half of the k outputs (t >> 7)
-__global__ void __launch_bounds__(256) srv_other_kernel(const SrvReq *__restrict__ reqs,
-                                                        const SrvOtherItem *__restrict__ items) {
-  __shared__ float sv[kSrvMaxK * 128];
-  const SrvOtherItem it = items[blockIdx.x];
-  const SrvReq &q = reqs[it.req];
-  const int k = q.k;
+  // ---- other factor (Alg. 1 l.11-13 / l.15-17) for this request, split over the cluster
+  cluster_sync_all();  // every CTA's rows of vout are written
   const int64_t m = q.m, n = q.n;
   const float *__restrict__ A = q.A;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   if (!q.trans) {
-    // U[r][l] = sum_j A[r][j] V[j][l] / sigma_l; V = vout (n x k)
-    const int64_t rbase = (int64_t)it.block * kSrvOtherRows;
-    float acc[2][kSrvMaxK];
+    // U[r][l] = sum_j A[r][j] V[j][l] / sigma_l; this CTA's rows of U, one row per warp at a time,
+    // V staged in chunks of kSrvOtherChunk rows (l-major) in shared memory
+    const int64_t Rm = (m + C - 1) / C;
+    const int64_t u0 = min(m, (int64_t)rank * Rm), u1 = min(m, u0 + Rm);
+    for (int64_t rb = u0; rb < u1; rb += nwarps) {
+      const int64_t r = rb + warp;
+      float acc[kSrvMaxK];
 #pragma unroll
-    for (int a = 0; a < 2; ++a)
+      for (int l = 0; l < kSrvMaxK; ++l) acc[l] = 0.f;
+      for (int64_t j0 = 0; j0 < n; j0 += kSrvOtherChunk) {
+        __syncthreads();
+        for (int e = threadIdx.x; e < kSrvOtherChunk * kSrvMaxK; e += kSrvPowerThreads) {
+          const int l = e / kSrvOtherChunk, jj = e % kSrvOtherChunk;
+          ostage[e] = (j0 + jj < n && l < k) ? q.vout[(int64_t)l * n + j0 + jj] : 0.f;
+        }
+        __syncthreads();
+        if (r < u1) {
+          for (int jj = lane; jj < kSrvOtherChunk; jj += 32) {
+            const float x = (j0 + jj < n) ? __ldg(A + r * n + j0 + jj) : 0.f;
 #pragma unroll
-      for (int l = 0; l < kSrvMaxK; ++l) acc[a][l] = 0.f;
-    for (int64_t j0 = 0; j0 < n; j0 += 128) {
-      __syncthreads();
-      for (int e = threadIdx.x; e < 128 * kSrvMaxK; e += 256) {
-        const int l = e >> 7, jj = e & 127;  // sv[l][jj]
-        sv[e] = (j0 + jj < n && l < k) ? q.vout[(int64_t)l * n + j0 + jj] : 0.f;
-      }
-      __syncthreads();
-#pragma unroll
-      for (int a = 0; a < 2; ++a) {
-        const int64_t r = rbase + warp * 2 + a;
-        if (r >= m) continue;
-#pragma unroll
-        for (int h = 0; h < 4; ++h) {
-          const int jj = lane + 32 * h;
-          const float x = (j0 + jj < n) ? __ldg(A + r * n + j0 + jj) : 0.f;
-#pragma unroll
-          for (int l = 0; l < kSrvMaxK; ++l) acc[a][l] = fmaf(x, sv[l * 128 + jj], acc[a][l]);
+            for (int l = 0; l < kSrvMaxK; ++l) acc[l] = fmaf(x, ostage[l * kSrvOtherChunk + jj], acc[l]);
+          }
         }
       }
-    }
-#pragma unroll
-    for (int a = 0; a < 2; ++a) {
-      const int64_t r = rbase + warp * 2 + a;
       float mine = 0.f;
 #pragma unroll
       for (int l = 0; l < kSrvMaxK; ++l) {
-        const float s = warp_sumf(acc[a][l]);
-        mine = (lane == l) ? s : mine;
+        const float t = warp_sumf(acc[l]);
+        mine = (lane == l) ? t : mine;
       }
-      if (r < m && lane < k) {
-        const double sg = q.sigma[lane];
-        q.other[(int64_t)lane * m + r] = sg > 0.0 ? (float)((double)mine / sg) : 0.f;
+      if (r < u1 && lane < k) {
+        const double sg = s2hist[lane];
+        q.hU[(int64_t)lane * m + r] = sg > 0.0 ? (float)((double)mine / sqrt(sg)) : 0.f;
       }
     }
   } else {
-    // V[j][l] = sum_r A[r][j] U[r][l] / sigma_l; U = vout (m x k), staged row-major sv[rr][l]
-    const int64_t j = (int64_t)it.block * 128 + (threadIdx.x & 127);
-    const int half = threadIdx.x >> 7;
-    float acc[kSrvMaxK / 2];
+    // V[j][l] = sum_r A[r][j] U[r][l] / sigma_l; this CTA's columns of V, one per thread,
+    // U staged in chunks of kSrvOtherChunk rows (row-major) in shared memory
+    const int64_t Rn = (n + C - 1) / C;
+    const int64_t c0 = min(n, (int64_t)rank * Rn), c1 = min(n, c0 + Rn);
+    for (int64_t jb = c0; jb < c1; jb += kSrvPowerThreads) {
+      const int64_t j = jb + threadIdx.x;
+      float acc[kSrvMaxK];
 #pragma unroll
-    for (int l = 0; l < kSrvMaxK / 2; ++l) acc[l] = 0.f;
-    for (int64_t rb = 0; rb < m; rb += 128) {
-      __syncthreads();
-      for (int e = threadIdx.x; e < 128 * kSrvMaxK; e += 256) {
-        const int rr = e / kSrvMaxK, l = e % kSrvMaxK;
-        sv[e] = (rb + rr < m && l < k) ? q.vout[(int64_t)l * m + rb + rr] : 0.f;
+      for (int l = 0; l < kSrvMaxK; ++l) acc[l] = 0.f;
+      for (int64_t rb = 0; rb < m; rb += kSrvOtherChunk) {
+        __syncthreads();
+        for (int e = threadIdx.x; e < kSrvOtherChunk * kSrvMaxK; e += kSrvPowerThreads) {
+          const int rr = e / kSrvMaxK, l = e % kSrvMaxK;
+          ostage[e] = (rb + rr < m && l < k) ? q.vout[(int64_t)l * m + rb + rr] : 0.f;
+        }
+        __syncthreads();
+        const int64_t rn = min((int64_t)kSrvOtherChunk, m - rb);
+        if (j < c1) {
+          for (int64_t rr = 0; rr < rn; ++rr) {
+            const float x = __ldg(A + (rb + rr) * n + j);
+            const float *ur = ostage + rr * kSrvMaxK;  // same address across the warp
+#pragma unroll
+            for (int l = 0; l < kSrvMaxK; ++l) acc[l] = fmaf(x, ur[l], acc[l]);
+          }
+        }
       }
-      __syncthreads();
-      const int64_t rn = min((int64_t)128, m - rb);
-      for (int64_t rr = 0; rr < rn; ++rr) {
-        const float x = j < n ? __ldg(A + (rb + rr) * n + j) : 0.f;
-        const float *ur = sv + rr * kSrvMaxK + half * (kSrvMaxK / 2);  // same address across the warp
+      if (j < c1) {
 #pragma unroll
-        for (int l = 0; l < kSrvMaxK / 2; ++l) acc[l] = fmaf(x, ur[l], acc[l]);
-      }
-    }
-    if (j < n) {
-#pragma unroll
-      for (int l = 0; l < kSrvMaxK / 2; ++l) {
-        const int lg = half * (kSrvMaxK / 2) + l;
-        if (lg < k) {
-          const double sg = q.sigma[lg];
-          q.other[(int64_t)lg * n + j] = sg > 0.0 ? (float)((double)acc[l] / sg) : 0.f;
+        for (int l = 0; l < kSrvMaxK; ++l) {
+          if (l < k) {
+            const double sg = s2hist[l];
+            q.hV[(int64_t)l * n + j] = sg > 0.0 ? (float)((double)acc[l] / sqrt(sg)) : 0.f;
+          }
         }
       }
     }
+  }
+  // the power vectors (this CTA's rows) and, from rank 0, sigma and the per-triplet info
+  float *hvec = q.trans ? q.hU : q.hV;
+  for (int l = 0; l < k; ++l)
+    for (int64_t r = r0 + threadIdx.x; r < r1; r += kSrvPowerThreads) hvec[(int64_t)l * d + r] = q.vout[(int64_t)l * d + r];
+  if (rank == 0) {
+    for (int l = threadIdx.x; l < k; l += kSrvPowerThreads) {
+      q.hS[l] = sqrt(s2hist[l]);
+      for (int t = 0; t < 4; ++t) q.hInfo[4 * l + t] = q.info[4 * l + t];
+    }
+  }
+  __threadfence_system();
+  cluster_sync_all();
+  if (rank == 0 && threadIdx.x == 0) {
+    __threadfence_system();
+    asm volatile("st.release.sys.global.u32 [%0], %1;" ::"l"(q.hFlag), "r"(1u) : "memory");
   }
 }
 
@@ -559,13 +601,6 @@ tsvd_status launch_srv_power(const SrvReq *reqs, int n_reqs, int cluster, size_t
   cfg.attrs = at;
   cfg.numAttrs = 1;
   TSVD_CUDA(cudaLaunchKernelEx(&cfg, srv_power_kernel, reqs));
-  TSVD_LAUNCHED();
-  return TSVD_OK;
-}
-
-tsvd_status launch_srv_other(const SrvReq *reqs, const SrvOtherItem *items, int n_items, cudaStream_t stream) {
-  if (n_items <= 0) return TSVD_OK;
-  srv_other_kernel<<<n_items, 256, 0, stream>>>(reqs, items);
   TSVD_LAUNCHED();
   return TSVD_OK;
 }

@@ -8,8 +8,11 @@
 //   2. grouped power: one thread-block cluster per request runs Alg. 1/2 for
 //      all k triplets (Hotelling deflation of the FP32 copy, FP64 Rayleigh
 //      quotient and convergence test);
-//   3. grouped other factor: U = A V Sigma^-1 (m >= n) or V = A^T U Sigma^-1
-//      (m < n), Alg. 1 l.11-13 / l.15-17.
+//      then, in the same cluster, the other factor: U = A V Sigma^-1 (m >= n)
+//      or V = A^T U Sigma^-1 (m < n), Alg. 1 l.11-13 / l.15-17; the cluster
+//      writes U, sigma, V and the per-triplet info straight into the
+//      request's page-locked, device-mapped staging and raises the request's
+//      completion flag there, so each request completes on its own.
 #pragma once
 
 #include <stdint.h>
@@ -35,9 +38,16 @@ struct SrvReq {
   double eps;
   int32_t max_iter;
   int32_t sign_convention;
+  const int32_t *iters_override;  // k applications per triplet (convergence test skipped), or null
   uint32_t key0, key1;  // Philox key of the start draws (splitmix64 of the seed)
   int32_t cluster;      // CTAs that run this request's power method (1, 2, 4, 8)
   int32_t resident;     // 1: the power kernel keeps the CTA's rows of G32 in shared memory
+  // host-mapped staging (device addresses of page-locked host memory)
+  float *hU;            // m x k column-major
+  float *hV;            // n x k column-major
+  double *hS;           // k
+  int32_t *hInfo;       // 4 k
+  uint32_t *hFlag;      // set to 1 once everything above is written
 };
 
 // Work item of the grouped SYRK: request, tile row, tile column (ti >= tj).
@@ -49,8 +59,7 @@ constexpr int kSrvTile = 64;         // SYRK tile edge
 constexpr int kSrvMaxDim = 2048;     // largest d the cluster power kernel takes
 constexpr int kSrvMaxK = 32;         // largest k
 constexpr int kSrvPowerThreads = 256;
-constexpr int kSrvOtherRows = 16;     // rows of U per block of the tall other-factor kernel
-constexpr int kSrvOtherCols = 128;    // columns of V per block of the wide one
+constexpr int kSrvOtherChunk = 128;   // rows of V (tall) or U (wide) staged per step of the other factor
 
 // rows of G each CTA of a cluster owns: ceil(d / cluster) rounded up to 4
 __host__ __device__ inline int64_t srv_rows_per_cta(int64_t d, int64_t cluster) {
@@ -63,10 +72,5 @@ size_t srv_power_smem(int64_t d, int cluster, int resident);
 tsvd_status launch_srv_syrk(const SrvReq *reqs, const SrvTile *tiles, int n_tiles, cudaStream_t stream);
 // All requests of one launch share the cluster size; `smem` covers the largest.
 tsvd_status launch_srv_power(const SrvReq *reqs, int n_reqs, int cluster, size_t smem, cudaStream_t stream);
-// Work items: (request, 16-row block of U) or (request, 128-column block of V).
-struct SrvOtherItem {
-  int32_t req, block;
-};
-tsvd_status launch_srv_other(const SrvReq *reqs, const SrvOtherItem *items, int n_items, cudaStream_t stream);
 
 }  // namespace tsvd

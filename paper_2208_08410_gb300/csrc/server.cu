@@ -1,20 +1,25 @@
 // t-SVD server: continuous batching of many small requests on one GPU.
 //
-// The server owns one device arena (the HBM budget), a scheduler thread and
-// `n_streams` CUDA streams.  Requests are admitted first in, first out while
-// the arena and the in-flight limit allow.  Admitted requests are launched in
-// waves: a wave takes up to `max_wave` of them, copies their matrices in,
-// runs the three grouped launches of serve.cuh over all of them (one power
-// launch per cluster size) and copies the results out, all on one stream, and
-// ends with an event.  Waves on different streams overlap on the device, so
-// requests that arrive while others run are admitted as memory frees up and
-// start without waiting for the running waves.  The scheduler polls the
-// events, completes the requests of finished waves and releases their memory.
+// The server owns two arenas allocated once: the device budget (each admitted
+// request's A, Gram matrices, vectors and scalars) and a page-locked,
+// device-mapped staging area (each request's results and completion flag).
+// Requests are admitted first in, first out while both arenas and the
+// in-flight limit allow.  Admitted requests are launched in waves: a wave
+// takes up to `max_wave` of them, copies their matrices in and runs the
+// grouped launches of serve.cuh over all of them on one of `n_streams`
+// streams.  Each request's cluster writes its results into its staging and
+// raises its flag, so the scheduler completes requests one by one as their
+// flags appear (their device memory is released at once); the wave's event
+// only releases its descriptors and its stream.  Waves on different streams
+// overlap on the device, so requests that arrive while others run are
+// admitted as memory frees up and start without waiting for the running ones.
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <condition_variable>
 #include <cstring>
 #include <deque>
+#include <list>
 #include <map>
 #include <memory>
 #include <mutex>
@@ -31,20 +36,38 @@ namespace {
 constexpr size_t kAlign = 256;
 inline size_t al(size_t x) { return (x + kAlign - 1) & ~(kAlign - 1); }
 
-// First-fit allocator over one device allocation; free ranges are kept by
+// First-fit allocator over one allocation (device memory, or page-locked host
+// memory mapped into the device's address space); free ranges are kept by
 // offset and merged with their neighbours on release.
 class Arena {
  public:
-  unsigned char *base = nullptr;
+  unsigned char *base = nullptr;   // address the host uses
+  unsigned char *dbase = nullptr;  // address kernels use
+  bool host = false;
   size_t size = 0, used = 0, peak = 0;
   std::map<size_t, size_t> free_;  // offset -> bytes
 
-  tsvd_status init(size_t bytes) {
+  tsvd_status init(size_t bytes, bool on_host) {
     bytes = bytes & ~(kAlign - 1);
-    if (cudaMalloc(&base, bytes) != cudaSuccess) {
-      cudaGetLastError();
-      set_error_text("server: cudaMalloc of the device budget failed");
-      return TSVD_ENOMEM;
+    host = on_host;
+    if (!on_host) {
+      if (cudaMalloc(&base, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        set_error_text("server: cudaMalloc of the device budget failed");
+        return TSVD_ENOMEM;
+      }
+      dbase = base;
+    } else {
+      if (cudaHostAlloc(reinterpret_cast<void **>(&base), bytes, cudaHostAllocMapped | cudaHostAllocPortable) !=
+          cudaSuccess) {
+        cudaGetLastError();
+        base = nullptr;
+        set_error_text("server: cudaHostAlloc of the staging area failed");
+        return TSVD_ENOMEM;
+      }
+      void *d = nullptr;
+      TSVD_CUDA(cudaHostGetDevicePointer(&d, base, 0));
+      dbase = static_cast<unsigned char *>(d);
     }
     size = bytes;
     free_[0] = bytes;
@@ -83,8 +106,13 @@ class Arena {
     }
   }
   void destroy() {
-    if (base) cudaFree(base);
-    base = nullptr;
+    if (base) {
+      if (host)
+        cudaFreeHost(base);
+      else
+        cudaFree(base);
+    }
+    base = dbase = nullptr;
   }
 };
 
@@ -100,23 +128,30 @@ struct Request {
   float *U = nullptr;
   double *sigma = nullptr;
   float *V = nullptr;
-  size_t off = 0, bytes = 0;  // arena region
+  std::vector<int32_t> iters;   // forced applications per triplet (empty: convergence test)
+  size_t off = 0, bytes = 0;    // device arena region
+  size_t soff = 0, sbytes = 0;  // staging region
+  bool admitted = false;
   SrvReq dq{};
   bool done = false;
   tsvd_request_info rec{};
 };
 using ReqPtr = std::shared_ptr<Request>;
 
-// device region of one request: A, G64, G32, V64, sig2, info, vout, other, sigma
+// device region of one request: A, G64, G32, V64, sig2, info, vout, forced iteration counts
 size_t request_bytes(int64_t m, int64_t n, int64_t k) {
-  const int64_t d = std::min(m, n), od = std::max(m, n);
+  const int64_t d = std::min(m, n);
   return al(m * n * 4) + al(d * d * 8) + al(d * d * 4) + al(d * k * 8) + al(k * 8) + al(k * 16) + al(d * k * 4) +
-         al(od * k * 4) + al(k * 8);
+         al(k * 4);
+}
+// staging region: flag, info, sigma, U, V
+size_t staging_bytes(int64_t m, int64_t n, int64_t k) {
+  return al(64) + al(k * 16) + al(k * 8) + al(m * k * 4) + al(n * k * 4);
 }
 
-void carve(Request &r, unsigned char *p) {
+void carve(Request &r, unsigned char *p, unsigned char *sp_dev) {
   const int64_t m = r.m, n = r.n, k = r.k;
-  const int64_t d = std::min(m, n), od = std::max(m, n);
+  const int64_t d = std::min(m, n);
   SrvReq &q = r.dq;
   q.A = reinterpret_cast<const float *>(p);
   p += al(m * n * 4);
@@ -132,9 +167,16 @@ void carve(Request &r, unsigned char *p) {
   p += al(k * 16);
   q.vout = reinterpret_cast<float *>(p);
   p += al(d * k * 4);
-  q.other = reinterpret_cast<float *>(p);
-  p += al(od * k * 4);
-  q.sigma = reinterpret_cast<double *>(p);
+  q.iters_override = r.iters.empty() ? nullptr : reinterpret_cast<const int32_t *>(p);
+  q.hFlag = reinterpret_cast<uint32_t *>(sp_dev);
+  sp_dev += al(64);
+  q.hInfo = reinterpret_cast<int32_t *>(sp_dev);
+  sp_dev += al(k * 16);
+  q.hS = reinterpret_cast<double *>(sp_dev);
+  sp_dev += al(k * 8);
+  q.hU = reinterpret_cast<float *>(sp_dev);
+  sp_dev += al(m * k * 4);
+  q.hV = reinterpret_cast<float *>(sp_dev);
   q.m = m;
   q.n = n;
   q.trans = m < n ? 1 : 0;  // Eq. 3: the left vectors from A A^T when m < n
@@ -147,41 +189,39 @@ void carve(Request &r, unsigned char *p) {
   q.key1 = (uint32_t)(key >> 32);
 }
 
-struct Slot {  // one stream and the pinned staging of the wave it runs
+struct Slot {  // one stream and the page-locked descriptors of the wave it runs
   cudaStream_t stream = nullptr;
   cudaEvent_t done = nullptr;
-  unsigned char *stage = nullptr;  // pinned: descriptors, then info of every request
+  unsigned char *stage = nullptr;
   size_t stage_cap = 0;
   bool busy = false;
   std::vector<ReqPtr> reqs;
-  size_t dev_off = 0, dev_bytes = 0;  // descriptor arrays in the arena
-  size_t info_off = 0;                // offset of the info area in stage
-  double launched_s = 0.0;
+  size_t dev_off = 0, dev_bytes = 0;  // descriptor arrays in the device arena
   int64_t wave = 0;
 };
 
 }  // namespace
-
 }  // namespace tsvd
 
 struct tsvd_server_s {
   tsvd_server_options opt{};
   int device = 0;
-  tsvd::Arena arena;
+  tsvd::Arena arena, staging;
   std::vector<tsvd::Slot> slots;
   std::mutex mu;
   std::condition_variable cv_done, cv_work;
-  std::deque<tsvd::ReqPtr> pending;                     // submitted, not admitted
-  std::deque<tsvd::ReqPtr> admitted;                    // in the arena, not launched
-  std::unordered_map<uint64_t, tsvd::ReqPtr> table;     // every request not yet waited for
+  std::deque<tsvd::ReqPtr> pending;                  // submitted, not admitted
+  std::deque<tsvd::ReqPtr> admitted;                 // in the arenas, not launched
+  std::list<tsvd::ReqPtr> running;                   // launched, flag not seen yet
+  std::unordered_map<uint64_t, tsvd::ReqPtr> table;  // every request not yet waited for
   uint64_t next_id = 1;
-  int64_t inflight = 0;                                 // admitted and not completed
+  int64_t inflight = 0;                              // admitted and not completed
   bool stop = false;
   std::thread thr;
   std::chrono::steady_clock::time_point t0;
   tsvd_server_stats stats{};
   std::string err;
-  int32_t cluster_table[6] = {1, 1, 2, 4, 8, 8};        // d <= 64, 128, 256, 512, 1024, 2048
+  int32_t cluster_table[6] = {1, 2, 4, 8, 8, 8};     // d <= 64, 128, 256, 512, 1024, 2048
   double busy_since = -1.0;
 
   double now() const {
@@ -198,17 +238,24 @@ int bucket_of(int64_t d) {
   return b;
 }
 
-int cluster_for(const tsvd_server_s *s, int64_t d) {
-  int c = s->cluster_table[bucket_of(d)];
-  c = std::min(c, s->opt.cluster_cap);
+int clamp_cluster(int64_t d, int c) {
   while (c > 1 && srv_rows_per_cta(d, c) * (c - 1) >= d) c >>= 1;  // no CTA of the cluster without rows
   return std::max(c, 1);
+}
+
+int cluster_for(const tsvd_server_s *s, int64_t d) {
+  return clamp_cluster(d, std::min(s->cluster_table[bucket_of(d)], s->opt.cluster_cap));
 }
 
 size_t power_smem_budget() {
   DeviceInfo di;
   if (device_info(&di) != TSVD_OK) return 48 * 1024;
-  return di.smem_optin > 2048 ? di.smem_optin - 2048 : di.smem_optin;  // room for the static arrays
+  const size_t static_bytes = 24 * 1024;  // the power kernel's static shared arrays, rounded up
+  return di.smem_optin > static_bytes ? di.smem_optin - static_bytes : 0;
+}
+
+uint32_t flag_of(const tsvd_server_s *sv, const Request &r) {
+  return *reinterpret_cast<const volatile uint32_t *>(sv->staging.base + r.soff);
 }
 
 // Build and enqueue one wave on slot `s` (scheduler thread, lock not held).
@@ -226,7 +273,6 @@ tsvd_status launch_wave(tsvd_server_s *sv, Slot &s) {
     return std::make_pair(a->dq.cluster, a->dq.resident) < std::make_pair(b->dq.cluster, b->dq.resident);
   });
   std::vector<SrvTile> tiles;
-  std::vector<SrvOtherItem> items;
   std::vector<int64_t> tile_cost;
   for (size_t i = 0; i < rs.size(); ++i) {
     const Request &r = *rs[i];
@@ -237,11 +283,8 @@ tsvd_status launch_wave(tsvd_server_s *sv, Slot &s) {
         tiles.push_back({(int32_t)i, ti, tj, 0});
         tile_cost.push_back(K);
       }
-    const int64_t nb = r.m >= r.n ? ceil_div(r.m, kSrvOtherRows) : ceil_div(r.n, kSrvOtherCols);
-    for (int64_t b = 0; b < nb; ++b) items.push_back({(int32_t)i, (int32_t)b});
   }
-  // longest tiles first, so the tail of the launch is short
-  {
+  {  // longest tiles first, so the tail of the launch is short
     std::vector<size_t> idx(tiles.size());
     for (size_t i = 0; i < idx.size(); ++i) idx[i] = i;
     std::stable_sort(idx.begin(), idx.end(), [&](size_t a, size_t b) { return tile_cost[a] > tile_cost[b]; });
@@ -249,44 +292,44 @@ tsvd_status launch_wave(tsvd_server_s *sv, Slot &s) {
     for (size_t i = 0; i < idx.size(); ++i) t2[i] = tiles[idx[i]];
     tiles.swap(t2);
   }
-  const size_t b_req = al(rs.size() * sizeof(SrvReq)), b_tiles = al(tiles.size() * sizeof(SrvTile)),
-               b_items = al(items.size() * sizeof(SrvOtherItem));
-  size_t b_info = 0;
-  for (auto &r : rs) b_info += al(r->k * 16);
-  const size_t need_dev = b_req + b_tiles + b_items, need_stage = need_dev + b_info;
-  if (need_stage > s.stage_cap) {
+  const size_t b_req = al(rs.size() * sizeof(SrvReq)), b_tiles = al(tiles.size() * sizeof(SrvTile));
+  const size_t need = b_req + b_tiles;
+  if (need > s.stage_cap) {
     if (s.stage) cudaFreeHost(s.stage);
     s.stage = nullptr;
     s.stage_cap = 0;
-    TSVD_CUDA(cudaHostAlloc(reinterpret_cast<void **>(&s.stage), need_stage, cudaHostAllocPortable));
-    s.stage_cap = need_stage;
+    TSVD_CUDA(cudaHostAlloc(reinterpret_cast<void **>(&s.stage), need, cudaHostAllocPortable));
+    s.stage_cap = need;
   }
   {
     std::lock_guard<std::mutex> lk(sv->mu);
-    if (!sv->arena.alloc(need_dev, &s.dev_off)) {
+    if (!sv->arena.alloc(need, &s.dev_off)) {
       set_error_text("server: no arena room for the wave descriptors");
       return TSVD_ENOMEM;
     }
   }
-  s.dev_bytes = need_dev;
+  s.dev_bytes = need;
   unsigned char *dev = sv->arena.base + s.dev_off;
   SrvReq *hreq = reinterpret_cast<SrvReq *>(s.stage);
-  for (size_t i = 0; i < rs.size(); ++i) hreq[i] = rs[i]->dq;
+  for (size_t i = 0; i < rs.size(); ++i) {
+    hreq[i] = rs[i]->dq;
+    *reinterpret_cast<volatile uint32_t *>(sv->staging.base + rs[i]->soff) = 0u;  // completion flag
+  }
   std::memcpy(s.stage + b_req, tiles.data(), tiles.size() * sizeof(SrvTile));
-  std::memcpy(s.stage + b_req + b_tiles, items.data(), items.size() * sizeof(SrvOtherItem));
-  s.info_off = need_dev;
   cudaStream_t st = s.stream;
-  // inputs
-  for (auto &r : rs)
+  for (auto &r : rs) {
     TSVD_CUDA(cudaMemcpyAsync(const_cast<float *>(r->dq.A), r->A, (size_t)r->m * r->n * 4, cudaMemcpyHostToDevice, st));
-  TSVD_CUDA(cudaMemcpyAsync(dev, s.stage, need_dev, cudaMemcpyHostToDevice, st));
+    if (r->dq.iters_override)
+      TSVD_CUDA(cudaMemcpyAsync(const_cast<int32_t *>(r->dq.iters_override), r->iters.data(), r->iters.size() * 4,
+                                cudaMemcpyHostToDevice, st));
+  }
+  TSVD_CUDA(cudaMemcpyAsync(dev, s.stage, need, cudaMemcpyHostToDevice, st));
   const SrvReq *dreq = reinterpret_cast<const SrvReq *>(dev);
   // 1. grouped SYRK
   TSVD_TRY(launch_srv_syrk(dreq, reinterpret_cast<const SrvTile *>(dev + b_req), (int)tiles.size(), st));
-  // 2. grouped power, one launch per (cluster, residency) run of the sorted requests
+  // 2. grouped power + other factor, one launch per (cluster, residency) run of the sorted requests
   for (size_t i = 0; i < rs.size();) {
-    size_t j = i;
-    size_t smem = 0;
+    size_t j = i, smem = 0;
     while (j < rs.size() && rs[j]->dq.cluster == rs[i]->dq.cluster && rs[j]->dq.resident == rs[i]->dq.resident) {
       smem = std::max(smem, srv_power_smem(std::min(rs[j]->m, rs[j]->n), rs[j]->dq.cluster, rs[j]->dq.resident));
       ++j;
@@ -294,58 +337,42 @@ tsvd_status launch_wave(tsvd_server_s *sv, Slot &s) {
     TSVD_TRY(launch_srv_power(dreq + i, (int)(j - i), rs[i]->dq.cluster, smem, st));
     i = j;
   }
-  // 3. grouped other factor
-  TSVD_TRY(launch_srv_other(dreq, reinterpret_cast<const SrvOtherItem *>(dev + b_req + b_tiles), (int)items.size(), st));
-  // outputs
-  size_t io = s.info_off;
-  for (auto &r : rs) {
-    const SrvReq &q = r->dq;
-    const int64_t k = r->k;
-    const float *usrc = q.trans ? q.vout : q.other;
-    const float *vsrc = q.trans ? q.other : q.vout;
-    TSVD_CUDA(cudaMemcpyAsync(r->U, usrc, (size_t)r->m * k * 4, cudaMemcpyDeviceToHost, st));
-    TSVD_CUDA(cudaMemcpyAsync(r->V, vsrc, (size_t)r->n * k * 4, cudaMemcpyDeviceToHost, st));
-    TSVD_CUDA(cudaMemcpyAsync(r->sigma, q.sigma, (size_t)k * 8, cudaMemcpyDeviceToHost, st));
-    TSVD_CUDA(cudaMemcpyAsync(s.stage + io, q.info, (size_t)k * 16, cudaMemcpyDeviceToHost, st));
-    io += al(k * 16);
-  }
   TSVD_CUDA(cudaEventRecord(s.done, st));
   return TSVD_OK;
 }
 
-// Complete the requests of a finished wave (lock held by the caller).
-void finish_wave(tsvd_server_s *sv, Slot &s, tsvd_status st) {
-  size_t io = s.info_off;
-  const double t = sv->now();
-  for (auto &r : s.reqs) {
-    int flags = 0, status = TSVD_OK;
-    int64_t apps = 0;
-    if (st == TSVD_OK) {
-      const int32_t *info = reinterpret_cast<const int32_t *>(s.stage + io);
-      for (int l = 0; l < r->k; ++l) {
-        apps += info[4 * l];
-        if (info[4 * l + 1] == 1) flags |= TSVD_FLAG_NOCONV;
-        if (info[4 * l + 1] == 2) flags |= TSVD_FLAG_RANK;
-      }
-      for (int l = 1; l < r->k; ++l)
-        if (r->sigma[l] > r->sigma[l - 1]) flags |= TSVD_FLAG_NONMONOTONE;
-      status = (flags & TSVD_FLAG_RANK) ? TSVD_ERANK : (flags & TSVD_FLAG_NOCONV) ? TSVD_ENOCONV : TSVD_OK;
-    } else {
-      status = st;
+// Complete one request (lock held): status and flags from its staged info.
+void complete(tsvd_server_s *sv, const ReqPtr &r, tsvd_status st) {
+  int flags = 0, status = st;
+  int64_t apps = 0;
+  if (st == TSVD_OK) {
+    std::atomic_thread_fence(std::memory_order_acquire);
+    const unsigned char *sp = sv->staging.base + r->soff;
+    const int32_t *info = reinterpret_cast<const int32_t *>(sp + al(64));
+    const double *sg = reinterpret_cast<const double *>(sp + al(64) + al(r->k * 16));
+    for (int l = 0; l < r->k; ++l) {
+      apps += info[4 * l];
+      if (info[4 * l + 1] == 1) flags |= TSVD_FLAG_NOCONV;
+      if (info[4 * l + 1] == 2) flags |= TSVD_FLAG_RANK;
     }
-    io += al(r->k * 16);
-    r->rec.status = status;
-    r->rec.flags = flags;
-    r->rec.applications = apps;
-    r->rec.done_s = t;
-    r->done = true;
-    sv->arena.release(r->off, r->bytes);
-    --sv->inflight;
-    if (status == TSVD_OK || status == TSVD_ENOCONV || status == TSVD_ERANK)
-      ++sv->stats.completed;
-    else
-      ++sv->stats.failed;
+    for (int l = 1; l < r->k; ++l)
+      if (sg[l] > sg[l - 1]) flags |= TSVD_FLAG_NONMONOTONE;
+    status = (flags & TSVD_FLAG_RANK) ? TSVD_ERANK : (flags & TSVD_FLAG_NOCONV) ? TSVD_ENOCONV : TSVD_OK;
   }
+  r->rec.status = status;
+  r->rec.flags = flags;
+  r->rec.applications = apps;
+  r->rec.done_s = sv->now();
+  r->done = true;
+  sv->arena.release(r->off, r->bytes);
+  --sv->inflight;
+  if (status == TSVD_OK || status == TSVD_ENOCONV || status == TSVD_ERANK)
+    ++sv->stats.completed;
+  else
+    ++sv->stats.failed;
+}
+
+void retire_slot(tsvd_server_s *sv, Slot &s) {
   if (s.dev_bytes) sv->arena.release(s.dev_off, s.dev_bytes);
   s.dev_bytes = 0;
   s.reqs.clear();
@@ -358,28 +385,45 @@ void scheduler(tsvd_server_s *sv) {
   std::unique_lock<std::mutex> lk(sv->mu);
   while (true) {
     bool progressed = false;
-    // completions
+    // requests whose cluster raised the flag
+    for (auto it = sv->running.begin(); it != sv->running.end();) {
+      if (flag_of(sv, **it) != 0u) {
+        complete(sv, *it, TSVD_OK);
+        it = sv->running.erase(it);
+        progressed = true;
+      } else {
+        ++it;
+      }
+    }
+    // finished waves: release descriptors; a failed wave fails what it has not completed
     for (auto &s : sv->slots) {
       if (!s.busy) continue;
       const cudaError_t q = cudaEventQuery(s.done);
       if (q == cudaErrorNotReady) continue;
-      tsvd_status st = TSVD_OK;
-      if (q != cudaSuccess) {
-        sv->err = std::string("server: wave failed: ") + cudaGetErrorString(q);
-        st = TSVD_ECUDA;
+      if (q != cudaSuccess) sv->err = std::string("server: wave failed: ") + cudaGetErrorString(q);
+      for (auto &r : s.reqs) {
+        if (r->done) continue;
+        complete(sv, r, (q == cudaSuccess && flag_of(sv, *r) != 0u) ? TSVD_OK : TSVD_ECUDA);
+        sv->running.remove(r);
       }
-      finish_wave(sv, s, st);
+      retire_slot(sv, s);
       progressed = true;
     }
     if (progressed) sv->cv_done.notify_all();
     // admission, first in first out
     while (!sv->pending.empty() && sv->inflight < sv->opt.max_inflight) {
       ReqPtr r = sv->pending.front();
-      size_t off = 0;
+      size_t off = 0, soff = 0;
       if (!sv->arena.alloc(r->bytes, &off)) break;
+      if (!sv->staging.alloc(r->sbytes, &soff)) {
+        sv->arena.release(off, r->bytes);
+        break;
+      }
       sv->pending.pop_front();
       r->off = off;
-      carve(*r, sv->arena.base + off);
+      r->soff = soff;
+      r->admitted = true;
+      carve(*r, sv->arena.base + off, sv->staging.dbase + soff);
       r->rec.admit_s = sv->now();
       ++sv->inflight;
       sv->admitted.push_back(r);
@@ -401,11 +445,17 @@ void scheduler(tsvd_server_s *sv) {
       lk.unlock();
       const tsvd_status st = launch_wave(sv, s);
       lk.lock();
-      for (auto &r : s.reqs) r->rec.cluster = r->dq.cluster;
+      for (auto &r : s.reqs) {
+        r->rec.cluster = r->dq.cluster;
+        if (st == TSVD_OK) sv->running.push_back(r);
+      }
       if (st != TSVD_OK) {
         sv->err = std::string("server: launching a wave failed: ") + tsvd_last_cuda_error();
+        lk.unlock();
         cudaStreamSynchronize(s.stream);
-        finish_wave(sv, s, st);
+        lk.lock();
+        for (auto &r : s.reqs) complete(sv, r, st);
+        retire_slot(sv, s);
         sv->cv_done.notify_all();
       }
       progressed = true;
@@ -438,6 +488,73 @@ __global__ void fill_uniform_kernel(float *a, int64_t count, uint32_t seed) {
   }
 }
 
+// Time the power kernel on `nreq` synthetic d x d requests with cluster c
+// (`iters` applications per triplet, k = 2).  Returns milliseconds.
+tsvd_status time_power(tsvd_server_s *sv, int64_t d, int c, int nreq, int iters, cudaStream_t st, cudaEvent_t e0,
+                       cudaEvent_t e1, double *ms_out) {
+  const int k = 2;
+  const size_t per = request_bytes(d, d, k), sper = staging_bytes(d, d, k);
+  const int T = (int)ceil_div(d, kSrvTile);
+  const size_t ntiles = (size_t)nreq * T * (T + 1) / 2;
+  const size_t need = per * nreq + al(nreq * sizeof(SrvReq)) + al(ntiles * sizeof(SrvTile));
+  size_t off = 0, soff = 0;
+  {
+    std::lock_guard<std::mutex> lk(sv->mu);
+    if (!sv->arena.alloc(need, &off)) return TSVD_EBUDGET;
+    if (!sv->staging.alloc(sper * nreq, &soff)) {
+      sv->arena.release(off, need);
+      return TSVD_EBUDGET;
+    }
+  }
+  const size_t smem_cap = power_smem_budget();
+  const int resident = srv_power_smem(d, c, 1) <= smem_cap ? 1 : 0;
+  unsigned char *base = sv->arena.base + off;
+  std::vector<SrvReq> reqs(nreq);
+  std::vector<SrvTile> tiles;
+  tsvd_status ls = TSVD_OK;
+  for (int i = 0; i < nreq && ls == TSVD_OK; ++i) {
+    Request r;
+    r.m = d;
+    r.n = d;
+    r.k = k;
+    r.eps = 1e-300;  // never met: every triplet runs exactly max_iter applications
+    r.max_iter = iters;
+    r.seed = (uint64_t)i;
+    carve(r, base + per * i, sv->staging.dbase + soff + sper * i);
+    r.dq.cluster = c;
+    r.dq.resident = resident;
+    reqs[i] = r.dq;
+    fill_uniform_kernel<<<64, 256, 0, st>>>(const_cast<float *>(r.dq.A), d * d, (uint32_t)i);
+    if (cudaGetLastError() != cudaSuccess) ls = TSVD_ECUDA;
+    for (int ti = 0; ti < T; ++ti)
+      for (int tj = 0; tj <= ti; ++tj) tiles.push_back({i, ti, tj, 0});
+  }
+  SrvReq *dreq = reinterpret_cast<SrvReq *>(base + per * nreq);
+  SrvTile *dtiles = reinterpret_cast<SrvTile *>(base + per * nreq + al(nreq * sizeof(SrvReq)));
+  if (ls == TSVD_OK && cudaMemcpyAsync(dreq, reqs.data(), nreq * sizeof(SrvReq), cudaMemcpyHostToDevice, st) != cudaSuccess)
+    ls = TSVD_ECUDA;
+  if (ls == TSVD_OK &&
+      cudaMemcpyAsync(dtiles, tiles.data(), tiles.size() * sizeof(SrvTile), cudaMemcpyHostToDevice, st) != cudaSuccess)
+    ls = TSVD_ECUDA;
+  if (ls == TSVD_OK) ls = launch_srv_syrk(dreq, dtiles, (int)tiles.size(), st);
+  const size_t smem = srv_power_smem(d, c, resident);
+  if (ls == TSVD_OK) ls = launch_srv_power(dreq, nreq, c, smem, st);  // warm-up
+  if (ls == TSVD_OK && cudaEventRecord(e0, st) != cudaSuccess) ls = TSVD_ECUDA;
+  if (ls == TSVD_OK) ls = launch_srv_power(dreq, nreq, c, smem, st);
+  if (ls == TSVD_OK && cudaEventRecord(e1, st) != cudaSuccess) ls = TSVD_ECUDA;
+  float ms = 0.f;
+  if (ls == TSVD_OK && (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
+    ls = TSVD_ECUDA;
+  cudaStreamSynchronize(st);
+  {
+    std::lock_guard<std::mutex> lk(sv->mu);
+    sv->arena.release(off, need);
+    sv->staging.release(soff, sper * nreq);
+  }
+  *ms_out = ms;
+  return ls;
+}
+
 }  // namespace
 }  // namespace tsvd
 
@@ -450,9 +567,10 @@ tsvd_status tsvd_server_options_init(tsvd_server_options *opt) {
   std::memset(opt, 0, sizeof *opt);
   opt->device_budget = (size_t)8 << 30;
   opt->max_inflight = 4096;
-  opt->n_streams = 4;
-  opt->max_wave = 512;
+  opt->n_streams = 8;
+  opt->max_wave = 64;
   opt->cluster_cap = 8;
+  opt->host_staging = (size_t)2 << 30;
   return TSVD_OK;
 }
 
@@ -462,12 +580,14 @@ tsvd_status tsvd_server_create(tsvd_server_t *out, const tsvd_server_options *op
   tsvd_server_options opt;
   tsvd_server_options_init(&opt);
   if (opt_in) {
+    const tsvd_server_options d = opt;
     opt = *opt_in;
-    if (!opt.device_budget) opt.device_budget = (size_t)8 << 30;
-    if (!opt.max_inflight) opt.max_inflight = 4096;
-    if (!opt.n_streams) opt.n_streams = 4;
-    if (!opt.max_wave) opt.max_wave = 512;
-    if (!opt.cluster_cap) opt.cluster_cap = 8;
+    if (!opt.device_budget) opt.device_budget = d.device_budget;
+    if (!opt.max_inflight) opt.max_inflight = d.max_inflight;
+    if (!opt.n_streams) opt.n_streams = d.n_streams;
+    if (!opt.max_wave) opt.max_wave = d.max_wave;
+    if (!opt.cluster_cap) opt.cluster_cap = d.cluster_cap;
+    if (!opt.host_staging) opt.host_staging = d.host_staging;
   }
   if (opt.max_inflight < 1 || opt.n_streams < 1 || opt.n_streams > 64 || opt.max_wave < 1 ||
       (opt.cluster_cap != 1 && opt.cluster_cap != 2 && opt.cluster_cap != 4 && opt.cluster_cap != 8))
@@ -476,8 +596,11 @@ tsvd_status tsvd_server_create(tsvd_server_t *out, const tsvd_server_options *op
   sv->opt = opt;
   sv->t0 = std::chrono::steady_clock::now();
   cudaGetDevice(&sv->device);
-  tsvd_status st = sv->arena.init(opt.device_budget);
+  tsvd_status st = sv->arena.init(opt.device_budget, false);
+  if (st == TSVD_OK) st = sv->staging.init(opt.host_staging, true);
   if (st != TSVD_OK) {
+    sv->arena.destroy();
+    sv->staging.destroy();
     delete sv;
     return st;
   }
@@ -496,12 +619,15 @@ tsvd_status tsvd_server_create(tsvd_server_t *out, const tsvd_server_options *op
 }
 
 tsvd_status tsvd_server_submit(tsvd_server_t sv, const float *A, int64_t m, int64_t n, int32_t k, double eps,
-                               int32_t max_iter, uint64_t seed, int32_t sign_convention, float *U, double *sigma,
-                               float *V, uint64_t *ticket) {
+                               int32_t max_iter, uint64_t seed, int32_t sign_convention, const int32_t *iters_override,
+                               float *U, double *sigma, float *V, uint64_t *ticket) {
   if (!sv || !A || !U || !sigma || !V || !ticket || m <= 0 || n <= 0) return TSVD_EINVAL;
   const int64_t d = std::min(m, n);
   if (k < 1 || k > d) return TSVD_EINVAL;
-  if (!(eps > 0.0 && eps < 1.0)) return TSVD_EINVAL;
+  if (!iters_override && !(eps > 0.0 && eps < 1.0)) return TSVD_EINVAL;
+  if (iters_override)
+    for (int32_t l = 0; l < k; ++l)
+      if (iters_override[l] < 1) return TSVD_EINVAL;
   if (d > kSrvMaxDim || k > kSrvMaxK) return TSVD_EUNSUPPORTED;
   auto r = std::make_shared<Request>();
   r->A = A;
@@ -515,8 +641,10 @@ tsvd_status tsvd_server_submit(tsvd_server_t sv, const float *A, int64_t m, int6
   r->U = U;
   r->sigma = sigma;
   r->V = V;
+  if (iters_override) r->iters.assign(iters_override, iters_override + k);
   r->bytes = request_bytes(m, n, k);
-  if (al(r->bytes) > sv->arena.size) return TSVD_EBUDGET;
+  r->sbytes = staging_bytes(m, n, k);
+  if (al(r->bytes) > sv->arena.size || al(r->sbytes) > sv->staging.size) return TSVD_EBUDGET;
   {
     std::lock_guard<std::mutex> lk(sv->mu);
     if (sv->stop) return TSVD_EINVAL;
@@ -543,8 +671,25 @@ tsvd_status tsvd_server_wait(tsvd_server_t sv, uint64_t ticket, double timeout_s
   } else if (!sv->cv_done.wait_for(lk, std::chrono::duration<double>(timeout_s), pred)) {
     return TSVD_ETIMEDOUT;
   }
-  if (info) *info = r->rec;
   sv->table.erase(ticket);
+  const bool staged = r->admitted;
+  lk.unlock();
+  if (staged) {
+    // results from the staging into the caller's buffers (the kernel has finished with them)
+    const tsvd_status s = (tsvd_status)r->rec.status;
+    if (s == TSVD_OK || s == TSVD_ENOCONV || s == TSVD_ERANK) {
+      const unsigned char *sp = sv->staging.base + r->soff + al(64) + al(r->k * 16);
+      std::memcpy(r->sigma, sp, (size_t)r->k * 8);
+      sp += al(r->k * 8);
+      std::memcpy(r->U, sp, (size_t)r->m * r->k * 4);
+      sp += al(r->m * r->k * 4);
+      std::memcpy(r->V, sp, (size_t)r->n * r->k * 4);
+    }
+    lk.lock();
+    sv->staging.release(r->soff, r->sbytes);
+    lk.unlock();
+  }
+  if (info) *info = r->rec;
   return (tsvd_status)r->rec.status;
 }
 
@@ -572,89 +717,46 @@ tsvd_status tsvd_server_autotune(tsvd_server_t sv, int32_t iters) {
   }
   DeviceInfo di;
   TSVD_TRY(device_info(&di));
-  const size_t smem_cap = power_smem_budget();
   cudaStream_t st = nullptr;
   TSVD_CUDA(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
   cudaEvent_t e0, e1;
   TSVD_CUDA(cudaEventCreate(&e0));
   TSVD_CUDA(cudaEventCreate(&e1));
   const int64_t dims[6] = {64, 128, 256, 512, 1024, 2048};
-  const int k = 2;
   tsvd_status result = TSVD_OK;
   for (int b = 0; b < 6 && result == TSVD_OK; ++b) {
     const int64_t d = dims[b];
-    double best = -1.0;
-    int best_c = 1;
+    // per cluster size: one request alone (latency) and as many as fill the GPU (throughput)
+    std::vector<int> cs;
+    std::vector<double> lat, thr;
     for (int c = 1; c <= sv->opt.cluster_cap; c *= 2) {
-      if (c > 1 && srv_rows_per_cta(d, c) * (c - 1) >= d) break;
-      const int resident = srv_power_smem(d, c, 1) <= smem_cap ? 1 : 0;
-      const int nreq = std::max(1, di.sms / c);
-      const size_t per = request_bytes(d, d, k);
-      size_t off = 0;
-      {
-        std::lock_guard<std::mutex> lk(sv->mu);
-        if (!sv->arena.alloc(per * nreq + al(nreq * sizeof(SrvReq)) + al(nreq * (size_t)((d + 63) / 64) *
-                                                                          ((d + 63) / 64 + 1) / 2 * sizeof(SrvTile)),
-                             &off)) {
-          result = TSVD_EBUDGET;
-          break;
-        }
-      }
-      unsigned char *base = sv->arena.base + off;
-      std::vector<SrvReq> reqs(nreq);
-      std::vector<SrvTile> tiles;
-      for (int i = 0; i < nreq; ++i) {
-        Request r;
-        r.m = d;
-        r.n = d;
-        r.k = k;
-        r.eps = 1e-300;  // never met: every triplet runs exactly max_iter applications
-        r.max_iter = iters;
-        r.seed = (uint64_t)i;
-        carve(r, base + per * i);
-        r.dq.cluster = c;
-        r.dq.resident = resident;
-        reqs[i] = r.dq;
-        fill_uniform_kernel<<<64, 256, 0, st>>>(const_cast<float *>(r.dq.A), d * d, (uint32_t)i);
-        if (cudaGetLastError() != cudaSuccess) result = TSVD_ECUDA;
-        const int T = (int)ceil_div(d, kSrvTile);
-        for (int ti = 0; ti < T; ++ti)
-          for (int tj = 0; tj <= ti; ++tj) tiles.push_back({i, ti, tj, 0});
-      }
-      SrvReq *dreq = reinterpret_cast<SrvReq *>(base + per * nreq);
-      SrvTile *dtiles = reinterpret_cast<SrvTile *>(base + per * nreq + al(nreq * sizeof(SrvReq)));
-      cudaError_t ce = cudaMemcpyAsync(dreq, reqs.data(), nreq * sizeof(SrvReq), cudaMemcpyHostToDevice, st);
-      if (ce == cudaSuccess)
-        ce = cudaMemcpyAsync(dtiles, tiles.data(), tiles.size() * sizeof(SrvTile), cudaMemcpyHostToDevice, st);
-      tsvd_status ls = ce == cudaSuccess ? launch_srv_syrk(dreq, dtiles, (int)tiles.size(), st) : TSVD_ECUDA;
-      const size_t smem = srv_power_smem(d, c, resident);
-      if (ls == TSVD_OK) ls = launch_srv_power(dreq, nreq, c, smem, st);  // warm-up
-      if (ls == TSVD_OK && cudaEventRecord(e0, st) != cudaSuccess) ls = TSVD_ECUDA;
-      if (ls == TSVD_OK) ls = launch_srv_power(dreq, nreq, c, smem, st);
-      if (ls == TSVD_OK && cudaEventRecord(e1, st) != cudaSuccess) ls = TSVD_ECUDA;
-      float ms = 0.f;
-      if (ls == TSVD_OK && (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
-        ls = TSVD_ECUDA;
-      cudaStreamSynchronize(st);
-      {
-        std::lock_guard<std::mutex> lk(sv->mu);
-        sv->arena.release(off, per * nreq + al(nreq * sizeof(SrvReq)) +
-                                   al(nreq * (size_t)((d + 63) / 64) * ((d + 63) / 64 + 1) / 2 * sizeof(SrvTile)));
-      }
-      if (ls != TSVD_OK) {
-        result = ls;
-        break;
-      }
-      const double rate = (double)nreq * k * iters / (ms * 1e-3);  // applications per second, whole GPU
-      if (rate > best) {
-        best = rate;
-        best_c = c;
+      if (clamp_cluster(d, c) != c) break;
+      double ms1 = 0.0, msn = 0.0;
+      // as many requests as fill the GPU, within half of the arena
+      const size_t per = request_bytes(d, d, 2) + staging_bytes(d, d, 2);
+      const int nfill = (int)std::max<int64_t>(1, std::min<int64_t>(di.sms / c, (int64_t)(sv->arena.size / 2 / per)));
+      result = time_power(sv, d, c, 1, iters, st, e0, e1, &ms1);
+      if (result == TSVD_OK) result = time_power(sv, d, c, nfill, iters, st, e0, e1, &msn);
+      if (result != TSVD_OK) break;
+      cs.push_back(c);
+      lat.push_back(ms1);
+      thr.push_back((double)nfill / msn);  // requests per millisecond over the whole GPU
+    }
+    if (result != TSVD_OK || cs.empty()) break;
+    // the highest throughput among sizes whose lone request is within 4x of the fastest one
+    double best_lat = lat[0];
+    for (double x : lat) best_lat = std::min(best_lat, x);
+    int best_c = cs[0];
+    double best_thr = -1.0;
+    for (size_t i = 0; i < cs.size(); ++i) {
+      if (lat[i] > 4.0 * best_lat) continue;
+      if (thr[i] > best_thr) {
+        best_thr = thr[i];
+        best_c = cs[i];
       }
     }
-    if (result == TSVD_OK) {
-      std::lock_guard<std::mutex> lk(sv->mu);
-      sv->cluster_table[b] = best_c;
-    }
+    std::lock_guard<std::mutex> lk(sv->mu);
+    sv->cluster_table[b] = best_c;
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
@@ -691,6 +793,7 @@ void tsvd_server_destroy(tsvd_server_t sv) {
     if (s.stage) cudaFreeHost(s.stage);
   }
   sv->arena.destroy();
+  sv->staging.destroy();
   delete sv;
 }
 

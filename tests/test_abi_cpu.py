@@ -210,5 +210,5 @@ def test_server_options_validation(lib):
         B.tsvd_server_options_init(C.byref(o))
         setattr(o, field, bad)
         assert B.tsvd_server_create(C.byref(h), C.byref(o)) == B.TSVD_EINVAL, field
-    assert B.tsvd_server_submit(None, None, 10, 10, 1, 1e-6, 10, 0, 0, None, None, None, None) == B.TSVD_EINVAL
+    assert B.tsvd_server_submit(None, None, 10, 10, 1, 1e-6, 10, 0, 0, None, None, None, None, None) == B.TSVD_EINVAL
     assert B.tsvd_server_cluster_for(None, 100) == 0

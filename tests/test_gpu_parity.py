@@ -137,12 +137,19 @@ def test_power_dense_follows_oracle(l):
     dG64, dG32 = dev(Gf), dev(Gf.astype(np.float32))
     dV = dev(np.asfortranarray(V).T.copy()) if l else None  # column-major n x l == row-major l x n
     ds2 = dev(s2) if l else None
-    for j in range(l):  # Hotelling deflation of the FP32 copy, one triplet at a time
-        assert B.tsvd_gram_deflate(n, dG32.data_ptr(), dV[j].data_ptr(), ds2[j:].data_ptr(), S()) == 0
+    for j in range(l):  # Hotelling deflation in FP64, FP32 copy rounded from it, one triplet at a time
+        assert B.tsvd_gram_deflate(n, dG64.data_ptr(), dG32.data_ptr(), dV[j].data_ptr(), ds2[j:].data_ptr(),
+                                   S()) == 0
     if l:
-        want = (Gf - V @ np.diag(s2) @ V.T).astype(np.float32)
-        got32 = dG32.cpu().numpy()
-        assert np.max(np.abs(got32 - want)) <= 4 * 2.0 ** -24 * np.max(np.abs(Gf))
+        want = Gf - V @ np.diag(s2) @ V.T
+        got64 = dG64.cpu().numpy()
+        iu = np.triu_indices(n)
+        # l FP64 fused multiply-adds per entry
+        assert np.max(np.abs(got64[iu] - want[iu])) <= 4 * l * 2.0 ** -53 * np.max(np.abs(Gf))
+        il = np.tril_indices(n, -1)
+        assert np.array_equal(got64[il], Gf[il])  # the strict lower triangle is not touched
+        got32 = dG32.cpu().numpy().astype(np.float64)
+        assert np.max(np.abs(got32 - want) - 2.0 ** -24 * np.abs(want)) <= 8 * l * 2.0 ** -53 * np.max(np.abs(Gf))
     scratch_b = B.tsvd_power_scratch_bytes(n, l)
     scr = torch.empty(scratch_b, dtype=torch.uint8, device="cuda")
     info = torch.zeros(4, dtype=torch.int32, device="cuda")
@@ -163,7 +170,7 @@ def test_power_dense_follows_oracle(l):
             assert abs(int(inf[0]) - res.iters) <= 1
         assert abs(np.linalg.norm(got) - 1.0) < 1e-12
         assert ref.vector_angle(got, res.v) < 1e-5
-        s2_ref = float(res.v @ Gf @ res.v)
+        s2_ref = float(res.v @ Gf @ res.v)  # sigma_l^2 = v^T G v with the undeflated G
         assert abs(out_s2.item() - s2_ref) / s2_ref < 1e-6
 
 
