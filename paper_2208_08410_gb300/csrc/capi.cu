@@ -88,12 +88,19 @@ struct tsvd_plan_s {
   size_t ws = 0;
   size_t o_G64 = 0, o_G32 = 0, o_V64 = 0, o_V32 = 0, o_sig2 = 0, o_sigma = 0, o_info = 0;
   size_t o_pscr = 0, b_pscr = 0, o_gscr = 0, b_gscr = 0, o_ring = 0, b_slot = 0;
+  size_t o_gscr2 = 0;  // second Gram scratch: in-core tensor-core passes pipeline prep and SYRK
   size_t o_res = 0, o_ubuf = 0, b_ubuf = 0;
   size_t o_v = 0, o_vn = 0, o_w = 0, o_x64 = 0, o_Vr = 0, o_vsc = 0, o_flag = 0;
+  // column-chunked CSR operator (v and w larger than what L2 holds)
+  int csr_nch = 0;            // chunks (0: the fused single-pass kernel)
+  int64_t csr_cw = 0;         // columns per chunk
+  bool csr_sorted = true;     // every row's columns ascending (host CSR: checked at plan time)
+  size_t o_csr_y = 0, o_csr_split = 0, b_split_slot = 0;
   int vec_grid = 0;
   // runtime objects (created on first factor, on the device current then)
   int device = -1;
-  cudaStream_t copy_stream = nullptr, d2h_stream = nullptr;
+  cudaStream_t copy_stream = nullptr, d2h_stream = nullptr, prep_stream = nullptr;
+  cudaEvent_t ev_gstart = nullptr, ev_prep[2] = {nullptr, nullptr}, ev_syrk[2] = {nullptr, nullptr};
   std::vector<cudaEvent_t> ev_ready, ev_free;
   cudaEvent_t ev_u_ready[2] = {nullptr, nullptr}, ev_u_free[2] = {nullptr, nullptr};
   cudaEvent_t ev_t[4] = {nullptr, nullptr, nullptr, nullptr};
@@ -103,7 +110,7 @@ struct tsvd_plan_s {
 
 namespace {
 
-tsvd_status validate_csr_host(const tsvd_matrix *A) {
+tsvd_status validate_csr_host(const tsvd_matrix *A, bool *sorted) {
   const int64_t m = A->m, n = A->n, nnz = A->nnz;
   const int64_t *rp = A->row_ptr;
   if (rp[0] != 0 || rp[m] != nnz) return TSVD_EINVAL;
@@ -112,6 +119,14 @@ tsvd_status validate_csr_host(const tsvd_matrix *A) {
   const int32_t *ci = A->col_idx;
   for (int64_t p = 0; p < nnz; ++p)
     if (ci[p] < 0 || (int64_t)ci[p] >= n) return TSVD_EINVAL;
+  bool srt = true;
+  for (int64_t r = 0; r < m && srt; ++r)
+    for (int64_t p = rp[r] + 1; p < rp[r + 1]; ++p)
+      if (ci[p] < ci[p - 1]) {
+        srt = false;
+        break;
+      }
+  *sorted = srt;
   return TSVD_OK;
 }
 
@@ -169,6 +184,10 @@ tsvd_status plan_dense(tsvd_plan_s *p) {
   p->b_gscr = gram_tc_scratch_bytes(rows, n, prec);
   p->o_gscr = c.take(p->b_gscr + 256);
   if (mode == MODE_RESIDENT) p->o_res = c.take(resident_bytes);
+  // in core, a second scratch lets the prep of chunk c+1 run beside the SYRK of chunk c
+  if (mode != MODE_STREAM && prec != TSVD_GRAM_FP32 && p->n_chunks > 1 &&
+      (!budget || c.off + p->b_gscr + 256 + (host_u ? 2 * (size_t)round_up(rows * k * 4, 256) : 0) <= budget))
+    p->o_gscr2 = c.take(p->b_gscr + 256);
   if (host_u) {
     p->b_ubuf = (size_t)round_up(rows * k * 4, 256);
     p->o_ubuf = c.take(2 * p->b_ubuf);
@@ -215,8 +234,17 @@ tsvd_status plan_csr(tsvd_plan_s *p, const tsvd_matrix *A) {
   rows = std::max<int64_t>(1, std::min<int64_t>(rows, m));
   const size_t budget = p->opt.device_budget;
   const size_t resident_bytes = (size_t)round_up((m + 1) * 8, 256) + 2 * (size_t)round_up(std::max<int64_t>(p->nnz, 1) * 4, 256);
+  // v and w together beyond ~64 MB (half of L2): the column-chunked operator, with
+  // chunks of at most ~40 MB of v (or w)
+  if ((int64_t)n * 8 > ((int64_t)64 << 20)) {
+    p->csr_nch = (int)std::min<int64_t>(8, std::max<int64_t>(2, ceil_div((int64_t)n * 4, (int64_t)40 << 20)));
+    p->csr_cw = ceil_div(n, p->csr_nch);
+  }
+  const int nch = p->csr_nch;
+  auto split_bytes = [&](int64_t r) -> size_t { return nch ? (size_t)round_up(r * (nch - 1) * 4, 256) : 0; };
   auto slot_bytes = [&](int64_t r, int64_t maxnnz) -> size_t {
-    return (size_t)round_up((r + 1) * 8, 256) + 2 * (size_t)round_up(std::max<int64_t>(maxnnz, 1) * 4, 256);
+    return (size_t)round_up((r + 1) * 8, 256) + 2 * (size_t)round_up(std::max<int64_t>(maxnnz, 1) * 4, 256) +
+           split_bytes(r);
   };
   auto max_nnz_of = [&](int64_t r) -> int64_t {
     if (!host_a) return 0;
@@ -234,8 +262,9 @@ tsvd_status plan_csr(tsvd_plan_s *p, const tsvd_matrix *A) {
   if (budget) {
     auto total = [&](int64_t r, int64_t mx) -> size_t {
       size_t s = fixed + (host_u ? 2 * (size_t)round_up(r * k * 4, 256) : 0);
-      if (mode == MODE_STREAM) s += R * slot_bytes(r, mx);
+      if (mode == MODE_STREAM) s += R * slot_bytes(r, mx) + (nch ? (size_t)round_up(r * 4, 256) : 0);
       if (mode == MODE_RESIDENT) s += resident_bytes;
+      if (mode != MODE_STREAM && nch) s += (size_t)round_up(m * 4, 256) + split_bytes(m);
       return s;
     };
     while (rows > 1024 && total(rows, maxnnz) > budget) {
@@ -251,12 +280,18 @@ tsvd_status plan_csr(tsvd_plan_s *p, const tsvd_matrix *A) {
   p->max_block_nnz = maxnnz;
   if (mode == MODE_STREAM) {
     p->b_slot = slot_bytes(rows, maxnnz);
+    p->b_split_slot = split_bytes(rows);
     p->o_ring = c.take(p->b_slot * R);
   }
   if (mode == MODE_RESIDENT) p->o_res = c.take(resident_bytes);
   if (host_u) {
     p->b_ubuf = (size_t)round_up(rows * k * 4, 256);
     p->o_ubuf = c.take(2 * p->b_ubuf);
+  }
+  if (nch) {
+    // y of the rows a pass covers, and (in core) every row's split points
+    p->o_csr_y = c.take((size_t)(mode == MODE_STREAM ? rows : m) * 4);
+    if (mode != MODE_STREAM) p->o_csr_split = c.take(split_bytes(m));
   }
   p->ws = c.off;
   if (budget && p->ws > budget) return TSVD_EBUDGET;
@@ -301,6 +336,7 @@ tsvd_status tsvd_plan(tsvd_plan_t *out, const tsvd_matrix *A, int64_t k, double 
   *workspace_bytes = 0;
   tsvd_options opt;
   if (opt_in) opt = *opt_in; else tsvd_options_init(&opt);
+  bool csr_sorted = true;
   if (A->kind != TSVD_DENSE_F32_ROWMAJOR && A->kind != TSVD_CSR_F32_I32_I64) return TSVD_EINVAL;
   if (A->location != TSVD_HOST && A->location != TSVD_DEVICE) return TSVD_EINVAL;
   if (A->m <= 0 || A->n <= 0) return TSVD_EINVAL;
@@ -320,7 +356,7 @@ tsvd_status tsvd_plan(tsvd_plan_t *out, const tsvd_matrix *A, int64_t k, double 
     if (A->nnz < 0 || !A->row_ptr) return TSVD_EINVAL;
     if (A->nnz > 0 && (!A->col_idx || !A->values)) return TSVD_EINVAL;
     if (A->n > 0x7fffffffLL) return TSVD_EUNSUPPORTED;
-    if (A->location == TSVD_HOST) TSVD_TRY(validate_csr_host(A));
+    if (A->location == TSVD_HOST) TSVD_TRY(validate_csr_host(A, &csr_sorted));
   }
   if (A->m < A->n) return TSVD_EUNSUPPORTED;  // the m < n branch (Eq. 3) is not built
   if (A->kind == TSVD_DENSE_F32_ROWMAJOR && A->n > 32768) return TSVD_EUNSUPPORTED;
@@ -334,6 +370,7 @@ tsvd_status tsvd_plan(tsvd_plan_t *out, const tsvd_matrix *A, int64_t k, double 
   try {
     p->kind = A->kind;
     p->location = A->location;
+    p->csr_sorted = csr_sorted;
     p->m = A->m;
     p->n = A->n;
     p->ld = A->kind == TSVD_DENSE_F32_ROWMAJOR ? A->ld : 0;
@@ -377,6 +414,12 @@ void tsvd_destroy(tsvd_plan_t p) {
     for (auto e : p->ev_c) cudaEventDestroy(e);
     if (p->copy_stream) cudaStreamDestroy(p->copy_stream);
     if (p->d2h_stream) cudaStreamDestroy(p->d2h_stream);
+    if (p->prep_stream) cudaStreamDestroy(p->prep_stream);
+    if (p->ev_gstart) cudaEventDestroy(p->ev_gstart);
+    for (int i = 0; i < 2; ++i) {
+      if (p->ev_prep[i]) cudaEventDestroy(p->ev_prep[i]);
+      if (p->ev_syrk[i]) cudaEventDestroy(p->ev_syrk[i]);
+    }
     if (cur != p->device) cudaSetDevice(cur);
   }
   delete p;
@@ -406,6 +449,14 @@ tsvd_status ensure_runtime(tsvd_plan_s *p) {
     TSVD_CUDA(cudaEventCreateWithFlags(&p->ev_u_free[i], cudaEventDisableTiming));
   }
   for (int i = 0; i < 4; ++i) TSVD_CUDA(cudaEventCreate(&p->ev_t[i]));
+  if (p->o_gscr2) {
+    TSVD_CUDA(cudaStreamCreateWithFlags(&p->prep_stream, cudaStreamNonBlocking));
+    TSVD_CUDA(cudaEventCreateWithFlags(&p->ev_gstart, cudaEventDisableTiming));
+    for (int i = 0; i < 2; ++i) {
+      TSVD_CUDA(cudaEventCreateWithFlags(&p->ev_prep[i], cudaEventDisableTiming));
+      TSVD_CUDA(cudaEventCreateWithFlags(&p->ev_syrk[i], cudaEventDisableTiming));
+    }
+  }
   return TSVD_OK;
 }
 
@@ -420,6 +471,7 @@ struct Run {
   std::vector<double> copy_bytes;  // bytes of each timed copy
   double kernel_ms = 0.0;          // timed operator kernels (CSR pair)
   int64_t kernel_launches = 0;
+  bool chunked = false;            // this factorisation uses the column-chunked CSR operator
 };
 
 // Events around a block copy on the copy stream (only with time_kernels).
@@ -504,9 +556,9 @@ tsvd_status release_slot(Run &r, int slot) {
 
 tsvd_status gram_dispatch(const float *A, int64_t rows, int64_t n, int64_t ld, double *G, int prec,
                           void *scr, size_t scr_bytes, cudaStream_t s, cudaEvent_t ev0 = nullptr,
-                          cudaEvent_t ev1 = nullptr) {
+                          cudaEvent_t ev1 = nullptr, bool reset_status = true) {
   if (prec == TSVD_GRAM_FP32) return launch_gram_simt(A, rows, n, ld, G, s, ev0, ev1);
-  return launch_gram_tc(A, rows, n, ld, G, prec, scr, scr_bytes, s, ev0, ev1);
+  return launch_gram_tc(A, rows, n, ld, G, prec, scr, scr_bytes, s, ev0, ev1, reset_status);
 }
 
 tsvd_status left_pass_dense(Run &r, const float *V32, const double *sigma, float *U) {
@@ -573,19 +625,44 @@ tsvd_status factor_dense(Run &r, float *U, double *sigma_out, float *V_out, tsvd
   TSVD_CUDA(cudaEventRecord(p->ev_t[0], r.cs));
   // ---- Gram pass: B = sum_b A_b^T A_b
   TSVD_CUDA(cudaMemsetAsync(G64, 0, (size_t)n * n * 8, r.cs));
+  void *gbuf[2] = {gscr, p->o_gscr2 ? ws + p->o_gscr2 : nullptr};
+  // status words of the tensor-core scratch, zeroed once for the whole pass
+  // (the 256-byte aligned scratch starts with its status word)
+  if (p->opt.precision != TSVD_GRAM_FP32) TSVD_CUDA(cudaMemsetAsync(gscr, 0, 4, r.cs));
+  if (p->o_gscr2) TSVD_CUDA(cudaMemsetAsync(gbuf[1], 0, 4, r.cs));
+  if (p->o_gscr2) {
+    // two scratch buffers: the prep of chunk c (prep stream, one CTA per SM) waits
+    // for the SYRK that last read its buffer (chunk c-2); the SYRK of chunk c
+    // (caller's stream) waits for its prep, so prep c+1 runs beside SYRK c
+    TSVD_CUDA(cudaEventRecord(p->ev_gstart, r.cs));
+    TSVD_CUDA(cudaStreamWaitEvent(p->prep_stream, p->ev_gstart, 0));
+  }
   for (int64_t c = 0; c < p->n_chunks; ++c) {
     const int64_t r0 = c * p->chunk_rows, rows = std::min(p->chunk_rows, p->m - r0);
     const float *Ab;
     int64_t ldb;
     int slot;
     TSVD_TRY(acquire_dense(r, r0, rows, &Ab, &ldb, &slot, true));
-    TSVD_TRY(gram_dispatch(Ab, rows, n, ldb, G64, p->opt.precision, gscr, p->b_gscr, r.cs,
-                           timed ? p->ev_k[2 * c] : nullptr, timed ? p->ev_k[2 * c + 1] : nullptr));
+    if (p->o_gscr2) {
+      const int b = (int)(c & 1);
+      if (p->mode == MODE_RESIDENT) TSVD_CUDA(cudaStreamWaitEvent(p->prep_stream, p->ev_ready[0], 0));
+      if (c >= 2) TSVD_CUDA(cudaStreamWaitEvent(p->prep_stream, p->ev_syrk[b], 0));
+      TSVD_TRY(launch_gram_tc_prep(Ab, rows, n, ldb, p->opt.precision, gbuf[b], p->b_gscr, true, p->prep_stream));
+      TSVD_CUDA(cudaEventRecord(p->ev_prep[b], p->prep_stream));
+      TSVD_CUDA(cudaStreamWaitEvent(r.cs, p->ev_prep[b], 0));
+      TSVD_TRY(launch_gram_tc_syrk(rows, n, G64, p->opt.precision, gbuf[b], p->b_gscr, r.cs,
+                                   timed ? p->ev_k[2 * c] : nullptr, timed ? p->ev_k[2 * c + 1] : nullptr, false));
+      TSVD_CUDA(cudaEventRecord(p->ev_syrk[b], r.cs));
+    } else {
+      TSVD_TRY(gram_dispatch(Ab, rows, n, ldb, G64, p->opt.precision, gscr, p->b_gscr, r.cs,
+                             timed ? p->ev_k[2 * c] : nullptr, timed ? p->ev_k[2 * c + 1] : nullptr, false));
+    }
     TSVD_TRY(release_slot(r, slot));
   }
-  int32_t gram_err = 0;
+  int32_t gram_err = 0, gram_err2 = 0;
   if (p->opt.precision != TSVD_GRAM_FP32)
     TSVD_CUDA(cudaMemcpyAsync(&gram_err, gscr, 4, cudaMemcpyDeviceToHost, r.cs));
+  if (p->o_gscr2) TSVD_CUDA(cudaMemcpyAsync(&gram_err2, gbuf[1], 4, cudaMemcpyDeviceToHost, r.cs));
   TSVD_TRY(launch_symmetrize(n, G64, G32, r.cs));
   TSVD_CUDA(cudaEventRecord(p->ev_t[1], r.cs));
 
@@ -641,7 +718,7 @@ tsvd_status factor_dense(Run &r, float *U, double *sigma_out, float *V_out, tsvd
   }
   int flags = 0;
   int64_t apps = 0;
-  if (gram_err) flags |= TSVD_FLAG_TIMEOUT;
+  if (gram_err || gram_err2) flags |= TSVD_FLAG_TIMEOUT;
   for (int64_t l = 0; l < k; ++l) {
     if (hinfo[4 * l + 2]) flags |= TSVD_FLAG_TIMEOUT;
     if (hinfo[4 * l + 1] == 1) flags |= TSVD_FLAG_NOCONV;
@@ -675,17 +752,26 @@ struct CsrBlock {
   const float *va;
   int64_t rows;
   int slot;
+  int32_t *split;  // streamed blocks: the slot's split-point buffer (chunked operator)
 };
 
+// flag bit 0: invalid structure; bit 1: some row's columns are not ascending
 __global__ void csr_validate_kernel(int64_t m, int64_t n, int64_t nnz, const int64_t *rp, const int32_t *ci,
                                     int *flag) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i <= m; i += (int64_t)gridDim.x * blockDim.x) {
-    if (i == 0 && rp[0] != 0) atomicExch(flag, 1);
-    if (i == m && rp[m] != nnz) atomicExch(flag, 1);
-    if (i < m && rp[i + 1] < rp[i]) atomicExch(flag, 1);
+    if (i == 0 && rp[0] != 0) atomicOr(flag, 1);
+    if (i == m && rp[m] != nnz) atomicOr(flag, 1);
+    if (i < m && rp[i + 1] < rp[i]) atomicOr(flag, 1);
+    if (i < m && rp[i] >= 0 && rp[i + 1] <= nnz) {
+      for (int64_t p = rp[i] + 1; p < rp[i + 1]; ++p)
+        if (ci[p] < ci[p - 1]) {
+          atomicOr(flag, 2);
+          break;
+        }
+    }
   }
   for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < nnz; p += (int64_t)gridDim.x * blockDim.x)
-    if (ci[p] < 0 || (int64_t)ci[p] >= n) atomicExch(flag, 1);
+    if (ci[p] < 0 || (int64_t)ci[p] >= n) atomicOr(flag, 1);
 }
 
 tsvd_status acquire_csr(Run &r, int64_t b, const std::vector<int64_t> &bnd_nnz, CsrBlock *out) {
@@ -695,6 +781,7 @@ tsvd_status acquire_csr(Run &r, int64_t b, const std::vector<int64_t> &bnd_nnz, 
   const int64_t e0 = bnd_nnz[b], e1 = bnd_nnz[b + 1];
   out->rows = s1 - s0;
   out->slot = -1;
+  out->split = nullptr;
   if (p->mode == MODE_DEVICE) {
     out->rp = A->row_ptr + s0;
     out->ci = A->col_idx + e0;
@@ -718,6 +805,9 @@ tsvd_status acquire_csr(Run &r, int64_t b, const std::vector<int64_t> &bnd_nnz, 
   int32_t *ci = reinterpret_cast<int32_t *>(base + round_up((p->chunk_rows + 1) * 8, 256));
   float *va = reinterpret_cast<float *>(base + round_up((p->chunk_rows + 1) * 8, 256) +
                                         round_up(std::max<int64_t>(p->max_block_nnz, 1) * 4, 256));
+  if (p->b_split_slot)
+    out->split = reinterpret_cast<int32_t *>(reinterpret_cast<unsigned char *>(va) +
+                                             round_up(std::max<int64_t>(p->max_block_nnz, 1) * 4, 256));
   TSVD_CUDA(cudaStreamWaitEvent(p->copy_stream, p->ev_free[s], 0));
   TSVD_TRY(copy_event(r, true));
   TSVD_CUDA(cudaMemcpyAsync(rp, A->row_ptr + s0, (size_t)(out->rows + 1) * 8, cudaMemcpyHostToDevice, p->copy_stream));
@@ -738,11 +828,52 @@ tsvd_status acquire_csr(Run &r, int64_t b, const std::vector<int64_t> &bnd_nnz, 
 }
 
 // one application w += A^T (A v), ss += ||A v||^2 over all row blocks; with
-// time_kernels each block's kernel is bracketed by events (read back by
+// time_kernels each block's kernels are bracketed by events (read back by
 // csr_kernel_time once the stream has been synchronised)
 tsvd_status csr_apply(Run &r, const std::vector<int64_t> &bnd, const float *v, float *w, double *ss, int scatter) {
   tsvd_plan_s *p = r.p;
   const bool timed = p->opt.time_kernels != 0;
+  if (r.chunked) {
+    const int nch = p->csr_nch;
+    float *y = reinterpret_cast<float *>(r.ws + p->o_csr_y);
+    if (p->mode != MODE_STREAM) {
+      // in core: chunk-major over every block, so each chunk of v (then of w) stays in L2
+      const int32_t *split = reinterpret_cast<const int32_t *>(r.ws + p->o_csr_split);
+      if (timed) TSVD_CUDA(cudaEventRecord(p->ev_k[0], r.cs));
+      for (int pass = 0; pass < 2; ++pass) {
+        // without the scatter (||A v||^2 only) the second pass is one sweep over y (chunk 0)
+        const int nc = (pass == 1 && !scatter) ? 1 : nch;
+        for (int c = 0; c < nc; ++c)
+          for (int64_t b = 0; b < p->n_chunks; ++b) {
+            CsrBlock blk;
+            TSVD_TRY(acquire_csr(r, b, bnd, &blk));
+            const int64_t r0 = p->block_start[b];
+            if (pass == 0)
+              TSVD_TRY(launch_csr_chunk_y(blk.rows, blk.rp, blk.ci, blk.va, split + r0 * (nch - 1), nch, c, v, y + r0,
+                                          p->avg_nnz, r.cs));
+            else
+              TSVD_TRY(launch_csr_chunk_w(blk.rows, blk.rp, blk.ci, blk.va, split + r0 * (nch - 1), nch, c, y + r0, w,
+                                          ss, scatter, p->avg_nnz, r.cs));
+          }
+      }
+      if (timed) TSVD_CUDA(cudaEventRecord(p->ev_k[1], r.cs));
+      return TSVD_OK;
+    }
+    for (int64_t b = 0; b < p->n_chunks; ++b) {
+      CsrBlock blk;
+      TSVD_TRY(acquire_csr(r, b, bnd, &blk));
+      if (timed) TSVD_CUDA(cudaEventRecord(p->ev_k[2 * b], r.cs));
+      TSVD_TRY(launch_csr_split(blk.rows, blk.rp, blk.ci, nch, p->csr_cw, blk.split, r.cs));
+      for (int c = 0; c < nch; ++c)
+        TSVD_TRY(launch_csr_chunk_y(blk.rows, blk.rp, blk.ci, blk.va, blk.split, nch, c, v, y, p->avg_nnz, r.cs));
+      for (int c = 0; c < (scatter ? nch : 1); ++c)
+        TSVD_TRY(launch_csr_chunk_w(blk.rows, blk.rp, blk.ci, blk.va, blk.split, nch, c, y, w, ss, scatter,
+                                    p->avg_nnz, r.cs));
+      if (timed) TSVD_CUDA(cudaEventRecord(p->ev_k[2 * b + 1], r.cs));
+      TSVD_TRY(release_slot(r, blk.slot));
+    }
+    return TSVD_OK;
+  }
   for (int64_t b = 0; b < p->n_chunks; ++b) {
     CsrBlock blk;
     TSVD_TRY(acquire_csr(r, b, bnd, &blk));
@@ -758,7 +889,8 @@ tsvd_status csr_apply(Run &r, const std::vector<int64_t> &bnd, const float *v, f
 tsvd_status csr_kernel_time(Run &r) {
   tsvd_plan_s *p = r.p;
   if (!p->opt.time_kernels) return TSVD_OK;
-  for (int64_t b = 0; b < p->n_chunks; ++b) {
+  const int64_t pairs = (r.chunked && p->mode != MODE_STREAM) ? 1 : p->n_chunks;
+  for (int64_t b = 0; b < pairs; ++b) {
     float t = 0.f;
     TSVD_CUDA(cudaEventElapsedTime(&t, p->ev_k[2 * b], p->ev_k[2 * b + 1]));
     r.kernel_ms += t;
@@ -798,6 +930,7 @@ tsvd_status factor_csr(Run &r, float *U, double *sigma_out, float *V_out, tsvd_r
   std::vector<int64_t> bnd(p->n_chunks + 1);
   if (p->location == TSVD_HOST) {
     for (int64_t b = 0; b <= p->n_chunks; ++b) bnd[b] = A->row_ptr[p->block_start[b]];
+    r.chunked = p->csr_nch > 0 && p->csr_sorted;
   } else {
     // device CSR: validate on the device, then read the boundary offsets
     TSVD_CUDA(cudaMemsetAsync(flag, 0, 4, r.cs));
@@ -808,7 +941,8 @@ tsvd_status factor_csr(Run &r, float *U, double *sigma_out, float *V_out, tsvd_r
     for (int64_t b = 0; b <= p->n_chunks; ++b)
       TSVD_CUDA(cudaMemcpyAsync(&bnd[b], A->row_ptr + p->block_start[b], 8, cudaMemcpyDeviceToHost, r.cs));
     TSVD_CUDA(cudaStreamSynchronize(r.cs));
-    if (hflag) return TSVD_EINVAL;
+    if (hflag & 1) return TSVD_EINVAL;
+    r.chunked = p->csr_nch > 0 && !(hflag & 2);
   }
   if (p->mode == MODE_RESIDENT) {
     unsigned char *base = ws + p->o_res;
@@ -819,6 +953,15 @@ tsvd_status factor_csr(Run &r, float *U, double *sigma_out, float *V_out, tsvd_r
       TSVD_CUDA(cudaMemcpyAsync(base + ova, A->values, (size_t)p->nnz * 4, cudaMemcpyHostToDevice, r.cs));
     }
     r.h2d += (double)(m + 1) * 8 + (double)p->nnz * 8;
+  }
+  if (r.chunked && p->mode != MODE_STREAM) {
+    // in core: every row's chunk split points, once per factorisation
+    const int64_t *rp_all = p->mode == MODE_DEVICE ? A->row_ptr : reinterpret_cast<const int64_t *>(ws + p->o_res);
+    const int32_t *ci_all = p->mode == MODE_DEVICE
+                                ? A->col_idx
+                                : reinterpret_cast<const int32_t *>(ws + p->o_res + round_up((m + 1) * 8, 256));
+    TSVD_TRY(launch_csr_split(m, rp_all, ci_all, p->csr_nch, p->csr_cw,
+                              reinterpret_cast<int32_t *>(ws + p->o_csr_split), r.cs));
   }
   TSVD_CUDA(cudaEventRecord(p->ev_t[1], r.cs));
 

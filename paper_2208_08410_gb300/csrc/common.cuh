@@ -154,9 +154,18 @@ __device__ __forceinline__ bool grid_barrier(unsigned *bar, int *err) {
 tsvd_status launch_gram_simt(const float *A, int64_t rows, int64_t n, int64_t ld, double *G,
                              cudaStream_t stream, cudaEvent_t ev0 = nullptr, cudaEvent_t ev1 = nullptr);
 size_t gram_tc_scratch_bytes(int64_t rows, int64_t n, int precision);
+// reset_status: zero the scratch's status word first (a caller that runs many
+// chunks zeroes it once, so a timeout in any chunk stays visible)
 tsvd_status launch_gram_tc(const float *A, int64_t rows, int64_t n, int64_t ld, double *G,
                            int precision, void *scratch, size_t scratch_bytes, cudaStream_t stream,
-                           cudaEvent_t ev0 = nullptr, cudaEvent_t ev1 = nullptr);
+                           cudaEvent_t ev0 = nullptr, cudaEvent_t ev1 = nullptr, bool reset_status = true);
+// The two halves of launch_gram_tc, for pipelining the prep of one chunk with
+// the SYRK of the previous one (separate scratch buffers, separate streams).
+tsvd_status launch_gram_tc_prep(const float *A, int64_t rows, int64_t n, int64_t ld, int precision, void *scratch,
+                                size_t scratch_bytes, bool persistent, cudaStream_t stream);
+tsvd_status launch_gram_tc_syrk(int64_t rows, int64_t n, double *G, int precision, void *scratch,
+                                size_t scratch_bytes, cudaStream_t stream, cudaEvent_t ev0 = nullptr,
+                                cudaEvent_t ev1 = nullptr, bool reset_status = true);
 
 size_t power_scratch_bytes(int64_t n, int64_t l);
 tsvd_status launch_power_dense(int64_t n, const float *G32, const double *G64, const double *V64,
@@ -185,6 +194,15 @@ tsvd_status launch_left_dense(const float *A, int64_t rows, int64_t n, int64_t l
 tsvd_status launch_csr_pair(int64_t rows, int64_t n, const int64_t *row_ptr,
                             const int32_t *col_idx, const float *values, const float *v, float *w,
                             double *ss, int scatter, double avg_nnz, cudaStream_t stream);
+// Column-chunked form of the pair (see k_csr.cu): split points, then the two passes.
+tsvd_status launch_csr_split(int64_t rows, const int64_t *row_ptr, const int32_t *col_idx, int nch, int64_t cw,
+                             int32_t *split, cudaStream_t stream);
+tsvd_status launch_csr_chunk_y(int64_t rows, const int64_t *row_ptr, const int32_t *col_idx, const float *values,
+                               const int32_t *split, int nch, int c, const float *v, float *y, double avg_nnz,
+                               cudaStream_t stream);
+tsvd_status launch_csr_chunk_w(int64_t rows, const int64_t *row_ptr, const int32_t *col_idx, const float *values,
+                               const int32_t *split, int nch, int c, const float *y, float *w, double *ss, int scatter,
+                               double avg_nnz, cudaStream_t stream);
 tsvd_status launch_csr_left(int64_t rows, const int64_t *row_ptr, const int32_t *col_idx,
                             const float *values, const float *Vr, int64_t ldk, int64_t k,
                             const double *sigma, float *U, int64_t ldu, double avg_nnz,

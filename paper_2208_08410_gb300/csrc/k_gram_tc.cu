@@ -218,8 +218,11 @@ __global__ void __launch_bounds__(256) prep_kernel(const float *__restrict__ A, 
                                                    void *__restrict__ hi_, void *__restrict__ lo_, int64_t Kp) {
   __shared__ float s[4][32][33];
   const int tx = threadIdx.x, ty = threadIdx.y;
-  const int64_t r0 = (int64_t)blockIdx.x * 32;
-  const int64_t c0 = (int64_t)blockIdx.y * 128;
+  const int64_t row_strips = Kp / 32, strips = row_strips * ((n + 127) / 128);
+  for (int64_t strip = blockIdx.x; strip < strips; strip += gridDim.x) {
+  const int64_t r0 = (strip % row_strips) * 32;
+  const int64_t c0 = (strip / row_strips) * 128;
+  __syncthreads();  // the previous strip's reads of s are done
 #pragma unroll
   for (int t = 0; t < 4; ++t) {
 #pragma unroll
@@ -247,6 +250,7 @@ __global__ void __launch_bounds__(256) prep_kernel(const float *__restrict__ A, 
         }
       }
     }
+  }
   }
 }
 
@@ -532,44 +536,73 @@ static int tc_seg_stages(int precision) {
   return precision == TSVD_GRAM_TF32 ? 4 : 2;
 }
 
-tsvd_status launch_gram_tc(const float *A, int64_t rows, int64_t n, int64_t ld, double *G, int precision,
-                           void *scratch, size_t scratch_bytes, cudaStream_t stream, cudaEvent_t ev0,
-                           cudaEvent_t ev1) {
-  if (rows <= 0) return TSVD_OK;
+namespace {
+
+// Scratch layout of one Gram chunk: status word (first 1024 bytes), then At
+// (n x Kp) per part, each 1024-byte aligned.
+struct TcLayout {
+  int parts = 1;
+  int64_t Kp = 0;
+  int *err = nullptr;
+  void *hi = nullptr, *lo = nullptr;
+};
+
+tsvd_status tc_layout(int64_t rows, int64_t n, int precision, void *scratch, size_t scratch_bytes, TcLayout *L) {
   if (precision != TSVD_GRAM_TF32 && precision != TSVD_GRAM_TF32X3 && precision != TSVD_GRAM_BF16X3)
     return TSVD_EINVAL;
   if (n > (int64_t)TM * 65535) return TSVD_EUNSUPPORTED;
+  if (!scratch || scratch_bytes < gram_tc_scratch_bytes(rows, n, precision)) return TSVD_EINVAL;
+  if ((reinterpret_cast<uintptr_t>(scratch) & 255) != 0) return TSVD_EINVAL;
+  L->parts = tc_parts(precision);
+  L->Kp = padded_k(rows, precision);
+  const int64_t part_bytes = round_up(n * L->Kp * tc_elem(precision), 1024);
+  unsigned char *base = static_cast<unsigned char *>(scratch);
+  L->err = reinterpret_cast<int *>(base);  // status word: 0 ok, nonzero = a bounded wait gave up
+  const uintptr_t al = (reinterpret_cast<uintptr_t>(base) + 1024 + 1023) & ~uintptr_t(1023);
+  L->hi = reinterpret_cast<void *>(al);
+  L->lo = L->parts == 2 ? reinterpret_cast<void *>(al + part_bytes) : L->hi;
+  if (al + (size_t)L->parts * part_bytes > reinterpret_cast<uintptr_t>(base) + scratch_bytes) return TSVD_EINVAL;
+  return TSVD_OK;
+}
+
+}  // namespace
+
+tsvd_status launch_gram_tc_prep(const float *A, int64_t rows, int64_t n, int64_t ld, int precision, void *scratch,
+                                size_t scratch_bytes, bool persistent, cudaStream_t stream) {
+  if (rows <= 0) return TSVD_OK;
   DeviceInfo di;
   TSVD_TRY(device_info(&di));
   if (di.cc_major != 10) return TSVD_EUNSUPPORTED;  // tcgen05 needs the sm_100 family
-  if (!scratch || scratch_bytes < gram_tc_scratch_bytes(rows, n, precision)) return TSVD_EINVAL;
-  if ((reinterpret_cast<uintptr_t>(scratch) & 255) != 0) return TSVD_EINVAL;
-  const int parts = tc_parts(precision);
-  const int64_t Kp = padded_k(rows, precision);
-  const int64_t part_bytes = round_up(n * Kp * tc_elem(precision), 1024);
-  unsigned char *base = static_cast<unsigned char *>(scratch);
-  int *err = reinterpret_cast<int *>(base);  // status word: 0 ok, nonzero = a bounded wait gave up
-  const uintptr_t al = (reinterpret_cast<uintptr_t>(base) + 1024 + 1023) & ~uintptr_t(1023);
-  void *hi = reinterpret_cast<void *>(al);
-  void *lo = parts == 2 ? reinterpret_cast<void *>(al + part_bytes) : hi;
-  if (al + (size_t)parts * part_bytes > reinterpret_cast<uintptr_t>(base) + scratch_bytes) return TSVD_EINVAL;
+  TcLayout L;
+  TSVD_TRY(tc_layout(rows, n, precision, scratch, scratch_bytes, &L));
+  // transpose + rounding (+ split); Kp is a multiple of 32, the prep row tile.  A
+  // persistent grid (one CTA per SM) leaves room on every SM for a running SYRK.
+  const int64_t strips = (L.Kp / 32) * ceil_div(n, 128);
+  const int64_t grid = persistent ? std::min<int64_t>(strips, di.sms) : std::min<int64_t>(strips, 0x7fffffffLL);
+  dim3 block(32, 8);
+  if (precision == TSVD_GRAM_BF16X3)
+    prep_kernel<TSVD_GRAM_BF16X3><<<(unsigned)grid, block, 0, stream>>>(A, rows, n, ld, L.hi, L.lo, L.Kp);
+  else if (precision == TSVD_GRAM_TF32X3)
+    prep_kernel<TSVD_GRAM_TF32X3><<<(unsigned)grid, block, 0, stream>>>(A, rows, n, ld, L.hi, L.lo, L.Kp);
+  else
+    prep_kernel<TSVD_GRAM_TF32><<<(unsigned)grid, block, 0, stream>>>(A, rows, n, ld, L.hi, L.lo, L.Kp);
+  TSVD_LAUNCHED();
+  return TSVD_OK;
+}
 
-  // 1. prep: transpose + rounding (+ split); Kp is a multiple of 32, the prep row tile
-  {
-    dim3 grid((unsigned)ceil_div(Kp, 32), (unsigned)ceil_div(n, 128)), block(32, 8);
-    if (grid.y > 65535 || grid.x > 0x7fffffffu) return TSVD_EUNSUPPORTED;
-    if (precision == TSVD_GRAM_BF16X3)
-      prep_kernel<TSVD_GRAM_BF16X3><<<grid, block, 0, stream>>>(A, rows, n, ld, hi, lo, Kp);
-    else if (precision == TSVD_GRAM_TF32X3)
-      prep_kernel<TSVD_GRAM_TF32X3><<<grid, block, 0, stream>>>(A, rows, n, ld, hi, lo, Kp);
-    else
-      prep_kernel<TSVD_GRAM_TF32><<<grid, block, 0, stream>>>(A, rows, n, ld, hi, lo, Kp);
-    TSVD_LAUNCHED();
-  }
-  // 2. persistent tcgen05 SYRK over the lower-triangle tiles
+tsvd_status launch_gram_tc_syrk(int64_t rows, int64_t n, double *G, int precision, void *scratch, size_t scratch_bytes,
+                                cudaStream_t stream, cudaEvent_t ev0, cudaEvent_t ev1, bool reset_status) {
+  if (rows <= 0) return TSVD_OK;
+  DeviceInfo di;
+  TSVD_TRY(device_info(&di));
+  if (di.cc_major != 10) return TSVD_EUNSUPPORTED;
+  TcLayout L;
+  TSVD_TRY(tc_layout(rows, n, precision, scratch, scratch_bytes, &L));
+  const int64_t Kp = L.Kp;
+  // persistent tcgen05 SYRK over the lower-triangle tiles
   CUtensorMap mh, ml;
-  TSVD_TRY(make_map(&mh, hi, n, Kp, precision));
-  TSVD_TRY(make_map(&ml, lo, n, Kp, precision));
+  TSVD_TRY(make_map(&mh, L.hi, n, Kp, precision));
+  TSVD_TRY(make_map(&ml, L.lo, n, Kp, precision));
   TcArgs a;
   a.G = G;
   a.n = n;
@@ -594,8 +627,8 @@ tsvd_status launch_gram_tc(const float *A, int64_t rows, int64_t n, int64_t ld, 
     a.ksplit = ks;
     a.n_splits = (int)ceil_div(Kp, ks);
   }
-  a.err = err;
-  TSVD_CUDA(cudaMemsetAsync(err, 0, 4, stream));
+  a.err = L.err;
+  if (reset_status) TSVD_CUDA(cudaMemsetAsync(L.err, 0, 4, stream));
   const int64_t units = (int64_t)a.n_tiles * a.n_splits;
   const int grid = (int)std::min<int64_t>(units, di.sms);
   if (ev0) TSVD_CUDA(cudaEventRecord(ev0, stream));
@@ -607,6 +640,14 @@ tsvd_status launch_gram_tc(const float *A, int64_t rows, int64_t n, int64_t ld, 
     TSVD_TRY(launch_syrk<TSVD_GRAM_BF16X3>(mh, ml, a, grid, stream));
   if (ev1) TSVD_CUDA(cudaEventRecord(ev1, stream));
   return TSVD_OK;
+}
+
+tsvd_status launch_gram_tc(const float *A, int64_t rows, int64_t n, int64_t ld, double *G, int precision,
+                           void *scratch, size_t scratch_bytes, cudaStream_t stream, cudaEvent_t ev0,
+                           cudaEvent_t ev1, bool reset_status) {
+  if (rows <= 0) return TSVD_OK;
+  TSVD_TRY(launch_gram_tc_prep(A, rows, n, ld, precision, scratch, scratch_bytes, false, stream));
+  return launch_gram_tc_syrk(rows, n, G, precision, scratch, scratch_bytes, stream, ev0, ev1, reset_status);
 }
 
 }  // namespace tsvd

@@ -26,9 +26,9 @@
 // After the k triplets the same cluster forms the other factor (Alg. 1
 // l.11-13 / l.15-17: U = A V Sigma^-1 for tall requests, V = A^T U Sigma^-1
 // for wide ones), writes U, sigma, V and the per-triplet info into the
-// request's page-locked, device-mapped staging and raises its completion
-// flag there (system-scope release), so a request completes as soon as its
-// own cluster finishes.
+// request's output region and raises its completion flag (a release store
+// into the server's device flag array, which the server copies to the host),
+// so a request completes as soon as its own cluster finishes.
 #include "philox.cuh"
 #include "serve.cuh"
 
@@ -502,7 +502,7 @@ __global__ void __launch_bounds__(kSrvPowerThreads, 1) srv_power_kernel(const Sr
       }
       if (r < u1 && lane < k) {
         const double sg = s2hist[lane];
-        q.hU[(int64_t)lane * m + r] = sg > 0.0 ? (float)((double)mine / sqrt(sg)) : 0.f;
+        q.oU[(int64_t)lane * m + r] = sg > 0.0 ? (float)((double)mine / sqrt(sg)) : 0.f;
       }
     }
   } else {
@@ -537,27 +537,27 @@ __global__ void __launch_bounds__(kSrvPowerThreads, 1) srv_power_kernel(const Sr
         for (int l = 0; l < kSrvMaxK; ++l) {
           if (l < k) {
             const double sg = s2hist[l];
-            q.hV[(int64_t)l * n + j] = sg > 0.0 ? (float)((double)acc[l] / sqrt(sg)) : 0.f;
+            q.oV[(int64_t)l * n + j] = sg > 0.0 ? (float)((double)acc[l] / sqrt(sg)) : 0.f;
           }
         }
       }
     }
   }
   // the power vectors (this CTA's rows) and, from rank 0, sigma and the per-triplet info
-  float *hvec = q.trans ? q.hU : q.hV;
+  float *ovec = q.trans ? q.oU : q.oV;
   for (int l = 0; l < k; ++l)
-    for (int64_t r = r0 + threadIdx.x; r < r1; r += kSrvPowerThreads) hvec[(int64_t)l * d + r] = q.vout[(int64_t)l * d + r];
+    for (int64_t r = r0 + threadIdx.x; r < r1; r += kSrvPowerThreads) ovec[(int64_t)l * d + r] = q.vout[(int64_t)l * d + r];
   if (rank == 0) {
     for (int l = threadIdx.x; l < k; l += kSrvPowerThreads) {
-      q.hS[l] = sqrt(s2hist[l]);
-      for (int t = 0; t < 4; ++t) q.hInfo[4 * l + t] = q.info[4 * l + t];
+      q.oS[l] = sqrt(s2hist[l]);
+      for (int t = 0; t < 4; ++t) q.oInfo[4 * l + t] = q.info[4 * l + t];
     }
   }
   __threadfence_system();
   cluster_sync_all();
   if (rank == 0 && threadIdx.x == 0) {
     __threadfence_system();
-    asm volatile("st.release.sys.global.u32 [%0], %1;" ::"l"(q.hFlag), "r"(1u) : "memory");
+    asm volatile("st.release.sys.global.u32 [%0], %1;" ::"l"(q.flag), "r"(q.ticket) : "memory");
   }
 }
 
@@ -583,8 +583,13 @@ tsvd_status launch_srv_power(const SrvReq *reqs, int n_reqs, int cluster, size_t
   DeviceInfo di;
   TSVD_TRY(device_info(&di));
   if (smem > di.smem_optin) return TSVD_EINVAL;
+  // the kernel's static arrays (~17 KB) count toward the 48 KB a launch gets without
+  // opting in, so the attribute is raised for any size above what is already allowed
   static thread_local size_t attr = 0;
-  if (smem > 48 * 1024 && smem > attr) {
+  if (smem > attr) {
+    cudaFuncAttributes fa;
+    TSVD_CUDA(cudaFuncGetAttributes(&fa, srv_power_kernel));
+    if (fa.sharedSizeBytes + smem > di.smem_optin) return TSVD_EINVAL;
     TSVD_CUDA(cudaFuncSetAttribute(srv_power_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     attr = smem;
   }

@@ -10,9 +10,10 @@
 //      quotient and convergence test);
 //      then, in the same cluster, the other factor: U = A V Sigma^-1 (m >= n)
 //      or V = A^T U Sigma^-1 (m < n), Alg. 1 l.11-13 / l.15-17; the cluster
-//      writes U, sigma, V and the per-triplet info straight into the
-//      request's page-locked, device-mapped staging and raises the request's
-//      completion flag there, so each request completes on its own.
+//      writes U, sigma, V and the per-triplet info into the request's output
+//      region in device memory and then raises the request's completion flag
+//      (a word of a device array the server polls), so each request
+//      completes on its own.
 #pragma once
 
 #include <stdint.h>
@@ -42,12 +43,13 @@ struct SrvReq {
   uint32_t key0, key1;  // Philox key of the start draws (splitmix64 of the seed)
   int32_t cluster;      // CTAs that run this request's power method (1, 2, 4, 8)
   int32_t resident;     // 1: the power kernel keeps the CTA's rows of G32 in shared memory
-  // host-mapped staging (device addresses of page-locked host memory)
-  float *hU;            // m x k column-major
-  float *hV;            // n x k column-major
-  double *hS;           // k
-  int32_t *hInfo;       // 4 k
-  uint32_t *hFlag;      // set to 1 once everything above is written
+  // results in device memory, and the completion flag
+  float *oU;            // m x k column-major
+  float *oV;            // n x k column-major
+  double *oS;           // k
+  int32_t *oInfo;       // 4 k
+  uint32_t *flag;       // set to `ticket` (release, gpu scope) once everything above is written
+  uint32_t ticket;
 };
 
 // Work item of the grouped SYRK: request, tile row, tile column (ti >= tj).

@@ -1,18 +1,22 @@
 // t-SVD server: continuous batching of many small requests on one GPU.
 //
 // The server owns two arenas allocated once: the device budget (each admitted
-// request's A, Gram matrices, vectors and scalars) and a page-locked,
-// device-mapped staging area (each request's results and completion flag).
-// Requests are admitted first in, first out while both arenas and the
-// in-flight limit allow.  Admitted requests are launched in waves: a wave
-// takes up to `max_wave` of them, copies their matrices in and runs the
-// grouped launches of serve.cuh over all of them on one of `n_streams`
-// streams.  Each request's cluster writes its results into its staging and
-// raises its flag, so the scheduler completes requests one by one as their
-// flags appear (their device memory is released at once); the wave's event
-// only releases its descriptors and its stream.  Waves on different streams
-// overlap on the device, so requests that arrive while others run are
-// admitted as memory frees up and start without waiting for the running ones.
+// request's A, Gram matrices, vectors, scalars and results) and a page-locked
+// staging area (each request's results on the host), plus a device array of
+// completion flags with a page-locked mirror.  Requests are admitted first in,
+// first out while both arenas and the in-flight limit allow.  Admitted
+// requests are launched in waves: a wave takes up to `max_wave` of them,
+// copies their matrices in and runs the grouped launches of serve.cuh over all
+// of them on one of `n_streams` streams.  Each request's cluster writes its
+// results into device memory and then stores the request's ticket into its
+// flag word.  The scheduler copies the flag array to the host on a stream of
+// its own as often as it can; for every flag that shows its ticket it copies
+// the request's results to the staging (one copy) and completes the request
+// when that copy has finished, releasing its device memory.  So a request
+// completes as soon as its own cluster is done, not when its wave is; the
+// wave's event only releases its descriptors and its stream.  Waves on
+// different streams overlap on the device, so requests that arrive while
+// others run are admitted as memory frees up and start without waiting.
 #include <algorithm>
 #include <atomic>
 #include <chrono>
@@ -41,8 +45,7 @@ inline size_t al(size_t x) { return (x + kAlign - 1) & ~(kAlign - 1); }
 // offset and merged with their neighbours on release.
 class Arena {
  public:
-  unsigned char *base = nullptr;   // address the host uses
-  unsigned char *dbase = nullptr;  // address kernels use
+  unsigned char *base = nullptr;   // device memory, or page-locked host memory
   bool host = false;
   size_t size = 0, used = 0, peak = 0;
   std::map<size_t, size_t> free_;  // offset -> bytes
@@ -53,21 +56,17 @@ class Arena {
     if (!on_host) {
       if (cudaMalloc(&base, bytes) != cudaSuccess) {
         cudaGetLastError();
+        base = nullptr;
         set_error_text("server: cudaMalloc of the device budget failed");
         return TSVD_ENOMEM;
       }
-      dbase = base;
     } else {
-      if (cudaHostAlloc(reinterpret_cast<void **>(&base), bytes, cudaHostAllocMapped | cudaHostAllocPortable) !=
-          cudaSuccess) {
+      if (cudaHostAlloc(reinterpret_cast<void **>(&base), bytes, cudaHostAllocPortable) != cudaSuccess) {
         cudaGetLastError();
         base = nullptr;
         set_error_text("server: cudaHostAlloc of the staging area failed");
         return TSVD_ENOMEM;
       }
-      void *d = nullptr;
-      TSVD_CUDA(cudaHostGetDevicePointer(&d, base, 0));
-      dbase = static_cast<unsigned char *>(d);
     }
     size = bytes;
     free_[0] = bytes;
@@ -112,7 +111,7 @@ class Arena {
       else
         cudaFree(base);
     }
-    base = dbase = nullptr;
+    base = nullptr;
   }
 };
 
@@ -131,6 +130,9 @@ struct Request {
   std::vector<int32_t> iters;   // forced applications per triplet (empty: convergence test)
   size_t off = 0, bytes = 0;    // device arena region
   size_t soff = 0, sbytes = 0;  // staging region
+  size_t out_off = 0;           // results within the device region (same layout as the staging)
+  int32_t slot = -1;            // index of the request's completion flag
+  cudaEvent_t copied = nullptr; // results copied to the staging
   bool admitted = false;
   SrvReq dq{};
   bool done = false;
@@ -138,18 +140,18 @@ struct Request {
 };
 using ReqPtr = std::shared_ptr<Request>;
 
-// device region of one request: A, G64, G32, V64, sig2, info, vout, forced iteration counts
+// results of one request (device output region and host staging alike): info, sigma, U, V
+size_t staging_bytes(int64_t m, int64_t n, int64_t k) {
+  return al(k * 16) + al(k * 8) + al(m * k * 4) + al(n * k * 4);
+}
+// device region of one request: A, G64, G32, V64, sig2, info, vout, forced iteration counts, results
 size_t request_bytes(int64_t m, int64_t n, int64_t k) {
   const int64_t d = std::min(m, n);
   return al(m * n * 4) + al(d * d * 8) + al(d * d * 4) + al(d * k * 8) + al(k * 8) + al(k * 16) + al(d * k * 4) +
-         al(k * 4);
-}
-// staging region: flag, info, sigma, U, V
-size_t staging_bytes(int64_t m, int64_t n, int64_t k) {
-  return al(64) + al(k * 16) + al(k * 8) + al(m * k * 4) + al(n * k * 4);
+         al(k * 4) + staging_bytes(m, n, k);
 }
 
-void carve(Request &r, unsigned char *p, unsigned char *sp_dev) {
+void carve(Request &r, unsigned char *p) {
   const int64_t m = r.m, n = r.n, k = r.k;
   const int64_t d = std::min(m, n);
   SrvReq &q = r.dq;
@@ -168,15 +170,16 @@ void carve(Request &r, unsigned char *p, unsigned char *sp_dev) {
   q.vout = reinterpret_cast<float *>(p);
   p += al(d * k * 4);
   q.iters_override = r.iters.empty() ? nullptr : reinterpret_cast<const int32_t *>(p);
-  q.hFlag = reinterpret_cast<uint32_t *>(sp_dev);
-  sp_dev += al(64);
-  q.hInfo = reinterpret_cast<int32_t *>(sp_dev);
-  sp_dev += al(k * 16);
-  q.hS = reinterpret_cast<double *>(sp_dev);
-  sp_dev += al(k * 8);
-  q.hU = reinterpret_cast<float *>(sp_dev);
-  sp_dev += al(m * k * 4);
-  q.hV = reinterpret_cast<float *>(sp_dev);
+  p += al(k * 4);
+  unsigned char *o = p;
+  r.out_off = (size_t)(o - reinterpret_cast<unsigned char *>(const_cast<float *>(q.A)));
+  q.oInfo = reinterpret_cast<int32_t *>(o);
+  o += al(k * 16);
+  q.oS = reinterpret_cast<double *>(o);
+  o += al(k * 8);
+  q.oU = reinterpret_cast<float *>(o);
+  o += al(m * k * 4);
+  q.oV = reinterpret_cast<float *>(o);
   q.m = m;
   q.n = n;
   q.trans = m < n ? 1 : 0;  // Eq. 3: the left vectors from A A^T when m < n
@@ -208,11 +211,20 @@ struct tsvd_server_s {
   int device = 0;
   tsvd::Arena arena, staging;
   std::vector<tsvd::Slot> slots;
+  // completion flags: one word per in-flight request (device), its page-locked mirror,
+  // the stream and event of the copy that refreshes the mirror, the free flag words
+  uint32_t *dflags = nullptr, *hflags = nullptr;
+  cudaStream_t poll_stream = nullptr, out_stream = nullptr;
+  cudaEvent_t poll_done = nullptr;
+  bool poll_inflight = false;
+  std::vector<int32_t> free_flags;
+  std::vector<cudaEvent_t> event_pool;
   std::mutex mu;
   std::condition_variable cv_done, cv_work;
   std::deque<tsvd::ReqPtr> pending;                  // submitted, not admitted
   std::deque<tsvd::ReqPtr> admitted;                 // in the arenas, not launched
   std::list<tsvd::ReqPtr> running;                   // launched, flag not seen yet
+  std::list<tsvd::ReqPtr> copying;                   // flag seen, results on their way to the staging
   std::unordered_map<uint64_t, tsvd::ReqPtr> table;  // every request not yet waited for
   uint64_t next_id = 1;
   int64_t inflight = 0;                              // admitted and not completed
@@ -254,9 +266,6 @@ size_t power_smem_budget() {
   return di.smem_optin > static_bytes ? di.smem_optin - static_bytes : 0;
 }
 
-uint32_t flag_of(const tsvd_server_s *sv, const Request &r) {
-  return *reinterpret_cast<const volatile uint32_t *>(sv->staging.base + r.soff);
-}
 
 // Build and enqueue one wave on slot `s` (scheduler thread, lock not held).
 tsvd_status launch_wave(tsvd_server_s *sv, Slot &s) {
@@ -311,10 +320,7 @@ tsvd_status launch_wave(tsvd_server_s *sv, Slot &s) {
   s.dev_bytes = need;
   unsigned char *dev = sv->arena.base + s.dev_off;
   SrvReq *hreq = reinterpret_cast<SrvReq *>(s.stage);
-  for (size_t i = 0; i < rs.size(); ++i) {
-    hreq[i] = rs[i]->dq;
-    *reinterpret_cast<volatile uint32_t *>(sv->staging.base + rs[i]->soff) = 0u;  // completion flag
-  }
+  for (size_t i = 0; i < rs.size(); ++i) hreq[i] = rs[i]->dq;
   std::memcpy(s.stage + b_req, tiles.data(), tiles.size() * sizeof(SrvTile));
   cudaStream_t st = s.stream;
   for (auto &r : rs) {
@@ -348,8 +354,8 @@ void complete(tsvd_server_s *sv, const ReqPtr &r, tsvd_status st) {
   if (st == TSVD_OK) {
     std::atomic_thread_fence(std::memory_order_acquire);
     const unsigned char *sp = sv->staging.base + r->soff;
-    const int32_t *info = reinterpret_cast<const int32_t *>(sp + al(64));
-    const double *sg = reinterpret_cast<const double *>(sp + al(64) + al(r->k * 16));
+    const int32_t *info = reinterpret_cast<const int32_t *>(sp);
+    const double *sg = reinterpret_cast<const double *>(sp + al(r->k * 16));
     for (int l = 0; l < r->k; ++l) {
       apps += info[4 * l];
       if (info[4 * l + 1] == 1) flags |= TSVD_FLAG_NOCONV;
@@ -365,6 +371,10 @@ void complete(tsvd_server_s *sv, const ReqPtr &r, tsvd_status st) {
   r->rec.done_s = sv->now();
   r->done = true;
   sv->arena.release(r->off, r->bytes);
+  if (r->slot >= 0) sv->free_flags.push_back(r->slot);
+  r->slot = -1;
+  if (r->copied) sv->event_pool.push_back(r->copied);
+  r->copied = nullptr;
   --sv->inflight;
   if (status == TSVD_OK || status == TSVD_ENOCONV || status == TSVD_ERANK)
     ++sv->stats.completed;
@@ -385,26 +395,65 @@ void scheduler(tsvd_server_s *sv) {
   std::unique_lock<std::mutex> lk(sv->mu);
   while (true) {
     bool progressed = false;
-    // requests whose cluster raised the flag
-    for (auto it = sv->running.begin(); it != sv->running.end();) {
-      if (flag_of(sv, **it) != 0u) {
-        complete(sv, *it, TSVD_OK);
-        it = sv->running.erase(it);
-        progressed = true;
-      } else {
-        ++it;
+    // the flag mirror: requests whose cluster stored its ticket get their results copied out
+    if (sv->poll_inflight) {
+      const cudaError_t q = cudaEventQuery(sv->poll_done);
+      if (q != cudaErrorNotReady) {
+        sv->poll_inflight = false;
+        if (q != cudaSuccess) sv->err = std::string("server: flag copy failed: ") + cudaGetErrorString(q);
+        for (auto it = sv->running.begin(); q == cudaSuccess && it != sv->running.end();) {
+          Request &r = **it;
+          if (reinterpret_cast<volatile uint32_t *>(sv->hflags)[r.slot] == r.dq.ticket) {
+            if (sv->event_pool.empty()) {
+              cudaEvent_t e;
+              if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) break;
+              sv->event_pool.push_back(e);
+            }
+            r.copied = sv->event_pool.back();
+            sv->event_pool.pop_back();
+            const size_t ob = staging_bytes(r.m, r.n, r.k);
+            cudaMemcpyAsync(sv->staging.base + r.soff, reinterpret_cast<const unsigned char *>(r.dq.A) + r.out_off, ob,
+                            cudaMemcpyDeviceToHost, sv->out_stream);
+            cudaEventRecord(r.copied, sv->out_stream);
+            sv->copying.push_back(*it);
+            it = sv->running.erase(it);
+            progressed = true;
+          } else {
+            ++it;
+          }
+        }
       }
     }
-    // finished waves: release descriptors; a failed wave fails what it has not completed
+    if (!sv->poll_inflight && !sv->running.empty()) {
+      cudaMemcpyAsync(sv->hflags, sv->dflags, (size_t)sv->opt.max_inflight * 4, cudaMemcpyDeviceToHost,
+                      sv->poll_stream);
+      cudaEventRecord(sv->poll_done, sv->poll_stream);
+      sv->poll_inflight = true;
+    }
+    // results in the staging: the request is complete
+    for (auto it = sv->copying.begin(); it != sv->copying.end();) {
+      const cudaError_t q = cudaEventQuery((*it)->copied);
+      if (q == cudaErrorNotReady) {
+        ++it;
+        continue;
+      }
+      complete(sv, *it, q == cudaSuccess ? TSVD_OK : TSVD_ECUDA);
+      it = sv->copying.erase(it);
+      progressed = true;
+    }
+    // finished waves release their descriptors; a failed wave fails what it has not completed
     for (auto &s : sv->slots) {
       if (!s.busy) continue;
       const cudaError_t q = cudaEventQuery(s.done);
       if (q == cudaErrorNotReady) continue;
-      if (q != cudaSuccess) sv->err = std::string("server: wave failed: ") + cudaGetErrorString(q);
-      for (auto &r : s.reqs) {
-        if (r->done) continue;
-        complete(sv, r, (q == cudaSuccess && flag_of(sv, *r) != 0u) ? TSVD_OK : TSVD_ECUDA);
-        sv->running.remove(r);
+      if (q != cudaSuccess) {
+        sv->err = std::string("server: wave failed: ") + cudaGetErrorString(q);
+        for (auto &r : s.reqs) {
+          if (r->done) continue;
+          sv->running.remove(r);
+          sv->copying.remove(r);
+          complete(sv, r, TSVD_ECUDA);
+        }
       }
       retire_slot(sv, s);
       progressed = true;
@@ -419,11 +468,20 @@ void scheduler(tsvd_server_s *sv) {
         sv->arena.release(off, r->bytes);
         break;
       }
+      if (sv->free_flags.empty()) {
+        sv->arena.release(off, r->bytes);
+        sv->staging.release(soff, r->sbytes);
+        break;
+      }
       sv->pending.pop_front();
       r->off = off;
       r->soff = soff;
       r->admitted = true;
-      carve(*r, sv->arena.base + off, sv->staging.dbase + soff);
+      r->slot = sv->free_flags.back();
+      sv->free_flags.pop_back();
+      carve(*r, sv->arena.base + off);
+      r->dq.flag = sv->dflags + r->slot;
+      r->dq.ticket = (uint32_t)(r->id & 0x7fffffffu) | 0x80000000u;  // never 0, the flags' initial value
       r->rec.admit_s = sv->now();
       ++sv->inflight;
       sv->admitted.push_back(r);
@@ -462,7 +520,7 @@ void scheduler(tsvd_server_s *sv) {
     }
     sv->stats.kernel_launches = launches_so_far() - l0;
     sv->stats.peak_device_bytes = (int64_t)sv->arena.peak;
-    bool any_busy = false;
+    bool any_busy = !sv->running.empty() || !sv->copying.empty() || sv->poll_inflight;
     for (auto &s : sv->slots) any_busy |= s.busy;
     const double t = sv->now();
     if (any_busy && sv->busy_since < 0) sv->busy_since = t;
@@ -493,22 +551,22 @@ __global__ void fill_uniform_kernel(float *a, int64_t count, uint32_t seed) {
 tsvd_status time_power(tsvd_server_s *sv, int64_t d, int c, int nreq, int iters, cudaStream_t st, cudaEvent_t e0,
                        cudaEvent_t e1, double *ms_out) {
   const int k = 2;
-  const size_t per = request_bytes(d, d, k), sper = staging_bytes(d, d, k);
+  const size_t per = request_bytes(d, d, k);
   const int T = (int)ceil_div(d, kSrvTile);
   const size_t ntiles = (size_t)nreq * T * (T + 1) / 2;
-  const size_t need = per * nreq + al(nreq * sizeof(SrvReq)) + al(ntiles * sizeof(SrvTile));
-  size_t off = 0, soff = 0;
+  const size_t need = per * nreq + al(nreq * sizeof(SrvReq)) + al(ntiles * sizeof(SrvTile)) + al(nreq * 4);
+  size_t off = 0;
   {
     std::lock_guard<std::mutex> lk(sv->mu);
     if (!sv->arena.alloc(need, &off)) return TSVD_EBUDGET;
-    if (!sv->staging.alloc(sper * nreq, &soff)) {
-      sv->arena.release(off, need);
-      return TSVD_EBUDGET;
-    }
   }
   const size_t smem_cap = power_smem_budget();
   const int resident = srv_power_smem(d, c, 1) <= smem_cap ? 1 : 0;
   unsigned char *base = sv->arena.base + off;
+  SrvReq *dreq = reinterpret_cast<SrvReq *>(base + per * nreq);
+  SrvTile *dtiles = reinterpret_cast<SrvTile *>(base + per * nreq + al(nreq * sizeof(SrvReq)));
+  uint32_t *dflags = reinterpret_cast<uint32_t *>(base + per * nreq + al(nreq * sizeof(SrvReq)) +
+                                                  al(ntiles * sizeof(SrvTile)));
   std::vector<SrvReq> reqs(nreq);
   std::vector<SrvTile> tiles;
   tsvd_status ls = TSVD_OK;
@@ -520,17 +578,17 @@ tsvd_status time_power(tsvd_server_s *sv, int64_t d, int c, int nreq, int iters,
     r.eps = 1e-300;  // never met: every triplet runs exactly max_iter applications
     r.max_iter = iters;
     r.seed = (uint64_t)i;
-    carve(r, base + per * i, sv->staging.dbase + soff + sper * i);
+    carve(r, base + per * i);
     r.dq.cluster = c;
     r.dq.resident = resident;
+    r.dq.flag = dflags + i;
+    r.dq.ticket = 1u;
     reqs[i] = r.dq;
     fill_uniform_kernel<<<64, 256, 0, st>>>(const_cast<float *>(r.dq.A), d * d, (uint32_t)i);
     if (cudaGetLastError() != cudaSuccess) ls = TSVD_ECUDA;
     for (int ti = 0; ti < T; ++ti)
       for (int tj = 0; tj <= ti; ++tj) tiles.push_back({i, ti, tj, 0});
   }
-  SrvReq *dreq = reinterpret_cast<SrvReq *>(base + per * nreq);
-  SrvTile *dtiles = reinterpret_cast<SrvTile *>(base + per * nreq + al(nreq * sizeof(SrvReq)));
   if (ls == TSVD_OK && cudaMemcpyAsync(dreq, reqs.data(), nreq * sizeof(SrvReq), cudaMemcpyHostToDevice, st) != cudaSuccess)
     ls = TSVD_ECUDA;
   if (ls == TSVD_OK &&
@@ -549,7 +607,6 @@ tsvd_status time_power(tsvd_server_s *sv, int64_t d, int c, int nreq, int iters,
   {
     std::lock_guard<std::mutex> lk(sv->mu);
     sv->arena.release(off, need);
-    sv->staging.release(soff, sper * nreq);
   }
   *ms_out = ms;
   return ls;
@@ -603,6 +660,19 @@ tsvd_status tsvd_server_create(tsvd_server_t *out, const tsvd_server_options *op
     sv->staging.destroy();
     delete sv;
     return st;
+  }
+  {
+    const size_t fb = (size_t)opt.max_inflight * 4;
+    if (cudaMalloc(&sv->dflags, fb) != cudaSuccess || cudaMemset(sv->dflags, 0, fb) != cudaSuccess ||
+        cudaHostAlloc(reinterpret_cast<void **>(&sv->hflags), fb, cudaHostAllocPortable) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&sv->poll_stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&sv->out_stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&sv->poll_done, cudaEventDisableTiming) != cudaSuccess) {
+      set_cuda_error(cudaGetLastError(), "server flags", __FILE__, __LINE__);
+      tsvd_server_destroy(sv);
+      return TSVD_ECUDA;
+    }
+    for (int32_t i = opt.max_inflight - 1; i >= 0; --i) sv->free_flags.push_back(i);
   }
   sv->slots.resize(opt.n_streams);
   for (auto &s : sv->slots) {
@@ -678,7 +748,7 @@ tsvd_status tsvd_server_wait(tsvd_server_t sv, uint64_t ticket, double timeout_s
     // results from the staging into the caller's buffers (the kernel has finished with them)
     const tsvd_status s = (tsvd_status)r->rec.status;
     if (s == TSVD_OK || s == TSVD_ENOCONV || s == TSVD_ERANK) {
-      const unsigned char *sp = sv->staging.base + r->soff + al(64) + al(r->k * 16);
+      const unsigned char *sp = sv->staging.base + r->soff + al(r->k * 16);
       std::memcpy(r->sigma, sp, (size_t)r->k * 8);
       sp += al(r->k * 8);
       std::memcpy(r->U, sp, (size_t)r->m * r->k * 4);
@@ -733,7 +803,7 @@ tsvd_status tsvd_server_autotune(tsvd_server_t sv, int32_t iters) {
       if (clamp_cluster(d, c) != c) break;
       double ms1 = 0.0, msn = 0.0;
       // as many requests as fill the GPU, within half of the arena
-      const size_t per = request_bytes(d, d, 2) + staging_bytes(d, d, 2);
+      const size_t per = request_bytes(d, d, 2);
       const int nfill = (int)std::max<int64_t>(1, std::min<int64_t>(di.sms / c, (int64_t)(sv->arena.size / 2 / per)));
       result = time_power(sv, d, c, 1, iters, st, e0, e1, &ms1);
       if (result == TSVD_OK) result = time_power(sv, d, c, nfill, iters, st, e0, e1, &msn);
@@ -792,6 +862,15 @@ void tsvd_server_destroy(tsvd_server_t sv) {
     if (s.done) cudaEventDestroy(s.done);
     if (s.stage) cudaFreeHost(s.stage);
   }
+  for (cudaStream_t st : {sv->poll_stream, sv->out_stream})
+    if (st) {
+      cudaStreamSynchronize(st);
+      cudaStreamDestroy(st);
+    }
+  if (sv->poll_done) cudaEventDestroy(sv->poll_done);
+  for (auto e : sv->event_pool) cudaEventDestroy(e);
+  if (sv->dflags) cudaFree(sv->dflags);
+  if (sv->hflags) cudaFreeHost(sv->hflags);
   sv->arena.destroy();
   sv->staging.destroy();
   delete sv;

@@ -383,6 +383,47 @@ def test_tsvd_csr_matches_oracle(mode):
     assert abs(r2.sigma[0] - o.sigma[0]) / o.sigma[0] <= 1e-5
 
 
+@pytest.mark.parametrize("mode,unsorted", [("device", False), ("stream", False), ("device", True)])
+def test_tsvd_csr_column_chunked_matches_oracle(mode, unsorted):
+    """n = 2^24 > 8M columns: v and w (64 MB each) exceed half of L2, so the
+    library applies A^T A in column chunks (two passes, split points per row);
+    rows whose columns are not ascending fall back to the fused pair.  Same
+    trajectory as the oracle (its application counts forced)."""
+    import torch as _t
+    m = n = 1 << 24
+    k, eps = 3, 1e-6
+    g = _t.Generator(device="cuda")
+    g.manual_seed(17)
+    counts = _t.randint(2, 7, (m,), generator=g, device="cuda", dtype=_t.int64)
+    rp = _t.zeros(m + 1, dtype=_t.int64, device="cuda")
+    _t.cumsum(counts, 0, out=rp[1:])
+    nnz = int(rp[-1].item())
+    rows = _t.repeat_interleave(_t.arange(m, device="cuda"), counts)
+    cols = _t.randint(0, n, (nnz,), generator=g, device="cuda", dtype=_t.int64)
+    key, _ = _t.sort(rows * n + cols)  # sorted within rows (repeated columns allowed: they add up)
+    cols = (key - rows * n).to(_t.int32)
+    if unsorted:
+        # reverse the entries of every row that has more than one
+        first = rp[:-1][rows]
+        last = rp[1:][rows] - 1
+        pos = _t.arange(nnz, device="cuda")
+        cols = cols[first + last - pos]
+    vals = _t.rand(nnz, generator=g, device="cuda", dtype=_t.float32)
+    csr = {"row_ptr": rp.cpu().numpy(), "col_idx": cols.cpu().numpy(), "values": vals.cpu().numpy(), "m": m, "n": n}
+    del key, rows
+    x = synth.start_normals(n, k, seed=8)
+    o = ref.tsvd_csr(csr, k, eps, x_start=x, iters_override=[4, 4, 4])
+    if mode == "device":
+        Ain = {"row_ptr": rp, "col_idx": cols, "values": vals, "m": m, "n": n}
+        kw = {}
+    else:
+        Ain = csr
+        kw = dict(force_stream=True, block_rows=1 << 21, n_buffers=3, device_budget=3 << 30)
+    r = tsvd(Ain, k, eps, start_draws=x, iters_override=o.iters, **kw)
+    assert r.iters == o.iters
+    _compare(r, o, k, gapped=[0])
+
+
 def test_tsvd_csr_empty_matrix_reports_rank():
     # no stored entries: every application gives w = 0 exactly
     m, n = 400, 200
@@ -516,4 +557,25 @@ def test_tsvd_tensor_cores_c2_shape(prec, budget):
              block_rows=(1 << 14) if budget else (1 << 15), device_budget=budget)
     assert r.report["n_blocks"] == (8 if budget else 4)
     assert r.report["ring_slots"] == (6 if budget else 3)
+    _compare(r, o, k, gapped=gapped)
+
+
+@pytest.mark.parametrize("prec,where", [(B.TSVD_GRAM_TF32X3, "device"), (B.TSVD_GRAM_BF16X3, "device"),
+                                        (B.TSVD_GRAM_TF32X3, "resident")])
+def test_tsvd_in_core_prep_pipeline(prec, where):
+    """In core with many chunks the prep of chunk c+1 (its own stream, one CTA
+    per SM) runs beside the SYRK of chunk c, on two scratch buffers; the
+    result is the same trajectory as the oracle's."""
+    m, n, k, eps = 40000, 384, 6, 1e-6
+    sig = 1.0 / (1.0 + np.arange(64))
+    V = synth.orthonormal_columns(n, 64, 5, 1)
+    A = synth.dense_lowrank_rows(0, m, V, sig, m, 1e-4, seed=5)
+    x = synth.start_normals(n, k, seed=4)
+    Gf = ref.gram(A)
+    o = ref.tsvd_dense(A, k, eps, x_start=x, B=Gf)
+    gapped = ref.gapped_indices(np.linalg.eigvalsh(Gf)[::-1], k)
+    Ain = torch.from_numpy(A).cuda() if where == "device" else A
+    r = tsvd(Ain, k, eps, start_draws=x, iters_override=o.iters, precision=prec, block_rows=3000)
+    assert r.report["n_blocks"] == -(-m // 3008) and r.report["mode"] == (0 if where == "device" else 1)
+    assert r.report["flags"] == 0
     _compare(r, o, k, gapped=gapped)
