@@ -491,35 +491,43 @@ def c1_latency(reps: int = 50):
     k = 8, eps = 1e-8, plain FP32 Gram): latency-bound (G is 256 KB), so the
     figures are the device time of one whole t-SVD call (CUDA events on the
     launching stream, median of `reps`), the time per power application and
-    the kernel launches per call."""
+    the kernel launches per call, for the default power kernel (one
+    thread-block cluster for all triplets) and for the grid-wide cooperative
+    kernel beside it."""
     import torch
 
     import synth
-    from paper_2208_08410_gb300 import Plan
+    from paper_2208_08410_gb300 import Plan, _binding as B
     inp = synth.dense_prescribed(2048, 256, synth.spectrum_geometric(256, 0.8), 1e-6, seed=0)
     dA = torch.from_numpy(inp["A"]).cuda()
-    plan = Plan(dA, 8, 1e-8, precision=0, out_device=True, time_kernels=True)
-    for _ in range(5):
-        plan.factor(dA)
-    torch.cuda.synchronize()
-    times, reps_out = [], []
-    for _ in range(reps):
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record()
-        r = plan.factor(dA)
-        e1.record()
+
+    def run(pk):
+        plan = Plan(dA, 8, 1e-8, precision=0, out_device=True, time_kernels=True, power_kernel=pk)
+        for _ in range(5):
+            plan.factor(dA)
         torch.cuda.synchronize()
-        times.append(e0.elapsed_time(e1))
-        reps_out.append(r.report)
-    plan.close()
-    t = float(np.median(times))
-    rep = reps_out[-1]
-    return {"workload": "m=2048, n=256, sigma_i=0.8^i + 1e-6 noise, k=8, eps=1e-8, FP32 Gram, A in HBM",
-            "ms_per_tsvd": round(t, 4), "ms_min": round(float(np.min(times)), 4),
-            "us_per_power_application": round(rep["power_ms"] * 1e3 / max(rep["applications"], 1), 3),
-            "applications": rep["applications"], "kernel_launches_per_tsvd": rep["kernel_launches"],
-            "phases_ms": {"gram": round(rep["gram_ms"], 4), "power": round(rep["power_ms"], 4),
-                          "left": round(rep["left_ms"], 4)}}
+        times, reps_out = [], []
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            r = plan.factor(dA)
+            e1.record()
+            torch.cuda.synchronize()
+            times.append(e0.elapsed_time(e1))
+            reps_out.append(r.report)
+        plan.close()
+        rep = reps_out[-1]
+        return {"ms_per_tsvd": round(float(np.median(times)), 4), "ms_min": round(float(np.min(times)), 4),
+                "us_per_power_application": round(rep["power_ms"] * 1e3 / max(rep["applications"], 1), 3),
+                "applications": rep["applications"], "kernel_launches_per_tsvd": rep["kernel_launches"],
+                "phases_ms": {"gram": round(rep["gram_ms"], 4), "power": round(rep["power_ms"], 4),
+                              "left": round(rep["left_ms"], 4)}}
+
+    out = {"workload": "m=2048, n=256, sigma_i=0.8^i + 1e-6 noise, k=8, eps=1e-8, FP32 Gram, A in HBM",
+           "power_kernel": "cluster (all triplets in one launch on one thread-block cluster)"}
+    out.update(run(B.TSVD_POWER_AUTO))
+    out["grid_kernel"] = run(B.TSVD_POWER_GRID)
+    return out
 
 
 def dtype_peak(prec: int, peaks: dict, sustained: bool = True):

@@ -115,8 +115,22 @@ typedef struct {
   int32_t time_kernels;          /* 1: time each Gram kernel launch (compute stream)
                                     and each block copy (copy stream) with CUDA events
                                     (report.gram_kernel_ms, report.h2d_copy_ms) */
-  int32_t reserved[5];
+  int32_t power_kernel;          /* dense power phase (Alg. 1 loop over l, Alg. 2 per
+                                    triplet): TSVD_POWER_AUTO, TSVD_POWER_GRID or
+                                    TSVD_POWER_CLUSTER */
+  int32_t reserved[4];
 } tsvd_options;
+
+/* Kernels of the dense power phase.  GRID: one cooperative launch per
+ * triplet over up to one CTA per SM, a bounded grid-wide barrier per
+ * application (any n).  CLUSTER: one launch for all k triplets on a single
+ * thread-block cluster (up to 8 CTAs; the FP32 Gram rows in shared memory
+ * when they fit), a cluster barrier per application; n <= 2048 and k <= 32,
+ * otherwise tsvd_factor returns TSVD_EUNSUPPORTED.  AUTO takes CLUSTER
+ * where it applies (it has the lower latency per application there). */
+#define TSVD_POWER_AUTO 0
+#define TSVD_POWER_GRID 1
+#define TSVD_POWER_CLUSTER 2
 
 /* Per-call report (all fields written by tsvd_factor). */
 typedef struct {

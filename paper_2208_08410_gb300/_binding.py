@@ -15,6 +15,7 @@ TSVD_ETIMEDOUT, TSVD_ENOCONV, TSVD_ERANK, TSVD_EUNSUPPORTED = 5, 6, 7, 8
 TSVD_DENSE_F32_ROWMAJOR, TSVD_CSR_F32_I32_I64 = 0, 1
 TSVD_HOST, TSVD_DEVICE = 0, 1
 TSVD_GRAM_FP32, TSVD_GRAM_TF32, TSVD_GRAM_TF32X3, TSVD_GRAM_BF16X3 = 0, 1, 2, 3
+TSVD_POWER_AUTO, TSVD_POWER_GRID, TSVD_POWER_CLUSTER = 0, 1, 2
 TSVD_NOALLOC_MAX_N, TSVD_NOALLOC_MAX_L = 16384, 64
 TSVD_FLAG_NOCONV, TSVD_FLAG_RANK, TSVD_FLAG_NONMONOTONE, TSVD_FLAG_PAGEABLE, TSVD_FLAG_TIMEOUT = 1, 2, 4, 8, 16
 
@@ -33,7 +34,8 @@ class tsvd_options(C.Structure):
                 ("precision", C.c_int32), ("max_iter", C.c_int32), ("sign_convention", C.c_int32),
                 ("iters_override", C.c_void_p), ("start_draws", C.c_void_p), ("seed", C.c_uint64),
                 ("out_location", C.c_int32), ("force_stream", C.c_int32), ("time_kernels", C.c_int32),
-                ("reserved", C.c_int32 * 5)]
+                ("power_kernel", C.c_int32),
+                ("reserved", C.c_int32 * 4)]
 
 
 class tsvd_report(C.Structure):

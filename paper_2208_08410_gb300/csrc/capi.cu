@@ -13,6 +13,8 @@
 #include <vector>
 
 #include "common.cuh"
+#include "philox.cuh"
+#include "serve.cuh"
 
 namespace tsvd {
 
@@ -88,7 +90,6 @@ struct tsvd_plan_s {
   size_t ws = 0;
   size_t o_G64 = 0, o_G32 = 0, o_V64 = 0, o_V32 = 0, o_sig2 = 0, o_sigma = 0, o_info = 0;
   size_t o_pscr = 0, b_pscr = 0, o_gscr = 0, b_gscr = 0, o_ring = 0, b_slot = 0;
-  size_t o_gscr2 = 0;  // second Gram scratch: in-core tensor-core passes pipeline prep and SYRK
   size_t o_res = 0, o_ubuf = 0, b_ubuf = 0;
   size_t o_v = 0, o_vn = 0, o_w = 0, o_x64 = 0, o_Vr = 0, o_vsc = 0, o_flag = 0;
   // column-chunked CSR operator (v and w larger than what L2 holds)
@@ -97,10 +98,14 @@ struct tsvd_plan_s {
   bool csr_sorted = true;     // every row's columns ascending (host CSR: checked at plan time)
   size_t o_csr_y = 0, o_csr_split = 0, b_split_slot = 0;
   int vec_grid = 0;
+  // dense power phase on one thread-block cluster (n <= kSrvMaxDim, k <= kSrvMaxK)
+  bool cluster_power = false;
+  SrvReq srv_req{};  // host copy of the descriptor the cluster kernel reads (copied per call)
   // runtime objects (created on first factor, on the device current then)
   int device = -1;
-  cudaStream_t copy_stream = nullptr, d2h_stream = nullptr, prep_stream = nullptr;
-  cudaEvent_t ev_gstart = nullptr, ev_prep[2] = {nullptr, nullptr}, ev_syrk[2] = {nullptr, nullptr};
+  cudaStream_t copy_stream = nullptr, d2h_stream = nullptr;
+  cudaStream_t copy_stream2 = nullptr;  // second half of every block copy (a second copy engine)
+  cudaEvent_t ev_csplit = nullptr, ev_cjoin = nullptr;
   std::vector<cudaEvent_t> ev_ready, ev_free;
   cudaEvent_t ev_u_ready[2] = {nullptr, nullptr}, ev_u_free[2] = {nullptr, nullptr};
   cudaEvent_t ev_t[4] = {nullptr, nullptr, nullptr, nullptr};
@@ -184,10 +189,6 @@ tsvd_status plan_dense(tsvd_plan_s *p) {
   p->b_gscr = gram_tc_scratch_bytes(rows, n, prec);
   p->o_gscr = c.take(p->b_gscr + 256);
   if (mode == MODE_RESIDENT) p->o_res = c.take(resident_bytes);
-  // in core, a second scratch lets the prep of chunk c+1 run beside the SYRK of chunk c
-  if (mode != MODE_STREAM && prec != TSVD_GRAM_FP32 && p->n_chunks > 1 &&
-      (!budget || c.off + p->b_gscr + 256 + (host_u ? 2 * (size_t)round_up(rows * k * 4, 256) : 0) <= budget))
-    p->o_gscr2 = c.take(p->b_gscr + 256);
   if (host_u) {
     p->b_ubuf = (size_t)round_up(rows * k * 4, 256);
     p->o_ubuf = c.take(2 * p->b_ubuf);
@@ -350,6 +351,13 @@ tsvd_status tsvd_plan(tsvd_plan_t *out, const tsvd_matrix *A, int64_t k, double 
   if (opt.max_iter <= 0) opt.max_iter = 10000;
   if (opt.out_location != TSVD_HOST && opt.out_location != TSVD_DEVICE) return TSVD_EINVAL;
   if (opt.block_rows < 0) return TSVD_EINVAL;
+  if (opt.power_kernel < TSVD_POWER_AUTO || opt.power_kernel > TSVD_POWER_CLUSTER) return TSVD_EINVAL;
+  const bool cluster_fits = A->kind == TSVD_DENSE_F32_ROWMAJOR && A->n <= kSrvMaxDim && k <= kSrvMaxK;
+  if (opt.power_kernel == TSVD_POWER_CLUSTER && !cluster_fits) {
+    set_error_text("tsvd_plan: the cluster power kernel takes dense A with n <= " + std::to_string(kSrvMaxDim) +
+                   " and k <= " + std::to_string(kSrvMaxK));
+    return TSVD_EUNSUPPORTED;
+  }
   if (A->kind == TSVD_DENSE_F32_ROWMAJOR) {
     if (!A->values || A->ld < A->n) return TSVD_EINVAL;
   } else {
@@ -383,6 +391,9 @@ tsvd_status tsvd_plan(tsvd_plan_t *out, const tsvd_matrix *A, int64_t k, double 
     if (opt.start_draws) p->start_draws.assign(opt.start_draws, opt.start_draws + (size_t)A->n * k);
     p->opt.iters_override = nullptr;
     p->opt.start_draws = nullptr;
+    p->cluster_power = A->kind == TSVD_DENSE_F32_ROWMAJOR &&
+                       (opt.power_kernel == TSVD_POWER_CLUSTER ||
+                        (opt.power_kernel == TSVD_POWER_AUTO && cluster_fits));
   } catch (...) {
     delete p;
     return TSVD_ENOMEM;
@@ -413,13 +424,10 @@ void tsvd_destroy(tsvd_plan_t p) {
     for (auto e : p->ev_k) cudaEventDestroy(e);
     for (auto e : p->ev_c) cudaEventDestroy(e);
     if (p->copy_stream) cudaStreamDestroy(p->copy_stream);
+    if (p->copy_stream2) cudaStreamDestroy(p->copy_stream2);
+    if (p->ev_csplit) cudaEventDestroy(p->ev_csplit);
+    if (p->ev_cjoin) cudaEventDestroy(p->ev_cjoin);
     if (p->d2h_stream) cudaStreamDestroy(p->d2h_stream);
-    if (p->prep_stream) cudaStreamDestroy(p->prep_stream);
-    if (p->ev_gstart) cudaEventDestroy(p->ev_gstart);
-    for (int i = 0; i < 2; ++i) {
-      if (p->ev_prep[i]) cudaEventDestroy(p->ev_prep[i]);
-      if (p->ev_syrk[i]) cudaEventDestroy(p->ev_syrk[i]);
-    }
     if (cur != p->device) cudaSetDevice(cur);
   }
   delete p;
@@ -437,6 +445,9 @@ tsvd_status ensure_runtime(tsvd_plan_s *p) {
   if (p->device >= 0) return TSVD_EINVAL;  // a plan serves one device
   p->device = dev;
   TSVD_CUDA(cudaStreamCreateWithFlags(&p->copy_stream, cudaStreamNonBlocking));
+  TSVD_CUDA(cudaStreamCreateWithFlags(&p->copy_stream2, cudaStreamNonBlocking));
+  TSVD_CUDA(cudaEventCreateWithFlags(&p->ev_csplit, cudaEventDisableTiming));
+  TSVD_CUDA(cudaEventCreateWithFlags(&p->ev_cjoin, cudaEventDisableTiming));
   TSVD_CUDA(cudaStreamCreateWithFlags(&p->d2h_stream, cudaStreamNonBlocking));
   p->ev_ready.resize(p->n_buffers, nullptr);
   p->ev_free.resize(p->n_buffers, nullptr);
@@ -449,14 +460,6 @@ tsvd_status ensure_runtime(tsvd_plan_s *p) {
     TSVD_CUDA(cudaEventCreateWithFlags(&p->ev_u_free[i], cudaEventDisableTiming));
   }
   for (int i = 0; i < 4; ++i) TSVD_CUDA(cudaEventCreate(&p->ev_t[i]));
-  if (p->o_gscr2) {
-    TSVD_CUDA(cudaStreamCreateWithFlags(&p->prep_stream, cudaStreamNonBlocking));
-    TSVD_CUDA(cudaEventCreateWithFlags(&p->ev_gstart, cudaEventDisableTiming));
-    for (int i = 0; i < 2; ++i) {
-      TSVD_CUDA(cudaEventCreateWithFlags(&p->ev_prep[i], cudaEventDisableTiming));
-      TSVD_CUDA(cudaEventCreateWithFlags(&p->ev_syrk[i], cudaEventDisableTiming));
-    }
-  }
   return TSVD_OK;
 }
 
@@ -534,12 +537,25 @@ tsvd_status acquire_dense(Run &r, int64_t r0, int64_t rows, const float **out, i
   }
   const float *src = A->values + r0 * A->ld;
   TSVD_TRY(copy_event(r, true));
-  if (A->ld == p->n) {
-    TSVD_CUDA(cudaMemcpyAsync(dst, src, (size_t)rows * p->n * 4, cudaMemcpyHostToDevice, p->copy_stream));
-  } else {
-    TSVD_CUDA(cudaMemcpy2DAsync(dst, (size_t)p->n * 4, src, (size_t)A->ld * 4, (size_t)p->n * 4, (size_t)rows,
-                                cudaMemcpyHostToDevice, p->copy_stream));
+  // the block in two halves on two copy streams: host memory that a single copy
+  // drains slowly (seen on some hosts for parts of a large pinned allocation)
+  // gets two copy engines; the halves join on the first stream
+  const int64_t h0 = rows / 2, h1 = rows - h0;
+  TSVD_CUDA(cudaEventRecord(p->ev_csplit, p->copy_stream));
+  TSVD_CUDA(cudaStreamWaitEvent(p->copy_stream2, p->ev_csplit, 0));
+  for (int half = 0; half < 2; ++half) {
+    const int64_t rr0 = half ? h0 : 0, rr = half ? h1 : h0;
+    if (rr == 0) continue;
+    cudaStream_t cst = half ? p->copy_stream2 : p->copy_stream;
+    if (A->ld == p->n) {
+      TSVD_CUDA(cudaMemcpyAsync(dst + rr0 * p->n, src + rr0 * A->ld, (size_t)rr * p->n * 4, cudaMemcpyHostToDevice, cst));
+    } else {
+      TSVD_CUDA(cudaMemcpy2DAsync(dst + rr0 * p->n, (size_t)p->n * 4, src + rr0 * A->ld, (size_t)A->ld * 4,
+                                  (size_t)p->n * 4, (size_t)rr, cudaMemcpyHostToDevice, cst));
+    }
   }
+  TSVD_CUDA(cudaEventRecord(p->ev_cjoin, p->copy_stream2));
+  TSVD_CUDA(cudaStreamWaitEvent(p->copy_stream, p->ev_cjoin, 0));
   TSVD_TRY(copy_event(r, false));
   if (p->opt.time_kernels) r.copy_bytes.push_back((double)rows * p->n * 4);
   r.h2d += (double)rows * p->n * 4;
@@ -602,6 +618,75 @@ tsvd_status left_pass_dense(Run &r, const float *V32, const double *sigma, float
   return TSVD_OK;
 }
 
+// Power phase of a dense plan on one thread-block cluster: all k triplets in
+// one launch (Alg. 1 loop over l, Alg. 2 per triplet, Hotelling deflation of
+// the full FP64 G64 and its FP32 copy row by row), writing V64, V32, sig2,
+// sigma and info.  The descriptor, the forced counts and the completion word
+// sit at the start of the power scratch, which the grid kernel would use.
+tsvd_status power_cluster_dense(Run &r, double *G64, float *G32, double *V64, float *V32, double *sig2,
+                                double *sigma, int32_t *info, void *pscr) {
+  tsvd_plan_s *p = r.p;
+  const int64_t n = p->n, k = p->k;
+  unsigned char *base = static_cast<unsigned char *>(pscr);
+  SrvReq *dq = reinterpret_cast<SrvReq *>(base);
+  int32_t *d_iters = reinterpret_cast<int32_t *>(base + round_up(sizeof(SrvReq), 256));
+  uint32_t *d_flag = reinterpret_cast<uint32_t *>(base + round_up(sizeof(SrvReq), 256) + 256);
+  static_assert(kSrvMaxK * 4 <= 256, "forced counts fit their slot");
+  if (round_up(sizeof(SrvReq), 256) + 512 > p->b_pscr) return TSVD_EINVAL;
+
+  DeviceInfo di;
+  TSVD_TRY(device_info(&di));
+  const size_t static_bytes = 24 * 1024;  // the kernel's static shared arrays, rounded up
+  const size_t cap = di.smem_optin > static_bytes ? di.smem_optin - static_bytes : 0;
+  const int C = srv_clamp_cluster(n, 8);
+  const int resident = srv_power_smem(n, C, 1) <= cap ? 1 : 0;
+  const size_t smem = srv_power_smem(n, C, resident);
+  if (smem > cap) return TSVD_EUNSUPPORTED;
+
+  if (!p->start_draws.empty()) {
+    // the kernel reads x_l from column l of V64 before the triplet overwrites it
+    TSVD_CUDA(cudaMemcpyAsync(V64, p->start_draws.data(), (size_t)n * k * 8, cudaMemcpyHostToDevice, r.cs));
+    r.h2d += (double)n * k * 8;
+  }
+  if (!p->iters_override.empty())
+    TSVD_CUDA(cudaMemcpyAsync(d_iters, p->iters_override.data(), (size_t)k * 4, cudaMemcpyHostToDevice, r.cs));
+  SrvReq &q = p->srv_req;
+  q = SrvReq{};
+  q.A = nullptr;  // the other factor is the left pass's
+  q.m = p->m;
+  q.n = n;
+  q.trans = 0;
+  q.k = (int32_t)k;
+  q.G64 = G64;
+  q.G32 = G32;
+  q.V64 = V64;
+  q.sig2 = sig2;
+  q.info = info;
+  q.vout = V32;
+  q.eps = p->eps;
+  q.max_iter = p->opt.max_iter;
+  q.sign_convention = p->opt.sign_convention;
+  q.iters_override = p->iters_override.empty() ? nullptr : d_iters;
+  const uint64_t key = splitmix64(p->opt.seed);
+  q.key0 = (uint32_t)key;
+  q.key1 = (uint32_t)(key >> 32);
+  q.cluster = C;
+  q.resident = resident;
+  q.oU = nullptr;
+  q.oV = V32;  // the epilogue's copy of the power vectors lands on itself
+  q.oS = sigma;
+  q.oInfo = info;
+  q.flag = d_flag;
+  q.ticket = 1;
+  q.no_other = 1;
+  q.x_start = p->start_draws.empty() ? nullptr : V64;
+  if (!srv_req_complete(q)) return TSVD_EINVAL;
+  // pageable source: the copy is staged before the call returns; the plan
+  // keeps the host copy alive anyway
+  TSVD_CUDA(cudaMemcpyAsync(dq, &q, sizeof(SrvReq), cudaMemcpyHostToDevice, r.cs));
+  return launch_srv_power(dq, 1, C, smem, r.cs);
+}
+
 tsvd_status factor_dense(Run &r, float *U, double *sigma_out, float *V_out, tsvd_report *rep) {
   tsvd_plan_s *p = r.p;
   const int64_t n = p->n, k = p->k;
@@ -625,50 +710,32 @@ tsvd_status factor_dense(Run &r, float *U, double *sigma_out, float *V_out, tsvd
   TSVD_CUDA(cudaEventRecord(p->ev_t[0], r.cs));
   // ---- Gram pass: B = sum_b A_b^T A_b
   TSVD_CUDA(cudaMemsetAsync(G64, 0, (size_t)n * n * 8, r.cs));
-  void *gbuf[2] = {gscr, p->o_gscr2 ? ws + p->o_gscr2 : nullptr};
-  // status words of the tensor-core scratch, zeroed once for the whole pass
+  // status word of the tensor-core scratch, zeroed once for the whole pass
   // (the 256-byte aligned scratch starts with its status word)
   if (p->opt.precision != TSVD_GRAM_FP32) TSVD_CUDA(cudaMemsetAsync(gscr, 0, 4, r.cs));
-  if (p->o_gscr2) TSVD_CUDA(cudaMemsetAsync(gbuf[1], 0, 4, r.cs));
-  if (p->o_gscr2) {
-    // two scratch buffers: the prep of chunk c (prep stream, one CTA per SM) waits
-    // for the SYRK that last read its buffer (chunk c-2); the SYRK of chunk c
-    // (caller's stream) waits for its prep, so prep c+1 runs beside SYRK c
-    TSVD_CUDA(cudaEventRecord(p->ev_gstart, r.cs));
-    TSVD_CUDA(cudaStreamWaitEvent(p->prep_stream, p->ev_gstart, 0));
-  }
   for (int64_t c = 0; c < p->n_chunks; ++c) {
     const int64_t r0 = c * p->chunk_rows, rows = std::min(p->chunk_rows, p->m - r0);
     const float *Ab;
     int64_t ldb;
     int slot;
     TSVD_TRY(acquire_dense(r, r0, rows, &Ab, &ldb, &slot, true));
-    if (p->o_gscr2) {
-      const int b = (int)(c & 1);
-      if (p->mode == MODE_RESIDENT) TSVD_CUDA(cudaStreamWaitEvent(p->prep_stream, p->ev_ready[0], 0));
-      if (c >= 2) TSVD_CUDA(cudaStreamWaitEvent(p->prep_stream, p->ev_syrk[b], 0));
-      TSVD_TRY(launch_gram_tc_prep(Ab, rows, n, ldb, p->opt.precision, gbuf[b], p->b_gscr, true, p->prep_stream));
-      TSVD_CUDA(cudaEventRecord(p->ev_prep[b], p->prep_stream));
-      TSVD_CUDA(cudaStreamWaitEvent(r.cs, p->ev_prep[b], 0));
-      TSVD_TRY(launch_gram_tc_syrk(rows, n, G64, p->opt.precision, gbuf[b], p->b_gscr, r.cs,
-                                   timed ? p->ev_k[2 * c] : nullptr, timed ? p->ev_k[2 * c + 1] : nullptr, false));
-      TSVD_CUDA(cudaEventRecord(p->ev_syrk[b], r.cs));
-    } else {
-      TSVD_TRY(gram_dispatch(Ab, rows, n, ldb, G64, p->opt.precision, gscr, p->b_gscr, r.cs,
-                             timed ? p->ev_k[2 * c] : nullptr, timed ? p->ev_k[2 * c + 1] : nullptr, false));
-    }
+    TSVD_TRY(gram_dispatch(Ab, rows, n, ldb, G64, p->opt.precision, gscr, p->b_gscr, r.cs,
+                           timed ? p->ev_k[2 * c] : nullptr, timed ? p->ev_k[2 * c + 1] : nullptr, false));
     TSVD_TRY(release_slot(r, slot));
   }
-  int32_t gram_err = 0, gram_err2 = 0;
+  int32_t gram_err = 0;
   if (p->opt.precision != TSVD_GRAM_FP32)
     TSVD_CUDA(cudaMemcpyAsync(&gram_err, gscr, 4, cudaMemcpyDeviceToHost, r.cs));
-  if (p->o_gscr2) TSVD_CUDA(cudaMemcpyAsync(&gram_err2, gbuf[1], 4, cudaMemcpyDeviceToHost, r.cs));
-  TSVD_TRY(launch_symmetrize(n, G64, G32, r.cs));
+  // the cluster kernel reads and deflates full rows of G64: mirror its lower triangle too
+  TSVD_TRY(launch_symmetrize(n, G64, G32, r.cs, p->cluster_power));
   TSVD_CUDA(cudaEventRecord(p->ev_t[1], r.cs));
 
   // ---- power phase: Alg. 1 loop over l, Alg. 2 per triplet (on the device)
   TSVD_CUDA(cudaMemsetAsync(info, 0, (size_t)k * 4 * sizeof(int32_t), r.cs));
-  for (int64_t l = 0; l < k; ++l) {
+  if (p->cluster_power) {
+    TSVD_TRY(power_cluster_dense(r, G64, G32, V64, V32, sig2, sigma, info, pscr));
+  }
+  for (int64_t l = 0; l < k && !p->cluster_power; ++l) {
     double *x = V64 + l * n;
     if (!p->start_draws.empty()) {
       TSVD_CUDA(cudaMemcpyAsync(x, p->start_draws.data() + l * n, (size_t)n * 8, cudaMemcpyHostToDevice, r.cs));
@@ -683,8 +750,10 @@ tsvd_status factor_dense(Run &r, float *U, double *sigma_out, float *V_out, tsvd
     // Hotelling deflation of the FP32 Gram copy for the next triplet
     if (l + 1 < k) TSVD_TRY(launch_gram_deflate(n, G64, G32, x, sig2 + l, r.cs));
   }
-  TSVD_TRY(launch_sigma_from_sigma2(sig2, sigma, k, r.cs));
-  TSVD_TRY(launch_f64_to_f32(V64, V32, n * k, r.cs));
+  if (!p->cluster_power) {
+    TSVD_TRY(launch_sigma_from_sigma2(sig2, sigma, k, r.cs));
+    TSVD_TRY(launch_f64_to_f32(V64, V32, n * k, r.cs));
+  }
   TSVD_CUDA(cudaEventRecord(p->ev_t[2], r.cs));
 
   // ---- left vectors: U = A V diag(sigma)^-1
@@ -718,7 +787,7 @@ tsvd_status factor_dense(Run &r, float *U, double *sigma_out, float *V_out, tsvd
   }
   int flags = 0;
   int64_t apps = 0;
-  if (gram_err || gram_err2) flags |= TSVD_FLAG_TIMEOUT;
+  if (gram_err) flags |= TSVD_FLAG_TIMEOUT;
   for (int64_t l = 0; l < k; ++l) {
     if (hinfo[4 * l + 2]) flags |= TSVD_FLAG_TIMEOUT;
     if (hinfo[4 * l + 1] == 1) flags |= TSVD_FLAG_NOCONV;
@@ -812,8 +881,13 @@ tsvd_status acquire_csr(Run &r, int64_t b, const std::vector<int64_t> &bnd_nnz, 
   TSVD_TRY(copy_event(r, true));
   TSVD_CUDA(cudaMemcpyAsync(rp, A->row_ptr + s0, (size_t)(out->rows + 1) * 8, cudaMemcpyHostToDevice, p->copy_stream));
   if (e1 > e0) {
+    // column indices and values on two copy streams, joined on the first
+    TSVD_CUDA(cudaEventRecord(p->ev_csplit, p->copy_stream));
+    TSVD_CUDA(cudaStreamWaitEvent(p->copy_stream2, p->ev_csplit, 0));
     TSVD_CUDA(cudaMemcpyAsync(ci, A->col_idx + e0, (size_t)(e1 - e0) * 4, cudaMemcpyHostToDevice, p->copy_stream));
-    TSVD_CUDA(cudaMemcpyAsync(va, A->values + e0, (size_t)(e1 - e0) * 4, cudaMemcpyHostToDevice, p->copy_stream));
+    TSVD_CUDA(cudaMemcpyAsync(va, A->values + e0, (size_t)(e1 - e0) * 4, cudaMemcpyHostToDevice, p->copy_stream2));
+    TSVD_CUDA(cudaEventRecord(p->ev_cjoin, p->copy_stream2));
+    TSVD_CUDA(cudaStreamWaitEvent(p->copy_stream, p->ev_cjoin, 0));
   }
   TSVD_TRY(copy_event(r, false));
   const double bytes = (double)(out->rows + 1) * 8 + (double)(e1 - e0) * 8;
@@ -1195,7 +1269,8 @@ tsvd_status tsvd_gram_deflate(int64_t n, double *G64, float *G32, const double *
 
 tsvd_status tsvd_gram_symmetrize(int64_t n, const double *G64, float *G32, void *stream) {
   if (n <= 0 || !G64 || !G32) return TSVD_EINVAL;
-  return launch_symmetrize(n, G64, G32, static_cast<cudaStream_t>(stream));
+  // G64 is only read when the FP64 lower triangle is not mirrored
+  return launch_symmetrize(n, const_cast<double *>(G64), G32, static_cast<cudaStream_t>(stream), false);
 }
 
 tsvd_status tsvd_start_draws(uint64_t seed, int64_t l, int64_t n, double *x, void *stream) {

@@ -159,10 +159,10 @@ size_t gram_tc_scratch_bytes(int64_t rows, int64_t n, int precision);
 tsvd_status launch_gram_tc(const float *A, int64_t rows, int64_t n, int64_t ld, double *G,
                            int precision, void *scratch, size_t scratch_bytes, cudaStream_t stream,
                            cudaEvent_t ev0 = nullptr, cudaEvent_t ev1 = nullptr, bool reset_status = true);
-// The two halves of launch_gram_tc, for pipelining the prep of one chunk with
-// the SYRK of the previous one (separate scratch buffers, separate streams).
+// The two halves of launch_gram_tc: the prep (transpose, rounding, split) into
+// the scratch, then the SYRK from it.
 tsvd_status launch_gram_tc_prep(const float *A, int64_t rows, int64_t n, int64_t ld, int precision, void *scratch,
-                                size_t scratch_bytes, bool persistent, cudaStream_t stream);
+                                size_t scratch_bytes, cudaStream_t stream);
 tsvd_status launch_gram_tc_syrk(int64_t rows, int64_t n, double *G, int precision, void *scratch,
                                 size_t scratch_bytes, cudaStream_t stream, cudaEvent_t ev0 = nullptr,
                                 cudaEvent_t ev1 = nullptr, bool reset_status = true);
@@ -177,7 +177,7 @@ tsvd_status launch_power_dense_noalloc(int64_t n, const float *G32, const double
                                        const double *sigma2, int64_t l, double *x, double eps, int max_iter,
                                        int iters_override, int sign_convention, double *out_sigma2, int *info,
                                        cudaStream_t stream);
-tsvd_status launch_symmetrize(int64_t n, const double *G64, float *G32, cudaStream_t stream);
+tsvd_status launch_symmetrize(int64_t n, double *G64, float *G32, cudaStream_t stream, bool full64 = false);
 tsvd_status launch_gram_deflate(int64_t n, double *G64, float *G32, const double *v, const double *sigma2,
                                 cudaStream_t stream);
 tsvd_status launch_start_draws(uint64_t seed, int64_t l, int64_t n, double *x, cudaStream_t stream);

@@ -568,17 +568,16 @@ tsvd_status tc_layout(int64_t rows, int64_t n, int precision, void *scratch, siz
 }  // namespace
 
 tsvd_status launch_gram_tc_prep(const float *A, int64_t rows, int64_t n, int64_t ld, int precision, void *scratch,
-                                size_t scratch_bytes, bool persistent, cudaStream_t stream) {
+                                size_t scratch_bytes, cudaStream_t stream) {
   if (rows <= 0) return TSVD_OK;
   DeviceInfo di;
   TSVD_TRY(device_info(&di));
   if (di.cc_major != 10) return TSVD_EUNSUPPORTED;  // tcgen05 needs the sm_100 family
   TcLayout L;
   TSVD_TRY(tc_layout(rows, n, precision, scratch, scratch_bytes, &L));
-  // transpose + rounding (+ split); Kp is a multiple of 32, the prep row tile.  A
-  // persistent grid (one CTA per SM) leaves room on every SM for a running SYRK.
+  // transpose + rounding (+ split); Kp is a multiple of 32, the prep row tile
   const int64_t strips = (L.Kp / 32) * ceil_div(n, 128);
-  const int64_t grid = persistent ? std::min<int64_t>(strips, di.sms) : std::min<int64_t>(strips, 0x7fffffffLL);
+  const int64_t grid = std::min<int64_t>(strips, 0x7fffffffLL);
   dim3 block(32, 8);
   if (precision == TSVD_GRAM_BF16X3)
     prep_kernel<TSVD_GRAM_BF16X3><<<(unsigned)grid, block, 0, stream>>>(A, rows, n, ld, L.hi, L.lo, L.Kp);
@@ -646,7 +645,7 @@ tsvd_status launch_gram_tc(const float *A, int64_t rows, int64_t n, int64_t ld, 
                            void *scratch, size_t scratch_bytes, cudaStream_t stream, cudaEvent_t ev0,
                            cudaEvent_t ev1, bool reset_status) {
   if (rows <= 0) return TSVD_OK;
-  TSVD_TRY(launch_gram_tc_prep(A, rows, n, ld, precision, scratch, scratch_bytes, false, stream));
+  TSVD_TRY(launch_gram_tc_prep(A, rows, n, ld, precision, scratch, scratch_bytes, stream));
   return launch_gram_tc_syrk(rows, n, G, precision, scratch, scratch_bytes, stream, ev0, ev1, reset_status);
 }
 

@@ -441,25 +441,40 @@ __global__ void __launch_bounds__(PT, 1) power_dense_kernel(PowerArgs a) {
   }
 }
 
-__global__ void symmetrize_kernel(int64_t n, const double *__restrict__ G64, float *__restrict__ G32) {
+// FULL64: also mirror the upper triangle of G64 into its lower triangle, so
+// that every row of G64 holds the full symmetric row
+template <bool FULL64>
+__global__ void symmetrize_kernel(int64_t n, double *__restrict__ G64, float *__restrict__ G32) {
   // 32 x 32 tiles: G32[i][j] = G64[min(i,j)][max(i,j)]
   __shared__ float t[32][33];
+  __shared__ double t64[FULL64 ? 32 : 1][33];
   const int64_t bi = (int64_t)blockIdx.y * 32, bj = (int64_t)blockIdx.x * 32;
   const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8
   if (bj >= bi) {
     // tile in the upper triangle: direct copy (row i <= col j) and mirrored copy
     for (int r = ty; r < 32; r += 8) {
       const int64_t i = bi + r, j = bj + tx;
-      float v = 0.f;
-      if (i < n && j < n) v = (float)(j >= i ? G64[i * n + j] : G64[j * n + i]);
+      double g = 0.0;
+      if (i < n && j < n) g = j >= i ? G64[i * n + j] : G64[j * n + i];
+      const float v = (float)g;
       t[r][tx] = v;
+      if (FULL64) t64[FULL64 ? r : 0][tx] = g;
       if (i < n && j < n) G32[i * n + j] = v;
     }
     __syncthreads();
     if (bj != bi) {
       for (int r = ty; r < 32; r += 8) {
         const int64_t i = bj + r, j = bi + tx;  // mirrored tile
-        if (i < n && j < n) G32[i * n + j] = t[tx][r];
+        if (i < n && j < n) {
+          G32[i * n + j] = t[tx][r];
+          if (FULL64) G64[i * n + j] = t64[FULL64 ? tx : 0][r];
+        }
+      }
+    } else if (FULL64) {
+      // diagonal tile: its strict lower part from the tile (only upper entries were read)
+      for (int r = ty; r < 32; r += 8) {
+        const int64_t i = bi + r, j = bj + tx;
+        if (i < n && j < n && tx < r) G64[i * n + j] = t64[FULL64 ? tx : 0][r];
       }
     }
   }
@@ -592,10 +607,14 @@ tsvd_status launch_power_dense(int64_t n, const float *G32, const double *G64, c
   return TSVD_OK;
 }
 
-tsvd_status launch_symmetrize(int64_t n, const double *G64, float *G32, cudaStream_t stream) {
+tsvd_status launch_symmetrize(int64_t n, double *G64, float *G32, cudaStream_t stream, bool full64) {
   const int64_t nb = ceil_div(n, 32);
+  if (nb > 65535) return TSVD_EUNSUPPORTED;
   dim3 grid((unsigned)nb, (unsigned)nb), block(32, 8);
-  symmetrize_kernel<<<grid, block, 0, stream>>>(n, G64, G32);
+  if (full64)
+    symmetrize_kernel<true><<<grid, block, 0, stream>>>(n, G64, G32);
+  else
+    symmetrize_kernel<false><<<grid, block, 0, stream>>>(n, G64, G32);
   TSVD_LAUNCHED();
   return TSVD_OK;
 }

@@ -149,17 +149,6 @@ __device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
   const float bb = s - a;
   e = (a - (s - bb)) + (b - bb);
 }
-__device__ __forceinline__ void warp_sum_pair(float &hi, float &lo) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    const float ho = __shfl_xor_sync(0xffffffffu, hi, o);
-    const float lo2 = __shfl_xor_sync(0xffffffffu, lo, o);
-    float s, e;
-    two_sum(hi, ho, s, e);
-    hi = s;
-    lo = lo + lo2 + e;
-  }
-}
 
 constexpr int kMaxCluster = 8;
 constexpr int kPartSlot = kSrvMaxK + 4;  // doubles per (parity, rank) slot
@@ -208,11 +197,15 @@ __global__ void __launch_bounds__(kSrvPowerThreads, 1) srv_power_kernel(const Sr
 
   for (int l = 0; l < k; ++l) {
     // ---- start vector x ~ N(0,1)^d (every CTA draws all of it), v0 = x / ||x||
-    for (int64_t p = threadIdx.x; p < (d + 1) / 2; p += kSrvPowerThreads) {
-      double z0, z1;
-      start_normal_pair(q.key0, q.key1, (uint32_t)l, p, &z0, &z1);
-      sm.xs[2 * p] = z0;
-      if (2 * p + 1 < d) sm.xs[2 * p + 1] = z1;
+    if (q.x_start) {
+      for (int64_t i = threadIdx.x; i < d; i += kSrvPowerThreads) sm.xs[i] = q.x_start[(int64_t)l * d + i];
+    } else {
+      for (int64_t p = threadIdx.x; p < (d + 1) / 2; p += kSrvPowerThreads) {
+        double z0, z1;
+        start_normal_pair(q.key0, q.key1, (uint32_t)l, p, &z0, &z1);
+        sm.xs[2 * p] = z0;
+        if (2 * p + 1 < d) sm.xs[2 * p + 1] = z1;
+      }
     }
     __syncthreads();
     double xx = 0.0;
@@ -233,35 +226,70 @@ __global__ void __launch_bounds__(kSrvPowerThreads, 1) srv_power_kernel(const Sr
       const float *v = sm.vb[cur];
       float *nxt = sm.vb[cur ^ 1];
       double ww = 0.0, vw = 0.0, vv = 0.0;
-      for (int64_t r = r0 + warp; r < r1; r += nwarps) {
-        const float *g = Grow0 + (r - r0) * d;
-        float p0 = 0.f, p1 = 0.f, p2 = 0.f, p3 = 0.f;
+      // four rows per warp step (r0 and R are multiples of 4): four independent
+      // dot products and warp reductions in flight; rows past r1 repeat the
+      // last row and are dropped
+      for (int64_t rb = r0 + 4 * warp; rb < r1; rb += 4 * nwarps) {
+        const int nr = (int)min((int64_t)4, r1 - rb);
+        const float *g[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) g[u] = Grow0 + (min(rb + u, r1 - 1) - r0) * d;
+        float p[4][4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) p[u][0] = p[u][1] = p[u][2] = p[u][3] = 0.f;
         if (vec) {
-          const float4 *g4 = reinterpret_cast<const float4 *>(g);
           const float4 *v4 = reinterpret_cast<const float4 *>(v);
           for (int64_t c = lane; c < d / 4; c += 32) {
-            const float4 a = g4[c], b = v4[c];
-            p0 = fmaf(a.x, b.x, p0);
-            p1 = fmaf(a.y, b.y, p1);
-            p2 = fmaf(a.z, b.z, p2);
-            p3 = fmaf(a.w, b.w, p3);
+            const float4 b = v4[c];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+              const float4 a = reinterpret_cast<const float4 *>(g[u])[c];
+              p[u][0] = fmaf(a.x, b.x, p[u][0]);
+              p[u][1] = fmaf(a.y, b.y, p[u][1]);
+              p[u][2] = fmaf(a.z, b.z, p[u][2]);
+              p[u][3] = fmaf(a.w, b.w, p[u][3]);
+            }
           }
         } else {
-          for (int64_t c = lane; c < d; c += 32) p0 = fmaf(g[c], v[c], p0);
+          for (int64_t c = lane; c < d; c += 32) {
+            const float b = v[c];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) p[u][0] = fmaf(g[u][c], b, p[u][0]);
+          }
         }
-        float h, e, sa, ea, sb, eb;
-        two_sum(p0, p1, sa, ea);
-        two_sum(p2, p3, sb, eb);
-        two_sum(sa, sb, h, e);
-        e += ea + eb;
-        warp_sum_pair(h, e);
+        float h[4], e[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          float sa, ea, sb, eb;
+          two_sum(p[u][0], p[u][1], sa, ea);
+          two_sum(p[u][2], p[u][3], sb, eb);
+          two_sum(sa, sb, h[u], e[u]);
+          e[u] += ea + eb;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const float ho = __shfl_xor_sync(0xffffffffu, h[u], o);
+            const float lo2 = __shfl_xor_sync(0xffffffffu, e[u], o);
+            float sx, ex;
+            two_sum(h[u], ho, sx, ex);
+            h[u] = sx;
+            e[u] = e[u] + lo2 + ex;
+          }
+        }
         if (lane == 0) {
-          const double t = (double)(float)((double)h + (double)e);
-          const double vr = (double)v[r];
-          ww += t * t;
-          vw += vr * t;
-          vv += vr * vr;
-          nxt[r] = (float)t;
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            if (u < nr) {
+              const double t = (double)(float)((double)h[u] + (double)e[u]);
+              const double vr = (double)v[rb + u];
+              ww += t * t;
+              vw += vr * t;
+              vv += vr * vr;
+              nxt[rb + u] = (float)t;
+            }
+          }
         }
       }
       if (lane == 0) {
@@ -443,7 +471,6 @@ __global__ void __launch_bounds__(kSrvPowerThreads, 1) srv_power_kernel(const Sr
     }
     if (rank == 0 && threadIdx.x == 0) {
       q.sig2[l] = s2;
-      q.sigma[l] = sqrt(s2);
       q.info[4 * l] = it;
       q.info[4 * l + 1] = status;
       q.info[4 * l + 2] = 0;
@@ -469,7 +496,9 @@ __global__ void __launch_bounds__(kSrvPowerThreads, 1) srv_power_kernel(const Sr
   cluster_sync_all();  // every CTA's rows of vout are written
   const int64_t m = q.m, n = q.n;
   const float *__restrict__ A = q.A;
-  if (!q.trans) {
+  if (q.no_other) {
+    // the caller forms the other factor itself
+  } else if (!q.trans) {
     // U[r][l] = sum_j A[r][j] V[j][l] / sigma_l; this CTA's rows of U, one row per warp at a time,
     // V staged in chunks of kSrvOtherChunk rows (l-major) in shared memory
     const int64_t Rm = (m + C - 1) / C;

@@ -34,8 +34,6 @@ struct SrvReq {
   double *sig2;      // k
   int32_t *info;     // 4 per triplet: applications, status (0 ok, 1 no convergence, 2 rank), 0, 0
   float *vout;       // d x k column-major FP32 copy of V64
-  float *other;      // trans 0: U (m x k), trans 1: V (n x k); column-major
-  double *sigma;     // k
   double eps;
   int32_t max_iter;
   int32_t sign_convention;
@@ -50,6 +48,9 @@ struct SrvReq {
   int32_t *oInfo;       // 4 k
   uint32_t *flag;       // set to `ticket` (release, gpu scope) once everything above is written
   uint32_t ticket;
+  int32_t no_other;     // 1: skip the other factor (oU when m >= n); the power vectors, sigma and info are written
+  const double *x_start;  // d x k column-major start draws used as x_l, or null (Philox draws of key0/key1);
+                          // may alias V64: column l is read before the triplet's vector overwrites it
 };
 
 // Work item of the grouped SYRK: request, tile row, tile column (ti >= tj).
@@ -66,6 +67,20 @@ constexpr int kSrvOtherChunk = 128;   // rows of V (tall) or U (wide) staged per
 // rows of G each CTA of a cluster owns: ceil(d / cluster) rounded up to 4
 __host__ __device__ inline int64_t srv_rows_per_cta(int64_t d, int64_t cluster) {
   return ((d + cluster - 1) / cluster + 3) & ~int64_t(3);
+}
+
+// largest power-of-two cluster size <= c that leaves no CTA of the cluster without rows
+__host__ __device__ inline int srv_clamp_cluster(int64_t d, int c) {
+  while (c > 1 && srv_rows_per_cta(d, c) * (c - 1) >= d) c >>= 1;
+  return c > 1 ? c : 1;
+}
+
+// Every pointer the grouped kernels dereference is set (host check before a
+// launch; the kernels themselves do not test them).
+inline bool srv_req_complete(const SrvReq &q) {
+  if (!q.G64 || !q.G32 || !q.V64 || !q.sig2 || !q.info || !q.vout || !q.oS || !q.oInfo || !q.flag) return false;
+  if (q.no_other) return q.trans ? q.oU != nullptr : q.oV != nullptr;  // the power vectors' copy
+  return q.A && q.oU && q.oV;
 }
 
 // Dynamic shared memory of the power kernel for (d, cluster, resident).

@@ -250,10 +250,7 @@ int bucket_of(int64_t d) {
   return b;
 }
 
-int clamp_cluster(int64_t d, int c) {
-  while (c > 1 && srv_rows_per_cta(d, c) * (c - 1) >= d) c >>= 1;  // no CTA of the cluster without rows
-  return std::max(c, 1);
-}
+int clamp_cluster(int64_t d, int c) { return srv_clamp_cluster(d, c); }
 
 int cluster_for(const tsvd_server_s *s, int64_t d) {
   return clamp_cluster(d, std::min(s->cluster_table[bucket_of(d)], s->opt.cluster_cap));
@@ -320,7 +317,13 @@ tsvd_status launch_wave(tsvd_server_s *sv, Slot &s) {
   s.dev_bytes = need;
   unsigned char *dev = sv->arena.base + s.dev_off;
   SrvReq *hreq = reinterpret_cast<SrvReq *>(s.stage);
-  for (size_t i = 0; i < rs.size(); ++i) hreq[i] = rs[i]->dq;
+  for (size_t i = 0; i < rs.size(); ++i) {
+    if (!srv_req_complete(rs[i]->dq)) {
+      set_error_text("server: request descriptor with an unset pointer");
+      return TSVD_EINVAL;
+    }
+    hreq[i] = rs[i]->dq;
+  }
   std::memcpy(s.stage + b_req, tiles.data(), tiles.size() * sizeof(SrvTile));
   cudaStream_t st = s.stream;
   for (auto &r : rs) {
@@ -583,6 +586,7 @@ tsvd_status time_power(tsvd_server_s *sv, int64_t d, int c, int nreq, int iters,
     r.dq.resident = resident;
     r.dq.flag = dflags + i;
     r.dq.ticket = 1u;
+    if (!srv_req_complete(r.dq)) ls = TSVD_EINVAL;
     reqs[i] = r.dq;
     fill_uniform_kernel<<<64, 256, 0, st>>>(const_cast<float *>(r.dq.A), d * d, (uint32_t)i);
     if (cudaGetLastError() != cudaSuccess) ls = TSVD_ECUDA;

@@ -90,6 +90,18 @@ def test_plan_validation_dense(lib):
     d3, keep4 = _dense_desc(100, 20)
     d3.m = 0
     assert _plan(d3, 1, 1e-6)[0] == B.TSVD_EINVAL
+    # power-phase kernel choice
+    for pk in (B.TSVD_POWER_AUTO, B.TSVD_POWER_GRID, B.TSVD_POWER_CLUSTER):
+        assert _plan(d, 5, 1e-6, _opts(power_kernel=pk))[0] == B.TSVD_OK
+    assert _plan(d, 5, 1e-6, _opts(power_kernel=3))[0] == B.TSVD_EINVAL
+    assert _plan(d, 5, 1e-6, _opts(power_kernel=-1))[0] == B.TSVD_EINVAL
+    big, keep5 = _dense_desc(8, 2049, arr=np.zeros((1, 1), dtype=np.float32))
+    big.m = 4096  # plan reads no values
+    assert _plan(big, 4, 1e-6, _opts(power_kernel=B.TSVD_POWER_CLUSTER))[0] == B.TSVD_EUNSUPPORTED
+    assert _plan(big, 4, 1e-6, _opts(power_kernel=B.TSVD_POWER_AUTO))[0] == B.TSVD_OK
+    tall, keep6 = _dense_desc(200, 64)
+    assert _plan(tall, 33, 1e-6, _opts(power_kernel=B.TSVD_POWER_CLUSTER))[0] == B.TSVD_EUNSUPPORTED
+    assert _plan(tall, 32, 1e-6, _opts(power_kernel=B.TSVD_POWER_CLUSTER))[0] == B.TSVD_OK
 
 
 def test_plan_budget_and_streaming_layout(lib):

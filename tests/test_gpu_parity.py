@@ -288,8 +288,9 @@ def _compare(res, o, k, angle_tol=1e-4, sig_tol=1e-5, gapped=None):
         assert ref.vector_angle(np.asarray(res.U[:, l]), o.U[:, l]) <= angle_tol, l
 
 
+@pytest.mark.parametrize("pk", [B.TSVD_POWER_GRID, B.TSVD_POWER_CLUSTER])
 @pytest.mark.parametrize("mode", ["device", "resident", "stream"])
-def test_tsvd_c1_matches_oracle(mode):
+def test_tsvd_c1_matches_oracle(mode, pk):
     m, n, k, eps = 2048, 256, 8, 1e-8
     inp = synth.dense_prescribed(m, n, synth.spectrum_geometric(n, 0.8), 1e-6, seed=0)
     A = inp["A"]
@@ -304,6 +305,7 @@ def test_tsvd_c1_matches_oracle(mode):
         Ain = A
         if mode == "stream":
             kw = dict(force_stream=True, block_rows=300, n_buffers=2)
+    kw["power_kernel"] = pk
     # same trajectory: the oracle's iteration counts forced
     r = tsvd(Ain, k, eps, start_draws=x, iters_override=o.iters, **kw)
     assert r.iters == o.iters
@@ -319,6 +321,41 @@ def test_tsvd_c1_matches_oracle(mode):
     assert np.allclose(V.T @ V, np.eye(k), atol=3e-3)
     assert np.allclose(V.T @ V, o.V.T @ o.V, atol=1e-5)
     assert np.allclose(U.T @ U, o.U.T @ o.U, atol=1e-4)
+
+
+# m, n, k, rho: odd n (scalar row loads), n not a multiple of 4, n = 512 with k = 32 (rows of the
+# FP32 Gram resident in shared memory), n = 2048 (rows read from L2), n = 1000; sigma_{k-1}/sigma_0
+# stays above ~0.04, inside the FP32-Gram envelope of 1e-5 in sigma
+POWER_CASES = [(3000, 5, 5, 0.5), (2000, 130, 12, 0.8), (4096, 512, 32, 0.9), (6000, 2048, 8, 0.7),
+               (1024, 1000, 16, 0.85)]
+
+
+@pytest.mark.parametrize("pk", [B.TSVD_POWER_GRID, B.TSVD_POWER_CLUSTER])
+@pytest.mark.parametrize("m,n,k,rho", POWER_CASES)
+def test_tsvd_power_kernels_match_oracle(pk, m, n, k, rho):
+    """Both kernels of the dense power phase follow the oracle's trajectory
+    (forced counts, caller start draws, sign convention)."""
+    inp = synth.dense_prescribed(m, n, synth.spectrum_geometric(n, rho), 1e-7, seed=n)
+    x = synth.start_normals(n, k, seed=2)
+    o = ref.tsvd_dense(inp["A"], k, 1e-10, x_start=x, sign_convention=True)
+    r = tsvd(torch.from_numpy(inp["A"]).cuda(), k, 1e-10, start_draws=x, iters_override=o.iters,
+             sign_convention=True, power_kernel=pk)
+    assert r.iters == o.iters
+    _compare(r, o, k, gapped=ref.gapped_indices(o.sigma ** 2, k))
+    # the sign convention fixes the vectors themselves, not only their span
+    for l in ref.gapped_indices(o.sigma ** 2, k):
+        assert np.max(np.abs(np.asarray(r.V[:, l], dtype=np.float64) - o.V[:, l])) < 1e-4
+
+
+def test_tsvd_cluster_power_builtin_draws_and_own_convergence():
+    """The cluster kernel draws x_l from the built-in Philox stream itself and
+    takes its own convergence decisions (counts within one of the oracle's)."""
+    m, n, k, eps = 2048, 256, 8, 1e-8
+    inp = synth.dense_prescribed(m, n, synth.spectrum_geometric(n, 0.8), 1e-6, seed=0)
+    o = ref.tsvd_dense(inp["A"], k, eps, seed=11)
+    r = tsvd(torch.from_numpy(inp["A"]).cuda(), k, eps, seed=11, power_kernel=B.TSVD_POWER_CLUSTER)
+    assert all(abs(a - b) <= 1 for a, b in zip(r.iters, o.iters))
+    assert np.max(np.abs(r.sigma - o.sigma) / o.sigma) <= 1e-5
 
 
 def test_tsvd_builtin_start_vectors_match_oracle_generator():
@@ -562,10 +599,9 @@ def test_tsvd_tensor_cores_c2_shape(prec, budget):
 
 @pytest.mark.parametrize("prec,where", [(B.TSVD_GRAM_TF32X3, "device"), (B.TSVD_GRAM_BF16X3, "device"),
                                         (B.TSVD_GRAM_TF32X3, "resident")])
-def test_tsvd_in_core_prep_pipeline(prec, where):
-    """In core with many chunks the prep of chunk c+1 (its own stream, one CTA
-    per SM) runs beside the SYRK of chunk c, on two scratch buffers; the
-    result is the same trajectory as the oracle's."""
+def test_tsvd_in_core_many_chunks(prec, where):
+    """In core with many chunks (a ragged last one) on the tensor-core Gram:
+    the same trajectory as the oracle's, no flag but the pageable-input one."""
     m, n, k, eps = 40000, 384, 6, 1e-6
     sig = 1.0 / (1.0 + np.arange(64))
     V = synth.orthonormal_columns(n, 64, 5, 1)
@@ -577,5 +613,5 @@ def test_tsvd_in_core_prep_pipeline(prec, where):
     Ain = torch.from_numpy(A).cuda() if where == "device" else A
     r = tsvd(Ain, k, eps, start_draws=x, iters_override=o.iters, precision=prec, block_rows=3000)
     assert r.report["n_blocks"] == -(-m // 3008) and r.report["mode"] == (0 if where == "device" else 1)
-    assert r.report["flags"] == 0
+    assert r.report["flags"] & ~B.TSVD_FLAG_PAGEABLE == 0
     _compare(r, o, k, gapped=gapped)
