@@ -849,11 +849,24 @@ def csr_workload(args):
     iters = [args.csr_iters] * k
     peaks, peak_src = load_peaks()
     roofline, cpu = csr_pair_checks(dcsr, host, m, nnz, peaks, peak_src, args)
-    plan_d = Plan(dcsr, k, EPS, out_device=True, iters_override=iters)
+    plan_d = Plan(dcsr, k, EPS, out_device=True, iters_override=iters, time_kernels=True)
     sec, wall, reps, res = time_steps(plan_d, dcsr, args.steps, args.warmup)
     apps = reps[-1]["applications"]
     passes = apps + k + 1  # applications, one sigma pass per triplet, the U pass
     value = csr_bytes * passes * args.steps / sec / 1e9
+    # the operator the in-core t-SVD runs (column-chunked two-pass when v and w outgrow L2):
+    # CUDA events around every application on the launching stream
+    nch = reps[-1]["csr_chunks"]
+    if nch and reps[-1]["gram_kernel_launches"]:
+        t_app = reps[-1]["gram_kernel_ms"] / reps[-1]["gram_kernel_launches"] / 1e3
+        alg = roofline["algorithmic_bytes"]
+        fused = {k2: roofline[k2] for k2 in ("achieved", "frac", "traffic", "ms_per_application")}
+        roofline.update({"achieved": round(alg / t_app / 1e9, 1), "frac": round(alg / t_app / 1e9 / peaks["hbm_gbs"], 4),
+                         "traffic": measured_traffic("csr_chunk_y_kernel+csr_chunk_w_kernel", m, m),
+                         "kernel": f"column-chunked CSR operator ({nch} chunks: csr_chunk_y + csr_chunk_w)",
+                         "ms_per_application": round(t_app * 1e3, 3),
+                         "applications_timed": reps[-1]["gram_kernel_launches"],
+                         "fused_pair_kernel": fused})
     plan_d.close()
     del plan_d
     torch.cuda.empty_cache()

@@ -155,6 +155,11 @@ typedef struct {
   double h2d_copy_ms;       /* summed duration of those copies on the copy stream */
   double h2d_copy_min_gbps; /* slowest single timed copy, 1e9 bytes per second */
   double h2d_copy_max_gbps; /* fastest single timed copy */
+  int32_t csr_chunks;       /* CSR: column chunks of the two-pass operator (v and w
+                               chunks that fit in L2), 0 = the fused single-pass
+                               operator; dense: 0 */
+  int32_t power_cluster;    /* dense: CTAs of the cluster power kernel, 0 = the
+                               grid-wide cooperative kernel (and CSR) */
 } tsvd_report;
 
 #define TSVD_FLAG_NOCONV 1        /* a triplet hit max_iter */

@@ -45,7 +45,7 @@ class tsvd_report(C.Structure):
                 ("d2h_bytes", C.c_double), ("gram_kernel_ms", C.c_double), ("kernel_launches", C.c_int64),
                 ("applications", C.c_int64), ("ring_slots", C.c_int32), ("h2d_copies", C.c_int32),
                 ("h2d_copy_ms", C.c_double), ("h2d_copy_min_gbps", C.c_double),
-                ("h2d_copy_max_gbps", C.c_double)]
+                ("h2d_copy_max_gbps", C.c_double), ("csr_chunks", C.c_int32), ("power_cluster", C.c_int32)]
 
 
 class tsvd_server_options(C.Structure):

@@ -1194,6 +1194,8 @@ tsvd_status tsvd_factor(tsvd_plan_t plan, const tsvd_matrix *A, void *workspace,
   if (report) {
     report->h2d_bytes = r.h2d;
     report->d2h_bytes = r.d2h;
+    report->csr_chunks = (p->kind == TSVD_CSR_F32_I32_I64 && r.chunked) ? p->csr_nch : 0;
+    report->power_cluster = (p->kind == TSVD_DENSE_F32_ROWMAJOR && p->cluster_power) ? p->srv_req.cluster : 0;
     report->kernel_launches = launches_so_far() - l0;
     if (st == TSVD_OK || st == TSVD_ENOCONV || st == TSVD_ERANK) {
       double ms = 0.0, gmin = 0.0, gmax = 0.0;

@@ -324,10 +324,11 @@ def test_tsvd_c1_matches_oracle(mode, pk):
 
 
 # m, n, k, rho: odd n (scalar row loads), n not a multiple of 4, n = 512 with k = 32 (rows of the
-# FP32 Gram resident in shared memory), n = 2048 (rows read from L2), n = 1000; sigma_{k-1}/sigma_0
-# stays above ~0.04, inside the FP32-Gram envelope of 1e-5 in sigma
-POWER_CASES = [(3000, 5, 5, 0.5), (2000, 130, 12, 0.8), (4096, 512, 32, 0.9), (6000, 2048, 8, 0.7),
-               (1024, 1000, 16, 0.85)]
+# FP32 Gram resident in shared memory), n = 2048 (rows read from L2), n = 1000.  sigma_{k-1}/sigma_0
+# stays above 0.1: the FP32-accumulated Gram's error, relative to lambda_0, is ~1e-7 on these shapes,
+# so sigma_{k-1} moves by ~1e-7 / (2 (sigma_{k-1}/sigma_0)^2), and 1e-5 needs the ratio well above 0.07
+POWER_CASES = [(3000, 5, 5, 0.6), (2000, 130, 12, 0.82), (4096, 512, 32, 0.93), (6000, 2048, 8, 0.75),
+               (1024, 1000, 16, 0.87)]
 
 
 @pytest.mark.parametrize("pk", [B.TSVD_POWER_GRID, B.TSVD_POWER_CLUSTER])
