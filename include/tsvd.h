@@ -118,7 +118,13 @@ typedef struct {
   int32_t power_kernel;          /* dense power phase (Alg. 1 loop over l, Alg. 2 per
                                     triplet): TSVD_POWER_AUTO, TSVD_POWER_GRID or
                                     TSVD_POWER_CLUSTER */
-  int32_t reserved[4];
+  int32_t gram_tile;             /* dense: width of the column panels of the orthogonal
+                                    batching (a multiple of 256): the Gram matrix is
+                                    formed as tiles A_J^T A_I (J <= I) and kept as FP64
+                                    tiles on the device or, when they do not fit the
+                                    budget, in page-locked host memory; 0 = only when
+                                    the whole Gram matrix does not fit the budget */
+  int32_t reserved[3];
 } tsvd_options;
 
 /* Kernels of the dense power phase.  GRID: one cooperative launch per
@@ -160,6 +166,11 @@ typedef struct {
                                operator; dense: 0 */
   int32_t power_cluster;    /* dense: CTAs of the cluster power kernel, 0 = the
                                grid-wide cooperative kernel (and CSR) */
+  int32_t gram_panels;      /* dense, orthogonal batching: column panels of A
+                               (tasks = panels (panels + 1) / 2); 0 = one Gram */
+  int32_t tiles_on_host;    /* orthogonal batching: 1 = the Gram tiles live in
+                               page-locked host memory and every application
+                               streams them in; 0 = they stay on the device */
 } tsvd_report;
 
 #define TSVD_FLAG_NOCONV 1        /* a triplet hit max_iter */

@@ -34,8 +34,8 @@ class tsvd_options(C.Structure):
                 ("precision", C.c_int32), ("max_iter", C.c_int32), ("sign_convention", C.c_int32),
                 ("iters_override", C.c_void_p), ("start_draws", C.c_void_p), ("seed", C.c_uint64),
                 ("out_location", C.c_int32), ("force_stream", C.c_int32), ("time_kernels", C.c_int32),
-                ("power_kernel", C.c_int32),
-                ("reserved", C.c_int32 * 4)]
+                ("power_kernel", C.c_int32), ("gram_tile", C.c_int32),
+                ("reserved", C.c_int32 * 3)]
 
 
 class tsvd_report(C.Structure):
@@ -45,7 +45,8 @@ class tsvd_report(C.Structure):
                 ("d2h_bytes", C.c_double), ("gram_kernel_ms", C.c_double), ("kernel_launches", C.c_int64),
                 ("applications", C.c_int64), ("ring_slots", C.c_int32), ("h2d_copies", C.c_int32),
                 ("h2d_copy_ms", C.c_double), ("h2d_copy_min_gbps", C.c_double),
-                ("h2d_copy_max_gbps", C.c_double), ("csr_chunks", C.c_int32), ("power_cluster", C.c_int32)]
+                ("h2d_copy_max_gbps", C.c_double), ("csr_chunks", C.c_int32), ("power_cluster", C.c_int32),
+                ("gram_panels", C.c_int32), ("tiles_on_host", C.c_int32)]
 
 
 class tsvd_server_options(C.Structure):

@@ -8,6 +8,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <functional>
 #include <new>
 #include <string>
 #include <vector>
@@ -98,6 +99,13 @@ struct tsvd_plan_s {
   bool csr_sorted = true;     // every row's columns ascending (host CSR: checked at plan time)
   size_t o_csr_y = 0, o_csr_split = 0, b_split_slot = 0;
   int vec_grid = 0;
+  // orthogonal batching (dense; Sec. V-C, Alg. 3): the Gram matrix as FP64 tiles
+  // B_JI = A_J^T A_I (J <= I) of tb-column panels, formed task by task
+  bool tiled = false;
+  int64_t tb = 0, n_panels = 0, n_tasks = 0, pan_rows = 0;
+  bool tiles_host = false;   // tiles in page-locked host memory, streamed in every application
+  size_t b_tile = 0, o_tiles = 0, o_Gt = 0, o_pan = 0, b_pan = 0, o_w64 = 0, o_Vc = 0;
+  double *host_tiles = nullptr;  // n_tasks tiles of tb x tb (allocated on the first factorisation)
   // dense power phase on one thread-block cluster (n <= kSrvMaxDim, k <= kSrvMaxK)
   bool cluster_power = false;
   SrvReq srv_req{};  // host copy of the descriptor the cluster kernel reads (copied per call)
@@ -141,9 +149,12 @@ void partition_rows(int64_t m, int64_t block_rows, std::vector<int64_t> &starts)
   starts.push_back(m);
 }
 
+tsvd_status plan_dense_tiled(tsvd_plan_s *p);
+
 tsvd_status plan_dense(tsvd_plan_s *p) {
   const int64_t n = p->n, k = p->k, m = p->m;
   const int prec = p->opt.precision;
+  if (p->opt.gram_tile > 0) return plan_dense_tiled(p);
   Carve c;
   p->o_G64 = c.take((size_t)n * n * 8);
   p->o_G32 = c.take((size_t)n * n * 4);
@@ -181,7 +192,10 @@ tsvd_status plan_dense(tsvd_plan_s *p) {
   if (budget) {
     while (rows > 32 && fixed + (mode == MODE_RESIDENT ? resident_bytes : 0) + chunk_cost(rows, mode) > budget)
       rows = round_up(rows / 2, 32);
-    if (fixed + (mode == MODE_RESIDENT ? resident_bytes : 0) + chunk_cost(rows, mode) > budget) return TSVD_EBUDGET;
+    if (fixed + (mode == MODE_RESIDENT ? resident_bytes : 0) + chunk_cost(rows, mode) > budget) {
+      // the whole Gram matrix does not fit: orthogonal batching
+      return plan_dense_tiled(p);
+    }
   }
   p->mode = mode;
   p->chunk_rows = rows;
@@ -207,8 +221,113 @@ tsvd_status plan_dense(tsvd_plan_s *p) {
     p->o_ring = c.take(p->b_slot * slots);
   }
   p->ws = c.off;
-  if (budget && p->ws > budget) return TSVD_EBUDGET;
+  if (budget && p->ws > budget) return plan_dense_tiled(p);
   return TSVD_OK;
+}
+
+// Orthogonal batching: panels of tb columns, tasks (I, J) with J <= I (the
+// symmetric task reuse: only B_JI = A_J^T A_I is formed, B_IJ is its
+// transpose).  Workspace: the explicit power loop's vectors, the tiles (all
+// of them when they fit, else a ring of n_buffers through which every
+// application streams them from page-locked host memory), then one region
+// used in turn by the Gram tasks (task tile, tensor-core scratch, panel ring
+// for host A) and by the U pass (row-block ring for host A, U staging).
+tsvd_status plan_dense_tiled(tsvd_plan_s *p) {
+  const int64_t n = p->n, k = p->k, m = p->m;
+  const int prec = p->opt.precision;
+  if (k + 4 > kVecPartStride) return TSVD_EUNSUPPORTED;
+  const size_t budget = p->opt.device_budget;
+  const bool host_a = p->location == TSVD_HOST;
+  const bool host_u = p->opt.out_location == TSVD_HOST;
+  const int R = std::max(2, p->n_buffers);
+  p->n_buffers = R;
+  p->tiled = true;
+  p->cluster_power = false;
+  p->o_G64 = p->o_G32 = p->o_V64 = p->o_pscr = p->o_res = 0;
+  Carve c;
+  p->o_v = c.take((size_t)n * 4);
+  p->o_vn = c.take((size_t)n * 4);
+  p->o_w = c.take((size_t)n * 4);
+  p->o_x64 = c.take((size_t)n * 8);
+  p->o_w64 = c.take((size_t)n * 8);
+  p->o_Vr = c.take((size_t)n * k * 4);
+  p->o_Vc = c.take((size_t)n * k * 4);
+  p->o_sig2 = c.take((size_t)k * 8);
+  p->o_sigma = c.take((size_t)k * 8);
+  p->o_info = c.take((size_t)k * 4 * sizeof(int32_t));
+  p->o_flag = c.take(256);
+  p->vec_grid = 1024;
+  p->o_vsc = c.take(vec_scratch_bytes(p->vec_grid));
+  const size_t fixed = c.off;
+  auto al = [](size_t x) { return (size_t)round_up((int64_t)x, 256); };
+  auto gram_area = [&](int64_t bs, int64_t rows) -> size_t {
+    size_t g = al((size_t)bs * 2 * bs * 8);
+    if (prec != TSVD_GRAM_FP32) g += gram_tc_scratch_bytes(rows, 2 * bs, prec) + 256;
+    if (host_a) g += (size_t)R * al((size_t)rows * 2 * bs * 4);
+    return g;
+  };
+  auto u_area = [&](int64_t rows) -> size_t {
+    return (host_a ? (size_t)R * al((size_t)rows * n * 4) : 0) + (host_u ? 2 * al((size_t)rows * k * 4) : 0);
+  };
+  auto shrink = [&](int64_t target, const std::function<size_t(int64_t)> &need, size_t room) -> int64_t {
+    int64_t rows = std::min<int64_t>(round_up(std::max<int64_t>(target, 32), 32), round_up(m, 32));
+    while (rows > 32 && need(rows) > room) rows = round_up(rows / 2, 32);
+    return need(rows) <= room ? rows : 0;
+  };
+  std::vector<int64_t> cands;
+  if (p->opt.gram_tile > 0) {
+    cands.push_back(p->opt.gram_tile);
+  } else {
+    for (int64_t bs = std::min<int64_t>(round_up(n, 256), 8192); bs >= 256; bs = bs / 2 / 256 * 256) {
+      cands.push_back(bs);
+      if (bs == 256) break;
+    }
+  }
+  for (const int64_t bs : cands) {
+    const int64_t nb = ceil_div(n, bs), tasks = nb * (nb + 1) / 2;
+    const size_t bt = al((size_t)bs * bs * 8);
+    for (int host_tiles = 0; host_tiles < 2; ++host_tiles) {
+      const size_t tiles = host_tiles ? (size_t)R * bt : (size_t)tasks * bt;
+      size_t room = SIZE_MAX;
+      if (budget) {
+        if (fixed + tiles >= budget) continue;
+        room = budget - fixed - tiles;
+      }
+      const int64_t pr = shrink(std::max<int64_t>(256, ((int64_t)1 << 30) / (2 * bs * 4)),
+                                [&](int64_t r) { return gram_area(bs, r); }, room);
+      const int64_t ur = shrink(std::max<int64_t>(256, ((int64_t)1 << 30) / (n * 4)), u_area, room);
+      if (!pr || !ur) continue;
+      p->tb = bs;
+      p->n_panels = nb;
+      p->n_tasks = tasks;
+      p->tiles_host = host_tiles != 0;
+      p->b_tile = bt;
+      p->pan_rows = std::min(pr, m);
+      p->o_tiles = c.take(tiles);
+      const size_t o_phase = c.take(std::max(gram_area(bs, p->pan_rows), u_area(ur)));
+      // Gram tasks: task tile, tensor-core scratch, panel ring
+      p->o_Gt = o_phase;
+      size_t off = o_phase + al((size_t)bs * 2 * bs * 8);
+      p->b_gscr = prec != TSVD_GRAM_FP32 ? gram_tc_scratch_bytes(p->pan_rows, 2 * bs, prec) : 0;
+      p->o_gscr = off;
+      if (prec != TSVD_GRAM_FP32) off += p->b_gscr + 256;
+      p->b_pan = al((size_t)p->pan_rows * 2 * bs * 4);
+      p->o_pan = off;
+      // U pass: row-block ring (host A), then the U staging
+      p->mode = host_a ? MODE_STREAM : MODE_DEVICE;
+      p->chunk_rows = std::min(ur, m);
+      p->n_chunks = ceil_div(m, p->chunk_rows);
+      p->b_slot = host_a ? al((size_t)p->chunk_rows * n * 4) : 0;
+      p->o_ring = o_phase;
+      if (host_u) {
+        p->b_ubuf = al((size_t)p->chunk_rows * k * 4);
+        p->o_ubuf = o_phase + (host_a ? (size_t)R * p->b_slot : 0);
+      }
+      p->ws = c.off;
+      return TSVD_OK;
+    }
+  }
+  return TSVD_EBUDGET;
 }
 
 tsvd_status plan_csr(tsvd_plan_s *p, const tsvd_matrix *A) {
@@ -352,6 +471,8 @@ tsvd_status tsvd_plan(tsvd_plan_t *out, const tsvd_matrix *A, int64_t k, double 
   if (opt.out_location != TSVD_HOST && opt.out_location != TSVD_DEVICE) return TSVD_EINVAL;
   if (opt.block_rows < 0) return TSVD_EINVAL;
   if (opt.power_kernel < TSVD_POWER_AUTO || opt.power_kernel > TSVD_POWER_CLUSTER) return TSVD_EINVAL;
+  if (opt.gram_tile < 0 || opt.gram_tile % 256 != 0) return TSVD_EINVAL;
+  if (opt.gram_tile > 0 && A->kind != TSVD_DENSE_F32_ROWMAJOR) return TSVD_EINVAL;
   const bool cluster_fits = A->kind == TSVD_DENSE_F32_ROWMAJOR && A->n <= kSrvMaxDim && k <= kSrvMaxK;
   if (opt.power_kernel == TSVD_POWER_CLUSTER && !cluster_fits) {
     set_error_text("tsvd_plan: the cluster power kernel takes dense A with n <= " + std::to_string(kSrvMaxDim) +
@@ -428,6 +549,7 @@ void tsvd_destroy(tsvd_plan_t p) {
     if (p->ev_csplit) cudaEventDestroy(p->ev_csplit);
     if (p->ev_cjoin) cudaEventDestroy(p->ev_cjoin);
     if (p->d2h_stream) cudaStreamDestroy(p->d2h_stream);
+    if (p->host_tiles) cudaFreeHost(p->host_tiles);
     if (cur != p->device) cudaSetDevice(cur);
   }
   delete p;
@@ -583,15 +705,17 @@ tsvd_status left_pass_dense(Run &r, const float *V32, const double *sigma, float
   // In the streamed mode the last n_buffers row blocks of the Gram pass are
   // still in the ring (block c in slot c % n_buffers): use them first, then
   // stream the others through the slots they free.
+  // (Not after an orthogonally batched Gram: its ring held column panels.)
   const int64_t nc = p->n_chunks;
-  const int64_t first_res = p->mode == MODE_STREAM ? std::max<int64_t>(0, nc - p->n_buffers) : nc;
+  const bool reuse = p->mode == MODE_STREAM && !p->tiled;
+  const int64_t first_res = reuse ? std::max<int64_t>(0, nc - p->n_buffers) : nc;
   for (int64_t idx = 0; idx < nc; ++idx) {
-    const int64_t c = p->mode == MODE_STREAM ? (idx < nc - first_res ? first_res + idx : idx - (nc - first_res)) : idx;
+    const int64_t c = reuse ? (idx < nc - first_res ? first_res + idx : idx - (nc - first_res)) : idx;
     const int64_t r0 = c * p->chunk_rows, rows = std::min(p->chunk_rows, p->m - r0);
     const float *Ab;
     int64_t ldb;
     int slot;
-    if (p->mode == MODE_STREAM && c >= first_res) {
+    if (reuse && c >= first_res) {
       slot = (int)(c % p->n_buffers);
       Ab = reinterpret_cast<const float *>(r.ws + p->o_ring + p->b_slot * slot);
       ldb = p->n;
@@ -973,6 +1097,274 @@ tsvd_status csr_kernel_time(Run &r) {
   return TSVD_OK;
 }
 
+// Vectors of the power loop with an explicit operator (CSR, tiled Gram).
+struct ExplicitLoop {
+  float *v, *vn, *w;  // iterate, next iterate, operator output (n each)
+  double *x64;        // FP64 start draws (n)
+  double *ss;         // the operator's v^T G v (sigma pass)
+  float *Vr;          // the vectors found so far, n x k row-major (ld k)
+  float *Vcol;        // optional n x k column-major copy (ld n), or null
+  double *sig2;       // k
+  int32_t *info;      // 4 k
+  VecScratch sc;
+};
+
+// Alg. 1 loop over l with Alg. 2 per triplet, the operator B v applied
+// explicitly (w = A^T A v or w = G v) and Hotelling's correction
+// w -= V (sigma^2 . V^T v) (Eq. 2) in the vector kernels; the convergence
+// test runs on the device and the host reads its decision after every
+// application.  sigma_l^2 = v_l^T A^T A v_l from one more application.
+tsvd_status explicit_power(Run &r, ExplicitLoop &L,
+                           const std::function<tsvd_status(const float *, float *, double *, int)> &apply,
+                           const std::function<tsvd_status()> &after_sync, float *V_out, int *flags_out,
+                           int64_t *apps_out, tsvd_report *rep) {
+  tsvd_plan_s *p = r.p;
+  const int64_t n = p->n, k = p->k;
+  float *v = L.v, *vn = L.vn;
+  VecScratch sc = L.sc;
+  std::vector<double> hsig2((size_t)k, 0.0);
+  TSVD_CUDA(cudaMemsetAsync(L.info, 0, (size_t)k * 16, r.cs));
+  int flags = 0;
+  int64_t apps = 0;
+  const bool host_out = p->opt.out_location == TSVD_HOST;
+  for (int64_t l = 0; l < k; ++l) {
+    // start vector v0 = x / ||x||
+    if (!p->start_draws.empty()) {
+      TSVD_CUDA(cudaMemcpyAsync(L.x64, p->start_draws.data() + l * n, (size_t)n * 8, cudaMemcpyHostToDevice, r.cs));
+      r.h2d += (double)n * 8;
+    } else {
+      TSVD_TRY(launch_start_draws(p->opt.seed, l, n, L.x64, r.cs));
+    }
+    sc.info = L.info + 4 * l;
+    TSVD_TRY(launch_vec_normalize_f64_to_f32(L.x64, v, n, sc, r.cs));
+    const double rank_scale = l == 0 ? 1.0 : hsig2[0];
+    const int ovr = p->iters_override.empty() ? 0 : p->iters_override[l];
+    int32_t h[4] = {0, 0, 0, 0};
+    for (;;) {
+      TSVD_CUDA(cudaMemsetAsync(L.w, 0, (size_t)n * 4, r.cs));
+      TSVD_CUDA(cudaMemsetAsync(L.ss, 0, 8, r.cs));
+      TSVD_TRY(apply(v, L.w, L.ss, 1));
+      TSVD_TRY(launch_vec_deflate_step(n, L.Vr, k, L.sig2, l, v, L.w, vn, p->eps, p->opt.max_iter, ovr, rank_scale,
+                                       sc, 0, r.cs));
+      TSVD_CUDA(cudaMemcpyAsync(h, sc.info, 16, cudaMemcpyDeviceToHost, r.cs));
+      TSVD_CUDA(cudaStreamSynchronize(r.cs));
+      TSVD_TRY(after_sync());
+      if (h[1] == 2) break;  // rank: keep v (= v0 of this step)
+      std::swap(v, vn);
+      if (h[2]) break;
+    }
+    if (h[1] == 2) {
+      // v := v0 orthogonalised against earlier vectors, twice; sigma_l = 0
+      for (int pass = 0; pass < 2; ++pass) {
+        TSVD_TRY(launch_vec_deflate_step(n, L.Vr, k, L.sig2, l, v, L.w, vn, p->eps, p->opt.max_iter, ovr, rank_scale,
+                                         sc, 1, r.cs));
+        std::swap(v, vn);
+      }
+      TSVD_CUDA(cudaMemsetAsync(L.sig2 + l, 0, 8, r.cs));
+      flags |= TSVD_FLAG_RANK;
+    } else {
+      // sigma_l^2 = ||A v_l||^2 (Alg. 1 l.11-13)
+      TSVD_CUDA(cudaMemsetAsync(L.ss, 0, 8, r.cs));
+      TSVD_TRY(apply(v, L.w, L.ss, 0));
+      TSVD_CUDA(cudaMemcpyAsync(L.sig2 + l, L.ss, 8, cudaMemcpyDeviceToDevice, r.cs));
+      if (h[1] == 1) flags |= TSVD_FLAG_NOCONV;
+    }
+    TSVD_TRY(launch_vec_store_column(n, v, L.Vr, k, l, p->opt.sign_convention, sc, r.cs));
+    if (L.Vcol) TSVD_CUDA(cudaMemcpyAsync(L.Vcol + l * n, v, (size_t)n * 4, cudaMemcpyDeviceToDevice, r.cs));
+    TSVD_CUDA(cudaMemcpyAsync(V_out + l * n, v, (size_t)n * 4,
+                              host_out ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, r.cs));
+    if (host_out) r.d2h += (double)n * 4;
+    TSVD_CUDA(cudaMemcpyAsync(&hsig2[l], L.sig2 + l, 8, cudaMemcpyDeviceToHost, r.cs));
+    TSVD_CUDA(cudaStreamSynchronize(r.cs));
+    if (h[1] != 2) TSVD_TRY(after_sync());
+    apps += h[0];
+    if (rep && rep->iters) rep->iters[l] = h[0];
+  }
+  *flags_out |= flags;
+  *apps_out += apps;
+  return TSVD_OK;
+}
+
+// Dense t-SVD with an orthogonally batched Gram (Sec. V-C, Fig. 2c-d, Alg. 3):
+// every task (I, J), J <= I, streams the row range of panels J and I (device
+// pointers into A, or page-locked host rows copied into the panel ring) and
+// accumulates B_JI = A_J^T A_I in FP64 (triangular SYRK for J == I,
+// rectangular otherwise); the tile then goes to the device tile array or to
+// page-locked host memory.  The power phase applies G through the tiles
+// (explicit Hotelling correction, as for CSR), then U = A V Sigma^-1 over
+// row blocks.
+tsvd_status factor_dense_tiled(Run &r, float *U, double *sigma_out, float *V_out, tsvd_report *rep) {
+  tsvd_plan_s *p = r.p;
+  const tsvd_matrix *A = r.A;
+  const int64_t n = p->n, k = p->k, m = p->m, bs = p->tb, nb = p->n_panels;
+  const int prec = p->opt.precision;
+  const bool host_a = p->location == TSVD_HOST;
+  unsigned char *ws = r.ws;
+  float *v = reinterpret_cast<float *>(ws + p->o_v);
+  float *vn = reinterpret_cast<float *>(ws + p->o_vn);
+  float *w = reinterpret_cast<float *>(ws + p->o_w);
+  double *x64 = reinterpret_cast<double *>(ws + p->o_x64);
+  double *w64 = reinterpret_cast<double *>(ws + p->o_w64);
+  float *Vr = reinterpret_cast<float *>(ws + p->o_Vr);
+  float *Vc = reinterpret_cast<float *>(ws + p->o_Vc);
+  double *sig2 = reinterpret_cast<double *>(ws + p->o_sig2);
+  double *sigma = reinterpret_cast<double *>(ws + p->o_sigma);
+  int32_t *info = reinterpret_cast<int32_t *>(ws + p->o_info);
+  double *ss = reinterpret_cast<double *>(ws + p->o_flag + 64);
+  double *Gt = reinterpret_cast<double *>(ws + p->o_Gt);
+  void *tscr = ws + p->o_gscr;
+  double *dtiles = reinterpret_cast<double *>(ws + p->o_tiles);
+  const int64_t tstride = (int64_t)(p->b_tile / 8);  // doubles per device tile slot
+  VecScratch sc;
+  sc.part = reinterpret_cast<double *>(ws + p->o_vsc);
+  sc.coef = sc.part + (size_t)p->vec_grid * kVecPartStride;
+  sc.scal = sc.coef + 64 * 2;
+  sc.grid = p->vec_grid;
+  auto width = [&](int64_t P) { return std::min(bs, n - P * bs); };
+  if (p->tiles_host && !p->host_tiles)
+    TSVD_CUDA(cudaHostAlloc(reinterpret_cast<void **>(&p->host_tiles), (size_t)p->n_tasks * bs * bs * 8,
+                            cudaHostAllocPortable));
+
+  TSVD_CUDA(cudaEventRecord(p->ev_t[0], r.cs));
+  // ---- Gram, task by task
+  if (prec != TSVD_GRAM_FP32) TSVD_CUDA(cudaMemsetAsync(tscr, 0, 4, r.cs));
+  for (int64_t I = 0; I < nb; ++I) {
+    for (int64_t J = 0; J <= I; ++J) {
+      const int64_t nI = width(I), nJ = width(J);
+      const bool diag = I == J;
+      TSVD_CUDA(cudaMemsetAsync(Gt, 0, (size_t)bs * 2 * bs * 8, r.cs));
+      for (int64_t r0 = 0; r0 < m; r0 += p->pan_rows) {
+        const int64_t rows = std::min(p->pan_rows, m - r0);
+        const float *AJ, *AI;
+        int64_t ld;
+        int slot = -1;
+        if (!host_a) {
+          AJ = A->values + r0 * A->ld + J * bs;
+          AI = A->values + r0 * A->ld + I * bs;
+          ld = A->ld;
+        } else {
+          slot = (int)(r.chunk_seq++ % p->n_buffers);
+          float *dst = reinterpret_cast<float *>(ws + p->o_pan + p->b_pan * slot);
+          TSVD_CUDA(cudaStreamWaitEvent(p->copy_stream, p->ev_free[slot], 0));
+          TSVD_TRY(copy_event(r, true));
+          TSVD_CUDA(cudaEventRecord(p->ev_csplit, p->copy_stream));
+          TSVD_CUDA(cudaStreamWaitEvent(p->copy_stream2, p->ev_csplit, 0));
+          const float *src = A->values + r0 * A->ld;
+          TSVD_CUDA(cudaMemcpy2DAsync(dst, (size_t)2 * bs * 4, src + J * bs, (size_t)A->ld * 4, (size_t)nJ * 4,
+                                      (size_t)rows, cudaMemcpyHostToDevice, p->copy_stream));
+          if (!diag)
+            TSVD_CUDA(cudaMemcpy2DAsync(dst + bs, (size_t)2 * bs * 4, src + I * bs, (size_t)A->ld * 4,
+                                        (size_t)nI * 4, (size_t)rows, cudaMemcpyHostToDevice, p->copy_stream2));
+          TSVD_CUDA(cudaEventRecord(p->ev_cjoin, p->copy_stream2));
+          TSVD_CUDA(cudaStreamWaitEvent(p->copy_stream, p->ev_cjoin, 0));
+          TSVD_TRY(copy_event(r, false));
+          const double bytes = (double)rows * (nJ + (diag ? 0 : nI)) * 4;
+          if (p->opt.time_kernels) r.copy_bytes.push_back(bytes);
+          r.h2d += bytes;
+          TSVD_CUDA(cudaEventRecord(p->ev_ready[slot], p->copy_stream));
+          TSVD_CUDA(cudaStreamWaitEvent(r.cs, p->ev_ready[slot], 0));
+          AJ = dst;
+          AI = diag ? dst : dst + bs;
+          ld = 2 * bs;
+        }
+        if (diag)
+          TSVD_TRY(gram_dispatch(AI, rows, nI, ld, Gt, prec, tscr, p->b_gscr, r.cs, nullptr, nullptr, false));
+        else if (prec == TSVD_GRAM_FP32)
+          TSVD_TRY(launch_gram_simt_rect(AJ, AI, rows, nJ, nI, ld, Gt + bs, 2 * bs, r.cs));
+        else
+          TSVD_TRY(launch_gram_tc_rect(AJ, AI, rows, bs, nJ, nI, ld, Gt, prec, tscr, p->b_gscr, r.cs, false));
+        TSVD_TRY(release_slot(r, slot));
+      }
+      // the task's tile: nJ rows of nI, row stride bs
+      const int64_t t = I * (I + 1) / 2 + J;
+      const double *src = diag ? Gt : Gt + bs;
+      const size_t spitch = (size_t)(diag ? nI : 2 * bs) * 8;
+      if (p->tiles_host) {
+        TSVD_CUDA(cudaMemcpy2DAsync(p->host_tiles + t * bs * bs, (size_t)bs * 8, src, spitch, (size_t)nI * 8,
+                                    (size_t)nJ, cudaMemcpyDeviceToHost, r.cs));
+        r.d2h += (double)nI * nJ * 8;
+      } else {
+        TSVD_CUDA(cudaMemcpy2DAsync(dtiles + t * tstride, (size_t)bs * 8, src, spitch, (size_t)nI * 8, (size_t)nJ,
+                                    cudaMemcpyDeviceToDevice, r.cs));
+      }
+    }
+  }
+  int32_t gram_err = 0;
+  if (prec != TSVD_GRAM_FP32) TSVD_CUDA(cudaMemcpyAsync(&gram_err, tscr, 4, cudaMemcpyDeviceToHost, r.cs));
+  TSVD_CUDA(cudaEventRecord(p->ev_t[1], r.cs));
+
+  // ---- power phase: w = G v through the tiles
+  int64_t tseq = 0;
+  auto apply = [&](const float *vv, float *ww, double *s2, int) -> tsvd_status {
+    TSVD_CUDA(cudaMemsetAsync(w64, 0, (size_t)n * 8, r.cs));
+    for (int64_t I = 0; I < nb; ++I) {
+      for (int64_t J = 0; J <= I; ++J) {
+        const int64_t nI = width(I), nJ = width(J), t = I * (I + 1) / 2 + J;
+        const double *T = dtiles + t * tstride;
+        int slot = -1;
+        if (p->tiles_host) {
+          slot = (int)(tseq++ % p->n_buffers);
+          double *dst = dtiles + slot * tstride;
+          TSVD_CUDA(cudaStreamWaitEvent(p->copy_stream, p->ev_free[slot], 0));
+          TSVD_CUDA(cudaMemcpy2DAsync(dst, (size_t)bs * 8, p->host_tiles + t * bs * bs, (size_t)bs * 8,
+                                      (size_t)nI * 8, (size_t)nJ, cudaMemcpyHostToDevice, p->copy_stream));
+          r.h2d += (double)nI * nJ * 8;
+          TSVD_CUDA(cudaEventRecord(p->ev_ready[slot], p->copy_stream));
+          TSVD_CUDA(cudaStreamWaitEvent(r.cs, p->ev_ready[slot], 0));
+          T = dst;
+        }
+        TSVD_TRY(launch_tile_symv(T, bs, nJ, nI, vv + J * bs, vv + I * bs, w64 + J * bs, w64 + I * bs, I == J, r.cs));
+        TSVD_TRY(release_slot(r, slot));
+      }
+    }
+    return launch_tile_finish(n, vv, w64, ww, s2, r.cs);
+  };
+  ExplicitLoop L{v, vn, w, x64, ss, Vr, Vc, sig2, info, sc};
+  int flags = 0;
+  int64_t apps = 0;
+  TSVD_TRY(explicit_power(r, L, apply, []() { return TSVD_OK; }, V_out, &flags, &apps, rep));
+  TSVD_TRY(launch_sigma_from_sigma2(sig2, sigma, k, r.cs));
+  TSVD_CUDA(cudaEventRecord(p->ev_t[2], r.cs));
+
+  // ---- left vectors: U = A V Sigma^-1 over row blocks (their ring reuses the Gram region)
+  if (U) {
+    TSVD_CUDA(cudaEventRecord(p->ev_csplit, r.cs));
+    TSVD_CUDA(cudaStreamWaitEvent(p->copy_stream, p->ev_csplit, 0));
+    TSVD_TRY(left_pass_dense(r, Vc, sigma, U));
+  }
+  TSVD_CUDA(cudaEventRecord(p->ev_t[3], r.cs));
+  const bool host_out = p->opt.out_location == TSVD_HOST;
+  TSVD_CUDA(cudaMemcpyAsync(sigma_out, sigma, (size_t)k * 8, host_out ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice,
+                            r.cs));
+  if (host_out) r.d2h += (double)k * 8;
+  TSVD_CUDA(cudaStreamSynchronize(r.cs));
+  TSVD_CUDA(cudaStreamSynchronize(p->d2h_stream));
+  TSVD_CUDA(cudaStreamSynchronize(p->copy_stream));
+  float t01 = 0, t12 = 0, t23 = 0;
+  TSVD_CUDA(cudaEventElapsedTime(&t01, p->ev_t[0], p->ev_t[1]));
+  TSVD_CUDA(cudaEventElapsedTime(&t12, p->ev_t[1], p->ev_t[2]));
+  TSVD_CUDA(cudaEventElapsedTime(&t23, p->ev_t[2], p->ev_t[3]));
+  if (gram_err) flags |= TSVD_FLAG_TIMEOUT;
+  if (host_out) {
+    for (int64_t l = 1; l < k; ++l)
+      if (sigma_out[l] > sigma_out[l - 1]) flags |= TSVD_FLAG_NONMONOTONE;
+  }
+  if (rep) {
+    rep->gram_ms = t01;
+    rep->power_ms = t12;
+    rep->left_ms = t23;
+    rep->total_ms = (double)t01 + t12 + t23;
+    rep->applications = apps;
+    rep->flags |= flags;
+    rep->gram_panels = (int32_t)nb;
+    rep->tiles_on_host = p->tiles_host ? 1 : 0;
+  }
+  if (flags & TSVD_FLAG_TIMEOUT) return TSVD_ETIMEDOUT;
+  if (flags & TSVD_FLAG_RANK) return TSVD_ERANK;
+  if (flags & TSVD_FLAG_NOCONV) return TSVD_ENOCONV;
+  return TSVD_OK;
+}
+
 tsvd_status factor_csr(Run &r, float *U, double *sigma_out, float *V_out, tsvd_report *rep) {
   tsvd_plan_s *p = r.p;
   const tsvd_matrix *A = r.A;
@@ -1039,64 +1431,13 @@ tsvd_status factor_csr(Run &r, float *U, double *sigma_out, float *V_out, tsvd_r
   }
   TSVD_CUDA(cudaEventRecord(p->ev_t[1], r.cs));
 
-  std::vector<double> hsig2((size_t)k, 0.0);
-  std::vector<int32_t> hinfo((size_t)k * 4, 0);
-  TSVD_CUDA(cudaMemsetAsync(info, 0, (size_t)k * 16, r.cs));
+  ExplicitLoop L{v, vn, w, x64, ss, Vr, nullptr, sig2, info, sc};
   int flags = 0;
   int64_t apps = 0;
   const bool host_out = p->opt.out_location == TSVD_HOST;
-  for (int64_t l = 0; l < k; ++l) {
-    // start vector v0 = x / ||x||
-    if (!p->start_draws.empty()) {
-      TSVD_CUDA(cudaMemcpyAsync(x64, p->start_draws.data() + l * n, (size_t)n * 8, cudaMemcpyHostToDevice, r.cs));
-      r.h2d += (double)n * 8;
-    } else {
-      TSVD_TRY(launch_start_draws(p->opt.seed, l, n, x64, r.cs));
-    }
-    sc.info = info + 4 * l;
-    TSVD_TRY(launch_vec_normalize_f64_to_f32(x64, v, n, sc, r.cs));
-    const double rank_scale = l == 0 ? 1.0 : hsig2[0];
-    const int ovr = p->iters_override.empty() ? 0 : p->iters_override[l];
-    int32_t h[4] = {0, 0, 0, 0};
-    for (;;) {
-      TSVD_CUDA(cudaMemsetAsync(w, 0, (size_t)n * 4, r.cs));
-      TSVD_CUDA(cudaMemsetAsync(ss, 0, 8, r.cs));
-      TSVD_TRY(csr_apply(r, bnd, v, w, ss, 1));
-      TSVD_TRY(launch_vec_deflate_step(n, Vr, k, sig2, l, v, w, vn, p->eps, p->opt.max_iter, ovr, rank_scale,
-                                       sc, 0, r.cs));
-      TSVD_CUDA(cudaMemcpyAsync(h, sc.info, 16, cudaMemcpyDeviceToHost, r.cs));
-      TSVD_CUDA(cudaStreamSynchronize(r.cs));
-      TSVD_TRY(csr_kernel_time(r));
-      if (h[1] == 2) break;  // rank: keep v (= v0 of this step)
-      std::swap(v, vn);
-      if (h[2]) break;
-    }
-    if (h[1] == 2) {
-      // v := v0 orthogonalised against earlier vectors, twice; sigma_l = 0
-      for (int pass = 0; pass < 2; ++pass) {
-        TSVD_TRY(launch_vec_deflate_step(n, Vr, k, sig2, l, v, w, vn, p->eps, p->opt.max_iter, ovr, rank_scale,
-                                         sc, 1, r.cs));
-        std::swap(v, vn);
-      }
-      TSVD_CUDA(cudaMemsetAsync(sig2 + l, 0, 8, r.cs));
-      flags |= TSVD_FLAG_RANK;
-    } else {
-      // sigma_l^2 = ||A v_l||^2 (Alg. 1 l.11-13)
-      TSVD_CUDA(cudaMemsetAsync(ss, 0, 8, r.cs));
-      TSVD_TRY(csr_apply(r, bnd, v, w, ss, 0));
-      TSVD_CUDA(cudaMemcpyAsync(sig2 + l, ss, 8, cudaMemcpyDeviceToDevice, r.cs));
-      if (h[1] == 1) flags |= TSVD_FLAG_NOCONV;
-    }
-    TSVD_TRY(launch_vec_store_column(n, v, Vr, k, l, p->opt.sign_convention, sc, r.cs));
-    TSVD_CUDA(cudaMemcpyAsync(V_out + l * n, v, (size_t)n * 4,
-                              host_out ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, r.cs));
-    if (host_out) r.d2h += (double)n * 4;
-    TSVD_CUDA(cudaMemcpyAsync(&hsig2[l], sig2 + l, 8, cudaMemcpyDeviceToHost, r.cs));
-    TSVD_CUDA(cudaStreamSynchronize(r.cs));
-    if (h[1] != 2) TSVD_TRY(csr_kernel_time(r));
-    apps += h[0];
-    if (rep && rep->iters) rep->iters[l] = h[0];
-  }
+  TSVD_TRY(explicit_power(
+      r, L, [&](const float *vv, float *ww, double *s2, int scatter) { return csr_apply(r, bnd, vv, ww, s2, scatter); },
+      [&]() { return csr_kernel_time(r); }, V_out, &flags, &apps, rep));
   TSVD_TRY(launch_sigma_from_sigma2(sig2, sigma, k, r.cs));
   TSVD_CUDA(cudaEventRecord(p->ev_t[2], r.cs));
   if (U) {
@@ -1189,8 +1530,9 @@ tsvd_status tsvd_factor(tsvd_plan_t plan, const tsvd_matrix *A, void *workspace,
     report->n_blocks = (int32_t)p->n_chunks;
     report->ring_slots = p->mode == MODE_STREAM ? p->n_buffers : 0;
   }
-  tsvd_status st = p->kind == TSVD_DENSE_F32_ROWMAJOR ? factor_dense(r, U, sigma, V, report)
-                                                      : factor_csr(r, U, sigma, V, report);
+  tsvd_status st = p->kind != TSVD_DENSE_F32_ROWMAJOR ? factor_csr(r, U, sigma, V, report)
+                   : p->tiled                          ? factor_dense_tiled(r, U, sigma, V, report)
+                                                       : factor_dense(r, U, sigma, V, report);
   if (report) {
     report->h2d_bytes = r.h2d;
     report->d2h_bytes = r.d2h;

@@ -154,6 +154,15 @@ __device__ __forceinline__ bool grid_barrier(unsigned *bar, int *err) {
 tsvd_status launch_gram_simt(const float *A, int64_t rows, int64_t n, int64_t ld, double *G,
                              cudaStream_t stream, cudaEvent_t ev0 = nullptr, cudaEvent_t ev1 = nullptr);
 size_t gram_tc_scratch_bytes(int64_t rows, int64_t n, int precision);
+// One task of the orthogonal batching (Sec. V-C): G[a][bs + b] += sum_r AJ[r][a] AI[r][b]
+// for a < nJ, b < nI (panel J against panel I, both rows x n_* with stride ld);
+// G is bs x 2 bs, row stride 2 bs.  Scratch: gram_tc_scratch_bytes(rows, 2 bs, precision).
+tsvd_status launch_gram_tc_rect(const float *AJ, const float *AI, int64_t rows, int64_t bs, int64_t nJ, int64_t nI,
+                                int64_t ld, double *G, int precision, void *scratch, size_t scratch_bytes,
+                                cudaStream_t stream, bool reset_status);
+// The same on CUDA cores (FP32): G[a][b] += sum_r AJ[r][a] AI[r][b], row stride ldg.
+tsvd_status launch_gram_simt_rect(const float *AJ, const float *AI, int64_t rows, int64_t nJ, int64_t nI, int64_t ld,
+                                  double *G, int64_t ldg, cudaStream_t stream);
 // reset_status: zero the scratch's status word first (a caller that runs many
 // chunks zeroes it once, so a timeout in any chunk stays visible)
 tsvd_status launch_gram_tc(const float *A, int64_t rows, int64_t n, int64_t ld, double *G,
@@ -166,6 +175,14 @@ tsvd_status launch_gram_tc_prep(const float *A, int64_t rows, int64_t n, int64_t
 tsvd_status launch_gram_tc_syrk(int64_t rows, int64_t n, double *G, int precision, void *scratch,
                                 size_t scratch_bytes, cudaStream_t stream, cudaEvent_t ev0 = nullptr,
                                 cudaEvent_t ev1 = nullptr, bool reset_status = true);
+
+// Tiled Gram operator (orthogonal batching): w_J += T v_I and, for an
+// off-diagonal tile, w_I += T^T v_J (T: nJ x nI FP64, row stride ldt; a
+// diagonal tile holds its upper triangle).  Then w = FP32(w64), ss += v . w64.
+tsvd_status launch_tile_symv(const double *T, int64_t ldt, int64_t nJ, int64_t nI, const float *vJ, const float *vI,
+                             double *wJ, double *wI, bool diag, cudaStream_t stream);
+tsvd_status launch_tile_finish(int64_t n, const float *v, const double *w64, float *w, double *ss,
+                               cudaStream_t stream);
 
 size_t power_scratch_bytes(int64_t n, int64_t l);
 tsvd_status launch_power_dense(int64_t n, const float *G32, const double *G64, const double *V64,

@@ -10,6 +10,8 @@
 // FP64 result with one atomic per element, so G stays exact to FP64 across
 // slices and blocks.  Element G[i][j] (i >= j) is stored at row j, column i
 // of the n x n FP64 buffer (upper-triangle storage).
+#include <algorithm>
+
 #include "common.cuh"
 
 namespace tsvd {
@@ -38,11 +40,20 @@ __device__ __forceinline__ float4 load4(const float *row, int64_t c, int64_t n, 
   return r;
 }
 
+// Triangular mode (nbj == 0): AI == AJ == A, tiles of the lower block
+// triangle.  Rectangular mode (nbj > 0, a task of the orthogonal batching):
+// G[gj][gi] += sum_r AJ[r][gj] AI[r][gi] for every gj < nJ, gi < nI, tiles
+// enumerated row by row over ceil(nJ / 128) J blocks.
 __global__ void __launch_bounds__(NT, 2)
-syrk_simt_kernel(const float *__restrict__ A, int64_t rows, int64_t n, int64_t ld,
-                 double *__restrict__ G, int64_t rows_per_split, int vec) {
+syrk_simt_kernel(const float *__restrict__ AI, const float *__restrict__ AJ, int64_t rows, int64_t nI, int64_t nJ,
+                 int64_t ld, double *__restrict__ G, int64_t ldg, int nbj, int64_t rows_per_split, int vec) {
   int bi, bj;
-  tile_of(blockIdx.x, bi, bj);
+  if (nbj > 0) {
+    bi = (int)(blockIdx.x / nbj);
+    bj = (int)(blockIdx.x % nbj);
+  } else {
+    tile_of(blockIdx.x, bi, bj);
+  }
   const int64_t I0 = (int64_t)bi * BM, J0 = (int64_t)bj * BM;
   const int64_t k0 = (int64_t)blockIdx.y * rows_per_split;
   const int64_t k1 = min(rows, k0 + rows_per_split);
@@ -55,7 +66,7 @@ syrk_simt_kernel(const float *__restrict__ A, int64_t rows, int64_t n, int64_t l
   const int tx = tid & 15, ty = tid >> 4;
   const int lr = tid >> 5;         // row of the step this thread loads
   const int lc = (tid & 31) * 4;   // first column it loads
-  const bool diag = (bi == bj);
+  const bool diag = nbj == 0 && bi == bj;
 
   float acc[8][8];
 #pragma unroll
@@ -67,9 +78,8 @@ syrk_simt_kernel(const float *__restrict__ A, int64_t rows, int64_t n, int64_t l
   auto fetch = [&](int64_t kk) {
     const int64_t r = kk + lr;
     if (r < k1) {
-      const float *row = A + r * ld;
-      ra = load4(row, I0 + lc, n, vec);
-      rb = diag ? ra : load4(row, J0 + lc, n, vec);
+      ra = load4(AI + r * ld, I0 + lc, nI, vec);
+      rb = diag ? ra : load4(AJ + r * ld, J0 + lc, nJ, vec);
     } else {
       ra = rb = make_float4(0.f, 0.f, 0.f, 0.f);
     }
@@ -108,17 +118,33 @@ syrk_simt_kernel(const float *__restrict__ A, int64_t rows, int64_t n, int64_t l
     cur ^= 1;
   }
 
-  // acc[i][j] = sum_r A[r][gi] A[r][gj]; store G[gi][gj] at row gj, column gi
+  // acc[i][j] = sum_r AI[r][gi] AJ[r][gj]; store G[gi][gj] at row gj, column gi
+  // (triangular mode: only gi >= gj)
 #pragma unroll
   for (int j = 0; j < 8; ++j) {
     const int64_t gj = J0 + (j < 4 ? ty * 4 + j : 64 + ty * 4 + (j - 4));
-    if (gj >= n) continue;
+    if (gj >= nJ) continue;
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
       const int64_t gi = I0 + (i < 4 ? tx * 4 + i : 64 + tx * 4 + (i - 4));
-      if (gi < n && gi >= gj) atomicAdd(G + gj * n + gi, (double)acc[i][j]);
+      if (gi < nI && (nbj > 0 || gi >= gj)) atomicAdd(G + gj * ldg + gi, (double)acc[i][j]);
     }
   }
+}
+
+int64_t simt_splits(int64_t rows, int64_t tiles, int sms, int64_t *per_out) {
+  // enough CTAs for ~4 waves at 2 CTAs/SM, but at least 1024 rows per slice
+  const int64_t want = 8LL * sms;
+  int64_t splits = std::max<int64_t>(1, ceil_div(want, tiles));
+  int64_t per = round_up(ceil_div(rows, splits), BK);
+  if (per < 1024) per = round_up(std::min<int64_t>(rows, 1024), BK);
+  splits = ceil_div(rows, per);
+  if (splits > 65535) {
+    per = round_up(ceil_div(rows, 65535), BK);
+    splits = ceil_div(rows, per);
+  }
+  *per_out = per;
+  return splits;
 }
 
 }  // namespace
@@ -130,22 +156,32 @@ tsvd_status launch_gram_simt(const float *A, int64_t rows, int64_t n, int64_t ld
   TSVD_TRY(device_info(&di));
   const int64_t nb = ceil_div(n, BM);
   const int64_t tiles = nb * (nb + 1) / 2;
-  // enough CTAs for ~4 waves at 2 CTAs/SM, but at least 1024 rows per slice
-  const int64_t want = 8LL * di.sms;
-  int64_t splits = std::max<int64_t>(1, ceil_div(want, tiles));
-  int64_t per = round_up(ceil_div(rows, splits), BK);
-  if (per < 1024) per = round_up(std::min<int64_t>(rows, 1024), BK);
-  splits = ceil_div(rows, per);
-  if (splits > 65535) {
-    per = round_up(ceil_div(rows, 65535), BK);
-    splits = ceil_div(rows, per);
-  }
+  int64_t per = 0;
+  const int64_t splits = simt_splits(rows, tiles, di.sms, &per);
   const bool vec = (ld % 4 == 0) && ((reinterpret_cast<uintptr_t>(A) & 15) == 0);
   dim3 grid((unsigned)tiles, (unsigned)splits);
   if (ev0) TSVD_CUDA(cudaEventRecord(ev0, stream));
-  syrk_simt_kernel<<<grid, NT, 0, stream>>>(A, rows, n, ld, G, per, vec ? 1 : 0);
+  syrk_simt_kernel<<<grid, NT, 0, stream>>>(A, A, rows, n, n, ld, G, n, 0, per, vec ? 1 : 0);
   TSVD_LAUNCHED();
   if (ev1) TSVD_CUDA(cudaEventRecord(ev1, stream));
+  return TSVD_OK;
+}
+
+tsvd_status launch_gram_simt_rect(const float *AJ, const float *AI, int64_t rows, int64_t nJ, int64_t nI, int64_t ld,
+                                  double *G, int64_t ldg, cudaStream_t stream) {
+  if (rows <= 0 || nJ <= 0 || nI <= 0) return TSVD_OK;
+  DeviceInfo di;
+  TSVD_TRY(device_info(&di));
+  const int64_t nbi = ceil_div(nI, BM), nbj = ceil_div(nJ, BM);
+  const int64_t tiles = nbi * nbj;
+  if (tiles > 0x7fffffffLL) return TSVD_EUNSUPPORTED;
+  int64_t per = 0;
+  const int64_t splits = simt_splits(rows, tiles, di.sms, &per);
+  const bool vec = (ld % 4 == 0) && ((reinterpret_cast<uintptr_t>(AI) & 15) == 0) &&
+                   ((reinterpret_cast<uintptr_t>(AJ) & 15) == 0);
+  dim3 grid((unsigned)tiles, (unsigned)splits);
+  syrk_simt_kernel<<<grid, NT, 0, stream>>>(AI, AJ, rows, nI, nJ, ld, G, ldg, (int)nbj, per, vec ? 1 : 0);
+  TSVD_LAUNCHED();
   return TSVD_OK;
 }
 

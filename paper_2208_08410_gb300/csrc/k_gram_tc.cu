@@ -257,6 +257,9 @@ __global__ void __launch_bounds__(256) prep_kernel(const float *__restrict__ A, 
 // ---------------------------------------------------------------- syrk kernel
 struct TcArgs {
   double *G;
+  int64_t ldg;        // row stride of G
+  int rect_bi0;       // rectangular mode (rect_nbj > 0): I blocks rect_bi0 + t / rect_nbj,
+  int rect_nbj;       // J blocks t % rect_nbj, every element of those tiles stored
   int64_t n;
   int64_t Kp;         // padded K (rows) of At
   int64_t ksplit;     // rows per work unit (multiple of stage rows * seg_stages)
@@ -281,6 +284,15 @@ __device__ __forceinline__ void tc_tile(int t, int &bi, int &bj) {
   const long long cb = (lo & 1) ? (q + 1) * (q + 1) : q * (q + 1);
   bi = lo;
   bj = (int)(t - cb);
+}
+
+__device__ __forceinline__ void unit_tile(const TcArgs &a, int t, int &bi, int &bj) {
+  if (a.rect_nbj > 0) {
+    bi = a.rect_bi0 + t / a.rect_nbj;
+    bj = t % a.rect_nbj;
+  } else {
+    tc_tile(t, bi, bj);
+  }
 }
 
 // The tensor core adds each MMA into the FP32 TMEM accumulator with a
@@ -335,7 +347,7 @@ syrk_tc_kernel(const __grid_constant__ CUtensorMap map_hi, const __grid_constant
       for (int u = blockIdx.x; u < units && ok; u += gridDim.x) {
         const int t = u % a.n_tiles, sp = u / a.n_tiles;
         int bi, bj;
-        tc_tile(t, bi, bj);
+        unit_tile(a, t, bi, bj);
         const int64_t k0 = (int64_t)sp * a.ksplit;
         const int64_t k1 = min(a.Kp, k0 + a.ksplit);
         for (int64_t kk = k0; kk < k1; kk += TK, ++it) {
@@ -419,7 +431,7 @@ syrk_tc_kernel(const __grid_constant__ CUtensorMap map_hi, const __grid_constant
     for (int u = blockIdx.x; u < units && ok; u += gridDim.x) {
       const int t = u % a.n_tiles, sp = u / a.n_tiles;
       int bi, bj;
-      tc_tile(t, bi, bj);
+      unit_tile(a, t, bi, bj);
       const int64_t k0 = (int64_t)sp * a.ksplit;
       const int64_t k1 = min(a.Kp, k0 + a.ksplit);
       for (int64_t g0 = k0; g0 < k1; g0 += seg_rows, ++sc) {
@@ -436,10 +448,13 @@ syrk_tc_kernel(const __grid_constant__ CUtensorMap map_hi, const __grid_constant
       if (!ok) break;
       const int64_t gi = (int64_t)bi * TM + row;
       const int64_t jbase = (int64_t)bj * TN + h * TC_EPI_COLS;
-      // columns gj <= gi of this row (the lower triangle of G), stored at G[gj][gi]
-      const int jlim = gi < a.n ? (int)min((int64_t)TC_EPI_COLS, gi - jbase + 1) : 0;
-      double *gp = a.G + jbase * a.n + gi;
-      const int64_t stride = a.n;
+      // columns gj <= gi of this row (the lower triangle of G), stored at G[gj][gi];
+      // in rectangular mode every column of the tile
+      const int jlim = gi >= a.n ? 0
+                       : a.rect_nbj > 0 ? TC_EPI_COLS
+                                        : (int)min((int64_t)TC_EPI_COLS, gi - jbase + 1);
+      double *gp = a.G + jbase * a.ldg + gi;
+      const int64_t stride = a.ldg;
 #pragma unroll
       for (int j = 0; j < TC_EPI_COLS; ++j) {
         if (j < jlim) red_add_f64_from_f32(gp, accr[j]);
@@ -567,6 +582,64 @@ tsvd_status tc_layout(int64_t rows, int64_t n, int precision, void *scratch, siz
 
 }  // namespace
 
+namespace {
+
+// transpose + rounding (+ split) of A (rows x n, stride ld) into rows [0, n)
+// of the At parts at hi / lo; Kp is a multiple of 32, the prep row tile
+tsvd_status prep_raw(const float *A, int64_t rows, int64_t n, int64_t ld, int precision, void *hi, void *lo,
+                     int64_t Kp, cudaStream_t stream) {
+  const int64_t strips = (Kp / 32) * ceil_div(n, 128);
+  const int64_t grid = std::min<int64_t>(strips, 0x7fffffffLL);
+  dim3 block(32, 8);
+  if (precision == TSVD_GRAM_BF16X3)
+    prep_kernel<TSVD_GRAM_BF16X3><<<(unsigned)grid, block, 0, stream>>>(A, rows, n, ld, hi, lo, Kp);
+  else if (precision == TSVD_GRAM_TF32X3)
+    prep_kernel<TSVD_GRAM_TF32X3><<<(unsigned)grid, block, 0, stream>>>(A, rows, n, ld, hi, lo, Kp);
+  else
+    prep_kernel<TSVD_GRAM_TF32><<<(unsigned)grid, block, 0, stream>>>(A, rows, n, ld, hi, lo, Kp);
+  TSVD_LAUNCHED();
+  return TSVD_OK;
+}
+
+// K slices: about 8 units per SM balance the persistent grid; fewer, longer
+// units keep the FP64 reductions into G (one 128 x 256 tile per unit) small,
+// so slices are never shorter than 4096 rows
+void tc_ksplit(TcArgs &a, int precision, int sms) {
+  const int64_t quantum = (int64_t)stage_rows(precision) * a.seg_stages;
+  const int64_t want_units = 8LL * sms;
+  int64_t splits = std::max<int64_t>(1, ceil_div(want_units, a.n_tiles));
+  int64_t ks = round_up(ceil_div(a.Kp, splits), quantum);
+  ks = std::max<int64_t>(ks, std::min<int64_t>(round_up(4096, quantum), round_up(a.Kp, quantum)));
+  const char *e = getenv("TSVD_TC_KSPLIT");
+  if (e) ks = std::max<int64_t>(quantum, round_up(atoll(e), quantum));
+  a.ksplit = ks;
+  a.n_splits = (int)ceil_div(a.Kp, ks);
+}
+
+tsvd_status run_syrk(const TcLayout &L, const TcArgs &a0, int precision, int sms, cudaStream_t stream,
+                     cudaEvent_t ev0, cudaEvent_t ev1, bool reset_status) {
+  TcArgs a = a0;
+  CUtensorMap mh, ml;
+  TSVD_TRY(make_map(&mh, L.hi, a.n, a.Kp, precision));
+  TSVD_TRY(make_map(&ml, L.lo, a.n, a.Kp, precision));
+  tc_ksplit(a, precision, sms);
+  a.err = L.err;
+  if (reset_status) TSVD_CUDA(cudaMemsetAsync(L.err, 0, 4, stream));
+  const int64_t units = (int64_t)a.n_tiles * a.n_splits;
+  const int grid = (int)std::min<int64_t>(units, sms);
+  if (ev0) TSVD_CUDA(cudaEventRecord(ev0, stream));
+  if (precision == TSVD_GRAM_TF32)
+    TSVD_TRY(launch_syrk<TSVD_GRAM_TF32>(mh, ml, a, grid, stream));
+  else if (precision == TSVD_GRAM_TF32X3)
+    TSVD_TRY(launch_syrk<TSVD_GRAM_TF32X3>(mh, ml, a, grid, stream));
+  else
+    TSVD_TRY(launch_syrk<TSVD_GRAM_BF16X3>(mh, ml, a, grid, stream));
+  if (ev1) TSVD_CUDA(cudaEventRecord(ev1, stream));
+  return TSVD_OK;
+}
+
+}  // namespace
+
 tsvd_status launch_gram_tc_prep(const float *A, int64_t rows, int64_t n, int64_t ld, int precision, void *scratch,
                                 size_t scratch_bytes, cudaStream_t stream) {
   if (rows <= 0) return TSVD_OK;
@@ -575,18 +648,7 @@ tsvd_status launch_gram_tc_prep(const float *A, int64_t rows, int64_t n, int64_t
   if (di.cc_major != 10) return TSVD_EUNSUPPORTED;  // tcgen05 needs the sm_100 family
   TcLayout L;
   TSVD_TRY(tc_layout(rows, n, precision, scratch, scratch_bytes, &L));
-  // transpose + rounding (+ split); Kp is a multiple of 32, the prep row tile
-  const int64_t strips = (L.Kp / 32) * ceil_div(n, 128);
-  const int64_t grid = std::min<int64_t>(strips, 0x7fffffffLL);
-  dim3 block(32, 8);
-  if (precision == TSVD_GRAM_BF16X3)
-    prep_kernel<TSVD_GRAM_BF16X3><<<(unsigned)grid, block, 0, stream>>>(A, rows, n, ld, L.hi, L.lo, L.Kp);
-  else if (precision == TSVD_GRAM_TF32X3)
-    prep_kernel<TSVD_GRAM_TF32X3><<<(unsigned)grid, block, 0, stream>>>(A, rows, n, ld, L.hi, L.lo, L.Kp);
-  else
-    prep_kernel<TSVD_GRAM_TF32><<<(unsigned)grid, block, 0, stream>>>(A, rows, n, ld, L.hi, L.lo, L.Kp);
-  TSVD_LAUNCHED();
-  return TSVD_OK;
+  return prep_raw(A, rows, n, ld, precision, L.hi, L.lo, L.Kp, stream);
 }
 
 tsvd_status launch_gram_tc_syrk(int64_t rows, int64_t n, double *G, int precision, void *scratch, size_t scratch_bytes,
@@ -597,48 +659,49 @@ tsvd_status launch_gram_tc_syrk(int64_t rows, int64_t n, double *G, int precisio
   if (di.cc_major != 10) return TSVD_EUNSUPPORTED;
   TcLayout L;
   TSVD_TRY(tc_layout(rows, n, precision, scratch, scratch_bytes, &L));
-  const int64_t Kp = L.Kp;
   // persistent tcgen05 SYRK over the lower-triangle tiles
-  CUtensorMap mh, ml;
-  TSVD_TRY(make_map(&mh, L.hi, n, Kp, precision));
-  TSVD_TRY(make_map(&ml, L.lo, n, Kp, precision));
-  TcArgs a;
+  TcArgs a{};
   a.G = G;
+  a.ldg = n;
   a.n = n;
-  a.Kp = Kp;
+  a.Kp = L.Kp;
   a.seg_stages = tc_seg_stages(precision);
   a.n_iblk = (int)ceil_div(n, TM);
   {
     const int64_t q = (a.n_iblk) >> 1;  // tiles = C(n_iblk)
     a.n_tiles = (int)((a.n_iblk & 1) ? (q + 1) * (q + 1) : q * (q + 1));
   }
-  {
-    // K slices: about 8 units per SM balance the persistent grid; fewer,
-    // longer units keep the FP64 reductions into G (one 128 x 256 tile per
-    // unit) small, so slices are never shorter than 4096 rows
-    const int64_t quantum = (int64_t)stage_rows(precision) * a.seg_stages;
-    const int64_t want_units = 8LL * di.sms;
-    int64_t splits = std::max<int64_t>(1, ceil_div(want_units, a.n_tiles));
-    int64_t ks = round_up(ceil_div(Kp, splits), quantum);
-    ks = std::max<int64_t>(ks, std::min<int64_t>(round_up(4096, quantum), round_up(Kp, quantum)));
-    const char *e = getenv("TSVD_TC_KSPLIT");
-    if (e) ks = std::max<int64_t>(quantum, round_up(atoll(e), quantum));
-    a.ksplit = ks;
-    a.n_splits = (int)ceil_div(Kp, ks);
-  }
-  a.err = L.err;
-  if (reset_status) TSVD_CUDA(cudaMemsetAsync(L.err, 0, 4, stream));
-  const int64_t units = (int64_t)a.n_tiles * a.n_splits;
-  const int grid = (int)std::min<int64_t>(units, di.sms);
-  if (ev0) TSVD_CUDA(cudaEventRecord(ev0, stream));
-  if (precision == TSVD_GRAM_TF32)
-    TSVD_TRY(launch_syrk<TSVD_GRAM_TF32>(mh, ml, a, grid, stream));
-  else if (precision == TSVD_GRAM_TF32X3)
-    TSVD_TRY(launch_syrk<TSVD_GRAM_TF32X3>(mh, ml, a, grid, stream));
-  else
-    TSVD_TRY(launch_syrk<TSVD_GRAM_BF16X3>(mh, ml, a, grid, stream));
-  if (ev1) TSVD_CUDA(cudaEventRecord(ev1, stream));
-  return TSVD_OK;
+  return run_syrk(L, a, precision, di.sms, stream, ev0, ev1, reset_status);
+}
+
+tsvd_status launch_gram_tc_rect(const float *AJ, const float *AI, int64_t rows, int64_t bs, int64_t nJ, int64_t nI,
+                                int64_t ld, double *G, int precision, void *scratch, size_t scratch_bytes,
+                                cudaStream_t stream, bool reset_status) {
+  if (rows <= 0 || nJ <= 0 || nI <= 0) return TSVD_OK;
+  if (bs % TN != 0 || nJ > bs || nI > bs) return TSVD_EINVAL;
+  DeviceInfo di;
+  TSVD_TRY(device_info(&di));
+  if (di.cc_major != 10) return TSVD_EUNSUPPORTED;
+  TcLayout L;
+  TSVD_TRY(tc_layout(rows, 2 * bs, precision, scratch, scratch_bytes, &L));
+  // At rows [0, nJ): panel J; rows [bs, bs + nI): panel I.  Rows [nJ, bs) and
+  // [bs + nI, 2 bs) keep whatever they held: the tiles that read them only
+  // produce entries outside the J x I block, which the caller ignores
+  const int64_t off = bs * L.Kp * tc_elem(precision);
+  TSVD_TRY(prep_raw(AJ, rows, nJ, ld, precision, L.hi, L.lo, L.Kp, stream));
+  TSVD_TRY(prep_raw(AI, rows, nI, ld, precision, static_cast<unsigned char *>(L.hi) + off,
+                    static_cast<unsigned char *>(L.lo) + off, L.Kp, stream));
+  TcArgs a{};
+  a.G = G;
+  a.ldg = 2 * bs;
+  a.n = 2 * bs;
+  a.Kp = L.Kp;
+  a.seg_stages = tc_seg_stages(precision);
+  a.n_iblk = (int)ceil_div(2 * bs, TM);
+  a.rect_bi0 = (int)(bs / TM);
+  a.rect_nbj = (int)ceil_div(nJ, TN);
+  a.n_tiles = (int)ceil_div(nI, TM) * a.rect_nbj;
+  return run_syrk(L, a, precision, di.sms, stream, nullptr, nullptr, reset_status);
 }
 
 tsvd_status launch_gram_tc(const float *A, int64_t rows, int64_t n, int64_t ld, double *G, int precision,

@@ -104,6 +104,33 @@ def test_plan_validation_dense(lib):
     assert _plan(tall, 32, 1e-6, _opts(power_kernel=B.TSVD_POWER_CLUSTER))[0] == B.TSVD_OK
 
 
+def test_plan_orthogonal_batching(lib):
+    """Orthogonal batching: forced by gram_tile (a multiple of 256), or taken
+    when the whole Gram matrix does not fit the budget; the workspace stays
+    within the budget."""
+    d, keep = _dense_desc(6000, 1000)
+    assert _plan(d, 8, 1e-6, _opts(gram_tile=256))[0] == B.TSVD_OK
+    assert _plan(d, 8, 1e-6, _opts(gram_tile=512, precision=B.TSVD_GRAM_TF32X3))[0] == B.TSVD_OK
+    for bad in (100, 255, -256):
+        assert _plan(d, 8, 1e-6, _opts(gram_tile=bad))[0] == B.TSVD_EINVAL
+    # n = 4096: G64 + G32 alone are 201 MB; 64 MB forces the tiles, 2 MB is too little for anything
+    big, keep2 = _dense_desc(8, 4096, arr=np.zeros((1, 1), dtype=np.float32))
+    big.m = 100000
+    st, ws = _plan(big, 16, 1e-6, _opts(device_budget=64 << 20))
+    assert st == B.TSVD_OK and ws <= 64 << 20
+    st, ws = _plan(big, 16, 1e-6, _opts(device_budget=64 << 20, precision=B.TSVD_GRAM_BF16X3))
+    assert st == B.TSVD_OK and ws <= 64 << 20
+    assert _plan(big, 16, 1e-6, _opts(device_budget=2 << 20))[0] == B.TSVD_EBUDGET
+    # CSR takes no column panels
+    c = B.tsvd_matrix()
+    rp = np.array([0, 1, 2], dtype=np.int64)
+    ci = np.array([0, 1], dtype=np.int32)
+    va = np.ones(2, dtype=np.float32)
+    c.kind, c.location, c.m, c.n, c.nnz = B.TSVD_CSR_F32_I32_I64, B.TSVD_HOST, 2, 2, 2
+    c.values, c.row_ptr, c.col_idx = va.ctypes.data, rp.ctypes.data, ci.ctypes.data
+    assert _plan(c, 1, 1e-6, _opts(gram_tile=256))[0] == B.TSVD_EINVAL
+
+
 def test_plan_budget_and_streaming_layout(lib):
     m, n, k = 1 << 16, 512, 8
     d, keep = _dense_desc(m, n)

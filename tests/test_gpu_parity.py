@@ -359,6 +359,37 @@ def test_tsvd_cluster_power_builtin_draws_and_own_convergence():
     assert np.max(np.abs(r.sigma - o.sigma) / o.sigma) <= 1e-5
 
 
+# orthogonal batching: n, panel width, precision, where A lives, device budget (0 = none: tiles
+# resident on the device; 4 MB: the tiles go to page-locked host memory and stream back)
+TILED_CASES = [
+    (1000, 256, B.TSVD_GRAM_FP32, "device", 0), (1000, 256, B.TSVD_GRAM_TF32X3, "device", 0),
+    (1300, 512, B.TSVD_GRAM_TF32X3, "host", 0), (1300, 512, B.TSVD_GRAM_BF16X3, "device", 0),
+    (1000, 256, B.TSVD_GRAM_TF32X3, "host", 4 << 20), (1000, 256, B.TSVD_GRAM_FP32, "host", 4 << 20),
+]
+
+
+@pytest.mark.parametrize("n,bs,prec,where,budget", TILED_CASES)
+def test_tsvd_orthogonal_batching_matches_oracle(n, bs, prec, where, budget):
+    """Gram as tiles A_J^T A_I (J <= I) of bs-column panels with a ragged last
+    panel; the power loop applies G through the tiles.  Same trajectory as the
+    oracle (forced counts, caller start draws, sign convention)."""
+    m, k, eps = 6000, 8, 1e-10
+    inp = synth.dense_prescribed(m, n, synth.spectrum_geometric(n, 0.72), 1e-7, seed=n + bs)
+    A = inp["A"]
+    x = synth.start_normals(n, k, seed=9)
+    o = ref.tsvd_dense(A, k, eps, x_start=x, sign_convention=True)
+    Ain = torch.from_numpy(A).cuda() if where == "device" else A
+    kw = dict(device_budget=budget, force_stream=True) if budget else {}
+    r = tsvd(Ain, k, eps, start_draws=x, iters_override=o.iters, sign_convention=True, precision=prec,
+             gram_tile=bs, **kw)
+    assert r.iters == o.iters
+    assert r.report["gram_panels"] == -(-n // bs)
+    assert r.report["tiles_on_host"] == (1 if budget else 0)
+    _compare(r, o, k, gapped=ref.gapped_indices(o.sigma ** 2, k))
+    for l in ref.gapped_indices(o.sigma ** 2, k):
+        assert np.max(np.abs(np.asarray(r.V[:, l], dtype=np.float64) - o.V[:, l])) < 1e-4
+
+
 def test_tsvd_builtin_start_vectors_match_oracle_generator():
     m, n, k, eps = 1500, 120, 5, 1e-8
     inp = synth.dense_prescribed(m, n, synth.spectrum_geometric(n, 0.75), 1e-6, seed=4)
