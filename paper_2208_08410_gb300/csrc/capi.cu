@@ -9,6 +9,8 @@
 #include <cstdio>
 #include <cstring>
 #include <functional>
+#include <map>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -29,6 +31,19 @@ void set_cuda_error(cudaError_t e, const char *what, const char *file, int line)
   g_err = buf;
 }
 void set_error_text(const std::string &s) { g_err = s; }
+
+tsvd_status ensure_dynamic_smem(const void *func, size_t bytes) {
+  static std::mutex mu;
+  static std::map<std::pair<const void *, int>, size_t> set;
+  int dev = -1;
+  TSVD_CUDA(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lock(mu);
+  size_t &cur = set[std::make_pair(func, dev)];
+  if (bytes <= cur) return TSVD_OK;
+  TSVD_CUDA(cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+  cur = bytes;
+  return TSVD_OK;
+}
 void count_launch() { ++g_launches; }
 int64_t launches_so_far() { return g_launches; }
 

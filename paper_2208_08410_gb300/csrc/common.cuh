@@ -12,11 +12,18 @@ namespace tsvd {
 // ---------------------------------------------------------------- host side
 void set_cuda_error(cudaError_t e, const char *what, const char *file, int line);
 void set_error_text(const std::string &s);
+// Raise `func`'s dynamic shared-memory limit on the current device to at least
+// `bytes`.  The limit belongs to the process (every host thread sees it), so
+// the record of what was set is process-wide and the limit only grows.
+tsvd_status ensure_dynamic_smem(const void *func, size_t bytes);
 
+// A failed call's error is also this thread's last error; it is read here
+// (cudaGetLastError), so a later launch check does not report it again.
 #define TSVD_CUDA(call)                                                         \
   do {                                                                          \
     cudaError_t e_ = (call);                                                    \
     if (e_ != cudaSuccess) {                                                    \
+      (void)cudaGetLastError();                                                 \
       ::tsvd::set_cuda_error(e_, #call, __FILE__, __LINE__);                    \
       return TSVD_ECUDA;                                                        \
     }                                                                           \

@@ -136,11 +136,14 @@ __global__ void csr_split_kernel(int64_t rows, const int64_t *__restrict__ row_p
   }
 }
 
-// entries of chunk c of row r: [p0 + s_c, p0 + s_{c+1}) with s_0 = 0, s_nch = row length
+// entries of chunk c of row r: [p0 + s_c, p0 + s_{c+1}) with s_0 = 0, s_nch = row length.
+// The two passes stream the row pointers, split points, column indices and
+// values once per chunk; those loads are marked evict-first (ld.global.cs) so
+// that they do not push the chunk of v (pass 1) or w (pass 2) out of L2.
 __device__ __forceinline__ void chunk_range(const int32_t *split, int64_t r, int nch, int c, int64_t p0, int64_t p1,
                                             int64_t &q0, int64_t &q1) {
-  q0 = c == 0 ? p0 : p0 + __ldg(split + r * (nch - 1) + c - 1);
-  q1 = c == nch - 1 ? p1 : p0 + __ldg(split + r * (nch - 1) + c);
+  q0 = c == 0 ? p0 : p0 + __ldcs(split + r * (nch - 1) + c - 1);
+  q1 = c == nch - 1 ? p1 : p0 + __ldcs(split + r * (nch - 1) + c);
 }
 
 // pass 1: y[r] (c == 0: =, else +=) sum over the row's chunk-c entries of values * v[col]
@@ -160,9 +163,9 @@ __global__ void __launch_bounds__(CT) csr_chunk_y_kernel(int64_t rows, const int
   for (int64_t rb = warp_global * RPW; rb < rows; rb += nwarps_total * RPW) {
     const int64_t r = rb + grp;
     int64_t q0 = 0, q1 = 0;
-    if (r < rows) chunk_range(split, r, nch, c, __ldg(row_ptr + r) - base, __ldg(row_ptr + r + 1) - base, q0, q1);
+    if (r < rows) chunk_range(split, r, nch, c, __ldcs(row_ptr + r) - base, __ldcs(row_ptr + r + 1) - base, q0, q1);
     float t = 0.f;
-    for (int64_t p = q0 + sub; p < q1; p += G) t = fmaf(__ldg(values + p), __ldg(v + __ldg(col_idx + p)), t);
+    for (int64_t p = q0 + sub; p < q1; p += G) t = fmaf(__ldcs(values + p), __ldg(v + __ldcs(col_idx + p)), t);
 #pragma unroll
     for (int o = G / 2; o > 0; o >>= 1) t += __shfl_xor_sync(gmask, t, o);
     if (sub == 0 && r < rows) y[r] = c == 0 ? t : y[r] + t;
@@ -192,8 +195,8 @@ __global__ void __launch_bounds__(CT) csr_chunk_w_kernel(int64_t rows, const int
     if (c == 0 && sub == 0) ssq += (double)yr * (double)yr;
     if (scatter) {
       int64_t q0, q1;
-      chunk_range(split, r, nch, c, __ldg(row_ptr + r) - base, __ldg(row_ptr + r + 1) - base, q0, q1);
-      for (int64_t p = q0 + sub; p < q1; p += G) atomicAdd(w + __ldg(col_idx + p), __ldg(values + p) * yr);
+      chunk_range(split, r, nch, c, __ldcs(row_ptr + r) - base, __ldcs(row_ptr + r + 1) - base, q0, q1);
+      for (int64_t p = q0 + sub; p < q1; p += G) atomicAdd(w + __ldcs(col_idx + p), __ldcs(values + p) * yr);
     }
   }
   if (c == 0) {

@@ -522,12 +522,7 @@ int64_t tc_elem(int precision) { return precision == TSVD_GRAM_BF16X3 ? 2 : 4; }
 template <int PREC>
 tsvd_status launch_syrk(const CUtensorMap &mh, const CUtensorMap &ml, const TcArgs &a, int grid,
                         cudaStream_t stream) {
-  static thread_local bool attr = false;
-  if (!attr) {
-    TSVD_CUDA(cudaFuncSetAttribute(syrk_tc_kernel<PREC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   Cfg<PREC>::kSmem));
-    attr = true;
-  }
+  TSVD_TRY(ensure_dynamic_smem(reinterpret_cast<const void *>(syrk_tc_kernel<PREC>), Cfg<PREC>::kSmem));
   syrk_tc_kernel<PREC><<<grid, TC_THREADS, Cfg<PREC>::kSmem, stream>>>(mh, ml, a);
   TSVD_LAUNCHED();
   return TSVD_OK;

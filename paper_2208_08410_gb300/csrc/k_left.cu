@@ -282,11 +282,7 @@ tsvd_status launch_left_dense(const float *A, int64_t rows, int64_t n, int64_t l
       CUtensorMap ma, mv;
       TSVD_TRY(encode_2d(&ma, A, n, rows, ld, TJ, TR));
       TSVD_TRY(encode_2d(&mv, V, n, k, ldv, TJ, LK));
-      static thread_local bool attr = false;
-      if (!attr) {
-        TSVD_CUDA(cudaFuncSetAttribute(left_tma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, T_SMEM));
-        attr = true;
-      }
+      TSVD_TRY(ensure_dynamic_smem(reinterpret_cast<const void *>(left_tma_kernel), T_SMEM));
       const int64_t tiles = ceil_div(rows, TR);
       const int grid = (int)std::min<int64_t>(tiles, di.sms);
       left_tma_kernel<<<grid, TT, T_SMEM, stream>>>(ma, mv, rows, n, k, sigma, U, ldu, (int)l0);

@@ -571,12 +571,7 @@ tsvd_status launch_power_dense(int64_t n, const float *G32, const double *G64, c
   TSVD_TRY(device_info(&di));
   const size_t smem = (size_t)round_up(n, 4) * sizeof(float) + 16 + (size_t)l * sizeof(double);
   if (smem > di.smem_optin) return TSVD_EUNSUPPORTED;
-  static thread_local size_t configured = 0;
-  if (smem > 48 * 1024 && smem > configured) {
-    TSVD_CUDA(cudaFuncSetAttribute(power_dense_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   (int)smem));
-    configured = smem;
-  }
+  if (smem > 48 * 1024) TSVD_TRY(ensure_dynamic_smem(reinterpret_cast<const void *>(power_dense_kernel), smem));
   int per_sm = 0;
   TSVD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, power_dense_kernel, PT, smem));
   if (per_sm < 1) return TSVD_EUNSUPPORTED;

@@ -151,6 +151,20 @@ __device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
 }
 
 constexpr int kMaxCluster = 8;
+static_assert(kSrvPowerThreads == 256 && kMaxCluster == 8, "the partial sums reduce over 8 lanes");
+
+// 1 / sqrt(x): the FP32 reciprocal square root as the seed, then two Newton-Raphson
+// steps for x^(-1/2) in FP64 (y <- y (3 - x y^2) / 2; each squares the relative
+// error, so ~1e-7 becomes ~1e-16); outside the FP32 normal range, the FP64 quotient
+__device__ __forceinline__ double inv_sqrt(double x) {
+  if (x > 1e-36 && x < 1e36) {
+    double y = (double)rsqrtf((float)x);
+    y = y * fma(-0.5 * x * y, y, 1.5);
+    y = y * fma(-0.5 * x * y, y, 1.5);
+    return y;
+  }
+  return 1.0 / sqrt(x);
+}
 constexpr int kPartSlot = kSrvMaxK + 4;  // doubles per (parity, rank) slot
 
 struct PowerSmem {
@@ -278,19 +292,32 @@ __global__ void __launch_bounds__(kSrvPowerThreads, 1) srv_power_kernel(const Sr
             e[u] = e[u] + lo2 + ex;
           }
         }
-        if (lane == 0) {
+        // every lane holds the four sums; lane u finishes row rb + u (its FP64 work in
+        // parallel with the other three rows'): the iterate is the FP32 rounding of
+        // the exact h + e, and the FP64 sums use exactly that stored value
+        if (lane < nr) {
+          float hu = h[0], eu = e[0];
 #pragma unroll
-          for (int u = 0; u < 4; ++u) {
-            if (u < nr) {
-              const double t = (double)(float)((double)h[u] + (double)e[u]);
-              const double vr = (double)v[rb + u];
-              ww += t * t;
-              vw += vr * t;
-              vv += vr * vr;
-              nxt[rb + u] = (float)t;
+          for (int u = 1; u < 4; ++u) {
+            if (lane == u) {
+              hu = h[u];
+              eu = e[u];
             }
           }
+          const float t32 = __fadd_rn(hu, eu);
+          const double t = (double)t32, vr = (double)v[rb + lane];
+          ww = fma(t, t, ww);
+          vw = fma(vr, t, vw);
+          vv = fma(vr, vr, vv);
+          nxt[rb + lane] = t32;
         }
+      }
+      // lanes 0..3 hold the warp's partial sums
+#pragma unroll
+      for (int o = 2; o > 0; o >>= 1) {
+        ww += __shfl_xor_sync(0xffffffffu, ww, o);
+        vw += __shfl_xor_sync(0xffffffffu, vw, o);
+        vv += __shfl_xor_sync(0xffffffffu, vv, o);
       }
       if (lane == 0) {
         wred[3 * warp] = ww;
@@ -314,16 +341,23 @@ __global__ void __launch_bounds__(kSrvPowerThreads, 1) srv_power_kernel(const Sr
         }
       }
       const int par = (int)(phase & 1u);
-      if (threadIdx.x == 0) {
+      if (warp == 0) {
+        // the warps' partials, summed over lanes 0..7 (xor tree: every lane ends with the sums),
+        // then lane c stores them into CTA c's slot for this rank
         double t0 = 0.0, t1 = 0.0, t2 = 0.0;
-        for (int w = 0; w < nwarps; ++w) {
-          t0 += wred[3 * w];
-          t1 += wred[3 * w + 1];
-          t2 += wred[3 * w + 2];
+        if (lane < nwarps) {
+          t0 = wred[3 * lane];
+          t1 = wred[3 * lane + 1];
+          t2 = wred[3 * lane + 2];
         }
-        const uint32_t slot = smem_addr(sm.part + (par * kMaxCluster + rank) * kPartSlot);
-        for (uint32_t c = 0; c < C; ++c) {
-          const uint32_t pa = peer_addr(slot, c);
+#pragma unroll
+        for (int o = 4; o > 0; o >>= 1) {
+          t0 += __shfl_xor_sync(0xffffffffu, t0, o);
+          t1 += __shfl_xor_sync(0xffffffffu, t1, o);
+          t2 += __shfl_xor_sync(0xffffffffu, t2, o);
+        }
+        if (lane < (int)C) {
+          const uint32_t pa = peer_addr(smem_addr(sm.part + (par * kMaxCluster + rank) * kPartSlot), (uint32_t)lane);
           st_peer_f64(pa, t0);
           st_peer_f64(pa + 8, t1);
           st_peer_f64(pa + 16, t2);
@@ -331,37 +365,47 @@ __global__ void __launch_bounds__(kSrvPowerThreads, 1) srv_power_kernel(const Sr
       }
       cluster_sync_all();
       ++phase;
-      if (threadIdx.x == 0) {
+      if (warp == 0) {
+        // the C ranks' partials, same xor tree in every CTA, so all take the same decision
         double t0 = 0.0, t1 = 0.0, t2 = 0.0;
-        for (uint32_t c = 0; c < C; ++c) {
-          const double *s = sm.part + (par * kMaxCluster + c) * kPartSlot;
-          t0 += s[0];
-          t1 += s[1];
-          t2 += s[2];
+        if (lane < (int)C) {
+          const double *ps = sm.part + (par * kMaxCluster + lane) * kPartSlot;
+          t0 = ps[0];
+          t1 = ps[1];
+          t2 = ps[2];
         }
-        const int it1 = it + 1;
-        const double nw = sqrt(t0);
-        int st = 0, done = 0;
-        double sc = 0.0;
-        if (!(nw > 1e-30 * rank_scale)) {
-          st = 2;
-          done = 1;
-        } else {
-          sc = 1.0 / nw;
-          if (q.iters_override) {
-            done = it1 >= q.iters_override[l];
+#pragma unroll
+        for (int o = 4; o > 0; o >>= 1) {
+          t0 += __shfl_xor_sync(0xffffffffu, t0, o);
+          t1 += __shfl_xor_sync(0xffffffffu, t1, o);
+          t2 += __shfl_xor_sync(0xffffffffu, t2, o);
+        }
+        if (lane == 0) {
+          const int it1 = it + 1;
+          int st = 0, done = 0;
+          double sc = 0.0;
+          const double floor = 1e-30 * rank_scale;  // ||w|| <= floor: B v0 vanished
+          if (!(t0 > floor * floor)) {
+            st = 2;
+            done = 1;
           } else {
-            const double cosv = fabs(t1) / (nw * sqrt(t2));
-            done = cosv >= 1.0 - q.eps;
-            if (!done && it1 >= q.max_iter) {
-              done = 1;
-              st = 1;
+            sc = inv_sqrt(t0);
+            if (q.iters_override) {
+              done = it1 >= q.iters_override[l];
+            } else {
+              // |v . w| / (||v|| ||w||) >= 1 - eps, squared: both sides are non-negative
+              const double c1 = 1.0 - q.eps;
+              done = t1 * t1 >= c1 * c1 * t0 * t2;
+              if (!done && it1 >= q.max_iter) {
+                done = 1;
+                st = 1;
+              }
             }
           }
+          s_scal[0] = sc;
+          s_scal[1] = (double)st;
+          s_scal[2] = (double)done;
         }
-        s_scal[0] = sc;
-        s_scal[1] = (double)st;
-        s_scal[2] = (double)done;
       }
       __syncthreads();
       ++it;
@@ -614,14 +658,10 @@ tsvd_status launch_srv_power(const SrvReq *reqs, int n_reqs, int cluster, size_t
   if (smem > di.smem_optin) return TSVD_EINVAL;
   // the kernel's static arrays (~17 KB) count toward the 48 KB a launch gets without
   // opting in, so the attribute is raised for any size above what is already allowed
-  static thread_local size_t attr = 0;
-  if (smem > attr) {
-    cudaFuncAttributes fa;
-    TSVD_CUDA(cudaFuncGetAttributes(&fa, srv_power_kernel));
-    if (fa.sharedSizeBytes + smem > di.smem_optin) return TSVD_EINVAL;
-    TSVD_CUDA(cudaFuncSetAttribute(srv_power_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    attr = smem;
-  }
+  cudaFuncAttributes fa;
+  TSVD_CUDA(cudaFuncGetAttributes(&fa, srv_power_kernel));
+  if (fa.sharedSizeBytes + smem > di.smem_optin) return TSVD_EINVAL;
+  TSVD_TRY(ensure_dynamic_smem(reinterpret_cast<const void *>(srv_power_kernel), smem));
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)(n_reqs * cluster));
   cfg.blockDim = dim3(kSrvPowerThreads);
