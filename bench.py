@@ -767,6 +767,8 @@ def serve_workload(args):
         errs = np.zeros(n_req)      # every triplet
         errs_env = np.zeros(n_req)  # triplets with sigma_i >= 0.1 sigma_0
         lat = np.zeros(n_req)
+        serv = np.zeros(n_req)     # launch -> completion (the request's time on the GPU, shared)
+        apps = np.zeros(n_req)
         done_t = np.zeros(n_req)
         sub_t = np.zeros(n_req)
         status = np.zeros(n_req, dtype=np.int64)
@@ -783,6 +785,8 @@ def serve_workload(args):
                 env = truth >= ENVELOPE
                 errs_env[i] = float(np.max(rel[env])) if env.any() else 0.0
                 lat[i] = info["done_s"] - info["submit_s"]
+                serv[i] = info["done_s"] - info["launch_s"]
+                apps[i] = info["applications"]
                 done_t[i], sub_t[i], status[i] = info["done_s"], info["submit_s"], st
                 free.put(sl)
         th = threading.Thread(target=collector)
@@ -800,6 +804,15 @@ def serve_workload(args):
             recs.put((i, t, sl))
         th.join()
         span = float(done_t.max() - sub_t.min())
+        dims = np.array([min(shapes[p]["m"], shapes[p]["n"]) for p in picks])
+        by_dim = {}
+        for lo, hi in ((0, 64), (64, 128), (128, 256), (256, 512), (512, 1024), (1024, 2048)):
+            sel = (dims > lo) & (dims <= hi)
+            if sel.any():
+                by_dim[f"d<={hi}"] = {"requests": int(sel.sum()),
+                                      "mean_service_ms": round(float(serv[sel].mean()) * 1e3, 2),
+                                      "p99_service_ms": round(float(np.percentile(serv[sel], 99)) * 1e3, 2),
+                                      "mean_applications": round(float(apps[sel].mean()), 1)}
         return {"p50_ms": round(float(np.percentile(lat, 50)) * 1e3, 3),
                 "p99_ms": round(float(np.percentile(lat, 99)) * 1e3, 3),
                 "mean_ms": round(float(lat.mean()) * 1e3, 3), "solves_per_s": round(n_req / span, 1),
@@ -808,7 +821,8 @@ def serve_workload(args):
                 "frac_requests_sigma_err_le_1e-5_in_envelope": float(np.mean(errs_env <= 1e-5)),
                 "sigma_max_rel_err_all_triplets": float("%.3g" % errs.max()),
                 "frac_requests_sigma_err_le_1e-5_all_triplets": float(np.mean(errs <= 1e-5)),
-                "status_counts": {B.STATUS_NAMES[int(c)]: int((status == c).sum()) for c in np.unique(status)}}
+                "status_counts": {B.STATUS_NAMES[int(c)]: int((status == c).sum()) for c in np.unique(status)},
+                "by_dim": by_dim}
 
     server = Server(device_budget=args.serve_budget << 30, n_streams=4, max_wave=256)
     server.autotune(iters=30)

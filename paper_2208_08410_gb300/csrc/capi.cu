@@ -114,6 +114,11 @@ struct tsvd_plan_s {
   bool csr_sorted = true;     // every row's columns ascending (host CSR: checked at plan time)
   size_t o_csr_y = 0, o_csr_split = 0, b_split_slot = 0;
   int vec_grid = 0;
+  // dense: the Gram's dimension d = min(m, n) and the contraction length K = max(m, n).
+  // wide (m < n, Eq. 3): the Gram is A A^T, blocks are column blocks of A, the
+  // power method finds U and the pass over A forms V = A^T U Sigma^-1
+  bool wide = false;
+  int64_t d = 0, K = 0;
   // orthogonal batching (dense; Sec. V-C, Alg. 3): the Gram matrix as FP64 tiles
   // B_JI = A_J^T A_I (J <= I) of tb-column panels, formed task by task
   bool tiled = false;
@@ -167,7 +172,9 @@ void partition_rows(int64_t m, int64_t block_rows, std::vector<int64_t> &starts)
 tsvd_status plan_dense_tiled(tsvd_plan_s *p);
 
 tsvd_status plan_dense(tsvd_plan_s *p) {
-  const int64_t n = p->n, k = p->k, m = p->m;
+  // in Gram terms: n = d (the Gram's dimension), m = K (the contraction length,
+  // cut into blocks: rows of a tall A, columns of a wide one)
+  const int64_t n = p->d, k = p->k, m = p->K;
   const int prec = p->opt.precision;
   if (p->opt.gram_tile > 0) return plan_dense_tiled(p);
   Carve c;
@@ -248,6 +255,7 @@ tsvd_status plan_dense(tsvd_plan_s *p) {
 // used in turn by the Gram tasks (task tile, tensor-core scratch, panel ring
 // for host A) and by the U pass (row-block ring for host A, U staging).
 tsvd_status plan_dense_tiled(tsvd_plan_s *p) {
+  if (p->wide) return TSVD_EUNSUPPORTED;  // column panels of a wide A: not built
   const int64_t n = p->n, k = p->k, m = p->m;
   const int prec = p->opt.precision;
   if (k + 4 > kVecPartStride) return TSVD_EUNSUPPORTED;
@@ -488,7 +496,7 @@ tsvd_status tsvd_plan(tsvd_plan_t *out, const tsvd_matrix *A, int64_t k, double 
   if (opt.power_kernel < TSVD_POWER_AUTO || opt.power_kernel > TSVD_POWER_CLUSTER) return TSVD_EINVAL;
   if (opt.gram_tile < 0 || opt.gram_tile % 256 != 0) return TSVD_EINVAL;
   if (opt.gram_tile > 0 && A->kind != TSVD_DENSE_F32_ROWMAJOR) return TSVD_EINVAL;
-  const bool cluster_fits = A->kind == TSVD_DENSE_F32_ROWMAJOR && A->n <= kSrvMaxDim && k <= kSrvMaxK;
+  const bool cluster_fits = A->kind == TSVD_DENSE_F32_ROWMAJOR && mn <= kSrvMaxDim && k <= kSrvMaxK;
   if (opt.power_kernel == TSVD_POWER_CLUSTER && !cluster_fits) {
     set_error_text("tsvd_plan: the cluster power kernel takes dense A with n <= " + std::to_string(kSrvMaxDim) +
                    " and k <= " + std::to_string(kSrvMaxK));
@@ -502,7 +510,8 @@ tsvd_status tsvd_plan(tsvd_plan_t *out, const tsvd_matrix *A, int64_t k, double 
     if (A->n > 0x7fffffffLL) return TSVD_EUNSUPPORTED;
     if (A->location == TSVD_HOST) TSVD_TRY(validate_csr_host(A, &csr_sorted));
   }
-  if (A->m < A->n) return TSVD_EUNSUPPORTED;  // the m < n branch (Eq. 3) is not built
+  // the CSR path applies A^T (A v) on R^n and needs m >= n; dense m < n takes Eq. 3
+  if (A->kind == TSVD_CSR_F32_I32_I64 && A->m < A->n) return TSVD_EUNSUPPORTED;
   if (A->kind == TSVD_DENSE_F32_ROWMAJOR && A->n > 32768) return TSVD_EUNSUPPORTED;
   if (opt.iters_override) {
     for (int64_t l = 0; l < k; ++l)
@@ -522,9 +531,12 @@ tsvd_status tsvd_plan(tsvd_plan_t *out, const tsvd_matrix *A, int64_t k, double 
     p->k = k;
     p->eps = eps;
     p->opt = opt;
+    p->wide = A->kind == TSVD_DENSE_F32_ROWMAJOR && A->m < A->n;
+    p->d = std::min(A->m, A->n);
+    p->K = std::max(A->m, A->n);
     p->n_buffers = opt.n_buffers;
     if (opt.iters_override) p->iters_override.assign(opt.iters_override, opt.iters_override + k);
-    if (opt.start_draws) p->start_draws.assign(opt.start_draws, opt.start_draws + (size_t)A->n * k);
+    if (opt.start_draws) p->start_draws.assign(opt.start_draws, opt.start_draws + (size_t)mn * k);
     p->opt.iters_override = nullptr;
     p->opt.start_draws = nullptr;
     p->cluster_power = A->kind == TSVD_DENSE_F32_ROWMAJOR &&
@@ -646,56 +658,67 @@ tsvd_status copy_time_ms(Run &r, double *ms, double *min_gbps, double *max_gbps)
   return TSVD_OK;
 }
 
-// Bring dense rows [r0, r0+rows) to the device; returns the pointer/stride to
-// use on the compute stream.  The slot is released by release_dense().
+// Bring dense block [r0, r0+rows) of the contraction index to the device (rows
+// of a tall A; columns of a wide A, all m rows of them); returns the pointer /
+// stride to use on the compute stream.  The slot is released by release_slot().
 tsvd_status acquire_dense(Run &r, int64_t r0, int64_t rows, const float **out, int64_t *ldo, int *slot,
                           bool resident_fill) {
   tsvd_plan_s *p = r.p;
   const tsvd_matrix *A = r.A;
+  const bool wide = p->wide;
   *slot = -1;
   if (p->mode == MODE_DEVICE) {
-    *out = A->values + r0 * A->ld;
+    *out = wide ? A->values + r0 : A->values + r0 * A->ld;
     *ldo = A->ld;
     return TSVD_OK;
   }
+  // destination and its row stride: the resident copy of A (m x n, stride n), or a ring slot
+  // (a tall block: rows x n, stride n; a wide block: m x rows, stride chunk_rows)
   float *dst;
+  int64_t ldd;
   if (p->mode == MODE_RESIDENT) {
-    dst = reinterpret_cast<float *>(r.ws + p->o_res) + r0 * p->n;
+    float *res = reinterpret_cast<float *>(r.ws + p->o_res);
+    dst = wide ? res + r0 : res + r0 * p->n;
+    ldd = p->n;
     *out = dst;
-    *ldo = p->n;
+    *ldo = ldd;
     if (!resident_fill) return TSVD_OK;
   } else {
     const int s = (int)(r.chunk_seq++ % p->n_buffers);
     *slot = s;
     dst = reinterpret_cast<float *>(r.ws + p->o_ring + p->b_slot * s);
+    ldd = wide ? p->chunk_rows : p->n;
     TSVD_CUDA(cudaStreamWaitEvent(p->copy_stream, p->ev_free[s], 0));
     *out = dst;
-    *ldo = p->n;
+    *ldo = ldd;
   }
-  const float *src = A->values + r0 * A->ld;
+  // copy height x width floats: a tall block is rows x n, a wide block m x rows
+  const int64_t height = wide ? p->m : rows, width = wide ? rows : p->n;
+  const float *src = wide ? A->values + r0 : A->values + r0 * A->ld;
   TSVD_TRY(copy_event(r, true));
   // the block in two halves on two copy streams: host memory that a single copy
   // drains slowly (seen on some hosts for parts of a large pinned allocation)
   // gets two copy engines; the halves join on the first stream
-  const int64_t h0 = rows / 2, h1 = rows - h0;
+  const int64_t h0 = height / 2, h1 = height - h0;
   TSVD_CUDA(cudaEventRecord(p->ev_csplit, p->copy_stream));
   TSVD_CUDA(cudaStreamWaitEvent(p->copy_stream2, p->ev_csplit, 0));
   for (int half = 0; half < 2; ++half) {
     const int64_t rr0 = half ? h0 : 0, rr = half ? h1 : h0;
     if (rr == 0) continue;
     cudaStream_t cst = half ? p->copy_stream2 : p->copy_stream;
-    if (A->ld == p->n) {
-      TSVD_CUDA(cudaMemcpyAsync(dst + rr0 * p->n, src + rr0 * A->ld, (size_t)rr * p->n * 4, cudaMemcpyHostToDevice, cst));
+    if (A->ld == width && ldd == width) {
+      TSVD_CUDA(cudaMemcpyAsync(dst + rr0 * ldd, src + rr0 * A->ld, (size_t)rr * width * 4, cudaMemcpyHostToDevice,
+                                cst));
     } else {
-      TSVD_CUDA(cudaMemcpy2DAsync(dst + rr0 * p->n, (size_t)p->n * 4, src + rr0 * A->ld, (size_t)A->ld * 4,
-                                  (size_t)p->n * 4, (size_t)rr, cudaMemcpyHostToDevice, cst));
+      TSVD_CUDA(cudaMemcpy2DAsync(dst + rr0 * ldd, (size_t)ldd * 4, src + rr0 * A->ld, (size_t)A->ld * 4,
+                                  (size_t)width * 4, (size_t)rr, cudaMemcpyHostToDevice, cst));
     }
   }
   TSVD_CUDA(cudaEventRecord(p->ev_cjoin, p->copy_stream2));
   TSVD_CUDA(cudaStreamWaitEvent(p->copy_stream, p->ev_cjoin, 0));
   TSVD_TRY(copy_event(r, false));
-  if (p->opt.time_kernels) r.copy_bytes.push_back((double)rows * p->n * 4);
-  r.h2d += (double)rows * p->n * 4;
+  if (p->opt.time_kernels) r.copy_bytes.push_back((double)height * width * 4);
+  r.h2d += (double)height * width * 4;
   const int ev = *slot >= 0 ? *slot : 0;
   TSVD_CUDA(cudaEventRecord(p->ev_ready[ev], p->copy_stream));
   TSVD_CUDA(cudaStreamWaitEvent(r.cs, p->ev_ready[ev], 0));
@@ -709,48 +732,66 @@ tsvd_status release_slot(Run &r, int slot) {
 
 tsvd_status gram_dispatch(const float *A, int64_t rows, int64_t n, int64_t ld, double *G, int prec,
                           void *scr, size_t scr_bytes, cudaStream_t s, cudaEvent_t ev0 = nullptr,
-                          cudaEvent_t ev1 = nullptr, bool reset_status = true) {
+                          cudaEvent_t ev1 = nullptr, bool reset_status = true, bool trans = false) {
+  if (trans) {
+    // a column block of a wide A: X[r][c] = A[c ld + r], Gram X^T X (Eq. 3)
+    if (prec == TSVD_GRAM_FP32) {
+      if (ev0) TSVD_CUDA(cudaEventRecord(ev0, s));
+      TSVD_TRY(launch_gram_simt_t(A, rows, n, ld, G, s));
+      if (ev1) TSVD_CUDA(cudaEventRecord(ev1, s));
+      return TSVD_OK;
+    }
+    return launch_gram_tc_t(A, rows, n, ld, G, prec, scr, scr_bytes, s, ev0, ev1, reset_status);
+  }
   if (prec == TSVD_GRAM_FP32) return launch_gram_simt(A, rows, n, ld, G, s, ev0, ev1);
   return launch_gram_tc(A, rows, n, ld, G, prec, scr, scr_bytes, s, ev0, ev1, reset_status);
 }
 
-tsvd_status left_pass_dense(Run &r, const float *V32, const double *sigma, float *U) {
+// The other factor, one pass over A (Alg. 1 l.11-13 / l.15-17): OUT = A P
+// Sigma^-1 for a tall A (P = V, OUT = U) or A^T P Sigma^-1 for a wide A
+// (P = U from A A^T, OUT = V); P is d x k and OUT is K x k, both column-major.
+tsvd_status left_pass_dense(Run &r, const float *P32, const double *sigma, float *OUT) {
   tsvd_plan_s *p = r.p;
   const bool host_u = p->opt.out_location == TSVD_HOST;
-  // In the streamed mode the last n_buffers row blocks of the Gram pass are
+  const int64_t d = p->d, K = p->K, k = p->k;
+  // In the streamed mode the last n_buffers blocks of the Gram pass are
   // still in the ring (block c in slot c % n_buffers): use them first, then
   // stream the others through the slots they free.
   // (Not after an orthogonally batched Gram: its ring held column panels.)
   const int64_t nc = p->n_chunks;
   const bool reuse = p->mode == MODE_STREAM && !p->tiled;
   const int64_t first_res = reuse ? std::max<int64_t>(0, nc - p->n_buffers) : nc;
+  auto kernel = [&](const float *Ab, int64_t rows, int64_t ldb, float *dst, int64_t ldo) -> tsvd_status {
+    if (p->wide) return launch_left_trans(Ab, rows, d, ldb, P32, d, k, sigma, dst, ldo, r.cs);
+    return launch_left_dense(Ab, rows, d, ldb, P32, d, k, sigma, dst, ldo, r.cs);
+  };
   for (int64_t idx = 0; idx < nc; ++idx) {
     const int64_t c = reuse ? (idx < nc - first_res ? first_res + idx : idx - (nc - first_res)) : idx;
-    const int64_t r0 = c * p->chunk_rows, rows = std::min(p->chunk_rows, p->m - r0);
+    const int64_t r0 = c * p->chunk_rows, rows = std::min(p->chunk_rows, K - r0);
     const float *Ab;
     int64_t ldb;
     int slot;
     if (reuse && c >= first_res) {
       slot = (int)(c % p->n_buffers);
       Ab = reinterpret_cast<const float *>(r.ws + p->o_ring + p->b_slot * slot);
-      ldb = p->n;
+      ldb = p->wide ? p->chunk_rows : p->n;
     } else {
       TSVD_TRY(acquire_dense(r, r0, rows, &Ab, &ldb, &slot, false));
     }
     if (!host_u) {
-      TSVD_TRY(launch_left_dense(Ab, rows, p->n, ldb, V32, p->n, p->k, sigma, U + r0, p->m, r.cs));
+      TSVD_TRY(kernel(Ab, rows, ldb, OUT + r0, K));
       TSVD_TRY(release_slot(r, slot));
     } else {
       const int b = (int)(idx & 1);
       float *ub = reinterpret_cast<float *>(r.ws + p->o_ubuf + p->b_ubuf * b);
       TSVD_CUDA(cudaStreamWaitEvent(r.cs, p->ev_u_free[b], 0));
-      TSVD_TRY(launch_left_dense(Ab, rows, p->n, ldb, V32, p->n, p->k, sigma, ub, rows, r.cs));
+      TSVD_TRY(kernel(Ab, rows, ldb, ub, rows));
       TSVD_TRY(release_slot(r, slot));
       TSVD_CUDA(cudaEventRecord(p->ev_u_ready[b], r.cs));
       TSVD_CUDA(cudaStreamWaitEvent(p->d2h_stream, p->ev_u_ready[b], 0));
-      TSVD_CUDA(cudaMemcpy2DAsync(U + r0, (size_t)p->m * 4, ub, (size_t)rows * 4, (size_t)rows * 4,
-                                  (size_t)p->k, cudaMemcpyDeviceToHost, p->d2h_stream));
-      r.d2h += (double)rows * p->k * 4;
+      TSVD_CUDA(cudaMemcpy2DAsync(OUT + r0, (size_t)K * 4, ub, (size_t)rows * 4, (size_t)rows * 4, (size_t)k,
+                                  cudaMemcpyDeviceToHost, p->d2h_stream));
+      r.d2h += (double)rows * k * 4;
       TSVD_CUDA(cudaEventRecord(p->ev_u_free[b], p->d2h_stream));
     }
   }
@@ -765,7 +806,7 @@ tsvd_status left_pass_dense(Run &r, const float *V32, const double *sigma, float
 tsvd_status power_cluster_dense(Run &r, double *G64, float *G32, double *V64, float *V32, double *sig2,
                                 double *sigma, int32_t *info, void *pscr) {
   tsvd_plan_s *p = r.p;
-  const int64_t n = p->n, k = p->k;
+  const int64_t n = p->d, k = p->k;  // the Gram's dimension
   unsigned char *base = static_cast<unsigned char *>(pscr);
   SrvReq *dq = reinterpret_cast<SrvReq *>(base);
   int32_t *d_iters = reinterpret_cast<int32_t *>(base + round_up(sizeof(SrvReq), 256));
@@ -792,7 +833,7 @@ tsvd_status power_cluster_dense(Run &r, double *G64, float *G32, double *V64, fl
   SrvReq &q = p->srv_req;
   q = SrvReq{};
   q.A = nullptr;  // the other factor is the left pass's
-  q.m = p->m;
+  q.m = p->K;  // the kernel reads d = n of a tall descriptor; the other factor is not formed here
   q.n = n;
   q.trans = 0;
   q.k = (int32_t)k;
@@ -828,7 +869,10 @@ tsvd_status power_cluster_dense(Run &r, double *G64, float *G32, double *V64, fl
 
 tsvd_status factor_dense(Run &r, float *U, double *sigma_out, float *V_out, tsvd_report *rep) {
   tsvd_plan_s *p = r.p;
-  const int64_t n = p->n, k = p->k;
+  const int64_t n = p->d, k = p->k;  // the Gram's dimension (n for a tall A, m for a wide one)
+  // the power method's vectors and the other factor (Alg. 1 l.11-13 / l.15-17)
+  float *P_out = p->wide ? U : V_out;
+  float *O_out = p->wide ? V_out : U;
   unsigned char *ws = r.ws;
   double *G64 = reinterpret_cast<double *>(ws + p->o_G64);
   float *G32 = reinterpret_cast<float *>(ws + p->o_G32);
@@ -853,13 +897,13 @@ tsvd_status factor_dense(Run &r, float *U, double *sigma_out, float *V_out, tsvd
   // (the 256-byte aligned scratch starts with its status word)
   if (p->opt.precision != TSVD_GRAM_FP32) TSVD_CUDA(cudaMemsetAsync(gscr, 0, 4, r.cs));
   for (int64_t c = 0; c < p->n_chunks; ++c) {
-    const int64_t r0 = c * p->chunk_rows, rows = std::min(p->chunk_rows, p->m - r0);
+    const int64_t r0 = c * p->chunk_rows, rows = std::min(p->chunk_rows, p->K - r0);
     const float *Ab;
     int64_t ldb;
     int slot;
     TSVD_TRY(acquire_dense(r, r0, rows, &Ab, &ldb, &slot, true));
     TSVD_TRY(gram_dispatch(Ab, rows, n, ldb, G64, p->opt.precision, gscr, p->b_gscr, r.cs,
-                           timed ? p->ev_k[2 * c] : nullptr, timed ? p->ev_k[2 * c + 1] : nullptr, false));
+                           timed ? p->ev_k[2 * c] : nullptr, timed ? p->ev_k[2 * c + 1] : nullptr, false, p->wide));
     TSVD_TRY(release_slot(r, slot));
   }
   int32_t gram_err = 0;
@@ -895,15 +939,16 @@ tsvd_status factor_dense(Run &r, float *U, double *sigma_out, float *V_out, tsvd
   }
   TSVD_CUDA(cudaEventRecord(p->ev_t[2], r.cs));
 
-  // ---- left vectors: U = A V diag(sigma)^-1
-  if (U) TSVD_TRY(left_pass_dense(r, V32, sigma, U));
+  // ---- the other factor: U = A V diag(sigma)^-1, or V = A^T U diag(sigma)^-1 for a wide A
+  // (a tall A skips it when U is NULL; a wide A always forms V)
+  if (O_out) TSVD_TRY(left_pass_dense(r, V32, sigma, O_out));
   TSVD_CUDA(cudaEventRecord(p->ev_t[3], r.cs));
 
   // ---- outputs
   const cudaMemcpyKind kind = p->opt.out_location == TSVD_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
   TSVD_CUDA(cudaMemcpyAsync(sigma_out, sigma, (size_t)k * 8, kind, r.cs));
-  TSVD_CUDA(cudaMemcpyAsync(V_out, V32, (size_t)n * k * 4, kind, r.cs));
-  if (kind == cudaMemcpyDeviceToHost) r.d2h += (double)k * 8 + (double)n * k * 4;
+  if (P_out) TSVD_CUDA(cudaMemcpyAsync(P_out, V32, (size_t)n * k * 4, kind, r.cs));
+  if (kind == cudaMemcpyDeviceToHost) r.d2h += (double)k * 8 + (P_out ? (double)n * k * 4 : 0.0);
   std::vector<int32_t> hinfo((size_t)k * 4);
   TSVD_CUDA(cudaMemcpyAsync(hinfo.data(), info, hinfo.size() * 4, cudaMemcpyDeviceToHost, r.cs));
   TSVD_CUDA(cudaStreamSynchronize(r.cs));

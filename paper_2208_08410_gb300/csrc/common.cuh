@@ -167,6 +167,13 @@ size_t gram_tc_scratch_bytes(int64_t rows, int64_t n, int precision);
 tsvd_status launch_gram_tc_rect(const float *AJ, const float *AI, int64_t rows, int64_t bs, int64_t nJ, int64_t nI,
                                 int64_t ld, double *G, int precision, void *scratch, size_t scratch_bytes,
                                 cudaStream_t stream, bool reset_status);
+// Gram of a transposed operand, G += X^T X with X[r][c] = A[c ld + r] (rows
+// contraction indices, n outputs): a column block of a wide A, whose Gram is
+// A A^T (Eq. 3).  Same storage of G as the row-major launchers.
+tsvd_status launch_gram_simt_t(const float *A, int64_t rows, int64_t n, int64_t ld, double *G, cudaStream_t stream);
+tsvd_status launch_gram_tc_t(const float *A, int64_t rows, int64_t n, int64_t ld, double *G, int precision,
+                             void *scratch, size_t scratch_bytes, cudaStream_t stream, cudaEvent_t ev0 = nullptr,
+                             cudaEvent_t ev1 = nullptr, bool reset_status = true);
 // The same on CUDA cores (FP32): G[a][b] += sum_r AJ[r][a] AI[r][b], row stride ldg.
 tsvd_status launch_gram_simt_rect(const float *AJ, const float *AI, int64_t rows, int64_t nJ, int64_t nI, int64_t ld,
                                   double *G, int64_t ldg, cudaStream_t stream);
@@ -211,6 +218,10 @@ tsvd_status launch_sigma_from_sigma2(const double *sig2, double *sigma, int64_t 
                                      cudaStream_t stream);
 tsvd_status launch_f64_to_f32(const double *src, float *dst, int64_t count, cudaStream_t stream);
 
+// V[j][l] = sum_i A[i][j] U[i][l] / sigma_l for j < K (a column block of a wide
+// A, d rows, stride ld); U d x k and V K x k column-major (ldu, ldv).
+tsvd_status launch_left_trans(const float *A, int64_t K, int64_t d, int64_t ld, const float *U, int64_t ldu,
+                              int64_t k, const double *sigma, float *V, int64_t ldv, cudaStream_t stream);
 tsvd_status launch_left_dense(const float *A, int64_t rows, int64_t n, int64_t ld, const float *V,
                               int64_t ldv, int64_t k, const double *sigma, float *U, int64_t ldu,
                               cudaStream_t stream);

@@ -40,13 +40,31 @@ __device__ __forceinline__ float4 load4(const float *row, int64_t c, int64_t n, 
   return r;
 }
 
+// X[r][c] = A[c ld + r]: four consecutive r of column c, zero outside (c < n, r < k1)
+__device__ __forceinline__ float4 load4t(const float *A, int64_t c, int64_t n, int64_t r, int64_t k1, int64_t ld,
+                                         bool vec) {
+  float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (c >= n) return v;
+  const float *p = A + c * ld + r;
+  if (vec && r + 3 < k1) return __ldg(reinterpret_cast<const float4 *>(p));
+  if (r < k1) v.x = __ldg(p);
+  if (r + 1 < k1) v.y = __ldg(p + 1);
+  if (r + 2 < k1) v.z = __ldg(p + 2);
+  if (r + 3 < k1) v.w = __ldg(p + 3);
+  return v;
+}
+
 // Triangular mode (nbj == 0): AI == AJ == A, tiles of the lower block
 // triangle.  Rectangular mode (nbj > 0, a task of the orthogonal batching):
 // G[gj][gi] += sum_r AJ[r][gj] AI[r][gi] for every gj < nJ, gi < nI, tiles
-// enumerated row by row over ceil(nJ / 128) J blocks.
+// enumerated row by row over ceil(nJ / 128) J blocks.  trans: the operand is
+// X with X[r][c] = A[c ld + r] (a column block of a wide A: its Gram X^T X is
+// A A^T, Eq. 3); the loads then run along r and the tile is transposed on its
+// way into shared memory.
 __global__ void __launch_bounds__(NT, 2)
 syrk_simt_kernel(const float *__restrict__ AI, const float *__restrict__ AJ, int64_t rows, int64_t nI, int64_t nJ,
-                 int64_t ld, double *__restrict__ G, int64_t ldg, int nbj, int64_t rows_per_split, int vec) {
+                 int64_t ld, double *__restrict__ G, int64_t ldg, int nbj, int64_t rows_per_split, int vec,
+                 int trans) {
   int bi, bj;
   if (nbj > 0) {
     bi = (int)(blockIdx.x / nbj);
@@ -75,7 +93,13 @@ syrk_simt_kernel(const float *__restrict__ AI, const float *__restrict__ AJ, int
     for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
 
   float4 ra, rb;
+  const int tc = tid >> 1, tk = (tid & 1) * 4;  // trans: column and first row this thread loads
   auto fetch = [&](int64_t kk) {
+    if (trans) {
+      ra = load4t(AI, I0 + tc, nI, kk + tk, k1, ld, vec);
+      rb = diag ? ra : load4t(AJ, J0 + tc, nJ, kk + tk, k1, ld, vec);
+      return;
+    }
     const int64_t r = kk + lr;
     if (r < k1) {
       ra = load4(AI + r * ld, I0 + lc, nI, vec);
@@ -84,10 +108,24 @@ syrk_simt_kernel(const float *__restrict__ AI, const float *__restrict__ AJ, int
       ra = rb = make_float4(0.f, 0.f, 0.f, 0.f);
     }
   };
+  auto put = [&](int buf) {
+    if (trans) {
+      sI[buf][tk][tc] = ra.x;
+      sI[buf][tk + 1][tc] = ra.y;
+      sI[buf][tk + 2][tc] = ra.z;
+      sI[buf][tk + 3][tc] = ra.w;
+      sJ[buf][tk][tc] = rb.x;
+      sJ[buf][tk + 1][tc] = rb.y;
+      sJ[buf][tk + 2][tc] = rb.z;
+      sJ[buf][tk + 3][tc] = rb.w;
+    } else {
+      *reinterpret_cast<float4 *>(&sI[buf][lr][lc]) = ra;
+      *reinterpret_cast<float4 *>(&sJ[buf][lr][lc]) = rb;
+    }
+  };
 
   fetch(k0);
-  *reinterpret_cast<float4 *>(&sI[0][lr][lc]) = ra;
-  *reinterpret_cast<float4 *>(&sJ[0][lr][lc]) = rb;
+  put(0);
   __syncthreads();
 
   int cur = 0;
@@ -110,10 +148,7 @@ syrk_simt_kernel(const float *__restrict__ AI, const float *__restrict__ AJ, int
 #pragma unroll
         for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
     }
-    if (more) {
-      *reinterpret_cast<float4 *>(&sI[cur ^ 1][lr][lc]) = ra;
-      *reinterpret_cast<float4 *>(&sJ[cur ^ 1][lr][lc]) = rb;
-    }
+    if (more) put(cur ^ 1);
     __syncthreads();
     cur ^= 1;
   }
@@ -161,9 +196,25 @@ tsvd_status launch_gram_simt(const float *A, int64_t rows, int64_t n, int64_t ld
   const bool vec = (ld % 4 == 0) && ((reinterpret_cast<uintptr_t>(A) & 15) == 0);
   dim3 grid((unsigned)tiles, (unsigned)splits);
   if (ev0) TSVD_CUDA(cudaEventRecord(ev0, stream));
-  syrk_simt_kernel<<<grid, NT, 0, stream>>>(A, A, rows, n, n, ld, G, n, 0, per, vec ? 1 : 0);
+  syrk_simt_kernel<<<grid, NT, 0, stream>>>(A, A, rows, n, n, ld, G, n, 0, per, vec ? 1 : 0, 0);
   TSVD_LAUNCHED();
   if (ev1) TSVD_CUDA(cudaEventRecord(ev1, stream));
+  return TSVD_OK;
+}
+
+tsvd_status launch_gram_simt_t(const float *A, int64_t rows, int64_t n, int64_t ld, double *G,
+                               cudaStream_t stream) {
+  if (rows <= 0) return TSVD_OK;
+  DeviceInfo di;
+  TSVD_TRY(device_info(&di));
+  const int64_t nb = ceil_div(n, BM);
+  const int64_t tiles = nb * (nb + 1) / 2;
+  int64_t per = 0;
+  const int64_t splits = simt_splits(rows, tiles, di.sms, &per);
+  const bool vec = (ld % 4 == 0) && ((reinterpret_cast<uintptr_t>(A) & 15) == 0);
+  dim3 grid((unsigned)tiles, (unsigned)splits);
+  syrk_simt_kernel<<<grid, NT, 0, stream>>>(A, A, rows, n, n, ld, G, n, 0, per, vec ? 1 : 0, 1);
+  TSVD_LAUNCHED();
   return TSVD_OK;
 }
 
@@ -180,7 +231,7 @@ tsvd_status launch_gram_simt_rect(const float *AJ, const float *AI, int64_t rows
   const bool vec = (ld % 4 == 0) && ((reinterpret_cast<uintptr_t>(AI) & 15) == 0) &&
                    ((reinterpret_cast<uintptr_t>(AJ) & 15) == 0);
   dim3 grid((unsigned)tiles, (unsigned)splits);
-  syrk_simt_kernel<<<grid, NT, 0, stream>>>(AI, AJ, rows, nI, nJ, ld, G, ldg, (int)nbj, per, vec ? 1 : 0);
+  syrk_simt_kernel<<<grid, NT, 0, stream>>>(AI, AJ, rows, nI, nJ, ld, G, ldg, (int)nbj, per, vec ? 1 : 0, 0);
   TSVD_LAUNCHED();
   return TSVD_OK;
 }

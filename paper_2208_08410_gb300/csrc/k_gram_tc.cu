@@ -254,6 +254,50 @@ __global__ void __launch_bounds__(256) prep_kernel(const float *__restrict__ A, 
   }
 }
 
+// The same rounding (+ split) for an operand whose contraction index is
+// already contiguous: At[c][r] = round(X[r][c]) with X[r][c] = A[c ld + r]
+// (the column block of a wide A, whose Gram A A^T is Eq. 3's).  No transpose:
+// each thread reads and writes four consecutive r of one row c; r in
+// [rows, Kp) is the zero pad.
+template <int PREC>
+__global__ void __launch_bounds__(256) prep_rows_kernel(const float *__restrict__ A, int64_t rows, int64_t n,
+                                                        int64_t ld, void *__restrict__ hi_, void *__restrict__ lo_,
+                                                        int64_t Kp, int vec) {
+  const int64_t q4 = Kp / 4, total = n * q4;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t c = i / q4, r = (i % q4) * 4;
+    const float *src = A + c * ld + r;
+    float x[4];
+    if (vec && r + 3 < rows) {
+      const float4 t = __ldg(reinterpret_cast<const float4 *>(src));
+      x[0] = t.x; x[1] = t.y; x[2] = t.z; x[3] = t.w;
+    } else {
+#pragma unroll
+      for (int j = 0; j < 4; ++j) x[j] = r + j < rows ? __ldg(src + j) : 0.f;
+    }
+    if (PREC == TSVD_GRAM_BF16X3) {
+      uint16_t h[4], l[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        h[j] = bf16_rne_bits(x[j]);
+        l[j] = bf16_rne_bits(x[j] - bf16_bits_value(h[j]));  // x - h is exact
+      }
+      *reinterpret_cast<uint2 *>(static_cast<uint16_t *>(hi_) + c * Kp + r) =
+          make_uint2((uint32_t)h[0] | ((uint32_t)h[1] << 16), (uint32_t)h[2] | ((uint32_t)h[3] << 16));
+      *reinterpret_cast<uint2 *>(static_cast<uint16_t *>(lo_) + c * Kp + r) =
+          make_uint2((uint32_t)l[0] | ((uint32_t)l[1] << 16), (uint32_t)l[2] | ((uint32_t)l[3] << 16));
+    } else {
+      float h[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) h[j] = tf32_rne(x[j]);
+      *reinterpret_cast<float4 *>(static_cast<float *>(hi_) + c * Kp + r) = make_float4(h[0], h[1], h[2], h[3]);
+      if (PREC == TSVD_GRAM_TF32X3)
+        *reinterpret_cast<float4 *>(static_cast<float *>(lo_) + c * Kp + r) =
+            make_float4(tf32_rne(x[0] - h[0]), tf32_rne(x[1] - h[1]), tf32_rne(x[2] - h[2]), tf32_rne(x[3] - h[3]));
+    }
+  }
+}
+
 // ---------------------------------------------------------------- syrk kernel
 struct TcArgs {
   double *G;
@@ -634,6 +678,28 @@ tsvd_status run_syrk(const TcLayout &L, const TcArgs &a0, int precision, int sms
 }
 
 }  // namespace
+
+tsvd_status launch_gram_tc_t(const float *A, int64_t rows, int64_t n, int64_t ld, double *G, int precision,
+                             void *scratch, size_t scratch_bytes, cudaStream_t stream, cudaEvent_t ev0,
+                             cudaEvent_t ev1, bool reset_status) {
+  if (rows <= 0) return TSVD_OK;
+  DeviceInfo di;
+  TSVD_TRY(device_info(&di));
+  if (di.cc_major != 10) return TSVD_EUNSUPPORTED;
+  TcLayout L;
+  TSVD_TRY(tc_layout(rows, n, precision, scratch, scratch_bytes, &L));
+  const int vec = (ld % 4 == 0) && ((reinterpret_cast<uintptr_t>(A) & 15) == 0);
+  const int64_t total = n * (L.Kp / 4);
+  const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(total, 256), (int64_t)di.sms * 16));
+  if (precision == TSVD_GRAM_BF16X3)
+    prep_rows_kernel<TSVD_GRAM_BF16X3><<<grid, 256, 0, stream>>>(A, rows, n, ld, L.hi, L.lo, L.Kp, vec);
+  else if (precision == TSVD_GRAM_TF32X3)
+    prep_rows_kernel<TSVD_GRAM_TF32X3><<<grid, 256, 0, stream>>>(A, rows, n, ld, L.hi, L.lo, L.Kp, vec);
+  else
+    prep_rows_kernel<TSVD_GRAM_TF32><<<grid, 256, 0, stream>>>(A, rows, n, ld, L.hi, L.lo, L.Kp, vec);
+  TSVD_LAUNCHED();
+  return launch_gram_tc_syrk(rows, n, G, precision, scratch, scratch_bytes, stream, ev0, ev1, reset_status);
+}
 
 tsvd_status launch_gram_tc_prep(const float *A, int64_t rows, int64_t n, int64_t ld, int precision, void *scratch,
                                 size_t scratch_bytes, cudaStream_t stream) {

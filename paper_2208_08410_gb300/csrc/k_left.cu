@@ -262,7 +262,71 @@ tsvd_status encode_2d(CUtensorMap *map, const float *base, int64_t inner, int64_
   return r == CUDA_SUCCESS ? TSVD_OK : TSVD_ECUDA;
 }
 
+// The other factor of a wide A (Eq. 3: the power method found the left
+// vectors U, then V = A^T U Sigma^-1, Alg. 1 l.15-17) for a block of its
+// columns: V[j][l] = sum_i A[i][j] U[i][l] / sigma_l for the block's K
+// columns j, over the d rows i.  One thread per column (the loads of A along
+// a row are coalesced across the warp); U is staged 32 rows at a time in
+// shared memory, row-major, and read as broadcasts.
+constexpr int kLtRows = 32;
+constexpr int kLtMaxK = 32;
+
+__global__ void __launch_bounds__(256) left_trans_kernel(const float *__restrict__ A, int64_t K, int64_t d, int64_t ld,
+                                                         const float *__restrict__ U, int64_t ldu, int k,
+                                                         const double *__restrict__ sigma, float *__restrict__ V,
+                                                         int64_t ldv) {
+  __shared__ __align__(16) float Us[kLtRows][kLtMaxK];
+  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  float acc[kLtMaxK];
+#pragma unroll
+  for (int l = 0; l < kLtMaxK; ++l) acc[l] = 0.f;
+  for (int64_t i0 = 0; i0 < d; i0 += kLtRows) {
+    __syncthreads();
+    for (int e = threadIdx.x; e < kLtRows * kLtMaxK; e += blockDim.x) {
+      const int ii = e / kLtMaxK, l = e % kLtMaxK;
+      Us[ii][l] = (i0 + ii < d && l < k) ? __ldg(U + (i0 + ii) + (int64_t)l * ldu) : 0.f;
+    }
+    __syncthreads();
+    if (j < K) {
+      const int64_t nr = min((int64_t)kLtRows, d - i0);
+      for (int64_t ii = 0; ii < nr; ++ii) {
+        const float a = __ldg(A + (i0 + ii) * ld + j);
+        const float4 *u4 = reinterpret_cast<const float4 *>(Us[ii]);
+#pragma unroll
+        for (int q = 0; q < kLtMaxK / 4; ++q) {
+          const float4 u = u4[q];
+          acc[4 * q] = fmaf(a, u.x, acc[4 * q]);
+          acc[4 * q + 1] = fmaf(a, u.y, acc[4 * q + 1]);
+          acc[4 * q + 2] = fmaf(a, u.z, acc[4 * q + 2]);
+          acc[4 * q + 3] = fmaf(a, u.w, acc[4 * q + 3]);
+        }
+      }
+    }
+  }
+  if (j < K) {
+#pragma unroll
+    for (int l = 0; l < kLtMaxK; ++l) {
+      if (l < k) {
+        const double s = __ldg(sigma + l);
+        V[j + (int64_t)l * ldv] = s > 0.0 ? (float)((double)acc[l] / s) : 0.f;
+      }
+    }
+  }
+}
+
 }  // namespace
+
+tsvd_status launch_left_trans(const float *A, int64_t K, int64_t d, int64_t ld, const float *U, int64_t ldu,
+                              int64_t k, const double *sigma, float *V, int64_t ldv, cudaStream_t stream) {
+  if (K <= 0 || k <= 0) return TSVD_OK;
+  for (int64_t l0 = 0; l0 < k; l0 += kLtMaxK) {
+    const int kk = (int)std::min<int64_t>(kLtMaxK, k - l0);
+    left_trans_kernel<<<(unsigned)ceil_div(K, 256), 256, 0, stream>>>(A, K, d, ld, U + l0 * ldu, ldu, kk, sigma + l0,
+                                                                    V + l0 * ldv, ldv);
+    TSVD_LAUNCHED();
+  }
+  return TSVD_OK;
+}
 
 tsvd_status launch_left_dense(const float *A, int64_t rows, int64_t n, int64_t ld, const float *V,
                               int64_t ldv, int64_t k, const double *sigma, float *U, int64_t ldu,

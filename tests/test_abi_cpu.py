@@ -86,7 +86,9 @@ def test_plan_validation_dense(lib):
     d2.ld = 10
     assert _plan(d2, 5, 1e-6)[0] == B.TSVD_EINVAL
     wide, keep3 = _dense_desc(20, 100)
-    assert _plan(wide, 5, 1e-6)[0] == B.TSVD_EUNSUPPORTED  # the m < n branch is not built
+    assert _plan(wide, 5, 1e-6)[0] == B.TSVD_OK  # m < n: Eq. 3
+    assert _plan(wide, 21, 1e-6)[0] == B.TSVD_EINVAL  # k <= min(m, n)
+    assert _plan(wide, 5, 1e-6, _opts(gram_tile=256))[0] == B.TSVD_EUNSUPPORTED  # no column panels of a wide A
     d3, keep4 = _dense_desc(100, 20)
     d3.m = 0
     assert _plan(d3, 1, 1e-6)[0] == B.TSVD_EINVAL

@@ -390,6 +390,41 @@ def test_tsvd_orthogonal_batching_matches_oracle(n, bs, prec, where, budget):
         assert np.max(np.abs(np.asarray(r.V[:, l], dtype=np.float64) - o.V[:, l])) < 1e-4
 
 
+# wide A (m < n, Eq. 3): the Gram is A A^T over column blocks, U from the power method,
+# V = A^T U Sigma^-1 from one more pass.  m, n, precision, where A lives, power kernel
+WIDE_CASES = [
+    (300, 5000, B.TSVD_GRAM_FP32, "device", B.TSVD_POWER_CLUSTER),
+    (300, 5000, B.TSVD_GRAM_TF32X3, "resident", B.TSVD_POWER_GRID),
+    (1000, 3001, B.TSVD_GRAM_FP32, "stream", B.TSVD_POWER_AUTO),
+    (1000, 3001, B.TSVD_GRAM_TF32X3, "stream", B.TSVD_POWER_AUTO),
+    (777, 4100, B.TSVD_GRAM_BF16X3, "device", B.TSVD_POWER_GRID),
+]
+
+
+@pytest.mark.parametrize("m,n,prec,where,pk", WIDE_CASES)
+def test_tsvd_wide_matches_oracle(m, n, prec, where, pk):
+    k, eps = 8, 1e-10
+    inp = synth.dense_prescribed(m, n, synth.spectrum_geometric(m, 0.74), 1e-7, seed=m + n)
+    A = inp["A"]
+    x = synth.start_normals(m, k, seed=6)  # start vectors of the left (power) side
+    o = ref.tsvd_dense(A, k, eps, x_start=x, sign_convention=True)
+    kw = dict(power_kernel=pk, precision=prec)
+    if where == "device":
+        Ain = torch.from_numpy(A).cuda()
+    else:
+        Ain = A
+        if where == "stream":
+            kw.update(force_stream=True, block_rows=700, n_buffers=3)
+    r = tsvd(Ain, k, eps, start_draws=x, iters_override=o.iters, sign_convention=True, **kw)
+    assert r.iters == o.iters
+    if where == "stream":
+        assert r.report["mode"] == 2 and r.report["n_blocks"] == -(-n // 704)
+    gapped = ref.gapped_indices(o.sigma ** 2, k)
+    _compare(r, o, k, gapped=gapped)
+    for l in gapped:  # the power vectors are U here, fixed by the sign convention
+        assert np.max(np.abs(np.asarray(r.U[:, l], dtype=np.float64) - o.U[:, l])) < 1e-4
+
+
 def test_tsvd_builtin_start_vectors_match_oracle_generator():
     m, n, k, eps = 1500, 120, 5, 1e-8
     inp = synth.dense_prescribed(m, n, synth.spectrum_geometric(n, 0.75), 1e-6, seed=4)
