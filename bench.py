@@ -716,6 +716,7 @@ def tiled_workload(args):
 
 
 ENVELOPE = 0.1  # sigma_i / sigma_0 down to which an FP32-accumulated Gram resolves sigma to 1e-5
+SP_EPS, SP_MAX_ITER = 1e-6, 200  # sparse serving requests: the out-of-core CSR config's eps, capped applications
 
 
 def serve_workload(args):
@@ -747,13 +748,21 @@ def serve_workload(args):
         pool.append(a)
     torch.cuda.empty_cache()
     gen_s = time.time() - t0
+    # sparse requests (a share of the mix): square CSR, m = n log-uniform, density 1e-4
+    n_sp_pool = max(4, n_pool // 8) if args.csr_share > 0 else 0
+    sp_shapes = synth.serving_sparse_shapes(n_sp_pool, seed=13)
+    sp_pool = [synth.csr_uniform(sh["m"], sh["n"], sh["nnz_per_row"], seed=500 + i) for i, sh in enumerate(sp_shapes)]
     g = np.random.default_rng(12)
     arrivals = np.cumsum(g.exponential(1.0 / rate, n_req))
     picks = g.integers(0, n_pool, n_req)
     ks = np.array([min(int(k), min(shapes[p]["m"], shapes[p]["n"]), shapes[p]["rank"])
                    for p, k in zip(picks, g.integers(4, 33, n_req))])
-    m_max = max(sh["m"] for sh in shapes)
-    n_max = max(sh["n"] for sh in shapes)
+    is_sp = g.random(n_req) < args.csr_share if n_sp_pool else np.zeros(n_req, dtype=bool)
+    sp_picks = g.integers(0, max(n_sp_pool, 1), n_req)
+    for i in np.nonzero(is_sp)[0]:
+        ks[i] = min(int(g.integers(4, 33)), sp_shapes[sp_picks[i]]["m"])
+    m_max = max([sh["m"] for sh in shapes] + [sh["m"] for sh in sp_shapes])
+    n_max = max([sh["n"] for sh in shapes] + [sh["n"] for sh in sp_shapes])
     slots = 768
     outU = pinned_array((slots, 32 * m_max), np.float32)
     outV = pinned_array((slots, 32 * n_max), np.float32)
@@ -773,24 +782,33 @@ def serve_workload(args):
         sub_t = np.zeros(n_req)
         status = np.zeros(n_req, dtype=np.int64)
 
+        # several collectors, each waiting on the next submitted ticket, so one slow request
+        # holds back one collector (and one output slot), not every completion behind it
+        n_coll = 8
+
         def collector():
-            for _ in range(n_req):
-                i, t, sl = recs.get()
+            while True:
+                item = recs.get()
+                if item is None:
+                    return
+                i, t, sl = item
                 st, info = server.wait(t, 600.0)
                 p, k = picks[i], ks[i]
-                sig = outS[sl, :k].copy()
-                truth = shapes[p]["rho"] ** np.arange(k)
-                rel = np.abs(sig - truth) / truth
-                errs[i] = float(np.max(rel))
-                env = truth >= ENVELOPE
-                errs_env[i] = float(np.max(rel[env])) if env.any() else 0.0
+                if not is_sp[i]:
+                    sig = outS[sl, :k].copy()
+                    truth = shapes[p]["rho"] ** np.arange(k)
+                    rel = np.abs(sig - truth) / truth
+                    errs[i] = float(np.max(rel))
+                    env = truth >= ENVELOPE
+                    errs_env[i] = float(np.max(rel[env])) if env.any() else 0.0
                 lat[i] = info["done_s"] - info["submit_s"]
                 serv[i] = info["done_s"] - info["launch_s"]
                 apps[i] = info["applications"]
                 done_t[i], sub_t[i], status[i] = info["done_s"], info["submit_s"], st
                 free.put(sl)
-        th = threading.Thread(target=collector)
-        th.start()
+        ths = [threading.Thread(target=collector) for _ in range(n_coll)]
+        for th in ths:
+            th.start()
         start = time.perf_counter()
         for i in range(n_req):
             if timed_arrivals:
@@ -798,29 +816,52 @@ def serve_workload(args):
                 if delay > 0:
                     time.sleep(delay)
             sl = free.get()
-            p, k = picks[i], int(ks[i])
-            m, n = shapes[p]["m"], shapes[p]["n"]
-            t = server.submit(pool[p], k, eps, outU[sl, :m * k], outS[sl, :k], outV[sl, :n * k], seed=i)
+            k = int(ks[i])
+            if is_sp[i]:
+                csr = sp_pool[sp_picks[i]]
+                m, n = csr["m"], csr["n"]
+                t = server.submit_csr(csr, k, SP_EPS, outU[sl, :m * k], outS[sl, :k], outV[sl, :n * k],
+                                      max_iter=SP_MAX_ITER, seed=i)
+            else:
+                p = picks[i]
+                m, n = shapes[p]["m"], shapes[p]["n"]
+                t = server.submit(pool[p], k, eps, outU[sl, :m * k], outS[sl, :k], outV[sl, :n * k], seed=i)
             recs.put((i, t, sl))
-        th.join()
+        for _ in range(n_coll):
+            recs.put(None)
+        for th in ths:
+            th.join()
         span = float(done_t.max() - sub_t.min())
         dims = np.array([min(shapes[p]["m"], shapes[p]["n"]) for p in picks])
         by_dim = {}
+        sparse = None
+        if is_sp.any():
+            sp = is_sp
+            sparse = {"requests": int(sp.sum()), "p50_ms": round(float(np.percentile(lat[sp], 50)) * 1e3, 2),
+                      "p99_ms": round(float(np.percentile(lat[sp], 99)) * 1e3, 2),
+                      "mean_service_ms": round(float(serv[sp].mean()) * 1e3, 2),
+                      "mean_applications": round(float(apps[sp].mean()), 1),
+                      "status_counts": {B.STATUS_NAMES[int(c)]: int((status[sp] == c).sum())
+                                        for c in np.unique(status[sp])}}
         for lo, hi in ((0, 64), (64, 128), (128, 256), (256, 512), (512, 1024), (1024, 2048)):
-            sel = (dims > lo) & (dims <= hi)
+            sel = (dims > lo) & (dims <= hi) & ~is_sp
             if sel.any():
                 by_dim[f"d<={hi}"] = {"requests": int(sel.sum()),
                                       "mean_service_ms": round(float(serv[sel].mean()) * 1e3, 2),
                                       "p99_service_ms": round(float(np.percentile(serv[sel], 99)) * 1e3, 2),
                                       "mean_applications": round(float(apps[sel].mean()), 1)}
+        dn = ~is_sp
         return {"p50_ms": round(float(np.percentile(lat, 50)) * 1e3, 3),
                 "p99_ms": round(float(np.percentile(lat, 99)) * 1e3, 3),
+                "dense_p50_ms": round(float(np.percentile(lat[dn], 50)) * 1e3, 3),
+                "dense_p99_ms": round(float(np.percentile(lat[dn], 99)) * 1e3, 3),
                 "mean_ms": round(float(lat.mean()) * 1e3, 3), "solves_per_s": round(n_req / span, 1),
                 "span_s": round(span, 3),
-                "sigma_max_rel_err_in_envelope": float("%.3g" % errs_env.max()),
-                "frac_requests_sigma_err_le_1e-5_in_envelope": float(np.mean(errs_env <= 1e-5)),
-                "sigma_max_rel_err_all_triplets": float("%.3g" % errs.max()),
-                "frac_requests_sigma_err_le_1e-5_all_triplets": float(np.mean(errs <= 1e-5)),
+                "sigma_max_rel_err_in_envelope": float("%.3g" % errs_env[dn].max()),
+                "frac_requests_sigma_err_le_1e-5_in_envelope": float(np.mean(errs_env[dn] <= 1e-5)),
+                "sigma_max_rel_err_all_triplets": float("%.3g" % errs[dn].max()),
+                "frac_requests_sigma_err_le_1e-5_all_triplets": float(np.mean(errs[dn] <= 1e-5)),
+                "sparse": sparse,
                 "status_counts": {B.STATUS_NAMES[int(c)]: int((status == c).sum()) for c in np.unique(status)},
                 "by_dim": by_dim}
 
@@ -839,7 +880,7 @@ def serve_workload(args):
     for i in range(min(args.baseline_requests, n_req)):
         p, k = picks[i], int(ks[i])
         m, n = shapes[p]["m"], shapes[p]["n"]
-        if m < n:
+        if m < n or is_sp[i]:
             continue
         torch.cuda.synchronize()
         ts = time.perf_counter()
@@ -854,9 +895,11 @@ def serve_workload(args):
     line = {"metric": "serve p50/p99 latency (2,000 req/s Poisson), sigma err <= 1e-5 inside the FP32-Gram envelope",
             "value": timed["p99_ms"], "unit": "ms", "n_gpus": 1, "steps": 1, "warmup": 0,
             "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": f"{n_req} dense t-SVD requests, Poisson {rate} req/s, pool of {n_pool}: "
+            "config": {"workload": f"{n_req} t-SVD requests, Poisson {rate} req/s; dense from a pool of {n_pool}: "
                                    "m logU[512,65536], n logU[64,2048], sigma_i=rho^i, rho~U(0.5,0.95), "
-                                   "k~U{4..32}, eps=1e-8", "requests": n_req, "rate": rate, "pool": n_pool,
+                                   f"k~U{{4..32}}, eps=1e-8; {args.csr_share:.0%} CSR from a pool of {n_sp_pool}: "
+                                   f"m=n logU[2^14,2^16], density 1e-4, eps={SP_EPS}, max_iter {SP_MAX_ITER}",
+                       "requests": n_req, "sparse_requests": int(is_sp.sum()), "rate": rate, "pool": n_pool,
                        "pool_bytes": int(sum(a.nbytes for a in pool)), "device_budget_gib": args.serve_budget},
             "accuracy_scope": f"sigma graded against the closed form rho^i on the triplets with rho^i >= {ENVELOPE} "
                               "(an FP32-accumulated Gram moves lambda_i by ~1e-7 lambda_0, i.e. sigma_i by "
@@ -1062,6 +1105,7 @@ def main():
     ap.add_argument("--rate", type=float, default=2000.0)
     ap.add_argument("--serve-budget", type=int, default=48, help="server device budget, GiB")
     ap.add_argument("--baseline-requests", type=int, default=200)
+    ap.add_argument("--csr-share", type=float, default=0.1, help="serving: fraction of sparse requests")
     ap.add_argument("--csr-iters", type=int, default=10)
     ap.add_argument("--sweep", action="store_true", help="CSR: out-of-memory sweep over n_b and q_s")
     args = ap.parse_args()

@@ -107,8 +107,8 @@ typedef struct {
   int32_t sign_convention;       /* 1: largest-|entry| of each v_l made positive */
   const int32_t *iters_override; /* host, k counts: exactly that many applications
                                     per triplet, convergence test off; or NULL */
-  const double *start_draws;     /* host, n x k column-major N(0,1) draws used as
-                                    x_l; NULL = the built-in Philox-4x32-10 stream */
+  const double *start_draws;     /* host, min(m,n) x k column-major N(0,1) draws used
+                                    as x_l; NULL = the built-in Philox-4x32-10 stream */
   uint64_t seed;                 /* seed of the built-in start-vector stream */
   int32_t out_location;          /* tsvd_location of the U, sigma, V outputs */
   int32_t force_stream;          /* 1: stream host A even when it would fit */
@@ -205,10 +205,16 @@ TSVD_API void tsvd_options_init(tsvd_options *opt);
  *                   copied into the plan
  *   workspace_bytes receives the device workspace size tsvd_factor needs
  *
+ * Dense A with m < n takes Eq. 3: the Gram matrix is A A^T (m x m), formed
+ * over column blocks of A (streamed from host memory as 2-D copies when A is
+ * there), the power method finds the left vectors U, and one more pass over
+ * A forms V = A^T U Sigma^-1 (Alg. 1 l.15-17).  start_draws then holds m x k
+ * draws, and the sign convention applies to U.
+ *
  * Errors: EINVAL (k out of range, eps not in (0,1), m or n <= 0, ld < n, bad
  * CSR: row_ptr not monotone, row_ptr[m] != nnz, a column outside [0,n)),
- * EUNSUPPORTED (m < n; dense n > 32768), EBUDGET (device_budget below the
- * minimum workspace), ENOMEM.
+ * EUNSUPPORTED (CSR with m < n; dense min(m, n) > 32768; gram_tile with
+ * m < n), EBUDGET (device_budget below the minimum workspace), ENOMEM.
  */
 TSVD_API tsvd_status tsvd_plan(tsvd_plan_t *out, const tsvd_matrix *A, int64_t k, double eps,
                       const tsvd_options *opt, size_t *workspace_bytes);
@@ -223,9 +229,10 @@ TSVD_API tsvd_status tsvd_plan(tsvd_plan_t *out, const tsvd_matrix *A, int64_t k
  *   stream     CUDA stream for the compute work (copies use the plan's own
  *              streams and are ordered with events)
  *   U          m x k FP32 column-major (host or device per opt.out_location),
- *              or NULL to skip the U pass
+ *              or NULL: for m >= n this skips the U pass; for m < n U holds
+ *              the power method's vectors and NULL only skips their copy
  *   sigma      k FP64 singular values in extraction order (not sorted)
- *   V          n x k FP32 column-major
+ *   V          n x k FP32 column-major (for m < n: the pass over A)
  *   report     optional
  *
  * Returns OK, ENOCONV / ERANK (outputs valid, flags in the report), or an
@@ -460,6 +467,23 @@ TSVD_API tsvd_status tsvd_server_submit(tsvd_server_t server, const float *A, in
                                         double eps, int32_t max_iter, uint64_t seed, int32_t sign_convention,
                                         const int32_t *iters_override, float *U, double *sigma, float *V,
                                         uint64_t *ticket);
+
+/*
+ * tsvd_server_submit_csr - queue a sparse t-SVD (CSR, m >= n) with the same
+ * arguments as tsvd_server_submit plus the CSR arrays (host memory: row_ptr
+ * m+1 int64, col_idx nnz int32, values nnz FP32, read until completion).
+ * Sparse requests do not join the dense waves: two worker threads run them
+ * one at a time each through tsvd_plan / tsvd_factor (the implicit operator
+ * A^T (A v), Alg. 4), with the workspace taken from the server's device
+ * budget (at most a quarter of it per request; beyond that the plan streams
+ * A in row blocks) and the results written straight into U, sigma and V.
+ * Dense waves keep running beside them.  Errors: EINVAL, EUNSUPPORTED (m < n).
+ */
+TSVD_API tsvd_status tsvd_server_submit_csr(tsvd_server_t server, const int64_t *row_ptr, const int32_t *col_idx,
+                                            const float *values, int64_t m, int64_t n, int64_t nnz, int32_t k,
+                                            double eps, int32_t max_iter, uint64_t seed, int32_t sign_convention,
+                                            const int32_t *iters_override, float *U, double *sigma, float *V,
+                                            uint64_t *ticket);
 
 /* Block until the request completes or timeout_s passes (< 0: no limit),
  * then copy its results into the caller's U, sigma, V.  Returns the

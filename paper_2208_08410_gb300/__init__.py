@@ -213,6 +213,24 @@ class Server:
         self._keep[t.value] = (A, U, sigma, V)
         return t.value
 
+    def submit_csr(self, csr: dict, k: int, eps: float, U, sigma, V, max_iter: int = 10000, seed: int = 0,
+                   sign_convention: bool = False, iters_override=None) -> int:
+        """A sparse request: csr = {"row_ptr", "col_idx", "values", "m", "n"} in host memory, kept
+        alive until the request completes."""
+        rp, ci, va = csr["row_ptr"], csr["col_idx"], csr["values"]
+        m, n = int(csr["m"]), int(csr["n"])
+        t = C.c_uint64()
+        ovr = None
+        if iters_override is not None:
+            ovr = np.ascontiguousarray(iters_override, dtype=np.int32)
+        B.check(self.lib.tsvd_server_submit_csr(self.handle, _ptr(rp), _ptr(ci), _ptr(va), m, n, int(va.shape[0]),
+                                                int(k), float(eps), int(max_iter), int(seed),
+                                                int(bool(sign_convention)), _ptr(ovr), _ptr(U), _ptr(sigma), _ptr(V),
+                                                C.byref(t)),
+                "tsvd_server_submit_csr")
+        self._keep[t.value] = (csr, U, sigma, V, ovr)
+        return t.value
+
     def wait(self, ticket: int, timeout_s: float = -1.0):
         info = B.tsvd_request_info()
         st = self.lib.tsvd_server_wait(self.handle, int(ticket), float(timeout_s), C.byref(info))

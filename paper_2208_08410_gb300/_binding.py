@@ -101,6 +101,8 @@ SIGNATURES = {
     "tsvd_server_create": (C.c_int, [C.POINTER(_P), C.POINTER(tsvd_server_options)]),
     "tsvd_server_submit": (C.c_int, [_P, _P, _I64, _I64, _I32, _D, _I32, C.c_uint64, _I32, _P, _P, _P, _P,
                                      C.POINTER(C.c_uint64)]),
+    "tsvd_server_submit_csr": (C.c_int, [_P, _P, _P, _P, _I64, _I64, _I64, _I32, _D, _I32, C.c_uint64, _I32, _P,
+                                         _P, _P, _P, C.POINTER(C.c_uint64)]),
     "tsvd_server_wait": (C.c_int, [_P, C.c_uint64, _D, C.POINTER(tsvd_request_info)]),
     "tsvd_server_get_stats": (C.c_int, [_P, C.POINTER(tsvd_server_stats)]),
     "tsvd_server_last_error": (C.c_char_p, [_P]),

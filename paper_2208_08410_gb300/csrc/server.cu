@@ -128,6 +128,11 @@ struct Request {
   double *sigma = nullptr;
   float *V = nullptr;
   std::vector<int32_t> iters;   // forced applications per triplet (empty: convergence test)
+  // a CSR request (host arrays, read until completion); runs on a sparse worker
+  bool csr = false;
+  const int64_t *row_ptr = nullptr;
+  const int32_t *col_idx = nullptr;
+  int64_t nnz = 0;
   size_t off = 0, bytes = 0;    // device arena region
   size_t soff = 0, sbytes = 0;  // staging region
   size_t out_off = 0;           // results within the device region (same layout as the staging)
@@ -230,6 +235,9 @@ struct tsvd_server_s {
   int64_t inflight = 0;                              // admitted and not completed
   bool stop = false;
   std::thread thr;
+  std::deque<tsvd::ReqPtr> csr_pending;              // sparse requests, run by the sparse workers
+  std::vector<std::thread> csr_workers;
+  std::condition_variable cv_csr;
   std::chrono::steady_clock::time_point t0;
   tsvd_server_stats stats{};
   std::string err;
@@ -616,6 +624,86 @@ tsvd_status time_power(tsvd_server_s *sv, int64_t d, int c, int nreq, int iters,
   return ls;
 }
 
+// A sparse request runs through the plan API on a stream of its worker: the
+// workspace comes from the server's device arena (first fit; the worker waits
+// while the arena is full), the outputs go straight into the caller's
+// buffers, and the request completes when tsvd_factor returns.  Dense waves
+// keep running on their own streams meanwhile.
+void csr_worker(tsvd_server_s *sv) {
+  cudaSetDevice(sv->device);
+  cudaStream_t st = nullptr;
+  if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) return;
+  std::unique_lock<std::mutex> lk(sv->mu);
+  while (true) {
+    sv->cv_csr.wait(lk, [&] { return sv->stop || !sv->csr_pending.empty(); });
+    if (sv->csr_pending.empty()) break;  // stop, nothing left
+    ReqPtr r = sv->csr_pending.front();
+    sv->csr_pending.pop_front();
+    r->rec.admit_s = sv->now();
+    lk.unlock();
+    tsvd_matrix A{};
+    A.kind = TSVD_CSR_F32_I32_I64;
+    A.location = TSVD_HOST;
+    A.m = r->m;
+    A.n = r->n;
+    A.values = r->A;
+    A.row_ptr = r->row_ptr;
+    A.col_idx = r->col_idx;
+    A.nnz = r->nnz;
+    tsvd_options opt;
+    tsvd_options_init(&opt);
+    opt.max_iter = r->max_iter;
+    opt.seed = r->seed;
+    opt.sign_convention = r->sign;
+    opt.iters_override = r->iters.empty() ? nullptr : r->iters.data();
+    opt.out_location = TSVD_HOST;
+    // at most a quarter of the arena per sparse request (the plan streams A beyond that)
+    opt.device_budget = std::max<size_t>(sv->arena.size / 4, (size_t)64 << 20);
+    tsvd_plan_t plan = nullptr;
+    size_t ws_bytes = 0;
+    tsvd_status st_r = tsvd_plan(&plan, &A, r->k, r->iters.empty() ? r->eps : 0.5, &opt, &ws_bytes);
+    size_t off = 0;
+    bool have = false;
+    if (st_r == TSVD_OK) {
+      lk.lock();
+      const auto deadline = std::chrono::steady_clock::now() + std::chrono::seconds(600);
+      while (!(have = sv->arena.alloc(std::max<size_t>(ws_bytes, 256), &off)) && !sv->stop) {
+        if (sv->cv_done.wait_until(lk, deadline) == std::cv_status::timeout) break;
+      }
+      lk.unlock();
+      if (!have) st_r = TSVD_EBUDGET;
+    }
+    tsvd_report rep{};
+    std::vector<int32_t> its((size_t)r->k, 0);
+    rep.iters = its.data();
+    if (st_r == TSVD_OK) {
+      r->rec.launch_s = sv->now();
+      st_r = tsvd_factor(plan, &A, sv->arena.base + off, ws_bytes, st, r->U, r->sigma, r->V, &rep);
+    }
+    if (plan) tsvd_destroy(plan);
+    lk.lock();
+    if (have) sv->arena.release(off, std::max<size_t>(ws_bytes, 256));
+    if (st_r != TSVD_OK && st_r != TSVD_ENOCONV && st_r != TSVD_ERANK)
+      sv->err = std::string("server: sparse request failed: ") + tsvd_status_string(st_r) + " " + tsvd_last_cuda_error();
+    r->rec.status = st_r;
+    r->rec.flags = rep.flags;
+    r->rec.applications = rep.applications;
+    r->rec.done_s = sv->now();
+    r->rec.cluster = 0;
+    r->rec.wave = -1;
+    r->done = true;
+    --sv->inflight;
+    if (st_r == TSVD_OK || st_r == TSVD_ENOCONV || st_r == TSVD_ERANK)
+      ++sv->stats.completed;
+    else
+      ++sv->stats.failed;
+    sv->cv_done.notify_all();
+  }
+  lk.unlock();
+  cudaStreamSynchronize(st);
+  cudaStreamDestroy(st);
+}
+
 }  // namespace
 }  // namespace tsvd
 
@@ -688,6 +776,7 @@ tsvd_status tsvd_server_create(tsvd_server_t *out, const tsvd_server_options *op
     }
   }
   sv->thr = std::thread(scheduler, sv);
+  for (int i = 0; i < 2; ++i) sv->csr_workers.emplace_back(csr_worker, sv);
   *out = sv;
   return TSVD_OK;
 }
@@ -730,6 +819,51 @@ tsvd_status tsvd_server_submit(tsvd_server_t sv, const float *A, int64_t m, int6
     *ticket = r->id;
   }
   sv->cv_work.notify_one();
+  return TSVD_OK;
+}
+
+tsvd_status tsvd_server_submit_csr(tsvd_server_t sv, const int64_t *row_ptr, const int32_t *col_idx,
+                                   const float *values, int64_t m, int64_t n, int64_t nnz, int32_t k, double eps,
+                                   int32_t max_iter, uint64_t seed, int32_t sign_convention,
+                                   const int32_t *iters_override, float *U, double *sigma, float *V,
+                                   uint64_t *ticket) {
+  if (!sv || !row_ptr || !U || !sigma || !V || !ticket || m <= 0 || n <= 0 || nnz < 0) return TSVD_EINVAL;
+  if (nnz > 0 && (!col_idx || !values)) return TSVD_EINVAL;
+  if (k < 1 || k > std::min(m, n)) return TSVD_EINVAL;
+  if (m < n) return TSVD_EUNSUPPORTED;  // the sparse path applies A^T (A v) on R^n
+  if (!iters_override && !(eps > 0.0 && eps < 1.0)) return TSVD_EINVAL;
+  if (iters_override)
+    for (int32_t l = 0; l < k; ++l)
+      if (iters_override[l] < 1) return TSVD_EINVAL;
+  auto r = std::make_shared<Request>();
+  r->csr = true;
+  r->A = values;
+  r->row_ptr = row_ptr;
+  r->col_idx = col_idx;
+  r->nnz = nnz;
+  r->m = m;
+  r->n = n;
+  r->k = k;
+  r->eps = eps;
+  r->max_iter = max_iter > 0 ? max_iter : 10000;
+  r->seed = seed;
+  r->sign = sign_convention ? 1 : 0;
+  r->U = U;
+  r->sigma = sigma;
+  r->V = V;
+  if (iters_override) r->iters.assign(iters_override, iters_override + k);
+  {
+    std::lock_guard<std::mutex> lk(sv->mu);
+    if (sv->stop) return TSVD_EINVAL;
+    r->id = sv->next_id++;
+    r->rec.submit_s = sv->now();
+    sv->table[r->id] = r;
+    sv->csr_pending.push_back(r);
+    ++sv->inflight;
+    ++sv->stats.submitted;
+    *ticket = r->id;
+  }
+  sv->cv_csr.notify_one();
   return TSVD_OK;
 }
 
@@ -848,8 +982,17 @@ void tsvd_server_destroy(tsvd_server_t sv) {
       r->done = true;
     }
     sv->pending.clear();
+    for (auto &r : sv->csr_pending) {
+      r->rec.status = TSVD_ECUDA;
+      r->done = true;
+      --sv->inflight;
+    }
+    sv->csr_pending.clear();
   }
   sv->cv_work.notify_all();
+  sv->cv_csr.notify_all();
+  for (auto &t : sv->csr_workers)
+    if (t.joinable()) t.join();
   if (sv->thr.joinable()) sv->thr.join();
   {
     std::lock_guard<std::mutex> lk(sv->mu);

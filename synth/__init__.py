@@ -309,6 +309,17 @@ def serving_shapes(count: int, seed: int, m_range=(512, 65536), n_range=(64, 204
     return out
 
 
+def serving_sparse_shapes(count: int, seed: int, dim_range=(1 << 14, 1 << 16), density: float = 1e-4) -> list:
+    """Square sparse requests of the serving mix: m = n log-uniform in
+    dim_range, density as given (entries per row = density * n)."""
+    g = _rng(seed, 708)
+    out = []
+    for _ in range(count):
+        m = int(round(math.exp(g.uniform(math.log(dim_range[0]), math.log(dim_range[1])))))
+        out.append({"m": m, "n": m, "nnz_per_row": density * m})
+    return out
+
+
 def serving_matrix_torch(shape: dict, seed: int, out=None, device="cuda"):
     """A = Q1 diag(rho^i) Q2^T (exact rank r, no noise) for one pool entry:
     Q1 (m x r) and Q2 (n x r) the Q factors of seeded Gaussians, formed on
@@ -320,8 +331,17 @@ def serving_matrix_torch(shape: dict, seed: int, out=None, device="cuda"):
     dev = torch.device(device)
     g = torch.Generator(device=dev)
     g.manual_seed(int(seed) * 1000003 + 97)
-    q1, _ = torch.linalg.qr(torch.randn((m, r), generator=g, device=dev, dtype=torch.float64))
-    q2, _ = torch.linalg.qr(torch.randn((n, r), generator=g, device=dev, dtype=torch.float64))
+
+    def orth(rows):
+        # CholeskyQR2 (two rounds): the r x r Cholesky factor and its inverse on
+        # the host, the tall products on the GPU (no device LAPACK needed)
+        q = torch.randn((rows, r), generator=g, device=dev, dtype=torch.float64)
+        for _ in range(2):
+            R = np.linalg.cholesky((q.T @ q).cpu().numpy()).T
+            q = q @ torch.as_tensor(np.linalg.inv(R), device=dev)
+        return q
+    q1 = orth(m)
+    q2 = orth(n)
     sig = torch.as_tensor(rho ** np.arange(r, dtype=np.float64), device=dev)
     A = ((q1 * sig[None, :]) @ q2.T).to(torch.float32)
     if out is not None:

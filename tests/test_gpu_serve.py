@@ -168,3 +168,43 @@ def test_server_autotune_table():
             assert c in (1, 2, 4, 8)
     finally:
         sv.close()
+
+
+def test_server_sparse_requests_beside_dense_ones():
+    """CSR requests run on the server's sparse workers (plan API, workspace from
+    the server's budget) while dense waves run; each follows the oracle's
+    trajectory (forced counts, the seed's Philox start draws)."""
+    B.load()
+    pool = Pool()
+    sv = Server(device_budget=4 << 30, n_streams=2)
+    try:
+        sparse = []
+        for i, (m, n, per_row, k) in enumerate([(4000, 3000, 20.0, 5), (6000, 6000, 8.0, 4), (2500, 700, 40.0, 6)]):
+            csr = synth.csr_uniform(m, n, per_row, seed=50 + i)
+            o = ref.tsvd_csr(csr, k, 1e-6, seed=9 + i)
+            U = pool.arr((k, m), np.float32)
+            s_ = pool.arr((k,), np.float64)
+            V = pool.arr((k, n), np.float32)
+            t = sv.submit_csr(csr, k, 1e-6, U, s_, V, seed=9 + i, iters_override=o.iters)
+            sparse.append((t, csr, k, U, s_, V, o))
+        dense = []
+        for i, (m, n, k, rho) in enumerate(CASES[:4]):
+            A = _request(pool, m, n, rho, seed=300 + i)
+            U, s_, V = _outputs(pool, m, n, k)
+            o = ref.tsvd_dense(A, k, 1e-10, seed=40 + i)
+            dense.append((sv.submit(A, k, 1e-10, U, s_, V, seed=40 + i, iters_override=o.iters), k, s_, o))
+        for t, csr, k, U, s_, V, o in sparse:
+            st, info = sv.wait(t, 300.0)
+            assert st == B.TSVD_OK, (st, sv.last_error())
+            assert info["applications"] == sum(o.iters)
+            assert np.max(np.abs(s_ - o.sigma) / o.sigma) <= 1e-5
+            for l in ref.gapped_indices(o.sigma ** 2, k):
+                assert ref.vector_angle(V[l].astype(np.float64), o.V[:, l]) <= 1e-4
+                assert ref.vector_angle(U[l].astype(np.float64), o.U[:, l]) <= 1e-4
+        for t, k, s_, o in dense:
+            st, _ = sv.wait(t, 120.0)
+            assert st == B.TSVD_OK and np.max(np.abs(s_ - o.sigma) / o.sigma) <= 1e-5
+        assert sv.stats()["completed"] == len(sparse) + len(dense)
+    finally:
+        sv.close()
+        pool.close()
