@@ -472,7 +472,7 @@ TSVD_API tsvd_status tsvd_server_submit(tsvd_server_t server, const float *A, in
  * tsvd_server_submit_csr - queue a sparse t-SVD (CSR, m >= n) with the same
  * arguments as tsvd_server_submit plus the CSR arrays (host memory: row_ptr
  * m+1 int64, col_idx nnz int32, values nnz FP32, read until completion).
- * Sparse requests do not join the dense waves: two worker threads run them
+ * Sparse requests do not join the dense waves: eight worker threads run them
  * one at a time each through tsvd_plan / tsvd_factor (the implicit operator
  * A^T (A v), Alg. 4), with the workspace taken from the server's device
  * budget (at most a quarter of it per request; beyond that the plan streams

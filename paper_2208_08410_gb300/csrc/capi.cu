@@ -1174,10 +1174,16 @@ struct ExplicitLoop {
 // w -= V (sigma^2 . V^T v) (Eq. 2) in the vector kernels; the convergence
 // test runs on the device and the host reads its decision after every
 // application.  sigma_l^2 = v_l^T A^T A v_l from one more application.
+// `batch` applications are queued per host round trip: an application that
+// finds the triplet already stopped by an earlier one in the same batch
+// changes nothing (the decision and the next-iterate kernels test the stop
+// word), so the trajectory is the same as with one round trip per
+// application; the queued operator applications still run (they only write
+// scratch), so batching is for cheap operators.
 tsvd_status explicit_power(Run &r, ExplicitLoop &L,
                            const std::function<tsvd_status(const float *, float *, double *, int)> &apply,
                            const std::function<tsvd_status()> &after_sync, float *V_out, int *flags_out,
-                           int64_t *apps_out, tsvd_report *rep) {
+                           int64_t *apps_out, tsvd_report *rep, int batch = 1) {
   tsvd_plan_s *p = r.p;
   const int64_t n = p->n, k = p->k;
   float *v = L.v, *vn = L.vn;
@@ -1200,19 +1206,28 @@ tsvd_status explicit_power(Run &r, ExplicitLoop &L,
     const double rank_scale = l == 0 ? 1.0 : hsig2[0];
     const int ovr = p->iters_override.empty() ? 0 : p->iters_override[l];
     int32_t h[4] = {0, 0, 0, 0};
+    // application e (1-based) reads buf[(e - 1) & 1] and writes buf[e & 1]
+    float *buf[2] = {v, vn};
+    int64_t e = 0;
     for (;;) {
-      TSVD_CUDA(cudaMemsetAsync(L.w, 0, (size_t)n * 4, r.cs));
-      TSVD_CUDA(cudaMemsetAsync(L.ss, 0, 8, r.cs));
-      TSVD_TRY(apply(v, L.w, L.ss, 1));
-      TSVD_TRY(launch_vec_deflate_step(n, L.Vr, k, L.sig2, l, v, L.w, vn, p->eps, p->opt.max_iter, ovr, rank_scale,
-                                       sc, 0, r.cs));
+      for (int b = 0; b < std::max(batch, 1); ++b) {
+        ++e;
+        float *in = buf[(e - 1) & 1], *out = buf[e & 1];
+        TSVD_CUDA(cudaMemsetAsync(L.w, 0, (size_t)n * 4, r.cs));
+        TSVD_CUDA(cudaMemsetAsync(L.ss, 0, 8, r.cs));
+        TSVD_TRY(apply(in, L.w, L.ss, 1));
+        TSVD_TRY(launch_vec_deflate_step(n, L.Vr, k, L.sig2, l, in, L.w, out, p->eps, p->opt.max_iter, ovr,
+                                         rank_scale, sc, 0, r.cs, (int)e));
+      }
       TSVD_CUDA(cudaMemcpyAsync(h, sc.info, 16, cudaMemcpyDeviceToHost, r.cs));
       TSVD_CUDA(cudaStreamSynchronize(r.cs));
       TSVD_TRY(after_sync());
-      if (h[1] == 2) break;  // rank: keep v (= v0 of this step)
-      std::swap(v, vn);
-      if (h[2]) break;
+      if (h[3] != 0) break;  // stopped at application h[3]: converged, forced count reached, or rank
     }
+    // rank: keep v0 of the stopping application; otherwise its output
+    const int64_t stop = h[3];
+    v = h[1] == 2 ? buf[(stop - 1) & 1] : buf[stop & 1];
+    vn = v == buf[0] ? buf[1] : buf[0];
     if (h[1] == 2) {
       // v := v0 orthogonalised against earlier vectors, twice; sigma_l = 0
       for (int pass = 0; pass < 2; ++pass) {
@@ -1495,9 +1510,12 @@ tsvd_status factor_csr(Run &r, float *U, double *sigma_out, float *V_out, tsvd_r
   int flags = 0;
   int64_t apps = 0;
   const bool host_out = p->opt.out_location == TSVD_HOST;
+  // small operators: 16 applications per host round trip (the round trip dominates them);
+  // large ones, or per-application kernel timing: one
+  const int batch = (p->opt.time_kernels || p->nnz >= ((int64_t)1 << 25)) ? 1 : 16;
   TSVD_TRY(explicit_power(
       r, L, [&](const float *vv, float *ww, double *s2, int scatter) { return csr_apply(r, bnd, vv, ww, s2, scatter); },
-      [&]() { return csr_kernel_time(r); }, V_out, &flags, &apps, rep));
+      [&]() { return csr_kernel_time(r); }, V_out, &flags, &apps, rep, batch));
   TSVD_TRY(launch_sigma_from_sigma2(sig2, sigma, k, r.cs));
   TSVD_CUDA(cudaEventRecord(p->ev_t[2], r.cs));
   if (U) {

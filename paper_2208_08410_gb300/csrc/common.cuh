@@ -259,7 +259,7 @@ tsvd_status launch_vec_normalize_f64_to_f32(const double *x, float *v, int64_t n
 tsvd_status launch_vec_deflate_step(int64_t n, const float *Vr, int64_t ldk, const double *sig2,
                                     int64_t l, const float *v, float *w, float *vnext, double eps,
                                     int max_iter, int iters_override, double scale, VecScratch sc,
-                                    int orth_only, cudaStream_t stream);
+                                    int orth_only, cudaStream_t stream, int expect = 0);
 tsvd_status launch_vec_store_column(int64_t n, const float *v, float *Vr, int64_t ldk, int64_t l,
                                     int sign_convention, VecScratch sc, cudaStream_t stream);
 

@@ -177,7 +177,7 @@ struct PowerSmem {
 __device__ __forceinline__ int64_t pad4(int64_t x) { return (x + 3) & ~int64_t(3); }
 
 // ---------------------------------------------------------------- grouped power
-__global__ void __launch_bounds__(kSrvPowerThreads, 1) srv_power_kernel(const SrvReq *__restrict__ reqs) {
+__global__ void __launch_bounds__(kSrvPowerThreads, 2) srv_power_kernel(const SrvReq *__restrict__ reqs) {
   extern __shared__ __align__(16) unsigned char srv_smem[];
   __shared__ double wred[3 * (kSrvPowerThreads / 32)];
   __shared__ double red[33];

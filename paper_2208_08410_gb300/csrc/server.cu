@@ -776,7 +776,7 @@ tsvd_status tsvd_server_create(tsvd_server_t *out, const tsvd_server_options *op
     }
   }
   sv->thr = std::thread(scheduler, sv);
-  for (int i = 0; i < 2; ++i) sv->csr_workers.emplace_back(csr_worker, sv);
+  for (int i = 0; i < 8; ++i) sv->csr_workers.emplace_back(csr_worker, sv);
   *out = sv;
   return TSVD_OK;
 }
