@@ -45,6 +45,7 @@ tsvd_status ensure_dynamic_smem(const void *func, size_t bytes) {
   return TSVD_OK;
 }
 void count_launch() { ++g_launches; }
+void count_launches(int64_t n) { g_launches += n; }
 int64_t launches_so_far() { return g_launches; }
 
 tsvd_status device_info(DeviceInfo *out) {
@@ -133,6 +134,10 @@ struct tsvd_plan_s {
   int device = -1;
   cudaStream_t copy_stream = nullptr, d2h_stream = nullptr;
   cudaStream_t copy_stream2 = nullptr;  // second half of every block copy (a second copy engine)
+  // the explicit power loop's stream when it replays graphs (a capture cannot use the
+  // legacy default stream a caller may pass), forked from and joined to the caller's
+  cudaStream_t aux_stream = nullptr;
+  cudaEvent_t ev_aux = nullptr;
   cudaEvent_t ev_csplit = nullptr, ev_cjoin = nullptr;
   std::vector<cudaEvent_t> ev_ready, ev_free;
   cudaEvent_t ev_u_ready[2] = {nullptr, nullptr}, ev_u_free[2] = {nullptr, nullptr};
@@ -573,6 +578,8 @@ void tsvd_destroy(tsvd_plan_t p) {
     for (auto e : p->ev_c) cudaEventDestroy(e);
     if (p->copy_stream) cudaStreamDestroy(p->copy_stream);
     if (p->copy_stream2) cudaStreamDestroy(p->copy_stream2);
+    if (p->aux_stream) cudaStreamDestroy(p->aux_stream);
+    if (p->ev_aux) cudaEventDestroy(p->ev_aux);
     if (p->ev_csplit) cudaEventDestroy(p->ev_csplit);
     if (p->ev_cjoin) cudaEventDestroy(p->ev_cjoin);
     if (p->d2h_stream) cudaStreamDestroy(p->d2h_stream);
@@ -595,6 +602,8 @@ tsvd_status ensure_runtime(tsvd_plan_s *p) {
   p->device = dev;
   TSVD_CUDA(cudaStreamCreateWithFlags(&p->copy_stream, cudaStreamNonBlocking));
   TSVD_CUDA(cudaStreamCreateWithFlags(&p->copy_stream2, cudaStreamNonBlocking));
+  TSVD_CUDA(cudaStreamCreateWithFlags(&p->aux_stream, cudaStreamNonBlocking));
+  TSVD_CUDA(cudaEventCreateWithFlags(&p->ev_aux, cudaEventDisableTiming));
   TSVD_CUDA(cudaEventCreateWithFlags(&p->ev_csplit, cudaEventDisableTiming));
   TSVD_CUDA(cudaEventCreateWithFlags(&p->ev_cjoin, cudaEventDisableTiming));
   TSVD_CUDA(cudaStreamCreateWithFlags(&p->d2h_stream, cudaStreamNonBlocking));
@@ -1167,6 +1176,7 @@ struct ExplicitLoop {
   double *sig2;       // k
   int32_t *info;      // 4 k
   VecScratch sc;
+  int32_t *ctr;       // the current triplet's application counter (device)
 };
 
 // Alg. 1 loop over l with Alg. 2 per triplet, the operator B v applied
@@ -1177,13 +1187,40 @@ struct ExplicitLoop {
 // `batch` applications are queued per host round trip: an application that
 // finds the triplet already stopped by an earlier one in the same batch
 // changes nothing (the decision and the next-iterate kernels test the stop
-// word), so the trajectory is the same as with one round trip per
-// application; the queued operator applications still run (they only write
-// scratch), so batching is for cheap operators.
+// word against a device counter), so the trajectory is the same as with one
+// round trip per application; the queued operator applications still run
+// (they only write scratch), so batching is for cheap operators.  With
+// `graph`, two consecutive applications (v -> v', v' -> v) are captured once
+// per triplet into a CUDA graph and replayed, one launch instead of about a
+// dozen per application; the operator must then be capturable (no host
+// waits, no work on other streams).
+tsvd_status explicit_power_on(Run &r, ExplicitLoop &L,
+                              const std::function<tsvd_status(const float *, float *, double *, int)> &apply,
+                              const std::function<tsvd_status()> &after_sync, float *V_out, int *flags_out,
+                              int64_t *apps_out, tsvd_report *rep, int batch, bool graph);
+
 tsvd_status explicit_power(Run &r, ExplicitLoop &L,
                            const std::function<tsvd_status(const float *, float *, double *, int)> &apply,
                            const std::function<tsvd_status()> &after_sync, float *V_out, int *flags_out,
-                           int64_t *apps_out, tsvd_report *rep, int batch = 1) {
+                           int64_t *apps_out, tsvd_report *rep, int batch = 1, bool graph = false) {
+  if (!graph) return explicit_power_on(r, L, apply, after_sync, V_out, flags_out, apps_out, rep, batch, false);
+  // the loop on the plan's own stream, ordered after and before the caller's work
+  tsvd_plan_s *p = r.p;
+  cudaStream_t caller = r.cs;
+  TSVD_CUDA(cudaEventRecord(p->ev_aux, caller));
+  TSVD_CUDA(cudaStreamWaitEvent(p->aux_stream, p->ev_aux, 0));
+  r.cs = p->aux_stream;
+  const tsvd_status st = explicit_power_on(r, L, apply, after_sync, V_out, flags_out, apps_out, rep, batch, true);
+  r.cs = caller;
+  TSVD_CUDA(cudaEventRecord(p->ev_aux, p->aux_stream));
+  TSVD_CUDA(cudaStreamWaitEvent(caller, p->ev_aux, 0));
+  return st;
+}
+
+tsvd_status explicit_power_on(Run &r, ExplicitLoop &L,
+                              const std::function<tsvd_status(const float *, float *, double *, int)> &apply,
+                              const std::function<tsvd_status()> &after_sync, float *V_out, int *flags_out,
+                              int64_t *apps_out, tsvd_report *rep, int batch, bool graph) {
   tsvd_plan_s *p = r.p;
   const int64_t n = p->n, k = p->k;
   float *v = L.v, *vn = L.vn;
@@ -1208,22 +1245,75 @@ tsvd_status explicit_power(Run &r, ExplicitLoop &L,
     int32_t h[4] = {0, 0, 0, 0};
     // application e (1-based) reads buf[(e - 1) & 1] and writes buf[e & 1]
     float *buf[2] = {v, vn};
-    int64_t e = 0;
-    for (;;) {
-      for (int b = 0; b < std::max(batch, 1); ++b) {
-        ++e;
-        float *in = buf[(e - 1) & 1], *out = buf[e & 1];
-        TSVD_CUDA(cudaMemsetAsync(L.w, 0, (size_t)n * 4, r.cs));
-        TSVD_CUDA(cudaMemsetAsync(L.ss, 0, 8, r.cs));
-        TSVD_TRY(apply(in, L.w, L.ss, 1));
-        TSVD_TRY(launch_vec_deflate_step(n, L.Vr, k, L.sig2, l, in, L.w, out, p->eps, p->opt.max_iter, ovr,
-                                         rank_scale, sc, 0, r.cs, (int)e));
+    TSVD_CUDA(cudaMemsetAsync(L.ctr, 0, 4, r.cs));
+    auto one = [&](const float *in, float *out) -> tsvd_status {
+      TSVD_CUDA(cudaMemsetAsync(L.w, 0, (size_t)n * 4, r.cs));
+      TSVD_CUDA(cudaMemsetAsync(L.ss, 0, 8, r.cs));
+      TSVD_TRY(apply(in, L.w, L.ss, 1));
+      return launch_vec_deflate_step(n, L.Vr, k, L.sig2, l, in, L.w, out, p->eps, p->opt.max_iter, ovr, rank_scale,
+                                     sc, 0, r.cs, L.ctr);
+    };
+    cudaGraphExec_t ge = nullptr;
+    int64_t nodes = 0;
+    if (graph) {
+      // the pair v -> v', v' -> v as one graph (the same for every pair of the triplet)
+      const int64_t c0 = launches_so_far();
+      TSVD_CUDA(cudaStreamBeginCapture(r.cs, cudaStreamCaptureModeThreadLocal));
+      tsvd_status cst = one(buf[0], buf[1]);
+      if (cst == TSVD_OK) cst = one(buf[1], buf[0]);
+      cudaGraph_t g = nullptr;
+      const cudaError_t ce = cudaStreamEndCapture(r.cs, &g);
+      if (cst != TSVD_OK || ce != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        (void)cudaGetLastError();
+        if (cst != TSVD_OK) return cst;
+        TSVD_CUDA(ce);
       }
-      TSVD_CUDA(cudaMemcpyAsync(h, sc.info, 16, cudaMemcpyDeviceToHost, r.cs));
-      TSVD_CUDA(cudaStreamSynchronize(r.cs));
-      TSVD_TRY(after_sync());
-      if (h[3] != 0) break;  // stopped at application h[3]: converged, forced count reached, or rank
+      const cudaError_t ie = cudaGraphInstantiate(&ge, g, 0);
+      cudaGraphDestroy(g);
+      TSVD_CUDA(ie);
+      nodes = launches_so_far() - c0;
+      count_launches(-nodes);  // counted again per replay
     }
+    const int per_sync = std::max(batch, 1);
+    int64_t e = 0;
+    tsvd_status lst = TSVD_OK;
+    for (;;) {
+      if (ge) {
+        for (int b = 0; b < per_sync; b += 2) {
+          const cudaError_t le = cudaGraphLaunch(ge, r.cs);
+          if (le != cudaSuccess) {
+            (void)cudaGetLastError();
+            set_cuda_error(le, "cudaGraphLaunch", __FILE__, __LINE__);
+            lst = TSVD_ECUDA;
+            break;
+          }
+          count_launches(nodes);
+          e += 2;
+        }
+      } else {
+        for (int b = 0; b < per_sync && lst == TSVD_OK; ++b) {
+          ++e;
+          lst = one(buf[(e - 1) & 1], buf[e & 1]);
+        }
+      }
+      if (lst == TSVD_OK && cudaMemcpyAsync(h, sc.info, 16, cudaMemcpyDeviceToHost, r.cs) != cudaSuccess) {
+        (void)cudaGetLastError();
+        lst = TSVD_ECUDA;
+      }
+      if (lst == TSVD_OK) {
+        const cudaError_t se = cudaStreamSynchronize(r.cs);
+        if (se != cudaSuccess) {
+          (void)cudaGetLastError();
+          set_cuda_error(se, "cudaStreamSynchronize", __FILE__, __LINE__);
+          lst = TSVD_ECUDA;
+        }
+      }
+      if (lst == TSVD_OK) lst = after_sync();
+      if (lst != TSVD_OK || h[3] != 0) break;  // stopped at application h[3]: converged, forced count, or rank
+    }
+    if (ge) cudaGraphExecDestroy(ge);
+    TSVD_TRY(lst);
     // rank: keep v0 of the stopping application; otherwise its output
     const int64_t stop = h[3];
     v = h[1] == 2 ? buf[(stop - 1) & 1] : buf[stop & 1];
@@ -1394,7 +1484,7 @@ tsvd_status factor_dense_tiled(Run &r, float *U, double *sigma_out, float *V_out
     }
     return launch_tile_finish(n, vv, w64, ww, s2, r.cs);
   };
-  ExplicitLoop L{v, vn, w, x64, ss, Vr, Vc, sig2, info, sc};
+  ExplicitLoop L{v, vn, w, x64, ss, Vr, Vc, sig2, info, sc, reinterpret_cast<int32_t *>(ws + p->o_flag) + 32};
   int flags = 0;
   int64_t apps = 0;
   TSVD_TRY(explicit_power(r, L, apply, []() { return TSVD_OK; }, V_out, &flags, &apps, rep));
@@ -1506,16 +1596,19 @@ tsvd_status factor_csr(Run &r, float *U, double *sigma_out, float *V_out, tsvd_r
   }
   TSVD_CUDA(cudaEventRecord(p->ev_t[1], r.cs));
 
-  ExplicitLoop L{v, vn, w, x64, ss, Vr, nullptr, sig2, info, sc};
+  ExplicitLoop L{v, vn, w, x64, ss, Vr, nullptr, sig2, info, sc, flag + 32};
   int flags = 0;
   int64_t apps = 0;
   const bool host_out = p->opt.out_location == TSVD_HOST;
-  // small operators: 16 applications per host round trip (the round trip dominates them);
-  // large ones, or per-application kernel timing: one
-  const int batch = (p->opt.time_kernels || p->nnz >= ((int64_t)1 << 25)) ? 1 : 16;
+  // small operators: 16 applications per host round trip (the round trip dominates them),
+  // replayed from a CUDA graph when A is on the device (the streamed operator waits on
+  // copies); large ones, or per-application kernel timing: one at a time
+  const bool small = !p->opt.time_kernels && p->nnz < ((int64_t)1 << 25);
+  const int batch = small ? 16 : 1;
+  const bool graph = small && p->mode != MODE_STREAM;
   TSVD_TRY(explicit_power(
       r, L, [&](const float *vv, float *ww, double *s2, int scatter) { return csr_apply(r, bnd, vv, ww, s2, scatter); },
-      [&]() { return csr_kernel_time(r); }, V_out, &flags, &apps, rep, batch));
+      [&]() { return csr_kernel_time(r); }, V_out, &flags, &apps, rep, batch, graph));
   TSVD_TRY(launch_sigma_from_sigma2(sig2, sigma, k, r.cs));
   TSVD_CUDA(cudaEventRecord(p->ev_t[2], r.cs));
   if (U) {

@@ -12,6 +12,8 @@ namespace tsvd {
 // ---------------------------------------------------------------- host side
 void set_cuda_error(cudaError_t e, const char *what, const char *file, int line);
 void set_error_text(const std::string &s);
+// kernel launches made by this thread (counted at launch; a replayed graph adds its kernel nodes)
+void count_launches(int64_t n);
 // Raise `func`'s dynamic shared-memory limit on the current device to at least
 // `bytes`.  The limit belongs to the process (every host thread sees it), so
 // the record of what was set is process-wide and the limit only grows.
@@ -259,7 +261,7 @@ tsvd_status launch_vec_normalize_f64_to_f32(const double *x, float *v, int64_t n
 tsvd_status launch_vec_deflate_step(int64_t n, const float *Vr, int64_t ldk, const double *sig2,
                                     int64_t l, const float *v, float *w, float *vnext, double eps,
                                     int max_iter, int iters_override, double scale, VecScratch sc,
-                                    int orth_only, cudaStream_t stream, int expect = 0);
+                                    int orth_only, cudaStream_t stream, int *ctr = nullptr);
 tsvd_status launch_vec_store_column(int64_t n, const float *v, float *Vr, int64_t ldk, int64_t l,
                                     int sign_convention, VecScratch sc, cudaStream_t stream);
 

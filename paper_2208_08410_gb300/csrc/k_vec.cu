@@ -122,12 +122,18 @@ __global__ void __launch_bounds__(VT) deflate_kernel(const float *__restrict__ V
 
 // decide: scal[0..2] = ww, vw, vv; info[0] += 1 unless orth_only; info[1] status; info[2] done;
 // info[3] the application (1-based) at which the triplet stopped, 0 while it runs.
-// expect > 0: this is application `expect` of the triplet, queued without knowing whether an
-// earlier one already stopped it; then it does nothing
+// ctr (not with orth_only): the triplet's application counter; an application queued after
+// the one that stopped the triplet does nothing.  The counter lives in device memory, so
+// every application of a triplet launches with the same arguments (a captured graph
+// replays them)
 __global__ void decide_kernel(double *scal, int *info, double eps, int max_iter, int iters_override,
-                              double rank_scale, int orth_only, int expect) {
+                              double rank_scale, int orth_only, int *ctr) {
   if (threadIdx.x != 0) return;
-  if (!orth_only && expect > 0 && info[3] != 0 && info[3] < expect) return;
+  int app = 0;
+  if (!orth_only && ctr) {
+    app = ++(*ctr);
+    if (info[3] != 0 && info[3] < app) return;
+  }
   const double ww = scal[0], vw = scal[1], vv = scal[2];
   const double nw = sqrt(ww);
   scal[4] = nw > 0.0 ? 1.0 / nw : 0.0;
@@ -140,7 +146,7 @@ __global__ void decide_kernel(double *scal, int *info, double eps, int max_iter,
   if (!(nw > 1e-30 * rank_scale)) {
     info[1] = 2;
     info[2] = 1;
-    info[3] = it;
+    info[3] = app ? app : it;
     return;
   }
   const double cosv = fabs(vw) / (nw * sqrt(vv));
@@ -156,14 +162,14 @@ __global__ void decide_kernel(double *scal, int *info, double eps, int max_iter,
     }
   }
   info[2] = done;
-  if (done) info[3] = it;
+  if (done) info[3] = app ? app : it;
 }
 
 __global__ void scale_f32_kernel(const float *__restrict__ w, float *__restrict__ out, int64_t n,
-                                 const double *scal, const int *info, int expect) {
-  if (expect > 0) {
+                                 const double *scal, const int *info, const int *ctr) {
+  if (ctr) {
     const int stop = info[3];
-    if (stop != 0 && stop < expect) return;  // an earlier application stopped the triplet
+    if (stop != 0 && stop < *ctr) return;  // an earlier application stopped the triplet
   }
   const double s = scal[4];
   for (int64_t i = gtid(); i < n; i += gstride()) out[i] = (float)((double)w[i] * s);
@@ -245,7 +251,7 @@ tsvd_status launch_vec_normalize_f64_to_f32(const double *x, float *v, int64_t n
 tsvd_status launch_vec_deflate_step(int64_t n, const float *Vr, int64_t ldk, const double *sig2,
                                     int64_t l, const float *v, float *w, float *vnext, double eps,
                                     int max_iter, int iters_override, double scale, VecScratch sc,
-                                    int orth_only, cudaStream_t stream, int expect) {
+                                    int orth_only, cudaStream_t stream, int *ctr) {
   const int g = vec_grid(n, sc);
   if (l + 4 > kVecPartStride) return TSVD_EUNSUPPORTED;
   if (l > 0) {
@@ -264,9 +270,10 @@ tsvd_status launch_vec_deflate_step(int64_t n, const float *Vr, int64_t ldk, con
   TSVD_LAUNCHED();
   reduce_parts_kernel<<<1, 96, 0, stream>>>(sc.part, kVecPartStride, g, kVecPartStride - 3, 3, sc.scal);
   TSVD_LAUNCHED();
-  decide_kernel<<<1, 32, 0, stream>>>(sc.scal, sc.info, eps, max_iter, iters_override, scale, orth_only, expect);
+  decide_kernel<<<1, 32, 0, stream>>>(sc.scal, sc.info, eps, max_iter, iters_override, scale, orth_only,
+                                      orth_only ? nullptr : ctr);
   TSVD_LAUNCHED();
-  scale_f32_kernel<<<g, VT, 0, stream>>>(w, vnext, n, sc.scal, sc.info, orth_only ? 0 : expect);
+  scale_f32_kernel<<<g, VT, 0, stream>>>(w, vnext, n, sc.scal, sc.info, orth_only ? nullptr : ctr);
   TSVD_LAUNCHED();
   return TSVD_OK;
 }
