@@ -1246,9 +1246,9 @@ tsvd_status explicit_power_on(Run &r, ExplicitLoop &L,
     // application e (1-based) reads buf[(e - 1) & 1] and writes buf[e & 1]
     float *buf[2] = {v, vn};
     TSVD_CUDA(cudaMemsetAsync(L.ctr, 0, 4, r.cs));
+    // (the operator's v^T G v accumulates into L.ss here unread; the sigma pass clears it first)
     auto one = [&](const float *in, float *out) -> tsvd_status {
       TSVD_CUDA(cudaMemsetAsync(L.w, 0, (size_t)n * 4, r.cs));
-      TSVD_CUDA(cudaMemsetAsync(L.ss, 0, 8, r.cs));
       TSVD_TRY(apply(in, L.w, L.ss, 1));
       return launch_vec_deflate_step(n, L.Vr, k, L.sig2, l, in, L.w, out, p->eps, p->opt.max_iter, ovr, rank_scale,
                                      sc, 0, r.cs, L.ctr);

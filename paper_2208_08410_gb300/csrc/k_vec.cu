@@ -55,25 +55,28 @@ __global__ void scale_f64_to_f32_kernel(const double *__restrict__ x, float *__r
   for (int64_t i = gtid(); i < n; i += gstride()) v[i] = (float)(x[i] * s);
 }
 
-// partial c_j = sum_i Vr[i*ldk + j0 + j] v[i] for j < cols (cols <= 32)
+// partial c_j = sum_i Vr[i*ldk + j0 + j] v[i] for j < cols (cols <= 32).  Each thread sums
+// its few elements (n / grid threads; 128 at n = 2^25) in FP32, the warp and block sums
+// are FP64: the FP64 pipe of this part is narrow, and an FP64 product per (i, j) made
+// these kernels FP64-bound
 __global__ void __launch_bounds__(VT) proj_partial_kernel(const float *__restrict__ Vr, int64_t ldk,
                                                           int j0, int cols, const float *__restrict__ v,
                                                           int64_t n, double *part, int ps) {
-  double acc[kVecMaxCols];
+  float acc[kVecMaxCols];
 #pragma unroll
-  for (int j = 0; j < kVecMaxCols; ++j) acc[j] = 0.0;
+  for (int j = 0; j < kVecMaxCols; ++j) acc[j] = 0.f;
   for (int64_t i = gtid(); i < n; i += gstride()) {
-    const double vi = (double)v[i];
+    const float vi = v[i];
     const float *row = Vr + i * ldk + j0;
 #pragma unroll
     for (int j = 0; j < kVecMaxCols; ++j)
-      if (j < cols) acc[j] += (double)__ldg(row + j) * vi;
+      if (j < cols) acc[j] = fmaf(__ldg(row + j), vi, acc[j]);
   }
   __shared__ double sm[VT / 32][kVecMaxCols];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
   for (int j = 0; j < kVecMaxCols; ++j) {
-    const double t = warp_sum(acc[j]);
+    const double t = warp_sum((double)acc[j]);
     if (lane == 0) sm[warp][j] = t;
   }
   __syncthreads();
@@ -88,23 +91,24 @@ __global__ void coef_kernel(const double *c, const double *sig2, int l, int orth
   for (int j = threadIdx.x; j < l; j += blockDim.x) coef[j] = orth_only ? c[j] : sig2[j] * c[j];
 }
 
-// w[i] = base[i] - sum_j Vr[i*ldk+j] coef[j]; partial ww, vw, vv
+// w[i] = base[i] - sum_j Vr[i*ldk+j] coef[j] (the l corrections in FP32, like the
+// iterate itself); partial ww, vw, vv of the stored FP32 values, in FP64
 __global__ void __launch_bounds__(VT) deflate_kernel(const float *__restrict__ Vr, int64_t ldk, int l,
                                                      const double *__restrict__ coef,
                                                      const float *__restrict__ v, float *w, int64_t n,
                                                      int orth_only, double *part, int ps, int off) {
-  __shared__ double cs[256];
+  __shared__ float cs[256];
   __shared__ double red[33];
-  for (int j = threadIdx.x; j < l && j < 256; j += blockDim.x) cs[j] = coef[j];
+  for (int j = threadIdx.x; j < l && j < 256; j += blockDim.x) cs[j] = (float)coef[j];
   __syncthreads();
   double ww = 0.0, vw = 0.0, vv = 0.0;
   for (int64_t i = gtid(); i < n; i += gstride()) {
-    const double vi = (double)v[i];
-    double wi = orth_only ? vi : (double)w[i];
+    const float vf = v[i];
+    float wf = orth_only ? vf : w[i];
     const float *row = Vr + i * ldk;
-    for (int j = 0; j < l; ++j) wi -= (double)__ldg(row + j) * (j < 256 ? cs[j] : coef[j]);
-    const float wf = (float)wi;
+    for (int j = 0; j < l; ++j) wf = fmaf(-__ldg(row + j), j < 256 ? cs[j] : (float)coef[j], wf);
     w[i] = wf;
+    const double wi = (double)wf, vi = (double)vf;
     ww += wi * wi;
     vw += vi * wi;
     vv += vi * vi;
