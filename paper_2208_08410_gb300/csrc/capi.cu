@@ -1194,23 +1194,28 @@ struct ExplicitLoop {
 // per triplet into a CUDA graph and replayed, one launch instead of about a
 // dozen per application; the operator must then be capturable (no host
 // waits, no work on other streams).
+// A whole triplet's loop in one launch: (buf0 = v0, buf1, l, forced count, rank scale, info)
+using TripletLoop = std::function<tsvd_status(float *, float *, int64_t, int, double, int32_t *)>;
+
 tsvd_status explicit_power_on(Run &r, ExplicitLoop &L,
                               const std::function<tsvd_status(const float *, float *, double *, int)> &apply,
                               const std::function<tsvd_status()> &after_sync, float *V_out, int *flags_out,
-                              int64_t *apps_out, tsvd_report *rep, int batch, bool graph);
+                              int64_t *apps_out, tsvd_report *rep, int batch, bool graph, const TripletLoop *coop);
 
 tsvd_status explicit_power(Run &r, ExplicitLoop &L,
                            const std::function<tsvd_status(const float *, float *, double *, int)> &apply,
                            const std::function<tsvd_status()> &after_sync, float *V_out, int *flags_out,
-                           int64_t *apps_out, tsvd_report *rep, int batch = 1, bool graph = false) {
-  if (!graph) return explicit_power_on(r, L, apply, after_sync, V_out, flags_out, apps_out, rep, batch, false);
+                           int64_t *apps_out, tsvd_report *rep, int batch = 1, bool graph = false,
+                           const TripletLoop *coop = nullptr) {
+  if (!graph && !coop)
+    return explicit_power_on(r, L, apply, after_sync, V_out, flags_out, apps_out, rep, batch, false, nullptr);
   // the loop on the plan's own stream, ordered after and before the caller's work
   tsvd_plan_s *p = r.p;
   cudaStream_t caller = r.cs;
   TSVD_CUDA(cudaEventRecord(p->ev_aux, caller));
   TSVD_CUDA(cudaStreamWaitEvent(p->aux_stream, p->ev_aux, 0));
   r.cs = p->aux_stream;
-  const tsvd_status st = explicit_power_on(r, L, apply, after_sync, V_out, flags_out, apps_out, rep, batch, true);
+  const tsvd_status st = explicit_power_on(r, L, apply, after_sync, V_out, flags_out, apps_out, rep, batch, graph, coop);
   r.cs = caller;
   TSVD_CUDA(cudaEventRecord(p->ev_aux, p->aux_stream));
   TSVD_CUDA(cudaStreamWaitEvent(caller, p->ev_aux, 0));
@@ -1220,7 +1225,7 @@ tsvd_status explicit_power(Run &r, ExplicitLoop &L,
 tsvd_status explicit_power_on(Run &r, ExplicitLoop &L,
                               const std::function<tsvd_status(const float *, float *, double *, int)> &apply,
                               const std::function<tsvd_status()> &after_sync, float *V_out, int *flags_out,
-                              int64_t *apps_out, tsvd_report *rep, int batch, bool graph) {
+                              int64_t *apps_out, tsvd_report *rep, int batch, bool graph, const TripletLoop *coop) {
   tsvd_plan_s *p = r.p;
   const int64_t n = p->n, k = p->k;
   float *v = L.v, *vn = L.vn;
@@ -1255,7 +1260,15 @@ tsvd_status explicit_power_on(Run &r, ExplicitLoop &L,
     };
     cudaGraphExec_t ge = nullptr;
     int64_t nodes = 0;
-    if (graph) {
+    if (coop) {
+      // the whole loop of this triplet in one cooperative launch
+      TSVD_TRY((*coop)(buf[0], buf[1], l, ovr, rank_scale, sc.info));
+      TSVD_CUDA(cudaMemcpyAsync(h, sc.info, 16, cudaMemcpyDeviceToHost, r.cs));
+      TSVD_CUDA(cudaStreamSynchronize(r.cs));
+      TSVD_TRY(after_sync());
+      if (h[3] == 0) return TSVD_ETIMEDOUT;  // a bounded barrier wait gave up before the triplet stopped
+    }
+    if (graph && !coop) {
       // the pair v -> v', v' -> v as one graph (the same for every pair of the triplet)
       const int64_t c0 = launches_so_far();
       TSVD_CUDA(cudaStreamBeginCapture(r.cs, cudaStreamCaptureModeThreadLocal));
@@ -1278,7 +1291,7 @@ tsvd_status explicit_power_on(Run &r, ExplicitLoop &L,
     const int per_sync = std::max(batch, 1);
     int64_t e = 0;
     tsvd_status lst = TSVD_OK;
-    for (;;) {
+    for (; !coop;) {
       if (ge) {
         for (int b = 0; b < per_sync; b += 2) {
           const cudaError_t le = cudaGraphLaunch(ge, r.cs);
@@ -1606,9 +1619,30 @@ tsvd_status factor_csr(Run &r, float *U, double *sigma_out, float *V_out, tsvd_r
   const bool small = !p->opt.time_kernels && p->nnz < ((int64_t)1 << 25);
   const int batch = small ? 16 : 1;
   const bool graph = small && p->mode != MODE_STREAM;
+  // small, in core, single-pass operator, at most 32 earlier vectors: the whole loop of a
+  // triplet in one cooperative launch (k_csr_power.cu)
+  const bool coop = graph && !r.chunked && k <= 33;
+  const int64_t *rp_all = p->mode == MODE_DEVICE ? A->row_ptr : reinterpret_cast<const int64_t *>(ws + p->o_res);
+  const int32_t *ci_all = p->mode == MODE_DEVICE
+                              ? A->col_idx
+                              : reinterpret_cast<const int32_t *>(ws + p->o_res + round_up((m + 1) * 8, 256));
+  const float *va_all = p->mode == MODE_DEVICE
+                            ? A->values
+                            : reinterpret_cast<const float *>(ws + p->o_res + round_up((m + 1) * 8, 256) +
+                                                              round_up(std::max<int64_t>(p->nnz, 1) * 4, 256));
+  TripletLoop coop_fn = [&](float *b0, float *b1, int64_t l, int ovr, double rank_scale,
+                            int32_t *info_l) -> tsvd_status {
+    unsigned *bar = reinterpret_cast<unsigned *>(flag + 48);  // bytes 192..199 of the flag region
+    int *err = flag + 50;                                     // bytes 200..203
+    TSVD_CUDA(cudaMemsetAsync(bar, 0, 16, r.cs));
+    TSVD_CUDA(cudaMemsetAsync(w, 0, (size_t)n * 4, r.cs));
+    return launch_csr_power(m, n, rp_all, ci_all, va_all, Vr, k, sig2, l, b0, b1, w, sc.part,
+                            (size_t)sc.grid * kVecPartStride * sizeof(double), bar, err, p->eps, p->opt.max_iter,
+                            ovr, rank_scale, info_l, p->avg_nnz, 64, r.cs);
+  };
   TSVD_TRY(explicit_power(
       r, L, [&](const float *vv, float *ww, double *s2, int scatter) { return csr_apply(r, bnd, vv, ww, s2, scatter); },
-      [&]() { return csr_kernel_time(r); }, V_out, &flags, &apps, rep, batch, graph));
+      [&]() { return csr_kernel_time(r); }, V_out, &flags, &apps, rep, batch, graph, coop ? &coop_fn : nullptr));
   TSVD_TRY(launch_sigma_from_sigma2(sig2, sigma, k, r.cs));
   TSVD_CUDA(cudaEventRecord(p->ev_t[2], r.cs));
   if (U) {

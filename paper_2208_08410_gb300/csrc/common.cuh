@@ -200,6 +200,20 @@ tsvd_status launch_tile_symv(const double *T, int64_t ldt, int64_t nJ, int64_t n
 tsvd_status launch_tile_finish(int64_t n, const float *v, const double *w64, float *w, double *ss,
                                cudaStream_t stream);
 
+// One triplet of the sparse power method (CSR on the device, whole matrix,
+// rows m, columns n; l <= 32 earlier vectors in Vr, n x ldk row-major) in one
+// cooperative launch of at most max_blocks blocks: buf0 holds v0 on entry,
+// the iterate alternates between buf0 and buf1, w (n floats) is zero on entry
+// and on exit; info as the explicit loop's (applications, status, done,
+// stopping application).  part: csr_power_part_bytes(grid) bytes; bar / err:
+// two zeroed words and a status word (a bounded barrier wait sets it).
+size_t csr_power_part_bytes(int grid);
+tsvd_status launch_csr_power(int64_t m, int64_t n, const int64_t *rp, const int32_t *ci, const float *va,
+                             const float *Vr, int64_t ldk, const double *sig2, int64_t l, float *buf0, float *buf1,
+                             float *w, double *part, size_t part_bytes, unsigned *bar, int *err, double eps,
+                             int max_iter, int iters_override, double rank_scale, int *info, double avg_nnz,
+                             int max_blocks, cudaStream_t stream);
+
 size_t power_scratch_bytes(int64_t n, int64_t l);
 tsvd_status launch_power_dense(int64_t n, const float *G32, const double *G64, const double *V64,
                                const double *sigma2, int64_t l, double *x, double eps,
