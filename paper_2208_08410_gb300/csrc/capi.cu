@@ -1209,9 +1209,12 @@ tsvd_status explicit_power(Run &r, ExplicitLoop &L,
                            const TripletLoop *coop = nullptr) {
   if (!graph && !coop)
     return explicit_power_on(r, L, apply, after_sync, V_out, flags_out, apps_out, rep, batch, false, nullptr);
-  // the loop on the plan's own stream, ordered after and before the caller's work
+  // a capture cannot use the legacy default stream: then the loop runs on the plan's own
+  // stream, ordered after and before the caller's work (any other stream is used as it is)
   tsvd_plan_s *p = r.p;
   cudaStream_t caller = r.cs;
+  if (caller != nullptr && caller != cudaStreamLegacy && caller != cudaStreamPerThread)
+    return explicit_power_on(r, L, apply, after_sync, V_out, flags_out, apps_out, rep, batch, graph, coop);
   TSVD_CUDA(cudaEventRecord(p->ev_aux, caller));
   TSVD_CUDA(cudaStreamWaitEvent(p->aux_stream, p->ev_aux, 0));
   r.cs = p->aux_stream;

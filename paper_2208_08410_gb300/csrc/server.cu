@@ -631,8 +631,12 @@ tsvd_status time_power(tsvd_server_s *sv, int64_t d, int c, int nreq, int iters,
 // keep running on their own streams meanwhile.
 void csr_worker(tsvd_server_s *sv) {
   cudaSetDevice(sv->device);
+  // the highest stream priority: a sparse request's cooperative launches wait for whole SMs,
+  // and the block scheduler then serves them before the dense waves' pending blocks
+  int lo = 0, hi = 0;
+  cudaDeviceGetStreamPriorityRange(&lo, &hi);
   cudaStream_t st = nullptr;
-  if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) return;
+  if (cudaStreamCreateWithPriority(&st, cudaStreamNonBlocking, hi) != cudaSuccess) return;
   std::unique_lock<std::mutex> lk(sv->mu);
   while (true) {
     sv->cv_csr.wait(lk, [&] { return sv->stop || !sv->csr_pending.empty(); });
