@@ -463,6 +463,30 @@ def kernel_case(args):
                     "frac_hbm": round(m * n * 4 / t / 1e9 / peaks["hbm_gbs"], 3)})
     elif args.case == "c1":
         out.update(c1_latency(reps=max(reps, 5)))
+    elif args.case == "csr_small":
+        # one sparse serving request alone: m = n = 65,536 at density 1e-4, k = 16, eps = 1e-6,
+        # at most 200 applications per triplet, the CSR on the device (the cooperative loop)
+        import synth
+        from paper_2208_08410_gb300 import Plan
+        m = args.m or (1 << 16)
+        csr = synth.csr_uniform(m, m, 1e-4 * m, seed=3)
+        dcsr = {"row_ptr": torch.from_numpy(csr["row_ptr"]).cuda(), "col_idx": torch.from_numpy(csr["col_idx"]).cuda(),
+                "values": torch.from_numpy(csr["values"]).cuda(), "m": m, "n": m}
+        plan = Plan(dcsr, 16, 1e-6, out_device=True, max_iter=200)
+        for _ in range(max(args.warmup, 1)):
+            plan.factor(dcsr, ok=(B.TSVD_OK, B.TSVD_ENOCONV))
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        r = plan.factor(dcsr, ok=(B.TSVD_OK, B.TSVD_ENOCONV))
+        e1.record()
+        torch.cuda.synchronize()
+        plan.close()
+        ms = e0.elapsed_time(e1)
+        out.update({"m": m, "nnz": int(csr["values"].shape[0]), "ms_per_tsvd": round(ms, 2),
+                    "applications": r.report["applications"],
+                    "us_per_application": round(ms * 1e3 / max(r.report["applications"], 1), 2),
+                    "phases_ms": {"power": round(r.report["power_ms"], 2)}, "launches": r.report["kernel_launches"]})
     elif args.case == "csr_tsvd":
         # in-core CSR t-SVD alone (device CSR, k = 4, 3 applications per triplet): the
         # column-chunked operator when 8 n exceeds 64 MB
@@ -851,16 +875,20 @@ def serve_workload(args):
                                       "p99_service_ms": round(float(np.percentile(serv[sel], 99)) * 1e3, 2),
                                       "mean_applications": round(float(apps[sel].mean()), 1)}
         dn = ~is_sp
-        return {"p50_ms": round(float(np.percentile(lat, 50)) * 1e3, 3),
-                "p99_ms": round(float(np.percentile(lat, 99)) * 1e3, 3),
-                "dense_p50_ms": round(float(np.percentile(lat[dn], 50)) * 1e3, 3),
-                "dense_p99_ms": round(float(np.percentile(lat[dn], 99)) * 1e3, 3),
+
+        def pct(x, q):
+            return round(float(np.percentile(x, q)) * 1e3, 3) if x.size else None
+
+        def mx(x):
+            return float("%.3g" % x.max()) if x.size else None
+        return {"p50_ms": pct(lat, 50), "p99_ms": pct(lat, 99),
+                "dense_p50_ms": pct(lat[dn], 50), "dense_p99_ms": pct(lat[dn], 99),
                 "mean_ms": round(float(lat.mean()) * 1e3, 3), "solves_per_s": round(n_req / span, 1),
                 "span_s": round(span, 3),
-                "sigma_max_rel_err_in_envelope": float("%.3g" % errs_env[dn].max()),
-                "frac_requests_sigma_err_le_1e-5_in_envelope": float(np.mean(errs_env[dn] <= 1e-5)),
-                "sigma_max_rel_err_all_triplets": float("%.3g" % errs[dn].max()),
-                "frac_requests_sigma_err_le_1e-5_all_triplets": float(np.mean(errs[dn] <= 1e-5)),
+                "sigma_max_rel_err_in_envelope": mx(errs_env[dn]),
+                "frac_requests_sigma_err_le_1e-5_in_envelope": float(np.mean(errs_env[dn] <= 1e-5)) if dn.any() else None,
+                "sigma_max_rel_err_all_triplets": mx(errs[dn]),
+                "frac_requests_sigma_err_le_1e-5_all_triplets": float(np.mean(errs[dn] <= 1e-5)) if dn.any() else None,
                 "sparse": sparse,
                 "status_counts": {B.STATUS_NAMES[int(c)]: int((status == c).sum()) for c in np.unique(status)},
                 "by_dim": by_dim}
@@ -1096,7 +1124,7 @@ def main():
     ap.add_argument("--no-parity", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=0)
-    ap.add_argument("--case", default="", choices=["", "gram", "power", "csr", "left", "c1", "csr_tsvd"],
+    ap.add_argument("--case", default="", choices=["", "gram", "power", "csr", "left", "c1", "csr_tsvd", "csr_small"],
                     help="single-kernel microbenchmark instead of the t-SVD step")
     ap.add_argument("--n", type=int, default=N_COLS)
     ap.add_argument("--workload", default="dense", choices=["dense", "csr", "c4", "serve", "tiled"])

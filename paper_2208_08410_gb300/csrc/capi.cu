@@ -1641,7 +1641,7 @@ tsvd_status factor_csr(Run &r, float *U, double *sigma_out, float *V_out, tsvd_r
     TSVD_CUDA(cudaMemsetAsync(w, 0, (size_t)n * 4, r.cs));
     return launch_csr_power(m, n, rp_all, ci_all, va_all, Vr, k, sig2, l, b0, b1, w, sc.part,
                             (size_t)sc.grid * kVecPartStride * sizeof(double), bar, err, p->eps, p->opt.max_iter,
-                            ovr, rank_scale, info_l, p->avg_nnz, 64, r.cs);
+                            ovr, rank_scale, info_l, p->avg_nnz, 128, r.cs);
   };
   TSVD_TRY(explicit_power(
       r, L, [&](const float *vv, float *ww, double *s2, int scatter) { return csr_apply(r, bnd, vv, ww, s2, scatter); },

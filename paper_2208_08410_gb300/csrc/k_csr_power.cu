@@ -51,13 +51,6 @@ struct CsrPowerArgs {
   int *info;  // [0] applications, [1] status, [2] done, [3] stopping application
 };
 
-__device__ __forceinline__ double reduce_slot(const double *part, int ps, int off, double *red) {
-  // every block sums the blocks' partials in the same order
-  double t = 0.0;
-  for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) t += __ldcg(part + (int64_t)b * ps + off);
-  return block_sum(t, red);
-}
-
 template <int G>
 __global__ void __launch_bounds__(PT) csr_power_kernel(CsrPowerArgs a) {
   __shared__ double red[33];
@@ -122,10 +115,13 @@ __global__ void __launch_bounds__(PT) csr_power_kernel(CsrPowerArgs a) {
       for (int64_t p = p0 + sub; p < p1; p += G) atomicAdd(a.w + __ldg(a.ci + p), __ldg(a.va + p) * y);
     }
     if (!grid_barrier(a.bar, a.err)) return;
-    // ---- deflate: w -= V (sigma^2 . c), partial norms
-    for (int j = 0; j < l; ++j) {
-      const double c = reduce_slot(a.part, a.ps, j, red);
-      if (threadIdx.x == 0) cs[j] = (float)(__ldg(a.sig2 + j) * c);
+    // ---- deflate: w -= V (sigma^2 . c), partial norms.  c_j summed over the blocks' partials
+    // by warp j % 8 (the same order in every block)
+    for (int j = warp; j < l; j += PT / 32) {
+      double t = 0.0;
+      for (int b = lane; b < (int)gridDim.x; b += 32) t += __ldcg(a.part + (int64_t)b * a.ps + j);
+      t = warp_sum(t);
+      if (lane == 0) cs[j] = (float)(__ldg(a.sig2 + j) * t);
     }
     __syncthreads();
     double ww = 0.0, vw = 0.0, vv = 0.0;
@@ -149,10 +145,17 @@ __global__ void __launch_bounds__(PT) csr_power_kernel(CsrPowerArgs a) {
       mypart[NRM + 2] = vv;
     }
     if (!grid_barrier(a.bar, a.err)) return;
-    // ---- decision (identical in every block) and the next iterate
-    const double tw = reduce_slot(a.part, a.ps, NRM, red);
-    const double tvw = reduce_slot(a.part, a.ps, NRM + 1, red);
-    const double tvv = reduce_slot(a.part, a.ps, NRM + 2, red);
+    // ---- decision (identical in every block) and the next iterate; the three norms
+    // summed over the blocks' partials by warps 0..2
+    if (warp < 3) {
+      double t = 0.0;
+      for (int b = lane; b < (int)gridDim.x; b += 32) t += __ldcg(a.part + (int64_t)b * a.ps + NRM + warp);
+      t = warp_sum(t);
+      if (lane == 0) scal[warp] = t;
+    }
+    __syncthreads();
+    const double tw = scal[0], tvw = scal[1], tvv = scal[2];
+    __syncthreads();
     if (threadIdx.x == 0) {
       const int it1 = it + 1;
       const double nw = sqrt(tw);
