@@ -283,6 +283,9 @@ tsvd_status plan_dense_tiled(tsvd_plan_s *p) {
   p->o_sig2 = c.take((size_t)k * 8);
   p->o_sigma = c.take((size_t)k * 8);
   p->o_info = c.take((size_t)k * 4 * sizeof(int32_t));
+  // 256-byte word region: [0] validation flag of a device CSR, [64] the operator's v^T G v
+  // (FP64), [128] the triplet's application counter, [192] barrier words and [200] the
+  // barrier status of the cooperative triplet loop
   p->o_flag = c.take(256);
   p->vec_grid = 1024;
   p->o_vsc = c.take(vec_scratch_bytes(p->vec_grid));

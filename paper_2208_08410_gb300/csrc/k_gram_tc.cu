@@ -28,6 +28,15 @@
 // Every wait is bounded (global timer); on timeout the kernel raises an error
 // flag, stops issuing, waits (bounded) for its own copies and MMAs, frees
 // TMEM and returns.
+//
+// Two more uses of the same kernels:
+//  - a column block of a wide A (m < n, Eq. 3: the Gram is A A^T): its
+//    contraction index is already contiguous in memory, so prep_rows_kernel
+//    only rounds and splits (no transpose) before the same SYRK;
+//  - one task of the orthogonal batching (Sec. V-C, Fig. 2c-d): panel J is
+//    prepped into rows [0, bs) of the operand and panel I into rows
+//    [bs, 2 bs), and the SYRK visits only the rectangle of tiles that holds
+//    A_J^T A_I (rectangular mode: every element of those tiles is stored).
 #include <cuda.h>
 
 #include <algorithm>
