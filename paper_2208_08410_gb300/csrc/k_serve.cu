@@ -14,9 +14,12 @@
 // [c R, (c+1) R) of G (R = ceil(d / C)), kept in shared memory when they fit.
 // An iteration: w = G32 v for the CTA's rows (FP32 products, error-free FP32
 // row sums), the rows of w stored into every CTA's next-iterate buffer and
-// the CTA's partial ||w||^2, v.w, v.v into every CTA's partial slots through
+// the CTA's partial ||w||^2, v.w, v.v (pairs of FP32 numbers, ~48 bits, since
+// the FP64 pipe of this part is narrow) into every CTA's partial slots through
 // distributed shared memory, one cluster barrier, then every CTA adds the C
-// partials in rank order and takes the same decision.  After the loop every
+// partials in rank order and takes the same decision (FP64).  The iterate is
+// normalised inside the next product (w = s G r for the stored r), so one
+// application has one cluster barrier and two block barriers.  After the loop every
 // CTA holds the whole v_l.  The CTA's rows of the FP64 Gram are kept deflated
 // (Hotelling, in FP64) and its rows of the FP32 copy are rounded from them,
 // so the copy's rounding error is relative to the spectrum that remains;
@@ -150,21 +153,29 @@ __device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
   e = (a - (s - bb)) + (b - bb);
 }
 
+// Unevaluated FP32 pairs (h, l), value h + l: the FP64 pipe of this part is
+// narrow, so the per-row sums of the power loop are kept as pairs on the FP32
+// pipe.  a*b is split exactly into p + pe (FMA), h + p into s + e (two-sum), and
+// the low part collects both errors, so a pair carries about 48 bits.
+__device__ __forceinline__ void ff_add_prod(float &h, float &l, float a, float b) {
+  const float p = __fmul_rn(a, b);
+  const float pe = fmaf(a, b, -p);
+  float s, e;
+  two_sum(h, p, s, e);
+  h = s;
+  l = __fadd_rn(l, __fadd_rn(e, pe));
+}
+__device__ __forceinline__ void ff_add(float &h, float &l, float h2, float l2) {
+  float s, e;
+  two_sum(h, h2, s, e);
+  h = s;
+  l = __fadd_rn(l, __fadd_rn(e, l2));
+}
+__device__ __forceinline__ double ff_value(float h, float l) { return (double)h + (double)l; }
+
 constexpr int kMaxCluster = 8;
 static_assert(kSrvPowerThreads == 256 && kMaxCluster == 8, "the partial sums reduce over 8 lanes");
 
-// 1 / sqrt(x): the FP32 reciprocal square root as the seed, then two Newton-Raphson
-// steps for x^(-1/2) in FP64 (y <- y (3 - x y^2) / 2; each squares the relative
-// error, so ~1e-7 becomes ~1e-16); outside the FP32 normal range, the FP64 quotient
-__device__ __forceinline__ double inv_sqrt(double x) {
-  if (x > 1e-36 && x < 1e36) {
-    double y = (double)rsqrtf((float)x);
-    y = y * fma(-0.5 * x * y, y, 1.5);
-    y = y * fma(-0.5 * x * y, y, 1.5);
-    return y;
-  }
-  return 1.0 / sqrt(x);
-}
 constexpr int kPartSlot = kSrvMaxK + 4;  // doubles per (parity, rank) slot
 
 struct PowerSmem {
@@ -204,6 +215,28 @@ __global__ void __launch_bounds__(kSrvPowerThreads, 2) srv_power_kernel(const Sr
   if (res) {
     for (int64_t e = threadIdx.x; e < (r1 - r0) * d; e += kSrvPowerThreads) sm.Gs[e] = q.G32[r0 * d + e];
   }
+  // pw = 2^-E, 2^E the largest diagonal entry of G (every CTA forms the same power
+  // of two): the stored iterates are r = pw G v, whose entries stay below 2 d, so
+  // the products G_ij r_j stay inside the FP32 range up to max G_ii of about 1e31;
+  // the pair sums take qs r (qs = 2^20), whose squares stay inside it down to
+  // about 1e-25 max G_ii.  Scaling by powers of two is exact.
+  float gmax = 0.f;
+  for (int64_t i = threadIdx.x; i < d; i += kSrvPowerThreads) gmax = fmaxf(gmax, fabsf(q.G32[i * d + i]));
+  {
+    float *fred = reinterpret_cast<float *>(wred);
+    for (int o = 16; o > 0; o >>= 1) gmax = fmaxf(gmax, __shfl_xor_sync(0xffffffffu, gmax, o));
+    if (lane == 0) fred[warp] = gmax;
+    __syncthreads();
+    gmax = fred[0];
+    for (int w = 1; w < nwarps; ++w) gmax = fmaxf(gmax, fred[w]);
+    __syncthreads();
+  }
+  int shift = 0;
+  if (gmax > 0.f && gmax < INFINITY) shift = -ilogbf(gmax);
+  shift = max(-126, min(126, shift));
+  const float pw = __int_as_float((shift + 127) << 23);
+  constexpr float qs = 1048576.f;  // 2^20
+  const double pq2 = (double)pw * (double)pw * (double)qs * (double)qs;
   __syncthreads();
   uint32_t phase = 0;  // running count of cluster exchanges (selects the partial slots)
   const bool vec = (d % 4) == 0;
@@ -228,18 +261,18 @@ __global__ void __launch_bounds__(kSrvPowerThreads, 2) srv_power_kernel(const Sr
     const double inv = xx > 0.0 ? 1.0 / sqrt(xx) : 0.0;
     for (int64_t i = threadIdx.x; i < d; i += kSrvPowerThreads) sm.vb[0][i] = (float)(sm.xs[i] * inv);
     const double rank_scale = l == 0 ? 1.0 : sig0sq;
+    const double floor_s = 1e-30 * rank_scale * 1e-30 * rank_scale * pq2;  // floor^2 in the units of the sums
     int cur = 0, it = 0, status = 0;
-    double vscale = 1.0;  // the iterate in vb[cur] times vscale is v0
+    // vb[cur] holds the raw iterate r (pw G v of the previous application; x / ||x||
+    // at first) and v = sc r is the unit iterate of this one: pw G v is formed as
+    // pw sc (G r), so no pass over the iterate is needed to normalise it
+    float sc = 1.f;
+    double vscale = 1.0;  // on exit: v_l = vscale * vb[cur]
+    __syncthreads();
     for (;;) {
-      __syncthreads();
-      if (it > 0) {
-        const float sc = (float)vscale;
-        for (int64_t i = threadIdx.x; i < d; i += kSrvPowerThreads) sm.vb[cur][i] *= sc;
-        __syncthreads();
-      }
       const float *v = sm.vb[cur];
       float *nxt = sm.vb[cur ^ 1];
-      double ww = 0.0, vw = 0.0, vv = 0.0;
+      float wwh = 0.f, wwl = 0.f, vwh = 0.f, vwl = 0.f, vvh = 0.f, vvl = 0.f;
       // four rows per warp step (r0 and R are multiples of 4): four independent
       // dot products and warp reductions in flight; rows past r1 repeat the
       // last row and are dropped
@@ -292,9 +325,9 @@ __global__ void __launch_bounds__(kSrvPowerThreads, 2) srv_power_kernel(const Sr
             e[u] = e[u] + lo2 + ex;
           }
         }
-        // every lane holds the four sums; lane u finishes row rb + u (its FP64 work in
-        // parallel with the other three rows'): the iterate is the FP32 rounding of
-        // the exact h + e, and the FP64 sums use exactly that stored value
+        // every lane holds the four sums; lane u finishes row rb + u: the stored entry
+        // is pw times the FP32 rounding of sc (h + e), and the pair sums use exactly
+        // the stored entry and v_r
         if (lane < nr) {
           float hu = h[0], eu = e[0];
 #pragma unroll
@@ -304,25 +337,33 @@ __global__ void __launch_bounds__(kSrvPowerThreads, 2) srv_power_kernel(const Sr
               eu = e[u];
             }
           }
-          const float t32 = __fadd_rn(hu, eu);
-          const double t = (double)t32, vr = (double)v[rb + lane];
-          ww = fma(t, t, ww);
-          vw = fma(vr, t, vw);
-          vv = fma(vr, vr, vv);
-          nxt[rb + lane] = t32;
+          const float rr = __fmul_rn(__fmul_rn(__fadd_rn(hu, eu), sc), pw);
+          const float ts = __fmul_rn(rr, qs);
+          const float vr = __fmul_rn(v[rb + lane], sc);
+          ff_add_prod(wwh, wwl, ts, ts);
+          ff_add_prod(vwh, vwl, vr, ts);
+          ff_add_prod(vvh, vvl, vr, vr);
+          nxt[rb + lane] = rr;
         }
       }
       // lanes 0..3 hold the warp's partial sums
 #pragma unroll
       for (int o = 2; o > 0; o >>= 1) {
-        ww += __shfl_xor_sync(0xffffffffu, ww, o);
-        vw += __shfl_xor_sync(0xffffffffu, vw, o);
-        vv += __shfl_xor_sync(0xffffffffu, vv, o);
+        const float a0 = __shfl_xor_sync(0xffffffffu, wwh, o), a1 = __shfl_xor_sync(0xffffffffu, wwl, o);
+        const float b0 = __shfl_xor_sync(0xffffffffu, vwh, o), b1 = __shfl_xor_sync(0xffffffffu, vwl, o);
+        const float c0 = __shfl_xor_sync(0xffffffffu, vvh, o), c1 = __shfl_xor_sync(0xffffffffu, vvl, o);
+        ff_add(wwh, wwl, a0, a1);
+        ff_add(vwh, vwl, b0, b1);
+        ff_add(vvh, vvl, c0, c1);
       }
       if (lane == 0) {
-        wred[3 * warp] = ww;
-        wred[3 * warp + 1] = vw;
-        wred[3 * warp + 2] = vv;
+        float *wr = reinterpret_cast<float *>(wred) + 6 * warp;
+        wr[0] = wwh;
+        wr[1] = wwl;
+        wr[2] = vwh;
+        wr[3] = vwl;
+        wr[4] = vvh;
+        wr[5] = vvl;
       }
       __syncthreads();
       // this CTA's rows of w into the same place of every other CTA's next iterate
@@ -342,54 +383,61 @@ __global__ void __launch_bounds__(kSrvPowerThreads, 2) srv_power_kernel(const Sr
       }
       const int par = (int)(phase & 1u);
       if (warp == 0) {
-        // the warps' partials, summed over lanes 0..7 (xor tree: every lane ends with the sums),
-        // then lane c stores them into CTA c's slot for this rank
-        double t0 = 0.0, t1 = 0.0, t2 = 0.0;
+        // the warps' pairs, summed over lanes 0..7 (xor tree: every lane ends with the
+        // sums), then lane c stores them into CTA c's slot for this rank
+        float x[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
         if (lane < nwarps) {
-          t0 = wred[3 * lane];
-          t1 = wred[3 * lane + 1];
-          t2 = wred[3 * lane + 2];
+          const float *wr = reinterpret_cast<const float *>(wred) + 6 * lane;
+#pragma unroll
+          for (int t = 0; t < 6; ++t) x[t] = wr[t];
         }
 #pragma unroll
         for (int o = 4; o > 0; o >>= 1) {
-          t0 += __shfl_xor_sync(0xffffffffu, t0, o);
-          t1 += __shfl_xor_sync(0xffffffffu, t1, o);
-          t2 += __shfl_xor_sync(0xffffffffu, t2, o);
+          float y[6];
+#pragma unroll
+          for (int t = 0; t < 6; ++t) y[t] = __shfl_xor_sync(0xffffffffu, x[t], o);
+#pragma unroll
+          for (int t = 0; t < 6; t += 2) ff_add(x[t], x[t + 1], y[t], y[t + 1]);
         }
         if (lane < (int)C) {
           const uint32_t pa = peer_addr(smem_addr(sm.part + (par * kMaxCluster + rank) * kPartSlot), (uint32_t)lane);
-          st_peer_f64(pa, t0);
-          st_peer_f64(pa + 8, t1);
-          st_peer_f64(pa + 16, t2);
+          asm volatile("st.shared::cluster.v2.f32 [%0], {%1, %2};" ::"r"(pa), "f"(x[0]), "f"(x[1]) : "memory");
+          asm volatile("st.shared::cluster.v2.f32 [%0], {%1, %2};" ::"r"(pa + 8), "f"(x[2]), "f"(x[3]) : "memory");
+          asm volatile("st.shared::cluster.v2.f32 [%0], {%1, %2};" ::"r"(pa + 16), "f"(x[4]), "f"(x[5]) : "memory");
         }
       }
       cluster_sync_all();
       ++phase;
       if (warp == 0) {
-        // the C ranks' partials, same xor tree in every CTA, so all take the same decision
-        double t0 = 0.0, t1 = 0.0, t2 = 0.0;
+        // the C ranks' pairs, same xor tree in every CTA, so all take the same decision
+        float x[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
         if (lane < (int)C) {
-          const double *ps = sm.part + (par * kMaxCluster + lane) * kPartSlot;
-          t0 = ps[0];
-          t1 = ps[1];
-          t2 = ps[2];
+          const float *ps = reinterpret_cast<const float *>(sm.part + (par * kMaxCluster + lane) * kPartSlot);
+#pragma unroll
+          for (int t = 0; t < 6; ++t) x[t] = ps[t];
         }
 #pragma unroll
         for (int o = 4; o > 0; o >>= 1) {
-          t0 += __shfl_xor_sync(0xffffffffu, t0, o);
-          t1 += __shfl_xor_sync(0xffffffffu, t1, o);
-          t2 += __shfl_xor_sync(0xffffffffu, t2, o);
+          float y[6];
+#pragma unroll
+          for (int t = 0; t < 6; ++t) y[t] = __shfl_xor_sync(0xffffffffu, x[t], o);
+#pragma unroll
+          for (int t = 0; t < 6; t += 2) ff_add(x[t], x[t + 1], y[t], y[t + 1]);
         }
         if (lane == 0) {
+          // t0 = ||r||^2 qs^2, t1 = (v.r) qs, t2 = v.v for the new r = pw w
+          const double t0 = ff_value(x[0], x[1]), t1 = ff_value(x[2], x[3]), t2 = ff_value(x[4], x[5]);
           const int it1 = it + 1;
           int st = 0, done = 0;
-          double sc = 0.0;
-          const double floor = 1e-30 * rank_scale;  // ||w|| <= floor: B v0 vanished
-          if (!(t0 > floor * floor)) {
+          float scn = 0.f;
+          double vs = 0.0;
+          if (!(t0 > floor_s)) {  // ||w|| <= floor: B v0 vanished
             st = 2;
             done = 1;
           } else {
-            sc = inv_sqrt(t0);
+            // 1 / ||r|| = qs / sqrt(t0): FP32 for the next application (its scale only),
+            // FP64 on exit
+            scn = x[0] > 1e-30f ? __fmul_rn(rsqrtf(x[0]), qs) : (float)((double)qs / sqrt(t0));
             if (q.iters_override) {
               done = it1 >= q.iters_override[l];
             } else {
@@ -401,10 +449,12 @@ __global__ void __launch_bounds__(kSrvPowerThreads, 2) srv_power_kernel(const Sr
                 st = 1;
               }
             }
+            if (done) vs = (double)qs / sqrt(t0);
           }
-          s_scal[0] = sc;
+          s_scal[0] = vs;
           s_scal[1] = (double)st;
           s_scal[2] = (double)done;
+          s_scal[3] = (double)scn;
         }
       }
       __syncthreads();
@@ -412,12 +462,13 @@ __global__ void __launch_bounds__(kSrvPowerThreads, 2) srv_power_kernel(const Sr
       const int st = (int)s_scal[1];
       const bool done = s_scal[2] != 0.0;
       if (st == 2) {
-        status = 2;  // vb[cur] still holds v0 of this step
+        status = 2;  // vb[cur] still holds the raw iterate of this step
         break;
       }
-      vscale = s_scal[0];
+      sc = (float)s_scal[3];
       cur ^= 1;
       if (done) {
+        vscale = s_scal[0];
         status = st;
         break;
       }

@@ -348,6 +348,25 @@ def test_tsvd_power_kernels_match_oracle(pk, m, n, k, rho):
         assert np.max(np.abs(np.asarray(r.V[:, l], dtype=np.float64) - o.V[:, l])) < 1e-4
 
 
+@pytest.mark.parametrize("pk", [B.TSVD_POWER_GRID, B.TSVD_POWER_CLUSTER])
+@pytest.mark.parametrize("e", [-40, 30])
+def test_tsvd_power_kernels_scale_invariant(pk, e):
+    """sigma(2^e A) = 2^e sigma(A) and the same vectors: Alg. 2 is invariant
+    under scaling A, and the power kernels keep their FP32 sums inside range
+    for Gram diagonals from ~1e-24 to ~1e18 (the oracle's trajectory forced)."""
+    m, n, k = 2048, 256, 8
+    inp = synth.dense_prescribed(m, n, synth.spectrum_geometric(n, 0.8), 1e-6, seed=4)
+    x = synth.start_normals(n, k, seed=5)
+    o = ref.tsvd_dense(inp["A"], k, 1e-10, x_start=x, sign_convention=True)
+    As = np.ldexp(inp["A"], e).astype(np.float32)
+    r = tsvd(torch.from_numpy(As).cuda(), k, 1e-10, start_draws=x, iters_override=o.iters,
+             sign_convention=True, power_kernel=pk)
+    assert r.status == B.TSVD_OK
+    assert np.max(np.abs(np.ldexp(r.sigma, -e) - o.sigma) / o.sigma) <= 1e-5
+    for l in ref.gapped_indices(o.sigma ** 2, k):
+        assert np.max(np.abs(np.asarray(r.V[:, l], dtype=np.float64) - o.V[:, l])) < 1e-4
+
+
 def test_tsvd_cluster_power_builtin_draws_and_own_convergence():
     """The cluster kernel draws x_l from the built-in Philox stream itself and
     takes its own convergence decisions (counts within one of the oracle's)."""
