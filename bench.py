@@ -556,8 +556,9 @@ def c1_latency(reps: int = 50):
     inp = synth.dense_prescribed(2048, 256, synth.spectrum_geometric(256, 0.8), 1e-6, seed=0)
     dA = torch.from_numpy(inp["A"]).cuda()
 
-    def run(pk):
-        plan = Plan(dA, 8, 1e-8, precision=0, out_device=True, time_kernels=True, power_kernel=pk)
+    def run(pk, ctas=0):
+        plan = Plan(dA, 8, 1e-8, precision=0, out_device=True, time_kernels=True, power_kernel=pk,
+                    power_ctas=ctas)
         for _ in range(5):
             plan.factor(dA)
         torch.cuda.synchronize()
@@ -576,12 +577,20 @@ def c1_latency(reps: int = 50):
                 "us_per_power_application": round(rep["power_ms"] * 1e3 / max(rep["applications"], 1), 3),
                 "applications": rep["applications"], "kernel_launches_per_tsvd": rep["kernel_launches"],
                 "phases_ms": {"gram": round(rep["gram_ms"], 4), "power": round(rep["power_ms"], 4),
-                              "left": round(rep["left_ms"], 4)}}
+                              "left": round(rep["left_ms"], 4)},
+                "power_cluster_ctas": rep.get("power_cluster", 0)}
 
     out = {"workload": "m=2048, n=256, sigma_i=0.8^i + 1e-6 noise, k=8, eps=1e-8, FP32 Gram, A in HBM",
            "power_kernel": "cluster (all triplets in one launch on one thread-block cluster)"}
     out.update(run(B.TSVD_POWER_AUTO))
+    out["power_cluster"] = out.pop("power_cluster_ctas")
+    out["cluster_sizes"] = {}
+    for c in (1, 2, 4, 8):
+        t = run(B.TSVD_POWER_CLUSTER, c)
+        out["cluster_sizes"][str(t.pop("power_cluster_ctas"))] = {
+            "ms_per_tsvd": t["ms_per_tsvd"], "us_per_power_application": t["us_per_power_application"]}
     out["grid_kernel"] = run(B.TSVD_POWER_GRID)
+    out["grid_kernel"].pop("power_cluster_ctas")
     return out
 
 

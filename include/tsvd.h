@@ -124,7 +124,10 @@ typedef struct {
                                     tiles on the device or, when they do not fit the
                                     budget, in page-locked host memory; 0 = only when
                                     the whole Gram matrix does not fit the budget */
-  int32_t reserved[3];
+  int32_t power_ctas;            /* CLUSTER: CTAs of the thread-block cluster (1, 2, 4
+                                    or 8, reduced while a CTA would own no rows);
+                                    0 = the planner's choice */
+  int32_t reserved[2];
 } tsvd_options;
 
 /* Kernels of the dense power phase.  GRID: one cooperative launch per

@@ -86,7 +86,7 @@ class Plan:
                  block_rows: int = 0, n_buffers: int = 3, max_iter: int = 10000, iters_override=None,
                  start_draws=None, seed: int = 0, out_device: bool = False, sign_convention: bool = False,
                  force_stream: bool = False, time_kernels: bool = False, power_kernel: int = B.TSVD_POWER_AUTO,
-                 gram_tile: int = 0):
+                 gram_tile: int = 0, power_ctas: int = 0):
         import torch
         self.lib = B.load()
         self.mat, self._keep = make_matrix(A)
@@ -104,6 +104,7 @@ class Plan:
         opt.time_kernels = int(bool(time_kernels))
         opt.power_kernel = int(power_kernel)
         opt.gram_tile = int(gram_tile)
+        opt.power_ctas = int(power_ctas)
         mn = min(self.mat.m, self.mat.n)
         self.k = mn if k == -1 else int(k)
         if iters_override is not None:

@@ -503,6 +503,9 @@ tsvd_status tsvd_plan(tsvd_plan_t *out, const tsvd_matrix *A, int64_t k, double 
   if (opt.block_rows < 0) return TSVD_EINVAL;
   if (opt.power_kernel < TSVD_POWER_AUTO || opt.power_kernel > TSVD_POWER_CLUSTER) return TSVD_EINVAL;
   if (opt.gram_tile < 0 || opt.gram_tile % 256 != 0) return TSVD_EINVAL;
+  if (opt.power_ctas != 0 && opt.power_ctas != 1 && opt.power_ctas != 2 && opt.power_ctas != 4 &&
+      opt.power_ctas != 8)
+    return TSVD_EINVAL;
   if (opt.gram_tile > 0 && A->kind != TSVD_DENSE_F32_ROWMAJOR) return TSVD_EINVAL;
   const bool cluster_fits = A->kind == TSVD_DENSE_F32_ROWMAJOR && mn <= kSrvMaxDim && k <= kSrvMaxK;
   if (opt.power_kernel == TSVD_POWER_CLUSTER && !cluster_fits) {
@@ -830,7 +833,7 @@ tsvd_status power_cluster_dense(Run &r, double *G64, float *G32, double *V64, fl
   TSVD_TRY(device_info(&di));
   const size_t static_bytes = 24 * 1024;  // the kernel's static shared arrays, rounded up
   const size_t cap = di.smem_optin > static_bytes ? di.smem_optin - static_bytes : 0;
-  const int C = srv_clamp_cluster(n, 8);
+  const int C = srv_clamp_cluster(n, p->opt.power_ctas > 0 ? p->opt.power_ctas : 8);
   const int resident = srv_power_smem(n, C, 1) <= cap ? 1 : 0;
   const size_t smem = srv_power_smem(n, C, resident);
   if (smem > cap) return TSVD_EUNSUPPORTED;

@@ -348,6 +348,22 @@ def test_tsvd_power_kernels_match_oracle(pk, m, n, k, rho):
         assert np.max(np.abs(np.asarray(r.V[:, l], dtype=np.float64) - o.V[:, l])) < 1e-4
 
 
+@pytest.mark.parametrize("ctas", [1, 2, 4])
+@pytest.mark.parametrize("n", [256, 520])
+def test_tsvd_cluster_sizes_follow_oracle(ctas, n):
+    """The cluster kernel on 1, 2 or 4 CTAs (Gram rows resident in shared
+    memory or read from L2) follows the oracle's trajectory."""
+    m, k = 3000, 12
+    inp = synth.dense_prescribed(m, n, synth.spectrum_geometric(n, 0.82), 1e-7, seed=n + ctas)
+    x = synth.start_normals(n, k, seed=3)
+    o = ref.tsvd_dense(inp["A"], k, 1e-10, x_start=x, sign_convention=True)
+    r = tsvd(torch.from_numpy(inp["A"]).cuda(), k, 1e-10, start_draws=x, iters_override=o.iters,
+             sign_convention=True, power_kernel=B.TSVD_POWER_CLUSTER, power_ctas=ctas)
+    assert r.report["power_cluster"] == ctas
+    assert r.iters == o.iters
+    _compare(r, o, k, gapped=ref.gapped_indices(o.sigma ** 2, k))
+
+
 @pytest.mark.parametrize("pk", [B.TSVD_POWER_GRID, B.TSVD_POWER_CLUSTER])
 @pytest.mark.parametrize("e", [-40, 30])
 def test_tsvd_power_kernels_scale_invariant(pk, e):
