@@ -237,7 +237,9 @@ __global__ void __launch_bounds__(kSrvPowerThreads, 2) srv_power_kernel(const Sr
   const float pw = __int_as_float((shift + 127) << 23);
   constexpr float qs = 1048576.f;  // 2^20
   const double pq2 = (double)pw * (double)pw * (double)qs * (double)qs;
-  __syncthreads();
+  // every CTA of the cluster is running before any of them stores into another's
+  // shared memory
+  cluster_sync_all();
   uint32_t phase = 0;  // running count of cluster exchanges (selects the partial slots)
   const bool vec = (d % 4) == 0;
   double sig0sq = 1.0;  // sigma_0^2 (every CTA forms the same value)

@@ -371,10 +371,14 @@ void complete(tsvd_server_s *sv, const ReqPtr &r, tsvd_status st) {
       apps += info[4 * l];
       if (info[4 * l + 1] == 1) flags |= TSVD_FLAG_NOCONV;
       if (info[4 * l + 1] == 2) flags |= TSVD_FLAG_RANK;
+      if (info[4 * l + 2]) flags |= TSVD_FLAG_TIMEOUT;
     }
     for (int l = 1; l < r->k; ++l)
       if (sg[l] > sg[l - 1]) flags |= TSVD_FLAG_NONMONOTONE;
-    status = (flags & TSVD_FLAG_RANK) ? TSVD_ERANK : (flags & TSVD_FLAG_NOCONV) ? TSVD_ENOCONV : TSVD_OK;
+    status = (flags & TSVD_FLAG_TIMEOUT) ? TSVD_ETIMEDOUT
+             : (flags & TSVD_FLAG_RANK)  ? TSVD_ERANK
+             : (flags & TSVD_FLAG_NOCONV) ? TSVD_ENOCONV
+                                          : TSVD_OK;
   }
   r->rec.status = status;
   r->rec.flags = flags;
