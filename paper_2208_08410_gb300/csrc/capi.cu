@@ -61,6 +61,9 @@ tsvd_status device_info(DeviceInfo *out) {
     int optin = 0;
     TSVD_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
     d.smem_optin = (size_t)optin;
+    int l2 = 0;
+    TSVD_CUDA(cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev));
+    d.l2_bytes = (size_t)l2;
     cache = d;
   }
   *out = cache;

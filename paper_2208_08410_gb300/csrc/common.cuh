@@ -60,6 +60,7 @@ struct DeviceInfo {
   int sms = 0;
   int cc_major = 0, cc_minor = 0;
   size_t smem_optin = 0;
+  size_t l2_bytes = 0;
 };
 tsvd_status device_info(DeviceInfo *out);
 

@@ -54,6 +54,8 @@ struct PowerArgs {
   unsigned *bar;       // 2 counters
   int *err;
   int64_t rows_per_block;
+  int keep8;           // row pairs p with (p mod 8) < keep8 are read with normal loads, the others
+                       // evict-first, so the kept share of G32 stays in L2 across iterations
 };
 
 // s + e == a + b exactly (Knuth's TwoSum, FP32, no FMA contraction possible)
@@ -174,14 +176,23 @@ __global__ void __launch_bounds__(PT, 1) power_dense_kernel(PowerArgs a) {
         const float4 *gb = reinterpret_cast<const float4 *>(g1);
         const float4 *v4 = reinterpret_cast<const float4 *>(vs);
         const int64_t n4 = n >> 2;
+        const bool keep = ((i >> 1) & 7) < a.keep8;
         int64_t q = lane;
         // sixteen independent 16-byte loads in flight per lane
         for (; q + 32 * 7 < n4; q += 32 * 8) {
           float4 ra[8], rb[8];
+          if (keep) {
 #pragma unroll
-          for (int u = 0; u < 8; ++u) {
-            ra[u] = __ldg(ga + q + 32 * u);
-            rb[u] = __ldg(gb + q + 32 * u);
+            for (int u = 0; u < 8; ++u) {
+              ra[u] = __ldg(ga + q + 32 * u);
+              rb[u] = __ldg(gb + q + 32 * u);
+            }
+          } else {
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+              ra[u] = __ldcs(ga + q + 32 * u);
+              rb[u] = __ldcs(gb + q + 32 * u);
+            }
           }
 #pragma unroll
           for (int u = 0; u < 8; ++u) {
@@ -592,6 +603,12 @@ tsvd_status launch_power_dense(int64_t n, const float *G32, const double *G64, c
   a.part = reinterpret_cast<double *>(a.wb1 + round_up(n, 64));
   a.ps = (int)power_part_stride(l);
   a.rows_per_block = rows_per_block;
+  // G32 is read once per iteration.  When it is larger than ~60 % of L2, only
+  // that share of its rows (every row pair whose index mod 8 is below keep8,
+  // spread over all blocks) uses normal loads; the rest are evict-first, so
+  // they do not push the kept rows out and those are L2 hits next iteration.
+  const double l2_share = 0.6 * (double)di.l2_bytes, g_bytes = 4.0 * (double)n * (double)n;
+  a.keep8 = g_bytes <= l2_share ? 8 : (int)(8.0 * l2_share / g_bytes);
   TSVD_CUDA(cudaMemsetAsync(s, 0, 256, stream));
   void *args[] = {&a};
   TSVD_CUDA(cudaLaunchCooperativeKernel((void *)power_dense_kernel, dim3((unsigned)grid), dim3(PT),
