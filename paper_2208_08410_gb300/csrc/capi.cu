@@ -830,7 +830,7 @@ tsvd_status power_cluster_dense(Run &r, double *G64, float *G32, double *V64, fl
   int32_t *d_iters = reinterpret_cast<int32_t *>(base + round_up(sizeof(SrvReq), 256));
   uint32_t *d_flag = reinterpret_cast<uint32_t *>(base + round_up(sizeof(SrvReq), 256) + 256);
   static_assert(kSrvMaxK * 4 <= 256, "forced counts fit their slot");
-  if (round_up(sizeof(SrvReq), 256) + 512 > p->b_pscr) return TSVD_EINVAL;
+  if ((size_t)round_up(sizeof(SrvReq), 256) + 512 > p->b_pscr) return TSVD_EINVAL;
 
   DeviceInfo di;
   TSVD_TRY(device_info(&di));
