@@ -60,7 +60,7 @@ typedef enum {
   TSVD_ETIMEDOUT = 5,    /* a bounded device or host wait gave up */
   TSVD_ENOCONV = 6,      /* max_iter reached for some triplet; outputs written */
   TSVD_ERANK = 7,        /* B v0 vanished (rank(A) < k); outputs written */
-  TSVD_EUNSUPPORTED = 8  /* valid request outside what this build implements */
+  TSVD_EUNSUPPORTED = 8  /* valid request outside what this library implements */
 } tsvd_status;
 
 typedef enum { TSVD_DENSE_F32_ROWMAJOR = 0, TSVD_CSR_F32_I32_I64 = 1 } tsvd_kind;
