@@ -415,9 +415,10 @@ typedef struct {
   int32_t max_wave;       /* most requests one wave launches together (0: 64) */
   int32_t cluster_cap;    /* largest thread-block cluster of the power kernel
                              (1, 2, 4 or 8; 0: 8) */
-  size_t host_staging;    /* page-locked, device-mapped memory the kernels
-                             write each request's results into before they
-                             are copied to the caller (0: 2 GiB) */
+  size_t host_staging;    /* page-locked host memory each request's results
+                             are copied into from its device output region
+                             before tsvd_server_wait hands them to the
+                             caller (0: 2 GiB) */
   int32_t reserved[6];
 } tsvd_server_options;
 
