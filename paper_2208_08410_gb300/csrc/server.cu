@@ -40,8 +40,8 @@ namespace {
 constexpr size_t kAlign = 256;
 inline size_t al(size_t x) { return (x + kAlign - 1) & ~(kAlign - 1); }
 
-// First-fit allocator over one allocation (device memory, or page-locked host
-// memory mapped into the device's address space); free ranges are kept by
+// First-fit allocator over one allocation (device memory, or the page-locked
+// host staging area the results are copied into); free ranges are kept by
 // offset and merged with their neighbours on release.
 class Arena {
  public:
