@@ -456,8 +456,9 @@ TSVD_API tsvd_status tsvd_server_create(tsvd_server_t *server, const tsvd_server
  *            valid and unchanged until the request completes.  Page-locked
  *            memory (tsvd_host_alloc) lets the copy overlap other work.
  *   U, sigma, V  host outputs: U m x k and V n x k column-major FP32, sigma k
- *            FP64; the kernels write the results into the server's
- *            page-locked staging and tsvd_server_wait copies them here.
+ *            FP64; the kernels write the results into the request's device
+ *            output region, the scheduler copies that to the server's
+ *            page-locked staging, and tsvd_server_wait copies them here.
  *   k        1 <= k <= min(m, n), k <= 32;  min(m, n) <= 2048
  *   eps, max_iter, seed, sign_convention, iters_override  as for tsvd_plan /
  *            tsvd_options (start draws: the built-in Philox-4x32-10 stream of
@@ -508,10 +509,11 @@ TSVD_API int32_t tsvd_server_cluster_for(tsvd_server_t server, int64_t d);
 /*
  * Pick the power-kernel cluster size per Gram dimension by measurement: for
  * d in {64, 128, 256, 512, 1024, 2048} and each cluster size up to
- * cluster_cap, time `iters` iterations of synthetic requests (as many as fill
- * the GPU) and keep the size with the highest iterations per second over the
- * whole GPU.  Call with no requests in flight.  The table is used by later
- * submissions; tsvd_server_cluster_for reads it.
+ * cluster_cap, time `iters` iterations of one synthetic request alone and of
+ * as many as fill the GPU, and keep the size with the highest iterations per
+ * second over the whole GPU among those whose single-request time is within
+ * 4x of the fastest.  Call with no requests in flight.  The table is used by
+ * later submissions; tsvd_server_cluster_for reads it.
  */
 TSVD_API tsvd_status tsvd_server_autotune(tsvd_server_t server, int32_t iters);
 
