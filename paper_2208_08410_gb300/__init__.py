@@ -80,7 +80,17 @@ def make_matrix(A):
 
 
 class Plan:
-    """A tsvd plan plus its device workspace (torch-allocated)."""
+    """A tsvd plan plus its device workspace (torch-allocated).
+
+    The keyword options map one to one onto `tsvd_options` in include/tsvd.h:
+    precision (TSVD_GRAM_FP32 / TF32 / TF32X3 / BF16X3), device_budget (bytes,
+    0 = none), block_rows and n_buffers (the streamed ring), max_iter,
+    iters_override (k forced application counts), start_draws (min(m, n) x k
+    N(0,1) draws instead of the built-in Philox stream), seed, out_device
+    (outputs in device memory), sign_convention, force_stream, time_kernels,
+    power_kernel (TSVD_POWER_AUTO / GRID / CLUSTER), gram_tile (orthogonal
+    batching panel width) and power_ctas (cluster size of the cluster kernel).
+    `factor()` runs the t-SVD; `close()` releases the plan."""
 
     def __init__(self, A, k: int, eps: float, *, precision: int = B.TSVD_GRAM_FP32, device_budget: int = 0,
                  block_rows: int = 0, n_buffers: int = 3, max_iter: int = 10000, iters_override=None,
