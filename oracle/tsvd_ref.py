@@ -420,13 +420,20 @@ def dist_compute_v0(X, U, S, V, v0, n_b: int, N: int):
 # Checks used by the tests (closed forms, invariants)
 # ----------------------------------------------------------------------------
 def subspace_angle(a: np.ndarray, b: np.ndarray) -> float:
-    """Largest principal angle between span(a) and span(b) (columns)."""
+    """Largest principal angle between span(a) and span(b), both of the same
+    dimension (columns).  With Qa, Qb orthonormal bases, sin of the angle is
+    the 2-norm of the part of Qb outside span(a), ||Qb - Qa Qa^T Qb||_2, and
+    its cos the smallest singular value of Qa^T Qb; atan2 of the pair keeps
+    full relative accuracy at tiny angles, where acos of the cosine alone
+    loses about half the digits (Bjorck & Golub 1973; Knyazev & Argentati
+    2002 for the sine form)."""
     a = np.atleast_2d(np.asarray(a, dtype=np.float64).T).T
     b = np.atleast_2d(np.asarray(b, dtype=np.float64).T).T
     qa, _ = np.linalg.qr(a)
     qb, _ = np.linalg.qr(b)
-    s = np.linalg.svd(qa.T @ qb, compute_uv=False)
-    return float(math.acos(min(1.0, max(0.0, s.min()))))
+    c = float(np.linalg.svd(qa.T @ qb, compute_uv=False).min())
+    s = float(np.linalg.norm(qb - qa @ (qa.T @ qb), 2))
+    return float(math.atan2(s, c))
 
 
 def vector_angle(a: np.ndarray, b: np.ndarray) -> float:

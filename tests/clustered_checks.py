@@ -19,6 +19,9 @@ def check_clustered(r, sig_o, V_o, k, prec, sig_truth):
         return
     V = np.asarray(r.V, dtype=np.float64)
     gapped = [i for i in ref.gapped_indices(sig_truth ** 2, k) if i not in C4_PAIR]
+    # harmonic spectrum: every triplet but the clustered pair is gapped (the smallest gap, at
+    # i = 31, is 1 - (32/33)^2 = 0.0597), so 30 vectors are graded one by one
+    assert gapped == [i for i in range(k) if i not in C4_PAIR], gapped
     for l in gapped:
         assert ref.vector_angle(V[:, l], V_o[:, l]) <= 1e-4, l
     assert ref.subspace_angle(V[:, list(C4_PAIR)], V_o[:, list(C4_PAIR)]) <= 1e-4

@@ -89,6 +89,7 @@ def test_server_mixed_wave_matches_oracle():
             assert info["applications"] == sum(o.iters)
             m, n = A.shape
             gapped = ref.gapped_indices(o.sigma ** 2, k)
+            assert gapped == list(range(k)), gapped  # geometric, rho <= 0.9: every gap >= 0.19
             # U is m x k and V is n x k, column-major (stored as k rows)
             for l in gapped:
                 assert ref.vector_angle(V[l].astype(np.float64), o.V[:, l]) <= 1e-4, (m, n, l)
@@ -198,7 +199,9 @@ def test_server_sparse_requests_beside_dense_ones():
             assert st == B.TSVD_OK, (st, sv.last_error())
             assert info["applications"] == sum(o.iters)
             assert np.max(np.abs(s_ - o.sigma) / o.sigma) <= 1e-5
-            for l in ref.gapped_indices(o.sigma ** 2, k):
+            gapped = ref.gapped_indices(o.sigma ** 2, k)
+            assert gapped and gapped[0] == 0, gapped  # the leading (Perron) triplet of a positive A is gapped
+            for l in gapped:
                 assert ref.vector_angle(V[l].astype(np.float64), o.V[:, l]) <= 1e-4
                 assert ref.vector_angle(U[l].astype(np.float64), o.U[:, l]) <= 1e-4
         for t, k, s_, o in dense:

@@ -317,6 +317,81 @@ def test_csr_generator_structure():
     assert np.all((csr["values"] >= 0) & (csr["values"] < 1))
 
 
+# ---------------------------------------------------------------- grading helpers
+# The parity tests grade a singular vector only when its eigenvalue is gapped
+# (relative gap >= 0.05 to both neighbours) and grade a clustered pair as a
+# 2-D subspace by its largest principal angle.  These pins tie the helpers
+# that make those decisions to closed forms.
+def _planes(theta, phi, n=7, perm=None, signs=None):
+    """span(e0, e1) and span(cos(phi) e0 + sin(phi) e2, cos(theta) e1 + sin(theta) e3):
+    principal angles phi and theta, built from exact entries (row permutations
+    and sign flips keep them exact)."""
+    a = np.zeros((n, 2))
+    a[0, 0] = a[1, 1] = 1.0
+    b = np.zeros((n, 2))
+    b[0, 0], b[2, 0] = math.cos(phi), math.sin(phi)
+    b[1, 1], b[3, 1] = math.cos(theta), math.sin(theta)
+    if perm is not None:
+        a, b = a[perm], b[perm]
+    if signs is not None:
+        a, b = a * signs[:, None], b * signs[:, None]
+    return a, b
+
+
+def _grading_pins_hold():
+    """True when both grading helpers agree with their closed forms."""
+    ok = True
+    rng = np.random.default_rng(3)
+    for theta in (1e-6, 1e-3, 0.5):
+        for perm, signs in ((None, None), (rng.permutation(7), rng.choice([-1.0, 1.0], 7))):
+            a, b = _planes(theta, theta / 3, perm=perm, signs=signs)
+            for x, y in ((a, b), (b, a)):
+                ok &= abs(ref.subspace_angle(x, y) - theta) <= 1e-12 * theta
+    # the same span in another basis (an in-plane rotation) has angle zero
+    a, _ = _planes(0.1, 0.05)
+    c, s_ = math.cos(0.7), math.sin(0.7)
+    ok &= ref.subspace_angle(a, a @ np.array([[c, -s_], [s_, c]])) <= 1e-15
+    # a one-dimensional span is the vector angle
+    ok &= abs(ref.subspace_angle(a[:, 0], _planes(1e-6, 1e-6)[1][:, 0]) - 1e-6) <= 1e-18
+    # hand-built spectrum: i = 1 is 0.0449 / 0.9 = 0.0499 under the bar on its right,
+    # i = 2 is 0.0449 / 0.8551 = 0.0525 over it on its left, i = 3 and 4 are 0.0199 apart,
+    # i = 5 has its right neighbour (beyond k = 6) only 1e-4 below it, i = 0 has no left one
+    lam = np.array([1.0, 0.9, 0.8551, 0.5, 0.4801, 0.3, 0.2999, 0.1])
+    ok &= ref.gapped_indices(lam, 6) == [0, 2]
+    ok &= ref.gapped_indices(lam, 8) == [0, 2, 7]
+    lam2 = np.array([4.0, 2.0, 1.0, 0.0])  # a zero eigenvalue is never graded
+    ok &= ref.gapped_indices(lam2, 4) == [0, 1, 2]
+    ok &= ref.gapped_indices(lam2, 3, rel_gap=0.6) == [2]  # relative gaps 0.5, 0.5, 1.0
+    return bool(ok)
+
+
+def test_subspace_angle_closed_forms():
+    """Largest principal angle of two planes built at a known angle (1e-6,
+    1e-3, 0.5) to 1e-12 relative; zero for the same span in a rotated basis."""
+    assert _grading_pins_hold()
+
+
+def test_vector_angle_closed_forms():
+    e0, e1 = np.eye(5)[0], np.eye(5)[1]
+    for theta in (1e-7, 1e-4, 0.3, 1.2):
+        b = math.cos(theta) * e0 + math.sin(theta) * e1
+        assert abs(ref.vector_angle(e0, b) - theta) <= 1e-12 * theta
+        assert abs(ref.vector_angle(e0, -3.0 * b) - theta) <= 1e-12 * theta  # sign and scale free
+    assert ref.vector_angle(e0, e1) == pytest.approx(math.pi / 2, rel=1e-15)
+
+
+def test_gapped_indices_hand_built_spectrum():
+    lam = np.array([1.0, 0.9, 0.8551, 0.5, 0.4801, 0.3, 0.2999, 0.1])
+    # relative gaps min(left, right) / lam_i: 0.1, 0.0499, 0.0525, 0.0398, 0.0414, 3.3e-4, 3.3e-4, 1.999
+    assert ref.gapped_indices(lam, 6) == [0, 2]
+    assert ref.gapped_indices(lam, 8) == [0, 2, 7]
+    assert ref.gapped_indices(lam, 3, rel_gap=0.0) == [0, 1, 2]
+    # a geometric spectrum rho^(2i): every gap is 1 - rho^2
+    assert ref.gapped_indices(0.97 ** (2 * np.arange(10.0)), 9) == list(range(9))  # 0.0591
+    assert ref.gapped_indices(0.98 ** (2 * np.arange(10.0)), 9) == []  # 0.0396
+    assert ref.gapped_indices(np.array([4.0, 2.0, 1.0, 0.0]), 4) == [0, 1, 2]
+
+
 # ---------------------------------------------------------------- planted mistakes
 def _pins_hold():
     """Run a compact set of pins; returns True when all hold."""
@@ -370,6 +445,56 @@ def test_pins_catch_planted_mistakes(monkeypatch):
         return M @ M.T if M.shape[0] == M.shape[1] else M.T @ M
     monkeypatch.setattr(ref, "gram", gram_t)
     assert not _pins_hold()
+    monkeypatch.undo()
+
+    # grading helpers: each plausible slip must break a closed form
+    assert _grading_pins_hold()
+    true_angle = ref.subspace_angle
+
+    def smallest_angle(a, b):  # cos from the largest singular value: the smallest principal angle
+        qa, _ = np.linalg.qr(np.atleast_2d(np.asarray(a, float).T).T)
+        qb, _ = np.linalg.qr(np.atleast_2d(np.asarray(b, float).T).T)
+        return math.acos(min(1.0, np.linalg.svd(qa.T @ qb, compute_uv=False).max()))
+
+    def acos_form(a, b):  # the cosine alone: half the digits lost at tiny angles
+        qa, _ = np.linalg.qr(np.atleast_2d(np.asarray(a, float).T).T)
+        qb, _ = np.linalg.qr(np.atleast_2d(np.asarray(b, float).T).T)
+        return math.acos(min(1.0, np.linalg.svd(qa.T @ qb, compute_uv=False).min()))
+
+    for bad in (smallest_angle, acos_form, lambda a, b: true_angle(a, b[:, ::-1] if b.ndim > 1 else b) / 2):
+        monkeypatch.setattr(ref, "subspace_angle", bad)
+        assert not _grading_pins_hold()
+    monkeypatch.undo()
+
+    def right_only(lam, k, rel_gap=0.05):  # left neighbour ignored
+        return [i for i in range(k) if lam[i] > 0 and
+                ((lam[i] - lam[i + 1]) if i + 1 < len(lam) else np.inf) / lam[i] >= rel_gap]
+
+    def absolute_gap(lam, k, rel_gap=0.05):  # gap not divided by lam_i
+        out = []
+        for i in range(k):
+            le = lam[i - 1] - lam[i] if i > 0 else np.inf
+            ri = lam[i] - lam[i + 1] if i + 1 < len(lam) else np.inf
+            if lam[i] > 0 and min(le, ri) >= rel_gap:
+                out.append(i)
+        return out
+
+    def truncated(lam, k, rel_gap=0.05):  # neighbours beyond k ignored
+        return true_gapped(np.asarray(lam)[:k], k, rel_gap)
+
+    def over_previous(lam, k, rel_gap=0.05):  # divided by lam_{i-1} instead of lam_i
+        out = []
+        for i in range(k):
+            le = lam[i - 1] - lam[i] if i > 0 else np.inf
+            ri = lam[i] - lam[i + 1] if i + 1 < len(lam) else np.inf
+            if lam[i] > 0 and min(le, ri) / lam[max(i - 1, 0)] >= rel_gap:
+                out.append(i)
+        return out
+
+    true_gapped = ref.gapped_indices
+    for bad in (right_only, absolute_gap, truncated, over_previous):
+        monkeypatch.setattr(ref, "gapped_indices", bad)
+        assert not _grading_pins_hold(), bad.__name__
 
 
 def test_stacked_workload_identities():
