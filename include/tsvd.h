@@ -127,7 +127,16 @@ typedef struct {
   int32_t power_ctas;            /* CLUSTER: CTAs of the thread-block cluster (1, 2, 4
                                     or 8, reduced while a CTA would own no rows);
                                     0 = the planner's choice */
-  int32_t reserved[2];
+  int32_t wait_limit_ns;         /* limit in nanoseconds of the pipeline waits of the
+                                    tensor-core Gram kernel (TF32, TF32X3, BF16X3) in
+                                    the dense Gram pass; 0 = the default 2 s, < 0 =
+                                    TSVD_EINVAL.  A limit shorter than a wait normally
+                                    takes makes a correct kernel give up: it raises its
+                                    status word, stops issuing, lets its own copies and
+                                    MMAs complete, frees its tensor memory and returns,
+                                    and tsvd_factor returns TSVD_ETIMEDOUT with
+                                    TSVD_FLAG_TIMEOUT set.  It exists to test that path */
+  int32_t reserved;
 } tsvd_options;
 
 /* Kernels of the dense power phase.  GRID: one cooperative launch per
@@ -394,8 +403,16 @@ TSVD_API tsvd_status tsvd_left_vectors(const float *dA, int64_t rows, int64_t n,
 TSVD_API tsvd_status tsvd_csr_partition(int64_t m, const int64_t *row_ptr, int64_t block_rows,
                                int64_t *block_start, int64_t *n_blocks, int64_t *max_block_nnz);
 
-/* Page-locked host memory for A (cudaHostAlloc with portable flag); *ptr is
- * NULL on failure.  Free with tsvd_host_free. */
+/* Page-locked host memory for A: an anonymous mapping aligned to the
+ * transparent-huge-page size and advised MADV_HUGEPAGE (huge pages where the
+ * host has them, base pages otherwise), zero-filled, then registered with
+ * cudaHostRegister (portable: page-locked for every device).  With huge pages
+ * the copy engines translate the range through a few hundred page-table
+ * entries instead of millions, so row-block copies keep the link rate while
+ * kernels run beside them.  *ptr is NULL on failure (TSVD_ENOMEM, or
+ * TSVD_ECUDA when the registration fails).  Free with tsvd_host_free, which
+ * accepts only pointers from tsvd_host_alloc (TSVD_EINVAL otherwise; NULL is
+ * a no-op). */
 TSVD_API tsvd_status tsvd_host_alloc(void **ptr, size_t bytes);
 TSVD_API tsvd_status tsvd_host_free(void *ptr);
 

@@ -89,14 +89,16 @@ class Plan:
     N(0,1) draws instead of the built-in Philox stream), seed, out_device
     (outputs in device memory), sign_convention, force_stream, time_kernels,
     power_kernel (TSVD_POWER_AUTO / GRID / CLUSTER), gram_tile (orthogonal
-    batching panel width) and power_ctas (cluster size of the cluster kernel).
+    batching panel width), power_ctas (cluster size of the cluster kernel) and
+    wait_limit_ns (limit of the tensor-core Gram kernel's waits, for testing the
+    timeout path; 0 = 2 s).
     `factor()` runs the t-SVD; `close()` releases the plan."""
 
     def __init__(self, A, k: int, eps: float, *, precision: int = B.TSVD_GRAM_FP32, device_budget: int = 0,
                  block_rows: int = 0, n_buffers: int = 3, max_iter: int = 10000, iters_override=None,
                  start_draws=None, seed: int = 0, out_device: bool = False, sign_convention: bool = False,
                  force_stream: bool = False, time_kernels: bool = False, power_kernel: int = B.TSVD_POWER_AUTO,
-                 gram_tile: int = 0, power_ctas: int = 0):
+                 gram_tile: int = 0, power_ctas: int = 0, wait_limit_ns: int = 0):
         import torch
         self.lib = B.load()
         self.mat, self._keep = make_matrix(A)
@@ -115,6 +117,7 @@ class Plan:
         opt.power_kernel = int(power_kernel)
         opt.gram_tile = int(gram_tile)
         opt.power_ctas = int(power_ctas)
+        opt.wait_limit_ns = int(wait_limit_ns)
         mn = min(self.mat.m, self.mat.n)
         self.k = mn if k == -1 else int(k)
         if iters_override is not None:

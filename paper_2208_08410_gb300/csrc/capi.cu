@@ -4,9 +4,13 @@
 // event hand-off to the compute stream, Sec. V-C and the stream queue of
 // Alg. 3), and the drivers of the three phases: Gram pass (dense), power
 // phase (Alg. 1 loop over l, Alg. 2 per triplet) and the left-vector pass.
+#include <sys/mman.h>
+#include <unistd.h>
+
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <functional>
 #include <map>
@@ -47,6 +51,82 @@ tsvd_status ensure_dynamic_smem(const void *func, size_t bytes) {
 void count_launch() { ++g_launches; }
 void count_launches(int64_t n) { g_launches += n; }
 int64_t launches_so_far() { return g_launches; }
+
+// ---------------------------------------------------------------- page-locked host memory
+static std::mutex g_pinned_mu;
+static std::map<uintptr_t, size_t> g_pinned;  // start -> mapped length, for pinned_free
+
+// Size of a transparent huge page (the PMD size the kernel reports), or 2 MiB.
+static size_t thp_bytes() {
+  static size_t cached = 0;
+  if (!cached) {
+    size_t v = 0;
+    if (FILE *f = fopen("/sys/kernel/mm/transparent_hugepage/hpage_pmd_size", "r")) {
+      unsigned long long x = 0;
+      if (fscanf(f, "%llu", &x) == 1) v = (size_t)x;
+      fclose(f);
+    }
+    cached = (v >= 4096 && (v & (v - 1)) == 0) ? v : ((size_t)2 << 20);
+  }
+  return cached;
+}
+
+tsvd_status pinned_alloc(void **ptr, size_t bytes) {
+  if (!ptr) return TSVD_EINVAL;
+  *ptr = nullptr;
+  if (bytes == 0) return TSVD_EINVAL;
+  const size_t page = (size_t)sysconf(_SC_PAGESIZE);
+  const size_t hp = std::max(thp_bytes(), page);
+  const size_t len = (bytes + page - 1) / page * page;
+  if (len > SIZE_MAX - hp) return TSVD_EINVAL;
+  // map one huge page more than needed so the start can be aligned, then trim
+  void *raw = mmap(nullptr, len + hp, PROT_READ | PROT_WRITE, MAP_PRIVATE | MAP_ANONYMOUS, -1, 0);
+  if (raw == MAP_FAILED) {
+    set_error_text("tsvd_host_alloc: mmap failed");
+    return TSVD_ENOMEM;
+  }
+  const uintptr_t r0 = reinterpret_cast<uintptr_t>(raw);
+  const uintptr_t start = (r0 + hp - 1) / hp * hp;
+  if (start > r0) munmap(raw, start - r0);
+  const uintptr_t end = start + len, rend = r0 + len + hp;
+  if (rend > end) munmap(reinterpret_cast<void *>(end), rend - end);
+  unsigned char *p = reinterpret_cast<unsigned char *>(start);
+  madvise(p, len, MADV_HUGEPAGE);  // advisory: base pages where huge ones are not available
+  for (size_t o = 0; o < len; o += page) p[o] = 0;  // fault the pages in before pinning them
+  const cudaError_t e = cudaHostRegister(p, len, cudaHostRegisterPortable);
+  if (e != cudaSuccess) {
+    set_cuda_error(e, "cudaHostRegister", __FILE__, __LINE__);
+    cudaGetLastError();
+    munmap(p, len);
+    return e == cudaErrorMemoryAllocation ? TSVD_ENOMEM : TSVD_ECUDA;
+  }
+  {
+    std::lock_guard<std::mutex> lk(g_pinned_mu);
+    g_pinned[start] = len;
+  }
+  *ptr = p;
+  return TSVD_OK;
+}
+
+tsvd_status pinned_free(void *ptr) {
+  if (!ptr) return TSVD_OK;
+  size_t len = 0;
+  {
+    std::lock_guard<std::mutex> lk(g_pinned_mu);
+    auto it = g_pinned.find(reinterpret_cast<uintptr_t>(ptr));
+    if (it == g_pinned.end()) return TSVD_EINVAL;
+    len = it->second;
+    g_pinned.erase(it);
+  }
+  const cudaError_t e = cudaHostUnregister(ptr);
+  munmap(ptr, len);
+  if (e != cudaSuccess) {
+    set_cuda_error(e, "cudaHostUnregister", __FILE__, __LINE__);
+    cudaGetLastError();
+    return TSVD_ECUDA;
+  }
+  return TSVD_OK;
+}
 
 tsvd_status device_info(DeviceInfo *out) {
   static thread_local DeviceInfo cache;
@@ -510,6 +590,7 @@ tsvd_status tsvd_plan(tsvd_plan_t *out, const tsvd_matrix *A, int64_t k, double 
       opt.power_ctas != 8)
     return TSVD_EINVAL;
   if (opt.gram_tile > 0 && A->kind != TSVD_DENSE_F32_ROWMAJOR) return TSVD_EINVAL;
+  if (opt.wait_limit_ns < 0) return TSVD_EINVAL;
   const bool cluster_fits = A->kind == TSVD_DENSE_F32_ROWMAJOR && mn <= kSrvMaxDim && k <= kSrvMaxK;
   if (opt.power_kernel == TSVD_POWER_CLUSTER && !cluster_fits) {
     set_error_text("tsvd_plan: the cluster power kernel takes dense A with n <= " + std::to_string(kSrvMaxDim) +
@@ -592,7 +673,7 @@ void tsvd_destroy(tsvd_plan_t p) {
     if (p->ev_csplit) cudaEventDestroy(p->ev_csplit);
     if (p->ev_cjoin) cudaEventDestroy(p->ev_cjoin);
     if (p->d2h_stream) cudaStreamDestroy(p->d2h_stream);
-    if (p->host_tiles) cudaFreeHost(p->host_tiles);
+    if (p->host_tiles) pinned_free(p->host_tiles);
     if (cur != p->device) cudaSetDevice(cur);
   }
   delete p;
@@ -750,7 +831,8 @@ tsvd_status release_slot(Run &r, int slot) {
 
 tsvd_status gram_dispatch(const float *A, int64_t rows, int64_t n, int64_t ld, double *G, int prec,
                           void *scr, size_t scr_bytes, cudaStream_t s, cudaEvent_t ev0 = nullptr,
-                          cudaEvent_t ev1 = nullptr, bool reset_status = true, bool trans = false) {
+                          cudaEvent_t ev1 = nullptr, bool reset_status = true, bool trans = false,
+                          uint64_t wait_ns = 0) {
   if (trans) {
     // a column block of a wide A: X[r][c] = A[c ld + r], Gram X^T X (Eq. 3)
     if (prec == TSVD_GRAM_FP32) {
@@ -759,10 +841,10 @@ tsvd_status gram_dispatch(const float *A, int64_t rows, int64_t n, int64_t ld, d
       if (ev1) TSVD_CUDA(cudaEventRecord(ev1, s));
       return TSVD_OK;
     }
-    return launch_gram_tc_t(A, rows, n, ld, G, prec, scr, scr_bytes, s, ev0, ev1, reset_status);
+    return launch_gram_tc_t(A, rows, n, ld, G, prec, scr, scr_bytes, s, ev0, ev1, reset_status, wait_ns);
   }
   if (prec == TSVD_GRAM_FP32) return launch_gram_simt(A, rows, n, ld, G, s, ev0, ev1);
-  return launch_gram_tc(A, rows, n, ld, G, prec, scr, scr_bytes, s, ev0, ev1, reset_status);
+  return launch_gram_tc(A, rows, n, ld, G, prec, scr, scr_bytes, s, ev0, ev1, reset_status, wait_ns);
 }
 
 // The other factor, one pass over A (Alg. 1 l.11-13 / l.15-17): OUT = A P
@@ -921,7 +1003,8 @@ tsvd_status factor_dense(Run &r, float *U, double *sigma_out, float *V_out, tsvd
     int slot;
     TSVD_TRY(acquire_dense(r, r0, rows, &Ab, &ldb, &slot, true));
     TSVD_TRY(gram_dispatch(Ab, rows, n, ldb, G64, p->opt.precision, gscr, p->b_gscr, r.cs,
-                           timed ? p->ev_k[2 * c] : nullptr, timed ? p->ev_k[2 * c + 1] : nullptr, false, p->wide));
+                           timed ? p->ev_k[2 * c] : nullptr, timed ? p->ev_k[2 * c + 1] : nullptr, false, p->wide,
+                           (uint64_t)p->opt.wait_limit_ns));
     TSVD_TRY(release_slot(r, slot));
   }
   int32_t gram_err = 0;
@@ -1412,8 +1495,7 @@ tsvd_status factor_dense_tiled(Run &r, float *U, double *sigma_out, float *V_out
   sc.grid = p->vec_grid;
   auto width = [&](int64_t P) { return std::min(bs, n - P * bs); };
   if (p->tiles_host && !p->host_tiles)
-    TSVD_CUDA(cudaHostAlloc(reinterpret_cast<void **>(&p->host_tiles), (size_t)p->n_tasks * bs * bs * 8,
-                            cudaHostAllocPortable));
+    TSVD_TRY(pinned_alloc(reinterpret_cast<void **>(&p->host_tiles), (size_t)p->n_tasks * bs * bs * 8));
 
   TSVD_CUDA(cudaEventRecord(p->ev_t[0], r.cs));
   // ---- Gram, task by task
@@ -1868,18 +1950,8 @@ tsvd_status tsvd_csr_partition(int64_t m, const int64_t *row_ptr, int64_t block_
   return TSVD_OK;
 }
 
-tsvd_status tsvd_host_alloc(void **ptr, size_t bytes) {
-  if (!ptr) return TSVD_EINVAL;
-  *ptr = nullptr;
-  if (bytes == 0) return TSVD_EINVAL;
-  TSVD_CUDA(cudaHostAlloc(ptr, bytes, cudaHostAllocPortable));
-  return TSVD_OK;
-}
+tsvd_status tsvd_host_alloc(void **ptr, size_t bytes) { return pinned_alloc(ptr, bytes); }
 
-tsvd_status tsvd_host_free(void *ptr) {
-  if (!ptr) return TSVD_OK;
-  TSVD_CUDA(cudaFreeHost(ptr));
-  return TSVD_OK;
-}
+tsvd_status tsvd_host_free(void *ptr) { return pinned_free(ptr); }
 
 }  // extern "C"

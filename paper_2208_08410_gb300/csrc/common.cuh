@@ -64,6 +64,16 @@ struct DeviceInfo {
 };
 tsvd_status device_info(DeviceInfo *out);
 
+// Page-locked host memory backed by transparent huge pages: an anonymous
+// mapping aligned to the huge-page size, advised MADV_HUGEPAGE, touched, then
+// registered with cudaHostRegister (portable).  Copy engines translate a
+// large page-locked range through far fewer host page-table entries than with
+// the base pages of cudaHostAlloc, which keeps block copies at the link rate
+// while kernels run beside them.  pinned_free takes only pointers returned by
+// pinned_alloc (TSVD_EINVAL otherwise).
+tsvd_status pinned_alloc(void **ptr, size_t bytes);
+tsvd_status pinned_free(void *ptr);
+
 // ------------------------------------------------------------- device side
 // A bounded wait gives up after this many nanoseconds of %globaltimer.
 constexpr uint64_t kWaitLimitNs = 2000000000ull;  // 2 s
@@ -176,22 +186,25 @@ tsvd_status launch_gram_tc_rect(const float *AJ, const float *AI, int64_t rows, 
 tsvd_status launch_gram_simt_t(const float *A, int64_t rows, int64_t n, int64_t ld, double *G, cudaStream_t stream);
 tsvd_status launch_gram_tc_t(const float *A, int64_t rows, int64_t n, int64_t ld, double *G, int precision,
                              void *scratch, size_t scratch_bytes, cudaStream_t stream, cudaEvent_t ev0 = nullptr,
-                             cudaEvent_t ev1 = nullptr, bool reset_status = true);
+                             cudaEvent_t ev1 = nullptr, bool reset_status = true, uint64_t wait_ns = 0);
 // The same on CUDA cores (FP32): G[a][b] += sum_r AJ[r][a] AI[r][b], row stride ldg.
 tsvd_status launch_gram_simt_rect(const float *AJ, const float *AI, int64_t rows, int64_t nJ, int64_t nI, int64_t ld,
                                   double *G, int64_t ldg, cudaStream_t stream);
 // reset_status: zero the scratch's status word first (a caller that runs many
-// chunks zeroes it once, so a timeout in any chunk stays visible)
+// chunks zeroes it once, so a timeout in any chunk stays visible).
+// wait_ns: limit of the SYRK's pipeline waits, 0 = kWaitLimitNs (a shorter one
+// only serves tests of the timeout path)
 tsvd_status launch_gram_tc(const float *A, int64_t rows, int64_t n, int64_t ld, double *G,
                            int precision, void *scratch, size_t scratch_bytes, cudaStream_t stream,
-                           cudaEvent_t ev0 = nullptr, cudaEvent_t ev1 = nullptr, bool reset_status = true);
+                           cudaEvent_t ev0 = nullptr, cudaEvent_t ev1 = nullptr, bool reset_status = true,
+                           uint64_t wait_ns = 0);
 // The two halves of launch_gram_tc: the prep (transpose, rounding, split) into
 // the scratch, then the SYRK from it.
 tsvd_status launch_gram_tc_prep(const float *A, int64_t rows, int64_t n, int64_t ld, int precision, void *scratch,
                                 size_t scratch_bytes, cudaStream_t stream);
 tsvd_status launch_gram_tc_syrk(int64_t rows, int64_t n, double *G, int precision, void *scratch,
                                 size_t scratch_bytes, cudaStream_t stream, cudaEvent_t ev0 = nullptr,
-                                cudaEvent_t ev1 = nullptr, bool reset_status = true);
+                                cudaEvent_t ev1 = nullptr, bool reset_status = true, uint64_t wait_ns = 0);
 
 // Tiled Gram operator (orthogonal batching): w_J += T v_I and, for an
 // off-diagonal tile, w_I += T^T v_J (T: nJ x nI FP64, row stride ldt; a

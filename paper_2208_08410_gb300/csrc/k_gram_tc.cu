@@ -96,19 +96,35 @@ __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
   return ok != 0;
 }
 
-// Bounded wait on an mbarrier phase; false on timeout or when *err is raised.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int *err) {
+// Bounded wait on an mbarrier phase; false on timeout (after limit_ns) or when
+// *err is raised.  The clock and *err are read every 256 failed tries, or on
+// every try when the limit is below 100 us (the test-only short limits).
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int *err, uint64_t limit_ns) {
   if (mbar_try(bar, parity)) return true;
   const uint64_t t0 = global_timer_ns();
+  const uint32_t mask = limit_ns < 100000ull ? 0u : 255u;
   for (uint32_t spin = 1;; ++spin) {
     if (mbar_try(bar, parity)) return true;
-    if ((spin & 255u) == 0) {
+    if ((spin & mask) == 0) {
       if (*(volatile int *)err) return false;
-      if (global_timer_ns() - t0 > kWaitLimitNs) {
+      if (global_timer_ns() - t0 > limit_ns) {
         atomicExch(err, 2);
         return false;
       }
     }
+  }
+}
+
+// Wait for this CTA's own asynchronous work (a TMA load or the MMAs behind a
+// commit) to complete before the CTA frees TMEM and exits.  It does not give
+// up when *err is raised: that work completes by itself; the wait is bounded
+// by kWaitLimitNs only as a guard.
+__device__ __forceinline__ bool mbar_drain(uint32_t bar, uint32_t parity) {
+  if (mbar_try(bar, parity)) return true;
+  const uint64_t t0 = global_timer_ns();
+  for (uint32_t spin = 1;; ++spin) {
+    if (mbar_try(bar, parity)) return true;
+    if ((spin & 255u) == 0 && global_timer_ns() - t0 > kWaitLimitNs) return false;
   }
 }
 
@@ -321,6 +337,7 @@ struct TcArgs {
   int n_tiles;
   int n_iblk;         // ceil(n / 128)
   int *err;
+  uint64_t wait_ns;   // limit of the pipeline waits (kWaitLimitNs unless a caller sets a shorter one)
 };
 
 // tile t -> (bi, bj): tiles are listed by I block; block bi has bi/2 + 1 tiles
@@ -405,7 +422,7 @@ syrk_tc_kernel(const __grid_constant__ CUtensorMap map_hi, const __grid_constant
         const int64_t k1 = min(a.Kp, k0 + a.ksplit);
         for (int64_t kk = k0; kk < k1; kk += TK, ++it) {
           const uint32_t s = it % C::kStages, ph = (it / C::kStages) & 1u;
-          if (!mbar_wait(empty0 + 8 * s, ph ^ 1u, a.err)) { ok = false; break; }
+          if (!mbar_wait(empty0 + 8 * s, ph ^ 1u, a.err, a.wait_ns)) { ok = false; break; }
           unsigned char *st = smem + s * C::kStageBytes;
           mbar_expect_tx(full0 + 8 * s, C::kStageBytes);
           const int x = (int)kk;
@@ -420,10 +437,14 @@ syrk_tc_kernel(const __grid_constant__ CUtensorMap map_hi, const __grid_constant
           }
         }
       }
-      if (!ok) {
-        // drain: wait (bounded) for the stages still in flight to land
+      // Drain: the last kStages loads may still be in flight when the MMA
+      // warp stopped early (a wait gave up here or in another CTA), so wait
+      // for them to land before the CTA exits.  Every earlier load has landed:
+      // its stage was refilled only after the MMAs that read it completed.  On
+      // the normal path these loads were consumed and the waits return at once.
+      {
         const uint32_t from = it > (uint32_t)C::kStages ? it - C::kStages : 0;
-        for (uint32_t j = from; j < it; ++j) mbar_wait(full0 + 8 * (j % C::kStages), (j / C::kStages) & 1u, a.err);
+        for (uint32_t j = from; j < it; ++j) mbar_drain(full0 + 8 * (j % C::kStages), (j / C::kStages) & 1u);
       }
     }
   } else if (warp == 1) {
@@ -438,13 +459,13 @@ syrk_tc_kernel(const __grid_constant__ CUtensorMap map_hi, const __grid_constant
         for (int64_t g0 = k0; g0 < k1 && ok; g0 += seg_rows, ++sc) {
           const int64_t g1 = min(k1, g0 + seg_rows);
           const uint32_t acc = sc & 1u, aph = (sc >> 1) & 1u;
-          if (!mbar_wait(tempty0 + 8 * acc, aph ^ 1u, a.err)) { ok = false; break; }
+          if (!mbar_wait(tempty0 + 8 * acc, aph ^ 1u, a.err, a.wait_ns)) { ok = false; break; }
           tc_fence_after();
           const uint32_t dtm = tmem + acc * TN;
           uint32_t first = 1;
           for (int64_t kk = g0; kk < g1; kk += TK, ++it) {
             const uint32_t s = it % C::kStages, ph = (it / C::kStages) & 1u;
-            if (!mbar_wait(full0 + 8 * s, ph, a.err)) { ok = false; break; }
+            if (!mbar_wait(full0 + 8 * s, ph, a.err, a.wait_ns)) { ok = false; break; }
             tc_fence_after();
             const uint32_t st = smem_u32(smem + s * C::kStageBytes);
             const uint64_t dah = umma_desc_sw128(st), dbh = umma_desc_sw128(st + A_SLAB);
@@ -468,8 +489,9 @@ syrk_tc_kernel(const __grid_constant__ CUtensorMap map_hi, const __grid_constant
         }
       }
       // wait for every MMA this thread issued before TMEM is released
+      // (also after a wait gave up: the MMAs in flight complete by themselves)
       umma_commit(final_bar);
-      mbar_wait(final_bar, 0, a.err);
+      mbar_drain(final_bar, 0);
     }
   } else {
     // ------------------------------------------------ epilogue: TMEM -> registers -> FP64 G
@@ -489,7 +511,7 @@ syrk_tc_kernel(const __grid_constant__ CUtensorMap map_hi, const __grid_constant
       const int64_t k1 = min(a.Kp, k0 + a.ksplit);
       for (int64_t g0 = k0; g0 < k1; g0 += seg_rows, ++sc) {
         const uint32_t acc = sc & 1u, aph = (sc >> 1) & 1u;
-        if (!mbar_wait(tfull0 + 8 * acc, aph, a.err)) { ok = false; break; }
+        if (!mbar_wait(tfull0 + 8 * acc, aph, a.err, a.wait_ns)) { ok = false; break; }
         tc_fence_after();
         const uint32_t tbase = tmem + ((uint32_t)(q * 32) << 16) + acc * TN + h * TC_EPI_COLS;
 #pragma unroll
@@ -672,6 +694,7 @@ tsvd_status run_syrk(const TcLayout &L, const TcArgs &a0, int precision, int sms
   TSVD_TRY(make_map(&ml, L.lo, a.n, a.Kp, precision));
   tc_ksplit(a, precision, sms);
   a.err = L.err;
+  if (a.wait_ns == 0) a.wait_ns = kWaitLimitNs;
   if (reset_status) TSVD_CUDA(cudaMemsetAsync(L.err, 0, 4, stream));
   const int64_t units = (int64_t)a.n_tiles * a.n_splits;
   const int grid = (int)std::min<int64_t>(units, sms);
@@ -690,7 +713,7 @@ tsvd_status run_syrk(const TcLayout &L, const TcArgs &a0, int precision, int sms
 
 tsvd_status launch_gram_tc_t(const float *A, int64_t rows, int64_t n, int64_t ld, double *G, int precision,
                              void *scratch, size_t scratch_bytes, cudaStream_t stream, cudaEvent_t ev0,
-                             cudaEvent_t ev1, bool reset_status) {
+                             cudaEvent_t ev1, bool reset_status, uint64_t wait_ns) {
   if (rows <= 0) return TSVD_OK;
   DeviceInfo di;
   TSVD_TRY(device_info(&di));
@@ -707,7 +730,8 @@ tsvd_status launch_gram_tc_t(const float *A, int64_t rows, int64_t n, int64_t ld
   else
     prep_rows_kernel<TSVD_GRAM_TF32><<<grid, 256, 0, stream>>>(A, rows, n, ld, L.hi, L.lo, L.Kp, vec);
   TSVD_LAUNCHED();
-  return launch_gram_tc_syrk(rows, n, G, precision, scratch, scratch_bytes, stream, ev0, ev1, reset_status);
+  return launch_gram_tc_syrk(rows, n, G, precision, scratch, scratch_bytes, stream, ev0, ev1, reset_status,
+                             wait_ns);
 }
 
 tsvd_status launch_gram_tc_prep(const float *A, int64_t rows, int64_t n, int64_t ld, int precision, void *scratch,
@@ -722,7 +746,8 @@ tsvd_status launch_gram_tc_prep(const float *A, int64_t rows, int64_t n, int64_t
 }
 
 tsvd_status launch_gram_tc_syrk(int64_t rows, int64_t n, double *G, int precision, void *scratch, size_t scratch_bytes,
-                                cudaStream_t stream, cudaEvent_t ev0, cudaEvent_t ev1, bool reset_status) {
+                                cudaStream_t stream, cudaEvent_t ev0, cudaEvent_t ev1, bool reset_status,
+                                uint64_t wait_ns) {
   if (rows <= 0) return TSVD_OK;
   DeviceInfo di;
   TSVD_TRY(device_info(&di));
@@ -737,6 +762,7 @@ tsvd_status launch_gram_tc_syrk(int64_t rows, int64_t n, double *G, int precisio
   a.Kp = L.Kp;
   a.seg_stages = tc_seg_stages(precision);
   a.n_iblk = (int)ceil_div(n, TM);
+  a.wait_ns = wait_ns;
   {
     const int64_t q = (a.n_iblk) >> 1;  // tiles = C(n_iblk)
     a.n_tiles = (int)((a.n_iblk & 1) ? (q + 1) * (q + 1) : q * (q + 1));
@@ -776,10 +802,11 @@ tsvd_status launch_gram_tc_rect(const float *AJ, const float *AI, int64_t rows, 
 
 tsvd_status launch_gram_tc(const float *A, int64_t rows, int64_t n, int64_t ld, double *G, int precision,
                            void *scratch, size_t scratch_bytes, cudaStream_t stream, cudaEvent_t ev0,
-                           cudaEvent_t ev1, bool reset_status) {
+                           cudaEvent_t ev1, bool reset_status, uint64_t wait_ns) {
   if (rows <= 0) return TSVD_OK;
   TSVD_TRY(launch_gram_tc_prep(A, rows, n, ld, precision, scratch, scratch_bytes, stream));
-  return launch_gram_tc_syrk(rows, n, G, precision, scratch, scratch_bytes, stream, ev0, ev1, reset_status);
+  return launch_gram_tc_syrk(rows, n, G, precision, scratch, scratch_bytes, stream, ev0, ev1, reset_status,
+                             wait_ns);
 }
 
 }  // namespace tsvd

@@ -140,6 +140,19 @@ __device__ __forceinline__ bool mbar_wait_l(uint32_t bar, uint32_t parity) {
   }
 }
 
+// Wait for a TMA load this CTA issued to land before the CTA exits, also after
+// a wait gave up (the load completes by itself); bounded only as a guard.
+__device__ __forceinline__ bool mbar_drain_l(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  const uint64_t t0 = global_timer_ns();
+  for (uint32_t spin = 0;; ++spin) {
+    asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+                 : "=r"(ok) : "r"(bar), "r"(parity) : "memory");
+    if (ok) return true;
+    if ((spin & 255u) == 255u && global_timer_ns() - t0 > kWaitLimitNs) return false;
+  }
+}
+
 __global__ void __launch_bounds__(TT, 1)
 left_tma_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapV, int64_t rows,
                 int64_t n, int64_t k, const double *__restrict__ sigma, float *__restrict__ U, int64_t ldu, int l0) {
@@ -175,6 +188,7 @@ left_tma_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
   }
   float acc[1][TRW][TLH];
   bool ok = true;
+  int64_t stop = total;  // the chunk at which a failed wait ended the loop
   for (int64_t c = 0; c < total; ++c) {
     const int64_t cj = c % chunks;
     if (cj == 0) {
@@ -186,7 +200,10 @@ left_tma_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
     // stage (c + T_NST - 1) % T_NST was released by the sync at the end of iteration c - 1
     if (threadIdx.x == 0 && c + T_NST - 1 < total) issue(c + T_NST - 1);
     if (!mbar_wait_l(su32(full + (c % T_NST)), (uint32_t)((c / T_NST) & 1))) ok = false;
-    if (__syncthreads_or(!ok)) break;
+    if (__syncthreads_or(!ok)) {
+      stop = c;
+      break;
+    }
     const float *As = reinterpret_cast<const float *>(sm + (c % T_NST) * T_STAGE);
     const float *Vs = reinterpret_cast<const float *>(sm + (c % T_NST) * T_STAGE + T_ABYTES);
     const int jj = 4 * lane;
@@ -231,9 +248,11 @@ left_tma_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
       }
     }
   }
-  // a copy may still be in flight if the loop broke early: wait (bounded) for it
-  if (!ok && threadIdx.x == 0) {
-    for (int b = 0; b < T_NST; ++b) mbar_wait_l(su32(full + b), 0);
+  // After an early stop, chunks stop .. stop + T_NST - 1 may have been issued
+  // and not waited for: let them land before the CTA exits.
+  if (stop < total && threadIdx.x == 0) {
+    for (int64_t j = stop; j < total && j < stop + T_NST; ++j)
+      mbar_drain_l(su32(full + (j % T_NST)), (uint32_t)((j / T_NST) & 1));
   }
   __syncthreads();
 }

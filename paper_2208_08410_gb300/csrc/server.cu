@@ -61,10 +61,9 @@ class Arena {
         return TSVD_ENOMEM;
       }
     } else {
-      if (cudaHostAlloc(reinterpret_cast<void **>(&base), bytes, cudaHostAllocPortable) != cudaSuccess) {
-        cudaGetLastError();
+      if (pinned_alloc(reinterpret_cast<void **>(&base), bytes) != TSVD_OK) {
         base = nullptr;
-        set_error_text("server: cudaHostAlloc of the staging area failed");
+        set_error_text("server: page-locked allocation of the staging area failed");
         return TSVD_ENOMEM;
       }
     }
@@ -107,7 +106,7 @@ class Arena {
   void destroy() {
     if (base) {
       if (host)
-        cudaFreeHost(base);
+        pinned_free(base);
       else
         cudaFree(base);
     }

@@ -101,6 +101,9 @@ def test_plan_validation_dense(lib):
         assert _plan(d, 5, 1e-6, _opts(power_ctas=c))[0] == B.TSVD_OK
     for c in (-1, 3, 16):
         assert _plan(d, 5, 1e-6, _opts(power_ctas=c))[0] == B.TSVD_EINVAL
+    # the test-only limit of the tensor-core Gram kernel's waits
+    assert _plan(d, 5, 1e-6, _opts(wait_limit_ns=1))[0] == B.TSVD_OK
+    assert _plan(d, 5, 1e-6, _opts(wait_limit_ns=-1))[0] == B.TSVD_EINVAL
     big, keep5 = _dense_desc(8, 2049, arr=np.zeros((1, 1), dtype=np.float32))
     big.m = 4096  # plan reads no values
     assert _plan(big, 4, 1e-6, _opts(power_kernel=B.TSVD_POWER_CLUSTER))[0] == B.TSVD_EUNSUPPORTED

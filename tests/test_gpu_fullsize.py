@@ -140,6 +140,61 @@ def test_dense_full_size_in_core():
     torch.cuda.empty_cache()
 
 
+C2S_M = 1_048_576          # the out-of-core configuration's small case: 16 GiB of FP32
+C2S_BUDGET = 8_000_000_000  # device budget that forces streaming
+
+
+def test_c2_small_streamed_follows_oracle():
+    """The dense out-of-core configuration at m = 1,048,576, n = 4096: A (16 GiB)
+    in page-locked host memory, streamed in row blocks under an 8 GB device
+    budget, Gram in 3xTF32, k = 16, eps = 1e-6.  The oracle forms the FP64 Gram
+    of the same stored values block by block (Alg. 2 B = X^T X over row
+    batches, Sec. V-C), runs O-1 (Alg. 1/2, Hotelling deflation) from the same
+    start draws with its own convergence test, and forms U = A V Sigma^-1;
+    the GPU follows with the oracle's iteration counts forced.  sigma within
+    1e-5 on every triplet; u_l and v_l within 1e-4 on the gapped triplets."""
+    B.load()
+    m = C2S_M
+    ptr, flat = _pinned(m * N, np.float32)
+    try:
+        A = flat.reshape(m, N)
+        sigma_p = 1.0 / (1.0 + np.arange(RANK))
+        synth.dense_lowrank_blocks_torch(torch.from_numpy(A), m, N, RANK, sigma_p, 1e-4, seed=2,
+                                         block_rows=BLOCK_ROWS)
+        x = synth.start_normals(N, K, seed=3)
+        G = ref.gram_row_blocks(A, 65536)
+        sig_o, V_o, it_o, st_o = ref.right_vectors(G, K, EPS, x_start=x)
+        assert all(s == "ok" for s in st_o), st_o
+        lam = np.linalg.eigvalsh(G)[::-1]
+        del G
+        # noise Gram ~ m 1e-8 I = 0.0105 I: the relative gaps fall below 0.05 near i = 12
+        gapped = ref.gapped_indices(lam, K)
+        assert gapped[:11] == list(range(11)), gapped
+        U_o = np.empty((m, K))
+        for r0 in range(0, m, 65536):
+            U_o[r0:r0 + 65536] = np.asarray(A[r0:r0 + 65536], dtype=np.float64) @ V_o
+        U_o /= sig_o[None, :]
+
+        plan = Plan(A, K, EPS, precision=B.TSVD_GRAM_TF32X3, device_budget=C2S_BUDGET, force_stream=True,
+                    start_draws=x, iters_override=it_o)
+        try:
+            res = plan.factor()
+        finally:
+            plan.close()
+        assert res.status == B.TSVD_OK and res.report["flags"] == 0, res.report
+        assert res.report["mode"] == 2 and res.report["n_blocks"] >= 2, res.report
+        assert res.iters == it_o
+        rel = np.abs(np.asarray(res.sigma) - sig_o) / sig_o
+        assert float(rel.max()) <= 1e-5, rel
+        V = np.asarray(res.V, dtype=np.float64)
+        U = np.asarray(res.U, dtype=np.float64)
+        for l in gapped:
+            assert ref.vector_angle(V[:, l], V_o[:, l]) <= 1e-4, (l, ref.vector_angle(V[:, l], V_o[:, l]))
+            assert ref.vector_angle(U[:, l], U_o[:, l]) <= 1e-4, (l, ref.vector_angle(U[:, l], U_o[:, l]))
+    finally:
+        B.tsvd_host_free(ptr)
+
+
 def test_csr_full_size_streamed():
     B.load()
     m = 1 << 25
