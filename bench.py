@@ -169,7 +169,9 @@ def measure_h2d_peak(A: np.ndarray):
     """Pinned host -> HBM copy rates (cudaMemcpyAsync via torch, one copy stream):
     burst = best of 3 copies of the first 4 GiB block; sustained = every row
     block of A copied back to back into a 2-buffer ring (what a streamed pass
-    over the whole matrix can reach)."""
+    over the whole matrix can reach), measured on a second pass: the first
+    pass after the generator wrote A runs through every block once untimed,
+    as the benchmark's warm-up steps do before the timed ones."""
     import torch
     rows = min(A.shape[0], BLOCK_ROWS)
     dst = [torch.empty((rows, A.shape[1]), dtype=torch.float32, device="cuda") for _ in range(2)]
@@ -183,6 +185,9 @@ def measure_h2d_peak(A: np.ndarray):
         e1.record()
         torch.cuda.synchronize()
         best = max(best, rows * A.shape[1] * 4 / (e0.elapsed_time(e1) / 1e3) / 1e9)
+    for i, r0 in enumerate(range(0, A.shape[0], rows)):  # untimed first pass
+        blk = torch.from_numpy(A[r0:r0 + rows])
+        dst[i & 1][:blk.shape[0]].copy_(blk, non_blocking=True)
     evs = []
     torch.cuda.synchronize()
     total = 0
@@ -219,14 +224,28 @@ def whole_job_rate(sec_local: float, units_local: float, dist=None, device="cpu"
 
 
 # ----------------------------------------------------------------------------- runs
+_PINNED = {}  # address of a page-locked array's first byte -> the allocator's pointer
+
+
 def pinned_array(shape, dtype):
-    """Page-locked host array from the library's allocator (freed at exit)."""
+    """Page-locked host array from the library's allocator (freed at exit, or
+    by free_pinned)."""
     from paper_2208_08410_gb300 import _binding as B
     nbytes = int(np.prod(shape)) * np.dtype(dtype).itemsize
     ptr = C.c_void_p()
     B.check(B.tsvd_host_alloc(C.byref(ptr), max(nbytes, 16)), "tsvd_host_alloc")
     ctype = {np.float32: C.c_float, np.float64: C.c_double}[dtype]
-    return np.ctypeslib.as_array(C.cast(ptr, C.POINTER(ctype)), shape=shape)
+    arr = np.ctypeslib.as_array(C.cast(ptr, C.POINTER(ctype)), shape=shape)
+    _PINNED[ptr.value] = ptr
+    return arr
+
+
+def free_pinned(arr):
+    """Return a pinned_array's memory (views of it must not be used after)."""
+    from paper_2208_08410_gb300 import _binding as B
+    ptr = _PINNED.pop(arr.__array_interface__["data"][0], None)
+    if ptr is not None:
+        B.tsvd_host_free(ptr)
 
 
 def time_steps(plan, A_in, steps: int, warmup: int, want_u=True, outs=None):
@@ -407,7 +426,8 @@ def kernel_case(args):
         fl = m * n * (n + 1)
         out.update({"m": m, "n": n, "precision": PREC_NAMES[args.precision], "ms": round(t * 1e3, 3),
                     "tflops_algorithmic": round(fl / t / 1e12, 2),
-                    "frac_of_dtype_peak_burst": round(fl / t / 1e12 / dtype_peak(args.precision, peaks, False)[0], 4),
+                    "frac_of_dtype_peak_burst": round(fl / t / 1e12 / dtype_peak(
+                        args.precision, peaks, False, getattr(measure_tf32_peak, "result", None))[0], 4),
                     "note": "time covers prep (transpose/round) + SYRK for tensor precisions"})
     elif args.case == "power":
         n = args.n
@@ -524,7 +544,7 @@ def tf32_in_core(dA, args, m, res_ref, peaks):
     plan.close()
     gk_ms = sum(r["gram_kernel_ms"] for r in reps)
     tf = m * N_COLS * (N_COLS + 1) * args.steps / (gk_ms / 1e3) / 1e12
-    peak, _ = dtype_peak(1, peaks, sustained=True)
+    peak, _, _ = dtype_peak(1, peaks, sustained=True, tf32_measured=getattr(measure_tf32_peak, "result", None))
     s1 = np.asarray(res.sigma.cpu(), dtype=np.float64)
     s0 = np.asarray(res_ref.sigma.cpu(), dtype=np.float64)
     return {"value": round(2 * m * N_COLS * 4 * args.steps / sec / 1e9, 3), "unit": "GB/s",
@@ -533,12 +553,6 @@ def tf32_in_core(dA, args, m, res_ref, peaks):
             "sigma_max_rel_diff_vs_tf32x3": float("%.3g" % np.max(np.abs(s1 - s0) / s0))}
 
 
-PEAK_NOTES = {
-    0: "152 SMs x 128 FP32 lanes x 2 flop x max SM clock",
-    1: "TF32 = bf16 {src} {kind} x 1.1/2.25 nominal ratio",
-    2: "3xTF32 = TF32 peak / 3 (three TF32 MMAs per product); TF32 = bf16 {src} {kind} x 1.1/2.25",
-    3: "BF16x3 = bf16 {src} {kind} / 3 (three BF16 MMAs per product)",
-}
 
 
 def c1_latency(reps: int = 50):
@@ -594,36 +608,189 @@ def c1_latency(reps: int = 50):
     return out
 
 
-def dtype_peak(prec: int, peaks: dict, sustained: bool = True):
+def measure_tf32_peak(n: int = 8192, burst_reps: int = 10, sustained_s: float = 3.0):
+    """cuBLAS TF32 GEMM rate on this GPU (torch.matmul of two n x n FP32
+    matrices with TF32 allowed, 2 n^3 flop): best of `burst_reps` launches
+    (burst) and back-to-back launches for `sustained_s` seconds (sustained).
+    Kept on the function as `result` for the legs that report against it."""
+    import torch
+    prev = torch.backends.cuda.matmul.allow_tf32
+    torch.backends.cuda.matmul.allow_tf32 = True
+    try:
+        g = torch.Generator(device="cuda").manual_seed(3)
+        a = torch.randn((n, n), generator=g, device="cuda")
+        b = torch.randn((n, n), generator=g, device="cuda")
+        c = torch.empty((n, n), device="cuda")
+        for _ in range(3):
+            torch.matmul(a, b, out=c)
+        torch.cuda.synchronize()
+        best = 0.0
+        for _ in range(burst_reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            torch.matmul(a, b, out=c)
+            e1.record()
+            e1.synchronize()
+            best = max(best, 2 * n ** 3 / (e0.elapsed_time(e1) / 1e3) / 1e12)
+        reps = max(1, int(sustained_s * best * 1e12 / (2 * n ** 3)))
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            torch.matmul(a, b, out=c)
+        e1.record()
+        e1.synchronize()
+        sus = 2 * n ** 3 * reps / (e0.elapsed_time(e1) / 1e3) / 1e12
+        del a, b, c
+        torch.cuda.empty_cache()
+    finally:
+        torch.backends.cuda.matmul.allow_tf32 = prev
+    measure_tf32_peak.result = {"burst_tflops": round(best, 1), "sustained_tflops": round(sus, 1),
+                                "how": f"torch.matmul FP32 {n}^3 with TF32 allowed (cuBLAS), best of {burst_reps} "
+                                       f"and {reps} back to back"}
+    return measure_tf32_peak.result
+
+
+def dtype_peak(prec: int, peaks: dict, sustained: bool = True, tf32_measured=None):
     """Roofline denominator of the Gram arithmetic in TFLOP/s (algorithmic
-    flops: a split mode's three MMAs per product count once).  Kernels timed
-    inside a long step take the sustained bf16 figure, kernels timed alone
-    the burst one."""
+    flops: a split mode's three MMAs per product count once), its bound and a
+    note on where it comes from.  Kernels timed inside a long step take the
+    sustained figures, kernels timed alone the burst ones.  TF32-based modes
+    take the larger of the bf16 measurement x the nominal 1.1/2.25 ratio and
+    this GPU's measured cuBLAS TF32 rate, so a kernel is never graded against
+    the smaller of two estimates of the same peak."""
+    kind = "sustained" if sustained else "burst"
     bf = peaks["bf16_tflops_sustained"] if sustained else peaks["bf16_tflops"]
     if prec == 0:
-        return 152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12, "alu"
-    if prec == 1:
-        return bf * (1.1 / 2.25), "tensor"
-    if prec == 2:
-        return bf * (1.1 / 2.25) / 3, "tensor"
-    return bf / 3, "tensor"
+        return 152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12, "alu", \
+            "152 SMs x 128 FP32 lanes x 2 flop x max SM clock"
+    if prec in (1, 2):
+        derived = bf * (1.1 / 2.25)
+        meas = (tf32_measured or {}).get(f"{kind}_tflops")
+        tf32 = max(derived, meas or 0.0)
+        src = (f"TF32 = max(bf16 measured {kind} {bf:.0f} x 1.1/2.25 = {derived:.0f}, cuBLAS TF32 measured "
+               f"{kind} {meas:.0f})" if meas else f"TF32 = bf16 measured {kind} {bf:.0f} x 1.1/2.25 = {derived:.0f}")
+        if prec == 1:
+            return tf32, "tensor", src
+        return tf32 / 3, "tensor", "3xTF32 = TF32 / 3 (three TF32 MMAs per product); " + src
+    return bf / 3, "tensor", f"BF16x3 = bf16 measured {kind} {bf:.0f} / 3 (three BF16 MMAs per product)"
 
 
-def c4_workload(args):
-    """Mixed-precision Gram on a clustered spectrum: m = 2^20, n = 8192,
-    sigma_i = 1/(1+i) with sigma_11 = sigma_10 - 1e-3, k = 32, eps = 1e-8, A
-    resident in HBM (32 GiB), stacked-orthogonal construction (its singular
-    values are the prescribed sigma to ~1e-8).  Every Gram precision runs the
-    same t-SVD; the line reports seconds per t-SVD, the Gram kernel against
-    its dtype's peak and the sigma error against the closed form."""
+C2S_M = 1_048_576            # the dense out-of-core configuration's small case (16 GiB)
+C2S_BUDGET = 8 * 10 ** 9      # its device budget
+
+
+def leg_c2_small(args, h2d_peak=None):
+    """The dense out-of-core configuration's small case: m = 1,048,576, n = 4096
+    (16 GiB in page-locked host memory), streamed under an 8 GB device budget,
+    3xTF32 Gram, k = 16, eps = 1e-6.
+    - e2e: A-stream throughput of whole t-SVDs (own convergence test), host A
+      and host outputs, every copy inside the timed region; the Gram pass
+      against the pinned copy rate of the same blocks.
+    - parity: the oracle forms the FP64 Gram of the same stored values (row
+      blocks of 65,536), runs O-1 from the same start draws with its own
+      convergence test and forms U = A V Sigma^-1; the GPU reruns with the
+      oracle's counts forced.  sigma error on all triplets, angles of u_l and
+      v_l on the gapped ones (relative eigen-gap >= 0.05)."""
     import torch
 
     import synth
+    from oracle import tsvd_ref as ref
     from paper_2208_08410_gb300 import Plan, _binding as B
-    B.load(build_if_missing=True)
-    torch.cuda.set_device(0)
+    m = C2S_M
+    A, ptr, _ = make_host_A(m, seed=5)
+    try:
+        burst, sustained = measure_h2d_peak(A)
+        per_block = getattr(measure_h2d_peak, "per_block", None)
+        x = synth.start_normals(N_COLS, K, seed=3)
+        outs = {"U": pinned_array((K, m), np.float32), "sigma": pinned_array((K,), np.float64),
+                "V": pinned_array((K, N_COLS), np.float32)}
+        steps = max(1, min(args.steps, 5))
+        plan = Plan(A, K, EPS, precision=2, device_budget=C2S_BUDGET, force_stream=True, time_kernels=True,
+                    start_draws=x)
+        clocks = ClockSampler(0)
+        clocks.start()
+        sec, wall, reps, res = time_steps(plan, A, steps, max(1, min(args.warmup, 3)), outs=outs)
+        clk = clocks.stop()
+        plan.close()
+        r = reps[-1]
+        own_iters = list(res.iters)
+        gram_s = r["gram_ms"] / 1e3
+        e2e = {"value": round(2 * m * N_COLS * 4 * steps / sec / 1e9, 2), "unit": "GB/s",
+               "ms_per_step": round(sec / steps * 1e3, 2), "steps": steps,
+               "h2d_bytes_per_step": int(r["h2d_bytes"]), "d2h_bytes_per_step": int(r["d2h_bytes"]),
+               "phases_ms": {"gram": round(r["gram_ms"], 2), "power": round(r["power_ms"], 2),
+                             "left": round(r["left_ms"], 2)},
+               "gram_pass_GBps": round(m * N_COLS * 4 / gram_s / 1e9, 2),
+               "pinned_copy_peak_GBps": round(sustained, 2), "pinned_copy_burst_GBps": round(burst, 2),
+               "pinned_copy_per_block_GBps": per_block,
+               "frac_gram_pass": round(m * N_COLS * 4 / gram_s / 1e9 / sustained, 4),
+               "blocks_per_pass": r["n_blocks"], "ring_slots": r["ring_slots"],
+               "copy_stream_GBps": round(r["h2d_bytes"] / (r["h2d_copy_ms"] / 1e3) / 1e9, 2)
+               if r["h2d_copy_ms"] else None,
+               "copy_min_GBps": round(r["h2d_copy_min_gbps"], 1), "copy_max_GBps": round(r["h2d_copy_max_gbps"], 1),
+               "clocks": clk}
+        # ---- parity against the oracle's trajectory
+        t0 = time.time()
+        G = ref.gram_row_blocks(A, 65_536)
+        t_gram = time.time() - t0
+        sig_o, V_o, it_o, st_o = ref.right_vectors(G, K, EPS, x_start=x)
+        lam = np.linalg.eigvalsh(G)[::-1]
+        del G
+        gapped = ref.gapped_indices(lam, K)
+        U_o = np.empty((m, K))
+        for r0 in range(0, m, 65_536):
+            U_o[r0:r0 + 65_536] = np.asarray(A[r0:r0 + 65_536], dtype=np.float64) @ V_o
+        U_o /= sig_o[None, :]
+        t_oracle = time.time() - t0
+        plan = Plan(A, K, EPS, precision=2, device_budget=C2S_BUDGET, force_stream=True, start_draws=x,
+                    iters_override=it_o)
+        res2 = plan.factor(A, **outs)
+        plan.close()
+        sig = np.asarray(res2.sigma, dtype=np.float64)
+        V = np.asarray(res2.V, dtype=np.float64)
+        U = np.asarray(res2.U, dtype=np.float64)
+        sig_err = float(np.max(np.abs(sig - sig_o) / sig_o))
+        ang_v = {int(l): float("%.3g" % ref.vector_angle(V[:, l], V_o[:, l])) for l in gapped}
+        ang_u = {int(l): float("%.3g" % ref.vector_angle(U[:, l], U_o[:, l])) for l in gapped}
+        parity = {"oracle": "O-1: FP64 Gram of the stored values, Hotelling deflation, same start draws, "
+                            "own convergence test; GPU with the oracle's counts forced",
+                  "sigma_rel_err_vs_oracle": float("%.3g" % sig_err),
+                  "gapped": [int(l) for l in gapped],
+                  "v_angle_max_gapped": max(ang_v.values()) if ang_v else None,
+                  "u_angle_max_gapped": max(ang_u.values()) if ang_u else None,
+                  "v_angles": ang_v, "u_angles": ang_u,
+                  "pass": bool(sig_err <= 1e-5 and all(a <= 1e-4 for a in list(ang_v.values()) + list(ang_u.values()))
+                               and len(gapped) > 0),
+                  "oracle_iters": [int(i) for i in it_o], "gpu_own_iters": own_iters,
+                  "oracle_status": sorted(set(st_o)), "oracle_seconds": round(t_oracle, 1),
+                  "oracle_gram_seconds": round(t_gram, 1), "oracle_cores": len(os.sched_getaffinity(0))}
+        return {"workload": f"dense out-of-core t-SVD (rank-64 + 1e-4 noise), m={m}, n={N_COLS}, k={K}, "
+                            f"eps={EPS}, 3xTF32 Gram, host A streamed under an {C2S_BUDGET / 1e9:.0f} GB "
+                            "device budget", "m": m, "e2e": e2e, "parity": parity}
+    finally:
+        B.tsvd_host_free(ptr)
+        torch.cuda.empty_cache()
+
+
+def leg_c4(args, steps: int, warmup: int):
+    """Mixed-precision Gram on a clustered spectrum: m = 2^20, n = 8192,
+    sigma_i = 1/(1+i) with sigma_11 = sigma_10 - 1e-3, k = 32, eps = 1e-8, A
+    resident in HBM (32 GiB), stacked-orthogonal construction (A^T A = 128
+    M^T M exactly, so the oracle's FP64 Gram is exact and O-1 runs at full
+    size).  The oracle runs from fixed start draws with its own convergence
+    test; every Gram precision follows its trajectory (counts forced) and is
+    timed.  Reported per precision: seconds per t-SVD, the Gram kernel
+    against its dtype's peak, the sigma error against O-1 and against the
+    closed form, the gapped vectors' angles to O-1 and the clustered pair's
+    largest principal angle."""
+    import torch
+
+    import synth
+    from oracle import tsvd_ref as ref
+    from paper_2208_08410_gb300 import Plan, _binding as B
     n, copies, k, eps = 8192, 128, 32, 1e-8
     m = n * copies
+    pair = (10, 11)
     t0 = time.time()
     sig_t = synth.spectrum_harmonic_clustered(n, 10, 1e-3)
     fac = synth.stacked_factor(n, sig_t, copies, seed=0)
@@ -631,38 +798,79 @@ def c4_workload(args):
     synth.stacked_rows_torch(dA, fac["M32"], seed=0)
     torch.cuda.synchronize()
     gen_s = time.time() - t0
+    x = synth.start_normals(n, k, seed=4)
+    t0 = time.time()
+    G = copies * ref.gram(fac["M32"])
+    sig_o, V_o, it_o, st_o = ref.right_vectors(G, k, eps, x_start=x)
+    del G
+    t_oracle = time.time() - t0
+    gapped = [i for i in ref.gapped_indices(sig_t ** 2, k) if i not in pair]
     peaks, peak_src = load_peaks()
+    tf32_meas = getattr(measure_tf32_peak, "result", None)
     flops = m * n * (n + 1)
     rows = {}
+    clocks = ClockSampler(0)
+    clocks.start()
     for prec in (0, 1, 2, 3):
-        plan = Plan(dA, k, eps, precision=prec, out_device=True, time_kernels=True)
-        sec, wall, reps, res = time_steps(plan, dA, args.steps, args.warmup, want_u=True)
+        plan = Plan(dA, k, eps, precision=prec, out_device=True, time_kernels=True, start_draws=x,
+                    iters_override=it_o)
+        sec, wall, reps, res = time_steps(plan, dA, steps, warmup, want_u=True)
         plan.close()
         sig = np.asarray(res.sigma.cpu(), dtype=np.float64)
-        err = float(np.max(np.abs(sig - sig_t[:k]) / sig_t[:k]))
+        V = res.V.cpu().numpy().astype(np.float64)
+        err_o = float(np.max(np.abs(sig - sig_o) / sig_o))
+        err_t = float(np.max(np.abs(sig - sig_t[:k]) / sig_t[:k]))
+        ang = max(ref.vector_angle(V[:, l], V_o[:, l]) for l in gapped)
+        ang_pair = ref.subspace_angle(V[:, list(pair)], V_o[:, list(pair)])
         gk = sum(r["gram_kernel_ms"] for r in reps) / 1e3
-        tf = flops * args.steps / gk / 1e12 if gk > 0 else None
-        pk, bound = dtype_peak(prec, peaks, sustained=True)
+        tf = flops * steps / gk / 1e12 if gk > 0 else None
+        pk, bound, note = dtype_peak(prec, peaks, sustained=True, tf32_measured=tf32_meas)
         rows[PREC_NAMES[prec]] = {
-            "seconds_per_tsvd": round(sec / args.steps, 4), "sigma_max_rel_err_vs_truth": float("%.3g" % err),
+            "seconds_per_tsvd": round(sec / steps, 4),
+            "sigma_max_rel_err_vs_oracle": float("%.3g" % err_o),
+            "sigma_max_rel_err_vs_truth": float("%.3g" % err_t),
+            "v_angle_max_gapped_vs_oracle": float("%.3g" % ang),
+            "pair_subspace_angle_vs_oracle": float("%.3g" % ang_pair),
+            "within_1e-5": bool(err_o <= 1e-5 and ang <= 1e-4 and ang_pair <= 1e-4),
             "gram_tflops": round(tf, 1) if tf else None, "gram_peak_tflops": round(pk, 1), "bound": bound,
-            "gram_frac_of_dtype_peak": round(tf / pk, 4) if tf else None,
+            "gram_frac_of_dtype_peak": round(tf / pk, 4) if tf else None, "peak_note": note,
             "phases_ms": {"gram": round(reps[-1]["gram_ms"], 1), "power": round(reps[-1]["power_ms"], 1),
                           "left": round(reps[-1]["left_ms"], 1)},
             "applications": reps[-1]["applications"], "gpu_launches": int(sum(r["kernel_launches"] for r in reps))}
         torch.cuda.empty_cache()
-    ok = {p: r for p, r in rows.items() if r["sigma_max_rel_err_vs_truth"] <= 1e-5}
+    clk = clocks.stop()
+    del dA
+    torch.cuda.empty_cache()
+    ok = {p: r for p, r in rows.items() if r["within_1e-5"]}
     best = min(ok, key=lambda p: ok[p]["seconds_per_tsvd"]) if ok else None
     fp32 = rows["f32"]["seconds_per_tsvd"]
-    line = {"metric": "t-SVD seconds, mixed-precision Gram at sigma err <= 1e-5 (clustered spectrum)",
-            "value": ok[best]["seconds_per_tsvd"] if best else None, "unit": "s", "n_gpus": 1,
-            "steps": args.steps, "warmup": args.warmup, "higher_is_better": False, "scaling": "weak",
-            "vs_baseline": None, "dtype": best, "data": "synthetic",
-            "config": {"workload": f"dense in-core t-SVD, stacked-orthogonal A, m={m}, n={n}, sigma_i=1/(1+i), "
-                                   f"sigma_11=sigma_10-1e-3, k={k}, eps={eps}", "m": m, "n": n, "k": k, "eps": eps,
-                       "l2": "inputs larger than L2 (A is 32 GiB)"},
+    return {"workload": f"dense in-core t-SVD, stacked-orthogonal A, m={m}, n={n}, sigma_i=1/(1+i), "
+                        f"sigma_11=sigma_10-1e-3, k={k}, eps={eps}; every precision on the oracle's trajectory",
+            "m": m, "n": n, "k": k, "eps": eps, "steps": steps, "warmup": warmup,
+            "fastest_within_1e-5": best, "seconds_per_tsvd": ok[best]["seconds_per_tsvd"] if best else None,
             "speedup_vs_f32": round(fp32 / ok[best]["seconds_per_tsvd"], 3) if best else None,
-            "precisions": rows, "gen_seconds": round(gen_s, 1), "peak_source": peak_src}
+            "precisions": rows, "oracle_iters": [int(i) for i in it_o], "oracle_seconds": round(t_oracle, 1),
+            "gapped_graded": gapped, "clustered_pair": list(pair), "gen_seconds": round(gen_s, 1),
+            "peak_source": peak_src, "clocks": clk}
+
+
+def c4_workload(args):
+    """The mixed-precision leg as its own JSON line (seconds per t-SVD of the
+    fastest precision within 1e-5 of the oracle)."""
+    import torch
+
+    from paper_2208_08410_gb300 import _binding as B
+    B.load(build_if_missing=True)
+    torch.cuda.set_device(0)
+    measure_tf32_peak()
+    leg = leg_c4(args, args.steps, args.warmup)
+    line = {"metric": "t-SVD seconds, mixed-precision Gram at sigma err <= 1e-5 vs the FP64 oracle "
+                      "(clustered spectrum)",
+            "value": leg["seconds_per_tsvd"], "unit": "s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+            "dtype": leg["fastest_within_1e-5"], "data": "synthetic",
+            "config": {"workload": leg["workload"], "l2": "inputs larger than L2 (A is 32 GiB)"}, "c4": leg,
+            "clocks": leg["clocks"]}
     print(json.dumps(line), flush=True)
 
 
@@ -716,7 +924,8 @@ def tiled_workload(args):
             row["tile_stream_GBps"] = round(gbps, 1)
         out[name] = row
         torch.cuda.empty_cache()
-    pk = dtype_peak(B.TSVD_GRAM_TF32X3, peaks, sustained=True)[0]
+    pk = dtype_peak(B.TSVD_GRAM_TF32X3, peaks, sustained=True,
+                    tf32_measured=getattr(measure_tf32_peak, "result", None))[0]
     h = out["tiles_on_host"]
     # the pinned-copy peak for tile-sized copies: best of 5 copies of one tile
     tile_h = pinned_array((bs, bs), np.float64)
@@ -753,6 +962,16 @@ SP_EPS, SP_MAX_ITER = 1e-6, 200  # sparse serving requests: the out-of-core CSR 
 
 
 def serve_workload(args):
+    """The serving leg as its own JSON line."""
+    import torch
+
+    from paper_2208_08410_gb300 import _binding as B
+    B.load(build_if_missing=True)
+    torch.cuda.set_device(0)
+    print(json.dumps(leg_serve(args, args.requests)), flush=True)
+
+
+def leg_serve(args, n_req: int):
     """Serving: 10,000 dense t-SVD requests with Poisson arrivals at 2,000 req/s
     drawn from a pool of 512 matrices (m log-uniform in [512, 65536], n
     log-uniform in [64, 2048], sigma_i = rho^i with rho ~ U(0.5, 0.95), exact
@@ -769,9 +988,7 @@ def serve_workload(args):
 
     import synth
     from paper_2208_08410_gb300 import Plan, Server, _binding as B
-    B.load(build_if_missing=True)
-    torch.cuda.set_device(0)
-    n_pool, n_req, rate, eps = args.pool, args.requests, args.rate, 1e-8
+    n_pool, rate, eps = args.pool, args.rate, 1e-8
     t0 = time.time()
     shapes = synth.serving_shapes(n_pool, seed=11)
     pool = []
@@ -906,10 +1123,13 @@ def serve_workload(args):
     server.autotune(iters=30)
     table = {d: server.cluster_for(d) for d in (64, 128, 256, 512, 1024, 2048)}
     s0 = server.stats()
+    clocks = ClockSampler(0)
+    clocks.start()
     timed = run(server, True)
     s1 = server.stats()
     capacity = run(server, False)
     s2 = server.stats()
+    clk = clocks.stop()
     server.close()
     # baseline: the per-request path, one request at a time, FP32 Gram, same requests
     # (the per-request path takes m >= n only, so the sample skips wide requests)
@@ -954,11 +1174,14 @@ def serve_workload(args):
                                                                  "Gram, pinned host A, one at a time"},
             "speedup_capacity_vs_per_request": round(capacity["solves_per_s"] / base_rate, 2) if base_rate else None,
             "waves": s2["waves"] - s0["waves"], "gpu_launches": launches,
-            "peak_device_bytes": s2["peak_device_bytes"], "gen_seconds": round(gen_s, 1)}
-    print(json.dumps(line), flush=True)
+            "peak_device_bytes": s2["peak_device_bytes"], "gen_seconds": round(gen_s, 1), "clocks": clk}
+    for a in pool + [outU, outV, outS]:
+        free_pinned(a)
+    torch.cuda.empty_cache()
+    return line
 
 
-def csr_pair_checks(dcsr, host, m, nnz, peaks, peak_src, args):
+def csr_pair_checks(dcsr, host, m, nnz, peaks, peak_src, args, with_cpu=True):
     """Full-size measurements of the fused CSR pair (one operator application
     w = A^T (A v), ||A v||^2) on the device-resident matrix:
     - roofline: average duration of tsvd_csr_gram_apply over the whole matrix
@@ -998,7 +1221,7 @@ def csr_pair_checks(dcsr, host, m, nnz, peaks, peak_src, args):
                 "ms_per_application": round(t * 1e3, 3), "algorithmic_bytes": alg,
                 "peak_source": f"{peak_src} copy bandwidth"}
     cpu = None
-    if not args.no_cpu:
+    if with_cpu:
         from oracle.csr_c import csr_gram_apply as oracle_apply
         vh = v.cpu().numpy().astype(np.float64)
         bl = 1 << 20
@@ -1045,20 +1268,32 @@ def csr_oom_sweep(host, m, nnz, args):
 
 
 def csr_workload(args):
+    """The sparse out-of-core leg as its own JSON line (plus the out-of-memory
+    sweep with --sweep)."""
+    import torch
+
+    from paper_2208_08410_gb300 import _binding as B
+    B.load(build_if_missing=True)
+    torch.cuda.set_device(0)
+    print(json.dumps(leg_c3(args, args.steps, args.warmup, with_cpu=not args.no_cpu, sweep=args.sweep)),
+          flush=True)
+
+
+def leg_c3(args, steps: int, warmup: int, with_cpu: bool = False, sweep: bool = False, h2d_peak=None,
+           m: int = 0):
     """Sparse out-of-core t-SVD: m = n = 2^25 (default), ~33.5 entries per row
     at uniform random positions, U(0,1) values, row blocks of 2^20 rows under a
     4 GB device budget, k = 16.  A-stream throughput = CSR bytes consumed per
     step (every operator application, the sigma passes and the U pass read the
     whole matrix) / step seconds.  The number of applications per triplet is
     fixed with --csr-iters (the paper's out-of-memory runs fix it at 100) to
-    bound the run time."""
+    bound the run time.  value: CSR resident in HBM; e2e: CSR streamed from
+    page-locked host memory, against the pinned copy rate (h2d_peak)."""
     import torch
 
     import synth
     from paper_2208_08410_gb300 import Plan, _binding as B
-    B.load(build_if_missing=True)
-    torch.cuda.set_device(0)
-    m = args.m or (1 << 25)
+    m = m or args.m or (1 << 25)
     k = K
     t0 = time.time()
     dcsr = synth.csr_uniform_torch(m, m, 33.5, seed=1)
@@ -1075,12 +1310,14 @@ def csr_workload(args):
     gen_s = time.time() - t0
     iters = [args.csr_iters] * k
     peaks, peak_src = load_peaks()
-    roofline, cpu = csr_pair_checks(dcsr, host, m, nnz, peaks, peak_src, args)
+    roofline, cpu = csr_pair_checks(dcsr, host, m, nnz, peaks, peak_src, args, with_cpu)
+    clocks = ClockSampler(0)
+    clocks.start()
     plan_d = Plan(dcsr, k, EPS, out_device=True, iters_override=iters, time_kernels=True)
-    sec, wall, reps, res = time_steps(plan_d, dcsr, args.steps, args.warmup)
+    sec, wall, reps, res = time_steps(plan_d, dcsr, steps, warmup)
     apps = reps[-1]["applications"]
     passes = apps + k + 1  # applications, one sigma pass per triplet, the U pass
-    value = csr_bytes * passes * args.steps / sec / 1e9
+    value = csr_bytes * passes * steps / sec / 1e9
     # the operator the in-core t-SVD runs (column-chunked two-pass when v and w outgrow L2):
     # CUDA events around every application on the launching stream
     nch = reps[-1]["csr_chunks"]
@@ -1099,19 +1336,35 @@ def csr_workload(args):
     torch.cuda.empty_cache()
     plan_h = Plan(host, k, EPS, iters_override=iters, device_budget=4 * 10 ** 9, block_rows=1 << 20,
                   force_stream=True, time_kernels=True)
-    sec_e, wall_e, reps_e, res_e = time_steps(plan_h, host, max(1, args.e2e_steps or args.steps), args.warmup)
-    nst = max(1, args.e2e_steps or args.steps)
+    nst = max(1, min(steps, args.e2e_steps or steps))
+    sec_e, wall_e, reps_e, res_e = time_steps(plan_h, host, nst, warmup)
     e2e = csr_bytes * passes * nst / sec_e / 1e9
     plan_h.close()
-    sweep = csr_oom_sweep(host, m, nnz, args) if args.sweep else None
+    clk = clocks.stop()
+    if h2d_peak is None:
+        blk = torch.from_numpy(hvals[:1 << 26])
+        dst = torch.empty_like(blk, device="cuda")
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        best = 0.0
+        for _ in range(3):
+            e0.record()
+            dst.copy_(blk, non_blocking=True)
+            e1.record()
+            e1.synchronize()
+            best = max(best, blk.numel() * 4 / (e0.elapsed_time(e1) / 1e3) / 1e9)
+        h2d_peak = best
+        del dst
+    sweep = csr_oom_sweep(host, m, nnz, args) if sweep else None
     line = {"metric": "t-SVD A-stream throughput (CSR)", "value": round(value, 2), "unit": "GB/s", "n_gpus": 1,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(sec / args.steps * 1e3, 1),
+            "steps": steps, "warmup": warmup, "ms_per_step": round(sec / steps * 1e3, 1),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": f"sparse CSR t-SVD, m=n={m}, ~33.5 nnz/row ({nnz} nnz), k={k}, "
                                    f"{args.csr_iters} applications per triplet", "m": m, "nnz": nnz,
                        "csr_bytes": csr_bytes, "k": k, "block_rows_e2e": 1 << 20,
                        "device_budget_bytes_e2e": 4 * 10 ** 9},
             "e2e": {"value": round(e2e, 2), "unit": "GB/s", "ms_per_step": round(sec_e / nst * 1e3, 1),
+                    "steps": nst, "pinned_copy_peak_GBps": round(h2d_peak, 2),
+                    "frac_of_pinned_copy": round(e2e / h2d_peak, 4),
                     "h2d_bytes_per_step": int(reps_e[-1]["h2d_bytes"]),
                     "d2h_bytes_per_step": int(reps_e[-1]["d2h_bytes"]),
                     "blocks_per_pass": reps_e[-1]["n_blocks"],
@@ -1123,8 +1376,12 @@ def csr_workload(args):
                     "pair_kernel_launches_per_step": reps_e[-1]["gram_kernel_launches"]},
             "roofline": roofline, "cpu_baseline": cpu, "oom_sweep": sweep,
             "sigma": [round(float(x), 6) for x in res.sigma.cpu().numpy()], "gen_seconds": round(gen_s, 1),
-            "gpu_launches": int(sum(r["kernel_launches"] for r in reps))}
-    print(json.dumps(line), flush=True)
+            "gpu_launches": int(sum(r["kernel_launches"] for r in reps)), "clocks": clk}
+    for a in (hrp, hci, hvals):
+        free_pinned(a)
+    del dcsr
+    torch.cuda.empty_cache()
+    return line
 
 
 def main():
@@ -1152,6 +1409,13 @@ def main():
     ap.add_argument("--csr-share", type=float, default=0.1, help="serving: fraction of sparse requests")
     ap.add_argument("--csr-iters", type=int, default=10)
     ap.add_argument("--sweep", action="store_true", help="CSR: out-of-memory sweep over n_b and q_s")
+    ap.add_argument("--legs", default="c2_small,c4,c3_streamed,serve",
+                    help="dense workload: further configurations run after the headline and reported as keys of "
+                         "the same line (comma list, empty for none)")
+    ap.add_argument("--legs-budget-s", type=float, default=1500.0,
+                    help="skip the remaining legs once the run has taken this long")
+    ap.add_argument("--serve-requests-leg", type=int, default=10_000, help="requests of the serving leg")
+    ap.add_argument("--e2e-block-rows", type=int, default=BLOCK_ROWS, help="rows per streamed block (e2e)")
     args = ap.parse_args()
     if args.case:
         kernel_case(args)
@@ -1187,6 +1451,7 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     from paper_2208_08410_gb300 import Plan, _binding as B
     B.load(build_if_missing=True)
+    t_run = time.time()
 
     m = pick_m(args.m)
     t0 = time.time()
@@ -1200,6 +1465,7 @@ def main():
 
     prec = args.precision
     peaks, peak_src = load_peaks()
+    tf32_meas = measure_tf32_peak()
     # ---------------- value: A in HBM
     plan_dev = Plan(dA, K, EPS, precision=prec, out_device=True, time_kernels=True)
     clocks = ClockSampler(local)
@@ -1218,8 +1484,8 @@ def main():
     gk_n = sum(r["gram_kernel_launches"] for r in reps)
     flops_per_step = m * N_COLS * (N_COLS + 1)
     achieved_tf = flops_per_step * args.steps / (gk_ms / 1e3) / 1e12 if gk_ms > 0 else None
-    peak, bound = dtype_peak(prec, peaks, sustained=True)
-    roof = {"bound": bound, "peak_note": PEAK_NOTES[prec].format(src=peak_src, kind="sustained")}
+    peak, bound, peak_note = dtype_peak(prec, peaks, sustained=True, tf32_measured=tf32_meas)
+    roof = {"bound": bound, "peak_note": peak_note}
     chunk_rows = int(round(m / max(gk_n / max(args.steps, 1), 1)))
     kname = {0: "syrk_simt_kernel", 1: "syrk_tc_kernel<TF32>", 2: "syrk_tc_kernel<TF32X3>",
              3: "syrk_tc_kernel<BF16X3>"}[prec]
@@ -1239,12 +1505,15 @@ def main():
     small = c1_latency() if rank == 0 else None
 
     # ---------------- e2e: pinned host A, streamed, outputs to host
-    e2e_steps = args.e2e_steps or args.steps
-    plan_host = Plan(A, K, EPS, precision=prec, device_budget=BUDGET, block_rows=BLOCK_ROWS, force_stream=True,
-                     time_kernels=True)
+    e2e_steps = args.e2e_steps or min(args.steps, 10)
+    plan_host = Plan(A, K, EPS, precision=prec, device_budget=BUDGET, block_rows=args.e2e_block_rows,
+                     force_stream=True, time_kernels=True)
     outs = {"U": pinned_array((K, m), np.float32), "sigma": pinned_array((K,), np.float64),
             "V": pinned_array((K, N_COLS), np.float32)}
+    clocks_e = ClockSampler(local)
+    clocks_e.start()
     sec_e, wall_e, reps_e, res_host = time_steps(plan_host, A, e2e_steps, args.warmup, outs=outs)
+    clk_e = clocks_e.stop()
     rate_e, sec_e = whole_job_rate(sec_e, bytes_per_step * e2e_steps, dist, "cuda")
     e2e_step = sec_e / e2e_steps
     h2d_b = reps_e[-1]["h2d_bytes"]
@@ -1266,9 +1535,17 @@ def main():
                    "copy_stream_GBps": round(reps_e[-1]["h2d_bytes"] / (reps_e[-1]["h2d_copy_ms"] / 1e3) / 1e9, 2)
                    if reps_e[-1]["h2d_copy_ms"] else None,
                    "copy_min_GBps": round(reps_e[-1]["h2d_copy_min_gbps"], 1),
-                   "copy_max_GBps": round(reps_e[-1]["h2d_copy_max_gbps"], 1)}}
+                   "copy_max_GBps": round(reps_e[-1]["h2d_copy_max_gbps"], 1)},
+           "gram_kernels": {"syrk_ms_per_step": round(reps_e[-1]["gram_kernel_ms"], 2),
+                            "launches_per_step": reps_e[-1]["gram_kernel_launches"],
+                            "syrk_tflops": round(m * N_COLS * (N_COLS + 1) / (reps_e[-1]["gram_kernel_ms"] / 1e3)
+                                                 / 1e12, 1) if reps_e[-1]["gram_kernel_ms"] else None},
+           "clocks": clk_e}
     launches_e = int(sum(r["kernel_launches"] for r in reps_e))
     plan_host.close()
+    for a in outs.values():
+        free_pinned(a)
+    del res_host
 
     parity = None
     if not args.no_parity and rank == 0:
@@ -1279,13 +1556,43 @@ def main():
         Vg = res_dev.V.cpu().numpy()
         cpu = cpu_baseline(m, A, Vg, sig, res_dev.iters)
 
+    del dA
+    torch.cuda.empty_cache()
+    B.tsvd_host_free(hptr)
+    hptr = None
+    del A
+    legs = {}
+    if rank == 0 and world == 1:
+        steps_leg, warm_leg = max(1, min(args.steps, 3)), max(1, min(args.warmup, 2))
+        runners = {"c2_small": lambda: leg_c2_small(args),
+                   "c4": lambda: leg_c4(args, steps_leg, warm_leg),
+                   "c3_streamed": lambda: leg_c3(args, steps_leg, 1, with_cpu=False, h2d_peak=h2d_peak,
+                                                 m=1 << 25),
+                   "serve": lambda: leg_serve(args, args.serve_requests_leg)}
+        for name in [x for x in args.legs.split(",") if x]:
+            if name not in runners:
+                legs[name] = {"error": "unknown leg"}
+                continue
+            if time.time() - t_run > args.legs_budget_s:
+                legs[name] = {"skipped": f"run time above {args.legs_budget_s:.0f} s before this leg"}
+                continue
+            t_leg = time.time()
+            try:
+                legs[name] = runners[name]()
+            except Exception as e:  # a leg's failure is reported in the line, not fatal to it
+                legs[name] = {"error": repr(e)[:400]}
+            legs[name]["leg_seconds"] = round(time.time() - t_leg, 1)
+            torch.cuda.empty_cache()
+
     if rank == 0:
         line = {"metric": "t-SVD A-stream throughput", "value": round(value, 3), "unit": "GB/s", "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(step_s * 1e3, 2),
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-                "dtype": "f32" if prec != 1 else "tf32", "data": "synthetic",
-                "config": {"workload": f"dense out-of-core t-SVD (rank-64 + 1e-4 noise), m={m}, n={N_COLS}, "
-                                       f"k={K}, eps={EPS}", "m": m, "n": N_COLS, "k": K, "eps": EPS,
+                "dtype": PREC_NAMES[prec], "data": "synthetic",
+                "config": {"workload": f"dense t-SVD (rank-64 + 1e-4 noise), m={m}, n={N_COLS}, k={K}, eps={EPS}; "
+                                       "value: A resident in HBM (in-core); e2e: A streamed from page-locked host "
+                                       f"memory under a {BUDGET / 1e9:.0f} GB device budget (out-of-core)",
+                           "m": m, "n": N_COLS, "k": K, "eps": EPS,
                            "block_rows": BLOCK_ROWS, "device_budget_bytes_e2e": BUDGET,
                            "full_m": FULL_M, "host_ram_limited": m < FULL_M,
                            "l2": "inputs larger than L2 (A is %.0f GiB)" % (m * N_COLS * 4 / 2 ** 30),
@@ -1298,12 +1605,13 @@ def main():
                 "phases_ms": {"gram": round(reps[-1]["gram_ms"], 2), "power": round(reps[-1]["power_ms"], 2),
                               "left": round(reps[-1]["left_ms"], 2), "applications": reps[-1]["applications"]},
                 "iters": res_dev.iters, "sigma": [round(float(s), 8) for s in np.asarray(res_dev.sigma.cpu())],
-                "parity": parity, "gen_seconds": round(gen_s, 1)}
+                "parity": parity, "gen_seconds": round(gen_s, 1), "tf32_cublas_peak": tf32_meas,
+                "run_seconds": round(time.time() - t_run, 1)}
+        line.update(legs)
         print(json.dumps(line), flush=True)
     if dist:
         dist.barrier()
         dist.destroy_process_group()
-    B.tsvd_host_free(hptr)
 
 
 if __name__ == "__main__":

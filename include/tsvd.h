@@ -341,8 +341,10 @@ TSVD_API tsvd_status tsvd_power_dense(int64_t n, const float *G32, const double 
  * Limits: n <= TSVD_NOALLOC_MAX_N and l <= TSVD_NOALLOC_MAX_L, otherwise
  * TSVD_EINVAL with a message in tsvd_last_cuda_error().
  * The first call on a device looks up the array's device address for that
- * device (cudaGetSymbolAddress, with that device current); make that first
- * call before any stream capture.  All calls share the one array, which keeps
+ * device (cudaGetSymbolAddress, with that device current), and so does the
+ * first call after the device's context was recreated (cudaDeviceReset): the
+ * address is kept with the context it belongs to.  Make such a call before
+ * any stream capture.  All calls share the one array, which keeps
  * the last call's contents (the call clears what must start at zero): calls
  * that overlap on the GPU, on any streams, race and give wrong results.
  */

@@ -181,6 +181,8 @@ struct tsvd_plan_s {
   // planning
   int mode = MODE_DEVICE;
   int64_t chunk_rows = 0, n_chunks = 0;
+  int64_t gram_rows = 0;        // dense: rows per Gram launch (a block is cut into launches of this size)
+  int64_t n_gram_launches = 0;  // dense: Gram launches per pass
   int n_buffers = 3;
   // CSR partition (rows) and per-block entry counts (host-located CSR)
   std::vector<int64_t> block_start;
@@ -279,8 +281,13 @@ tsvd_status plan_dense(tsvd_plan_s *p) {
   const bool host_a = p->location == TSVD_HOST;
   const bool host_u = p->opt.out_location == TSVD_HOST;
   const int R = p->n_buffers;
+  // The Gram kernels run on sub-chunks of at most gram_target rows (the
+  // in-core launch size, ~1 GiB of A): a larger streamed block is cut into
+  // several launches, so the tensor-core scratch stays that size and the SYRK
+  // keeps the K-slice working set it was tuned for.
+  const int64_t gram_target = std::max<int64_t>(256, round_up(((int64_t)1 << 30) / (n * 4), 32));
   auto chunk_cost = [&](int64_t rows, int mode) -> size_t {
-    size_t s = gram_tc_scratch_bytes(rows, n, prec) + 256;
+    size_t s = gram_tc_scratch_bytes(std::min(rows, gram_target), n, prec) + 256;
     if (mode == MODE_STREAM) s += (size_t)R * (size_t)round_up(rows * n * 4, 256);
     if (host_u) s += 2 * (size_t)round_up(rows * k * 4, 256);
     return s;
@@ -310,7 +317,11 @@ tsvd_status plan_dense(tsvd_plan_s *p) {
   p->mode = mode;
   p->chunk_rows = rows;
   p->n_chunks = ceil_div(m, rows);
-  p->b_gscr = gram_tc_scratch_bytes(rows, n, prec);
+  p->gram_rows = std::min(rows, gram_target);
+  p->n_gram_launches = 0;
+  for (int64_t c = 0; c < p->n_chunks; ++c)
+    p->n_gram_launches += ceil_div(std::min(rows, m - c * rows), p->gram_rows);
+  p->b_gscr = gram_tc_scratch_bytes(p->gram_rows, n, prec);
   p->o_gscr = c.take(p->b_gscr + 256);
   if (mode == MODE_RESIDENT) p->o_res = c.take(resident_bytes);
   if (host_u) {
@@ -985,9 +996,9 @@ tsvd_status factor_dense(Run &r, float *U, double *sigma_out, float *V_out, tsvd
   void *gscr = ws + p->o_gscr;
 
   const bool timed = p->opt.time_kernels != 0;
-  if (timed && (int64_t)p->ev_k.size() < 2 * p->n_chunks) {
+  if (timed && (int64_t)p->ev_k.size() < 2 * p->n_gram_launches) {
     const size_t have = p->ev_k.size();
-    p->ev_k.resize(2 * p->n_chunks, nullptr);
+    p->ev_k.resize(2 * p->n_gram_launches, nullptr);
     for (size_t i = have; i < p->ev_k.size(); ++i) TSVD_CUDA(cudaEventCreate(&p->ev_k[i]));
   }
   TSVD_CUDA(cudaEventRecord(p->ev_t[0], r.cs));
@@ -996,15 +1007,22 @@ tsvd_status factor_dense(Run &r, float *U, double *sigma_out, float *V_out, tsvd
   // status word of the tensor-core scratch, zeroed once for the whole pass
   // (the 256-byte aligned scratch starts with its status word)
   if (p->opt.precision != TSVD_GRAM_FP32) TSVD_CUDA(cudaMemsetAsync(gscr, 0, 4, r.cs));
+  int64_t gl = 0;  // Gram launches so far
   for (int64_t c = 0; c < p->n_chunks; ++c) {
     const int64_t r0 = c * p->chunk_rows, rows = std::min(p->chunk_rows, p->K - r0);
     const float *Ab;
     int64_t ldb;
     int slot;
     TSVD_TRY(acquire_dense(r, r0, rows, &Ab, &ldb, &slot, true));
-    TSVD_TRY(gram_dispatch(Ab, rows, n, ldb, G64, p->opt.precision, gscr, p->b_gscr, r.cs,
-                           timed ? p->ev_k[2 * c] : nullptr, timed ? p->ev_k[2 * c + 1] : nullptr, false, p->wide,
-                           (uint64_t)p->opt.wait_limit_ns));
+    // the block in launches of gram_rows contraction indices (rows of a tall
+    // block, columns of a wide one)
+    for (int64_t s0 = 0; s0 < rows; s0 += p->gram_rows, ++gl) {
+      const int64_t sr = std::min(p->gram_rows, rows - s0);
+      const float *As = p->wide ? Ab + s0 : Ab + s0 * ldb;
+      TSVD_TRY(gram_dispatch(As, sr, n, ldb, G64, p->opt.precision, gscr, p->b_gscr, r.cs,
+                             timed ? p->ev_k[2 * gl] : nullptr, timed ? p->ev_k[2 * gl + 1] : nullptr, false,
+                             p->wide, (uint64_t)p->opt.wait_limit_ns));
+    }
     TSVD_TRY(release_slot(r, slot));
   }
   int32_t gram_err = 0;
@@ -1062,13 +1080,13 @@ tsvd_status factor_dense(Run &r, float *U, double *sigma_out, float *V_out, tsvd
   TSVD_CUDA(cudaEventElapsedTime(&t23, p->ev_t[2], p->ev_t[3]));
   if (timed && rep) {
     double sum = 0.0;
-    for (int64_t c = 0; c < p->n_chunks; ++c) {
+    for (int64_t c = 0; c < p->n_gram_launches; ++c) {
       float t = 0.f;
       TSVD_CUDA(cudaEventElapsedTime(&t, p->ev_k[2 * c], p->ev_k[2 * c + 1]));
       sum += t;
     }
     rep->gram_kernel_ms = sum;
-    rep->gram_kernel_launches = (int32_t)p->n_chunks;
+    rep->gram_kernel_launches = (int32_t)p->n_gram_launches;
   }
   int flags = 0;
   int64_t apps = 0;

@@ -22,6 +22,8 @@
 //   convergence decision without a host round trip.
 // Also here: the symmetrising copy G64 -> G32, the Philox-4x32-10 start
 // draws, and small conversions.
+#include <cuda.h>
+
 #include <algorithm>
 #include <mutex>
 
@@ -655,23 +657,53 @@ tsvd_status launch_philox_raw(const uint32_t *ctr, const uint32_t *key, uint32_t
 // the largest problem it accepts.  Every GPU that loads the library holds it
 // until the process exits.  Host code may not use the array's name as a
 // device address (on the host it is only a stand-in for the symbol), so its
-// device address is looked up once per device with cudaGetSymbolAddress.
+// device address is looked up per device with cudaGetSymbolAddress, with that
+// device current.  The address belongs to the device's context: it is kept
+// with the context it was found in and looked up again when the current
+// context is a different one (the primary context recreated after
+// cudaDeviceReset loads the module again, possibly at another address).
 constexpr int64_t kNoallocScratchBytes =
     256 + 2 * TSVD_NOALLOC_MAX_N * 4 + (int64_t)kMaxPowerBlocks * ((2 * TSVD_NOALLOC_MAX_L + 12 + 3) / 4 * 4) * 8;
 static __device__ __align__(256) unsigned char g_power_noalloc_scratch[kNoallocScratchBytes];
 
+typedef CUresult (*CtxGetCurrentFn)(CUcontext *);
+
+static tsvd_status current_context(CUcontext *ctx) {
+  static CtxGetCurrentFn fn = nullptr;
+  if (!fn) {
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    TSVD_CUDA(cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q));
+    if (q != cudaDriverEntryPointSuccess || !p) {
+      set_error_text("cuCtxGetCurrent not available");
+      return TSVD_ECUDA;
+    }
+    fn = reinterpret_cast<CtxGetCurrentFn>(p);
+  }
+  *ctx = nullptr;
+  if (fn(ctx) != CUDA_SUCCESS) return TSVD_ECUDA;
+  return TSVD_OK;
+}
+
 static tsvd_status noalloc_scratch(void **out) {
   static std::mutex mu;
   static void *addr[128] = {};
+  static CUcontext ctx_of[128] = {};
   int dev = -1;
   TSVD_CUDA(cudaGetDevice(&dev));
   if (dev < 0 || dev >= 128) return TSVD_EUNSUPPORTED;
+  CUcontext ctx = nullptr;
+  TSVD_TRY(current_context(&ctx));
   std::lock_guard<std::mutex> lock(mu);
-  if (!addr[dev]) {
+  if (!addr[dev] || !ctx || ctx_of[dev] != ctx) {
     void *p = nullptr;
+    // (the lookup also makes the device's primary context current if no
+    // runtime call on this thread has done so yet)
     TSVD_CUDA(cudaGetSymbolAddress(&p, g_power_noalloc_scratch));
     if (!p) return TSVD_ECUDA;
+    TSVD_TRY(current_context(&ctx));
     addr[dev] = p;
+    ctx_of[dev] = ctx;
   }
   *out = addr[dev];
   return TSVD_OK;

@@ -260,3 +260,25 @@ def test_server_options_validation(lib):
         assert B.tsvd_server_create(C.byref(h), C.byref(o)) == B.TSVD_EINVAL, field
     assert B.tsvd_server_submit(None, None, 10, 10, 1, 1e-6, 10, 0, 0, None, None, None, None, None) == B.TSVD_EINVAL
     assert B.tsvd_server_cluster_for(None, 100) == 0
+
+
+def test_binding_constants_match_the_header():
+    """Every #define and enum value the binding copies from include/tsvd.h
+    has the header's value (the no-allocation limits, flags, kernel choices,
+    status codes), so a change to the header cannot drift from Python."""
+    import re
+    hdr = open(os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include",
+                            "tsvd.h")).read()
+    defines = {m.group(1): int(m.group(2)) for m in re.finditer(r"#define\s+(TSVD_\w+)\s+(-?\d+)\b", hdr)}
+    enums = {m.group(1): int(m.group(2)) for m in re.finditer(r"\b(TSVD_\w+)\s*=\s*(-?\d+)", hdr)}
+    named = dict(defines, **enums)
+    checked = 0
+    for name, value in named.items():
+        if hasattr(B, name):
+            assert getattr(B, name) == value, name
+            checked += 1
+    for must in ("TSVD_NOALLOC_MAX_N", "TSVD_NOALLOC_MAX_L", "TSVD_FLAG_TIMEOUT", "TSVD_POWER_CLUSTER",
+                 "TSVD_ETIMEDOUT", "TSVD_GRAM_BF16X3"):
+        assert must in named and hasattr(B, must), must
+    assert checked >= 20, checked
+

@@ -67,6 +67,36 @@ def test_noalloc_power_matches_allocating_entry_point():
             assert abs(got_s2 - want_s2) <= 1e-6 * want_s2
 
 
+def test_noalloc_power_at_its_size_limit():
+    """The largest problem the fixed array accepts (n = TSVD_NOALLOC_MAX_N,
+    l = TSVD_NOALLOC_MAX_L earlier vectors; the launch needs the array's whole
+    size and more than 48 KB of dynamic shared memory): the same result as the
+    allocating entry point with its own scratch, twice in a row."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    B.load()
+    n, l, r = B.TSVD_NOALLOC_MAX_N, B.TSVD_NOALLOC_MAX_L, B.TSVD_NOALLOC_MAX_L + 16
+    rng = np.random.default_rng(5)
+    W, _ = np.linalg.qr(rng.standard_normal((n, r)))  # seeded orthonormal basis of a rank-r Gram matrix
+    lam = 0.9 ** np.arange(r)
+    dW = torch.from_numpy(W).cuda()
+    dG64 = (dW * torch.from_numpy(lam).cuda()) @ dW.T  # G = W diag(lam) W^T, 2 GiB in FP64
+    dG32 = dG64.float()
+    dV = torch.from_numpy(np.ascontiguousarray(W[:, :l].T)).cuda()  # the l earlier vectors, column-major
+    ds2 = torch.from_numpy(lam[:l].copy()).cuda()
+    x = rng.standard_normal(n)
+    scratch = torch.empty(B.tsvd_power_scratch_bytes(n, l), dtype=torch.uint8, device="cuda")
+    want_v, want_s2, want_info = _run("tsvd_power_dense", n, l, dG32, dG64, dV, ds2, x, 30, scratch)
+    assert want_info[0] == 30 and want_info[2] == 0
+    for _ in range(2):
+        v, got_s2, info = _run("tsvd_power_dense_noalloc", n, l, dG32, dG64, dV, ds2, x, 30)
+        assert info[0] == 30 and info[2] == 0
+        assert ref.vector_angle(v, want_v) < 1e-5
+        assert abs(got_s2 - want_s2) <= 1e-6 * want_s2
+    del dG64, dG32, dW, scratch
+    torch.cuda.empty_cache()
+
+
 def test_noalloc_rejects_sizes_beyond_its_scratch():
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
