@@ -165,6 +165,30 @@ def make_host_A(m: int, seed: int):
     return A, ptr, facts
 
 
+def thp_coverage(arr: np.ndarray) -> dict:
+    """Resident and huge-page-backed bytes of the mappings that hold `arr`
+    (from /proc/self/smaps), to see whether the page-locked buffer got the
+    transparent huge pages its allocator asked for."""
+    lo = arr.__array_interface__["data"][0]
+    hi = lo + arr.nbytes
+    rss = huge = 0
+    cur = False
+    try:
+        for ln in open("/proc/self/smaps"):
+            parts = ln.split()
+            if parts and "-" in parts[0] and len(parts) >= 5 and not parts[0].endswith(":"):
+                a, b = (int(x, 16) for x in parts[0].split("-"))
+                cur = a < hi and b > lo
+            elif cur and parts[0] == "Rss:":
+                rss += int(parts[1]) * 1024
+            elif cur and parts[0] == "AnonHugePages:":
+                huge += int(parts[1]) * 1024
+    except OSError:
+        return {}
+    return {"rss_GiB": round(rss / 2 ** 30, 2), "huge_GiB": round(huge / 2 ** 30, 2),
+            "huge_frac": round(huge / rss, 4) if rss else None}
+
+
 def measure_h2d_peak(A: np.ndarray):
     """Pinned host -> HBM copy rates (cudaMemcpyAsync via torch, one copy stream):
     burst = best of 3 copies of the first 4 GiB block; sustained = every row
@@ -701,6 +725,7 @@ def leg_c2_small(args, h2d_peak=None):
     try:
         burst, sustained = measure_h2d_peak(A)
         per_block = getattr(measure_h2d_peak, "per_block", None)
+        thp = thp_coverage(A)
         x = synth.start_normals(N_COLS, K, seed=3)
         outs = {"U": pinned_array((K, m), np.float32), "sigma": pinned_array((K,), np.float64),
                 "V": pinned_array((K, N_COLS), np.float32)}
@@ -728,7 +753,7 @@ def leg_c2_small(args, h2d_peak=None):
                "copy_stream_GBps": round(r["h2d_bytes"] / (r["h2d_copy_ms"] / 1e3) / 1e9, 2)
                if r["h2d_copy_ms"] else None,
                "copy_min_GBps": round(r["h2d_copy_min_gbps"], 1), "copy_max_GBps": round(r["h2d_copy_max_gbps"], 1),
-               "clocks": clk}
+               "host_A_pages": thp, "clocks": clk}
         # ---- parity against the oracle's trajectory
         t0 = time.time()
         G = ref.gram_row_blocks(A, 65_536)
@@ -1364,6 +1389,7 @@ def leg_c3(args, steps: int, warmup: int, with_cpu: bool = False, sweep: bool = 
                        "device_budget_bytes_e2e": 4 * 10 ** 9},
             "e2e": {"value": round(e2e, 2), "unit": "GB/s", "ms_per_step": round(sec_e / nst * 1e3, 1),
                     "steps": nst, "pinned_copy_peak_GBps": round(h2d_peak, 2),
+                    "host_values_pages": thp_coverage(hvals), "host_col_idx_pages": thp_coverage(hci),
                     "frac_of_pinned_copy": round(e2e / h2d_peak, 4),
                     "h2d_bytes_per_step": int(reps_e[-1]["h2d_bytes"]),
                     "d2h_bytes_per_step": int(reps_e[-1]["d2h_bytes"]),
@@ -1457,6 +1483,7 @@ def main():
     t0 = time.time()
     A, hptr, facts = make_host_A(m, seed=rank)
     gen_s = time.time() - t0
+    thp_A = thp_coverage(A)
     h2d_burst, h2d_peak = measure_h2d_peak(A)
     dA = torch.empty((m, N_COLS), dtype=torch.float32, device="cuda")
     for r0 in range(0, m, BLOCK_ROWS):
@@ -1535,7 +1562,8 @@ def main():
                    "copy_stream_GBps": round(reps_e[-1]["h2d_bytes"] / (reps_e[-1]["h2d_copy_ms"] / 1e3) / 1e9, 2)
                    if reps_e[-1]["h2d_copy_ms"] else None,
                    "copy_min_GBps": round(reps_e[-1]["h2d_copy_min_gbps"], 1),
-                   "copy_max_GBps": round(reps_e[-1]["h2d_copy_max_gbps"], 1)},
+                   "copy_max_GBps": round(reps_e[-1]["h2d_copy_max_gbps"], 1),
+                   "host_A_pages": thp_A},
            "gram_kernels": {"syrk_ms_per_step": round(reps_e[-1]["gram_kernel_ms"], 2),
                             "launches_per_step": reps_e[-1]["gram_kernel_launches"],
                             "syrk_tflops": round(m * N_COLS * (N_COLS + 1) / (reps_e[-1]["gram_kernel_ms"] / 1e3)

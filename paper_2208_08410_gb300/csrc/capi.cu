@@ -93,6 +93,13 @@ tsvd_status pinned_alloc(void **ptr, size_t bytes) {
   unsigned char *p = reinterpret_cast<unsigned char *>(start);
   madvise(p, len, MADV_HUGEPAGE);  // advisory: base pages where huge ones are not available
   for (size_t o = 0; o < len; o += page) p[o] = 0;  // fault the pages in before pinning them
+#ifndef MADV_COLLAPSE
+#define MADV_COLLAPSE 25
+#endif
+  // ranges that faulted in as base pages (no free huge page at the time) are
+  // collapsed into huge pages now, with compaction, where the kernel can;
+  // an error (an older kernel, no memory to compact) leaves them as they are
+  if (len >= hp) madvise(p, len, MADV_COLLAPSE);
   const cudaError_t e = cudaHostRegister(p, len, cudaHostRegisterPortable);
   if (e != cudaSuccess) {
     set_cuda_error(e, "cudaHostRegister", __FILE__, __LINE__);
