@@ -189,6 +189,38 @@ def thp_coverage(arr: np.ndarray) -> dict:
             "huge_frac": round(huge / rss, 4) if rss else None}
 
 
+def thp_by_block(arr: np.ndarray, block_bytes: int, samples: int = 16):
+    """Per block of `arr`, the fraction of sampled base pages that belong to a
+    transparent huge page: the page frame from /proc/self/pagemap and its THP
+    flag (bit 22) from /proc/kpageflags.  Both need root; None otherwise."""
+    base = arr.__array_interface__["data"][0]
+    page = os.sysconf("SC_PAGE_SIZE")
+    try:
+        pm = open("/proc/self/pagemap", "rb")
+        kf = open("/proc/kpageflags", "rb")
+    except OSError:
+        return None
+    out = []
+    with pm, kf:
+        for b0 in range(0, arr.nbytes, block_bytes):
+            span = min(block_bytes, arr.nbytes - b0)
+            hits = seen = 0
+            for j in range(samples):
+                va = base + b0 + span * j // samples
+                va -= va % page
+                pm.seek(va // page * 8)
+                e = int.from_bytes(pm.read(8), "little")
+                pfn = e & ((1 << 55) - 1)
+                if not (e >> 63) & 1 or pfn == 0:
+                    continue
+                kf.seek(pfn * 8)
+                f = int.from_bytes(kf.read(8), "little")
+                seen += 1
+                hits += (f >> 22) & 1
+            out.append(round(hits / seen, 2) if seen else None)
+    return out
+
+
 def measure_h2d_peak(A: np.ndarray):
     """Pinned host -> HBM copy rates (cudaMemcpyAsync via torch, one copy stream):
     burst = best of 3 copies of the first 4 GiB block; sustained = every row
@@ -1541,6 +1573,8 @@ def main():
     clocks_e.start()
     sec_e, wall_e, reps_e, res_host = time_steps(plan_host, A, e2e_steps, args.warmup, outs=outs)
     clk_e = clocks_e.stop()
+    _, lb, lg = plan_host.copy_log()
+    nb_gram = reps_e[-1]["n_blocks"]
     rate_e, sec_e = whole_job_rate(sec_e, bytes_per_step * e2e_steps, dist, "cuda")
     e2e_step = sec_e / e2e_steps
     h2d_b = reps_e[-1]["h2d_bytes"]
@@ -1563,7 +1597,10 @@ def main():
                    if reps_e[-1]["h2d_copy_ms"] else None,
                    "copy_min_GBps": round(reps_e[-1]["h2d_copy_min_gbps"], 1),
                    "copy_max_GBps": round(reps_e[-1]["h2d_copy_max_gbps"], 1),
-                   "host_A_pages": thp_A},
+                   "host_A_pages": thp_A,
+                   "gram_pass_block_GBps": [round(float(x), 1) for x in lg[:nb_gram]],
+                   "u_pass_block_GBps": [round(float(x), 1) for x in lg[nb_gram:]],
+                   "block_huge_page_frac": thp_by_block(A, args.e2e_block_rows * N_COLS * 4)},
            "gram_kernels": {"syrk_ms_per_step": round(reps_e[-1]["gram_kernel_ms"], 2),
                             "launches_per_step": reps_e[-1]["gram_kernel_launches"],
                             "syrk_tflops": round(m * N_COLS * (N_COLS + 1) / (reps_e[-1]["gram_kernel_ms"] / 1e3)

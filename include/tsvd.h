@@ -254,6 +254,17 @@ TSVD_API tsvd_status tsvd_factor(tsvd_plan_t plan, const tsvd_matrix *A, void *w
                         size_t workspace_bytes, void *stream, float *U, double *sigma,
                         float *V, tsvd_report *report);
 
+/* The host -> device block copies of the plan's last tsvd_factor call, when
+ * it ran with time_kernels (none otherwise), in issue order: for copy i,
+ * first[i] is the block's first contraction index (a row of a tall dense or a
+ * CSR A, a column of a wide A), bytes[i] its size and gbps[i] its rate in
+ * 1e9 bytes per second between CUDA events on the copy stream.  The streamed
+ * passes' rates per block show which host ranges copy slowly.  Up to `cap`
+ * entries are written into each non-NULL array; *count gets the number of
+ * copies recorded.  TSVD_EINVAL for a NULL plan or count or a negative cap. */
+TSVD_API tsvd_status tsvd_plan_copy_log(tsvd_plan_t plan, int64_t *first, double *bytes, double *gbps,
+                                        int64_t cap, int64_t *count);
+
 /* Release a plan (NULL is accepted). */
 TSVD_API void tsvd_destroy(tsvd_plan_t plan);
 

@@ -167,6 +167,19 @@ class Plan:
         Uo = U.T if U is not None else None
         return TSVDResult(Uo, sigma, V.T, iters.tolist(), st, report)
 
+    def copy_log(self):
+        """(first, bytes, GB/s) of each timed block copy of the last factor()
+        call (time_kernels=True), from tsvd_plan_copy_log."""
+        cnt = C.c_int64()
+        B.check(self.lib.tsvd_plan_copy_log(self.handle, None, None, None, 0, C.byref(cnt)), "tsvd_plan_copy_log")
+        n = int(cnt.value)
+        first = np.zeros(n, dtype=np.int64)
+        nb = np.zeros(n, dtype=np.float64)
+        g = np.zeros(n, dtype=np.float64)
+        B.check(self.lib.tsvd_plan_copy_log(self.handle, first.ctypes.data, nb.ctypes.data, g.ctypes.data, n,
+                                            C.byref(cnt)), "tsvd_plan_copy_log")
+        return first, nb, g
+
     def close(self):
         if getattr(self, "handle", None):
             self.lib.tsvd_destroy(self.handle)

@@ -97,6 +97,7 @@ SIGNATURES = {
     "tsvd_csr_partition": (C.c_int, [_I64, _P, _I64, _P, C.POINTER(_I64), C.POINTER(_I64)]),
     "tsvd_host_alloc": (C.c_int, [C.POINTER(_P), _SZ]),
     "tsvd_host_free": (C.c_int, [_P]),
+    "tsvd_plan_copy_log": (C.c_int, [_P, _P, _P, _P, C.c_int64, C.POINTER(C.c_int64)]),
     "tsvd_server_options_init": (C.c_int, [C.POINTER(tsvd_server_options)]),
     "tsvd_server_create": (C.c_int, [C.POINTER(_P), C.POINTER(tsvd_server_options)]),
     "tsvd_server_submit": (C.c_int, [_P, _P, _I64, _I64, _I32, _D, _I32, C.c_uint64, _I32, _P, _P, _P, _P,

@@ -236,6 +236,11 @@ struct tsvd_plan_s {
   cudaEvent_t ev_t[4] = {nullptr, nullptr, nullptr, nullptr};
   std::vector<cudaEvent_t> ev_k;  // pairs around each timed Gram kernel
   std::vector<cudaEvent_t> ev_c;  // pairs around each timed block copy
+  struct CopyRec {
+    int64_t first;
+    double bytes, gbps;
+  };
+  std::vector<CopyRec> copy_log;  // the timed block copies of the last tsvd_factor call
 };
 
 namespace {
@@ -738,6 +743,7 @@ struct Run {
   int64_t chunk_seq = 0;  // ring position, continues across passes
   int64_t copies = 0;     // timed block copies recorded so far
   std::vector<double> copy_bytes;  // bytes of each timed copy
+  std::vector<int64_t> copy_first; // first contraction index (row, or column of a wide A) of each timed copy
   double kernel_ms = 0.0;          // timed operator kernels (CSR pair)
   int64_t kernel_launches = 0;
   bool chunked = false;            // this factorisation uses the column-chunked CSR operator
@@ -834,7 +840,10 @@ tsvd_status acquire_dense(Run &r, int64_t r0, int64_t rows, const float **out, i
   TSVD_CUDA(cudaEventRecord(p->ev_cjoin, p->copy_stream2));
   TSVD_CUDA(cudaStreamWaitEvent(p->copy_stream, p->ev_cjoin, 0));
   TSVD_TRY(copy_event(r, false));
-  if (p->opt.time_kernels) r.copy_bytes.push_back((double)height * width * 4);
+  if (p->opt.time_kernels) {
+    r.copy_bytes.push_back((double)height * width * 4);
+    r.copy_first.push_back(r0);
+  }
   r.h2d += (double)height * width * 4;
   const int ev = *slot >= 0 ? *slot : 0;
   TSVD_CUDA(cudaEventRecord(p->ev_ready[ev], p->copy_stream));
@@ -1201,7 +1210,10 @@ tsvd_status acquire_csr(Run &r, int64_t b, const std::vector<int64_t> &bnd_nnz, 
   }
   TSVD_TRY(copy_event(r, false));
   const double bytes = (double)(out->rows + 1) * 8 + (double)(e1 - e0) * 8;
-  if (p->opt.time_kernels) r.copy_bytes.push_back(bytes);
+  if (p->opt.time_kernels) {
+    r.copy_bytes.push_back(bytes);
+    r.copy_first.push_back(s0);
+  }
   r.h2d += bytes;
   TSVD_CUDA(cudaEventRecord(p->ev_ready[s], p->copy_stream));
   TSVD_CUDA(cudaStreamWaitEvent(r.cs, p->ev_ready[s], 0));
@@ -1556,7 +1568,10 @@ tsvd_status factor_dense_tiled(Run &r, float *U, double *sigma_out, float *V_out
           TSVD_CUDA(cudaStreamWaitEvent(p->copy_stream, p->ev_cjoin, 0));
           TSVD_TRY(copy_event(r, false));
           const double bytes = (double)rows * (nJ + (diag ? 0 : nI)) * 4;
-          if (p->opt.time_kernels) r.copy_bytes.push_back(bytes);
+          if (p->opt.time_kernels) {
+            r.copy_bytes.push_back(bytes);
+            r.copy_first.push_back(r0);
+          }
           r.h2d += bytes;
           TSVD_CUDA(cudaEventRecord(p->ev_ready[slot], p->copy_stream));
           TSVD_CUDA(cudaStreamWaitEvent(r.cs, p->ev_ready[slot], 0));
@@ -1873,7 +1888,33 @@ tsvd_status tsvd_factor(tsvd_plan_t plan, const tsvd_matrix *A, void *workspace,
       }
     }
   }
+  // the copy log of this call (time_kernels): block, bytes, rate
+  p->copy_log.clear();
+  if (p->opt.time_kernels && (st == TSVD_OK || st == TSVD_ENOCONV || st == TSVD_ERANK)) {
+    for (int64_t c = 0; c < r.copies && c < (int64_t)r.copy_bytes.size(); ++c) {
+      float t = 0.f;
+      if (cudaEventElapsedTime(&t, p->ev_c[2 * c], p->ev_c[2 * c + 1]) != cudaSuccess) {
+        cudaGetLastError();
+        break;
+      }
+      p->copy_log.push_back({c < (int64_t)r.copy_first.size() ? r.copy_first[(size_t)c] : -1,
+                             r.copy_bytes[(size_t)c], t > 0.f ? r.copy_bytes[(size_t)c] / ((double)t * 1e6) : 0.0});
+    }
+  }
   return st;
+}
+
+tsvd_status tsvd_plan_copy_log(tsvd_plan_t p, int64_t *first, double *bytes, double *gbps, int64_t cap,
+                               int64_t *count) {
+  if (!p || !count || cap < 0) return TSVD_EINVAL;
+  const int64_t nrec = (int64_t)p->copy_log.size();
+  *count = nrec;
+  for (int64_t i = 0; i < nrec && i < cap; ++i) {
+    if (first) first[i] = p->copy_log[(size_t)i].first;
+    if (bytes) bytes[i] = p->copy_log[(size_t)i].bytes;
+    if (gbps) gbps[i] = p->copy_log[(size_t)i].gbps;
+  }
+  return TSVD_OK;
 }
 
 // ---------------------------------------------------------------- step entry points

@@ -282,3 +282,20 @@ def test_binding_constants_match_the_header():
         assert must in named and hasattr(B, must), must
     assert checked >= 20, checked
 
+
+
+def test_copy_log_arguments():
+    """tsvd_plan_copy_log: a fresh plan has recorded no copies; NULL plan or
+    count and a negative capacity are TSVD_EINVAL."""
+    d, keep = _dense_desc(100, 20)
+    st, h, _ = _plan(d, 5, 1e-6)
+    assert st == B.TSVD_OK
+    lib = B.load()
+    try:
+        cnt = C.c_int64(-1)
+        assert lib.tsvd_plan_copy_log(h, None, None, None, 0, C.byref(cnt)) == B.TSVD_OK and cnt.value == 0
+        assert lib.tsvd_plan_copy_log(h, None, None, None, -1, C.byref(cnt)) == B.TSVD_EINVAL
+        assert lib.tsvd_plan_copy_log(h, None, None, None, 0, None) == B.TSVD_EINVAL
+        assert lib.tsvd_plan_copy_log(None, None, None, None, 0, C.byref(cnt)) == B.TSVD_EINVAL
+    finally:
+        lib.tsvd_destroy(h)
