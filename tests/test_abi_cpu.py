@@ -288,8 +288,9 @@ def test_copy_log_arguments():
     """tsvd_plan_copy_log: a fresh plan has recorded no copies; NULL plan or
     count and a negative capacity are TSVD_EINVAL."""
     d, keep = _dense_desc(100, 20)
-    st, h, _ = _plan(d, 5, 1e-6)
-    assert st == B.TSVD_OK
+    h = C.c_void_p()
+    ws = C.c_size_t()
+    assert B.tsvd_plan(C.byref(h), C.byref(d), 5, 1e-6, None, C.byref(ws)) == B.TSVD_OK
     lib = B.load()
     try:
         cnt = C.c_int64(-1)
