@@ -1176,7 +1176,7 @@ def leg_serve(args, n_req: int):
                 "status_counts": {B.STATUS_NAMES[int(c)]: int((status == c).sum()) for c in np.unique(status)},
                 "by_dim": by_dim}
 
-    server = Server(device_budget=args.serve_budget << 30, n_streams=4, max_wave=256)
+    server = Server(device_budget=args.serve_budget << 30, n_streams=args.serve_streams, max_wave=args.serve_max_wave)
     server.autotune(iters=30)
     table = {d: server.cluster_for(d) for d in (64, 128, 256, 512, 1024, 2048)}
     s0 = server.stats()
@@ -1230,6 +1230,8 @@ def leg_serve(args, n_req: int):
                                                                  "requests of the same mix, dense and sparse), FP32 "
                                                                  "Gram, pinned host A, one at a time"},
             "speedup_capacity_vs_per_request": round(capacity["solves_per_s"] / base_rate, 2) if base_rate else None,
+            "server": {"streams": args.serve_streams, "max_wave": args.serve_max_wave,
+                       "busy_s": round(s2.get("busy_s", 0.0) - s0.get("busy_s", 0.0), 3)},
             "waves": s2["waves"] - s0["waves"], "gpu_launches": launches,
             "peak_device_bytes": s2["peak_device_bytes"], "gen_seconds": round(gen_s, 1), "clocks": clk}
     for a in pool + [outU, outV, outS]:
@@ -1474,6 +1476,8 @@ def main():
                     help="skip the remaining legs once the run has taken this long")
     ap.add_argument("--serve-requests-leg", type=int, default=10_000, help="requests of the serving leg")
     ap.add_argument("--e2e-block-rows", type=int, default=BLOCK_ROWS, help="rows per streamed block (e2e)")
+    ap.add_argument("--serve-streams", type=int, default=4, help="serving: waves in flight (streams)")
+    ap.add_argument("--serve-max-wave", type=int, default=256, help="serving: requests per wave")
     args = ap.parse_args()
     if args.case:
         kernel_case(args)

@@ -542,10 +542,31 @@ TSVD_API int32_t tsvd_server_cluster_for(tsvd_server_t server, int64_t d);
  * cluster_cap, time `iters` iterations of one synthetic request alone and of
  * as many as fill the GPU, and keep the size with the highest iterations per
  * second over the whole GPU among those whose single-request time is within
- * 4x of the fastest.  Call with no requests in flight.  The table is used by
- * later submissions; tsvd_server_cluster_for reads it.
+ * 4x of the fastest.  Then pick the Gram step's tile shape per size: for
+ * d in {256, 512, 1024, 2048} it times the grouped tensor-core SYRK (128 x 256
+ * tiles, 3xTF32) and the grouped CUDA-core SYRK (64 x 64 tiles, FP32) on
+ * synthetic 8192 x d requests, enough to give both kernels work for every SM,
+ * and sets the tensor-core threshold (tsvd_server_tc_min_d) to the smallest d
+ * from which the tensor cores are faster at that size and every larger one
+ * (INT64_MAX when they never are).  Call with no requests in flight.  Both
+ * choices apply to later submissions; tsvd_server_cluster_for reads the first.
  */
 TSVD_API tsvd_status tsvd_server_autotune(tsvd_server_t server, int32_t iters);
+
+/*
+ * Gram dimension d = min(m, n) from which a dense request forms its Gram
+ * matrix on the tensor cores: a grouped, persistent tcgen05 SYRK over all
+ * such requests of a wave (3xTF32: each FP32 value split into two TF32 parts,
+ * three MMAs per product, FP32 accumulation in short TMEM segments carried
+ * into FP64 every 512 rows).  Each 128 x 256 tile spans its request's whole
+ * contraction range and writes its own entries without atomics, so a
+ * request's result is bitwise the same alone and in any wave.  Smaller
+ * requests use the CUDA-core SYRK.  Default 256 until tsvd_server_autotune
+ * measures it; the setter overrides it for later submissions (d >= 1;
+ * INT64_MAX: never).  The getter returns 0 for a NULL server.
+ */
+TSVD_API int64_t tsvd_server_tc_min_d(tsvd_server_t server);
+TSVD_API tsvd_status tsvd_server_set_tc_min_d(tsvd_server_t server, int64_t d);
 
 /* Stop the scheduler (requests still queued fail with TSVD_ECUDA) and free
  * the device arena.  NULL is accepted. */

@@ -273,6 +273,13 @@ class Server:
     def cluster_for(self, d: int) -> int:
         return int(self.lib.tsvd_server_cluster_for(self.handle, int(d)))
 
+    def tc_min_d(self) -> int:
+        """Gram dimension from which requests use the tensor-core SYRK."""
+        return int(self.lib.tsvd_server_tc_min_d(self.handle))
+
+    def set_tc_min_d(self, d: int):
+        B.check(self.lib.tsvd_server_set_tc_min_d(self.handle, int(d)), "tsvd_server_set_tc_min_d")
+
     def autotune(self, iters: int = 50):
         B.check(self.lib.tsvd_server_autotune(self.handle, int(iters)), "tsvd_server_autotune")
 

@@ -108,6 +108,8 @@ SIGNATURES = {
     "tsvd_server_get_stats": (C.c_int, [_P, C.POINTER(tsvd_server_stats)]),
     "tsvd_server_last_error": (C.c_char_p, [_P]),
     "tsvd_server_cluster_for": (_I32, [_P, _I64]),
+    "tsvd_server_tc_min_d": (C.c_int64, [_P]),
+    "tsvd_server_set_tc_min_d": (C.c_int, [_P, C.c_int64]),
     "tsvd_server_autotune": (C.c_int, [_P, _I32]),
     "tsvd_server_destroy": (None, [_P]),
 }

@@ -1,6 +1,7 @@
 // Shared host/device helpers of the tsvd library (internal header).
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <string>
@@ -174,6 +175,10 @@ __device__ __forceinline__ bool grid_barrier(unsigned *bar, int *err) {
 tsvd_status launch_gram_simt(const float *A, int64_t rows, int64_t n, int64_t ld, double *G,
                              cudaStream_t stream, cudaEvent_t ev0 = nullptr, cudaEvent_t ev1 = nullptr);
 size_t gram_tc_scratch_bytes(int64_t rows, int64_t n, int precision);
+// TMA map of a K-major tensor-core operand: n rows of Kp elements (TF32 in
+// 32-bit words, or BF16), 1024-byte aligned base; box = one 128-byte swizzle
+// row of K by 128 rows (64-byte aligned)
+tsvd_status tc_make_map(CUtensorMap *map, const void *base, int64_t n, int64_t Kp, int precision);
 // One task of the orthogonal batching (Sec. V-C): G[a][bs + b] += sum_r AJ[r][a] AI[r][b]
 // for a < nJ, b < nI (panel J against panel I, both rows x n_* with stride ld);
 // G is bs x 2 bs, row stride 2 bs.  Scratch: gram_tc_scratch_bytes(rows, 2 bs, precision).

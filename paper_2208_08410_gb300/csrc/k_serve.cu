@@ -203,6 +203,25 @@ __global__ void __launch_bounds__(kSrvPowerThreads, 2) srv_power_kernel(const Sr
   const int64_t R = srv_rows_per_cta(d, C);  // a multiple of 4, so every CTA's row range starts 16-byte aligned
   const int64_t r0 = min(d, (int64_t)rank * R), r1 = min(d, r0 + R);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = kSrvPowerThreads / 32;
+  if (q.gram_err && *reinterpret_cast<const volatile int32_t *>(q.gram_err) != 0) {
+    // the tensor-core SYRK that formed this request's G gave up on a bounded wait:
+    // no results; every triplet reports the timeout (every CTA reads the same word,
+    // written by an earlier launch, so the whole cluster takes this branch)
+    if (rank == 0) {
+      for (int l = threadIdx.x; l < k; l += kSrvPowerThreads) {
+        q.oS[l] = 0.0;
+        q.oInfo[4 * l] = 0;
+        q.oInfo[4 * l + 1] = 0;
+        q.oInfo[4 * l + 2] = 1;
+        q.oInfo[4 * l + 3] = 0;
+      }
+    }
+    __threadfence_system();
+    cluster_sync_all();
+    if (rank == 0 && threadIdx.x == 0)
+      asm volatile("st.release.sys.global.u32 [%0], %1;" ::"l"(q.flag), "r"(q.ticket) : "memory");
+    return;
+  }
   const int64_t dp = pad4(d);
   PowerSmem sm;
   sm.vb[0] = reinterpret_cast<float *>(srv_smem);

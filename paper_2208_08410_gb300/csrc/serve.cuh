@@ -51,6 +51,27 @@ struct SrvReq {
   int32_t no_other;     // 1: skip the other factor (oU when m >= n); the power vectors, sigma and info are written
   const double *x_start;  // d x k column-major start draws used as x_l, or null (Philox draws of key0/key1);
                           // may alias V64: column l is read before the triplet's vector overwrites it
+  const int32_t *gram_err;  // status word of the tensor-core SYRK that formed G (nonzero: a bounded wait
+                            // gave up, G is not valid), or null for the CUDA-core SYRK
+};
+
+// One request of the grouped tensor-core SYRK (3xTF32): its operand At (d rows
+// of Kp contraction indices, K-major, TF32 hi and lo parts) and its Gram
+// matrix.  The SYRK stores each tile's entries (gi, gj), gj <= gi, at
+// G64[gj d + gi]; the finish pass mirrors them and writes the FP32 copy.
+struct SrvTcReq {
+  int32_t req;       // index of the request in the wave's SrvReq array
+  int32_t pad;
+  int64_t d, K, Kp;  // Gram dimension, contraction length, K padded to a stage (32)
+  float *hi, *lo;    // d x Kp each, 1024-byte aligned
+  double *G64;
+  float *G32;
+};
+
+// Work unit of the grouped tensor-core SYRK: one 128 x 256 tile (bi, bj),
+// bj * 256 <= bi * 128 + 127, over the request's whole contraction range.
+struct SrvTcUnit {
+  int32_t tc, bi, bj, pad;  // tc: index into the SrvTcReq array
 };
 
 // Work item of the grouped SYRK: request, tile row, tile column (ti >= tj).
@@ -87,6 +108,21 @@ inline bool srv_req_complete(const SrvReq &q) {
 size_t srv_power_smem(int64_t d, int cluster, int resident);
 
 tsvd_status launch_srv_syrk(const SrvReq *reqs, const SrvTile *tiles, int n_tiles, cudaStream_t stream);
+
+// Grouped tensor-core SYRK of the requests in `tcs` (device arrays): prep
+// (round and split each A into its K-major hi / lo operand), the SYRK over
+// `units` (maps: 2 per request, hi then lo, 64-byte aligned, device memory),
+// then the finish pass (mirror, FP32 copy).  prep_start and fin_start are the
+// n_tc + 1 prefix sums of each request's prep strips and finish tiles
+// (srv_tc_prep_strips, srv_tc_finish_tiles).  err: the wave's status word,
+// zeroed here.
+constexpr int kSrvTcTM = 128, kSrvTcTN = 256, kSrvTcKStage = 32;
+int64_t srv_tc_prep_strips(int64_t d, int64_t Kp);
+int64_t srv_tc_finish_tiles(int64_t d);
+int64_t srv_tc_tiles(int64_t d);  // 128 x 256 tiles touching the lower triangle
+tsvd_status launch_srv_syrk_tc(const SrvReq *reqs, const SrvTcReq *tcs, int n_tc, const int64_t *prep_start,
+                               int64_t n_prep, const int64_t *fin_start, int64_t n_fin, const CUtensorMap *maps,
+                               const SrvTcUnit *units, int n_units, int32_t *err, cudaStream_t stream);
 // All requests of one launch share the cluster size; `smem` covers the largest.
 tsvd_status launch_srv_power(const SrvReq *reqs, int n_reqs, int cluster, size_t smem, cudaStream_t stream);
 

@@ -17,6 +17,8 @@
 // wave's event only releases its descriptors and its stream.  Waves on
 // different streams overlap on the device, so requests that arrive while
 // others run are admitted as memory frees up and start without waiting.
+#include <cuda.h>
+
 #include <algorithm>
 #include <atomic>
 #include <chrono>
@@ -141,6 +143,10 @@ struct Request {
   SrvReq dq{};
   bool done = false;
   tsvd_request_info rec{};
+  // Gram on the tensor cores (grouped 3xTF32 SYRK): the K-major operand pair in the device region
+  bool tc = false;
+  int64_t Kp = 0;
+  float *At_hi = nullptr, *At_lo = nullptr;
 };
 using ReqPtr = std::shared_ptr<Request>;
 
@@ -148,11 +154,16 @@ using ReqPtr = std::shared_ptr<Request>;
 size_t staging_bytes(int64_t m, int64_t n, int64_t k) {
   return al(k * 16) + al(k * 8) + al(m * k * 4) + al(n * k * 4);
 }
-// device region of one request: A, G64, G32, V64, sig2, info, vout, forced iteration counts, results
-size_t request_bytes(int64_t m, int64_t n, int64_t k) {
+// contraction length of a request padded to a stage of the tensor-core SYRK
+int64_t tc_kp(int64_t m, int64_t n) { return round_up(std::max(m, n), (int64_t)kSrvTcKStage); }
+
+// device region of one request: A, G64, G32, V64, sig2, info, vout, forced iteration counts,
+// the tensor-core operand pair (tc), results
+size_t request_bytes(int64_t m, int64_t n, int64_t k, bool tc = false) {
   const int64_t d = std::min(m, n);
+  const size_t op = tc ? 2 * al((size_t)d * tc_kp(m, n) * 4) : 0;
   return al(m * n * 4) + al(d * d * 8) + al(d * d * 4) + al(d * k * 8) + al(k * 8) + al(k * 16) + al(d * k * 4) +
-         al(k * 4) + staging_bytes(m, n, k);
+         al(k * 4) + op + staging_bytes(m, n, k);
 }
 
 void carve(Request &r, unsigned char *p) {
@@ -175,6 +186,13 @@ void carve(Request &r, unsigned char *p) {
   p += al(d * k * 4);
   q.iters_override = r.iters.empty() ? nullptr : reinterpret_cast<const int32_t *>(p);
   p += al(k * 4);
+  if (r.tc) {
+    r.Kp = tc_kp(m, n);
+    r.At_hi = reinterpret_cast<float *>(p);
+    p += al((size_t)d * r.Kp * 4);
+    r.At_lo = reinterpret_cast<float *>(p);
+    p += al((size_t)d * r.Kp * 4);
+  }
   unsigned char *o = p;
   r.out_off = (size_t)(o - reinterpret_cast<unsigned char *>(const_cast<float *>(q.A)));
   q.oInfo = reinterpret_cast<int32_t *>(o);
@@ -241,6 +259,9 @@ struct tsvd_server_s {
   tsvd_server_stats stats{};
   std::string err;
   int32_t cluster_table[6] = {1, 2, 4, 8, 8, 8};     // d <= 64, 128, 256, 512, 1024, 2048
+  // requests with d >= tc_min_d form their Gram matrix on the tensor cores (128 x 256 tiles,
+  // 3xTF32), the others on the CUDA cores (64 x 64 tiles, FP32); set by the autotuner
+  std::atomic<int64_t> tc_min_d{256};
   double busy_since = -1.0;
 
   double now() const {
@@ -271,6 +292,82 @@ size_t power_smem_budget() {
 }
 
 
+// The tensor-core part of a wave: for every request with the tc flag, its
+// operand descriptor, prep strips, finish tiles and SYRK units (longest
+// contraction first, so the tail of the persistent launch is short) and its two
+// tensor maps; laid out in one block of `bytes` (offsets from the block's start).
+struct TcWave {
+  std::vector<SrvTcReq> tcs;
+  std::vector<int64_t> prep_start{0}, fin_start{0};
+  std::vector<SrvTcUnit> units;
+  std::vector<CUtensorMap> maps;
+  size_t o_ps = 0, o_fs = 0, o_units = 0, o_maps = 0, bytes = 0;
+};
+
+tsvd_status build_tc_wave(const std::vector<ReqPtr> &rs, TcWave *w) {
+  std::vector<int64_t> unit_cost;
+  for (size_t i = 0; i < rs.size(); ++i) {
+    const Request &r = *rs[i];
+    if (!r.tc) continue;
+    SrvTcReq c{};
+    c.req = (int32_t)i;
+    c.d = std::min(r.m, r.n);
+    c.K = std::max(r.m, r.n);
+    c.Kp = r.Kp;
+    c.hi = r.At_hi;
+    c.lo = r.At_lo;
+    c.G64 = r.dq.G64;
+    c.G32 = r.dq.G32;
+    const int32_t t = (int32_t)w->tcs.size();
+    const int64_t nb = ceil_div(c.d, (int64_t)kSrvTcTM);
+    for (int64_t bi = 0; bi < nb; ++bi)
+      for (int64_t bj = 0; bj <= bi / 2; ++bj) {  // 256-row block bj with bj 256 <= bi 128 + 127
+        w->units.push_back({t, (int32_t)bi, (int32_t)bj, 0});
+        unit_cost.push_back(c.Kp);
+      }
+    w->prep_start.push_back(w->prep_start.back() + srv_tc_prep_strips(c.d, c.Kp));
+    w->fin_start.push_back(w->fin_start.back() + srv_tc_finish_tiles(c.d));
+    w->tcs.push_back(c);
+  }
+  std::vector<size_t> idx(w->units.size());
+  for (size_t i = 0; i < idx.size(); ++i) idx[i] = i;
+  std::stable_sort(idx.begin(), idx.end(), [&](size_t a, size_t b) { return unit_cost[a] > unit_cost[b]; });
+  std::vector<SrvTcUnit> u2(w->units.size());
+  for (size_t i = 0; i < idx.size(); ++i) u2[i] = w->units[idx[i]];
+  w->units.swap(u2);
+  const size_t ntc = w->tcs.size();
+  w->maps.resize(2 * ntc);
+  for (size_t t = 0; t < ntc; ++t) {
+    TSVD_TRY(tc_make_map(&w->maps[2 * t], w->tcs[t].hi, w->tcs[t].d, w->tcs[t].Kp, TSVD_GRAM_TF32X3));
+    TSVD_TRY(tc_make_map(&w->maps[2 * t + 1], w->tcs[t].lo, w->tcs[t].d, w->tcs[t].Kp, TSVD_GRAM_TF32X3));
+  }
+  w->o_ps = al(ntc * sizeof(SrvTcReq));
+  w->o_fs = w->o_ps + al((ntc + 1) * 8);
+  w->o_units = w->o_fs + al((ntc + 1) * 8);
+  w->o_maps = w->o_units + al(w->units.size() * sizeof(SrvTcUnit));  // 256-byte aligned (maps need 64)
+  w->bytes = w->o_maps + al(2 * ntc * sizeof(CUtensorMap));
+  return TSVD_OK;
+}
+
+void stage_tc_wave(const TcWave &w, unsigned char *p) {
+  const size_t ntc = w.tcs.size();
+  if (!ntc) return;
+  std::memcpy(p, w.tcs.data(), ntc * sizeof(SrvTcReq));
+  std::memcpy(p + w.o_ps, w.prep_start.data(), (ntc + 1) * 8);
+  std::memcpy(p + w.o_fs, w.fin_start.data(), (ntc + 1) * 8);
+  std::memcpy(p + w.o_units, w.units.data(), w.units.size() * sizeof(SrvTcUnit));
+  std::memcpy(p + w.o_maps, w.maps.data(), 2 * ntc * sizeof(CUtensorMap));
+}
+
+// `dev`: the device copy of the block stage_tc_wave filled
+tsvd_status launch_tc_wave(const TcWave &w, const SrvReq *dreq, unsigned char *dev, int32_t *derr, cudaStream_t st) {
+  return launch_srv_syrk_tc(dreq, reinterpret_cast<const SrvTcReq *>(dev), (int)w.tcs.size(),
+                            reinterpret_cast<const int64_t *>(dev + w.o_ps), w.prep_start.back(),
+                            reinterpret_cast<const int64_t *>(dev + w.o_fs), w.fin_start.back(),
+                            reinterpret_cast<const CUtensorMap *>(dev + w.o_maps),
+                            reinterpret_cast<const SrvTcUnit *>(dev + w.o_units), (int)w.units.size(), derr, st);
+}
+
 // Build and enqueue one wave on slot `s` (scheduler thread, lock not held).
 tsvd_status launch_wave(tsvd_server_s *sv, Slot &s) {
   std::vector<ReqPtr> &rs = s.reqs;
@@ -289,6 +386,7 @@ tsvd_status launch_wave(tsvd_server_s *sv, Slot &s) {
   std::vector<int64_t> tile_cost;
   for (size_t i = 0; i < rs.size(); ++i) {
     const Request &r = *rs[i];
+    if (r.tc) continue;  // its Gram matrix comes from the tensor-core SYRK
     const int64_t d = std::min(r.m, r.n), K = std::max(r.m, r.n);
     const int T = (int)ceil_div(d, kSrvTile);
     for (int ti = 0; ti < T; ++ti)
@@ -305,8 +403,12 @@ tsvd_status launch_wave(tsvd_server_s *sv, Slot &s) {
     for (size_t i = 0; i < idx.size(); ++i) t2[i] = tiles[idx[i]];
     tiles.swap(t2);
   }
+  TcWave tw;
+  TSVD_TRY(build_tc_wave(rs, &tw));
+  const size_t ntc = tw.tcs.size();
   const size_t b_req = al(rs.size() * sizeof(SrvReq)), b_tiles = al(tiles.size() * sizeof(SrvTile));
-  const size_t need = b_req + b_tiles;
+  const size_t o_tc = b_req + b_tiles, o_err = o_tc + tw.bytes;
+  const size_t need = o_err + al(4);
   if (need > s.stage_cap) {
     if (s.stage) cudaFreeHost(s.stage);
     s.stage = nullptr;
@@ -323,15 +425,18 @@ tsvd_status launch_wave(tsvd_server_s *sv, Slot &s) {
   }
   s.dev_bytes = need;
   unsigned char *dev = sv->arena.base + s.dev_off;
+  int32_t *derr = reinterpret_cast<int32_t *>(dev + o_err);
   SrvReq *hreq = reinterpret_cast<SrvReq *>(s.stage);
   for (size_t i = 0; i < rs.size(); ++i) {
-    if (!srv_req_complete(rs[i]->dq)) {
+    rs[i]->dq.gram_err = rs[i]->tc ? derr : nullptr;
+    if (!srv_req_complete(rs[i]->dq) || (rs[i]->tc && (!rs[i]->At_hi || !rs[i]->At_lo))) {
       set_error_text("server: request descriptor with an unset pointer");
       return TSVD_EINVAL;
     }
     hreq[i] = rs[i]->dq;
   }
   std::memcpy(s.stage + b_req, tiles.data(), tiles.size() * sizeof(SrvTile));
+  stage_tc_wave(tw, s.stage + o_tc);
   cudaStream_t st = s.stream;
   for (auto &r : rs) {
     TSVD_CUDA(cudaMemcpyAsync(const_cast<float *>(r->dq.A), r->A, (size_t)r->m * r->n * 4, cudaMemcpyHostToDevice, st));
@@ -341,7 +446,8 @@ tsvd_status launch_wave(tsvd_server_s *sv, Slot &s) {
   }
   TSVD_CUDA(cudaMemcpyAsync(dev, s.stage, need, cudaMemcpyHostToDevice, st));
   const SrvReq *dreq = reinterpret_cast<const SrvReq *>(dev);
-  // 1. grouped SYRK
+  // 1. grouped SYRK: the tensor-core requests (prep, SYRK, finish), then the CUDA-core ones
+  TSVD_TRY(launch_tc_wave(tw, dreq, dev + o_tc, derr, st));
   TSVD_TRY(launch_srv_syrk(dreq, reinterpret_cast<const SrvTile *>(dev + b_req), (int)tiles.size(), st));
   // 2. grouped power + other factor, one launch per (cluster, residency) run of the sorted requests
   for (size_t i = 0; i < rs.size();) {
@@ -627,6 +733,88 @@ tsvd_status time_power(tsvd_server_s *sv, int64_t d, int c, int nreq, int iters,
   return ls;
 }
 
+// Time the grouped Gram step on `nreq` synthetic tall requests of K x d, on the
+// tensor cores (tc) or on the CUDA cores: a warm-up launch sequence, then one
+// timed.  Milliseconds of the timed one.
+tsvd_status time_syrk(tsvd_server_s *sv, int64_t d, int64_t K, int nreq, bool tc, cudaStream_t st, cudaEvent_t e0,
+                      cudaEvent_t e1, double *ms_out) {
+  const int k = 2;
+  const size_t per = al(request_bytes(K, d, k, tc));
+  size_t off = 0;
+  {
+    std::lock_guard<std::mutex> lk(sv->mu);
+    if (!sv->arena.alloc(per * nreq, &off)) return TSVD_EBUDGET;
+  }
+  unsigned char *base = sv->arena.base + off;
+  std::vector<ReqPtr> rs(nreq);
+  tsvd_status ls = TSVD_OK;
+  for (int i = 0; i < nreq && ls == TSVD_OK; ++i) {
+    rs[i] = std::make_shared<Request>();
+    Request &r = *rs[i];
+    r.m = K;
+    r.n = d;
+    r.k = k;
+    r.eps = 0.5;
+    r.max_iter = 1;
+    r.tc = tc;
+    carve(r, base + per * i);
+    fill_uniform_kernel<<<64, 256, 0, st>>>(const_cast<float *>(r.dq.A), K * d, (uint32_t)i);
+    if (cudaGetLastError() != cudaSuccess) ls = TSVD_ECUDA;
+  }
+  std::vector<SrvTile> tiles;
+  TcWave tw;
+  if (ls == TSVD_OK && tc) ls = build_tc_wave(rs, &tw);
+  if (!tc) {
+    const int T = (int)ceil_div(d, kSrvTile);
+    for (int i = 0; i < nreq; ++i)
+      for (int ti = 0; ti < T; ++ti)
+        for (int tj = 0; tj <= ti; ++tj) tiles.push_back({i, ti, tj, 0});
+  }
+  const size_t o_tiles = al(nreq * sizeof(SrvReq)), o_tc = o_tiles + al(tiles.size() * sizeof(SrvTile));
+  const size_t o_err = o_tc + tw.bytes, need = o_err + al(4);
+  size_t doff = 0;
+  bool have_d = false;
+  if (ls == TSVD_OK) {
+    std::lock_guard<std::mutex> lk(sv->mu);
+    have_d = sv->arena.alloc(need, &doff);
+    if (!have_d) ls = TSVD_EBUDGET;
+  }
+  std::vector<unsigned char> stage(need, 0);
+  unsigned char *dev = have_d ? sv->arena.base + doff : nullptr;
+  if (ls == TSVD_OK) {
+    for (int i = 0; i < nreq; ++i) {
+      rs[i]->dq.gram_err = tc ? reinterpret_cast<int32_t *>(dev + o_err) : nullptr;
+      reinterpret_cast<SrvReq *>(stage.data())[i] = rs[i]->dq;
+    }
+    std::memcpy(stage.data() + o_tiles, tiles.data(), tiles.size() * sizeof(SrvTile));
+    stage_tc_wave(tw, stage.data() + o_tc);
+    if (cudaMemcpyAsync(dev, stage.data(), need, cudaMemcpyHostToDevice, st) != cudaSuccess) ls = TSVD_ECUDA;
+  }
+  auto run = [&]() -> tsvd_status {
+    const SrvReq *dreq = reinterpret_cast<const SrvReq *>(dev);
+    if (tc) return launch_tc_wave(tw, dreq, dev + o_tc, reinterpret_cast<int32_t *>(dev + o_err), st);
+    return launch_srv_syrk(dreq, reinterpret_cast<const SrvTile *>(dev + o_tiles), (int)tiles.size(), st);
+  };
+  if (ls == TSVD_OK) ls = run();  // warm-up
+  if (ls == TSVD_OK && cudaEventRecord(e0, st) != cudaSuccess) ls = TSVD_ECUDA;
+  if (ls == TSVD_OK) ls = run();
+  if (ls == TSVD_OK && cudaEventRecord(e1, st) != cudaSuccess) ls = TSVD_ECUDA;
+  float ms = 0.f;
+  if (ls == TSVD_OK && (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
+    ls = TSVD_ECUDA;
+  cudaStreamSynchronize(st);  // the copy of `stage` and every launch are done before it is freed
+  int32_t herr = 0;
+  if (ls == TSVD_OK && tc && cudaMemcpy(&herr, dev + o_err, 4, cudaMemcpyDeviceToHost) == cudaSuccess && herr)
+    ls = TSVD_ETIMEDOUT;
+  {
+    std::lock_guard<std::mutex> lk(sv->mu);
+    sv->arena.release(off, per * nreq);
+    if (have_d) sv->arena.release(doff, need);
+  }
+  *ms_out = ms;
+  return ls;
+}
+
 // A sparse request runs through the plan API on a stream of its worker: the
 // workspace comes from the server's device arena (first fit; the worker waits
 // while the arena is full), the outputs go straight into the caller's
@@ -812,7 +1000,8 @@ tsvd_status tsvd_server_submit(tsvd_server_t sv, const float *A, int64_t m, int6
   r->sigma = sigma;
   r->V = V;
   if (iters_override) r->iters.assign(iters_override, iters_override + k);
-  r->bytes = request_bytes(m, n, k);
+  r->tc = d >= sv->tc_min_d.load();
+  r->bytes = request_bytes(m, n, k, r->tc);
   r->sbytes = staging_bytes(m, n, k);
   if (al(r->bytes) > sv->arena.size || al(r->sbytes) > sv->staging.size) return TSVD_EBUDGET;
   {
@@ -918,6 +1107,14 @@ tsvd_status tsvd_server_get_stats(tsvd_server_t sv, tsvd_server_stats *stats) {
 
 const char *tsvd_server_last_error(tsvd_server_t sv) { return sv ? sv->err.c_str() : ""; }
 
+int64_t tsvd_server_tc_min_d(tsvd_server_t sv) { return sv ? sv->tc_min_d.load() : 0; }
+
+tsvd_status tsvd_server_set_tc_min_d(tsvd_server_t sv, int64_t d) {
+  if (!sv || d < 1) return TSVD_EINVAL;
+  sv->tc_min_d.store(d);
+  return TSVD_OK;
+}
+
 int32_t tsvd_server_cluster_for(tsvd_server_t sv, int64_t d) {
   if (!sv || d <= 0) return 0;
   std::lock_guard<std::mutex> lk(sv->mu);
@@ -972,6 +1169,31 @@ tsvd_status tsvd_server_autotune(tsvd_server_t sv, int32_t iters) {
     }
     std::lock_guard<std::mutex> lk(sv->mu);
     sv->cluster_table[b] = best_c;
+  }
+  // the Gram step's tile shape per size: 128 x 256 tensor-core tiles (3xTF32) against
+  // 64 x 64 CUDA-core tiles (FP32), on as many K = 8192 requests as give both kernels
+  // work for every SM (within half of the arena); tensor cores from the smallest d at
+  // which they are faster there and at every larger size
+  if (result == TSVD_OK && di.cc_major == 10) {
+    const int64_t tdims[4] = {256, 512, 1024, 2048};
+    bool tc_wins[4] = {false, false, false, false};
+    const int64_t K = 8192;
+    for (int b = 0; b < 4 && result == TSVD_OK; ++b) {
+      const int64_t d = tdims[b];
+      const size_t per = al(request_bytes(K, d, 2, true));
+      const int64_t want = std::max<int64_t>(1, ceil_div(2 * (int64_t)di.sms, srv_tc_tiles(d)));
+      const int nreq = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)(sv->arena.size / 2 / per) / 2));
+      double ms_tc = 0.0, ms_cc = 0.0;
+      result = time_syrk(sv, d, K, nreq, true, st, e0, e1, &ms_tc);
+      if (result == TSVD_OK) result = time_syrk(sv, d, K, nreq, false, st, e0, e1, &ms_cc);
+      if (result == TSVD_OK) tc_wins[b] = ms_tc < ms_cc;
+      if (result == TSVD_EBUDGET) result = TSVD_OK;  // a budget too small for the size: keep the default
+    }
+    if (result == TSVD_OK) {
+      int64_t from = INT64_MAX;
+      for (int b = 3; b >= 0 && tc_wins[b]; --b) from = tdims[b];
+      sv->tc_min_d.store(from);
+    }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);

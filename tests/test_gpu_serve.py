@@ -69,10 +69,17 @@ CASES = [
 ]
 
 
-def test_server_mixed_wave_matches_oracle():
+@pytest.mark.parametrize("tc_min_d", [256, 64, 1 << 62])
+def test_server_mixed_wave_matches_oracle(tc_min_d):
+    """A wave of tall and wide requests of many sizes follows the oracle's
+    trajectory.  The tensor-core threshold puts the Gram step of requests with
+    d >= 256 (the default), of every request with d >= 64, or of none on the
+    grouped tcgen05 SYRK; the others take the CUDA-core SYRK."""
     B.load()
     pool = Pool()
     sv = Server(device_budget=4 << 30, n_streams=2)
+    sv.set_tc_min_d(tc_min_d)
+    assert sv.tc_min_d() == tc_min_d
     try:
         eps = 1e-10
         jobs = []
@@ -112,6 +119,7 @@ def test_server_result_alone_equals_result_in_the_mix():
     alone = _outputs(pool, m, n, k)
     sv = Server(device_budget=2 << 30)
     try:
+        assert sv.tc_min_d() <= n  # this request's Gram step runs on the tensor-core SYRK
         st, _ = sv.wait(sv.submit(A, k, 1e-9, *alone, seed=3), 60.0)
         assert st == B.TSVD_OK
     finally:
@@ -167,6 +175,8 @@ def test_server_autotune_table():
         for d in (64, 128, 256, 512, 1024, 2048):
             c = sv.cluster_for(d)
             assert c in (1, 2, 4, 8)
+        # the Gram step's tile shape: tensor cores from one of the timed sizes on, or never
+        assert sv.tc_min_d() in (256, 512, 1024, 2048, (1 << 63) - 1)
     finally:
         sv.close()
 
