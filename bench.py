@@ -394,6 +394,42 @@ def cpu_baseline(m: int, A: np.ndarray, V_gpu: np.ndarray, sig_gpu: np.ndarray, 
                       f"applications ({t_pow:.1f} s); est. t-SVD {total:.0f} s"}
 
 
+def parity_full_oracle(A: np.ndarray, res, seed: int = 0):
+    """The oracle's trajectory at the headline size: FP64 Gram of the stored
+    values of all of A (row blocks of 65,536), O-1 from the start draws of the
+    GPU run (the built-in Philox stream of `seed`, which the oracle's generator
+    reproduces bit for bit) with the GPU's iteration counts, and U = A V
+    Sigma^-1; sigma on every triplet, u_l and v_l angles on the gapped ones."""
+    from oracle import tsvd_ref as ref
+    m = A.shape[0]
+    t0 = time.time()
+    G = ref.gram_row_blocks(A, 65_536)
+    t_gram = time.time() - t0
+    it = [int(i) for i in res.iters]
+    sig_o, V_o, it_o, st_o = ref.right_vectors(G, K, EPS, seed=seed, iters_override=it)
+    lam = np.linalg.eigvalsh(G)[::-1]
+    del G
+    gapped = ref.gapped_indices(lam, K)
+    V = res.V.cpu().numpy().astype(np.float64)
+    sig = np.asarray(res.sigma.cpu(), dtype=np.float64)
+    Ug = res.U  # (m, k) on the device
+    ang_u = {}
+    U_o_cols = np.zeros((m, len(gapped)))
+    for r0 in range(0, m, 65_536):
+        U_o_cols[r0:r0 + 65_536] = (np.asarray(A[r0:r0 + 65_536], dtype=np.float64) @ V_o[:, gapped]) / sig_o[gapped]
+    for j, l in enumerate(gapped):
+        ang_u[int(l)] = float("%.3g" % ref.vector_angle(Ug[:, l].cpu().numpy().astype(np.float64), U_o_cols[:, j]))
+    ang_v = {int(l): float("%.3g" % ref.vector_angle(V[:, l], V_o[:, l])) for l in gapped}
+    err = float(np.max(np.abs(sig - sig_o) / sig_o))
+    return {"oracle": "O-1 on the FP64 Gram of all of A, start draws of the GPU run (Philox seed), GPU counts forced",
+            "sigma_rel_err_vs_oracle": float("%.3g" % err), "gapped": [int(l) for l in gapped],
+            "v_angle_max_gapped": max(ang_v.values()) if ang_v else None,
+            "u_angle_max_gapped": max(ang_u.values()) if ang_u else None, "v_angles": ang_v, "u_angles": ang_u,
+            "pass": bool(err <= 1e-5 and gapped and all(a <= 1e-4 for a in list(ang_v.values()) + list(ang_u.values()))),
+            "oracle_gram_seconds": round(t_gram, 1), "oracle_seconds": round(time.time() - t0, 1),
+            "oracle_cores": len(os.sched_getaffinity(0))}
+
+
 def parity_full_size(A: np.ndarray, dA, res, prec: int):
     """Checks at full size on outputs the oracle computes one by one."""
     import torch
@@ -1176,9 +1212,12 @@ def leg_serve(args, n_req: int):
                 "status_counts": {B.STATUS_NAMES[int(c)]: int((status == c).sum()) for c in np.unique(status)},
                 "by_dim": by_dim}
 
-    server = Server(device_budget=args.serve_budget << 30, n_streams=args.serve_streams, max_wave=args.serve_max_wave)
+    server = Server(device_budget=args.serve_budget << 30, n_streams=args.serve_streams, max_wave=args.serve_max_wave,
+                    heavy_dim=args.serve_heavy_dim, heavy_streams=args.serve_heavy_streams)
     server.autotune(iters=30)
     table = {d: server.cluster_for(d) for d in (64, 128, 256, 512, 1024, 2048)}
+    tc_from = server.tc_min_d()
+    syrk_times = server.autotune_syrk_times()
     s0 = server.stats()
     clocks = ClockSampler(0)
     clocks.start()
@@ -1225,12 +1264,15 @@ def leg_serve(args, n_req: int):
                               "(an FP32-accumulated Gram moves lambda_i by ~1e-7 lambda_0, i.e. sigma_i by "
                               "~5e-8 / (sigma_i/sigma_0)^2 relative; smaller sigma_i are reported, not graded)",
             "latency": timed, "capacity": capacity, "cluster_table": table,
+            "syrk_tensor_cores_from_d": tc_from if tc_from < (1 << 62) else None,
+            "syrk_autotune_ms_tensor_cuda_requests": syrk_times,
             "baseline_per_request": {"solves_per_s": round(base_rate, 1) if base_rate else None,
                                      "requests": n_tall, "path": "tsvd_plan/tsvd_factor per request (the first "
                                                                  "requests of the same mix, dense and sparse), FP32 "
                                                                  "Gram, pinned host A, one at a time"},
             "speedup_capacity_vs_per_request": round(capacity["solves_per_s"] / base_rate, 2) if base_rate else None,
             "server": {"streams": args.serve_streams, "max_wave": args.serve_max_wave,
+                       "heavy_dim": args.serve_heavy_dim or 1024, "heavy_streams": args.serve_heavy_streams or "auto",
                        "busy_s": round(s2.get("busy_s", 0.0) - s0.get("busy_s", 0.0), 3)},
             "waves": s2["waves"] - s0["waves"], "gpu_launches": launches,
             "peak_device_bytes": s2["peak_device_bytes"], "gen_seconds": round(gen_s, 1), "clocks": clk}
@@ -1476,8 +1518,12 @@ def main():
                     help="skip the remaining legs once the run has taken this long")
     ap.add_argument("--serve-requests-leg", type=int, default=10_000, help="requests of the serving leg")
     ap.add_argument("--e2e-block-rows", type=int, default=BLOCK_ROWS, help="rows per streamed block (e2e)")
+    ap.add_argument("--full-oracle", action="store_true",
+                    help="dense: the oracle's trajectory over all of A (FP64 Gram on the host, ~5 min on 16 cores)")
     ap.add_argument("--serve-streams", type=int, default=4, help="serving: waves in flight (streams)")
     ap.add_argument("--serve-max-wave", type=int, default=256, help="serving: requests per wave")
+    ap.add_argument("--serve-heavy-dim", type=int, default=0, help="serving: heavy lane above this d (0: 1024, -1: none)")
+    ap.add_argument("--serve-heavy-streams", type=int, default=0, help="serving: streams of the heavy lane (0: auto)")
     args = ap.parse_args()
     if args.case:
         kernel_case(args)
@@ -1619,6 +1665,9 @@ def main():
     parity = None
     if not args.no_parity and rank == 0:
         parity = parity_full_size(A, dA, res_dev, prec)
+    full_oracle = None
+    if args.full_oracle and rank == 0:
+        full_oracle = parity_full_oracle(A, res_dev, seed=0)
     cpu = None
     if not args.no_cpu and rank == 0 and world == 1:
         sig = np.asarray(res_dev.sigma.cpu().numpy())
@@ -1674,7 +1723,8 @@ def main():
                 "phases_ms": {"gram": round(reps[-1]["gram_ms"], 2), "power": round(reps[-1]["power_ms"], 2),
                               "left": round(reps[-1]["left_ms"], 2), "applications": reps[-1]["applications"]},
                 "iters": res_dev.iters, "sigma": [round(float(s), 8) for s in np.asarray(res_dev.sigma.cpu())],
-                "parity": parity, "gen_seconds": round(gen_s, 1), "tf32_cublas_peak": tf32_meas,
+                "parity": parity, "parity_oracle_full_size": full_oracle,
+                "gen_seconds": round(gen_s, 1), "tf32_cublas_peak": tf32_meas,
                 "run_seconds": round(time.time() - t_run, 1)}
         line.update(legs)
         print(json.dumps(line), flush=True)

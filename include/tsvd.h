@@ -449,7 +449,18 @@ typedef struct {
                              are copied into from its device output region
                              before tsvd_server_wait hands them to the
                              caller (0: 2 GiB) */
-  int32_t reserved[6];
+  int32_t heavy_dim;      /* requests with min(m, n) above this run in waves
+                             of their own ("heavy" lane): their power phase
+                             reads a large Gram matrix per application and
+                             can last long, and a wave's stream stays busy
+                             until its last request is done, so light waves
+                             are never held behind them (0: 1024; -1: one
+                             lane for all) */
+  int32_t heavy_streams;  /* streams that may run heavy waves (they also take
+                             light requests when no heavy one waits; the
+                             others take light requests only);
+                             0: max(1, n_streams / 4); < n_streams */
+  int32_t reserved[4];
 } tsvd_server_options;
 
 /* Per-request record (tsvd_server_wait / tsvd_server_poll). */
@@ -566,6 +577,12 @@ TSVD_API tsvd_status tsvd_server_autotune(tsvd_server_t server, int32_t iters);
  * INT64_MAX: never).  The getter returns 0 for a NULL server.
  */
 TSVD_API int64_t tsvd_server_tc_min_d(tsvd_server_t server);
+/* The autotuner's Gram-step timings behind that choice: for d = 256, 512,
+ * 1024, 2048 (4 entries each), milliseconds of the tensor-core and of the
+ * CUDA-core grouped SYRK over `requests` synthetic 8192 x d requests (zeros
+ * before tsvd_server_autotune or for a size the budget could not hold). */
+TSVD_API tsvd_status tsvd_server_autotune_syrk_times(tsvd_server_t server, int64_t *d, double *ms_tensor,
+                                                     double *ms_cuda, int32_t *requests);
 TSVD_API tsvd_status tsvd_server_set_tc_min_d(tsvd_server_t server, int64_t d);
 
 /* Stop the scheduler (requests still queued fail with TSVD_ECUDA) and free

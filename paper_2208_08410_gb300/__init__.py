@@ -210,7 +210,7 @@ class Server:
     tsvd_host_alloc, let the copies overlap other work)."""
 
     def __init__(self, device_budget: int = 8 << 30, max_inflight: int = 0, n_streams: int = 0,
-                 max_wave: int = 0, cluster_cap: int = 0):
+                 max_wave: int = 0, cluster_cap: int = 0, heavy_dim: int = 0, heavy_streams: int = 0):
         import torch
         torch.cuda.init()
         self.lib = B.load()
@@ -221,6 +221,8 @@ class Server:
         opt.n_streams = int(n_streams)
         opt.max_wave = int(max_wave)
         opt.cluster_cap = int(cluster_cap)
+        opt.heavy_dim = int(heavy_dim)
+        opt.heavy_streams = int(heavy_streams)
         h = C.c_void_p()
         B.check(self.lib.tsvd_server_create(C.byref(h), C.byref(opt)), "tsvd_server_create")
         self.handle = h
@@ -276,6 +278,16 @@ class Server:
     def tc_min_d(self) -> int:
         """Gram dimension from which requests use the tensor-core SYRK."""
         return int(self.lib.tsvd_server_tc_min_d(self.handle))
+
+    def autotune_syrk_times(self) -> dict:
+        """{d: (ms tensor cores, ms CUDA cores, requests)} of the last autotune."""
+        d = np.zeros(4, dtype=np.int64)
+        a = np.zeros(4)
+        b = np.zeros(4)
+        n = np.zeros(4, dtype=np.int32)
+        B.check(self.lib.tsvd_server_autotune_syrk_times(self.handle, d.ctypes.data, a.ctypes.data, b.ctypes.data,
+                                                          n.ctypes.data), "tsvd_server_autotune_syrk_times")
+        return {int(d[i]): (round(float(a[i]), 3), round(float(b[i]), 3), int(n[i])) for i in range(4)}
 
     def set_tc_min_d(self, d: int):
         B.check(self.lib.tsvd_server_set_tc_min_d(self.handle, int(d)), "tsvd_server_set_tc_min_d")

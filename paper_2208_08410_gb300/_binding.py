@@ -52,7 +52,7 @@ class tsvd_report(C.Structure):
 class tsvd_server_options(C.Structure):
     _fields_ = [("device_budget", C.c_size_t), ("max_inflight", C.c_int32), ("n_streams", C.c_int32),
                 ("max_wave", C.c_int32), ("cluster_cap", C.c_int32), ("host_staging", C.c_size_t),
-                ("reserved", C.c_int32 * 6)]
+                ("heavy_dim", C.c_int32), ("heavy_streams", C.c_int32), ("reserved", C.c_int32 * 4)]
 
 
 class tsvd_request_info(C.Structure):
@@ -110,6 +110,7 @@ SIGNATURES = {
     "tsvd_server_cluster_for": (_I32, [_P, _I64]),
     "tsvd_server_tc_min_d": (C.c_int64, [_P]),
     "tsvd_server_set_tc_min_d": (C.c_int, [_P, C.c_int64]),
+    "tsvd_server_autotune_syrk_times": (C.c_int, [_P, _P, _P, _P, _P]),
     "tsvd_server_autotune": (C.c_int, [_P, _I32]),
     "tsvd_server_destroy": (None, [_P]),
 }

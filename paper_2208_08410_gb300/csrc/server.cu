@@ -17,6 +17,10 @@
 // wave's event only releases its descriptors and its stream.  Waves on
 // different streams overlap on the device, so requests that arrive while
 // others run are admitted as memory frees up and start without waiting.
+// Requests with a large Gram dimension (above `heavy_dim`) form waves of their
+// own on the first `heavy_streams` streams: their power phase can last long,
+// and a stream stays busy until its wave's last request is done, so light
+// waves, which turn over quickly, never queue behind them.
 #include <cuda.h>
 
 #include <algorithm>
@@ -145,6 +149,7 @@ struct Request {
   tsvd_request_info rec{};
   // Gram on the tensor cores (grouped 3xTF32 SYRK): the K-major operand pair in the device region
   bool tc = false;
+  bool heavy = false;  // runs in the heavy lane
   int64_t Kp = 0;
   float *At_hi = nullptr, *At_lo = nullptr;
 };
@@ -244,7 +249,8 @@ struct tsvd_server_s {
   std::mutex mu;
   std::condition_variable cv_done, cv_work;
   std::deque<tsvd::ReqPtr> pending;                  // submitted, not admitted
-  std::deque<tsvd::ReqPtr> admitted;                 // in the arenas, not launched
+  std::deque<tsvd::ReqPtr> admitted;                 // in the arenas, not launched (light lane)
+  std::deque<tsvd::ReqPtr> admitted_heavy;           // the same, heavy lane (min(m, n) > heavy_dim)
   std::list<tsvd::ReqPtr> running;                   // launched, flag not seen yet
   std::list<tsvd::ReqPtr> copying;                   // flag seen, results on their way to the staging
   std::unordered_map<uint64_t, tsvd::ReqPtr> table;  // every request not yet waited for
@@ -262,6 +268,8 @@ struct tsvd_server_s {
   // requests with d >= tc_min_d form their Gram matrix on the tensor cores (128 x 256 tiles,
   // 3xTF32), the others on the CUDA cores (64 x 64 tiles, FP32); set by the autotuner
   std::atomic<int64_t> tc_min_d{256};
+  double syrk_ms_tc[4] = {0, 0, 0, 0}, syrk_ms_cc[4] = {0, 0, 0, 0};  // the autotuner's timings (d = 256 .. 2048)
+  int32_t syrk_nreq[4] = {0, 0, 0, 0};
   double busy_since = -1.0;
 
   double now() const {
@@ -604,15 +612,20 @@ void scheduler(tsvd_server_s *sv) {
       r->dq.ticket = (uint32_t)(r->id & 0x7fffffffu) | 0x80000000u;  // never 0, the flags' initial value
       r->rec.admit_s = sv->now();
       ++sv->inflight;
-      sv->admitted.push_back(r);
+      (r->heavy ? sv->admitted_heavy : sv->admitted).push_back(r);
       progressed = true;
     }
     // waves
-    for (auto &s : sv->slots) {
-      if (s.busy || sv->admitted.empty()) continue;
-      const size_t take = std::min(sv->admitted.size(), (size_t)sv->opt.max_wave);
-      s.reqs.assign(sv->admitted.begin(), sv->admitted.begin() + take);
-      sv->admitted.erase(sv->admitted.begin(), sv->admitted.begin() + take);
+    for (size_t si = 0; si < sv->slots.size(); ++si) {
+      Slot &s = sv->slots[si];
+      // the first heavy_streams streams take heavy requests first (light ones when none
+      // waits); the others light ones only, so a light wave never waits behind a heavy one
+      std::deque<ReqPtr> &q = ((int)si < sv->opt.heavy_streams && !sv->admitted_heavy.empty()) ? sv->admitted_heavy
+                                                                                               : sv->admitted;
+      if (s.busy || q.empty()) continue;
+      const size_t take = std::min(q.size(), (size_t)sv->opt.max_wave);
+      s.reqs.assign(q.begin(), q.begin() + take);
+      q.erase(q.begin(), q.begin() + take);
       s.busy = true;
       s.wave = sv->stats.waves++;
       const double t = sv->now();
@@ -936,6 +949,9 @@ tsvd_status tsvd_server_create(tsvd_server_t *out, const tsvd_server_options *op
   if (opt.max_inflight < 1 || opt.n_streams < 1 || opt.n_streams > 64 || opt.max_wave < 1 ||
       (opt.cluster_cap != 1 && opt.cluster_cap != 2 && opt.cluster_cap != 4 && opt.cluster_cap != 8))
     return TSVD_EINVAL;
+  if (opt.heavy_dim == 0) opt.heavy_dim = 1024;
+  if (opt.heavy_streams == 0) opt.heavy_streams = std::max(1, opt.n_streams / 4);
+  if (opt.heavy_dim < -1 || opt.heavy_streams < 1 || opt.heavy_streams > opt.n_streams) return TSVD_EINVAL;
   auto *sv = new tsvd_server_s();
   sv->opt = opt;
   sv->t0 = std::chrono::steady_clock::now();
@@ -1001,6 +1017,7 @@ tsvd_status tsvd_server_submit(tsvd_server_t sv, const float *A, int64_t m, int6
   r->V = V;
   if (iters_override) r->iters.assign(iters_override, iters_override + k);
   r->tc = d >= sv->tc_min_d.load();
+  r->heavy = sv->opt.heavy_dim >= 0 && d > sv->opt.heavy_dim;
   r->bytes = request_bytes(m, n, k, r->tc);
   r->sbytes = staging_bytes(m, n, k);
   if (al(r->bytes) > sv->arena.size || al(r->sbytes) > sv->staging.size) return TSVD_EBUDGET;
@@ -1109,6 +1126,19 @@ const char *tsvd_server_last_error(tsvd_server_t sv) { return sv ? sv->err.c_str
 
 int64_t tsvd_server_tc_min_d(tsvd_server_t sv) { return sv ? sv->tc_min_d.load() : 0; }
 
+tsvd_status tsvd_server_autotune_syrk_times(tsvd_server_t sv, int64_t *d, double *ms_tensor, double *ms_cuda,
+                                            int32_t *requests) {
+  if (!sv || !d || !ms_tensor || !ms_cuda || !requests) return TSVD_EINVAL;
+  std::lock_guard<std::mutex> lk(sv->mu);
+  for (int b = 0; b < 4; ++b) {
+    d[b] = (int64_t)256 << b;
+    ms_tensor[b] = sv->syrk_ms_tc[b];
+    ms_cuda[b] = sv->syrk_ms_cc[b];
+    requests[b] = sv->syrk_nreq[b];
+  }
+  return TSVD_OK;
+}
+
 tsvd_status tsvd_server_set_tc_min_d(tsvd_server_t sv, int64_t d) {
   if (!sv || d < 1) return TSVD_EINVAL;
   sv->tc_min_d.store(d);
@@ -1186,7 +1216,13 @@ tsvd_status tsvd_server_autotune(tsvd_server_t sv, int32_t iters) {
       double ms_tc = 0.0, ms_cc = 0.0;
       result = time_syrk(sv, d, K, nreq, true, st, e0, e1, &ms_tc);
       if (result == TSVD_OK) result = time_syrk(sv, d, K, nreq, false, st, e0, e1, &ms_cc);
-      if (result == TSVD_OK) tc_wins[b] = ms_tc < ms_cc;
+      if (result == TSVD_OK) {
+        tc_wins[b] = ms_tc < ms_cc;
+        std::lock_guard<std::mutex> lk(sv->mu);
+        sv->syrk_ms_tc[b] = ms_tc;
+        sv->syrk_ms_cc[b] = ms_cc;
+        sv->syrk_nreq[b] = nreq;
+      }
       if (result == TSVD_EBUDGET) result = TSVD_OK;  // a budget too small for the size: keep the default
     }
     if (result == TSVD_OK) {
@@ -1225,11 +1261,13 @@ void tsvd_server_destroy(tsvd_server_t sv) {
   if (sv->thr.joinable()) sv->thr.join();
   {
     std::lock_guard<std::mutex> lk(sv->mu);
-    for (auto &r : sv->admitted) {
-      r->rec.status = TSVD_ECUDA;
-      r->done = true;
+    for (auto *qq : {&sv->admitted, &sv->admitted_heavy}) {
+      for (auto &r : *qq) {
+        r->rec.status = TSVD_ECUDA;
+        r->done = true;
+      }
+      qq->clear();
     }
-    sv->admitted.clear();
   }
   sv->cv_done.notify_all();
   for (auto &s : sv->slots) {
