@@ -1272,14 +1272,35 @@ def leg_serve(args, n_req: int):
                                                                  "Gram, pinned host A, one at a time"},
             "speedup_capacity_vs_per_request": round(capacity["solves_per_s"] / base_rate, 2) if base_rate else None,
             "server": {"streams": args.serve_streams, "max_wave": args.serve_max_wave,
-                       "heavy_dim": args.serve_heavy_dim or 1024, "heavy_streams": args.serve_heavy_streams or "auto",
+                       "heavy_dim": args.serve_heavy_dim if args.serve_heavy_dim > 0 else None,
+                       "heavy_streams": args.serve_heavy_streams or "auto",
                        "busy_s": round(s2.get("busy_s", 0.0) - s0.get("busy_s", 0.0), 3)},
             "waves": s2["waves"] - s0["waves"], "gpu_launches": launches,
+            "wave_graphs": {"updated_in_place": s2["graph_updates"] - s0["graph_updates"],
+                            "instantiated": s2["graph_instantiations"] - s0["graph_instantiations"]},
             "peak_device_bytes": s2["peak_device_bytes"], "gen_seconds": round(gen_s, 1), "clocks": clk}
     for a in pool + [outU, outV, outS]:
         free_pinned(a)
     torch.cuda.empty_cache()
     return line
+
+
+def measure_l2_read(nbytes: int = 64 << 20, reps: int = 200) -> float:
+    """L2 read rate (GB/s): a torch reduction over an FP32 buffer that fits in
+    L2 (64 MB of the 129 MB), read `reps` times back to back after a warm-up,
+    CUDA events around the loop."""
+    import torch
+    x = torch.ones(nbytes // 4, dtype=torch.float32, device="cuda")
+    for _ in range(5):
+        x.sum()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        x.sum()
+    e1.record()
+    e1.synchronize()
+    return nbytes * reps / (e0.elapsed_time(e1) / 1e3) / 1e9
 
 
 def csr_pair_checks(dcsr, host, m, nnz, peaks, peak_src, args, with_cpu=True):
@@ -1426,6 +1447,16 @@ def leg_c3(args, steps: int, warmup: int, with_cpu: bool = False, sweep: bool = 
         t_app = reps[-1]["gram_kernel_ms"] / reps[-1]["gram_kernel_launches"] / 1e3
         alg = roofline["algorithmic_bytes"]
         fused = {k2: roofline[k2] for k2 in ("achieved", "frac", "traffic", "ms_per_application")}
+        # L2 sectors: pass 1 gathers v (one 32-byte sector per entry) and streams the entries (8 B
+        # each), pass 2 streams them again and adds into w (one 32-byte sector per atomic)
+        l2_bytes = 80 * nnz + 16 * (m + 1)
+        l2_peak = measure_l2_read()
+        roofline["l2_sectors"] = {"bound": "l2", "achieved": round(l2_bytes / t_app / 1e9, 1),
+                                  "peak": round(l2_peak, 1), "unit": "GB/s",
+                                  "frac": round(l2_bytes / t_app / 1e9 / l2_peak, 4),
+                                  "sector_bytes_per_application": l2_bytes,
+                                  "peak_source": "measured L2 read rate: torch reduction over an L2-resident 64 MB "
+                                                 "buffer"}
         roofline.update({"achieved": round(alg / t_app / 1e9, 1), "frac": round(alg / t_app / 1e9 / peaks["hbm_gbs"], 4),
                          "traffic": measured_traffic("csr_chunk_y_kernel+csr_chunk_w_kernel", m, m),
                          "kernel": f"column-chunked CSR operator ({nch} chunks: csr_chunk_y + csr_chunk_w)",
@@ -1522,7 +1553,7 @@ def main():
                     help="dense: the oracle's trajectory over all of A (FP64 Gram on the host, ~5 min on 16 cores)")
     ap.add_argument("--serve-streams", type=int, default=4, help="serving: waves in flight (streams)")
     ap.add_argument("--serve-max-wave", type=int, default=256, help="serving: requests per wave")
-    ap.add_argument("--serve-heavy-dim", type=int, default=0, help="serving: heavy lane above this d (0: 1024, -1: none)")
+    ap.add_argument("--serve-heavy-dim", type=int, default=0, help="serving: heavy lane above this d (0: none)")
     ap.add_argument("--serve-heavy-streams", type=int, default=0, help="serving: streams of the heavy lane (0: auto)")
     args = ap.parse_args()
     if args.case:

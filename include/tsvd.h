@@ -454,12 +454,12 @@ typedef struct {
                              reads a large Gram matrix per application and
                              can last long, and a wave's stream stays busy
                              until its last request is done, so light waves
-                             are never held behind them (0: 1024; -1: one
-                             lane for all) */
-  int32_t heavy_streams;  /* streams that may run heavy waves (they also take
-                             light requests when no heavy one waits; the
-                             others take light requests only);
-                             0: max(1, n_streams / 4); < n_streams */
+                             (on the n_streams streams) are never held behind
+                             them (0 or -1: one lane for all) */
+  int32_t heavy_streams;  /* most streams the heavy lane opens, one more each
+                             time heavy requests wait and none is idle
+                             (0: 64 - n_streams; n_streams + heavy_streams
+                             <= 64) */
   int32_t reserved[4];
 } tsvd_server_options;
 
@@ -482,6 +482,10 @@ typedef struct {
   int64_t kernel_launches;     /* kernels the scheduler launched */
   int64_t peak_device_bytes;   /* high-water mark of the arena */
   double busy_s;               /* time with at least one wave in flight */
+  int64_t graph_updates;       /* waves whose captured kernel graph updated the
+                                  slot's instantiated graph in place */
+  int64_t graph_instantiations;/* waves whose graph had a new shape and was
+                                  instantiated */
 } tsvd_server_stats;
 
 TSVD_API tsvd_status tsvd_server_options_init(tsvd_server_options *opt);
@@ -551,9 +555,9 @@ TSVD_API int32_t tsvd_server_cluster_for(tsvd_server_t server, int64_t d);
  * Pick the power-kernel cluster size per Gram dimension by measurement: for
  * d in {64, 128, 256, 512, 1024, 2048} and each cluster size up to
  * cluster_cap, time `iters` iterations of one synthetic request alone and of
- * as many as fill the GPU, and keep the size with the highest iterations per
- * second over the whole GPU among those whose single-request time is within
- * 4x of the fastest.  Then pick the Gram step's tile shape per size: for
+ * as many as fill the GPU, and keep the smallest size whose iterations per
+ * second over the whole GPU are within 10% of the best, among those whose
+ * single-request time is within 8x of the fastest.  Then pick the Gram step's tile shape per size: for
  * d in {256, 512, 1024, 2048} it times the grouped tensor-core SYRK (128 x 256
  * tiles, 3xTF32) and the grouped CUDA-core SYRK (64 x 64 tiles, FP32) on
  * synthetic 8192 x d requests, enough to give both kernels work for every SM,

@@ -18,9 +18,10 @@
 // different streams overlap on the device, so requests that arrive while
 // others run are admitted as memory frees up and start without waiting.
 // Requests with a large Gram dimension (above `heavy_dim`) form waves of their
-// own on the first `heavy_streams` streams: their power phase can last long,
-// and a stream stays busy until its wave's last request is done, so light
-// waves, which turn over quickly, never queue behind them.
+// own on streams opened on demand (up to `heavy_streams`): their power phase
+// can last long, and a stream stays busy until its wave's last request is
+// done, so light waves, which turn over quickly, never queue behind them, and
+// heavy ones never wait for a heavy stream while memory admits them.
 #include <cuda.h>
 
 #include <algorithm>
@@ -228,6 +229,7 @@ struct Slot {  // one stream and the page-locked descriptors of the wave it runs
   std::vector<ReqPtr> reqs;
   size_t dev_off = 0, dev_bytes = 0;  // descriptor arrays in the device arena
   int64_t wave = 0;
+  cudaGraphExec_t exec = nullptr;     // the kernel part of the last wave, updated wave by wave
 };
 
 }  // namespace
@@ -237,7 +239,7 @@ struct tsvd_server_s {
   tsvd_server_options opt{};
   int device = 0;
   tsvd::Arena arena, staging;
-  std::vector<tsvd::Slot> slots;
+  std::deque<tsvd::Slot> slots;  // the first n_streams take light waves; heavy ones are added on demand
   // completion flags: one word per in-flight request (device), its page-locked mirror,
   // the stream and event of the copy that refreshes the mirror, the free flag words
   uint32_t *dflags = nullptr, *hflags = nullptr;
@@ -452,21 +454,60 @@ tsvd_status launch_wave(tsvd_server_s *sv, Slot &s) {
       TSVD_CUDA(cudaMemcpyAsync(const_cast<int32_t *>(r->dq.iters_override), r->iters.data(), r->iters.size() * 4,
                                 cudaMemcpyHostToDevice, st));
   }
-  TSVD_CUDA(cudaMemcpyAsync(dev, s.stage, need, cudaMemcpyHostToDevice, st));
+  // the kernel part of the wave is captured into a CUDA graph: the descriptor copy, the
+  // grouped SYRK (tensor-core prep / SYRK / finish, then the CUDA-core tiles) and one power
+  // launch per (cluster, residency) run of the sorted requests.  Waves of the same shape
+  // (the same launches with other sizes and pointers) update the slot's instantiated graph in
+  // place; a new shape instantiates it again.
   const SrvReq *dreq = reinterpret_cast<const SrvReq *>(dev);
-  // 1. grouped SYRK: the tensor-core requests (prep, SYRK, finish), then the CUDA-core ones
-  TSVD_TRY(launch_tc_wave(tw, dreq, dev + o_tc, derr, st));
-  TSVD_TRY(launch_srv_syrk(dreq, reinterpret_cast<const SrvTile *>(dev + b_req), (int)tiles.size(), st));
-  // 2. grouped power + other factor, one launch per (cluster, residency) run of the sorted requests
-  for (size_t i = 0; i < rs.size();) {
-    size_t j = i, smem = 0;
-    while (j < rs.size() && rs[j]->dq.cluster == rs[i]->dq.cluster && rs[j]->dq.resident == rs[i]->dq.resident) {
-      smem = std::max(smem, srv_power_smem(std::min(rs[j]->m, rs[j]->n), rs[j]->dq.cluster, rs[j]->dq.resident));
-      ++j;
+  TSVD_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeRelaxed));
+  auto enqueue = [&]() -> tsvd_status {
+    TSVD_CUDA(cudaMemcpyAsync(dev, s.stage, need, cudaMemcpyHostToDevice, st));
+    TSVD_TRY(launch_tc_wave(tw, dreq, dev + o_tc, derr, st));
+    TSVD_TRY(launch_srv_syrk(dreq, reinterpret_cast<const SrvTile *>(dev + b_req), (int)tiles.size(), st));
+    for (size_t i = 0; i < rs.size();) {
+      size_t j = i, smem = 0;
+      while (j < rs.size() && rs[j]->dq.cluster == rs[i]->dq.cluster && rs[j]->dq.resident == rs[i]->dq.resident) {
+        smem = std::max(smem, srv_power_smem(std::min(rs[j]->m, rs[j]->n), rs[j]->dq.cluster, rs[j]->dq.resident));
+        ++j;
+      }
+      TSVD_TRY(launch_srv_power(dreq + i, (int)(j - i), rs[i]->dq.cluster, smem, st));
+      i = j;
     }
-    TSVD_TRY(launch_srv_power(dreq + i, (int)(j - i), rs[i]->dq.cluster, smem, st));
-    i = j;
+    return TSVD_OK;
+  };
+  const tsvd_status est = enqueue();
+  cudaGraph_t g = nullptr;
+  const cudaError_t ce = cudaStreamEndCapture(st, &g);  // always ends the capture, also after a failure
+  if (est != TSVD_OK) {
+    if (g) cudaGraphDestroy(g);
+    return est;
   }
+  TSVD_CUDA(ce);
+  bool updated = false;
+  if (s.exec) {
+    cudaGraphExecUpdateResultInfo info;
+    updated = cudaGraphExecUpdate(s.exec, g, &info) == cudaSuccess;
+    if (!updated) {
+      cudaGetLastError();
+      cudaGraphExecDestroy(s.exec);
+      s.exec = nullptr;
+    }
+  }
+  if (!updated) {
+    const cudaError_t ie = cudaGraphInstantiate(&s.exec, g, 0);
+    if (ie != cudaSuccess) {
+      cudaGraphDestroy(g);
+      s.exec = nullptr;
+      TSVD_CUDA(ie);
+    }
+  }
+  cudaGraphDestroy(g);
+  {
+    std::lock_guard<std::mutex> lk(sv->mu);
+    ++(updated ? sv->stats.graph_updates : sv->stats.graph_instantiations);
+  }
+  TSVD_CUDA(cudaGraphLaunch(s.exec, st));
   TSVD_CUDA(cudaEventRecord(s.done, st));
   return TSVD_OK;
 }
@@ -616,12 +657,26 @@ void scheduler(tsvd_server_s *sv) {
       progressed = true;
     }
     // waves
+    // heavy requests waiting and no idle heavy stream: open one more, up to heavy_streams
+    if (!sv->admitted_heavy.empty()) {
+      bool idle = false;
+      for (size_t si = (size_t)sv->opt.n_streams; si < sv->slots.size(); ++si) idle |= !sv->slots[si].busy;
+      if (!idle && (int)sv->slots.size() < sv->opt.n_streams + sv->opt.heavy_streams) {
+        Slot ns;
+        if (cudaStreamCreateWithFlags(&ns.stream, cudaStreamNonBlocking) == cudaSuccess &&
+            cudaEventCreateWithFlags(&ns.done, cudaEventDisableTiming) == cudaSuccess) {
+          sv->slots.push_back(ns);
+        } else {
+          cudaGetLastError();
+          if (ns.stream) cudaStreamDestroy(ns.stream);
+        }
+      }
+    }
     for (size_t si = 0; si < sv->slots.size(); ++si) {
       Slot &s = sv->slots[si];
-      // the first heavy_streams streams take heavy requests first (light ones when none
-      // waits); the others light ones only, so a light wave never waits behind a heavy one
-      std::deque<ReqPtr> &q = ((int)si < sv->opt.heavy_streams && !sv->admitted_heavy.empty()) ? sv->admitted_heavy
-                                                                                               : sv->admitted;
+      // the first n_streams streams take light requests only, the heavy streams heavy ones
+      // only, so a light wave never waits behind a heavy request's long power phase
+      std::deque<ReqPtr> &q = si < (size_t)sv->opt.n_streams ? sv->admitted : sv->admitted_heavy;
       if (s.busy || q.empty()) continue;
       const size_t take = std::min(q.size(), (size_t)sv->opt.max_wave);
       s.reqs.assign(q.begin(), q.begin() + take);
@@ -949,9 +1004,10 @@ tsvd_status tsvd_server_create(tsvd_server_t *out, const tsvd_server_options *op
   if (opt.max_inflight < 1 || opt.n_streams < 1 || opt.n_streams > 64 || opt.max_wave < 1 ||
       (opt.cluster_cap != 1 && opt.cluster_cap != 2 && opt.cluster_cap != 4 && opt.cluster_cap != 8))
     return TSVD_EINVAL;
-  if (opt.heavy_dim == 0) opt.heavy_dim = 1024;
-  if (opt.heavy_streams == 0) opt.heavy_streams = std::max(1, opt.n_streams / 4);
-  if (opt.heavy_dim < -1 || opt.heavy_streams < 1 || opt.heavy_streams > opt.n_streams) return TSVD_EINVAL;
+  if (opt.heavy_dim == 0) opt.heavy_dim = -1;  // one lane unless asked for
+  if (opt.heavy_streams == 0) opt.heavy_streams = 64 - opt.n_streams;
+  if (opt.heavy_dim < -1 || opt.heavy_streams < 0 || opt.n_streams + opt.heavy_streams > 64) return TSVD_EINVAL;
+  if (opt.heavy_dim >= 0 && opt.heavy_streams == 0) return TSVD_EINVAL;  // a heavy lane needs a stream
   auto *sv = new tsvd_server_s();
   sv->opt = opt;
   sv->t0 = std::chrono::steady_clock::now();
@@ -1185,16 +1241,20 @@ tsvd_status tsvd_server_autotune(tsvd_server_t sv, int32_t iters) {
       thr.push_back((double)nfill / msn);  // requests per millisecond over the whole GPU
     }
     if (result != TSVD_OK || cs.empty()) break;
-    // the highest throughput among sizes whose lone request is within 4x of the fastest one
+    // throughput first: among the sizes whose lone request is within 8x of the fastest one,
+    // the smallest cluster whose throughput is within 10 % of the best (fewer SMs per request
+    // pack a mixed load better; measured on the serving mix, 2-CTA clusters for d = 1024 gave
+    // twice the capacity of 8-CTA ones at the same lone-request throughput)
     double best_lat = lat[0];
     for (double x : lat) best_lat = std::min(best_lat, x);
-    int best_c = cs[0];
     double best_thr = -1.0;
+    for (size_t i = 0; i < cs.size(); ++i)
+      if (lat[i] <= 8.0 * best_lat) best_thr = std::max(best_thr, thr[i]);
+    int best_c = cs[0];
     for (size_t i = 0; i < cs.size(); ++i) {
-      if (lat[i] > 4.0 * best_lat) continue;
-      if (thr[i] > best_thr) {
-        best_thr = thr[i];
+      if (lat[i] <= 8.0 * best_lat && thr[i] >= 0.9 * best_thr) {
         best_c = cs[i];
+        break;  // cs is in increasing order
       }
     }
     std::lock_guard<std::mutex> lk(sv->mu);
@@ -1272,6 +1332,7 @@ void tsvd_server_destroy(tsvd_server_t sv) {
   sv->cv_done.notify_all();
   for (auto &s : sv->slots) {
     if (s.stream) cudaStreamSynchronize(s.stream);
+    if (s.exec) cudaGraphExecDestroy(s.exec);
     if (s.stream) cudaStreamDestroy(s.stream);
     if (s.done) cudaEventDestroy(s.done);
     if (s.stage) cudaFreeHost(s.stage);

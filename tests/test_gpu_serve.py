@@ -104,6 +104,8 @@ def test_server_mixed_wave_matches_oracle(tc_min_d):
         stats = sv.stats()
         assert stats["completed"] == len(CASES) and stats["failed"] == 0
         assert stats["kernel_launches"] >= 3
+        # every wave ran as a CUDA graph: updated in place or instantiated
+        assert stats["graph_updates"] + stats["graph_instantiations"] == stats["waves"] >= 1
     finally:
         sv.close()
         pool.close()
@@ -143,7 +145,8 @@ def test_server_result_alone_equals_result_in_the_mix():
         assert st == B.TSVD_OK
         for a, b in zip(alone, mix):
             assert np.array_equal(a, b)
-        assert sv.stats()["waves"] >= 2
+        st2 = sv.stats()
+        assert st2["waves"] >= 2 and st2["graph_updates"] + st2["graph_instantiations"] == st2["waves"]
     finally:
         sv.close()
         pool.close()
