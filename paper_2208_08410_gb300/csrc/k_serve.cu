@@ -188,7 +188,8 @@ struct PowerSmem {
 __device__ __forceinline__ int64_t pad4(int64_t x) { return (x + 3) & ~int64_t(3); }
 
 // ---------------------------------------------------------------- grouped power
-__global__ void __launch_bounds__(kSrvPowerThreads, 2) srv_power_kernel(const SrvReq *__restrict__ reqs) {
+__global__ void __launch_bounds__(kSrvPowerThreads, 2) srv_power_kernel(const SrvReq *__restrict__ reqs,
+                                                                       int n_reqs) {
   extern __shared__ __align__(16) unsigned char srv_smem[];
   __shared__ double wred[3 * (kSrvPowerThreads / 32)];
   __shared__ double red[33];
@@ -197,16 +198,21 @@ __global__ void __launch_bounds__(kSrvPowerThreads, 2) srv_power_kernel(const Sr
   __shared__ __align__(16) float ostage[kSrvOtherChunk * kSrvMaxK];  // other factor: a chunk of V or U
   __shared__ double cpart[kSrvMaxK + 1];  // this CTA's v^T G_defl v and v_j . v partials
   const uint32_t C = cta_count(), rank = cta_rank();
+  // self-checks of the launch (every CTA of a cluster takes the same branch): a cluster
+  // past the descriptors has nothing to do; a request whose descriptor names another
+  // cluster size than the launch has is failed, not run on a wrong partition of its rows
+  if (blockIdx.x / C >= (unsigned)n_reqs) return;
   const SrvReq &q = reqs[blockIdx.x / C];
   const int64_t d = q.trans ? q.m : q.n;
   const int k = q.k;
   const int64_t R = srv_rows_per_cta(d, C);  // a multiple of 4, so every CTA's row range starts 16-byte aligned
   const int64_t r0 = min(d, (int64_t)rank * R), r1 = min(d, r0 + R);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = kSrvPowerThreads / 32;
-  if (q.gram_err && *reinterpret_cast<const volatile int32_t *>(q.gram_err) != 0) {
-    // the tensor-core SYRK that formed this request's G gave up on a bounded wait:
-    // no results; every triplet reports the timeout (every CTA reads the same word,
-    // written by an earlier launch, so the whole cluster takes this branch)
+  if (q.cluster != (int32_t)C || (q.gram_err && *reinterpret_cast<const volatile int32_t *>(q.gram_err) != 0)) {
+    // the tensor-core SYRK that formed this request's G gave up on a bounded wait (or the
+    // launch's cluster size is not the descriptor's): no results; every triplet reports
+    // the failure (every CTA reads the same words, written before this launch, so the
+    // whole cluster takes this branch)
     if (rank == 0) {
       for (int l = threadIdx.x; l < k; l += kSrvPowerThreads) {
         q.oS[l] = 0.0;
@@ -746,7 +752,7 @@ tsvd_status launch_srv_power(const SrvReq *reqs, int n_reqs, int cluster, size_t
   at[0].val.clusterDim.z = 1;
   cfg.attrs = at;
   cfg.numAttrs = 1;
-  TSVD_CUDA(cudaLaunchKernelEx(&cfg, srv_power_kernel, reqs));
+  TSVD_CUDA(cudaLaunchKernelEx(&cfg, srv_power_kernel, reqs, n_reqs));
   TSVD_LAUNCHED();
   return TSVD_OK;
 }

@@ -230,6 +230,7 @@ struct Slot {  // one stream and the page-locked descriptors of the wave it runs
   size_t dev_off = 0, dev_bytes = 0;  // descriptor arrays in the device arena
   int64_t wave = 0;
   cudaGraphExec_t exec = nullptr;     // the kernel part of the last wave, updated wave by wave
+  std::vector<int32_t> shape;         // its launch signature (see launch_wave)
 };
 
 }  // namespace
@@ -484,7 +485,23 @@ tsvd_status launch_wave(tsvd_server_s *sv, Slot &s) {
     return est;
   }
   TSVD_CUDA(ce);
+  // The launch signature: which SYRK launches there are and the (cluster, residency) of
+  // every power launch.  The instantiated graph is updated in place only for a wave with
+  // the same signature, so every node keeps its kernel and its launch attributes (the
+  // power kernel's cluster size is one) and only sizes and pointers change.
+  std::vector<int32_t> shape = {ntc > 0 ? 1 : 0, tiles.empty() ? 0 : 1};
+  for (size_t i = 0; i < rs.size();) {
+    size_t j = i;
+    while (j < rs.size() && rs[j]->dq.cluster == rs[i]->dq.cluster && rs[j]->dq.resident == rs[i]->dq.resident) ++j;
+    shape.push_back(rs[i]->dq.cluster * 2 + rs[i]->dq.resident);
+    i = j;
+  }
   bool updated = false;
+  if (s.exec && s.shape != shape) {
+    cudaGraphExecDestroy(s.exec);
+    s.exec = nullptr;
+  }
+  s.shape = shape;
   if (s.exec) {
     cudaGraphExecUpdateResultInfo info;
     updated = cudaGraphExecUpdate(s.exec, g, &info) == cudaSuccess;
