@@ -1092,9 +1092,20 @@ def leg_serve(args, n_req: int):
     torch.cuda.empty_cache()
     gen_s = time.time() - t0
     # sparse requests (a share of the mix): square CSR, m = n log-uniform, density 1e-4
-    n_sp_pool = max(4, n_pool // 8) if args.csr_share > 0 else 0
-    sp_shapes = synth.serving_sparse_shapes(n_sp_pool, seed=13)
-    sp_pool = [synth.csr_uniform(sh["m"], sh["n"], sh["nnz_per_row"], seed=500 + i) for i, sh in enumerate(sp_shapes)]
+    n_sp_pool = (args.serve_sparse_pool or max(4, n_pool // 8)) if args.csr_share > 0 else 0
+    sp_lo, sp_hi = (int(x) for x in args.serve_sparse_log2.split(","))
+    sp_shapes = synth.serving_sparse_shapes(n_sp_pool, seed=13, dim_range=(1 << sp_lo, 1 << sp_hi))
+    if sp_hi <= 16:
+        sp_pool = [synth.csr_uniform(sh["m"], sh["n"], sh["nnz_per_row"], seed=500 + i)
+                   for i, sh in enumerate(sp_shapes)]
+    else:  # up to 2^20 x 2^20 at density 1e-4 (1.1e8 entries): drawn on the GPU, kept on the host
+        sp_pool = []
+        for i, sh in enumerate(sp_shapes):
+            t = synth.csr_uniform_torch(sh["m"], sh["n"], sh["nnz_per_row"], seed=500 + i)
+            sp_pool.append({"row_ptr": t["row_ptr"].cpu().numpy(), "col_idx": t["col_idx"].cpu().numpy(),
+                            "values": t["values"].cpu().numpy(), "m": sh["m"], "n": sh["n"]})
+            del t
+        torch.cuda.empty_cache()
     g = np.random.default_rng(12)
     arrivals = np.cumsum(g.exponential(1.0 / rate, n_req))
     picks = g.integers(0, n_pool, n_req)
@@ -1257,7 +1268,7 @@ def leg_serve(args, n_req: int):
             "config": {"workload": f"{n_req} t-SVD requests, Poisson {rate} req/s; dense from a pool of {n_pool}: "
                                    "m logU[512,65536], n logU[64,2048], sigma_i=rho^i, rho~U(0.5,0.95), "
                                    f"k~U{{4..32}}, eps=1e-8; {args.csr_share:.0%} CSR from a pool of {n_sp_pool}: "
-                                   f"m=n logU[2^14,2^16], density 1e-4, eps={SP_EPS}, max_iter {SP_MAX_ITER}",
+                                   f"m=n logU[2^{sp_lo},2^{sp_hi}], density 1e-4, eps={SP_EPS}, max_iter {SP_MAX_ITER}",
                        "requests": n_req, "sparse_requests": int(is_sp.sum()), "rate": rate, "pool": n_pool,
                        "pool_bytes": int(sum(a.nbytes for a in pool)), "device_budget_gib": args.serve_budget},
             "accuracy_scope": f"sigma graded against the closed form rho^i on the triplets with rho^i >= {ENVELOPE} "
@@ -1554,6 +1565,9 @@ def main():
     ap.add_argument("--serve-streams", type=int, default=4, help="serving: waves in flight (streams)")
     ap.add_argument("--serve-max-wave", type=int, default=256, help="serving: requests per wave")
     ap.add_argument("--serve-heavy-dim", type=int, default=0, help="serving: heavy lane above this d (0: none)")
+    ap.add_argument("--serve-sparse-pool", type=int, default=0, help="serving: distinct sparse matrices (0: pool/8)")
+    ap.add_argument("--serve-sparse-log2", default="14,16",
+                    help="serving: sparse requests m = n log-uniform in [2^a, 2^b] (the config allows up to 2^20)")
     ap.add_argument("--serve-heavy-streams", type=int, default=0, help="serving: streams of the heavy lane (0: auto)")
     args = ap.parse_args()
     if args.case:

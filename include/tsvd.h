@@ -555,9 +555,9 @@ TSVD_API int32_t tsvd_server_cluster_for(tsvd_server_t server, int64_t d);
  * Pick the power-kernel cluster size per Gram dimension by measurement: for
  * d in {64, 128, 256, 512, 1024, 2048} and each cluster size up to
  * cluster_cap, time `iters` iterations of one synthetic request alone and of
- * as many as fill the GPU, and keep the smallest size whose iterations per
- * second over the whole GPU are within 10% of the best, among those whose
- * single-request time is within 8x of the fastest.  Then pick the Gram step's tile shape per size: for
+ * as many as fill the GPU, and keep the size with the highest iterations per
+ * second over the whole GPU among those whose single-request time is within
+ * 2.5x of the fastest.  Then pick the Gram step's tile shape per size: for
  * d in {256, 512, 1024, 2048} it times the grouped tensor-core SYRK (128 x 256
  * tiles, 3xTF32) and the grouped CUDA-core SYRK (64 x 64 tiles, FP32) on
  * synthetic 8192 x d requests, enough to give both kernels work for every SM,

@@ -1258,20 +1258,20 @@ tsvd_status tsvd_server_autotune(tsvd_server_t sv, int32_t iters) {
       thr.push_back((double)nfill / msn);  // requests per millisecond over the whole GPU
     }
     if (result != TSVD_OK || cs.empty()) break;
-    // throughput first: among the sizes whose lone request is within 8x of the fastest one,
-    // the smallest cluster whose throughput is within 10 % of the best (fewer SMs per request
-    // pack a mixed load better; measured on the serving mix, 2-CTA clusters for d = 1024 gave
-    // twice the capacity of 8-CTA ones at the same lone-request throughput)
+    // the highest whole-GPU throughput among the sizes whose lone request is within 2.5x
+    // of the fastest one.  Both limits matter on the serving mix: a wave's stream is busy
+    // until its slowest request is done, so 1-CTA clusters for d >= 1024 (best throughput
+    // alone) made long wave tails and halved capacity, and 8-CTA clusters for d = 1024
+    // halved it too against 2-CTA ones
     double best_lat = lat[0];
     for (double x : lat) best_lat = std::min(best_lat, x);
-    double best_thr = -1.0;
-    for (size_t i = 0; i < cs.size(); ++i)
-      if (lat[i] <= 8.0 * best_lat) best_thr = std::max(best_thr, thr[i]);
     int best_c = cs[0];
+    double best_thr = -1.0;
     for (size_t i = 0; i < cs.size(); ++i) {
-      if (lat[i] <= 8.0 * best_lat && thr[i] >= 0.9 * best_thr) {
+      if (lat[i] > 2.5 * best_lat) continue;
+      if (thr[i] > best_thr) {
+        best_thr = thr[i];
         best_c = cs[i];
-        break;  // cs is in increasing order
       }
     }
     std::lock_guard<std::mutex> lk(sv->mu);
