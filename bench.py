@@ -225,9 +225,9 @@ def measure_h2d_peak(A: np.ndarray):
     """Pinned host -> HBM copy rates (cudaMemcpyAsync via torch, one copy stream):
     burst = best of 3 copies of the first 4 GiB block; sustained = every row
     block of A copied back to back into a 2-buffer ring (what a streamed pass
-    over the whole matrix can reach), measured on a second pass: the first
-    pass after the generator wrote A runs through every block once untimed,
-    as the benchmark's warm-up steps do before the timed ones."""
+    over the whole matrix can reach), the faster of two timed passes after
+    an untimed one (the benchmark's warm-up steps also run before its timed
+    ones; a single stalled block can halve one pass)."""
     import torch
     rows = min(A.shape[0], BLOCK_ROWS)
     dst = [torch.empty((rows, A.shape[1]), dtype=torch.float32, device="cuda") for _ in range(2)]
@@ -244,20 +244,24 @@ def measure_h2d_peak(A: np.ndarray):
     for i, r0 in enumerate(range(0, A.shape[0], rows)):  # untimed first pass
         blk = torch.from_numpy(A[r0:r0 + rows])
         dst[i & 1][:blk.shape[0]].copy_(blk, non_blocking=True)
-    evs = []
-    torch.cuda.synchronize()
-    total = 0
-    for i, r0 in enumerate(range(0, A.shape[0], rows)):
-        blk = torch.from_numpy(A[r0:r0 + rows])
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record()
-        dst[i & 1][:blk.shape[0]].copy_(blk, non_blocking=True)
-        b.record()
-        evs.append((a, b, blk.numel() * 4))
-        total += blk.numel() * 4
-    torch.cuda.synchronize()
-    sustained = total / (evs[0][0].elapsed_time(evs[-1][1]) / 1e3) / 1e9
-    per = sorted(nb / (x.elapsed_time(y) / 1e3) / 1e9 for x, y, nb in evs)
+    sustained, per = 0.0, []
+    for _ in range(2):  # two timed passes; the faster one (a stalled block can halve a pass)
+        evs = []
+        torch.cuda.synchronize()
+        total = 0
+        for i, r0 in enumerate(range(0, A.shape[0], rows)):
+            blk = torch.from_numpy(A[r0:r0 + rows])
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            dst[i & 1][:blk.shape[0]].copy_(blk, non_blocking=True)
+            b.record()
+            evs.append((a, b, blk.numel() * 4))
+            total += blk.numel() * 4
+        torch.cuda.synchronize()
+        rate = total / (evs[0][0].elapsed_time(evs[-1][1]) / 1e3) / 1e9
+        if rate > sustained:
+            sustained = rate
+            per = sorted(nb / (x.elapsed_time(y) / 1e3) / 1e9 for x, y, nb in evs)
     measure_h2d_peak.per_block = {"min": round(per[0], 1), "median": round(per[len(per) // 2], 1),
                                   "max": round(per[-1], 1)}
     del dst
@@ -817,6 +821,7 @@ def leg_c2_small(args, h2d_peak=None):
                "pinned_copy_peak_GBps": round(sustained, 2), "pinned_copy_burst_GBps": round(burst, 2),
                "pinned_copy_per_block_GBps": per_block,
                "frac_gram_pass": round(m * N_COLS * 4 / gram_s / 1e9 / sustained, 4),
+               "frac_gram_pass_of_burst": round(m * N_COLS * 4 / gram_s / 1e9 / burst, 4),
                "blocks_per_pass": r["n_blocks"], "ring_slots": r["ring_slots"],
                "copy_stream_GBps": round(r["h2d_bytes"] / (r["h2d_copy_ms"] / 1e3) / 1e9, 2)
                if r["h2d_copy_ms"] else None,
@@ -1686,6 +1691,7 @@ def main():
                    "pinned_copy_per_block_GBps": getattr(measure_h2d_peak, "per_block", None),
                    "peak_note": "peak = sustained pinned copy of every row block of A back to back",
                    "frac_gram_pass": round(m * N_COLS * 4 / gram_pass_s / 1e9 / h2d_peak, 4),
+                   "frac_gram_pass_of_burst": round(m * N_COLS * 4 / gram_pass_s / 1e9 / h2d_burst, 4),
                    "blocks_per_pass": reps_e[-1]["n_blocks"], "ring_slots": reps_e[-1]["ring_slots"],
                    "block_copies_per_step": reps_e[-1]["h2d_copies"],
                    "copy_stream_GBps": round(reps_e[-1]["h2d_bytes"] / (reps_e[-1]["h2d_copy_ms"] / 1e3) / 1e9, 2)
