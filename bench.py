@@ -507,7 +507,11 @@ def kernel_case(args):
         return e0.elapsed_time(e1) / 1e3 / reps
 
     peaks, src = load_peaks()
-    if args.case == "gram":
+    if args.case == "tf32ref":
+        # the library GEMM the tensor-core Gram is compared with: cuBLAS TF32, 8192^3
+        res = measure_tf32_peak(burst_reps=3, sustained_s=0.2)
+        out.update({"n": 8192, "cublas_tf32": res})
+    elif args.case == "gram":
         m = args.m or BLOCK_ROWS
         n = args.n
         A = torch.randn((m, n), generator=gen, device="cuda", dtype=torch.float32)
@@ -1546,7 +1550,8 @@ def main():
     ap.add_argument("--no-parity", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=0)
-    ap.add_argument("--case", default="", choices=["", "gram", "power", "csr", "left", "c1", "csr_tsvd", "csr_small"],
+    ap.add_argument("--case", default="",
+                    choices=["", "gram", "power", "csr", "left", "c1", "csr_tsvd", "csr_small", "tf32ref"],
                     help="single-kernel microbenchmark instead of the t-SVD step")
     ap.add_argument("--n", type=int, default=N_COLS)
     ap.add_argument("--workload", default="dense", choices=["dense", "csr", "c4", "serve", "tiled"])
