@@ -18,6 +18,13 @@ Contents, each citing the passage it restates:
   eq1_gram, eq2_apply, eq3_apply       Eq. 1, Eq. 2, Eq. 3
   dist_compute_v0                      Alg. 4 (typos corrected, see below)
   csr_matvec, csr_rmatvec              y = A v, w = A^T y (Alg. 4 l.3-6)
+  gapped_indices, subspace_angle,      the grading rule of the parity tests: a triplet is graded
+  vector_angle                         when its relative eigen-gap is >= 0.05 to both neighbours,
+                                       a cluster by its largest principal angle
+
+Every function is pinned by tests/test_oracle_pins.py against something other
+than itself (closed forms, published known answers, LAPACK, brute force,
+identities); none is "parity unpinned".
 
 Readings of the paper taken here (each also listed in the design notes):
   * m >= n takes the right-vector branch (Alg. 4 uses m >= n; Alg. 1 says m > n).
