@@ -294,10 +294,25 @@ def pinned_array(shape, dtype):
     nbytes = int(np.prod(shape)) * np.dtype(dtype).itemsize
     ptr = C.c_void_p()
     B.check(B.tsvd_host_alloc(C.byref(ptr), max(nbytes, 16)), "tsvd_host_alloc")
-    ctype = {np.float32: C.c_float, np.float64: C.c_double}[dtype]
+    ctype = {np.float32: C.c_float, np.float64: C.c_double, np.uint8: C.c_uint8}[dtype]
     arr = np.ctypeslib.as_array(C.cast(ptr, C.POINTER(ctype)), shape=shape)
     _PINNED[ptr.value] = ptr
     return arr
+
+
+def pinned_views(shapes_dtypes, align: int = 4096):
+    """Many page-locked host arrays carved from ONE allocation of the library's
+    allocator, so that small arrays share its huge pages (a separate
+    allocation below the huge-page size stays on base pages).  Returns
+    (arena, views); free the arena with free_pinned(arena)."""
+    offs, total = [], 0
+    for shape, dtype in shapes_dtypes:
+        offs.append(total)
+        total += (int(np.prod(shape)) * np.dtype(dtype).itemsize + align - 1) // align * align
+    arena = pinned_array((max(total, 16),), np.uint8)
+    views = [arena[o:o + int(np.prod(sh)) * np.dtype(dt).itemsize].view(dt).reshape(sh)
+             for o, (sh, dt) in zip(offs, shapes_dtypes)]
+    return arena, views
 
 
 def free_pinned(arr):
@@ -1093,11 +1108,10 @@ def leg_serve(args, n_req: int):
     n_pool, rate, eps = args.pool, args.rate, 1e-8
     t0 = time.time()
     shapes = synth.serving_shapes(n_pool, seed=11)
-    pool = []
+    # the whole pool in one page-locked arena (huge pages for the small matrices too)
+    arena, pool = pinned_views([((sh["m"], sh["n"]), np.float32) for sh in shapes])
     for i, sh in enumerate(shapes):
-        a = pinned_array((sh["m"], sh["n"]), np.float32)
-        synth.serving_matrix_torch(sh, seed=i, out=a)
-        pool.append(a)
+        synth.serving_matrix_torch(sh, seed=i, out=pool[i])
     torch.cuda.empty_cache()
     gen_s = time.time() - t0
     # sparse requests (a share of the mix): square CSR, m = n log-uniform, density 1e-4
@@ -1105,16 +1119,28 @@ def leg_serve(args, n_req: int):
     sp_lo, sp_hi = (int(x) for x in args.serve_sparse_log2.split(","))
     sp_shapes = synth.serving_sparse_shapes(n_sp_pool, seed=13, dim_range=(1 << sp_lo, 1 << sp_hi))
     if sp_hi <= 16:
-        sp_pool = [synth.csr_uniform(sh["m"], sh["n"], sh["nnz_per_row"], seed=500 + i)
+        sp_host = [synth.csr_uniform(sh["m"], sh["n"], sh["nnz_per_row"], seed=500 + i)
                    for i, sh in enumerate(sp_shapes)]
-    else:  # up to 2^20 x 2^20 at density 1e-4 (1.1e8 entries): drawn on the GPU, kept on the host
-        sp_pool = []
+    else:  # up to 2^20 x 2^20 at density 1e-4 (1.1e8 entries): drawn on the GPU
+        sp_host = []
         for i, sh in enumerate(sp_shapes):
             t = synth.csr_uniform_torch(sh["m"], sh["n"], sh["nnz_per_row"], seed=500 + i)
-            sp_pool.append({"row_ptr": t["row_ptr"].cpu().numpy(), "col_idx": t["col_idx"].cpu().numpy(),
+            sp_host.append({"row_ptr": t["row_ptr"].cpu().numpy(), "col_idx": t["col_idx"].cpu().numpy(),
                             "values": t["values"].cpu().numpy(), "m": sh["m"], "n": sh["n"]})
             del t
         torch.cuda.empty_cache()
+    # the sparse pool, too, in one page-locked arena
+    keys = ("row_ptr", "col_idx", "values")
+    sp_arena, sp_views = pinned_views([(c[key].shape, c[key].dtype.type) for c in sp_host for key in keys])
+    sp_pool = []
+    for j, c in enumerate(sp_host):
+        d = {"m": c["m"], "n": c["n"]}
+        for q, key in enumerate(keys):
+            v = sp_views[3 * j + q]
+            v[...] = c[key]
+            d[key] = v
+        sp_pool.append(d)
+    del sp_host
     g = np.random.default_rng(12)
     arrivals = np.cumsum(g.exponential(1.0 / rate, n_req))
     picks = g.integers(0, n_pool, n_req)
@@ -1124,17 +1150,26 @@ def leg_serve(args, n_req: int):
     sp_picks = g.integers(0, max(n_sp_pool, 1), n_req)
     for i in np.nonzero(is_sp)[0]:
         ks[i] = min(int(g.integers(4, 33)), sp_shapes[sp_picks[i]]["m"])
-    m_max = max([sh["m"] for sh in shapes] + [sh["m"] for sh in sp_shapes])
-    n_max = max([sh["n"] for sh in shapes] + [sh["n"] for sh in sp_shapes])
+    # output slots: one pool sized for the dense shapes, a smaller one for the sparse shapes
+    # (a 2^20-row sparse slot holds 268 MB of U and V, so those are capped at 8 GiB in all)
+    m_max, n_max = max(sh["m"] for sh in shapes), max(sh["n"] for sh in shapes)
     slots = 768
     outU = pinned_array((slots, 32 * m_max), np.float32)
     outV = pinned_array((slots, 32 * n_max), np.float32)
     outS = pinned_array((slots, 32), np.float64)
+    sp_m = max([sh["m"] for sh in sp_shapes], default=1)
+    sp_n = max([sh["n"] for sh in sp_shapes], default=1)
+    sp_slots = max(4, min(128, (8 << 30) // (32 * (sp_m + sp_n) * 4))) if n_sp_pool else 1
+    outUs = pinned_array((sp_slots, 32 * sp_m), np.float32)
+    outVs = pinned_array((sp_slots, 32 * sp_n), np.float32)
+    outSs = pinned_array((sp_slots, 32), np.float64)
 
     def run(server, timed_arrivals):
-        free = queue.Queue()
+        free, free_sp = queue.Queue(), queue.Queue()
         for sl in range(slots):
             free.put(sl)
+        for sl in range(sp_slots):
+            free_sp.put(sl)
         recs = queue.Queue()
         errs = np.zeros(n_req)      # every triplet
         errs_env = np.zeros(n_req)  # triplets with sigma_i >= 0.1 sigma_0
@@ -1168,7 +1203,7 @@ def leg_serve(args, n_req: int):
                 serv[i] = info["done_s"] - info["launch_s"]
                 apps[i] = info["applications"]
                 done_t[i], sub_t[i], status[i] = info["done_s"], info["submit_s"], st
-                free.put(sl)
+                (free_sp if is_sp[i] else free).put(sl)
         ths = [threading.Thread(target=collector) for _ in range(n_coll)]
         for th in ths:
             th.start()
@@ -1178,12 +1213,12 @@ def leg_serve(args, n_req: int):
                 delay = start + arrivals[i] - time.perf_counter()
                 if delay > 0:
                     time.sleep(delay)
-            sl = free.get()
+            sl = (free_sp if is_sp[i] else free).get()
             k = int(ks[i])
             if is_sp[i]:
                 csr = sp_pool[sp_picks[i]]
                 m, n = csr["m"], csr["n"]
-                t = server.submit_csr(csr, k, SP_EPS, outU[sl, :m * k], outS[sl, :k], outV[sl, :n * k],
+                t = server.submit_csr(csr, k, SP_EPS, outUs[sl, :m * k], outSs[sl, :k], outVs[sl, :n * k],
                                       max_iter=SP_MAX_ITER, seed=i)
             else:
                 p = picks[i]
@@ -1259,7 +1294,7 @@ def leg_serve(args, n_req: int):
             csr = sp_pool[sp_picks[i]]
             m, n = csr["m"], csr["n"]
             plan = Plan(csr, k, SP_EPS, max_iter=SP_MAX_ITER, seed=i)
-            plan.factor(csr, U=outU[0, :m * k], sigma=outS[0, :k], V=outV[0, :n * k], ok=(B.TSVD_OK, B.TSVD_ENOCONV))
+            plan.factor(csr, U=outUs[0, :m * k], sigma=outSs[0, :k], V=outVs[0, :n * k], ok=(B.TSVD_OK, B.TSVD_ENOCONV))
         else:
             p = picks[i]
             m, n = shapes[p]["m"], shapes[p]["n"]
@@ -1279,6 +1314,7 @@ def leg_serve(args, n_req: int):
                                    f"k~U{{4..32}}, eps=1e-8; {args.csr_share:.0%} CSR from a pool of {n_sp_pool}: "
                                    f"m=n logU[2^{sp_lo},2^{sp_hi}], density 1e-4, eps={SP_EPS}, max_iter {SP_MAX_ITER}",
                        "requests": n_req, "sparse_requests": int(is_sp.sum()), "rate": rate, "pool": n_pool,
+                       "sparse_output_slots": sp_slots if n_sp_pool else 0,
                        "pool_bytes": int(sum(a.nbytes for a in pool)), "device_budget_gib": args.serve_budget},
             "accuracy_scope": f"sigma graded against the closed form rho^i on the triplets with rho^i >= {ENVELOPE} "
                               "(an FP32-accumulated Gram moves lambda_i by ~1e-7 lambda_0, i.e. sigma_i by "
@@ -1299,7 +1335,8 @@ def leg_serve(args, n_req: int):
             "wave_graphs": {"updated_in_place": s2["graph_updates"] - s0["graph_updates"],
                             "instantiated": s2["graph_instantiations"] - s0["graph_instantiations"]},
             "peak_device_bytes": s2["peak_device_bytes"], "gen_seconds": round(gen_s, 1), "clocks": clk}
-    for a in pool + [outU, outV, outS]:
+    del pool, sp_pool, sp_views
+    for a in (arena, sp_arena, outU, outV, outS, outUs, outVs, outSs):
         free_pinned(a)
     torch.cuda.empty_cache()
     return line
