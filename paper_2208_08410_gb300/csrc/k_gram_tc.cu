@@ -18,7 +18,8 @@
 //     lower triangle: the symmetric task reuse of Sec. V-C) and one slice of
 //     the K = row range.  Warp 0 streams 128-row (A operand) and 256-row
 //     (B operand) slabs of At into a 4-stage shared-memory ring with TMA
-//     (128-byte swizzle, no multicast); warp 1 issues tcgen05.mma kind::tf32
+//     (64-byte swizzle rows for the split precisions, 128-byte for plain
+//     TF32; no multicast); warp 1 issues tcgen05.mma kind::tf32
 //     (M=128, N=256, K=8) or kind::f16 with BF16 operands (K=16) into one of
 //     two 256-column TMEM accumulators, one
 //     short K segment at a time; warps 2-17 drain the other accumulator with
@@ -179,16 +180,34 @@ __device__ __forceinline__ void unit_tile(const TcArgs &a, int t, int &bi, int &
   }
 }
 
+// Stage geometry of the dense SYRK: one stage holds ROWB bytes of K (one
+// swizzle row) for the 128-row and 256-row slabs of every part.  The split
+// precisions take 64-byte rows (16 TF32 or 32 BF16 indices per stage, four
+// 48 KB stages); plain TF32 takes 128-byte rows (four 48 KB stages).  Both
+// fill 192 KB of shared memory; the shorter rows of the split precisions give
+// the TMA three stages of lead instead of one at the same bytes in flight.
+template <int PREC, int ROWB>
+struct Geo {
+  static constexpr int kParts = Cfg<PREC>::kParts;
+  static constexpr int kTK = ROWB / Cfg<PREC>::kElem;  // K rows per stage
+  static constexpr int kASlab = TM * ROWB, kBSlab = TN * ROWB;
+  static constexpr int kStageBytes = kParts * (kASlab + kBSlab);
+  static constexpr int kStages = (192 * 1024 / kStageBytes) < 8 ? 192 * 1024 / kStageBytes : 8;
+  static constexpr int kSmem = kStages * kStageBytes + 1024 /*align*/ + 256 /*barriers*/;
+  static constexpr int kMmaPerStage = ROWB / MMA_K_BYTES;  // MMAs per part product and stage
+};
+
 // The tensor core adds each MMA into the FP32 TMEM accumulator with a
 // directed (toward-zero) rounding, so a long accumulation chain drifts low by
 // about 0.4 ulp per MMA.  The accumulator is therefore restarted every
 // `seg_stages` stages (a segment of 16-48 MMAs) and the segment sums are
 // added into FP32 registers of the epilogue warps with round-to-nearest;
 // only the sum over a whole work unit goes to the FP64 G.
-template <int PREC>
+template <int PREC, int ROWB>
 __global__ void __launch_bounds__(TC_THREADS, 1)
 syrk_tc_kernel(const __grid_constant__ CUtensorMap map_hi, const __grid_constant__ CUtensorMap map_lo, TcArgs a) {
-  using C = Cfg<PREC>;
+  using C = Geo<PREC, ROWB>;
+  constexpr int A_SLAB = C::kASlab, B_SLAB = C::kBSlab;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char *smem = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint64_t *bars = reinterpret_cast<uint64_t *>(smem + C::kStages * C::kStageBytes);
@@ -282,13 +301,13 @@ syrk_tc_kernel(const __grid_constant__ CUtensorMap map_hi, const __grid_constant
             if (!mbar_wait(full0 + 8 * s, ph, a.err, a.wait_ns)) { ok = false; break; }
             tc_fence_after();
             const uint32_t st = smem_u32(smem + s * C::kStageBytes);
-            const uint64_t dah = umma_desc_sw128(st), dbh = umma_desc_sw128(st + A_SLAB);
+            const uint64_t dah = umma_desc_k<ROWB>(st), dbh = umma_desc_k<ROWB>(st + A_SLAB);
 #pragma unroll
-            for (int kq = 0; kq < ROW_BYTES / MMA_K_BYTES; ++kq) {
+            for (int kq = 0; kq < C::kMmaPerStage; ++kq) {
               const uint64_t off = (uint64_t)(kq * MMA_K_BYTES) >> 4;  // descriptor start, 16-byte units
               if (C::kParts == 2) {
                 const uint32_t sl = st + A_SLAB + B_SLAB;
-                const uint64_t dal = umma_desc_sw128(sl), dbl = umma_desc_sw128(sl + A_SLAB);
+                const uint64_t dal = umma_desc_k<ROWB>(sl), dbl = umma_desc_k<ROWB>(sl + A_SLAB);
                 umma<PREC>(dtm, dal + off, dbh + off, first ? 0u : 1u);  // small terms first
                 first = 0;
                 umma<PREC>(dtm, dah + off, dbl + off, 1u);
@@ -379,20 +398,24 @@ tsvd_status get_encode(EncodeTiledFn *out) {
   return TSVD_OK;
 }
 
-// At viewed as n rows of Kp elements; the box is one 128-byte swizzle row of K
-// by 128 rows (so every x coordinate the kernel passes is a multiple of 128 bytes)
-tsvd_status make_map(CUtensorMap *map, const void *base, int64_t n, int64_t Kp, int precision) {
+// At viewed as n rows of Kp elements; the box is one swizzle row of K (rowb =
+// 128 or 64 bytes) by 128 rows, so every x coordinate the kernel passes is a
+// multiple of rowb bytes
+tsvd_status make_map(CUtensorMap *map, const void *base, int64_t n, int64_t Kp, int precision, int rowb = 128) {
   EncodeTiledFn enc;
   TSVD_TRY(get_encode(&enc));
   const bool bf = precision == TSVD_GRAM_BF16X3;
   const int64_t elem = bf ? 2 : 4;
   const cuuint64_t dims[2] = {(cuuint64_t)Kp, (cuuint64_t)n};
   const cuuint64_t strides[1] = {(cuuint64_t)(Kp * elem)};
-  const cuuint32_t box[2] = {(cuuint32_t)(ROW_BYTES / elem), (cuuint32_t)TM};
+  if (rowb != 128 && rowb != 64) return TSVD_EINVAL;
+  const cuuint32_t box[2] = {(cuuint32_t)(rowb / elem), (cuuint32_t)TM};
   const cuuint32_t estr[2] = {1, 1};
   const CUresult r = enc(map, bf ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2,
                          const_cast<void *>(base), dims, strides, box, estr,
-                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                         CU_TENSOR_MAP_INTERLEAVE_NONE,
+                         rowb == 128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
+                         CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) {
     set_error_text("cuTensorMapEncodeTiled failed: " + std::to_string((int)r));
@@ -408,11 +431,12 @@ int64_t padded_k(int64_t rows, int precision) {
 int tc_parts(int precision) { return precision == TSVD_GRAM_TF32 ? 1 : 2; }
 int64_t tc_elem(int precision) { return precision == TSVD_GRAM_BF16X3 ? 2 : 4; }
 
-template <int PREC>
+template <int PREC, int ROWB>
 tsvd_status launch_syrk(const CUtensorMap &mh, const CUtensorMap &ml, const TcArgs &a, int grid,
                         cudaStream_t stream) {
-  TSVD_TRY(ensure_dynamic_smem(reinterpret_cast<const void *>(syrk_tc_kernel<PREC>), Cfg<PREC>::kSmem));
-  syrk_tc_kernel<PREC><<<grid, TC_THREADS, Cfg<PREC>::kSmem, stream>>>(mh, ml, a);
+  using G = Geo<PREC, ROWB>;
+  TSVD_TRY(ensure_dynamic_smem(reinterpret_cast<const void *>(syrk_tc_kernel<PREC, ROWB>), G::kSmem));
+  syrk_tc_kernel<PREC, ROWB><<<grid, TC_THREADS, G::kSmem, stream>>>(mh, ml, a);
   TSVD_LAUNCHED();
   return TSVD_OK;
 }
@@ -431,12 +455,27 @@ size_t gram_tc_scratch_bytes(int64_t rows, int64_t n, int precision) {
                     (size_t)round_up(n * padded_k(rows, precision) * tc_elem(precision), 1024);
 }
 
-// Stages per TMEM accumulation segment (bounds the truncation drift of one
-// FP32 accumulation chain to 16-24 MMAs); TSVD_TC_SEG overrides it.
-static int tc_seg_stages(int precision) {
+// Swizzle row bytes of the dense SYRK's stages: 64 for the split precisions,
+// 128 for plain TF32; TSVD_TC_ROW (64 or 128) overrides it.
+static int tc_row_bytes(int precision) {
+  const char *e = getenv("TSVD_TC_ROW");
+  if (e && (atoi(e) == 64 || atoi(e) == 128)) return atoi(e);
+  return precision == TSVD_GRAM_TF32 ? 128 : 64;
+}
+
+// K rows per stage of the dense SYRK
+static int tc_stage_k(int precision, int rowb) { return rowb / (precision == TSVD_GRAM_BF16X3 ? 2 : 4); }
+
+// Stages per TMEM accumulation segment: K rows per segment (bounds the
+// truncation drift of one FP32 accumulation chain to 16-24 MMAs: 128 rows of
+// TF32, 64 of 3xTF32, 128 of BF16x3) over the rows of a stage; TSVD_TC_SEG
+// overrides the rows per segment (a multiple of the stage's rows).
+static int tc_seg_stages(int precision, int rowb) {
+  const int tk = tc_stage_k(precision, rowb);
+  int rows = precision == TSVD_GRAM_TF32X3 ? 64 : 128;
   const char *e = getenv("TSVD_TC_SEG");
-  if (e) return std::max(1, atoi(e));
-  return precision == TSVD_GRAM_TF32 ? 4 : 2;
+  if (e) rows = std::max(tk, atoi(e));
+  return std::max(1, rows / tk);
 }
 
 namespace {
@@ -492,8 +531,8 @@ tsvd_status prep_raw(const float *A, int64_t rows, int64_t n, int64_t ld, int pr
 // K slices: about 8 units per SM balance the persistent grid; fewer, longer
 // units keep the FP64 reductions into G (one 128 x 256 tile per unit) small,
 // so slices are never shorter than 4096 rows
-void tc_ksplit(TcArgs &a, int precision, int sms) {
-  const int64_t quantum = (int64_t)stage_rows(precision) * a.seg_stages;
+void tc_ksplit(TcArgs &a, int precision, int rowb, int sms) {
+  const int64_t quantum = (int64_t)tc_stage_k(precision, rowb) * a.seg_stages;
   const int64_t want_units = 8LL * sms;
   int64_t splits = std::max<int64_t>(1, ceil_div(want_units, a.n_tiles));
   int64_t ks = round_up(ceil_div(a.Kp, splits), quantum);
@@ -507,10 +546,12 @@ void tc_ksplit(TcArgs &a, int precision, int sms) {
 tsvd_status run_syrk(const TcLayout &L, const TcArgs &a0, int precision, int sms, cudaStream_t stream,
                      cudaEvent_t ev0, cudaEvent_t ev1, bool reset_status) {
   TcArgs a = a0;
+  const int rowb = tc_row_bytes(precision);
+  a.seg_stages = tc_seg_stages(precision, rowb);
   CUtensorMap mh, ml;
-  TSVD_TRY(make_map(&mh, L.hi, a.n, a.Kp, precision));
-  TSVD_TRY(make_map(&ml, L.lo, a.n, a.Kp, precision));
-  tc_ksplit(a, precision, sms);
+  TSVD_TRY(make_map(&mh, L.hi, a.n, a.Kp, precision, rowb));
+  TSVD_TRY(make_map(&ml, L.lo, a.n, a.Kp, precision, rowb));
+  tc_ksplit(a, precision, rowb, sms);
   a.err = L.err;
   if (a.wait_ns == 0) a.wait_ns = kWaitLimitNs;
   if (reset_status) TSVD_CUDA(cudaMemsetAsync(L.err, 0, 4, stream));
@@ -518,11 +559,14 @@ tsvd_status run_syrk(const TcLayout &L, const TcArgs &a0, int precision, int sms
   const int grid = (int)std::min<int64_t>(units, sms);
   if (ev0) TSVD_CUDA(cudaEventRecord(ev0, stream));
   if (precision == TSVD_GRAM_TF32)
-    TSVD_TRY(launch_syrk<TSVD_GRAM_TF32>(mh, ml, a, grid, stream));
+    TSVD_TRY((rowb == 64 ? launch_syrk<TSVD_GRAM_TF32, 64>(mh, ml, a, grid, stream)
+                         : launch_syrk<TSVD_GRAM_TF32, 128>(mh, ml, a, grid, stream)));
   else if (precision == TSVD_GRAM_TF32X3)
-    TSVD_TRY(launch_syrk<TSVD_GRAM_TF32X3>(mh, ml, a, grid, stream));
+    TSVD_TRY((rowb == 64 ? launch_syrk<TSVD_GRAM_TF32X3, 64>(mh, ml, a, grid, stream)
+                         : launch_syrk<TSVD_GRAM_TF32X3, 128>(mh, ml, a, grid, stream)));
   else
-    TSVD_TRY(launch_syrk<TSVD_GRAM_BF16X3>(mh, ml, a, grid, stream));
+    TSVD_TRY((rowb == 64 ? launch_syrk<TSVD_GRAM_BF16X3, 64>(mh, ml, a, grid, stream)
+                         : launch_syrk<TSVD_GRAM_BF16X3, 128>(mh, ml, a, grid, stream)));
   if (ev1) TSVD_CUDA(cudaEventRecord(ev1, stream));
   return TSVD_OK;
 }
@@ -578,7 +622,6 @@ tsvd_status launch_gram_tc_syrk(int64_t rows, int64_t n, double *G, int precisio
   a.ldg = n;
   a.n = n;
   a.Kp = L.Kp;
-  a.seg_stages = tc_seg_stages(precision);
   a.n_iblk = (int)ceil_div(n, TM);
   a.wait_ns = wait_ns;
   {
@@ -610,7 +653,6 @@ tsvd_status launch_gram_tc_rect(const float *AJ, const float *AI, int64_t rows, 
   a.ldg = 2 * bs;
   a.n = 2 * bs;
   a.Kp = L.Kp;
-  a.seg_stages = tc_seg_stages(precision);
   a.n_iblk = (int)ceil_div(2 * bs, TM);
   a.rect_bi0 = (int)(bs / TM);
   a.rect_nbj = (int)ceil_div(nJ, TN);

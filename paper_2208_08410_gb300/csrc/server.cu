@@ -264,6 +264,7 @@ struct tsvd_server_s {
   std::deque<tsvd::ReqPtr> csr_pending;              // sparse requests, run by the sparse workers
   std::vector<std::thread> csr_workers;
   std::condition_variable cv_csr;
+  int csr_large_running = 0;                         // large sparse requests on the device now
   std::chrono::steady_clock::time_point t0;
   tsvd_server_stats stats{};
   std::string err;
@@ -900,6 +901,13 @@ tsvd_status time_syrk(tsvd_server_s *sv, int64_t d, int64_t K, int nreq, bool tc
   return ls;
 }
 
+// Sparse requests with at least this many stored entries run one operator
+// application per host round trip (the plan's explicit loop), with kernels
+// over every SM; smaller ones run each triplet in one cooperative launch.
+constexpr int64_t kLargeCsrNnz = (int64_t)1 << 25;
+// large sparse requests on the device at once
+constexpr int kLargeCsrConcurrent = 2;
+
 // A sparse request runs through the plan API on a stream of its worker: the
 // workspace comes from the server's device arena (first fit; the worker waits
 // while the arena is full), the outputs go straight into the caller's
@@ -907,18 +915,32 @@ tsvd_status time_syrk(tsvd_server_s *sv, int64_t d, int64_t K, int nreq, bool tc
 // keep running on their own streams meanwhile.
 void csr_worker(tsvd_server_s *sv) {
   cudaSetDevice(sv->device);
-  // the highest stream priority: a sparse request's cooperative launches wait for whole SMs,
-  // and the block scheduler then serves them before the dense waves' pending blocks
+  // small requests take the highest stream priority: their cooperative launches wait for
+  // whole SMs, and the block scheduler then serves them before the dense waves' pending
+  // blocks.  Large requests (seconds of back-to-back launches over every SM) take the
+  // default priority and run at most kLargeCsrConcurrent at a time, so that the dense
+  // waves keep their share of the SMs instead of queueing behind them.
   int lo = 0, hi = 0;
   cudaDeviceGetStreamPriorityRange(&lo, &hi);
-  cudaStream_t st = nullptr;
-  if (cudaStreamCreateWithPriority(&st, cudaStreamNonBlocking, hi) != cudaSuccess) return;
+  cudaStream_t st_hi = nullptr, st_lo = nullptr;
+  if (cudaStreamCreateWithPriority(&st_hi, cudaStreamNonBlocking, hi) != cudaSuccess) return;
+  if (cudaStreamCreateWithPriority(&st_lo, cudaStreamNonBlocking, lo) != cudaSuccess) {
+    cudaStreamDestroy(st_hi);
+    return;
+  }
   std::unique_lock<std::mutex> lk(sv->mu);
   while (true) {
     sv->cv_csr.wait(lk, [&] { return sv->stop || !sv->csr_pending.empty(); });
     if (sv->csr_pending.empty()) break;  // stop, nothing left
     ReqPtr r = sv->csr_pending.front();
     sv->csr_pending.pop_front();
+    const bool large = r->nnz >= kLargeCsrNnz;
+    if (large) {
+      // a stopping server still runs what was submitted (the destructor waits for it)
+      sv->cv_csr.wait(lk, [&] { return sv->csr_large_running < kLargeCsrConcurrent; });
+      ++sv->csr_large_running;
+    }
+    cudaStream_t st = large ? st_lo : st_hi;
     r->rec.admit_s = sv->now();
     lk.unlock();
     tsvd_matrix A{};
@@ -962,6 +984,10 @@ void csr_worker(tsvd_server_s *sv) {
     }
     if (plan) tsvd_destroy(plan);
     lk.lock();
+    if (large) {
+      --sv->csr_large_running;
+      sv->cv_csr.notify_all();
+    }
     if (have) sv->arena.release(off, std::max<size_t>(ws_bytes, 256));
     if (st_r != TSVD_OK && st_r != TSVD_ENOCONV && st_r != TSVD_ERANK)
       sv->err = std::string("server: sparse request failed: ") + tsvd_status_string(st_r) + " " + tsvd_last_cuda_error();
@@ -980,8 +1006,10 @@ void csr_worker(tsvd_server_s *sv) {
     sv->cv_done.notify_all();
   }
   lk.unlock();
-  cudaStreamSynchronize(st);
-  cudaStreamDestroy(st);
+  for (cudaStream_t st : {st_hi, st_lo}) {
+    cudaStreamSynchronize(st);
+    cudaStreamDestroy(st);
+  }
 }
 
 }  // namespace
@@ -1149,7 +1177,7 @@ tsvd_status tsvd_server_submit_csr(tsvd_server_t sv, const int64_t *row_ptr, con
     ++sv->stats.submitted;
     *ticket = r->id;
   }
-  sv->cv_csr.notify_one();
+  sv->cv_csr.notify_all();  // a worker may be parked on the large-request limit
   return TSVD_OK;
 }
 

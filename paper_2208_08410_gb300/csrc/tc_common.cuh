@@ -103,17 +103,23 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map
       : "memory");
 }
 
-// UMMA shared-memory descriptor: K-major operand, 128-byte swizzle, 8-row
-// core-matrix groups 1024 bytes apart (SBO), start address in 16-byte units.
-__device__ __forceinline__ uint64_t umma_desc_sw128(uint32_t saddr) {
+// UMMA shared-memory descriptor of a K-major operand whose rows are one
+// swizzle row of ROWB bytes (128-byte or 64-byte swizzle, as the TMA wrote
+// them): 8-row core-matrix groups 8 * ROWB bytes apart (SBO), start address in
+// 16-byte units.
+template <int ROWB>
+__device__ __forceinline__ uint64_t umma_desc_k(uint32_t saddr) {
+  static_assert(ROWB == 128 || ROWB == 64, "128- or 64-byte swizzle rows");
   uint64_t d = 0;
   d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
-  d |= (uint64_t)1 << 16;             // leading byte offset (unused for swizzled K-major)
-  d |= (uint64_t)(1024 >> 4) << 32;   // stride byte offset
-  d |= (uint64_t)1 << 46;             // descriptor version (sm_100 family)
-  d |= (uint64_t)2 << 61;             // swizzle mode: 128B
+  d |= (uint64_t)1 << 16;                      // leading byte offset (unused for swizzled K-major)
+  d |= (uint64_t)((8 * ROWB) >> 4) << 32;      // stride byte offset
+  d |= (uint64_t)1 << 46;                      // descriptor version (sm_100 family)
+  d |= (uint64_t)(ROWB == 128 ? 2 : 4) << 61;  // swizzle mode: 128B (2) or 64B (4)
   return d;
 }
+
+__device__ __forceinline__ uint64_t umma_desc_sw128(uint32_t saddr) { return umma_desc_k<128>(saddr); }
 
 // Instruction descriptor, kind::tf32: D F32, A/B TF32, both K-major, M x N.
 __host__ __device__ constexpr uint32_t idesc_tf32(int M, int N) {

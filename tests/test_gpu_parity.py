@@ -619,6 +619,21 @@ def _split_error(prec) -> float:
 def test_gram_tensor_cores_match_oracle(prec, rows, n, ld):
     """Products with the split error of the mode (_split_error), FP32
     accumulation over a K slice, then FP64.  Bound: (e_in + (K+2) 2^-23) (|A|^T |A|)."""
+    _check_gram_tc(prec, rows, n, ld)
+
+
+@pytest.mark.parametrize("prec", [B.TSVD_GRAM_TF32, B.TSVD_GRAM_TF32X3, B.TSVD_GRAM_BF16X3])
+@pytest.mark.parametrize("rowb", [64, 128])
+@pytest.mark.parametrize("rows,n,ld", [(5000, 300, 300), (300, 129, 133), (70, 640, 640)])
+def test_gram_tensor_cores_both_stage_layouts(prec, rowb, rows, n, ld, monkeypatch):
+    """Both stage layouts of the SYRK (64-byte and 128-byte swizzle rows of K,
+    TSVD_TC_ROW) meet the same bound, whichever one a precision takes by
+    default."""
+    monkeypatch.setenv("TSVD_TC_ROW", str(rowb))
+    _check_gram_tc(prec, rows, n, ld)
+
+
+def _check_gram_tc(prec, rows, n, ld):
     Afull = _tc_case(rows, n, ld, rows * 7 + n)
     A = Afull[:, :n]
     sentinel = -7.25
