@@ -646,25 +646,26 @@ def kernel_case(args):
     print(json.dumps(out), flush=True)
 
 
-def tf32_in_core(dA, args, m, res_ref, peaks):
-    """The same in-core step with the Gram in plain TF32 (one MMA per product;
-    reduced precision, reported beside the FP32-class headline, never as it):
-    throughput, SYRK fraction of the TF32 peak and the largest relative change
-    of sigma against the 3xTF32 run."""
-    import torch
-
+def alt_precision_in_core(dA, args, m, res_ref, peaks, prec):
+    """The same in-core step with the Gram in another tensor-core precision
+    (plain TF32: one MMA per product; BF16x3: three BF16 MMAs per product),
+    reported beside the FP32-class 3xTF32 headline, never as it: throughput,
+    SYRK fraction of that dtype's peak, the power phase's applications and the
+    largest relative change of sigma against the 3xTF32 run (whose own error
+    against the FP64 oracle the headline's parity fields give)."""
     from paper_2208_08410_gb300 import Plan
-    plan = Plan(dA, K, EPS, precision=1, out_device=True, time_kernels=True)
+    plan = Plan(dA, K, EPS, precision=prec, out_device=True, time_kernels=True)
     sec, wall, reps, res = time_steps(plan, dA, args.steps, args.warmup)
     plan.close()
     gk_ms = sum(r["gram_kernel_ms"] for r in reps)
     tf = m * N_COLS * (N_COLS + 1) * args.steps / (gk_ms / 1e3) / 1e12
-    peak, _, _ = dtype_peak(1, peaks, sustained=True, tf32_measured=getattr(measure_tf32_peak, "result", None))
+    peak, _, _ = dtype_peak(prec, peaks, sustained=True, tf32_measured=getattr(measure_tf32_peak, "result", None))
     s1 = np.asarray(res.sigma.cpu(), dtype=np.float64)
     s0 = np.asarray(res_ref.sigma.cpu(), dtype=np.float64)
     return {"value": round(2 * m * N_COLS * 4 * args.steps / sec / 1e9, 3), "unit": "GB/s",
             "ms_per_step": round(sec / args.steps * 1e3, 2), "syrk_tflops": round(tf, 1),
-            "syrk_frac_of_tf32_peak": round(tf / peak, 4),
+            f"syrk_frac_of_{PREC_NAMES[prec]}_peak": round(tf / peak, 4),
+            "applications": int(reps[-1]["applications"]) if "applications" in reps[-1] else None,
             "sigma_max_rel_diff_vs_tf32x3": float("%.3g" % np.max(np.abs(s1 - s0) / s0))}
 
 
@@ -1554,6 +1555,7 @@ def leg_c3(args, steps: int, warmup: int, with_cpu: bool = False, sweep: bool = 
             "e2e": {"value": round(e2e, 2), "unit": "GB/s", "ms_per_step": round(sec_e / nst * 1e3, 1),
                     "steps": nst, "pinned_copy_peak_GBps": round(h2d_peak, 2),
                     "host_values_pages": thp_coverage(hvals), "host_col_idx_pages": thp_coverage(hci),
+                    "host_row_ptr_pages": thp_coverage(hrp),
                     "frac_of_pinned_copy": round(e2e / h2d_peak, 4),
                     "h2d_bytes_per_step": int(reps_e[-1]["h2d_bytes"]),
                     "d2h_bytes_per_step": int(reps_e[-1]["d2h_bytes"]),
@@ -1699,9 +1701,11 @@ def main():
     plan_dev.close()
     del plan_dev
     torch.cuda.empty_cache()
-    alt = None
+    alt = alt_bf = None
     if prec == 2:
-        alt = tf32_in_core(dA, args, m, res_dev, peaks)
+        alt = alt_precision_in_core(dA, args, m, res_dev, peaks, 1)
+        torch.cuda.empty_cache()
+        alt_bf = alt_precision_in_core(dA, args, m, res_dev, peaks, 3)
         torch.cuda.empty_cache()
     small = c1_latency() if rank == 0 else None
 
@@ -1810,7 +1814,7 @@ def main():
                            "gram_precision": PREC_NAMES[prec] + (" (FP32-class split: hi*hi + hi*lo + lo*hi on the "
                                                                  "tensor cores, FP32 accumulate)" if prec == 2 else ""),
                            "parallelism": "replicas" if world > 1 else "1 GPU"},
-                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk, "tf32_in_core": alt,
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk, "tf32_in_core": alt, "bf16x3_in_core": alt_bf,
                 "c1_latency": small,
                 "gpu_launches": launches, "gpu_launches_e2e": launches_e,
                 "phases_ms": {"gram": round(reps[-1]["gram_ms"], 2), "power": round(reps[-1]["power_ms"], 2),

@@ -422,7 +422,9 @@ TSVD_API tsvd_status tsvd_csr_partition(int64_t m, const int64_t *row_ptr, int64
  * cudaHostRegister (portable: page-locked for every device).  With huge pages
  * the copy engines translate the range through a few hundred page-table
  * entries instead of millions, so row-block copies keep the link rate while
- * kernels run beside them.  *ptr is NULL on failure (TSVD_ENOMEM, or
+ * kernels run beside them.  From a quarter of a huge page up, the mapping is
+ * rounded up to whole huge pages (at most one huge page more than asked), so
+ * that its tail is not left on base pages.  *ptr is NULL on failure (TSVD_ENOMEM, or
  * TSVD_ECUDA when the registration fails).  Free with tsvd_host_free, which
  * accepts only pointers from tsvd_host_alloc (TSVD_EINVAL otherwise; NULL is
  * a no-op). */

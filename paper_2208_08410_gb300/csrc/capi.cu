@@ -77,8 +77,12 @@ tsvd_status pinned_alloc(void **ptr, size_t bytes) {
   if (bytes == 0) return TSVD_EINVAL;
   const size_t page = (size_t)sysconf(_SC_PAGESIZE);
   const size_t hp = std::max(thp_bytes(), page);
-  const size_t len = (bytes + page - 1) / page * page;
-  if (len > SIZE_MAX - hp) return TSVD_EINVAL;
+  if (bytes > SIZE_MAX - 2 * hp) return TSVD_EINVAL;
+  size_t len = (bytes + page - 1) / page * page;
+  // from a quarter of a huge page up, whole huge pages: the tail of a mapping
+  // that ends inside a huge page stays on base pages, and those copy slowly
+  // beside kernels on some hosts (every streamed pass pays for them again)
+  if (hp > page && len >= hp / 4) len = (len + hp - 1) / hp * hp;
   // map one huge page more than needed so the start can be aligned, then trim
   void *raw = mmap(nullptr, len + hp, PROT_READ | PROT_WRITE, MAP_PRIVATE | MAP_ANONYMOUS, -1, 0);
   if (raw == MAP_FAILED) {

@@ -13,6 +13,7 @@
 #include <cuda.h>
 
 #include <algorithm>
+#include <cstdlib>
 
 #include "common.cuh"
 
@@ -108,12 +109,14 @@ left_dense_kernel(const float *__restrict__ A, int64_t rows, int64_t n, int64_t 
 // Same arithmetic, but a persistent block streams 64-row x 128-column tiles
 // of A and the matching 128 x 16 tile of V^T into a four-stage shared-memory
 // ring with TMA, three tiles ahead, so HBM latency is hidden by the copy
-// engine instead of by warp occupancy.  Each of the 16 warps owns 4 rows of
-// the tile (4 x 16 accumulators per thread).
-constexpr int TT = 512;                         // threads (16 warps)
-constexpr int TRW = 4;                          // rows per warp
+// engine instead of by warp occupancy.  Each warp owns RW rows of the tile
+// (RW x 16 accumulators per thread): 8 warps of 8 rows by default.  Per
+// 128-column chunk a thread reads RW float4 of A and 16 float4 of V^T from
+// shared memory for 64 RW FMAs, so 8 rows per warp move 96 KB of shared
+// memory per chunk and SM (16 warps of 4 rows: 160 KB), below the 32 KB of A
+// the chunk brings from HBM at the link's pace.
 constexpr int TLH = 16;                         // columns of V per sweep
-constexpr int TR = 64;                          // rows per tile
+constexpr int TR = 64;                          // rows per tile (warps x RW)
 constexpr int TJ = 128;                         // columns per chunk (32 lanes x 4)
 constexpr int T_ABYTES = TR * TJ * 4;           // 32 KB
 constexpr int T_VBYTES = LK * TJ * 4;           // 8 KB
@@ -153,7 +156,8 @@ __device__ __forceinline__ bool mbar_drain_l(uint32_t bar, uint32_t parity) {
   }
 }
 
-__global__ void __launch_bounds__(TT, 1)
+template <int RW>
+__global__ void __launch_bounds__(TR / RW * 32, 1)
 left_tma_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapV, int64_t rows,
                 int64_t n, int64_t k, const double *__restrict__ sigma, float *__restrict__ U, int64_t ldu, int l0) {
   extern __shared__ __align__(1024) unsigned char smraw[];
@@ -186,6 +190,7 @@ left_tma_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
   if (threadIdx.x == 0) {
     for (int64_t c = 0; c < T_NST - 1 && c < total; ++c) issue(c);
   }
+  constexpr int TRW = RW;
   float acc[1][TRW][TLH];
   bool ok = true;
   int64_t stop = total;  // the chunk at which a failed wait ended the loop
@@ -347,6 +352,12 @@ tsvd_status launch_left_trans(const float *A, int64_t K, int64_t d, int64_t ld, 
   return TSVD_OK;
 }
 
+// Rows per warp of the TMA kernel: 8, or 4 with TSVD_LEFT_RW=4
+static int left_rows_per_warp() {
+  const char *e = getenv("TSVD_LEFT_RW");
+  return e && atoi(e) == 4 ? 4 : 8;
+}
+
 tsvd_status launch_left_dense(const float *A, int64_t rows, int64_t n, int64_t ld, const float *V,
                               int64_t ldv, int64_t k, const double *sigma, float *U, int64_t ldu,
                               cudaStream_t stream) {
@@ -365,10 +376,15 @@ tsvd_status launch_left_dense(const float *A, int64_t rows, int64_t n, int64_t l
       CUtensorMap ma, mv;
       TSVD_TRY(encode_2d(&ma, A, n, rows, ld, TJ, TR));
       TSVD_TRY(encode_2d(&mv, V, n, k, ldv, TJ, LK));
-      TSVD_TRY(ensure_dynamic_smem(reinterpret_cast<const void *>(left_tma_kernel), T_SMEM));
       const int64_t tiles = ceil_div(rows, TR);
       const int grid = (int)std::min<int64_t>(tiles, di.sms);
-      left_tma_kernel<<<grid, TT, T_SMEM, stream>>>(ma, mv, rows, n, k, sigma, U, ldu, (int)l0);
+      if (left_rows_per_warp() == 4) {
+        TSVD_TRY(ensure_dynamic_smem(reinterpret_cast<const void *>(left_tma_kernel<4>), T_SMEM));
+        left_tma_kernel<4><<<grid, TR / 4 * 32, T_SMEM, stream>>>(ma, mv, rows, n, k, sigma, U, ldu, (int)l0);
+      } else {
+        TSVD_TRY(ensure_dynamic_smem(reinterpret_cast<const void *>(left_tma_kernel<8>), T_SMEM));
+        left_tma_kernel<8><<<grid, TR / 8 * 32, T_SMEM, stream>>>(ma, mv, rows, n, k, sigma, U, ldu, (int)l0);
+      }
       TSVD_LAUNCHED();
     } else {
       left_dense_kernel<<<(unsigned)blocks, LT, 0, stream>>>(A, rows, n, ld, V, ldv, k, sigma, U, ldu, (int)l0,

@@ -194,6 +194,19 @@ def test_power_dense_rank_deficient():
 # ---------------------------------------------------------------- a6 left vectors
 @pytest.mark.parametrize("rows,n,k", [(1000, 300, 20), (37, 64, 3), (513, 256, 16)])
 def test_left_vectors_match_oracle(rows, n, k):
+    _check_left(rows, n, k)
+
+
+@pytest.mark.parametrize("rw", [4, 8])
+@pytest.mark.parametrize("rows,n,k", [(1000, 300, 20), (4133, 1000, 16), (20000, 4096, 7)])
+def test_left_vectors_both_warp_shapes(rw, rows, n, k, monkeypatch):
+    """The TMA kernel with 4 or 8 rows per warp (TSVD_LEFT_RW): many tiles per
+    block, a ragged last tile and chunk, and k below and above one sweep."""
+    monkeypatch.setenv("TSVD_LEFT_RW", str(rw))
+    _check_left(rows, n, k)
+
+
+def _check_left(rows, n, k):
     rng = np.random.default_rng(rows)
     A = rng.standard_normal((rows, n)).astype(np.float32)
     V = rng.standard_normal((n, k)).astype(np.float32)
