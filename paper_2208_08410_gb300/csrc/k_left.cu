@@ -262,12 +262,204 @@ left_tma_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
   __syncthreads();
 }
 
+// ---------------------------------------------------------------- tensor-core variant
+// The same product on the tensor cores: mma.sync m16n8k8 with TF32 operands
+// in the 3xTF32 split (x = hi + lo, hi = tf32(x), lo = tf32(x - hi); the
+// products hi*hi + hi*lo + lo*hi carry the FP32 product to ~2^-20, Ootomo &
+// Yokota 2022; split_tf32 below).  A persistent block of 8 warps streams the same 64-row x
+// 128-column tiles of A and 16 x 128 tiles of V^T through a four-stage TMA
+// ring, now as 32-column boxes with the 128-byte swizzle, so the fragment
+// loads below are free of bank conflicts.  Warp w owns rows 16 (w & 3) ..
+// +15 of the tile and columns 64 (w >> 2) .. +63 of every chunk (eight
+// k-steps of 8); per k-step it loads one A fragment and two V^T fragments
+// (16 columns of U), splits them and issues 6 MMAs into three accumulators
+// per column tile (one per product: three independent chains).  The tensor
+// core rounds its accumulation toward zero, so the accumulators are
+// restarted every chunk (8 MMAs each) and added into FP32 sums with
+// round-to-nearest.  At the end of a tile the two warps of a row group add
+// their halves through shared memory and write U.
+constexpr int MW = 8;                            // warps
+constexpr int M_SUB = 32;                        // floats per swizzled box row (128 bytes)
+constexpr int M_ASUB = TR * M_SUB * 4;           // 8 KB: one 64 x 32 box of A
+constexpr int M_VSUB = LK * M_SUB * 4;           // 2 KB: one 16 x 32 box of V^T
+constexpr int M_STAGE = 4 * M_ASUB + 4 * M_VSUB; // 40 KB: a 64 x 128 chunk of A, 16 x 128 of V^T
+constexpr int M_RED = MW * 32 * 8 * 4;           // 8 KB: partial sums of the k-halves
+constexpr int M_NST = 4;                         // stages (three chunks in flight)
+constexpr int M_SMEM = M_NST * M_STAGE + M_RED + 1024 + 64;
+
+// byte offset of element (r, c) of a box of 32-float rows written with the 128-byte swizzle
+__device__ __forceinline__ uint32_t sw128(int r, int c) {
+  return (uint32_t)(r * 128 + ((((c >> 2) ^ r) & 7) << 4) + ((c & 3) << 2));
+}
+
+// x = hi + lo: hi is x rounded to TF32's 10 stored mantissa bits (nearest, ties
+// away from zero) by an integer add and mask, lo = x - hi exactly (|lo| <=
+// 2^-11 |x|), passed as FP32: the tensor core reads its top 19 bits, so the
+// split drops at most 2^-21 |x|.  (|x| within 2^-11 of FLT_MAX would round hi
+// to infinity; such A overflows the Gram matrix long before.)
+__device__ __forceinline__ void split_tf32(float x, uint32_t &hi, uint32_t &lo) {
+  hi = (__float_as_uint(x) + 0x1000u) & 0xFFFFE000u;
+  lo = __float_as_uint(x - __uint_as_float(hi));
+}
+
+__device__ __forceinline__ void mma_tf32(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
+      "{%0, %1, %2, %3};"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+__global__ void __launch_bounds__(MW * 32, 1)
+left_mma_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapV, int64_t rows,
+                int64_t n, int64_t k, const double *__restrict__ sigma, float *__restrict__ U, int64_t ldu, int l0) {
+  extern __shared__ __align__(1024) unsigned char smraw[];
+  unsigned char *sm = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smraw) + 1023) & ~uintptr_t(1023));
+  float *red = reinterpret_cast<float *>(sm + M_NST * M_STAGE);
+  uint64_t *full = reinterpret_cast<uint64_t *>(sm + M_NST * M_STAGE + M_RED);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int g = lane >> 2, q = lane & 3;         // fragment row group and thread in group
+  const int rg = warp & 3, kh = warp >> 2;       // row group (16 rows) and k-half of a chunk
+  const int64_t tiles = ceil_div_dev(rows, TR);
+  const int64_t chunks = ceil_div_dev(n, TJ);
+  const int kc = (int)min((int64_t)LK, k - l0);
+  if (threadIdx.x == 0) {
+    for (int b = 0; b < M_NST; ++b)
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(full + b)) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  const int64_t my_tiles = tiles > blockIdx.x ? ceil_div_dev(tiles - blockIdx.x, gridDim.x) : 0;
+  const int64_t total = my_tiles * chunks;
+  // the four columns of U this lane writes (D fragment: 2q, 2q + 1 of both column tiles)
+  // and their 1 / sigma (0 where sigma is 0: a zero column)
+  float inv[2][2];
+#pragma unroll
+  for (int nt = 0; nt < 2; ++nt)
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+      const int t = nt * 8 + 2 * q + e;
+      const double sg = t < kc ? __ldg(sigma + l0 + t) : 0.0;
+      inv[nt][e] = sg > 0.0 ? (float)(1.0 / sg) : 0.f;
+    }
+  auto issue = [&](int64_t c) {  // chunk sequence number c -> stage c % M_NST
+    const int64_t tile = blockIdx.x + (c / chunks) * gridDim.x;
+    const int j0 = (int)((c % chunks) * TJ);
+    const uint32_t st = su32(sm + (c % M_NST) * M_STAGE);
+    const uint32_t bar = su32(full + (c % M_NST));
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(M_STAGE) : "memory");
+#pragma unroll
+    for (int s = 0; s < 4; ++s) {
+      asm volatile(
+          "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+              st + s * M_ASUB),
+          "l"(reinterpret_cast<uint64_t>(&mapA)), "r"(j0 + s * M_SUB), "r"((int)(tile * TR)), "r"(bar)
+          : "memory");
+      asm volatile(
+          "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+              st + 4 * M_ASUB + s * M_VSUB),
+          "l"(reinterpret_cast<uint64_t>(&mapV)), "r"(j0 + s * M_SUB), "r"(l0), "r"(bar)
+          : "memory");
+    }
+  };
+  int64_t issued = 0;  // chunks issued so far (thread 0)
+  if (threadIdx.x == 0) {
+    for (; issued < M_NST - 1 && issued < total; ++issued) issue(issued);
+  }
+  float sum[2][4];
+  bool ok = true;
+  int64_t stop = total;
+  for (int64_t c = 0; c < total; ++c) {
+    const int64_t cj = c % chunks;
+    if (cj == 0) {
+#pragma unroll
+      for (int nt = 0; nt < 2; ++nt)
+#pragma unroll
+        for (int e = 0; e < 4; ++e) sum[nt][e] = 0.f;
+    }
+    // stage (c + M_NST - 1) % M_NST was released by the barrier at the end of iteration c - 1
+    if (threadIdx.x == 0 && issued < total) issue(issued++);
+    if (!mbar_wait_l(su32(full + (c % M_NST)), (uint32_t)((c / M_NST) & 1))) ok = false;
+    if (__syncthreads_or(!ok)) {
+      stop = c;
+      break;
+    }
+    const unsigned char *As = sm + (c % M_NST) * M_STAGE;
+    const unsigned char *Vs = As + 4 * M_ASUB;
+    float acc[3][2][4];  // [product][column tile]: six independent chains
+#pragma unroll
+    for (int p = 0; p < 3; ++p)
+#pragma unroll
+      for (int nt = 0; nt < 2; ++nt)
+#pragma unroll
+        for (int e = 0; e < 4; ++e) acc[p][nt][e] = 0.f;
+#pragma unroll
+    for (int ks = 0; ks < 8; ++ks) {
+      const int col = kh * 64 + ks * 8;          // first column of this k-step within the chunk
+      const unsigned char *ab = As + (col >> 5) * M_ASUB;
+      const unsigned char *vb = Vs + (col >> 5) * M_VSUB;
+      const int cc = col & 31;
+      const int r0 = rg * 16 + g;
+      uint32_t ah[4], al[4];
+      split_tf32(*reinterpret_cast<const float *>(ab + sw128(r0, cc + q)), ah[0], al[0]);
+      split_tf32(*reinterpret_cast<const float *>(ab + sw128(r0 + 8, cc + q)), ah[1], al[1]);
+      split_tf32(*reinterpret_cast<const float *>(ab + sw128(r0, cc + q + 4)), ah[2], al[2]);
+      split_tf32(*reinterpret_cast<const float *>(ab + sw128(r0 + 8, cc + q + 4)), ah[3], al[3]);
+#pragma unroll
+      for (int nt = 0; nt < 2; ++nt) {
+        const int t = nt * 8 + g;                // column of U (row of V^T)
+        uint32_t bh0, bl0, bh1, bl1;
+        split_tf32(*reinterpret_cast<const float *>(vb + sw128(t, cc + q)), bh0, bl0);
+        split_tf32(*reinterpret_cast<const float *>(vb + sw128(t, cc + q + 4)), bh1, bl1);
+        mma_tf32(acc[0][nt], al, bh0, bh1);      // small terms in their own chains
+        mma_tf32(acc[1][nt], ah, bl0, bl1);
+        mma_tf32(acc[2][nt], ah, bh0, bh1);
+      }
+    }
+#pragma unroll
+    for (int nt = 0; nt < 2; ++nt)
+#pragma unroll
+      for (int e = 0; e < 4; ++e) sum[nt][e] += (acc[0][nt][e] + acc[1][nt][e]) + acc[2][nt][e];
+    __syncthreads();  // every warp is done with this stage before it is refilled
+    if (cj == chunks - 1) {
+      // the k-half 1 warps hand their sums to the k-half 0 warps of the same row group
+      float *rp = red + (rg * 32 + lane) * 8;
+      if (kh == 1) {
+#pragma unroll
+        for (int nt = 0; nt < 2; ++nt)
+#pragma unroll
+          for (int e = 0; e < 4; ++e) rp[nt * 4 + e] = sum[nt][e];
+      }
+      __syncthreads();
+      if (kh == 0) {
+        const int64_t tile = blockIdx.x + (c / chunks) * gridDim.x;
+#pragma unroll
+        for (int nt = 0; nt < 2; ++nt)
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            const int t = nt * 8 + 2 * q + (e & 1);                   // D fragment: column 2q (+1)
+            const int64_t row = tile * TR + rg * 16 + g + (e >> 1) * 8;  // rows g and g + 8
+            const float v = sum[nt][e] + rp[nt * 4 + e];
+            if (t < kc && row < rows) U[row + (int64_t)(l0 + t) * ldu] = v * inv[nt][e & 1];
+          }
+      }
+      __syncthreads();  // red is free again
+    }
+  }
+  // after an early stop, chunks stop .. issued - 1 were issued and not all waited for
+  if (stop < total && threadIdx.x == 0) {
+    for (int64_t j = stop; j < issued; ++j) mbar_drain_l(su32(full + (j % M_NST)), (uint32_t)((j / M_NST) & 1));
+  }
+  __syncthreads();
+}
+
 typedef CUresult (*EncodeTiledFnL)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
                                    const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
                                    CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
 
 tsvd_status encode_2d(CUtensorMap *map, const float *base, int64_t inner, int64_t outer, int64_t stride_elems,
-                      uint32_t box_inner, uint32_t box_outer) {
+                      uint32_t box_inner, uint32_t box_outer,
+                      CUtensorMapSwizzle swz = CU_TENSOR_MAP_SWIZZLE_NONE) {
   static EncodeTiledFnL fn = nullptr;
   if (!fn) {
     void *p = nullptr;
@@ -281,7 +473,7 @@ tsvd_status encode_2d(CUtensorMap *map, const float *base, int64_t inner, int64_
   const cuuint32_t box[2] = {box_inner, box_outer};
   const cuuint32_t es[2] = {1, 1};
   const CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float *>(base), dims, strides, box, es,
-                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, swz, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS ? TSVD_OK : TSVD_ECUDA;
 }
@@ -352,10 +544,16 @@ tsvd_status launch_left_trans(const float *A, int64_t K, int64_t d, int64_t ld, 
   return TSVD_OK;
 }
 
-// Rows per warp of the TMA kernel: 8, or 4 with TSVD_LEFT_RW=4
+// Rows per warp of the CUDA-core TMA kernel: 8, or 4 with TSVD_LEFT_RW=4
 static int left_rows_per_warp() {
   const char *e = getenv("TSVD_LEFT_RW");
   return e && atoi(e) == 4 ? 4 : 8;
+}
+
+// The TMA-fed form: tensor cores (3xTF32 mma.sync), or the CUDA cores with TSVD_LEFT_MMA=0
+static bool left_use_mma() {
+  const char *e = getenv("TSVD_LEFT_MMA");
+  return !(e && atoi(e) == 0);
 }
 
 tsvd_status launch_left_dense(const float *A, int64_t rows, int64_t n, int64_t ld, const float *V,
@@ -372,7 +570,16 @@ tsvd_status launch_left_dense(const float *A, int64_t rows, int64_t n, int64_t l
   const bool tma = vec && di.cc_major == 10 && (ldv % 4 == 0) && ((reinterpret_cast<uintptr_t>(V) & 15) == 0) &&
                    rows >= TR && n >= 64;
   for (int64_t l0 = 0; l0 < k; l0 += LK) {
-    if (tma) {
+    if (tma && left_use_mma()) {
+      CUtensorMap ma, mv;
+      TSVD_TRY(encode_2d(&ma, A, n, rows, ld, M_SUB, TR, CU_TENSOR_MAP_SWIZZLE_128B));
+      TSVD_TRY(encode_2d(&mv, V, n, k, ldv, M_SUB, LK, CU_TENSOR_MAP_SWIZZLE_128B));
+      const int64_t tiles = ceil_div(rows, TR);
+      const int grid = (int)std::min<int64_t>(tiles, di.sms);
+      TSVD_TRY(ensure_dynamic_smem(reinterpret_cast<const void *>(left_mma_kernel), M_SMEM));
+      left_mma_kernel<<<grid, MW * 32, M_SMEM, stream>>>(ma, mv, rows, n, k, sigma, U, ldu, (int)l0);
+      TSVD_LAUNCHED();
+    } else if (tma) {
       CUtensorMap ma, mv;
       TSVD_TRY(encode_2d(&ma, A, n, rows, ld, TJ, TR));
       TSVD_TRY(encode_2d(&mv, V, n, k, ldv, TJ, LK));
