@@ -1605,7 +1605,7 @@ def main():
     ap.add_argument("--pool", type=int, default=512)
     ap.add_argument("--requests", type=int, default=10_000)
     ap.add_argument("--rate", type=float, default=2000.0)
-    ap.add_argument("--serve-budget", type=int, default=48, help="server device budget, GiB")
+    ap.add_argument("--serve-budget", type=int, default=128, help="server device budget, GiB")
     ap.add_argument("--baseline-requests", type=int, default=200)
     ap.add_argument("--csr-share", type=float, default=0.1, help="serving: fraction of sparse requests")
     ap.add_argument("--csr-iters", type=int, default=10)
@@ -1619,7 +1619,7 @@ def main():
     ap.add_argument("--e2e-block-rows", type=int, default=BLOCK_ROWS, help="rows per streamed block (e2e)")
     ap.add_argument("--full-oracle", action="store_true",
                     help="dense: the oracle's trajectory over all of A (FP64 Gram on the host, ~5 min on 16 cores)")
-    ap.add_argument("--serve-streams", type=int, default=4, help="serving: waves in flight (streams)")
+    ap.add_argument("--serve-streams", type=int, default=8, help="serving: waves in flight (streams)")
     ap.add_argument("--serve-max-wave", type=int, default=256, help="serving: requests per wave")
     ap.add_argument("--serve-heavy-dim", type=int, default=0, help="serving: heavy lane above this d (0: none)")
     ap.add_argument("--serve-sparse-pool", type=int, default=0, help="serving: distinct sparse matrices (0: pool/8)")
