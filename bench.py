@@ -1339,7 +1339,12 @@ def leg_serve(args, n_req: int):
             "server": {"streams": args.serve_streams, "max_wave": args.serve_max_wave,
                        "heavy_dim": args.serve_heavy_dim if args.serve_heavy_dim > 0 else None,
                        "heavy_streams": args.serve_heavy_streams or "auto",
-                       "busy_s": round(s2.get("busy_s", 0.0) - s0.get("busy_s", 0.0), 3)},
+                       "busy_s": round(s2.get("busy_s", 0.0) - s0.get("busy_s", 0.0), 3),
+                       "wave_host_s": round(s2.get("wave_host_s", 0.0) - s0.get("wave_host_s", 0.0), 3),
+                       "wave_host_ms_per_wave": round(1e3 * (s2.get("wave_host_s", 0.0) - s0.get("wave_host_s", 0.0))
+                                                      / max(s2["waves"] - s0["waves"], 1), 3),
+                       "graph_host_s": round(s2.get("graph_host_s", 0.0) - s0.get("graph_host_s", 0.0), 3),
+                       "peak_streams_busy": s2.get("peak_streams_busy")},
             "waves": s2["waves"] - s0["waves"], "gpu_launches": launches,
             "wave_graphs": {"updated_in_place": s2["graph_updates"] - s0["graph_updates"],
                             "instantiated": s2["graph_instantiations"] - s0["graph_instantiations"]},

@@ -488,6 +488,13 @@ typedef struct {
                                   slot's instantiated graph in place */
   int64_t graph_instantiations;/* waves whose graph had a new shape and was
                                   instantiated */
+  double wave_host_s;          /* scheduler time spent forming and launching waves
+                                  (descriptors, copies, capture, graph update or
+                                  instantiation, launch) */
+  int64_t peak_streams_busy;   /* most streams with a wave in flight at once */
+  double graph_host_s;         /* the part of wave_host_s spent capturing and updating
+                                  or instantiating the waves' graphs (with graphs
+                                  off: enqueuing the launches) */
 } tsvd_server_stats;
 
 TSVD_API tsvd_status tsvd_server_options_init(tsvd_server_options *opt);

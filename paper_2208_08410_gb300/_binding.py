@@ -65,7 +65,8 @@ class tsvd_server_stats(C.Structure):
     _fields_ = [("submitted", C.c_int64), ("completed", C.c_int64), ("failed", C.c_int64),
                 ("waves", C.c_int64), ("kernel_launches", C.c_int64), ("peak_device_bytes", C.c_int64),
                 ("busy_s", C.c_double), ("graph_updates", C.c_int64),
-                ("graph_instantiations", C.c_int64)]
+                ("graph_instantiations", C.c_int64), ("wave_host_s", C.c_double),
+                ("peak_streams_busy", C.c_int64), ("graph_host_s", C.c_double)]
 
 
 _P = C.c_void_p

@@ -27,6 +27,7 @@
 #include <algorithm>
 #include <atomic>
 #include <chrono>
+#include <cstdlib>
 #include <condition_variable>
 #include <cstring>
 #include <deque>
@@ -229,9 +230,24 @@ struct Slot {  // one stream and the page-locked descriptors of the wave it runs
   std::vector<ReqPtr> reqs;
   size_t dev_off = 0, dev_bytes = 0;  // descriptor arrays in the device arena
   int64_t wave = 0;
-  cudaGraphExec_t exec = nullptr;     // the kernel part of the last wave, updated wave by wave
-  std::vector<int32_t> shape;         // its launch signature (see launch_wave)
+  // the kernel part of its waves as instantiated graphs, one per launch signature (see
+  // launch_wave), the least recently used replaced when kSlotGraphs are held
+  struct Graph {
+    std::vector<int32_t> shape;
+    cudaGraphExec_t exec = nullptr;
+    uint64_t used = 0;
+  };
+  std::vector<Graph> graphs;
+  uint64_t uses = 0;
 };
+constexpr size_t kSlotGraphs = 8;
+
+// Waves as captured graphs (the default) or as plain launches on the slot's stream
+// (TSVD_SERVER_GRAPHS=0)
+bool server_graphs() {
+  const char *e = getenv("TSVD_SERVER_GRAPHS");
+  return !(e && atoi(e) == 0);
+}
 
 }  // namespace
 }  // namespace tsvd
@@ -462,6 +478,29 @@ tsvd_status launch_wave(tsvd_server_s *sv, Slot &s) {
   // (the same launches with other sizes and pointers) update the slot's instantiated graph in
   // place; a new shape instantiates it again.
   const SrvReq *dreq = reinterpret_cast<const SrvReq *>(dev);
+  const auto g0 = std::chrono::steady_clock::now();
+  auto graph_time = [&]() {
+    const double t = std::chrono::duration<double>(std::chrono::steady_clock::now() - g0).count();
+    std::lock_guard<std::mutex> lk(sv->mu);
+    sv->stats.graph_host_s += t;
+  };
+  if (!server_graphs()) {
+    TSVD_CUDA(cudaMemcpyAsync(dev, s.stage, need, cudaMemcpyHostToDevice, st));
+    TSVD_TRY(launch_tc_wave(tw, dreq, dev + o_tc, derr, st));
+    TSVD_TRY(launch_srv_syrk(dreq, reinterpret_cast<const SrvTile *>(dev + b_req), (int)tiles.size(), st));
+    for (size_t i = 0; i < rs.size();) {
+      size_t j = i, smem = 0;
+      while (j < rs.size() && rs[j]->dq.cluster == rs[i]->dq.cluster && rs[j]->dq.resident == rs[i]->dq.resident) {
+        smem = std::max(smem, srv_power_smem(std::min(rs[j]->m, rs[j]->n), rs[j]->dq.cluster, rs[j]->dq.resident));
+        ++j;
+      }
+      TSVD_TRY(launch_srv_power(dreq + i, (int)(j - i), rs[i]->dq.cluster, smem, st));
+      i = j;
+    }
+    graph_time();
+    TSVD_CUDA(cudaEventRecord(s.done, st));
+    return TSVD_OK;
+  }
   TSVD_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeRelaxed));
   auto enqueue = [&]() -> tsvd_status {
     TSVD_CUDA(cudaMemcpyAsync(dev, s.stage, need, cudaMemcpyHostToDevice, st));
@@ -497,35 +536,46 @@ tsvd_status launch_wave(tsvd_server_s *sv, Slot &s) {
     shape.push_back(rs[i]->dq.cluster * 2 + rs[i]->dq.resident);
     i = j;
   }
+  size_t gi = s.graphs.size();
+  for (size_t x = 0; x < s.graphs.size(); ++x)
+    if (s.graphs[x].shape == shape) gi = x;
   bool updated = false;
-  if (s.exec && s.shape != shape) {
-    cudaGraphExecDestroy(s.exec);
-    s.exec = nullptr;
-  }
-  s.shape = shape;
-  if (s.exec) {
+  if (gi < s.graphs.size()) {
     cudaGraphExecUpdateResultInfo info;
-    updated = cudaGraphExecUpdate(s.exec, g, &info) == cudaSuccess;
+    updated = cudaGraphExecUpdate(s.graphs[gi].exec, g, &info) == cudaSuccess;
     if (!updated) {
       cudaGetLastError();
-      cudaGraphExecDestroy(s.exec);
-      s.exec = nullptr;
+      cudaGraphExecDestroy(s.graphs[gi].exec);
+      s.graphs[gi].exec = nullptr;
     }
+  } else if (s.graphs.size() < kSlotGraphs) {
+    s.graphs.emplace_back();
+  } else {
+    gi = 0;  // the least recently used signature makes room
+    for (size_t x = 1; x < s.graphs.size(); ++x)
+      if (s.graphs[x].used < s.graphs[gi].used) gi = x;
+    cudaGraphExecDestroy(s.graphs[gi].exec);
+    s.graphs[gi].exec = nullptr;
   }
+  Slot::Graph &ge = s.graphs[gi];
+  ge.shape = shape;
   if (!updated) {
-    const cudaError_t ie = cudaGraphInstantiate(&s.exec, g, 0);
+    const cudaError_t ie = cudaGraphInstantiate(&ge.exec, g, 0);
     if (ie != cudaSuccess) {
       cudaGraphDestroy(g);
-      s.exec = nullptr;
+      ge.exec = nullptr;
+      s.graphs.erase(s.graphs.begin() + (std::ptrdiff_t)gi);
       TSVD_CUDA(ie);
     }
   }
+  ge.used = ++s.uses;
   cudaGraphDestroy(g);
+  graph_time();
   {
     std::lock_guard<std::mutex> lk(sv->mu);
     ++(updated ? sv->stats.graph_updates : sv->stats.graph_instantiations);
   }
-  TSVD_CUDA(cudaGraphLaunch(s.exec, st));
+  TSVD_CUDA(cudaGraphLaunch(ge.exec, st));
   TSVD_CUDA(cudaEventRecord(s.done, st));
   return TSVD_OK;
 }
@@ -706,9 +756,17 @@ void scheduler(tsvd_server_s *sv) {
         r->rec.launch_s = t;
         r->rec.wave = (int32_t)s.wave;
       }
+      {
+        int64_t nb = 0;
+        for (auto &o : sv->slots) nb += o.busy ? 1 : 0;
+        sv->stats.peak_streams_busy = std::max(sv->stats.peak_streams_busy, nb);
+      }
       lk.unlock();
+      const auto h0 = std::chrono::steady_clock::now();
       const tsvd_status st = launch_wave(sv, s);
+      const double hs = std::chrono::duration<double>(std::chrono::steady_clock::now() - h0).count();
       lk.lock();
+      sv->stats.wave_host_s += hs;
       for (auto &r : s.reqs) {
         r->rec.cluster = r->dq.cluster;
         if (st == TSVD_OK) sv->running.push_back(r);
@@ -1377,7 +1435,8 @@ void tsvd_server_destroy(tsvd_server_t sv) {
   sv->cv_done.notify_all();
   for (auto &s : sv->slots) {
     if (s.stream) cudaStreamSynchronize(s.stream);
-    if (s.exec) cudaGraphExecDestroy(s.exec);
+    for (auto &x : s.graphs)
+      if (x.exec) cudaGraphExecDestroy(x.exec);
     if (s.stream) cudaStreamDestroy(s.stream);
     if (s.done) cudaEventDestroy(s.done);
     if (s.stage) cudaFreeHost(s.stage);
