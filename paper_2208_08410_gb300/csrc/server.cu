@@ -226,6 +226,9 @@ struct Slot {  // one stream and the page-locked descriptors of the wave it runs
   cudaEvent_t done = nullptr;
   unsigned char *stage = nullptr;
   size_t stage_cap = 0;
+  // stages outgrown by a larger wave, freed with the server: freeing page-locked memory
+  // waits for the whole device, which would stall the scheduler behind every wave in flight
+  std::vector<unsigned char *> stage_old;
   bool busy = false;
   std::vector<ReqPtr> reqs;
   size_t dev_off = 0, dev_bytes = 0;  // descriptor arrays in the device arena
@@ -438,11 +441,13 @@ tsvd_status launch_wave(tsvd_server_s *sv, Slot &s) {
   const size_t o_tc = b_req + b_tiles, o_err = o_tc + tw.bytes;
   const size_t need = o_err + al(4);
   if (need > s.stage_cap) {
-    if (s.stage) cudaFreeHost(s.stage);
-    s.stage = nullptr;
-    s.stage_cap = 0;
-    TSVD_CUDA(cudaHostAlloc(reinterpret_cast<void **>(&s.stage), need, cudaHostAllocPortable));
-    s.stage_cap = need;
+    // grow geometrically from 1 MB, so a slot reallocates a few times at most
+    const size_t cap = std::max({need, 2 * s.stage_cap, (size_t)1 << 20});
+    unsigned char *p = nullptr;
+    TSVD_CUDA(cudaHostAlloc(reinterpret_cast<void **>(&p), cap, cudaHostAllocPortable));
+    if (s.stage) s.stage_old.push_back(s.stage);
+    s.stage = p;
+    s.stage_cap = cap;
   }
   {
     std::lock_guard<std::mutex> lk(sv->mu);
@@ -1440,6 +1445,7 @@ void tsvd_server_destroy(tsvd_server_t sv) {
     if (s.stream) cudaStreamDestroy(s.stream);
     if (s.done) cudaEventDestroy(s.done);
     if (s.stage) cudaFreeHost(s.stage);
+    for (unsigned char *p : s.stage_old) cudaFreeHost(p);
   }
   for (cudaStream_t st : {sv->poll_stream, sv->out_stream})
     if (st) {
