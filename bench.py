@@ -1269,7 +1269,8 @@ def leg_serve(args, n_req: int):
                 "by_dim": by_dim}
 
     server = Server(device_budget=args.serve_budget << 30, n_streams=args.serve_streams, max_wave=args.serve_max_wave,
-                    heavy_dim=args.serve_heavy_dim, heavy_streams=args.serve_heavy_streams)
+                    heavy_dim=args.serve_heavy_dim, heavy_streams=args.serve_heavy_streams,
+                    wave_graphs=bool(args.serve_graphs))
     server.autotune(iters=30)
     table = {d: server.cluster_for(d) for d in (64, 128, 256, 512, 1024, 2048)}
     tc_from = server.tc_min_d()
@@ -1337,6 +1338,7 @@ def leg_serve(args, n_req: int):
                                                                  "Gram, pinned host A, one at a time"},
             "speedup_capacity_vs_per_request": round(capacity["solves_per_s"] / base_rate, 2) if base_rate else None,
             "server": {"streams": args.serve_streams, "max_wave": args.serve_max_wave,
+                       "wave_graphs": bool(args.serve_graphs),
                        "heavy_dim": args.serve_heavy_dim if args.serve_heavy_dim > 0 else None,
                        "heavy_streams": args.serve_heavy_streams or "auto",
                        "busy_s": round(s2.get("busy_s", 0.0) - s0.get("busy_s", 0.0), 3),
@@ -1625,6 +1627,7 @@ def main():
     ap.add_argument("--full-oracle", action="store_true",
                     help="dense: the oracle's trajectory over all of A (FP64 Gram on the host, ~5 min on 16 cores)")
     ap.add_argument("--serve-streams", type=int, default=8, help="serving: waves in flight (streams)")
+    ap.add_argument("--serve-graphs", type=int, default=0, help="serving: 1 launches each wave as a CUDA graph")
     ap.add_argument("--serve-max-wave", type=int, default=256, help="serving: requests per wave")
     ap.add_argument("--serve-heavy-dim", type=int, default=0, help="serving: heavy lane above this d (0: none)")
     ap.add_argument("--serve-sparse-pool", type=int, default=0, help="serving: distinct sparse matrices (0: pool/8)")

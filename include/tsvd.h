@@ -462,7 +462,13 @@ typedef struct {
                              time heavy requests wait and none is idle
                              (0: 64 - n_streams; n_streams + heavy_streams
                              <= 64) */
-  int32_t reserved[4];
+  int32_t wave_graphs;    /* 1: each dense wave's kernels are captured and
+                             launched as a CUDA graph (instantiated graphs
+                             cached per stream by launch signature and updated
+                             in place); 0 (default): launched directly on the
+                             wave's stream.  Both run the same kernels on the
+                             same descriptors, so results are bitwise equal */
+  int32_t reserved[3];
 } tsvd_server_options;
 
 /* Per-request record (tsvd_server_wait / tsvd_server_poll). */

@@ -210,7 +210,8 @@ class Server:
     tsvd_host_alloc, let the copies overlap other work)."""
 
     def __init__(self, device_budget: int = 8 << 30, max_inflight: int = 0, n_streams: int = 0,
-                 max_wave: int = 0, cluster_cap: int = 0, heavy_dim: int = 0, heavy_streams: int = 0):
+                 max_wave: int = 0, cluster_cap: int = 0, heavy_dim: int = 0, heavy_streams: int = 0,
+                 wave_graphs: bool = False):
         import torch
         torch.cuda.init()
         self.lib = B.load()
@@ -223,6 +224,7 @@ class Server:
         opt.cluster_cap = int(cluster_cap)
         opt.heavy_dim = int(heavy_dim)
         opt.heavy_streams = int(heavy_streams)
+        opt.wave_graphs = 1 if wave_graphs else 0
         h = C.c_void_p()
         B.check(self.lib.tsvd_server_create(C.byref(h), C.byref(opt)), "tsvd_server_create")
         self.handle = h

@@ -52,7 +52,8 @@ class tsvd_report(C.Structure):
 class tsvd_server_options(C.Structure):
     _fields_ = [("device_budget", C.c_size_t), ("max_inflight", C.c_int32), ("n_streams", C.c_int32),
                 ("max_wave", C.c_int32), ("cluster_cap", C.c_int32), ("host_staging", C.c_size_t),
-                ("heavy_dim", C.c_int32), ("heavy_streams", C.c_int32), ("reserved", C.c_int32 * 4)]
+                ("heavy_dim", C.c_int32), ("heavy_streams", C.c_int32), ("wave_graphs", C.c_int32),
+                ("reserved", C.c_int32 * 3)]
 
 
 class tsvd_request_info(C.Structure):

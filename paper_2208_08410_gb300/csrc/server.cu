@@ -245,12 +245,6 @@ struct Slot {  // one stream and the page-locked descriptors of the wave it runs
 };
 constexpr size_t kSlotGraphs = 8;
 
-// Waves as captured graphs (the default) or as plain launches on the slot's stream
-// (TSVD_SERVER_GRAPHS=0)
-bool server_graphs() {
-  const char *e = getenv("TSVD_SERVER_GRAPHS");
-  return !(e && atoi(e) == 0);
-}
 
 }  // namespace
 }  // namespace tsvd
@@ -489,7 +483,7 @@ tsvd_status launch_wave(tsvd_server_s *sv, Slot &s) {
     std::lock_guard<std::mutex> lk(sv->mu);
     sv->stats.graph_host_s += t;
   };
-  if (!server_graphs()) {
+  if (!sv->opt.wave_graphs) {
     TSVD_CUDA(cudaMemcpyAsync(dev, s.stage, need, cudaMemcpyHostToDevice, st));
     TSVD_TRY(launch_tc_wave(tw, dreq, dev + o_tc, derr, st));
     TSVD_TRY(launch_srv_syrk(dreq, reinterpret_cast<const SrvTile *>(dev + b_req), (int)tiles.size(), st));
