@@ -745,6 +745,7 @@ struct Run {
   cudaStream_t cs;
   double h2d = 0.0, d2h = 0.0;
   int64_t chunk_seq = 0;  // ring position, continues across passes
+  int32_t left_err = 0;   // the left kernels' status word after the pass (read back on the stream)
   int64_t copies = 0;     // timed block copies recorded so far
   std::vector<double> copy_bytes;  // bytes of each timed copy
   std::vector<int64_t> copy_first; // first contraction index (row, or column of a wide A) of each timed copy
@@ -891,6 +892,9 @@ tsvd_status left_pass_dense(Run &r, const float *P32, const double *sigma, float
   // (Not after an orthogonally batched Gram: its ring held column panels.)
   const int64_t nc = p->n_chunks;
   const bool reuse = p->mode == MODE_STREAM && !p->tiled;
+  int *lst = nullptr;
+  TSVD_TRY(left_status_word(&lst));
+  TSVD_CUDA(cudaMemsetAsync(lst, 0, 4, r.cs));
   const int64_t first_res = reuse ? std::max<int64_t>(0, nc - p->n_buffers) : nc;
   auto kernel = [&](const float *Ab, int64_t rows, int64_t ldb, float *dst, int64_t ldo) -> tsvd_status {
     if (p->wide) return launch_left_trans(Ab, rows, d, ldb, P32, d, k, sigma, dst, ldo, r.cs);
@@ -926,6 +930,7 @@ tsvd_status left_pass_dense(Run &r, const float *P32, const double *sigma, float
       TSVD_CUDA(cudaEventRecord(p->ev_u_free[b], p->d2h_stream));
     }
   }
+  TSVD_CUDA(cudaMemcpyAsync(&r.left_err, lst, 4, cudaMemcpyDeviceToHost, r.cs));
   return TSVD_OK;
 }
 
@@ -1110,7 +1115,7 @@ tsvd_status factor_dense(Run &r, float *U, double *sigma_out, float *V_out, tsvd
   }
   int flags = 0;
   int64_t apps = 0;
-  if (gram_err) flags |= TSVD_FLAG_TIMEOUT;
+  if (gram_err || r.left_err) flags |= TSVD_FLAG_TIMEOUT;
   for (int64_t l = 0; l < k; ++l) {
     if (hinfo[4 * l + 2]) flags |= TSVD_FLAG_TIMEOUT;
     if (hinfo[4 * l + 1] == 1) flags |= TSVD_FLAG_NOCONV;
@@ -1660,7 +1665,7 @@ tsvd_status factor_dense_tiled(Run &r, float *U, double *sigma_out, float *V_out
   TSVD_CUDA(cudaEventElapsedTime(&t01, p->ev_t[0], p->ev_t[1]));
   TSVD_CUDA(cudaEventElapsedTime(&t12, p->ev_t[1], p->ev_t[2]));
   TSVD_CUDA(cudaEventElapsedTime(&t23, p->ev_t[2], p->ev_t[3]));
-  if (gram_err) flags |= TSVD_FLAG_TIMEOUT;
+  if (gram_err || r.left_err) flags |= TSVD_FLAG_TIMEOUT;
   if (host_out) {
     for (int64_t l = 1; l < k; ++l)
       if (sigma_out[l] > sigma_out[l - 1]) flags |= TSVD_FLAG_NONMONOTONE;

@@ -257,6 +257,8 @@ tsvd_status launch_f64_to_f32(const double *src, float *dst, int64_t count, cuda
 // A, d rows, stride ld); U d x k and V K x k column-major (ldu, ldv).
 tsvd_status launch_left_trans(const float *A, int64_t K, int64_t d, int64_t ld, const float *U, int64_t ldu,
                               int64_t k, const double *sigma, float *V, int64_t ldv, cudaStream_t stream);
+// address of the status word the TMA-fed left kernels raise on a bounded wait that gave up
+tsvd_status left_status_word(int **p);
 tsvd_status launch_left_dense(const float *A, int64_t rows, int64_t n, int64_t ld, const float *V,
                               int64_t ldv, int64_t k, const double *sigma, float *U, int64_t ldu,
                               cudaStream_t stream);

@@ -453,6 +453,173 @@ left_mma_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
   __syncthreads();
 }
 
+// Warp-specialised form of the same tensor-core product: a ninth warp issues
+// the TMA loads, each stage is handed back by an "empty" mbarrier that every
+// consumer warp arrives on when it is done with it, and the two k-halves of a
+// row group meet at the end of a tile through a pair of mbarriers instead of
+// block barriers, so a warp that finishes a chunk early starts the next one.
+// Every wait is bounded; a wait that gives up raises g_left_status, the other
+// warps see it in their own waits, and each warp leaves its loop by itself.
+constexpr int MWS_THREADS = (MW + 1) * 32;
+constexpr int MWS_SMEM = M_NST * M_STAGE + M_RED + 1024 + 128;  // + full[4], empty[4], red_full, red_empty
+
+__global__ void __launch_bounds__(MWS_THREADS, 1)
+left_mma_ws_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapV,
+                   int64_t rows, int64_t n, int64_t k, const double *__restrict__ sigma, float *__restrict__ U,
+                   int64_t ldu, int l0) {
+  extern __shared__ __align__(1024) unsigned char smraw[];
+  unsigned char *sm = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smraw) + 1023) & ~uintptr_t(1023));
+  float *red = reinterpret_cast<float *>(sm + M_NST * M_STAGE);
+  uint64_t *full = reinterpret_cast<uint64_t *>(sm + M_NST * M_STAGE + M_RED);
+  uint64_t *empty = full + M_NST;
+  uint64_t *red_full = empty + M_NST, *red_empty = red_full + 1;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t tiles = ceil_div_dev(rows, TR);
+  const int64_t chunks = ceil_div_dev(n, TJ);
+  const int kc = (int)min((int64_t)LK, k - l0);
+  if (threadIdx.x == 0) {
+    for (int b = 0; b < M_NST; ++b) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(full + b)) : "memory");
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(empty + b)), "r"(MW) : "memory");
+    }
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 4;" ::"r"(su32(red_full)) : "memory");
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 4;" ::"r"(su32(red_empty)) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  const int64_t my_tiles = tiles > blockIdx.x ? ceil_div_dev(tiles - blockIdx.x, gridDim.x) : 0;
+  const int64_t total = my_tiles * chunks;
+  if (warp == MW) {
+    // ------------------------------------------------ producer
+    if (lane == 0) {
+      int64_t issued = 0;
+      for (; issued < total; ++issued) {
+        const int64_t c = issued;
+        if (c >= M_NST && !mbar_wait_l(su32(empty + (c % M_NST)), (uint32_t)(((c / M_NST) - 1) & 1))) break;
+        const int64_t tile = blockIdx.x + (c / chunks) * gridDim.x;
+        const int j0 = (int)((c % chunks) * TJ);
+        const uint32_t st = su32(sm + (c % M_NST) * M_STAGE);
+        const uint32_t bar = su32(full + (c % M_NST));
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(M_STAGE) : "memory");
+#pragma unroll
+        for (int s = 0; s < 4; ++s) {
+          asm volatile(
+              "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+                  st + s * M_ASUB),
+              "l"(reinterpret_cast<uint64_t>(&mapA)), "r"(j0 + s * M_SUB), "r"((int)(tile * TR)), "r"(bar)
+              : "memory");
+          asm volatile(
+              "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+                  st + 4 * M_ASUB + s * M_VSUB),
+              "l"(reinterpret_cast<uint64_t>(&mapV)), "r"(j0 + s * M_SUB), "r"(l0), "r"(bar)
+              : "memory");
+        }
+      }
+      // the last M_NST loads may not have been consumed (a consumer stopped early):
+      // let them land before the block exits
+      for (int64_t j = issued > M_NST ? issued - M_NST : 0; j < issued; ++j)
+        mbar_drain_l(su32(full + (j % M_NST)), (uint32_t)((j / M_NST) & 1));
+    }
+  } else {
+    // ------------------------------------------------ consumers
+    const int g = lane >> 2, q = lane & 3;
+    const int rg = warp & 3, kh = warp >> 2;
+    float inv[2][2];
+#pragma unroll
+    for (int nt = 0; nt < 2; ++nt)
+#pragma unroll
+      for (int e = 0; e < 2; ++e) {
+        const int t = nt * 8 + 2 * q + e;
+        const double sg = t < kc ? __ldg(sigma + l0 + t) : 0.0;
+        inv[nt][e] = sg > 0.0 ? (float)(1.0 / sg) : 0.f;
+      }
+    float sum[2][4];
+    int64_t tix = 0;  // tiles finished by this block
+    for (int64_t c = 0; c < total; ++c) {
+      const int64_t cj = c % chunks;
+      if (cj == 0) {
+#pragma unroll
+        for (int nt = 0; nt < 2; ++nt)
+#pragma unroll
+          for (int e = 0; e < 4; ++e) sum[nt][e] = 0.f;
+      }
+      if (!mbar_wait_l(su32(full + (c % M_NST)), (uint32_t)((c / M_NST) & 1))) break;
+      const unsigned char *As = sm + (c % M_NST) * M_STAGE;
+      const unsigned char *Vs = As + 4 * M_ASUB;
+      float acc[3][2][4];
+#pragma unroll
+      for (int p = 0; p < 3; ++p)
+#pragma unroll
+        for (int nt = 0; nt < 2; ++nt)
+#pragma unroll
+          for (int e = 0; e < 4; ++e) acc[p][nt][e] = 0.f;
+#pragma unroll
+      for (int ks = 0; ks < 8; ++ks) {
+        const int col = kh * 64 + ks * 8;
+        const unsigned char *ab = As + (col >> 5) * M_ASUB;
+        const unsigned char *vb = Vs + (col >> 5) * M_VSUB;
+        const int cc = col & 31;
+        const int r0 = rg * 16 + g;
+        uint32_t ah[4], al[4];
+        split_tf32(*reinterpret_cast<const float *>(ab + sw128(r0, cc + q)), ah[0], al[0]);
+        split_tf32(*reinterpret_cast<const float *>(ab + sw128(r0 + 8, cc + q)), ah[1], al[1]);
+        split_tf32(*reinterpret_cast<const float *>(ab + sw128(r0, cc + q + 4)), ah[2], al[2]);
+        split_tf32(*reinterpret_cast<const float *>(ab + sw128(r0 + 8, cc + q + 4)), ah[3], al[3]);
+#pragma unroll
+        for (int nt = 0; nt < 2; ++nt) {
+          const int t = nt * 8 + g;
+          uint32_t bh0, bl0, bh1, bl1;
+          split_tf32(*reinterpret_cast<const float *>(vb + sw128(t, cc + q)), bh0, bl0);
+          split_tf32(*reinterpret_cast<const float *>(vb + sw128(t, cc + q + 4)), bh1, bl1);
+          mma_tf32(acc[0][nt], al, bh0, bh1);
+          mma_tf32(acc[1][nt], ah, bl0, bl1);
+          mma_tf32(acc[2][nt], ah, bh0, bh1);
+        }
+      }
+      // the stage's operands are in registers or consumed: hand it back
+      __syncwarp();
+      if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(empty + (c % M_NST))) : "memory");
+#pragma unroll
+      for (int nt = 0; nt < 2; ++nt)
+#pragma unroll
+        for (int e = 0; e < 4; ++e) sum[nt][e] += (acc[0][nt][e] + acc[1][nt][e]) + acc[2][nt][e];
+      if (cj == chunks - 1) {
+        float *rp = red + (rg * 32 + lane) * 8;
+        if (kh == 1) {
+          // wait until the k-half 0 warps have read the previous tile's sums
+          if (tix > 0 && !mbar_wait_l(su32(red_empty), (uint32_t)((tix - 1) & 1))) break;
+#pragma unroll
+          for (int nt = 0; nt < 2; ++nt)
+#pragma unroll
+            for (int e = 0; e < 4; ++e) rp[nt * 4 + e] = sum[nt][e];
+          __syncwarp();
+          if (lane == 0) asm volatile("mbarrier.arrive.release.cta.shared::cta.b64 _, [%0];" ::"r"(su32(red_full)) : "memory");
+        } else {
+          if (!mbar_wait_l(su32(red_full), (uint32_t)(tix & 1))) break;
+          float other[2][4];
+#pragma unroll
+          for (int nt = 0; nt < 2; ++nt)
+#pragma unroll
+            for (int e = 0; e < 4; ++e) other[nt][e] = rp[nt * 4 + e];
+          __syncwarp();
+          if (lane == 0) asm volatile("mbarrier.arrive.release.cta.shared::cta.b64 _, [%0];" ::"r"(su32(red_empty)) : "memory");
+          const int64_t tile = blockIdx.x + (c / chunks) * gridDim.x;
+#pragma unroll
+          for (int nt = 0; nt < 2; ++nt)
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+              const int t = nt * 8 + 2 * q + (e & 1);
+              const int64_t row = tile * TR + rg * 16 + g + (e >> 1) * 8;
+              if (t < kc && row < rows) U[row + (int64_t)(l0 + t) * ldu] = (sum[nt][e] + other[nt][e]) * inv[nt][e & 1];
+            }
+        }
+        ++tix;
+      }
+    }
+  }
+  __syncthreads();
+}
+
 typedef CUresult (*EncodeTiledFnL)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
                                    const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
                                    CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
@@ -544,17 +711,29 @@ tsvd_status launch_left_trans(const float *A, int64_t K, int64_t d, int64_t ld, 
   return TSVD_OK;
 }
 
+// The device word the TMA-fed left kernels raise when a bounded wait gives up
+// (shared by every launch on the device: a caller zeroes it before its pass
+// and reads it after)
+tsvd_status left_status_word(int **p) {
+  TSVD_CUDA(cudaGetSymbolAddress(reinterpret_cast<void **>(p), g_left_status));
+  return TSVD_OK;
+}
+
 // Rows per warp of the CUDA-core TMA kernel: 8, or 4 with TSVD_LEFT_RW=4
 static int left_rows_per_warp() {
   const char *e = getenv("TSVD_LEFT_RW");
   return e && atoi(e) == 4 ? 4 : 8;
 }
 
-// The TMA-fed form: tensor cores (3xTF32 mma.sync), or the CUDA cores with TSVD_LEFT_MMA=0
-static bool left_use_mma() {
+// The TMA-fed form: 2 (default) the tensor cores with a producer warp and per-stage
+// mbarriers, 1 the tensor cores with a block barrier per chunk, 0 the CUDA cores (TSVD_LEFT_MMA)
+static int left_form() {
   const char *e = getenv("TSVD_LEFT_MMA");
-  return !(e && atoi(e) == 0);
+  if (!e) return 2;
+  const int v = atoi(e);
+  return v == 0 || v == 1 ? v : 2;
 }
+static bool left_use_mma() { return left_form() != 0; }
 
 tsvd_status launch_left_dense(const float *A, int64_t rows, int64_t n, int64_t ld, const float *V,
                               int64_t ldv, int64_t k, const double *sigma, float *U, int64_t ldu,
@@ -576,8 +755,13 @@ tsvd_status launch_left_dense(const float *A, int64_t rows, int64_t n, int64_t l
       TSVD_TRY(encode_2d(&mv, V, n, k, ldv, M_SUB, LK, CU_TENSOR_MAP_SWIZZLE_128B));
       const int64_t tiles = ceil_div(rows, TR);
       const int grid = (int)std::min<int64_t>(tiles, di.sms);
-      TSVD_TRY(ensure_dynamic_smem(reinterpret_cast<const void *>(left_mma_kernel), M_SMEM));
-      left_mma_kernel<<<grid, MW * 32, M_SMEM, stream>>>(ma, mv, rows, n, k, sigma, U, ldu, (int)l0);
+      if (left_form() == 2) {
+        TSVD_TRY(ensure_dynamic_smem(reinterpret_cast<const void *>(left_mma_ws_kernel), MWS_SMEM));
+        left_mma_ws_kernel<<<grid, MWS_THREADS, MWS_SMEM, stream>>>(ma, mv, rows, n, k, sigma, U, ldu, (int)l0);
+      } else {
+        TSVD_TRY(ensure_dynamic_smem(reinterpret_cast<const void *>(left_mma_kernel), M_SMEM));
+        left_mma_kernel<<<grid, MW * 32, M_SMEM, stream>>>(ma, mv, rows, n, k, sigma, U, ldu, (int)l0);
+      }
       TSVD_LAUNCHED();
     } else if (tma) {
       CUtensorMap ma, mv;
