@@ -461,8 +461,10 @@ left_mma_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
 // Every wait is bounded; a wait that gives up raises g_left_status, the other
 // warps see it in their own waits, and each warp leaves its loop by itself.
 constexpr int MWS_THREADS = (MW + 1) * 32;
-constexpr int MWS_SMEM = M_NST * M_STAGE + M_RED + 1024 + 128;  // + full[4], empty[4], red_full, red_empty
+// shared memory of the warp-specialised kernel with NST stages: + full[NST], empty[NST], red_full, red_empty
+constexpr int mws_smem(int nst) { return nst * M_STAGE + M_RED + 1024 + 16 * nst + 64; }
 
+template <int M_NST>
 __global__ void __launch_bounds__(MWS_THREADS, 1)
 left_mma_ws_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapV,
                    int64_t rows, int64_t n, int64_t k, const double *__restrict__ sigma, float *__restrict__ U,
@@ -735,6 +737,12 @@ static int left_form() {
 }
 static bool left_use_mma() { return left_form() != 0; }
 
+// TMA stages of the warp-specialised kernel: 4, or 5 with TSVD_LEFT_STAGES=5
+static int left_ws_stages() {
+  const char *e = getenv("TSVD_LEFT_STAGES");
+  return e && atoi(e) == 5 ? 5 : 4;
+}
+
 tsvd_status launch_left_dense(const float *A, int64_t rows, int64_t n, int64_t ld, const float *V,
                               int64_t ldv, int64_t k, const double *sigma, float *U, int64_t ldu,
                               cudaStream_t stream) {
@@ -755,9 +763,12 @@ tsvd_status launch_left_dense(const float *A, int64_t rows, int64_t n, int64_t l
       TSVD_TRY(encode_2d(&mv, V, n, k, ldv, M_SUB, LK, CU_TENSOR_MAP_SWIZZLE_128B));
       const int64_t tiles = ceil_div(rows, TR);
       const int grid = (int)std::min<int64_t>(tiles, di.sms);
-      if (left_form() == 2) {
-        TSVD_TRY(ensure_dynamic_smem(reinterpret_cast<const void *>(left_mma_ws_kernel), MWS_SMEM));
-        left_mma_ws_kernel<<<grid, MWS_THREADS, MWS_SMEM, stream>>>(ma, mv, rows, n, k, sigma, U, ldu, (int)l0);
+      if (left_form() == 2 && left_ws_stages() == 5) {
+        TSVD_TRY(ensure_dynamic_smem(reinterpret_cast<const void *>(left_mma_ws_kernel<5>), mws_smem(5)));
+        left_mma_ws_kernel<5><<<grid, MWS_THREADS, mws_smem(5), stream>>>(ma, mv, rows, n, k, sigma, U, ldu, (int)l0);
+      } else if (left_form() == 2) {
+        TSVD_TRY(ensure_dynamic_smem(reinterpret_cast<const void *>(left_mma_ws_kernel<4>), mws_smem(4)));
+        left_mma_ws_kernel<4><<<grid, MWS_THREADS, mws_smem(4), stream>>>(ma, mv, rows, n, k, sigma, U, ldu, (int)l0);
       } else {
         TSVD_TRY(ensure_dynamic_smem(reinterpret_cast<const void *>(left_mma_kernel), M_SMEM));
         left_mma_kernel<<<grid, MW * 32, M_SMEM, stream>>>(ma, mv, rows, n, k, sigma, U, ldu, (int)l0);

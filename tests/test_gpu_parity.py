@@ -197,7 +197,7 @@ def test_left_vectors_match_oracle(rows, n, k):
     _check_left(rows, n, k)
 
 
-@pytest.mark.parametrize("form", ["mma", "mma_ws", "simt8", "simt4"])
+@pytest.mark.parametrize("form", ["mma", "mma_ws", "mma_ws5", "simt8", "simt4"])
 @pytest.mark.parametrize("rows,n,k", [(1000, 300, 20), (4133, 1000, 16), (20000, 4096, 7), (70000, 160, 16)])
 def test_left_vectors_every_kernel_form(form, rows, n, k, monkeypatch):
     """The TMA-fed forms: tensor cores with a block barrier per chunk or a
@@ -207,7 +207,8 @@ def test_left_vectors_every_kernel_form(form, rows, n, k, monkeypatch):
     the n >= 64 that takes this path), CUDA cores with 8 or 4 rows
     per warp (TSVD_LEFT_MMA, TSVD_LEFT_RW): many tiles per block, a ragged
     last tile and chunk, k below and above one sweep of 16."""
-    monkeypatch.setenv("TSVD_LEFT_MMA", {"mma": "1", "mma_ws": "2"}.get(form, "0"))
+    monkeypatch.setenv("TSVD_LEFT_MMA", {"mma": "1", "mma_ws": "2", "mma_ws5": "2"}.get(form, "0"))
+    monkeypatch.setenv("TSVD_LEFT_STAGES", "5" if form == "mma_ws5" else "4")
     monkeypatch.setenv("TSVD_LEFT_RW", "4" if form == "simt4" else "8")
     _check_left(rows, n, k)
 
