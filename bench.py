@@ -483,7 +483,7 @@ def parity_full_size(A: np.ndarray, dA, res, prec: int):
     Gsu = np.where(np.arange(48)[:, None] <= np.arange(48)[None, :], Gs, Gs.T)
     relerr = np.abs(Gsu[iu] - Gref[iu]) / absref[iu]
     out["gram_sampled_max_err_over_absgram"] = float(relerr.max())
-    # sigma_l = ||A v_l|| (Alg. 1 l.11-13) for the GPU's v_l, FP64 over all rows
+    # sigma_l = ||A v_l|| (Alg. 1) for the GPU's v_l, FP64 over all rows
     V = res.V.cpu().numpy().astype(np.float64) if hasattr(res.V, "cpu") else np.asarray(res.V, dtype=np.float64)
     sig_g = res.sigma.cpu().numpy() if hasattr(res.sigma, "cpu") else np.asarray(res.sigma)
     AV2 = np.zeros(V.shape[1])
@@ -1270,7 +1270,7 @@ def leg_serve(args, n_req: int):
 
     server = Server(device_budget=args.serve_budget << 30, n_streams=args.serve_streams, max_wave=args.serve_max_wave,
                     heavy_dim=args.serve_heavy_dim, heavy_streams=args.serve_heavy_streams,
-                    wave_graphs=bool(args.serve_graphs))
+                    wave_graphs=bool(args.serve_graphs), cluster_cap=args.serve_cluster_cap)
     server.autotune(iters=30)
     table = {d: server.cluster_for(d) for d in (64, 128, 256, 512, 1024, 2048)}
     tc_from = server.tc_min_d()
@@ -1338,7 +1338,7 @@ def leg_serve(args, n_req: int):
                                                                  "Gram, pinned host A, one at a time"},
             "speedup_capacity_vs_per_request": round(capacity["solves_per_s"] / base_rate, 2) if base_rate else None,
             "server": {"streams": args.serve_streams, "max_wave": args.serve_max_wave,
-                       "wave_graphs": bool(args.serve_graphs),
+                       "wave_graphs": bool(args.serve_graphs), "cluster_cap": args.serve_cluster_cap or None,
                        "heavy_dim": args.serve_heavy_dim if args.serve_heavy_dim > 0 else None,
                        "heavy_streams": args.serve_heavy_streams or "auto",
                        "busy_s": round(s2.get("busy_s", 0.0) - s0.get("busy_s", 0.0), 3),
@@ -1628,6 +1628,8 @@ def main():
                     help="dense: the oracle's trajectory over all of A (FP64 Gram on the host, ~5 min on 16 cores)")
     ap.add_argument("--serve-streams", type=int, default=8, help="serving: waves in flight (streams)")
     ap.add_argument("--serve-graphs", type=int, default=0, help="serving: 1 launches each wave as a CUDA graph")
+    ap.add_argument("--serve-cluster-cap", type=int, default=0,
+                    help="serving: most CTAs per power-kernel cluster (0: the server's default, 8)")
     ap.add_argument("--serve-max-wave", type=int, default=256, help="serving: requests per wave")
     ap.add_argument("--serve-heavy-dim", type=int, default=0, help="serving: heavy lane above this d (0: none)")
     ap.add_argument("--serve-sparse-pool", type=int, default=0, help="serving: distinct sparse matrices (0: pool/8)")

@@ -220,7 +220,7 @@ TSVD_API void tsvd_options_init(tsvd_options *opt);
  * Dense A with m < n takes Eq. 3: the Gram matrix is A A^T (m x m), formed
  * over column blocks of A (streamed from host memory as 2-D copies when A is
  * there), the power method finds the left vectors U, and one more pass over
- * A forms V = A^T U Sigma^-1 (Alg. 1 l.15-17).  start_draws then holds m x k
+ * A forms V = A^T U Sigma^-1 (Alg. 1).  start_draws then holds m x k
  * draws, and the sign convention applies to U.
  *
  * Errors: EINVAL (k out of range, eps not in (0,1), m or n <= 0, ld < n, bad
@@ -293,7 +293,7 @@ TSVD_API tsvd_status tsvd_gram_accumulate(const float *dA, int64_t rows, int64_t
                                  void *stream);
 
 /*
- * Fused CSR pair for one row block (Alg. 4 l.3-6 on one GPU):
+ * Fused CSR pair for one row block (Alg. 4 on one GPU):
  *   y_r = sum_p values[p] v[col_idx[p]]   for rows r of the block
  *   w[c] += values[p] * y_r               (FP32 atomics)
  *   *ss  += sum_r y_r^2                   (FP64)
@@ -307,8 +307,8 @@ TSVD_API tsvd_status tsvd_csr_gram_apply(int64_t rows, int64_t n, const int64_t 
                                 float *w, double *ss, int32_t scatter, void *stream);
 
 /*
- * Deflated power iteration for one triplet on a dense Gram matrix (Alg. 2
- * l.10-15 with the deflated operator of Eq. 2 in its Hotelling form), one
+ * Deflated power iteration for one triplet on a dense Gram matrix (the
+ * iteration of Alg. 2 with the deflated operator of Eq. 2 in its Hotelling form), one
  * cooperative kernel that keeps the convergence loop on the device.
  *   n        order of G
  *   G32      device, n x n FP32 row-major: the Gram matrix already deflated
@@ -381,7 +381,7 @@ TSVD_API tsvd_status tsvd_gram_deflate(int64_t n, double *G64, float *G32, const
 TSVD_API tsvd_status tsvd_gram_symmetrize(int64_t n, const double *G64, float *G32, void *stream);
 
 /*
- * Start draw x ~ N(0,1)^n for triplet l (Alg. 2 l.3) from the Philox-4x32-10
+ * Start draw x ~ N(0,1)^n for triplet l (Alg. 2) from the Philox-4x32-10
  * stream keyed by splitmix64(seed) (Salmon et al., SC'11), Box-Muller in FP64:
  * counter (p mod 2^32, p div 2^32, l, 0x54535644) for pair p = i/2.
  *   x  device FP64, n entries
@@ -395,7 +395,7 @@ TSVD_API tsvd_status tsvd_philox4x32_10(const uint32_t *ctr, const uint32_t *key
                                int64_t count, void *stream);
 
 /*
- * Left vectors for one row block (Alg. 1 l.11-13): U_b = A_b V diag(sigma)^-1
+ * Left vectors for one row block (Alg. 1): U_b = A_b V diag(sigma)^-1
  *   dA     device rows x n FP32 row-major (stride ld)
  *   V      device n x k FP32 column-major (stride ldv >= n)
  *   sigma  device k FP64; a zero sigma gives a zero column

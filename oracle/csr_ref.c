@@ -2,7 +2,7 @@
  *
  * TEST INFRASTRUCTURE ONLY: part of the CPU oracle; never linked into the
  * library.  It restates one application of the sparse operator of the paper's
- * Sec. IV (Alg. 4 l.3-6 on one device): y = A v, w = A^T y, ||y||^2, all in
+ * Sec. IV (Alg. 4 on one device): y = A v, w = A^T y, ||y||^2, all in
  * double precision, with plain loops in row order.
  *
  * row_ptr: m+1 int64 offsets; col_idx: nnz int32; values: nnz float.

@@ -17,7 +17,7 @@ Contents, each citing the passage it restates:
   tsvd_literal                         Alg. 1 + Alg. 2 verbatim with the explicit residual
   eq1_gram, eq2_apply, eq3_apply       Eq. 1, Eq. 2, Eq. 3
   dist_compute_v0                      Alg. 4 (typos corrected, see below)
-  csr_matvec, csr_rmatvec              y = A v, w = A^T y (Alg. 4 l.3-6)
+  csr_matvec, csr_rmatvec              y = A v, w = A^T y (Alg. 4)
   gapped_indices, subspace_angle,      the grading rule of the parity tests: a triplet is graded
   vector_angle                         when its relative eigen-gap is >= 0.05 to both neighbours,
                                        a cluster by its largest principal angle
@@ -36,16 +36,17 @@ Readings of the paper taken here (each also listed in the design notes):
     iteration cap max_iter stops a non-converging loop; iters_override forces
     a fixed number of applications per triplet (the paper's benchmark mode
     with the convergence test disabled, Sec. V-E).
-  * sigma_l = ||A v_l|| (Alg. 1 l.11-13).  For dense A this is computed as
+  * sigma_l = ||A v_l|| (Alg. 1).  For dense A this is computed as
     sqrt(v_l^T B v_l), the same quantity.
   * Start vectors: x ~ N(0,1) of length min(m, n), one fresh draw per l, then
     x / ||x||; the draws are passed in (x_start) or taken from the Philox
     generator in oracle.philox.
   * A zero (or underflowing) B v0 means rank(A) < l: sigma_l = 0 and the
     returned vector is v0 made orthogonal to the earlier ones; status 'rank'.
-  * Alg. 4 corrections: the batch sum in l.4 runs over the n_b batches; l.11
-    multiplies by V_j^T; l.16 is Sigma^2 V^T v0; the last term of l.18 is
-    (V Sigma^2 V^T v0)_j (as printed it repeats the third term).
+  * Alg. 4 corrections: the batch sum forming X v0 runs over the n_b
+    batches; the projection V^T v0 multiplies by V_j^T; the deflation term
+    is Sigma^2 V^T v0; the last term of the update is (V Sigma^2 V^T v0)_j
+    (as printed it repeats the third term).
 """
 from __future__ import annotations
 
@@ -106,7 +107,7 @@ class PowerResult:
 def power_method(apply_B, v0: np.ndarray, eps: float, max_iter: int = 10000,
                  iters_override: int | None = None, scale: float = 1.0,
                  record: bool = False) -> PowerResult:
-    """Alg. 2 l.10-15: v1 = B v0; v1 /= ||v1||; stop when |v0 . v1| >= 1 - eps.
+    """Alg. 2: v1 = B v0; v1 /= ||v1||; stop when |v0 . v1| >= 1 - eps.
 
     With iters_override the loop runs exactly that many applications and the
     test is skipped (convergence disabled).  `scale` is the magnitude used for
@@ -137,7 +138,7 @@ def power_method(apply_B, v0: np.ndarray, eps: float, max_iter: int = 10000,
 
 
 def _normalise(x: np.ndarray) -> np.ndarray:
-    """Alg. 2 l.4: x / ||x||."""
+    """Alg. 2: x / ||x||."""
     x = np.asarray(x, dtype=np.float64)
     return x / math.sqrt(float(x @ x))
 
@@ -197,13 +198,13 @@ def tsvd_dense(A: np.ndarray, k: int, eps: float, x_start=None, seed: int = 0,
     A64 = np.asarray(A, dtype=np.float64)
     m, n = A64.shape
     if k == -1:
-        k = min(m, n)  # Alg. 1 l.2-4
+        k = min(m, n)  # Alg. 1
     right = m >= n
     M = A64 if right else A64.T  # Eq. 3 is Eq. 2 applied to A^T
     if B is None:
         B = gram(M)
     sig, W, iters, status = right_vectors(B, k, eps, x_start, seed, max_iter, iters_override, sign_convention)
-    # Alg. 1 l.11-13 (or l.15-17): the other factor from A and sigma
+    # Alg. 1: the other factor from A and sigma (U for a tall A, V for a wide one)
     with np.errstate(divide="ignore", invalid="ignore"):
         other = (M @ W) / np.where(sig > 0, sig, np.inf)[None, :]
     if right:
@@ -231,7 +232,7 @@ def right_vectors(B: np.ndarray, k: int, eps: float, x_start=None, seed: int = 0
             v = _orth_against(v0, W)
             s = 0.0
         else:
-            s = math.sqrt(max(float(v @ (B @ v)), 0.0))  # sigma_l = ||M v_l|| (Alg. 1 l.11-13)
+            s = math.sqrt(max(float(v @ (B @ v)), 0.0))  # sigma_l = ||M v_l|| (Alg. 1)
         if sign_convention:
             v = v * _sign_fix(v)
         if scale is None:
@@ -244,7 +245,7 @@ def right_vectors(B: np.ndarray, k: int, eps: float, x_start=None, seed: int = 0
 
 
 # ----------------------------------------------------------------------------
-# CSR operators (Alg. 4 l.3-6 on one device: y = X v0, w = X^T y)
+# CSR operators (Alg. 4 on one device: y = X v0, w = X^T y)
 # ----------------------------------------------------------------------------
 def csr_row_index(row_ptr: np.ndarray) -> np.ndarray:
     m = row_ptr.shape[0] - 1
@@ -272,7 +273,7 @@ def tsvd_csr(csr: dict, k: int, eps: float, x_start=None, seed: int = 0, max_ite
              iters_override=None, sign_convention: bool = False) -> TSVDResult:
     """Alg. 1 for a CSR matrix with m >= n, never forming B: each application
     is w = A^T (A v0) - V diag(sigma^2) V^T v0 (the Alg. 4 operator in the
-    Hotelling form), and sigma_l = ||A v_l|| (Alg. 1 l.11-13)."""
+    Hotelling form), and sigma_l = ||A v_l|| (Alg. 1)."""
     row_ptr, col_idx, values = csr["row_ptr"], csr["col_idx"], csr["values"]
     m, n = csr["m"], csr["n"]
     assert m >= n, "the CSR oracle covers the m >= n branch"
@@ -401,22 +402,22 @@ def dist_compute_v0(X, U, S, V, v0, n_b: int, N: int):
     m, n = X.shape
     rows = np.array_split(np.arange(m), N)
     cols = np.array_split(np.arange(n), n_b)
-    # l.3-4: (X v0)_i = sum_j X_ij (v0)_j
+    # (X v0)_i = sum_j X_ij (v0)_j
     Xv0 = [sum(X[np.ix_(ri, cj)] @ v0[cj] for cj in cols) for ri in rows]
-    # l.5-6: (X^T X v0)_j = sum_i X_ij^T (X v0)_i   (all-reduce over i)
+    # (X^T X v0)_j = sum_i X_ij^T (X v0)_i   (all-reduce over i)
     XtXv0 = [sum(X[np.ix_(ri, cj)].T @ Xv0[a] for a, ri in enumerate(rows)) for cj in cols]
-    # l.7-8: U^T X v0 = sum_i U_i^T (X v0)_i        (all-reduce over i)
+    # U^T X v0 = sum_i U_i^T (X v0)_i        (all-reduce over i)
     UtXv0 = sum(U[ri].T @ Xv0[a] for a, ri in enumerate(rows))
-    # l.9-10: (V S^T U^T X v0)_j
+    # (V S^T U^T X v0)_j
     VSUtXv0 = [V[cj] @ (S * UtXv0) for cj in cols]
-    # l.11-13: V^T v0 = sum_j V_j^T (v0)_j, then S V^T v0
+    # V^T v0 = sum_j V_j^T (v0)_j, then S V^T v0
     SVtv0 = S * sum(V[cj].T @ v0[cj] for cj in cols)
-    # l.14-16: (X^T U S V^T v0)_j = sum_i X_ij^T (U S V^T v0)_i
+    # (X^T U S V^T v0)_j = sum_i X_ij^T (U S V^T v0)_i
     USVtv0 = [U[ri] @ SVtv0 for ri in rows]
     XtUSVtv0 = [sum(X[np.ix_(ri, cj)].T @ USVtv0[a] for a, ri in enumerate(rows)) for cj in cols]
-    # l.16-17 (corrected): (V S^2 V^T v0)_j
+    # (V S^2 V^T v0)_j (the corrected deflation term)
     VS2Vtv0 = [V[cj] @ (S * SVtv0) for cj in cols]
-    # l.18 (corrected last term)
+    # the update with its corrected last term
     out = np.empty(n)
     for b, cj in enumerate(cols):
         out[cj] = XtXv0[b] - VSUtXv0[b] - XtUSVtv0[b] + VS2Vtv0[b]

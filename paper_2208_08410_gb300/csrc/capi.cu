@@ -879,7 +879,7 @@ tsvd_status gram_dispatch(const float *A, int64_t rows, int64_t n, int64_t ld, d
   return launch_gram_tc(A, rows, n, ld, G, prec, scr, scr_bytes, s, ev0, ev1, reset_status, wait_ns);
 }
 
-// The other factor, one pass over A (Alg. 1 l.11-13 / l.15-17): OUT = A P
+// The other factor, one pass over A (Alg. 1): OUT = A P
 // Sigma^-1 for a tall A (P = V, OUT = U) or A^T P Sigma^-1 for a wide A
 // (P = U from A A^T, OUT = V); P is d x k and OUT is K x k, both column-major.
 tsvd_status left_pass_dense(Run &r, const float *P32, const double *sigma, float *OUT) {
@@ -1006,7 +1006,7 @@ tsvd_status power_cluster_dense(Run &r, double *G64, float *G32, double *V64, fl
 tsvd_status factor_dense(Run &r, float *U, double *sigma_out, float *V_out, tsvd_report *rep) {
   tsvd_plan_s *p = r.p;
   const int64_t n = p->d, k = p->k;  // the Gram's dimension (n for a tall A, m for a wide one)
-  // the power method's vectors and the other factor (Alg. 1 l.11-13 / l.15-17)
+  // the power method's vectors and the other factor (Alg. 1)
   float *P_out = p->wide ? U : V_out;
   float *O_out = p->wide ? V_out : U;
   unsigned char *ws = r.ws;
@@ -1482,7 +1482,7 @@ tsvd_status explicit_power_on(Run &r, ExplicitLoop &L,
       TSVD_CUDA(cudaMemsetAsync(L.sig2 + l, 0, 8, r.cs));
       flags |= TSVD_FLAG_RANK;
     } else {
-      // sigma_l^2 = ||A v_l||^2 (Alg. 1 l.11-13)
+      // sigma_l^2 = ||A v_l||^2 (Alg. 1)
       TSVD_CUDA(cudaMemsetAsync(L.ss, 0, 8, r.cs));
       TSVD_TRY(apply(v, L.w, L.ss, 0));
       TSVD_CUDA(cudaMemcpyAsync(L.sig2 + l, L.ss, 8, cudaMemcpyDeviceToDevice, r.cs));

@@ -1,6 +1,6 @@
 // Sparse (CSR) kernels: the implicit Gram application and the left vectors.
 //
-// Fused pair (Sec. IV and Alg. 4 l.3-6 on one GPU; the Gram B = A^T A is never
+// Fused pair (Sec. IV and Alg. 4 on one GPU; the Gram B = A^T A is never
 // formed): for each row r of a row block
 //     y_r = sum_p values[p] * v[col_idx[p]]          (gather, group reduction)
 //     w[col_idx[p]] += values[p] * y_r               (FP32 atomics)
@@ -17,7 +17,7 @@
 // A^T y into w one chunk at a time (the atomics on w_c stay in L2); the CSR
 // is read twice instead of once, but the random accesses no longer go to DRAM.
 //
-// Left vectors (Alg. 1 l.11-13): U[r][l] = sum_p values[p] * V[col_p][l] /
+// Left vectors (Alg. 1): U[r][l] = sum_p values[p] * V[col_p][l] /
 // sigma_l, with V stored row-major (n x ldk) so one gather fetches all of a
 // row's deflation coordinates at once.
 #include <algorithm>

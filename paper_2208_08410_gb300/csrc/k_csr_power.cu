@@ -1,5 +1,5 @@
-// One triplet of the sparse power method in one cooperative launch: Alg. 2
-// l.10-15 with the implicit operator of Alg. 4 (w = A^T (A v), never forming
+// One triplet of the sparse power method in one cooperative launch: the
+// iteration of Alg. 2 with the implicit operator of Alg. 4 (w = A^T (A v), never forming
 // A^T A) and Hotelling's correction w -= V (sigma^2 . V^T v) (Eq. 2), for a
 // CSR matrix held on the device.  It serves small operators, where a dozen
 // kernels and a host round trip per application would cost more than the

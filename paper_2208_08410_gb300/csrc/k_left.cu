@@ -1,4 +1,4 @@
-// Left singular vectors of a dense row block (Alg. 1 l.11-13):
+// Left singular vectors of a dense row block (Alg. 1):
 //     U_b = A_b V diag(sigma)^-1,   u_l = A v_l / ||A v_l||
 // computed in one extra pass over A after all right vectors are known.
 //
@@ -648,7 +648,7 @@ tsvd_status encode_2d(CUtensorMap *map, const float *base, int64_t inner, int64_
 }
 
 // The other factor of a wide A (Eq. 3: the power method found the left
-// vectors U, then V = A^T U Sigma^-1, Alg. 1 l.15-17) for a block of its
+// vectors U, then V = A^T U Sigma^-1, Alg. 1) for a block of its
 // columns: V[j][l] = sum_i A[i][j] U[i][l] / sigma_l for the block's K
 // columns j, over the d rows i.  One thread per column (the loads of A along
 // a row are coalesced across the warp); U is staged 32 rows at a time in

@@ -1,10 +1,10 @@
 // Deflated power iteration on a dense Gram matrix, kept on the device.
 //
-// Restates Alg. 2 l.10-15 (v1 = B v0, v1 /= ||v1||, stop when
+// Restates Alg. 2 (v1 = B v0, v1 /= ||v1||, stop when
 // |v0 . v1| >= 1 - eps) with B deflated in the Hotelling form that Eq. 2
 // reduces to for exact earlier triplets:
 //     w = G v0 - sum_{j<l} sigma_j^2 v_j (v_j^T v0)
-// and closes with sigma_l^2 = v_l^T G v_l (Alg. 1 l.11-13: sigma = ||A v||).
+// and closes with sigma_l^2 = v_l^T G v_l (Alg. 1: sigma = ||A v||).
 //
 // The Gram matrix is deflated once per triplet (rank-1 update in FP64 of
 // the FP64 upper triangle, tsvd_gram_deflate) and the FP32 copy the loop
@@ -129,7 +129,7 @@ __global__ void __launch_bounds__(PT, 1) power_dense_kernel(PowerArgs a) {
   double *mypart = a.part + (int64_t)blockIdx.x * ps;
   const bool vec = (n % 4 == 0);
 
-  // ---- prologue: v0 = x / ||x|| (Alg. 2 l.4)
+  // ---- prologue: v0 = x / ||x|| (Alg. 2)
   double s = 0.0;
   for (int64_t i = r0 + threadIdx.x; i < r1; i += PT) {
     const double xi = __ldcg(a.x + i);

@@ -9,7 +9,7 @@
 // on what else is in the wave.  The epilogue writes the tile and its mirror
 // into the FP64 matrix and its FP32 copy.
 //
-// Grouped power (Alg. 1 l.5-13 with Alg. 2 for each triplet, Hotelling
+// Grouped power (Alg. 1 with Alg. 2 for each triplet, Hotelling
 // deflation).  One thread-block cluster per request; CTA c of C owns rows
 // [c R, (c+1) R) of G (R = ceil(d / C)), kept in shared memory when they fit.
 // An iteration: w = G32 v for the CTA's rows (FP32 products, error-free FP32
@@ -26,8 +26,8 @@
 // sigma_l^2 = v_l^T G v_l is formed as v_l^T G_defl v_l + sum_{j<l}
 // sigma_j^2 (v_j . v_l)^2 from row partials (one more exchange).
 //
-// After the k triplets the same cluster forms the other factor (Alg. 1
-// l.11-13 / l.15-17: U = A V Sigma^-1 for tall requests, V = A^T U Sigma^-1
+// After the k triplets the same cluster forms the other factor (Alg. 1:
+// U = A V Sigma^-1 for tall requests, V = A^T U Sigma^-1
 // for wide ones), writes U, sigma, V and the per-triplet info into the
 // request's output region and raises its completion flag (a release store
 // into the server's device flag array, which the server copies to the host),
@@ -614,7 +614,7 @@ __global__ void __launch_bounds__(kSrvPowerThreads, 2) srv_power_kernel(const Sr
     __syncthreads();
   }
 
-  // ---- other factor (Alg. 1 l.11-13 / l.15-17) for this request, split over the cluster
+  // ---- other factor (Alg. 1) for this request, split over the cluster
   cluster_sync_all();  // every CTA's rows of vout are written
   const int64_t m = q.m, n = q.n;
   const float *__restrict__ A = q.A;

@@ -1,7 +1,7 @@
 // Vector kernels of the streamed (CSR) power step.
 //
 // After the fused pair has produced w = A^T (A v0) for all row blocks, these
-// kernels finish one step of Alg. 2 l.10-15 in the Hotelling form of Eq. 2:
+// kernels finish one step of Alg. 2 in the Hotelling form of Eq. 2:
 //     c_j   = v_j^T v0                    (j < l)
 //     w    -= sum_j sigma_j^2 c_j v_j
 //     v1    = w / ||w||,  cos = |v0 . w| / (||v0|| ||w||),  stop if cos >= 1 - eps

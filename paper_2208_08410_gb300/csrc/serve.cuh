@@ -9,7 +9,7 @@
 //      all k triplets (Hotelling deflation of the FP32 copy, FP64 Rayleigh
 //      quotient and convergence test);
 //      then, in the same cluster, the other factor: U = A V Sigma^-1 (m >= n)
-//      or V = A^T U Sigma^-1 (m < n), Alg. 1 l.11-13 / l.15-17; the cluster
+//      or V = A^T U Sigma^-1 (m < n), Alg. 1; the cluster
 //      writes U, sigma, V and the per-triplet info into the request's output
 //      region in device memory and then raises the request's completion flag
 //      (a word of a device array the server polls), so each request

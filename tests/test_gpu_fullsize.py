@@ -17,7 +17,7 @@ At these sizes the oracle cannot run the whole method, so the checks are on
 outputs it computes one by one, in FP64 on the host:
 - sampled Gram entries (48 columns over all rows) against the oracle's Gram of
   those columns;
-- sigma_l = ||A v_l|| (Alg. 1 l.11-13) for the library's v_l;
+- sigma_l = ||A v_l|| (Alg. 1) for the library's v_l;
 - rows of U against (A v_l)_r / sigma_l;
 - one CSR row block's operator application (w and ||A_b v||^2) against the C
   oracle, every entry of w;
