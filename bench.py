@@ -1272,6 +1272,9 @@ def leg_serve(args, n_req: int):
                     heavy_dim=args.serve_heavy_dim, heavy_streams=args.serve_heavy_streams,
                     wave_graphs=bool(args.serve_graphs), cluster_cap=args.serve_cluster_cap)
     server.autotune(iters=30)
+    if args.serve_cluster_table:  # a fixed table instead of the autotuner's (d <= 64 .. 2048)
+        for d, c in zip((64, 128, 256, 512, 1024, 2048), (int(x) for x in args.serve_cluster_table.split(","))):
+            server.set_cluster_for(d, c)
     table = {d: server.cluster_for(d) for d in (64, 128, 256, 512, 1024, 2048)}
     tc_from = server.tc_min_d()
     syrk_times = server.autotune_syrk_times()
@@ -1628,6 +1631,8 @@ def main():
                     help="dense: the oracle's trajectory over all of A (FP64 Gram on the host, ~5 min on 16 cores)")
     ap.add_argument("--serve-streams", type=int, default=8, help="serving: waves in flight (streams)")
     ap.add_argument("--serve-graphs", type=int, default=0, help="serving: 1 launches each wave as a CUDA graph")
+    ap.add_argument("--serve-cluster-table", default="",
+                    help="serving: power-kernel cluster sizes for d <= 64,128,256,512,1024,2048 (default: autotuned)")
     ap.add_argument("--serve-cluster-cap", type=int, default=0,
                     help="serving: most CTAs per power-kernel cluster (0: the server's default, 8)")
     ap.add_argument("--serve-max-wave", type=int, default=256, help="serving: requests per wave")

@@ -566,13 +566,21 @@ TSVD_API const char *tsvd_server_last_error(tsvd_server_t server);
 /* Power-kernel cluster size the server uses for Gram dimension d. */
 TSVD_API int32_t tsvd_server_cluster_for(tsvd_server_t server, int64_t d);
 
+/* Set the power-kernel cluster size for the Gram dimensions of d's class
+ * (d <= 64, 128, 256, 512, 1024, 2048): c in {1, 2, 4, 8}, at most the
+ * server's cluster_cap, and reduced for small d as the kernel needs (every CTA
+ * owns rows).  Applies to later submissions; a request's cluster still depends
+ * on its own shape only.  EINVAL for other values. */
+TSVD_API tsvd_status tsvd_server_set_cluster_for(tsvd_server_t server, int64_t d, int32_t c);
+
 /*
  * Pick the power-kernel cluster size per Gram dimension by measurement: for
  * d in {64, 128, 256, 512, 1024, 2048} and each cluster size up to
- * cluster_cap, time `iters` iterations of one synthetic request alone and of
- * as many as fill the GPU, and keep the size with the highest iterations per
- * second over the whole GPU among those whose single-request time is within
- * 2.5x of the fastest.  Then pick the Gram step's tile shape per size: for
+ * cluster_cap, time `iters` iterations of one synthetic request alone, and
+ * keep the size with the lowest single-request
+ * time (the smaller size where two are within 5 %): a request holds its CTAs,
+ * memory and wave until it is done, so on a serving mix the fastest request
+ * gives the highest capacity.  Then pick the Gram step's tile shape per size: for
  * d in {256, 512, 1024, 2048} it times the grouped tensor-core SYRK (128 x 256
  * tiles, 3xTF32) and the grouped CUDA-core SYRK (64 x 64 tiles, FP32) on
  * synthetic 8192 x d requests, enough to give both kernels work for every SM,

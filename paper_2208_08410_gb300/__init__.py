@@ -277,6 +277,9 @@ class Server:
     def cluster_for(self, d: int) -> int:
         return int(self.lib.tsvd_server_cluster_for(self.handle, int(d)))
 
+    def set_cluster_for(self, d: int, c: int):
+        B.check(self.lib.tsvd_server_set_cluster_for(self.handle, int(d), int(c)), "tsvd_server_set_cluster_for")
+
     def tc_min_d(self) -> int:
         """Gram dimension from which requests use the tensor-core SYRK."""
         return int(self.lib.tsvd_server_tc_min_d(self.handle))

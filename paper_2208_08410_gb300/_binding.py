@@ -111,6 +111,7 @@ SIGNATURES = {
     "tsvd_server_get_stats": (C.c_int, [_P, C.POINTER(tsvd_server_stats)]),
     "tsvd_server_last_error": (C.c_char_p, [_P]),
     "tsvd_server_cluster_for": (_I32, [_P, _I64]),
+    "tsvd_server_set_cluster_for": (_I32, [_P, _I64, _I32]),
     "tsvd_server_tc_min_d": (C.c_int64, [_P]),
     "tsvd_server_set_tc_min_d": (C.c_int, [_P, C.c_int64]),
     "tsvd_server_autotune_syrk_times": (C.c_int, [_P, _P, _P, _P, _P]),

@@ -158,6 +158,32 @@ def test_server_result_alone_equals_result_in_the_mix():
         pool.close()
 
 
+def test_server_set_cluster_for():
+    """A fixed cluster size per class of Gram dimension: invalid sizes are
+    rejected, a valid one is what later requests of that class run with, and
+    the result still follows the oracle's trajectory."""
+    B.load()
+    pool = Pool()
+    sv = Server(device_budget=2 << 30)
+    try:
+        for bad_d, bad_c in ((0, 2), (4096, 2), (512, 3), (512, 16)):
+            assert sv.lib.tsvd_server_set_cluster_for(sv.handle, bad_d, bad_c) == B.TSVD_EINVAL
+        sv.set_cluster_for(700, 2)
+        assert sv.cluster_for(1000) == 2 and sv.cluster_for(600) == 2
+        m, n, k = 3000, 700, 6
+        A = _request(pool, m, n, 0.8, seed=41)
+        U, s, V = _outputs(pool, m, n, k)
+        o = ref.tsvd_dense(A, k, 1e-10, seed=9)
+        st, info = sv.wait(sv.submit(A, k, 1e-10, U, s, V, seed=9, iters_override=o.iters), 60.0)
+        assert st == B.TSVD_OK and info["cluster"] == 2
+        assert np.max(np.abs(s - o.sigma) / o.sigma) <= 1e-5
+        for l in range(k):
+            assert ref.vector_angle(V[l].astype(np.float64), o.V[:, l]) <= 1e-4
+    finally:
+        sv.close()
+        pool.close()
+
+
 def test_server_zero_matrix_reports_rank():
     B.load()
     pool = Pool()
