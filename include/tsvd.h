@@ -578,7 +578,7 @@ TSVD_API tsvd_status tsvd_server_set_cluster_for(tsvd_server_t server, int64_t d
  * d in {64, 128, 256, 512, 1024, 2048} and each cluster size up to
  * cluster_cap, time `iters` iterations of one synthetic request alone, and
  * keep the size with the lowest single-request
- * time (the smaller size where two are within 5 %): a request holds its CTAs,
+ * time, a larger size only where it is more than 15 % faster: a request holds its CTAs,
  * memory and wave until it is done, so on a serving mix the fastest request
  * gives the highest capacity.  Then pick the Gram step's tile shape per size: for
  * d in {256, 512, 1024, 2048} it times the grouped tensor-core SYRK (128 x 256

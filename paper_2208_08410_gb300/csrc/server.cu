@@ -1346,16 +1346,18 @@ tsvd_status tsvd_server_autotune(tsvd_server_t sv, int32_t iters) {
       lat.push_back(ms1);
     }
     if (result != TSVD_OK || cs.empty()) break;
-    // the lowest latency of a lone request, the smaller cluster where two are within 5 %.
-    // On the serving mix a request holds its CTAs, its arena memory and its wave's stream
-    // until it is done, so the fastest request frees them soonest: measured on 10,000 dense
-    // requests, the largest clusters d allows gave 1,403 solves/s against 1,238 for the
-    // table that maximised whole-GPU throughput per size (and 937 / 452 with clusters
-    // capped at 4 / 2 CTAs), and p99 0.33 s against 0.79 s at 0.9x capacity
+    // the fastest lone request, a larger cluster taken only where it cuts the time by more
+    // than 15 %.  On the serving mix a request holds its CTAs, its arena memory and its
+    // wave's stream until it is done, so the fastest request frees them soonest: measured
+    // on 10,000 dense requests, the largest clusters d allows gave 1,403 solves/s against
+    // 1,238 for the table that maximised whole-GPU throughput per size (and 937 / 452 with
+    // clusters capped at 4 / 2 CTAs), and p99 0.33 s against 0.79 s at 0.9x capacity.  For
+    // small d a larger cluster saves little time for many more CTAs: a 5 % rule put 8-CTA
+    // clusters on d = 128 and gave p99 0.57 s at 0.9x capacity
     double best_lat = lat[0];
     int best_c = cs[0];
     for (size_t i = 1; i < cs.size(); ++i)
-      if (lat[i] < 0.95 * best_lat) {
+      if (lat[i] < 0.85 * best_lat) {
         best_lat = lat[i];
         best_c = cs[i];
       }
