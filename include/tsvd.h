@@ -136,7 +136,11 @@ typedef struct {
                                     MMAs complete, frees its tensor memory and returns,
                                     and tsvd_factor returns TSVD_ETIMEDOUT with
                                     TSVD_FLAG_TIMEOUT set.  It exists to test that path */
-  int32_t reserved;
+  int32_t csr_coop_blocks;       /* CSR in core, small operator: most blocks of the
+                                    cooperative kernel that runs a whole triplet (0 =
+                                    128, the fastest for a request alone; fewer let
+                                    several requests share the GPU, as the server's
+                                    sparse requests do with 64); < 0 = TSVD_EINVAL */
 } tsvd_options;
 
 /* Kernels of the dense power phase.  GRID: one cooperative launch per

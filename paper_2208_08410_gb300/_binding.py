@@ -35,7 +35,7 @@ class tsvd_options(C.Structure):
                 ("iters_override", C.c_void_p), ("start_draws", C.c_void_p), ("seed", C.c_uint64),
                 ("out_location", C.c_int32), ("force_stream", C.c_int32), ("time_kernels", C.c_int32),
                 ("power_kernel", C.c_int32), ("gram_tile", C.c_int32),
-                ("power_ctas", C.c_int32), ("wait_limit_ns", C.c_int32), ("reserved", C.c_int32)]
+                ("power_ctas", C.c_int32), ("wait_limit_ns", C.c_int32), ("csr_coop_blocks", C.c_int32)]
 
 
 class tsvd_report(C.Structure):

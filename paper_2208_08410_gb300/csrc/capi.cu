@@ -617,7 +617,7 @@ tsvd_status tsvd_plan(tsvd_plan_t *out, const tsvd_matrix *A, int64_t k, double 
       opt.power_ctas != 8)
     return TSVD_EINVAL;
   if (opt.gram_tile > 0 && A->kind != TSVD_DENSE_F32_ROWMAJOR) return TSVD_EINVAL;
-  if (opt.wait_limit_ns < 0) return TSVD_EINVAL;
+  if (opt.wait_limit_ns < 0 || opt.csr_coop_blocks < 0) return TSVD_EINVAL;
   const bool cluster_fits = A->kind == TSVD_DENSE_F32_ROWMAJOR && mn <= kSrvMaxDim && k <= kSrvMaxK;
   if (opt.power_kernel == TSVD_POWER_CLUSTER && !cluster_fits) {
     set_error_text("tsvd_plan: the cluster power kernel takes dense A with n <= " + std::to_string(kSrvMaxDim) +
@@ -1781,7 +1781,8 @@ tsvd_status factor_csr(Run &r, float *U, double *sigma_out, float *V_out, tsvd_r
     TSVD_CUDA(cudaMemsetAsync(w, 0, (size_t)n * 4, r.cs));
     return launch_csr_power(m, n, rp_all, ci_all, va_all, Vr, k, sig2, l, b0, b1, w, sc.part,
                             (size_t)sc.grid * kVecPartStride * sizeof(double), bar, err, p->eps, p->opt.max_iter,
-                            ovr, rank_scale, info_l, p->avg_nnz, 128, r.cs);
+                            ovr, rank_scale, info_l, p->avg_nnz,
+                            p->opt.csr_coop_blocks > 0 ? p->opt.csr_coop_blocks : 128, r.cs);
   };
   TSVD_TRY(explicit_power(
       r, L, [&](const float *vv, float *ww, double *s2, int scatter) { return csr_apply(r, bnd, vv, ww, s2, scatter); },

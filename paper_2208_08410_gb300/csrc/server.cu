@@ -1016,6 +1016,10 @@ void csr_worker(tsvd_server_s *sv) {
     opt.sign_convention = r->sign;
     opt.iters_override = r->iters.empty() ? nullptr : r->iters.data();
     opt.out_location = TSVD_HOST;
+    // a smaller cooperative grid than a lone request takes (128), so that several sparse
+    // requests and the dense waves share the GPU: measured on the serving mix, 64 blocks
+    // gave 163 solves/s against 139 and dense p99 75 ms against 222 ms at 0.9x capacity
+    opt.csr_coop_blocks = 64;
     // at most a quarter of the arena per sparse request (the plan streams A beyond that)
     opt.device_budget = std::max<size_t>(sv->arena.size / 4, (size_t)64 << 20);
     tsvd_plan_t plan = nullptr;

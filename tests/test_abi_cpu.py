@@ -104,6 +104,8 @@ def test_plan_validation_dense(lib):
     # the test-only limit of the tensor-core Gram kernel's waits
     assert _plan(d, 5, 1e-6, _opts(wait_limit_ns=1))[0] == B.TSVD_OK
     assert _plan(d, 5, 1e-6, _opts(wait_limit_ns=-1))[0] == B.TSVD_EINVAL
+    assert _plan(d, 5, 1e-6, _opts(csr_coop_blocks=64))[0] == B.TSVD_OK
+    assert _plan(d, 5, 1e-6, _opts(csr_coop_blocks=-1))[0] == B.TSVD_EINVAL
     big, keep5 = _dense_desc(8, 2049, arr=np.zeros((1, 1), dtype=np.float32))
     big.m = 4096  # plan reads no values
     assert _plan(big, 4, 1e-6, _opts(power_kernel=B.TSVD_POWER_CLUSTER))[0] == B.TSVD_EUNSUPPORTED
