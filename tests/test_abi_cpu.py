@@ -302,3 +302,61 @@ def test_copy_log_arguments():
         assert lib.tsvd_plan_copy_log(None, None, None, None, 0, C.byref(cnt)) == B.TSVD_EINVAL
     finally:
         lib.tsvd_destroy(h)
+
+
+def _header_structs(hdr):
+    """name -> [(field, C type, is pointer, count)] for every typedef struct
+    with a body in the header (comments stripped; one declaration may name
+    several fields; arrays carry their length)."""
+    import re
+    out = {}
+    for m in re.finditer(r"typedef struct \{(.*?)\}\s*(\w+);", hdr, re.S):
+        body = re.sub(r"/\*.*?\*/", "", m.group(1), flags=re.S)
+        fields = []
+        for decl in body.split(";"):
+            decl = " ".join(decl.split())
+            if not decl:
+                continue
+            mm = re.match(r"(?:const\s+)?(\w+)\s*(\**)\s*(.+)$", decl)
+            assert mm, decl
+            ctype, stars, names = mm.group(1), mm.group(2), mm.group(3)
+            for nm in names.split(","):
+                nm = nm.strip()
+                ptr = bool(stars) or nm.startswith("*")
+                nm = nm.lstrip("* ")
+                count = 1
+                arr = re.match(r"(\w+)\s*\[(\d+)\]$", nm)
+                if arr:
+                    nm, count = arr.group(1), int(arr.group(2))
+                fields.append((nm, ctype, ptr, count))
+        out[m.group(2)] = fields
+    return out
+
+
+def test_binding_structs_match_the_header():
+    """Every struct the binding mirrors has the header's fields, in the
+    header's order, each of the header's size (pointers 8 bytes, the fixed-
+    width integers and double by their width), and the same total size, so a
+    field added to or moved in include/tsvd.h cannot shift the ones after it
+    on the Python side."""
+    import ctypes as C
+    hdr = open(os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include",
+                            "tsvd.h")).read()
+    size = {"int32_t": 4, "uint32_t": 4, "int64_t": 8, "uint64_t": 8, "double": 8, "size_t": 8, "float": 4}
+    structs = _header_structs(hdr)
+    checked = 0
+    for name, fields in structs.items():
+        cls = getattr(B, name, None)
+        if cls is None:
+            continue
+        py = cls._fields_
+        assert [f[0] for f in py] == [f[0] for f in fields], name
+        offset = 0
+        for (fname, ftype), (hname, ctype, ptr, count) in zip(py, fields):
+            want = (8 if ptr else size[ctype]) * count
+            assert C.sizeof(ftype) == want, (name, fname, C.sizeof(ftype), want)
+            align = 8 if ptr else size[ctype]
+            offset = (offset + align - 1) // align * align + want
+        assert C.sizeof(cls) == (offset + 7) // 8 * 8, name
+        checked += 1
+    assert checked >= 6, sorted(structs)
