@@ -343,6 +343,21 @@ def time_steps(plan, A_in, steps: int, warmup: int, want_u=True, outs=None):
     return e0.elapsed_time(e1) / 1e3, wall, reps, last
 
 
+def dense_config(m: int, prec: int, world: int) -> dict:
+    """The dense workload's config, the same on the GPU line and the reference
+    (oracle) line."""
+    return {"workload": f"dense t-SVD (rank-64 + 1e-4 noise), m={m}, n={N_COLS}, k={K}, eps={EPS}; "
+                        "value: A resident in HBM (in-core); e2e: A streamed from page-locked host "
+                        f"memory under a {BUDGET / 1e9:.0f} GB device budget (out-of-core)",
+            "m": m, "n": N_COLS, "k": K, "eps": EPS,
+            "block_rows": BLOCK_ROWS, "device_budget_bytes_e2e": BUDGET,
+            "full_m": FULL_M, "host_ram_limited": m < FULL_M,
+            "l2": "inputs larger than L2 (A is %.0f GiB)" % (m * N_COLS * 4 / 2 ** 30),
+            "gram_precision": PREC_NAMES[prec] + (" (FP32-class split: hi*hi + hi*lo + lo*hi on the "
+                                                  "tensor cores, FP32 accumulate)" if prec == 2 else ""),
+            "parallelism": "replicas" if world > 1 else "1 GPU"}
+
+
 def reference_arm(args, m: int):
     """The FP64 oracle timed on the host cores over one row block per step."""
     import synth
@@ -368,8 +383,7 @@ def reference_arm(args, m: int):
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": round(sec * 1e3, 3), "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": f"dense out-of-core t-SVD, m={m}, n={N_COLS}, k={K}, eps={EPS}", "m": m,
-                       "n": N_COLS, "k": K, "eps": EPS, "block_rows": BLOCK_ROWS},
+            "config": dense_config(m, args.precision, 1),
             "cpu_baseline": {"value": round(value, 3), "unit": "GB/s", "cores": cores, "kind": "oracle",
                              "sample": f"one {rows}-row block per step: FP64 Gram + left vectors; power phase "
                                        f"excluded (O(n^2) per iteration, independent of m)"},
@@ -1827,16 +1841,7 @@ def main():
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(step_s * 1e3, 2),
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                 "dtype": PREC_NAMES[prec], "data": "synthetic",
-                "config": {"workload": f"dense t-SVD (rank-64 + 1e-4 noise), m={m}, n={N_COLS}, k={K}, eps={EPS}; "
-                                       "value: A resident in HBM (in-core); e2e: A streamed from page-locked host "
-                                       f"memory under a {BUDGET / 1e9:.0f} GB device budget (out-of-core)",
-                           "m": m, "n": N_COLS, "k": K, "eps": EPS,
-                           "block_rows": BLOCK_ROWS, "device_budget_bytes_e2e": BUDGET,
-                           "full_m": FULL_M, "host_ram_limited": m < FULL_M,
-                           "l2": "inputs larger than L2 (A is %.0f GiB)" % (m * N_COLS * 4 / 2 ** 30),
-                           "gram_precision": PREC_NAMES[prec] + (" (FP32-class split: hi*hi + hi*lo + lo*hi on the "
-                                                                 "tensor cores, FP32 accumulate)" if prec == 2 else ""),
-                           "parallelism": "replicas" if world > 1 else "1 GPU"},
+                "config": dense_config(m, prec, world),
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk, "tf32_in_core": alt, "bf16x3_in_core": alt_bf,
                 "c1_latency": small,
                 "gpu_launches": launches, "gpu_launches_e2e": launches_e,
